@@ -1,0 +1,182 @@
+/*
+ * ns.h - C ABI of the GB300 (sm_103a) fractional-step Navier-Stokes hot path.
+ *
+ * The method (Ha, Park & You, arXiv:1812.01178):
+ *   Sec. 2.1  incompressible NS, Eq. (NScontinuity) and Eq. (NSmomentum), on a staggered grid:
+ *             u on x-faces, v on y-faces, w on z-faces, p at cell centres; uniform x and z,
+ *             wall-clustered y; no-slip wall at the bottom, no-slip or stress-free top;
+ *             periodic z (and periodic x for channel flow).
+ *   Sec. 2.2  semi-implicit fractional step: low-storage RK3 (convection) + Crank-Nicolson
+ *             (viscous), ADI factorisation into tridiagonal solves along x, y and z, Poisson
+ *             equation by Fourier transforms in x and z plus tridiagonal solves in y, projection
+ *             with the pseudo-pressure phi.
+ *   Sec. 3.2  PDD / PPT divide-and-conquer solution of tridiagonal systems, Eqs. (smidentity)
+ *             to (xppt): used here for the contiguous x-lines, split across the lanes of a warp.
+ *
+ * Units and layout.  Every field is a dense array of double with x fastest, then y, then z:
+ *   u : nz * ny     * nx   (x-face i, y-centre j, z-centre k)
+ *   v : nz * (ny+1) * nx   (x-centre i, y-face j, z-centre k); rows j = 0 and j = ny are the
+ *                          walls and hold 0
+ *   w : nz * ny     * nx   (x-centre i, y-centre j, z-face k)
+ *   p : nz * ny     * nx   (cell centres)
+ * Element (i, j, k) of u is u[(k * ny + j) * nx + i].  All device pointers must be 256-byte
+ * aligned (cudaMalloc / torch allocations are).  nx must be even, and nx and nz must be
+ * powers of two in [8, 4096].  ny is in [4, 1024].
+ *
+ * Ownership.  Fields and the workspace are allocated by the caller (device memory) and are
+ * never freed by the library.  The library owns only the opaque context (host memory) and the
+ * CUDA graph it captures.  If ns_init gets workspace == NULL, the library allocates the
+ * workspace itself with cudaMalloc and frees it in ns_destroy.
+ *
+ * Streams.  All work is enqueued on the stream passed to ns_init (a cudaStream_t cast to
+ * void*; NULL means the legacy default stream).  No call synchronises the host except
+ * ns_sync and the *_host entry points.
+ *
+ * Errors.  Every call returns an ns_status.  Argument errors are detected before any work is
+ * enqueued.  Asynchronous CUDA failures surface as NS_ERR_CUDA at the next call that checks
+ * the stream (ns_sync, ns_step_host).  ns_last_error(ctx) gives a one-line message.  No call
+ * aborts the process or throws.
+ */
+#ifndef NS_GB300_H
+#define NS_GB300_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ns_ctx ns_ctx;
+
+typedef enum {
+  NS_OK = 0,
+  NS_ERR_ARG = 1,        /* NULL pointer, bad enum value, misaligned pointer */
+  NS_ERR_SIZE = 2,       /* grid size outside the supported range */
+  NS_ERR_CUDA = 3,       /* a CUDA runtime call or kernel launch failed */
+  NS_ERR_TIMEOUT = 4,    /* a bounded device-side wait gave up (status word set) */
+  NS_ERR_STATE = 5,      /* call made in the wrong state (e.g. during graph capture) */
+  NS_ERR_UNSUPPORTED = 6 /* option not built */
+} ns_status;
+
+/* Precision of the increment path (Sec. 2.2 solves everything in one precision; the mixed
+ * form is this library's addition):
+ *   NS_FP64  : every stage in FP64.
+ *   NS_MIXED : RHS stencils and the ADI increment solves in FP32 (r, delta and N_prev stored
+ *              as float); state accumulation u* = u + delta, divergence, the Poisson solve
+ *              (all modes) and the projection stay FP64. */
+enum { NS_FP64 = 0, NS_MIXED = 1 };
+
+typedef struct {
+  int nx, ny, nz;        /* cells in x, y, z */
+  double lx, lz;         /* domain lengths in the periodic directions */
+  const double* yf;      /* ny+1 strictly increasing y-face coordinates, HOST memory, read
+                            only during ns_init (Sec. 2.1: wall-clustered y grid) */
+  int bc_x;              /* 0: periodic x.  1 (inflow / convective outflow) is not built:
+                            NS_ERR_UNSUPPORTED */
+  int bc_ytop;           /* 0: no-slip top wall, 1: stress-free top (v = 0, du/dy = dw/dy = 0) */
+  double re;             /* Reynolds number of Eq. (NSmomentum); re <= 0 means inviscid */
+  double fx;             /* constant body force along x (drives channel flow) */
+  double dt;             /* time step, fixed for the lifetime of the context */
+  int precision;         /* NS_FP64 or NS_MIXED */
+} ns_config;
+
+typedef struct {
+  double* u;             /* device pointers, layouts above; updated in place */
+  double* v;
+  double* w;
+  double* p;
+} ns_fields;
+
+/* Workspace bytes needed by ns_init for this configuration (0 if cfg is invalid). */
+size_t ns_workspace_bytes(const ns_config* cfg);
+
+/* Create a context: validates cfg, computes the line-independent coefficient tables of every
+ * ADI factor (Sec. 2.2) and of the partitioned x solver (Sec. 3.2: spikes v, w of Eq. (blockAY)
+ * and the reduced-system eliminators), the Poisson y factors per (kx, kz) and the FFT twiddles,
+ * and stores them in the workspace.  `fields` are the caller's state arrays (N_prev is kept in
+ * the workspace).  Returns NS_ERR_SIZE / NS_ERR_ARG / NS_ERR_UNSUPPORTED / NS_ERR_CUDA. */
+ns_status ns_init(ns_ctx** out, const ns_config* cfg, const ns_fields* fields,
+                  void* workspace, size_t ws_bytes, void* cuda_stream);
+
+/* Explicit right-hand side of RK3 sub-step `substep` (0, 1, 2), Sec. 2.2 in delta form:
+ *   r_i = dt [ -gamma_k N_i(u) - zeta_k N_prev_i - alpha_k G_i p + (alpha_k/Re) L u_i + alpha_k f_i ]
+ * with N = divergence-form convection (Eq. NSmomentum, 2nd-order central), L the viscous
+ * operator and G the pressure gradient.  Writes r into the workspace buffers NS_BUF_RU/RV/RW
+ * and N(u) into NS_BUF_NU/NV/NW (it is N_prev of the next sub-step; substep 0 ignores it). */
+ns_status ns_rhs(ns_ctx* ctx, int substep);
+
+/* One ADI factor (Sec. 2.2): solves (I - beta_k delta_dd) x = r in place on the r buffers for
+ * all three components, beta_k = alpha_k dt / (2 Re).
+ *   dir 0: x-lines (contiguous, periodic): each line split into P partitions across the lanes
+ *          of a warp and solved with PDD or PPT (Sec. 3.2, Eqs. blockAx - xppt).
+ *   dir 1: y-lines (stride nx), one thread per line, precomputed Thomas factors.
+ *   dir 2: z-lines (stride nx*ny, periodic), one thread per line; then forms the intermediate
+ *          velocity u* = u + delta in the caller's u, v, w (FP64 accumulation). */
+ns_status ns_adi_sweep(ns_ctx* ctx, int dir, int substep);
+
+/* Pressure Poisson solve of sub-step `substep` (Sec. 2.2): b = D u* / (alpha_k dt); forward
+ * real FFT along z and complex FFT along x; one complex tridiagonal solve along y per (kx, kz)
+ * with zero normal gradient at both y boundaries (the singular (0,0) mode is gauged by
+ * phi_hat(j=0) = 0); inverse FFTs.  Writes phi into NS_BUF_PHI.  substep = -1 uses scale 1
+ * (b = D u), for making an initial field divergence-free. */
+ns_status ns_poisson_solve(ns_ctx* ctx, int substep);
+
+/* Projection of sub-step `substep` (Sec. 2.2): u = u* - alpha_k dt G phi, p = p + phi.
+ * substep = -1 projects with scale 1 and leaves p unchanged. */
+ns_status ns_project(ns_ctx* ctx, int substep);
+
+/* One full RK3 sub-step: ns_rhs, ns_adi_sweep x/y/z, ns_poisson_solve, ns_project. */
+ns_status ns_substep(ns_ctx* ctx, int substep);
+
+/* nsteps time steps of three sub-steps each (Table 1 counts one step = three sub-steps).
+ * The three sub-steps are captured once as a CUDA graph and replayed. */
+ns_status ns_step(ns_ctx* ctx, int nsteps);
+
+/* End-to-end variant of ns_step for callers whose state lives in HOST memory: copies u, v, w,
+ * p from the host arrays (pinned memory recommended) to the context's device fields, runs
+ * nsteps steps, copies them back and synchronises.  Host arrays use the device layout. */
+ns_status ns_step_host(ns_ctx* ctx, double* u, double* v, double* w, double* p, int nsteps);
+
+/* Make the current velocity discretely divergence-free (ns_poisson_solve(-1) + ns_project(-1)). */
+ns_status ns_make_divergence_free(ns_ctx* ctx);
+
+/* Partitioning of the x-line solver (Sec. 3.2): P partitions per line (a power of two from
+ * 1 to 32 dividing nx, with nx/P <= 16), mode 0 = automatic (PDD when the coupling PDD drops
+ * is below its tolerance for every sub-step, else PPT), 1 = PPT, 2 = PDD.  Rebuilds the tables
+ * and drops the captured graph.  dir must be 0. */
+enum { NS_PART_AUTO = 0, NS_PART_PPT = 1, NS_PART_PDD = 2 };
+ns_status ns_set_partition(ns_ctx* ctx, int dir, int P, int mode);
+
+/* Query the partitioning in use: *P, *mode (NS_PART_PPT or NS_PART_PDD) and the largest
+ * coupling PDD drops over the three sub-steps (the admissibility measure). */
+ns_status ns_get_partition(ns_ctx* ctx, int dir, int* P, int* mode, double* pdd_dropped);
+
+/* Pick P and the PDD/PPT mode for the x solver by timing every admissible P on the context's
+ * stream (CUDA events).  Leaves the fastest installed. */
+ns_status ns_autotune(ns_ctx* ctx);
+
+/* Workspace buffers, for inspection and for stage-by-stage testing. */
+enum {
+  NS_BUF_RU = 0, NS_BUF_RV = 1, NS_BUF_RW = 2,   /* r / delta (double, or float if NS_MIXED) */
+  NS_BUF_NU = 3, NS_BUF_NV = 4, NS_BUF_NW = 5,   /* N_prev (double, or float if NS_MIXED) */
+  NS_BUF_PHI = 6,                               /* phi, double, nz*ny*nx */
+  NS_BUF_SPEC = 7                               /* spectral buffer, complex double,
+                                                   (nz/2+1)*ny*nx, layout [kz][j][kx] */
+};
+ns_status ns_get_buffer(ns_ctx* ctx, int which, void** ptr, size_t* bytes);
+
+/* Wait for all work on the context's stream; reports asynchronous CUDA errors. */
+ns_status ns_sync(ns_ctx* ctx);
+
+/* Last error message of the context (never NULL; "" when none).  ctx may be NULL, giving the
+ * message of the last failed ns_init on this thread. */
+const char* ns_last_error(ns_ctx* ctx);
+
+/* Destroy the context (frees the graph and a library-allocated workspace, not the fields). */
+void ns_destroy(ns_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NS_GB300_H */

@@ -1,0 +1,278 @@
+"""Thin ctypes binding of the C ABI in include/ns.h (argument marshalling only).
+
+Every computation runs in the CUDA library libns_gb300.so built from csrc/ (see build.py).
+There is no CPU or PyTorch fallback: if the library is missing or fails to load, importing
+this module's `lib()` raises.  PyTorch is used only to own device memory and streams.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "libns_gb300.so")
+
+NS_OK, NS_ERR_ARG, NS_ERR_SIZE, NS_ERR_CUDA, NS_ERR_TIMEOUT, NS_ERR_STATE, NS_ERR_UNSUPPORTED = range(7)
+NS_FP64, NS_MIXED = 0, 1
+NS_PART_AUTO, NS_PART_PPT, NS_PART_PDD = 0, 1, 2
+NS_BUF_RU, NS_BUF_RV, NS_BUF_RW, NS_BUF_NU, NS_BUF_NV, NS_BUF_NW, NS_BUF_PHI, NS_BUF_SPEC = range(8)
+
+STATUS_NAMES = {0: "NS_OK", 1: "NS_ERR_ARG", 2: "NS_ERR_SIZE", 3: "NS_ERR_CUDA", 4: "NS_ERR_TIMEOUT",
+                5: "NS_ERR_STATE", 6: "NS_ERR_UNSUPPORTED"}
+
+# Every symbol declared in include/ns.h.
+EXPORTS = ["ns_workspace_bytes", "ns_init", "ns_rhs", "ns_adi_sweep", "ns_poisson_solve", "ns_project",
+           "ns_substep", "ns_step", "ns_step_host", "ns_make_divergence_free", "ns_set_partition",
+           "ns_get_partition", "ns_autotune", "ns_get_buffer", "ns_sync", "ns_last_error", "ns_destroy"]
+
+
+class ns_config(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
+                ("lx", C.c_double), ("lz", C.c_double),
+                ("yf", C.POINTER(C.c_double)),
+                ("bc_x", C.c_int), ("bc_ytop", C.c_int),
+                ("re", C.c_double), ("fx", C.c_double), ("dt", C.c_double),
+                ("precision", C.c_int)]
+
+
+class ns_fields(C.Structure):
+    _fields_ = [("u", C.c_void_p), ("v", C.c_void_p), ("w", C.c_void_p), ("p", C.c_void_p)]
+
+
+class NSError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), msg))
+        self.status = status
+
+
+_LIB = None
+
+
+def lib(path: str = LIB_PATH):
+    """Load the CUDA library (raises if it is missing: there is no fallback)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    if not os.path.exists(path):
+        raise RuntimeError("CUDA library %s is missing: run paper_1812_01178_gb300/build.py "
+                           "(or __graft_entry__.build())" % path)
+    L = C.CDLL(path)
+    vp, i, d, sz = C.c_void_p, C.c_int, C.c_double, C.c_size_t
+    P = C.POINTER
+    L.ns_workspace_bytes.argtypes = [P(ns_config)]
+    L.ns_workspace_bytes.restype = sz
+    L.ns_init.argtypes = [P(vp), P(ns_config), P(ns_fields), vp, sz, vp]
+    for name in ("ns_rhs", "ns_poisson_solve", "ns_project", "ns_substep", "ns_step"):
+        getattr(L, name).argtypes = [vp, i]
+    L.ns_adi_sweep.argtypes = [vp, i, i]
+    L.ns_step_host.argtypes = [vp, vp, vp, vp, vp, i]
+    L.ns_make_divergence_free.argtypes = [vp]
+    L.ns_set_partition.argtypes = [vp, i, i, i]
+    L.ns_get_partition.argtypes = [vp, i, P(i), P(i), P(d)]
+    L.ns_autotune.argtypes = [vp]
+    L.ns_get_buffer.argtypes = [vp, i, P(vp), P(sz)]
+    L.ns_sync.argtypes = [vp]
+    L.ns_last_error.argtypes = [vp]
+    L.ns_last_error.restype = C.c_char_p
+    L.ns_destroy.argtypes = [vp]
+    L.ns_destroy.restype = None
+    for name in EXPORTS:
+        if name not in ("ns_workspace_bytes", "ns_last_error", "ns_destroy"):
+            getattr(L, name).restype = i
+    _LIB = L
+    return L
+
+
+def make_config(case, precision=None):
+    """ns_config from an inputs.Case (keeps the yf array alive on the returned object)."""
+    yf = np.ascontiguousarray(case.yf, dtype=np.float64)
+    cfg = ns_config(case.nx, case.ny, case.nz, case.lx, case.lz,
+                    yf.ctypes.data_as(C.POINTER(C.c_double)), case.bc_x, case.bc_ytop,
+                    case.re, case.fx, case.dt, case.precision if precision is None else precision)
+    cfg._yf_keep = yf
+    return cfg
+
+
+# ---------------------------------------------------------------------- C-ABI names
+def ns_workspace_bytes(cfg):
+    return lib().ns_workspace_bytes(C.byref(cfg))
+
+
+def _check(ctx, status):
+    if status != NS_OK:
+        raise NSError(status, lib().ns_last_error(ctx).decode())
+
+
+def ns_init(cfg, fields, workspace_ptr, ws_bytes, stream_ptr):
+    ctx = C.c_void_p()
+    s = lib().ns_init(C.byref(ctx), C.byref(cfg), C.byref(fields), workspace_ptr, ws_bytes, stream_ptr)
+    if s != NS_OK:
+        raise NSError(s, lib().ns_last_error(None).decode())
+    return ctx
+
+
+def ns_rhs(ctx, k):
+    _check(ctx, lib().ns_rhs(ctx, k))
+
+
+def ns_adi_sweep(ctx, direction, k):
+    _check(ctx, lib().ns_adi_sweep(ctx, direction, k))
+
+
+def ns_poisson_solve(ctx, k):
+    _check(ctx, lib().ns_poisson_solve(ctx, k))
+
+
+def ns_project(ctx, k):
+    _check(ctx, lib().ns_project(ctx, k))
+
+
+def ns_substep(ctx, k):
+    _check(ctx, lib().ns_substep(ctx, k))
+
+
+def ns_step(ctx, nsteps):
+    _check(ctx, lib().ns_step(ctx, nsteps))
+
+
+def ns_step_host(ctx, u, v, w, p, nsteps):
+    """u, v, w, p: C-contiguous float64 host arrays (pinned recommended), updated in place."""
+    _check(ctx, lib().ns_step_host(ctx, u.ctypes.data, v.ctypes.data, w.ctypes.data, p.ctypes.data, nsteps))
+
+
+def ns_make_divergence_free(ctx):
+    _check(ctx, lib().ns_make_divergence_free(ctx))
+
+
+def ns_set_partition(ctx, direction, P, mode):
+    _check(ctx, lib().ns_set_partition(ctx, direction, P, mode))
+
+
+def ns_get_partition(ctx, direction=0):
+    P, mode, drop = C.c_int(), C.c_int(), C.c_double()
+    _check(ctx, lib().ns_get_partition(ctx, direction, C.byref(P), C.byref(mode), C.byref(drop)))
+    return P.value, mode.value, drop.value
+
+
+def ns_autotune(ctx):
+    _check(ctx, lib().ns_autotune(ctx))
+
+
+def ns_get_buffer(ctx, which):
+    ptr, n = C.c_void_p(), C.c_size_t()
+    _check(ctx, lib().ns_get_buffer(ctx, which, C.byref(ptr), C.byref(n)))
+    return ptr.value, n.value
+
+
+def ns_sync(ctx):
+    _check(ctx, lib().ns_sync(ctx))
+
+
+def ns_last_error(ctx):
+    return lib().ns_last_error(ctx).decode()
+
+
+def ns_destroy(ctx):
+    lib().ns_destroy(ctx)
+
+
+# ---------------------------------------------------------------------- convenience owner
+class Solver:
+    """Owns torch device tensors for the fields and the workspace of one context.
+
+    Fields are float64 CUDA tensors with the layouts of include/ns.h.  Every method calls the
+    C ABI; nothing is computed in Python or PyTorch.
+    """
+
+    def __init__(self, case, u=None, v=None, w=None, p=None, precision=None, device="cuda:0", stream=None):
+        import torch
+        self.torch = torch
+        self.case = case
+        self.cfg = make_config(case, precision)
+        dev = torch.device(device)
+        nx, ny, nz = case.nx, case.ny, case.nz
+
+        def put(a, shape):
+            if a is None:
+                return torch.zeros(shape, dtype=torch.float64, device=dev)
+            t = torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64)).to(dev)
+            assert tuple(t.shape) == shape, (t.shape, shape)
+            return t.contiguous()
+
+        self.u = put(u, (nz, ny, nx))
+        self.v = put(v, (nz, ny + 1, nx))
+        self.w = put(w, (nz, ny, nx))
+        self.p = put(p, (nz, ny, nx))
+        nbytes = ns_workspace_bytes(self.cfg)
+        if nbytes == 0:
+            raise NSError(NS_ERR_SIZE, "invalid configuration")
+        self.ws = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(dev)
+        self.fields = ns_fields(self.u.data_ptr(), self.v.data_ptr(), self.w.data_ptr(), self.p.data_ptr())
+        self.ctx = ns_init(self.cfg, self.fields, self.ws.data_ptr(), nbytes, self.stream.cuda_stream)
+        self.es = 4 if self.cfg.precision == NS_MIXED else 8
+
+    # views of workspace buffers as torch tensors
+    def buffer(self, which):
+        torch = self.torch
+        ptr, n = ns_get_buffer(self.ctx, which)
+        off = ptr - self.ws.data_ptr()
+        raw = self.ws[off:off + n]
+        c = self.case
+        if which == NS_BUF_SPEC:
+            return raw.view(torch.float64).view(c.nz // 2 + 1, c.ny, c.nx, 2)
+        if which == NS_BUF_PHI:
+            return raw.view(torch.float64).view(c.nz, c.ny, c.nx)
+        dt = torch.float32 if self.es == 4 else torch.float64
+        rows = c.ny + 1 if which in (NS_BUF_RV, NS_BUF_NV) else c.ny
+        return raw.view(dt).view(c.nz, rows, c.nx)
+
+    def rhs(self, k):
+        ns_rhs(self.ctx, k)
+
+    def adi(self, direction, k):
+        ns_adi_sweep(self.ctx, direction, k)
+
+    def poisson(self, k):
+        ns_poisson_solve(self.ctx, k)
+
+    def project(self, k):
+        ns_project(self.ctx, k)
+
+    def substep(self, k):
+        ns_substep(self.ctx, k)
+
+    def step(self, n=1):
+        ns_step(self.ctx, n)
+
+    def make_divergence_free(self):
+        ns_make_divergence_free(self.ctx)
+
+    def set_partition(self, P, mode=NS_PART_AUTO):
+        ns_set_partition(self.ctx, 0, P, mode)
+
+    def partition(self):
+        return ns_get_partition(self.ctx, 0)
+
+    def autotune(self):
+        ns_autotune(self.ctx)
+
+    def sync(self):
+        ns_sync(self.ctx)
+
+    def state(self):
+        self.sync()
+        return tuple(t.cpu().numpy() for t in (self.u, self.v, self.w, self.p))
+
+    def close(self):
+        if getattr(self, "ctx", None) is not None:
+            ns_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,311 @@
+// ADI factors of the momentum increment (Sec. 2.2):  (I - b d_xx)(I - b d_yy)(I - b d_zz) delta = r.
+//
+// x: lines are contiguous and periodic.  Each line is split into P partitions of M rows, one
+//    partition per lane of a team of P lanes (Sec. 3.2, the PDD / PPT divide-and-conquer scheme
+//    moved from MPI ranks to warp lanes):
+//      A~ x~ = d                 (Eq. blockAx)  block Thomas with precomputed factors
+//      A~ Y  = V                 (Eq. blockAY)  spikes v, w: line-independent, precomputed
+//      Z y   = E^T x~            (Eq. Zpdd)     interface unknowns y = (x^{(r)}_m, x^{(r+1)}_1)
+//      x     = x~ - Y y          (Eq. xpdd)
+//    PDD keeps only the 2x2 diagonal blocks of Z; PPT solves all of Z exactly by block parallel
+//    cyclic reduction over the team with warp shuffles (line-independent eliminators).
+// y: lines have stride nx; one thread per line, Thomas with precomputed factors.
+// z: lines have stride nx*ny and are periodic; one thread per line, Thomas on the Sherman-
+//    Morrison-modified matrix plus the rank-one correction; then u* = u + delta (FP64).
+#include "ns_internal.cuh"
+
+namespace {
+
+// ----------------------------------------------------------------------------------------------
+// x: partitioned solve
+// ----------------------------------------------------------------------------------------------
+template <typename T>
+struct AdiXArgs {
+  const T* __restrict__ tab;
+  T* r[3];
+  int nx, ny, nz, P, L;
+  long nlines;  // nz*ny (u) + nz*(ny-1) (v) + nz*ny (w)
+};
+
+template <typename T, int M>
+__device__ __forceinline__ void load_part(const T* __restrict__ src, T (&d)[M]) {
+  if constexpr (sizeof(T) * M % 16 == 0) {
+    constexpr int V = 16 / sizeof(T);
+#pragma unroll
+    for (int e = 0; e < M; e += V) {
+      if constexpr (sizeof(T) == 8) {
+        const double2 t = *reinterpret_cast<const double2*>(src + e);
+        d[e] = t.x;
+        d[e + 1] = t.y;
+      } else {
+        const float4 t = *reinterpret_cast<const float4*>(src + e);
+        d[e] = t.x;
+        d[e + 1] = t.y;
+        d[e + 2] = t.z;
+        d[e + 3] = t.w;
+      }
+    }
+  } else {
+#pragma unroll
+    for (int e = 0; e < M; ++e) d[e] = src[e];
+  }
+}
+
+template <typename T, int M>
+__device__ __forceinline__ void store_part(T* __restrict__ dst, const T (&d)[M]) {
+  if constexpr (sizeof(T) * M % 16 == 0) {
+    constexpr int V = 16 / sizeof(T);
+#pragma unroll
+    for (int e = 0; e < M; e += V) {
+      if constexpr (sizeof(T) == 8) {
+        *reinterpret_cast<double2*>(dst + e) = make_double2(d[e], d[e + 1]);
+      } else {
+        *reinterpret_cast<float4*>(dst + e) = make_float4(d[e], d[e + 1], d[e + 2], d[e + 3]);
+      }
+    }
+  } else {
+#pragma unroll
+    for (int e = 0; e < M; ++e) dst[e] = d[e];
+  }
+}
+
+template <typename T, int M>
+__global__ void __launch_bounds__(256) adi_x_kernel(AdiXArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* st = reinterpret_cast<T*>(smem_raw);
+  const int P = a.P, L = a.L;
+  const int ntab = (int)xtab_count(M, P, L);
+  for (int q = threadIdx.x; q < ntab; q += blockDim.x) st[q] = a.tab[q];
+  __syncthreads();
+
+  const int lane = threadIdx.x & 31;
+  const int r = lane & (P - 1);
+  const int team = lane / P;
+  const int teams = 32 / P;
+  const T* INV = st + XT_INV * M * P;
+  const T* AINV = st + XT_AINV * M * P;
+  const T* CP = st + XT_CP * M * P;
+  const T* SV = st + XT_V * M * P;
+  const T* SW = st + XT_W * M * P;
+  const T* DINV = st + XT_NF * M * P;
+  const T* ML = DINV + 4 * P;
+  const T* MU = ML + 4 * L * P;
+
+  const int nx = a.nx, ny = a.ny;
+  const long Lu = (long)a.nz * ny;
+  const long Lv = (long)a.nz * (ny - 1);
+  const long warp = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long nwarps = ((long)gridDim.x * blockDim.x) >> 5;
+
+  for (long l0 = warp * teams; l0 < a.nlines; l0 += nwarps * teams) {
+    const long line = l0 + team;
+    const bool valid = line < a.nlines;
+    T* row = nullptr;
+    if (valid) {
+      if (line < Lu) {
+        row = a.r[0] + line * nx;
+      } else if (line < Lu + Lv) {
+        const long q = line - Lu;
+        const long kk = q / (ny - 1);
+        const long jj = 1 + (q - kk * (ny - 1));
+        row = a.r[1] + (kk * (ny + 1) + jj) * nx;
+      } else {
+        row = a.r[2] + (line - Lu - Lv) * nx;
+      }
+    }
+    T d[M];
+    if (valid) {
+      load_part<T, M>(row + r * M, d);
+    } else {
+#pragma unroll
+      for (int e = 0; e < M; ++e) d[e] = (T)0;
+    }
+    // A~ x~ = d on this partition (forward elimination, back substitution)
+    d[0] = d[0] * INV[r];
+#pragma unroll
+    for (int e = 1; e < M; ++e) d[e] = d[e] * INV[e * P + r] - AINV[e * P + r] * d[e - 1];
+#pragma unroll
+    for (int e = M - 2; e >= 0; --e) d[e] = d[e] - CP[e * P + r] * d[e + 1];
+    // interface r: g = (x~^{(r)}_m, x~^{(r+1)}_1)
+    T g0 = d[M - 1];
+    T g1 = __shfl_sync(NS_FULL_MASK, d[0], r + 1, P);
+    // reduced system: block PCR (PPT) over the team; L = 0 gives PDD
+    for (int lv = 0, s = 1; lv < L; ++lv, s <<= 1) {
+      const T h0 = __shfl_sync(NS_FULL_MASK, g0, r - s + P, P);
+      const T h1 = __shfl_sync(NS_FULL_MASK, g1, r - s + P, P);
+      const T k0 = __shfl_sync(NS_FULL_MASK, g0, r + s, P);
+      const T k1 = __shfl_sync(NS_FULL_MASK, g1, r + s, P);
+      const T* ml = ML + 4 * lv * P;
+      const T* mu = MU + 4 * lv * P;
+      const T n0 = g0 - ml[r] * h0 - ml[P + r] * h1 - mu[r] * k0 - mu[P + r] * k1;
+      const T n1 = g1 - ml[2 * P + r] * h0 - ml[3 * P + r] * h1 - mu[2 * P + r] * k0 - mu[3 * P + r] * k1;
+      g0 = n0;
+      g1 = n1;
+    }
+    const T y0 = DINV[r] * g0 + DINV[P + r] * g1;      // x^{(r)}_m
+    const T y1 = DINV[2 * P + r] * g0 + DINV[3 * P + r] * g1;  // x^{(r+1)}_1
+    const T left = __shfl_sync(NS_FULL_MASK, y0, r - 1 + P, P);  // x^{(r-1)}_m
+    // x = x~ - v x^{(r-1)}_m - w x^{(r+1)}_1
+#pragma unroll
+    for (int e = 0; e < M; ++e) d[e] = d[e] - SV[e * P + r] * left - SW[e * P + r] * y1;
+    if (valid) store_part<T, M>(row + r * M, d);
+  }
+}
+
+// ----------------------------------------------------------------------------------------------
+// y: one thread per line, Thomas with precomputed factors [INV, AINV, CP][n]
+// ----------------------------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(128) adi_y_kernel(T* __restrict__ ru, T* __restrict__ rv, T* __restrict__ rw,
+                                                    const T* __restrict__ tc, const T* __restrict__ tf, int nx,
+                                                    int ny, int nz) {
+  const int comp = blockIdx.z;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int k = blockIdx.y;
+  if (i >= nx) return;
+  T* line;
+  const T* tab;
+  int n;
+  if (comp == 1) {
+    line = rv + ((long)k * (ny + 1) + 1) * nx + i;
+    tab = tf;
+    n = ny - 1;
+  } else {
+    line = (comp == 0 ? ru : rw) + (long)k * ny * nx + i;
+    tab = tc;
+    n = ny;
+  }
+  const T* INV = tab;
+  const T* AINV = tab + n;
+  const T* CP = tab + 2 * n;
+  T prev = line[0] * __ldg(INV);
+  line[0] = prev;
+  for (int j = 1; j < n; ++j) {
+    const long o = (long)j * nx;
+    prev = line[o] * __ldg(INV + j) - __ldg(AINV + j) * prev;
+    line[o] = prev;
+  }
+  T next = prev;
+  for (int j = n - 2; j >= 0; --j) {
+    const long o = (long)j * nx;
+    next = line[o] - __ldg(CP + j) * next;
+    line[o] = next;
+  }
+}
+
+// ----------------------------------------------------------------------------------------------
+// z: one thread per line, cyclic (Sherman-Morrison), then u* = u + delta.
+// table: [INV, AINV, CP, Q][nz] then (FAC, BG)
+// ----------------------------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(128) adi_z_kernel(T* __restrict__ ru, T* __restrict__ rv, T* __restrict__ rw,
+                                                    double* __restrict__ u, double* __restrict__ v,
+                                                    double* __restrict__ w, const T* __restrict__ tab, int nx,
+                                                    int ny, int nz) {
+  const int comp = blockIdx.z;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y + (comp == 1 ? 1 : 0);
+  if (i >= nx) return;
+  if (comp == 1 && j > ny - 1) return;
+  const int rows = comp == 1 ? ny + 1 : ny;
+  const long stride = (long)rows * nx;
+  const long base = (long)j * nx + i;
+  T* line = (comp == 0 ? ru : comp == 1 ? rv : rw) + base;
+  double* f = (comp == 0 ? u : comp == 1 ? v : w) + base;
+  const T* INV = tab;
+  const T* AINV = tab + nz;
+  const T* CP = tab + 2 * nz;
+  const T* Q = tab + 3 * nz;
+  const T fac = __ldg(tab + 4 * nz);
+  const T bg = __ldg(tab + 4 * nz + 1);
+  T prev = line[0] * __ldg(INV);
+  line[0] = prev;
+  for (int kk = 1; kk < nz; ++kk) {
+    const long o = kk * stride;
+    prev = line[o] * __ldg(INV + kk) - __ldg(AINV + kk) * prev;
+    line[o] = prev;
+  }
+  const T ylast = prev;
+  T next = prev;
+  for (int kk = nz - 2; kk >= 0; --kk) {
+    const long o = kk * stride;
+    next = line[o] - __ldg(CP + kk) * next;
+    line[o] = next;
+  }
+  const T corr = (next + bg * ylast) * fac;
+  for (int kk = 0; kk < nz; ++kk) {
+    const long o = kk * stride;
+    const T x = line[o] - corr * __ldg(Q + kk);
+    f[o] = f[o] + (double)x;
+  }
+}
+
+template <typename T, int M>
+cudaError_t launch_x_t(ns_ctx* c, int k) {
+  AdiXArgs<T> a;
+  a.tab = (const T*)c->xtab[k];
+  a.r[0] = (T*)c->ru;
+  a.r[1] = (T*)c->rv;
+  a.r[2] = (T*)c->rw;
+  a.nx = c->cfg.nx;
+  a.ny = c->cfg.ny;
+  a.nz = c->cfg.nz;
+  a.P = c->P;
+  a.L = c->L[k];
+  a.nlines = (long)a.nz * a.ny * 2 + (long)a.nz * (a.ny - 1);
+  const size_t smem = xtab_count(M, a.P, a.L) * sizeof(T);
+  const long teams_per_block = 8L * (32 / a.P);
+  long blocks = (a.nlines + teams_per_block - 1) / teams_per_block;
+  if (blocks > 152L * 16) blocks = 152L * 16;
+  if (smem > 48 * 1024) cudaFuncSetAttribute(adi_x_kernel<T, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  adi_x_kernel<T, M><<<(unsigned)blocks, 256, smem, c->launch>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_x_m(ns_ctx* c, int k) {
+  switch (c->M) {
+    case 1: return launch_x_t<T, 1>(c, k);
+    case 2: return launch_x_t<T, 2>(c, k);
+    case 4: return launch_x_t<T, 4>(c, k);
+    case 8: return launch_x_t<T, 8>(c, k);
+    case 16: return launch_x_t<T, 16>(c, k);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_adi_x(ns_ctx* c, int k) {
+  if (c->cfg.precision == NS_MIXED) return launch_x_m<float>(c, k);
+  return launch_x_m<double>(c, k);
+}
+
+cudaError_t launch_adi_y(ns_ctx* c, int k) {
+  const int nx = c->cfg.nx, ny = c->cfg.ny, nz = c->cfg.nz;
+  dim3 grid((nx + 127) / 128, nz, 3);
+  if (c->cfg.precision == NS_MIXED)
+    adi_y_kernel<float><<<grid, 128, 0, c->launch>>>((float*)c->ru, (float*)c->rv, (float*)c->rw,
+                                                     (const float*)c->ytab[k][0], (const float*)c->ytab[k][1], nx,
+                                                     ny, nz);
+  else
+    adi_y_kernel<double><<<grid, 128, 0, c->launch>>>((double*)c->ru, (double*)c->rv, (double*)c->rw,
+                                                      (const double*)c->ytab[k][0], (const double*)c->ytab[k][1],
+                                                      nx, ny, nz);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adi_z(ns_ctx* c, int k) {
+  const int nx = c->cfg.nx, ny = c->cfg.ny, nz = c->cfg.nz;
+  dim3 grid((nx + 127) / 128, ny, 3);
+  if (c->cfg.precision == NS_MIXED)
+    adi_z_kernel<float><<<grid, 128, 0, c->launch>>>((float*)c->ru, (float*)c->rv, (float*)c->rw, c->f.u, c->f.v,
+                                                     c->f.w, (const float*)c->ztab[k], nx, ny, nz);
+  else
+    adi_z_kernel<double><<<grid, 128, 0, c->launch>>>((double*)c->ru, (double*)c->rv, (double*)c->rw, c->f.u,
+                                                      c->f.v, c->f.w, (const double*)c->ztab[k], nx, ny, nz);
+  return cudaGetLastError();
+}
+
+size_t adi_y_tab_count(int ny) { return 3 * (size_t)ny; }
+size_t adi_z_tab_count(int nz) { return 4 * (size_t)nz + 2; }

@@ -1,0 +1,333 @@
+// Pressure Poisson solve and projection (Sec. 2.2), FP64 throughout.
+//
+//   b = D u* / (alpha_k dt)                      divergence at cell centres
+//   b^(kx, j, kz) = FFT_x FFT_z b                 real FFT along z (two real columns packed into
+//                                                 one complex sequence), complex FFT along x
+//   for every (kx, kz): complex tridiagonal solve in y with rows
+//     a_j phi_{j-1} - (a_j + c_j + lam_x + lam_z) phi_j + c_j phi_{j+1} = b_j
+//   (zero normal gradient at both y boundaries; for (0,0) row 0 is replaced by phi_0 = 0)
+//   phi = IFFT_z IFFT_x phi^ / (nx nz)
+//   u = u* - alpha_k dt G phi,  p = p + phi
+//
+// FFTs are radix-2 Stockham autosort transforms in shared memory with a precomputed twiddle
+// table W_N^k = exp(-2 pi i k / N), k < N/2.  The y factors (1/pivot, c/pivot) of every (kx, kz)
+// system are precomputed once by pois_factor_kernel (the operator does not change).
+#include "ns_internal.cuh"
+
+namespace {
+
+__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+
+// Stockham radix-2 on nseq sequences of length N = 2^LN stored contiguously in A ([seq][N]);
+// B is scratch of the same size.  SIGN = -1 forward, +1 inverse (unscaled).  Returns the
+// buffer that holds the result.  All threads of the block take part.
+template <int SIGN>
+__device__ double2* stockham(double2* A, double2* B, int N, int LN, int nseq, const double2* __restrict__ tw) {
+  const int half = N >> 1;
+  const int total = nseq * half;
+  int s = 1;
+  int ls = 0;  // log2(s)
+  for (int st = 0; st < LN; ++st) {
+    const int m = half >> ls;   // n/2 with n = N/s
+    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+      const int sq = idx >> (LN - 1);
+      const int b = idx & (half - 1);
+      const int p = b >> ls;
+      const int q = b & (s - 1);
+      const double2* X = A + sq * N;
+      double2* Y = B + sq * N;
+      const double2 x0 = X[q + s * p];
+      const double2 x1 = X[q + s * (p + m)];
+      Y[q + 2 * s * p] = cadd(x0, x1);
+      double2 dlt = csub(x0, x1);
+      if (m > 1) {
+        double2 wv = __ldg(tw + p * s);
+        if (SIGN > 0) wv.y = -wv.y;
+        dlt = cmul(dlt, wv);
+      }
+      Y[q + s * (2 * p + 1)] = dlt;
+    }
+    __syncthreads();
+    double2* t = A;
+    A = B;
+    B = t;
+    s <<= 1;
+    ++ls;
+  }
+  return A;
+}
+
+// ------------------------------------------------------------------------------------------
+// divergence + forward z FFT.  Block = (x-tile of TX columns, row j).  Output spec[kz][j][i].
+// ------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) div_fftz_kernel(const double* __restrict__ u, const double* __restrict__ v,
+                                                       const double* __restrict__ w, const double* __restrict__ gc,
+                                                       const double2* __restrict__ twz, double2* __restrict__ spec,
+                                                       int nx, int ny, int nz, int lnz, int TX, double idx,
+                                                       double idz, double scale) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int nseq = TX >> 1;
+  double2* A = reinterpret_cast<double2*>(smem_raw);
+  double2* B = A + nseq * nz;
+  const int i0 = blockIdx.x * TX;
+  const int j = blockIdx.y;
+  const double idy = __ldg(gc + GC_IDY * (ny + 1) + j);
+  const long pl = (long)ny * nx, plv = (long)(ny + 1) * nx;
+  for (int q = threadIdx.x; q < TX * nz; q += blockDim.x) {
+    const int il = q % TX;
+    const int k = q / TX;
+    const int i = i0 + il;
+    const int ip = (i + 1 == nx) ? 0 : i + 1;
+    const int kp = (k + 1 == nz) ? 0 : k + 1;
+    const long c = k * pl + (long)j * nx;
+    const double du = __ldg(u + c + ip) - __ldg(u + c + i);
+    const double dv = __ldg(v + k * plv + (long)(j + 1) * nx + i) - __ldg(v + k * plv + (long)j * nx + i);
+    const double dw = __ldg(w + kp * pl + (long)j * nx + i) - __ldg(w + c + i);
+    const double b = (du * idx + dv * idy + dw * idz) * scale;
+    double* slot = reinterpret_cast<double*>(A + (il >> 1) * nz + k);
+    slot[il & 1] = b;
+  }
+  __syncthreads();
+  double2* R = stockham<-1>(A, B, nz, lnz, nseq, twz);
+  // unpack the two real transforms of each packed pair; write kz = 0..nz/2
+  const int nh = (nz >> 1) + 1;
+  for (int q = threadIdx.x; q < nh * TX; q += blockDim.x) {
+    const int il = q % TX;
+    const int m = q / TX;
+    const int c = il >> 1;
+    const double2 zm = R[c * nz + m];
+    const double2 zn = R[c * nz + ((nz - m) & (nz - 1))];
+    double2 X;
+    if ((il & 1) == 0)
+      X = make_double2(0.5 * (zm.x + zn.x), 0.5 * (zm.y - zn.y));
+    else
+      X = make_double2(0.5 * (zm.y + zn.y), 0.5 * (zn.x - zm.x));
+    spec[((long)m * ny + j) * nx + i0 + il] = X;
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// complex FFT along x of R rows per block (rows are contiguous, length nx), in place.
+// ------------------------------------------------------------------------------------------
+template <int SIGN>
+__global__ void __launch_bounds__(256) fftx_kernel(double2* __restrict__ spec, const double2* __restrict__ twx,
+                                                   long nrows, int nx, int lnx, int R, double scale) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double2* A = reinterpret_cast<double2*>(smem_raw);
+  double2* B = A + R * nx;
+  const long row0 = (long)blockIdx.x * R;
+  const int nr = (int)min((long)R, nrows - row0);
+  double2* g = spec + row0 * nx;
+  for (int q = threadIdx.x; q < nr * nx; q += blockDim.x) A[q] = g[q];
+  for (int q = nr * nx + threadIdx.x; q < R * nx; q += blockDim.x) A[q] = make_double2(0.0, 0.0);
+  __syncthreads();
+  double2* Rb = stockham<SIGN>(A, B, nx, lnx, R, twx);
+  for (int q = threadIdx.x; q < nr * nx; q += blockDim.x) {
+    const double2 t = Rb[q];
+    g[q] = make_double2(t.x * scale, t.y * scale);
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// y tridiagonal per (kx, kz), one thread per line, factors (1/pivot, c/pivot) precomputed.
+// ------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(128) tdma_y_kernel(double2* __restrict__ spec, const double2* __restrict__ fac,
+                                                     const double* __restrict__ gc, int nx, int ny) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int kz = blockIdx.y;
+  if (i >= nx) return;
+  const long base = (long)kz * ny * nx + i;
+  double2* d = spec + base;
+  const double2* f = fac + base;
+  const double* pa = gc + GC_PA * (ny + 1);
+  double2 prev = d[0];
+  if (i == 0 && kz == 0) prev = make_double2(0.0, 0.0);  // gauge row of the (0,0) mode
+  double2 ff = __ldg(f);
+  prev.x *= ff.x;
+  prev.y *= ff.x;
+  d[0] = prev;
+  for (int j = 1; j < ny; ++j) {
+    const long o = (long)j * nx;
+    const double aj = __ldg(pa + j);
+    const double2 dj = d[o];
+    ff = __ldg(f + o);
+    prev = make_double2(fma(-aj, prev.x, dj.x) * ff.x, fma(-aj, prev.y, dj.y) * ff.x);
+    d[o] = prev;
+  }
+  double2 next = prev;
+  for (int j = ny - 2; j >= 0; --j) {
+    const long o = (long)j * nx;
+    const double cp = __ldg(f + o).y;
+    const double2 dj = d[o];
+    next = make_double2(fma(-cp, next.x, dj.x), fma(-cp, next.y, dj.y));
+    d[o] = next;
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// inverse z FFT (complex-to-real on the half spectrum) -> phi.  Block = (x-tile, row j).
+// ------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) ifftz_kernel(const double2* __restrict__ spec, const double2* __restrict__ twz,
+                                                    double* __restrict__ phi, int nx, int ny, int nz, int lnz,
+                                                    int TX, double scale) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int nseq = TX >> 1;
+  double2* A = reinterpret_cast<double2*>(smem_raw);
+  double2* B = A + nseq * nz;
+  const int i0 = blockIdx.x * TX;
+  const int j = blockIdx.y;
+  const int nh = nz >> 1;
+  // Z[m] = Xa[m] + i Xb[m] (m <= nz/2), Z[nz-m] = conj(Xa[m]) + i conj(Xb[m]); the m = 0 and
+  // m = nz/2 coefficients of a real sequence are real, so only their real parts are used.
+  for (int q = threadIdx.x; q < nseq * (nh + 1); q += blockDim.x) {
+    const int c = q % nseq;
+    const int m = q / nseq;
+    const long o = ((long)m * ny + j) * nx + i0 + 2 * c;
+    double2 xa = spec[o];
+    double2 xb = spec[o + 1];
+    if (m == 0 || m == nh) {
+      xa.y = 0.0;
+      xb.y = 0.0;
+    }
+    A[c * nz + m] = make_double2(xa.x - xb.y, xa.y + xb.x);
+    if (m > 0 && m < nh) A[c * nz + nz - m] = make_double2(xa.x + xb.y, xb.x - xa.y);
+  }
+  __syncthreads();
+  const double2* R = stockham<1>(A, B, nz, lnz, nseq, twz);
+  const long pl = (long)ny * nx;
+  for (int q = threadIdx.x; q < TX * nz; q += blockDim.x) {
+    const int il = q % TX;
+    const int k = q / TX;
+    const double2 t = R[(il >> 1) * nz + k];
+    phi[k * pl + (long)j * nx + i0 + il] = ((il & 1) ? t.y : t.x) * scale;
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// projection u = u* - s G phi; p += phi (if update_p).  One thread per (i, j) of a z-plane,
+// j = 0..ny.
+// ------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(128) project_kernel(double* __restrict__ u, double* __restrict__ v,
+                                                      double* __restrict__ w, double* __restrict__ p,
+                                                      const double* __restrict__ phi, const double* __restrict__ gc,
+                                                      int nx, int ny, int nz, double sx, double sz, int update_p,
+                                                      double s) {
+  const long plane = (long)nx * (ny + 1);
+  const long q = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= plane) return;
+  const int j = (int)(q / nx);
+  const int i = (int)(q - (long)j * nx);
+  const int k = blockIdx.y;
+  const int im = (i == 0) ? nx - 1 : i - 1;
+  const int km = (k == 0) ? nz - 1 : k - 1;
+  const long pl = (long)ny * nx;
+  if (j < ny) {
+    const long cc = k * pl + (long)j * nx + i;
+    const double f0 = __ldg(phi + cc);
+    u[cc] -= sx * (f0 - __ldg(phi + k * pl + (long)j * nx + im));
+    w[cc] -= sz * (f0 - __ldg(phi + km * pl + (long)j * nx + i));
+    if (update_p) p[cc] += f0;
+  }
+  if (j >= 1 && j < ny) {
+    const double ihc = __ldg(gc + GC_IHC * (ny + 1) + j);
+    const long cc = k * pl + (long)j * nx + i;
+    v[(long)k * (ny + 1) * nx + (long)j * nx + i] -= s * ihc * (__ldg(phi + cc) - __ldg(phi + cc - nx));
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// factor table of the y systems: per (kx, kz, j): (1/pivot_j, c_j/pivot_j).  Init only.
+// ------------------------------------------------------------------------------------------
+__global__ void pois_factor_kernel(double2* __restrict__ fac, const double* __restrict__ gc,
+                                   const double* __restrict__ lamx, const double* __restrict__ lamz, int nx, int ny,
+                                   int nzh) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int kz = blockIdx.y;
+  if (i >= nx || kz >= nzh) return;
+  const double* pa = gc + GC_PA * (ny + 1);
+  const double* pc = gc + GC_PC * (ny + 1);
+  const double lam = lamx[i] + lamz[kz];
+  const bool gauge = (i == 0 && kz == 0);
+  double cprev = 0.0;
+  for (int j = 0; j < ny; ++j) {
+    double a = pa[j], c = pc[j];
+    double b = -(a + c) - lam;
+    if (gauge && j == 0) {
+      a = 0.0;
+      b = 1.0;
+      c = 0.0;
+    }
+    const double piv = b - a * cprev;
+    const double ip = 1.0 / piv;
+    cprev = c * ip;
+    fac[((long)kz * ny + j) * nx + i] = make_double2(ip, cprev);
+  }
+}
+
+int ilog2(int n) {
+  int l = 0;
+  while ((1 << l) < n) ++l;
+  return l;
+}
+
+}  // namespace
+
+cudaError_t poisson_set_attributes() {
+  cudaFuncSetAttribute(div_fftz_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaFuncSetAttribute(ifftz_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaFuncSetAttribute(fftx_kernel<-1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaFuncSetAttribute(fftx_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pois_factor(ns_ctx* c, const double* lamx, const double* lamz) {
+  dim3 grid((c->cfg.nx + 127) / 128, c->nzh);
+  pois_factor_kernel<<<grid, 128, 0, c->launch>>>(c->pois, c->gc, lamx, lamz, c->cfg.nx, c->cfg.ny, c->nzh);
+  return cudaGetLastError();
+}
+
+static int z_tile(int nz) {
+  // complex sequences of length nz: keep 2 * (TX/2) * nz * 16 B <= 64 KB
+  int tx = 16;
+  while (tx > 2 && (size_t)tx * nz * 16 > 64 * 1024) tx >>= 1;
+  return tx;
+}
+
+cudaError_t launch_poisson(ns_ctx* c, int k) {
+  const int nx = c->cfg.nx, ny = c->cfg.ny, nz = c->cfg.nz;
+  const double scale = (k >= 0) ? 1.0 / (NS_ALPHA[k] * c->cfg.dt) : 1.0;
+  const int lnz = ilog2(nz), lnx = ilog2(nx);
+  const int TX = min(z_tile(nz), nx);
+  size_t smz = (size_t)TX * nz * sizeof(double2);  // two buffers of TX/2 sequences
+  div_fftz_kernel<<<dim3(nx / TX, ny), 256, smz, c->launch>>>(c->f.u, c->f.v, c->f.w, c->gc, c->twz, c->spec, nx,
+                                                              ny, nz, lnz, TX, 1.0 / c->dx, 1.0 / c->dz, scale);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const long nrows = (long)c->nzh * ny;
+  int R = 1;
+  while (R < 16 && (size_t)2 * R * 2 * nx * sizeof(double2) <= 64 * 1024) R <<= 1;
+  const size_t smx = (size_t)2 * R * nx * sizeof(double2);
+  const unsigned bx = (unsigned)((nrows + R - 1) / R);
+  fftx_kernel<-1><<<bx, 256, smx, c->launch>>>(c->spec, c->twx, nrows, nx, lnx, R, 1.0);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  tdma_y_kernel<<<dim3((nx + 127) / 128, c->nzh), 128, 0, c->launch>>>(c->spec, c->pois, c->gc, nx, ny);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  fftx_kernel<1><<<bx, 256, smx, c->launch>>>(c->spec, c->twx, nrows, nx, lnx, R, 1.0 / ((double)nx * nz));
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  ifftz_kernel<<<dim3(nx / TX, ny), 256, smz, c->launch>>>(c->spec, c->twz, c->phi, nx, ny, nz, lnz, TX, 1.0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_project(ns_ctx* c, int k) {
+  const int nx = c->cfg.nx, ny = c->cfg.ny, nz = c->cfg.nz;
+  const double s = (k >= 0) ? NS_ALPHA[k] * c->cfg.dt : 1.0;
+  const long plane = (long)nx * (ny + 1);
+  dim3 grid((unsigned)((plane + 127) / 128), nz);
+  project_kernel<<<grid, 128, 0, c->launch>>>(c->f.u, c->f.v, c->f.w, c->f.p, c->phi, c->gc, nx, ny, nz, s / c->dx,
+                                              s / c->dz, k >= 0 ? 1 : 0, s);
+  return cudaGetLastError();
+}

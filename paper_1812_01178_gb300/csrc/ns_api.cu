@@ -1,0 +1,776 @@
+// C ABI entry points, workspace layout, coefficient tables and graph capture.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "ns_internal.cuh"
+
+namespace {
+
+thread_local std::string g_init_error;
+
+bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
+
+size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Returns "" if the configuration is valid, else a message; *kind receives the status to report.
+std::string check_cfg(const ns_config* c, ns_status* kind = nullptr) {
+  ns_status dummy;
+  ns_status& k = kind ? *kind : dummy;
+  k = NS_ERR_ARG;
+  if (!c) return "cfg is NULL";
+  if (!c->yf) return "cfg->yf is NULL";
+  if (c->bc_x != 0) {
+    k = NS_ERR_UNSUPPORTED;
+    return "bc_x = 1 (inflow / convective outflow) is not built";
+  }
+  if (c->bc_ytop != 0 && c->bc_ytop != 1) return "bc_ytop must be 0 or 1";
+  if (c->precision != NS_FP64 && c->precision != NS_MIXED) return "precision must be NS_FP64 or NS_MIXED";
+  k = NS_ERR_SIZE;
+  if (!is_pow2(c->nx) || c->nx < 8 || c->nx > 4096) return "nx must be a power of two in [8, 4096]";
+  if (!is_pow2(c->nz) || c->nz < 8 || c->nz > 4096) return "nz must be a power of two in [8, 4096]";
+  if (c->ny < 4 || c->ny > 1024) return "ny must be in [4, 1024]";
+  k = NS_ERR_ARG;
+  if (!(c->lx > 0) || !(c->lz > 0) || !(c->dt > 0)) return "lx, lz and dt must be positive";
+  for (int j = 0; j < c->ny; ++j)
+    if (!(c->yf[j + 1] > c->yf[j])) return "yf must be strictly increasing";
+  return "";
+}
+
+ns_layout make_layout(const ns_config* c) {
+  ns_layout L;
+  memset(&L, 0, sizeof(L));
+  const size_t es = c->precision == NS_MIXED ? 4 : 8;
+  const size_t nx = c->nx, ny = c->ny, nz = c->nz, nzh = nz / 2 + 1;
+  const size_t cells = nx * ny * nz, vcells = nx * (ny + 1) * nz;
+  size_t sz[LB_COUNT];
+  sz[LB_RU] = cells * es;
+  sz[LB_RV] = vcells * es;
+  sz[LB_RW] = cells * es;
+  sz[LB_NU] = cells * es;
+  sz[LB_NV] = vcells * es;
+  sz[LB_NW] = cells * es;
+  sz[LB_PHI] = cells * 8;
+  sz[LB_SPEC] = nzh * ny * nx * 16;
+  sz[LB_POIS] = nzh * ny * nx * 16;
+  sz[LB_GC] = NS_GC_COUNT * (ny + 1) * 8;
+  sz[LB_XTAB] = 3 * al256((5 * nx + 4 * 32 + 8 * 5 * 32) * es);
+  sz[LB_YTAB] = 6 * al256(3 * ny * es);
+  sz[LB_ZTAB] = 3 * al256((4 * nz + 2) * es);
+  sz[LB_TWZ] = (nz / 2) * 16;
+  sz[LB_TWX] = (nx / 2) * 16;
+  sz[LB_LAMX] = nx * 8;
+  sz[LB_LAMZ] = nzh * 8;
+  size_t o = 0;
+  for (int b = 0; b < LB_COUNT; ++b) {
+    L.off[b] = o;
+    o += al256(sz[b]);
+  }
+  L.total = o;
+  return L;
+}
+
+// --------------------------------------------------------------------------------------------
+// tridiagonal helpers (host, double)
+// --------------------------------------------------------------------------------------------
+// Thomas factors of rows (a, b, c), a[0] and c[n-1] ignored: inv = 1/pivot, ainv = a/pivot, cp = c/pivot.
+void thomas_factors(const std::vector<double>& a, const std::vector<double>& b, const std::vector<double>& c,
+                    std::vector<double>& inv, std::vector<double>& ainv, std::vector<double>& cp) {
+  const size_t n = b.size();
+  inv.assign(n, 0.0);
+  ainv.assign(n, 0.0);
+  cp.assign(n, 0.0);
+  double cprev = 0.0;
+  for (size_t j = 0; j < n; ++j) {
+    const double aj = j > 0 ? a[j] : 0.0;
+    const double cj = j + 1 < n ? c[j] : 0.0;
+    const double piv = b[j] - aj * cprev;
+    inv[j] = 1.0 / piv;
+    ainv[j] = aj * inv[j];
+    cp[j] = cj * inv[j];
+    cprev = cp[j];
+  }
+}
+
+std::vector<double> thomas_apply(const std::vector<double>& inv, const std::vector<double>& ainv,
+                                 const std::vector<double>& cp, std::vector<double> d) {
+  const size_t n = d.size();
+  d[0] *= inv[0];
+  for (size_t j = 1; j < n; ++j) d[j] = d[j] * inv[j] - ainv[j] * d[j - 1];
+  for (size_t j = n - 1; j-- > 0;) d[j] -= cp[j] * d[j + 1];
+  return d;
+}
+
+struct M2 {
+  double a, b, c, d;  // [[a, b], [c, d]]
+};
+M2 mmul(M2 x, M2 y) {
+  return {x.a * y.a + x.b * y.c, x.a * y.b + x.b * y.d, x.c * y.a + x.d * y.c, x.c * y.b + x.d * y.d};
+}
+M2 madd(M2 x, M2 y) { return {x.a + y.a, x.b + y.b, x.c + y.c, x.d + y.d}; }
+M2 msub(M2 x, M2 y) { return {x.a - y.a, x.b - y.b, x.c - y.c, x.d - y.d}; }
+M2 minv(M2 x) {
+  const double det = x.a * x.d - x.b * x.c;
+  return {x.d / det, -x.b / det, -x.c / det, x.a / det};
+}
+M2 mzero() { return {0, 0, 0, 0}; }
+
+// Partitioned x solver tables for constant rows (lo, di, up) on a periodic line of n = P*M rows
+// (Sec. 3.2).  mode: NS_PART_PDD or NS_PART_PPT.  Returns the table (doubles), its number of
+// reduction levels and the largest coupling PDD drops.
+std::vector<double> build_xtab(double lo, double di, double up, int n, int P, int mode, int* levels,
+                               double* dropped) {
+  const int M = n / P;
+  int L = 0;
+  while ((1 << L) < P) ++L;
+  // block Thomas factors of one partition of A~ (couplings to the neighbours cut)
+  std::vector<double> a(M, lo), b(M, di), c(M, up);
+  std::vector<double> inv, ainv, cp;
+  thomas_factors(a, b, c, inv, ainv, cp);
+  // spikes: A~ v = lo e_1, A~ w = up e_M  (Eq. blockAY, V columns of the cut couplings)
+  std::vector<double> e1(M, 0.0), em(M, 0.0);
+  e1[0] = lo;
+  em[M - 1] = up;
+  std::vector<double> sv = thomas_apply(inv, ainv, cp, e1);
+  std::vector<double> sw = thomas_apply(inv, ainv, cp, em);
+  // interface r couples partition r (last row) and r+1 (first row), cyclically.
+  // Z block row r: L_r Y_{r-1} + D_r Y_r + U_r Y_{r+1} = (x~^{(r)}_m, x~^{(r+1)}_1)
+  std::vector<M2> Lb(P), Db(P), Ub(P);
+  for (int r = 0; r < P; ++r) {
+    Db[r] = {1.0, sw[M - 1], sv[0], 1.0};
+    Lb[r] = {sv[M - 1], 0.0, 0.0, 0.0};
+    Ub[r] = {0.0, 0.0, 0.0, sw[0]};
+  }
+  double drop = 0.0;
+  for (int r = 0; r < P; ++r) drop = std::fmax(drop, std::fmax(std::fabs(Lb[r].a), std::fabs(Ub[r].d)));
+  *dropped = drop;
+  std::vector<M2> MLs, MUs;  // per level, per r
+  if (mode == NS_PART_PPT && P == 1) {
+    // one partition: both couplings of the single interface point back at itself
+    Db[0] = madd(Db[0], madd(Lb[0], Ub[0]));
+  }
+  if (mode == NS_PART_PPT) {
+    for (int lv = 0, s = 1; lv < L; ++lv, s <<= 1) {
+      std::vector<M2> nL(P), nD(P), nU(P);
+      for (int r = 0; r < P; ++r) {
+        const int rm = ((r - s) % P + P) % P, rp = (r + s) % P;
+        M2 ml, mu;
+        if (rm == rp) {
+          ml = mmul(madd(Lb[r], Ub[r]), minv(Db[rm]));
+          mu = mzero();
+          nD[r] = msub(Db[r], mmul(ml, madd(Lb[rm], Ub[rm])));
+          nL[r] = mzero();
+          nU[r] = mzero();
+        } else {
+          ml = mmul(Lb[r], minv(Db[rm]));
+          mu = mmul(Ub[r], minv(Db[rp]));
+          nD[r] = msub(msub(Db[r], mmul(ml, Ub[rm])), mmul(mu, Lb[rp]));
+          // new couplings at distance 2s; when they coincide (4s = P) the next level folds them
+          nL[r] = msub(mzero(), mmul(ml, Lb[rm]));
+          nU[r] = msub(mzero(), mmul(mu, Ub[rp]));
+        }
+        MLs.push_back(ml);
+        MUs.push_back(mu);
+      }
+      Lb = nL;
+      Db = nD;
+      Ub = nU;
+    }
+  } else {
+    L = 0;
+  }
+  std::vector<double> t(xtab_count(M, P, L), 0.0);
+  for (int r = 0; r < P; ++r)
+    for (int e = 0; e < M; ++e) {
+      t[(XT_INV * M + e) * P + r] = inv[e];
+      t[(XT_AINV * M + e) * P + r] = ainv[e];
+      t[(XT_CP * M + e) * P + r] = cp[e];
+      t[(XT_V * M + e) * P + r] = sv[e];
+      t[(XT_W * M + e) * P + r] = sw[e];
+    }
+  const size_t d0 = (size_t)XT_NF * M * P;
+  for (int r = 0; r < P; ++r) {
+    const M2 di = minv(Db[r]);
+    t[d0 + r] = di.a;
+    t[d0 + P + r] = di.b;
+    t[d0 + 2 * P + r] = di.c;
+    t[d0 + 3 * P + r] = di.d;
+  }
+  const size_t m0 = d0 + 4 * (size_t)P, u0 = m0 + 4 * (size_t)L * P;
+  for (int lv = 0; lv < L; ++lv)
+    for (int r = 0; r < P; ++r) {
+      const M2 ml = MLs[(size_t)lv * P + r], mu = MUs[(size_t)lv * P + r];
+      t[m0 + (4 * lv + 0) * P + r] = ml.a;
+      t[m0 + (4 * lv + 1) * P + r] = ml.b;
+      t[m0 + (4 * lv + 2) * P + r] = ml.c;
+      t[m0 + (4 * lv + 3) * P + r] = ml.d;
+      t[u0 + (4 * lv + 0) * P + r] = mu.a;
+      t[u0 + (4 * lv + 1) * P + r] = mu.b;
+      t[u0 + (4 * lv + 2) * P + r] = mu.c;
+      t[u0 + (4 * lv + 3) * P + r] = mu.d;
+    }
+  *levels = L;
+  return t;
+}
+
+cudaError_t upload_d(ns_ctx* c, void* dst, const std::vector<double>& src);
+
+// Copy a host table to the device in the context's element type (double or float).  Waits for
+// the copy, so the host vector may be released afterwards.
+cudaError_t upload(ns_ctx* c, void* dst, const std::vector<double>& src) {
+  if (c->es == 8) return upload_d(c, dst, src);
+  std::vector<float> f(src.begin(), src.end());
+  cudaError_t e = cudaMemcpyAsync(dst, f.data(), f.size() * 4, cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);  // f is a temporary
+  return e;
+}
+
+cudaError_t upload_d(ns_ctx* c, void* dst, const std::vector<double>& src) {
+  cudaError_t e = cudaMemcpyAsync(dst, src.data(), src.size() * 8, cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  return e;
+}
+
+double beta_of(const ns_ctx* c, int k) {
+  const double inv_re = c->cfg.re > 0 ? 1.0 / c->cfg.re : 0.0;
+  return NS_ALPHA[k] * c->cfg.dt * inv_re / 2.0;
+}
+
+// x-solver tables for every sub-step with the context's P and requested mode.
+ns_status build_x_tables(ns_ctx* c) {
+  const int nx = c->cfg.nx;
+  const double tol = c->es == 8 ? 1e-15 : 1e-8;
+  double drop_max = 0.0;
+  std::vector<double> tabs[3][2];
+  int levs[3][2];
+  for (int k = 0; k < 3; ++k) {
+    const double r = beta_of(c, k) / (c->dx * c->dx);
+    double d0, d1;
+    tabs[k][0] = build_xtab(-r, 1.0 + 2.0 * r, -r, nx, c->P, NS_PART_PDD, &levs[k][0], &d0);
+    tabs[k][1] = build_xtab(-r, 1.0 + 2.0 * r, -r, nx, c->P, NS_PART_PPT, &levs[k][1], &d1);
+    drop_max = std::fmax(drop_max, d0);
+  }
+  int mode = c->part_req;
+  if (mode == NS_PART_AUTO) mode = drop_max <= tol ? NS_PART_PDD : NS_PART_PPT;
+  c->part_mode = mode;
+  c->pdd_drop = drop_max;
+  const int sel = mode == NS_PART_PDD ? 0 : 1;
+  for (int k = 0; k < 3; ++k) {
+    c->L[k] = levs[k][sel];
+    if (tabs[k][sel].size() > c->xtab_stride) return NS_ERR_SIZE;
+    if (upload(c, c->xtab[k], tabs[k][sel]) != cudaSuccess) return NS_ERR_CUDA;
+  }
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return NS_ERR_CUDA;
+  return NS_OK;
+}
+
+void drop_graph(ns_ctx* c) {
+  if (c->have_graph) {
+    cudaGraphExecDestroy(c->gexec);
+    cudaGraphDestroy(c->graph);
+    c->have_graph = false;
+  }
+}
+
+ns_status fail(ns_ctx* c, ns_status s, const std::string& msg) {
+  c->err = msg;
+  return s;
+}
+
+ns_status cuda_fail(ns_ctx* c, cudaError_t e, const char* where) {
+  c->err = std::string(where) + ": " + cudaGetErrorString(e);
+  return NS_ERR_CUDA;
+}
+
+bool capturing(ns_ctx* c) {
+  cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(c->launch, &st);
+  return st != cudaStreamCaptureStatusNone;
+}
+
+ns_status run_substep(ns_ctx* c, int k) {
+  cudaError_t e;
+  if ((e = launch_rhs(c, k)) != cudaSuccess) return cuda_fail(c, e, "rhs");
+  if ((e = launch_adi_x(c, k)) != cudaSuccess) return cuda_fail(c, e, "adi_x");
+  if ((e = launch_adi_y(c, k)) != cudaSuccess) return cuda_fail(c, e, "adi_y");
+  if ((e = launch_adi_z(c, k)) != cudaSuccess) return cuda_fail(c, e, "adi_z");
+  if ((e = launch_poisson(c, k)) != cudaSuccess) return cuda_fail(c, e, "poisson");
+  if ((e = launch_project(c, k)) != cudaSuccess) return cuda_fail(c, e, "project");
+  return NS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t ns_workspace_bytes(const ns_config* cfg) {
+  if (!check_cfg(cfg).empty()) return 0;
+  return make_layout(cfg).total;
+}
+
+ns_status ns_init(ns_ctx** out, const ns_config* cfg, const ns_fields* fields, void* workspace, size_t ws_bytes,
+                  void* cuda_stream) {
+  g_init_error.clear();
+  if (!out) {
+    g_init_error = "out is NULL";
+    return NS_ERR_ARG;
+  }
+  *out = nullptr;
+  ns_status kind = NS_OK;
+  const std::string msg = check_cfg(cfg, &kind);
+  if (!msg.empty()) {
+    g_init_error = msg;
+    return kind;
+  }
+  if (!fields || !fields->u || !fields->v || !fields->w || !fields->p) {
+    g_init_error = "fields or a field pointer is NULL";
+    return NS_ERR_ARG;
+  }
+  const void* ptrs[4] = {fields->u, fields->v, fields->w, fields->p};
+  for (const void* p : ptrs)
+    if ((uintptr_t)p % 256 != 0) {
+      g_init_error = "field pointers must be 256-byte aligned";
+      return NS_ERR_ARG;
+    }
+  ns_ctx* c = new (std::nothrow) ns_ctx();
+  if (!c) {
+    g_init_error = "out of host memory";
+    return NS_ERR_ARG;
+  }
+  c->cfg = *cfg;
+  c->yf.assign(cfg->yf, cfg->yf + cfg->ny + 1);
+  c->cfg.yf = c->yf.data();
+  c->f = *fields;
+  c->stream = (cudaStream_t)cuda_stream;
+  c->launch = c->stream;
+  c->es = cfg->precision == NS_MIXED ? 4 : 8;
+  c->nzh = cfg->nz / 2 + 1;
+  c->dx = cfg->lx / cfg->nx;
+  c->dz = cfg->lz / cfg->nz;
+  c->lay = make_layout(cfg);
+  c->have_graph = false;
+  cudaError_t e;
+  if (workspace) {
+    if (ws_bytes < c->lay.total || (uintptr_t)workspace % 256 != 0) {
+      g_init_error = "workspace too small or not 256-byte aligned";
+      delete c;
+      return NS_ERR_ARG;
+    }
+    c->ws = workspace;
+    c->own_ws = false;
+  } else {
+    if ((e = cudaMalloc(&c->ws, c->lay.total)) != cudaSuccess) {
+      g_init_error = std::string("cudaMalloc workspace: ") + cudaGetErrorString(e);
+      delete c;
+      return NS_ERR_CUDA;
+    }
+    c->own_ws = true;
+  }
+  c->ws_bytes = c->lay.total;
+  if ((e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking)) != cudaSuccess) {
+    g_init_error = std::string("stream create: ") + cudaGetErrorString(e);
+    if (c->own_ws) cudaFree(c->ws);
+    delete c;
+    return NS_ERR_CUDA;
+  }
+  char* base = (char*)c->ws;
+  c->ru = base + c->lay.off[LB_RU];
+  c->rv = base + c->lay.off[LB_RV];
+  c->rw = base + c->lay.off[LB_RW];
+  c->nu = base + c->lay.off[LB_NU];
+  c->nv = base + c->lay.off[LB_NV];
+  c->nw = base + c->lay.off[LB_NW];
+  c->phi = (double*)(base + c->lay.off[LB_PHI]);
+  c->spec = (double2*)(base + c->lay.off[LB_SPEC]);
+  c->pois = (double2*)(base + c->lay.off[LB_POIS]);
+  c->gc = (double*)(base + c->lay.off[LB_GC]);
+  const int nx = cfg->nx, ny = cfg->ny, nz = cfg->nz;
+  c->xtab_stride = (5 * (size_t)nx + 4 * 32 + 8 * 5 * 32);
+  for (int k = 0; k < 3; ++k) {
+    c->xtab[k] = base + c->lay.off[LB_XTAB] + k * al256(c->xtab_stride * c->es);
+    for (int q = 0; q < 2; ++q) c->ytab[k][q] = base + c->lay.off[LB_YTAB] + (2 * k + q) * al256(3 * ny * c->es);
+    c->ztab[k] = base + c->lay.off[LB_ZTAB] + k * al256((4 * nz + 2) * c->es);
+  }
+  c->twz = (double2*)(base + c->lay.off[LB_TWZ]);
+  c->twx = (double2*)(base + c->lay.off[LB_TWX]);
+  double* lamx_d = (double*)(base + c->lay.off[LB_LAMX]);
+  double* lamz_d = (double*)(base + c->lay.off[LB_LAMZ]);
+
+  // ---------------- grid coefficients (Sec. 2.1 / 2.2 readings)
+  const std::vector<double>& yf = c->yf;
+  std::vector<double> yc(ny), dy(ny);
+  for (int j = 0; j < ny; ++j) {
+    yc[j] = 0.5 * (yf[j] + yf[j + 1]);
+    dy[j] = yf[j + 1] - yf[j];
+  }
+  const int G = ny + 1;
+  std::vector<double> gc((size_t)NS_GC_COUNT * G, 0.0);
+  auto GCv = [&](int f, int j) -> double& { return gc[(size_t)f * G + j]; };
+  for (int j = 0; j < ny; ++j) {
+    GCv(GC_DY, j) = dy[j];
+    GCv(GC_IDY, j) = 1.0 / dy[j];
+  }
+  for (int j = 1; j < ny; ++j) {
+    const double hc = yc[j] - yc[j - 1];
+    GCv(GC_HC, j) = hc;
+    GCv(GC_IHC, j) = 1.0 / hc;
+    const double whi = (yf[j] - yc[j - 1]) / hc;
+    GCv(GC_WHI, j) = whi;
+    GCv(GC_WLO, j) = 1.0 - whi;
+  }
+  for (int j = 0; j < ny; ++j) {
+    const double hm = j == 0 ? yc[0] - yf[0] : yc[j] - yc[j - 1];
+    const double hp = j == ny - 1 ? yf[ny] - yc[ny - 1] : yc[j + 1] - yc[j];
+    GCv(GC_AC, j) = 2.0 / (hm * (hm + hp));
+    GCv(GC_CC, j) = (j == ny - 1 && cfg->bc_ytop == 1) ? 0.0 : 2.0 / (hp * (hm + hp));
+  }
+  for (int j = 1; j < ny; ++j) {
+    const double hm = dy[j - 1], hp = dy[j];
+    GCv(GC_AF, j) = 2.0 / (hm * (hm + hp));
+    GCv(GC_CF, j) = 2.0 / (hp * (hm + hp));
+  }
+  for (int j = 1; j < ny; ++j) GCv(GC_PA, j) = 1.0 / (dy[j] * (yc[j] - yc[j - 1]));
+  for (int j = 0; j + 1 < ny; ++j) GCv(GC_PC, j) = 1.0 / (dy[j] * (yc[j + 1] - yc[j]));
+  ns_status st = NS_OK;
+  if (upload_d(c, c->gc, gc) != cudaSuccess) st = NS_ERR_CUDA;
+
+  // ---------------- ADI y and z factors per sub-step
+  for (int k = 0; k < 3 && st == NS_OK; ++k) {
+    const double beta = beta_of(c, k);
+    {  // centres (u, w): rows j = 0..ny-1
+      std::vector<double> a(ny), b(ny), cc(ny), inv, ainv, cp;
+      for (int j = 0; j < ny; ++j) {
+        a[j] = -beta * GCv(GC_AC, j);
+        cc[j] = -beta * GCv(GC_CC, j);
+        b[j] = 1.0 + beta * (GCv(GC_AC, j) + GCv(GC_CC, j));
+      }
+      thomas_factors(a, b, cc, inv, ainv, cp);
+      std::vector<double> t;
+      t.insert(t.end(), inv.begin(), inv.end());
+      t.insert(t.end(), ainv.begin(), ainv.end());
+      t.insert(t.end(), cp.begin(), cp.end());
+      if (upload(c, c->ytab[k][0], t) != cudaSuccess) st = NS_ERR_CUDA;
+    }
+    {  // faces (v): rows j = 1..ny-1
+      const int n = ny - 1;
+      std::vector<double> a(n), b(n), cc(n), inv, ainv, cp;
+      for (int q = 0; q < n; ++q) {
+        const int j = q + 1;
+        a[q] = -beta * GCv(GC_AF, j);
+        cc[q] = -beta * GCv(GC_CF, j);
+        b[q] = 1.0 + beta * (GCv(GC_AF, j) + GCv(GC_CF, j));
+      }
+      thomas_factors(a, b, cc, inv, ainv, cp);
+      std::vector<double> t;
+      t.insert(t.end(), inv.begin(), inv.end());
+      t.insert(t.end(), ainv.begin(), ainv.end());
+      t.insert(t.end(), cp.begin(), cp.end());
+      if (upload(c, c->ytab[k][1], t) != cudaSuccess) st = NS_ERR_CUDA;
+    }
+    {  // z: cyclic rows (-r, 1 + 2r, -r) by Sherman-Morrison
+      const double r = beta / (c->dz * c->dz);
+      const double lo = -r, di = 1.0 + 2.0 * r, up = -r;
+      const double gam = -di, alpha = up /* A[n-1][0] */, bet = lo /* A[0][n-1] */;
+      std::vector<double> a(nz, lo), b(nz, di), cc(nz, up), inv, ainv, cp;
+      b[0] = di - gam;
+      b[nz - 1] = di - alpha * bet / gam;
+      thomas_factors(a, b, cc, inv, ainv, cp);
+      std::vector<double> s(nz, 0.0);
+      s[0] = gam;
+      s[nz - 1] = alpha;
+      std::vector<double> q = thomas_apply(inv, ainv, cp, s);
+      const double bg = bet / gam;
+      const double fac = 1.0 / (1.0 + q[0] + bg * q[nz - 1]);
+      std::vector<double> t;
+      t.insert(t.end(), inv.begin(), inv.end());
+      t.insert(t.end(), ainv.begin(), ainv.end());
+      t.insert(t.end(), cp.begin(), cp.end());
+      t.insert(t.end(), q.begin(), q.end());
+      t.push_back(fac);
+      t.push_back(bg);
+      if (upload(c, c->ztab[k], t) != cudaSuccess) st = NS_ERR_CUDA;
+    }
+  }
+  // ---------------- x partitioned solver: default P
+  c->part_req = NS_PART_AUTO;
+  {
+    // default: partitions of 8 rows (at most 32 per line, one per lane)
+    int P = nx / 8;
+    if (P < 1) P = 1;
+    if (P > 32) P = 32;
+    c->P = P;
+    c->M = nx / P;
+    if (st == NS_OK && (c->M > 16 || P > 32)) {
+      st = NS_ERR_SIZE;
+      c->err = "nx too large for the partitioned x solver (nx/32 > 16)";
+    }
+  }
+  if (st == NS_OK) st = build_x_tables(c);
+  // ---------------- FFT twiddles, modified wavenumbers, Poisson y factors
+  if (st == NS_OK) {
+    const double PI = 3.14159265358979323846;
+    std::vector<double> tw(nz);  // nz/2 complex
+    for (int q = 0; q < nz / 2; ++q) {
+      tw[2 * q] = std::cos(2.0 * PI * q / nz);
+      tw[2 * q + 1] = -std::sin(2.0 * PI * q / nz);
+    }
+    if (upload_d(c, c->twz, tw) != cudaSuccess) st = NS_ERR_CUDA;
+    std::vector<double> tx(nx);
+    for (int q = 0; q < nx / 2; ++q) {
+      tx[2 * q] = std::cos(2.0 * PI * q / nx);
+      tx[2 * q + 1] = -std::sin(2.0 * PI * q / nx);
+    }
+    if (upload_d(c, c->twx, tx) != cudaSuccess) st = NS_ERR_CUDA;
+    std::vector<double> lx(nx), lz(c->nzh);
+    for (int q = 0; q < nx; ++q) {
+      const int qq = q <= nx - q ? q : nx - q;
+      lx[q] = (2.0 / (c->dx * c->dx)) * (1.0 - std::cos(2.0 * PI * qq / nx));
+    }
+    for (int q = 0; q < c->nzh; ++q) lz[q] = (2.0 / (c->dz * c->dz)) * (1.0 - std::cos(2.0 * PI * q / nz));
+    if (upload_d(c, lamx_d, lx) != cudaSuccess) st = NS_ERR_CUDA;
+    if (upload_d(c, lamz_d, lz) != cudaSuccess) st = NS_ERR_CUDA;
+    if (st == NS_OK && poisson_set_attributes() != cudaSuccess) st = NS_ERR_CUDA;
+    if (st == NS_OK && launch_pois_factor(c, lamx_d, lamz_d) != cudaSuccess) st = NS_ERR_CUDA;
+    if (st == NS_OK && cudaStreamSynchronize(c->stream) != cudaSuccess) st = NS_ERR_CUDA;
+  }
+  // N_prev starts at zero (sub-step 0 does not read it; zero keeps it finite)
+  if (st == NS_OK) {
+    for (int b = LB_NU; b <= LB_NW; ++b)
+      if (cudaMemsetAsync(base + c->lay.off[b], 0, c->lay.off[b + 1] - c->lay.off[b], c->stream) != cudaSuccess)
+        st = NS_ERR_CUDA;
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) st = NS_ERR_CUDA;
+  }
+  if (st != NS_OK) {
+    g_init_error = c->err.empty() ? std::string("init failed: ") + cudaGetErrorString(cudaGetLastError()) : c->err;
+    cudaStreamDestroy(c->cap_stream);
+    if (c->own_ws) cudaFree(c->ws);
+    delete c;
+    return st;
+  }
+  *out = c;
+  return NS_OK;
+}
+
+ns_status ns_rhs(ns_ctx* c, int k) {
+  if (!c) return NS_ERR_ARG;
+  if (k < 0 || k > 2) return fail(c, NS_ERR_ARG, "substep must be 0, 1 or 2");
+  cudaError_t e = launch_rhs(c, k);
+  return e == cudaSuccess ? NS_OK : cuda_fail(c, e, "rhs");
+}
+
+ns_status ns_adi_sweep(ns_ctx* c, int dir, int k) {
+  if (!c) return NS_ERR_ARG;
+  if (k < 0 || k > 2) return fail(c, NS_ERR_ARG, "substep must be 0, 1 or 2");
+  cudaError_t e;
+  switch (dir) {
+    case 0: e = launch_adi_x(c, k); break;
+    case 1: e = launch_adi_y(c, k); break;
+    case 2: e = launch_adi_z(c, k); break;
+    default: return fail(c, NS_ERR_ARG, "dir must be 0, 1 or 2");
+  }
+  return e == cudaSuccess ? NS_OK : cuda_fail(c, e, "adi");
+}
+
+ns_status ns_poisson_solve(ns_ctx* c, int k) {
+  if (!c) return NS_ERR_ARG;
+  if (k < -1 || k > 2) return fail(c, NS_ERR_ARG, "substep must be -1, 0, 1 or 2");
+  cudaError_t e = launch_poisson(c, k);
+  return e == cudaSuccess ? NS_OK : cuda_fail(c, e, "poisson");
+}
+
+ns_status ns_project(ns_ctx* c, int k) {
+  if (!c) return NS_ERR_ARG;
+  if (k < -1 || k > 2) return fail(c, NS_ERR_ARG, "substep must be -1, 0, 1 or 2");
+  cudaError_t e = launch_project(c, k);
+  return e == cudaSuccess ? NS_OK : cuda_fail(c, e, "project");
+}
+
+ns_status ns_substep(ns_ctx* c, int k) {
+  if (!c) return NS_ERR_ARG;
+  if (k < 0 || k > 2) return fail(c, NS_ERR_ARG, "substep must be 0, 1 or 2");
+  return run_substep(c, k);
+}
+
+ns_status ns_make_divergence_free(ns_ctx* c) {
+  if (!c) return NS_ERR_ARG;
+  ns_status s = ns_poisson_solve(c, -1);
+  if (s != NS_OK) return s;
+  return ns_project(c, -1);
+}
+
+ns_status ns_step(ns_ctx* c, int nsteps) {
+  if (!c) return NS_ERR_ARG;
+  if (nsteps < 0) return fail(c, NS_ERR_ARG, "nsteps must be >= 0");
+  if (nsteps == 0) return NS_OK;
+  if (capturing(c)) return fail(c, NS_ERR_STATE, "ns_step called while its stream is being captured");
+  cudaError_t e;
+  if (!c->have_graph) {
+    c->launch = c->cap_stream;
+    if ((e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) {
+      c->launch = c->stream;
+      return cuda_fail(c, e, "begin capture");
+    }
+    ns_status s = NS_OK;
+    for (int k = 0; k < 3 && s == NS_OK; ++k) s = run_substep(c, k);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(c->cap_stream, &g);
+    c->launch = c->stream;
+    if (s != NS_OK) {
+      if (g) cudaGraphDestroy(g);
+      return s;
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, "end capture");
+    if ((e = cudaGraphInstantiate(&c->gexec, g, 0)) != cudaSuccess) {
+      cudaGraphDestroy(g);
+      return cuda_fail(c, e, "graph instantiate");
+    }
+    c->graph = g;
+    c->have_graph = true;
+  }
+  for (int s = 0; s < nsteps; ++s)
+    if ((e = cudaGraphLaunch(c->gexec, c->stream)) != cudaSuccess) return cuda_fail(c, e, "graph launch");
+  return NS_OK;
+}
+
+ns_status ns_step_host(ns_ctx* c, double* u, double* v, double* w, double* p, int nsteps) {
+  if (!c || !u || !v || !w || !p) return NS_ERR_ARG;
+  const size_t nx = c->cfg.nx, ny = c->cfg.ny, nz = c->cfg.nz;
+  const size_t bc = nx * ny * nz * 8, bv = nx * (ny + 1) * nz * 8;
+  cudaError_t e;
+  if ((e = cudaMemcpyAsync(c->f.u, u, bc, cudaMemcpyHostToDevice, c->stream)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(c->f.v, v, bv, cudaMemcpyHostToDevice, c->stream)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(c->f.w, w, bc, cudaMemcpyHostToDevice, c->stream)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(c->f.p, p, bc, cudaMemcpyHostToDevice, c->stream)) != cudaSuccess)
+    return cuda_fail(c, e, "h2d");
+  ns_status s = ns_step(c, nsteps);
+  if (s != NS_OK) return s;
+  if ((e = cudaMemcpyAsync(u, c->f.u, bc, cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(v, c->f.v, bv, cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(w, c->f.w, bc, cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(p, c->f.p, bc, cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess)
+    return cuda_fail(c, e, "d2h");
+  return ns_sync(c);
+}
+
+ns_status ns_set_partition(ns_ctx* c, int dir, int P, int mode) {
+  if (!c) return NS_ERR_ARG;
+  if (dir != 0) return fail(c, NS_ERR_UNSUPPORTED, "only dir 0 (x) is partitioned");
+  const int nx = c->cfg.nx;
+  if (!is_pow2(P) || P > 32 || nx % P != 0 || nx / P > 16) return fail(c, NS_ERR_ARG, "invalid partition count");
+  if (mode != NS_PART_AUTO && mode != NS_PART_PPT && mode != NS_PART_PDD)
+    return fail(c, NS_ERR_ARG, "invalid partition mode");
+  if (capturing(c)) return fail(c, NS_ERR_STATE, "ns_set_partition during capture");
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return fail(c, NS_ERR_CUDA, "sync");
+  const int oldP = c->P, oldM = c->M, oldreq = c->part_req;
+  c->P = P;
+  c->M = nx / P;
+  c->part_req = mode;
+  ns_status s = build_x_tables(c);
+  if (s != NS_OK) {
+    c->P = oldP;
+    c->M = oldM;
+    c->part_req = oldreq;
+    build_x_tables(c);
+    return fail(c, s, "rebuilding x tables failed");
+  }
+  drop_graph(c);
+  return NS_OK;
+}
+
+ns_status ns_get_partition(ns_ctx* c, int dir, int* P, int* mode, double* dropped) {
+  if (!c) return NS_ERR_ARG;
+  if (dir != 0) return fail(c, NS_ERR_UNSUPPORTED, "only dir 0 (x) is partitioned");
+  if (P) *P = c->P;
+  if (mode) *mode = c->part_mode;
+  if (dropped) *dropped = c->pdd_drop;
+  return NS_OK;
+}
+
+ns_status ns_autotune(ns_ctx* c) {
+  if (!c) return NS_ERR_ARG;
+  if (capturing(c)) return fail(c, NS_ERR_STATE, "ns_autotune during capture");
+  const int nx = c->cfg.nx;
+  // The timed sweeps overwrite r: keep a copy and restore it afterwards.
+  const size_t rbytes = c->lay.off[LB_NU] - c->lay.off[LB_RU];
+  void* save = nullptr;
+  cudaError_t e = cudaMalloc(&save, rbytes);
+  if (e != cudaSuccess) return cuda_fail(c, e, "autotune scratch");
+  cudaMemcpyAsync(save, c->ru, rbytes, cudaMemcpyDeviceToDevice, c->stream);
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  int bestP = c->P, bestMode = c->part_req;
+  float best = 1e30f;
+  for (int P = 1; P <= 32; P <<= 1) {
+    if (nx % P || nx / P > 16 || nx / P < 1) continue;
+    for (int mode : {NS_PART_AUTO, NS_PART_PPT}) {
+      if (ns_set_partition(c, 0, P, mode) != NS_OK) continue;
+      if (mode == NS_PART_PPT && c->part_mode != NS_PART_PPT) continue;
+      launch_adi_x(c, 0);
+      cudaEventRecord(e0, c->stream);
+      for (int it = 0; it < 5; ++it) launch_adi_x(c, it % 3);
+      cudaEventRecord(e1, c->stream);
+      cudaEventSynchronize(e1);
+      float ms = 0;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (cudaGetLastError() == cudaSuccess && ms < best) {
+        best = ms;
+        bestP = P;
+        bestMode = mode;
+      }
+    }
+  }
+  cudaMemcpyAsync(c->ru, save, rbytes, cudaMemcpyDeviceToDevice, c->stream);
+  cudaStreamSynchronize(c->stream);
+  cudaFree(save);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return ns_set_partition(c, 0, bestP, bestMode);
+}
+
+ns_status ns_get_buffer(ns_ctx* c, int which, void** ptr, size_t* bytes) {
+  if (!c || !ptr) return NS_ERR_ARG;
+  static const int map[8] = {LB_RU, LB_RV, LB_RW, LB_NU, LB_NV, LB_NW, LB_PHI, LB_SPEC};
+  if (which < 0 || which > 7) return fail(c, NS_ERR_ARG, "unknown buffer");
+  const int b = map[which];
+  const size_t nx = c->cfg.nx, ny = c->cfg.ny, nz = c->cfg.nz;
+  size_t n;
+  switch (which) {
+    case NS_BUF_RV:
+    case NS_BUF_NV: n = nx * (ny + 1) * nz * c->es; break;
+    case NS_BUF_PHI: n = nx * ny * nz * 8; break;
+    case NS_BUF_SPEC: n = (size_t)c->nzh * ny * nx * 16; break;
+    default: n = nx * ny * nz * c->es;
+  }
+  *ptr = (char*)c->ws + c->lay.off[b];
+  if (bytes) *bytes = n;
+  return NS_OK;
+}
+
+ns_status ns_sync(ns_ctx* c) {
+  if (!c) return NS_ERR_ARG;
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "stream");
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(c, e, "async");
+  return NS_OK;
+}
+
+const char* ns_last_error(ns_ctx* c) {
+  if (!c) return g_init_error.c_str();
+  return c->err.c_str();
+}
+
+void ns_destroy(ns_ctx* c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->stream);
+  drop_graph(c);
+  cudaStreamDestroy(c->cap_stream);
+  if (c->own_ws) cudaFree(c->ws);
+  delete c;
+}
+
+}  // extern "C"

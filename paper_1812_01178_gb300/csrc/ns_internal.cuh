@@ -1,0 +1,107 @@
+// Internal declarations shared by the CUDA translation units of the library.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string>
+#include <vector>
+
+#include "../../include/ns.h"
+
+#define NS_FULL_MASK 0xffffffffu
+
+// ---------------------------------------------------------------------------------------------
+// Grid coefficient block (device, double): NS_GC_COUNT arrays of (ny + 1) entries each.
+//   DY, IDY    : cell height dy_j = yf_{j+1} - yf_j and its inverse (j < ny)
+//   HC, IHC    : centre spacing across face j, hc_j = yc_j - yc_{j-1}, and inverse (1 <= j < ny)
+//   WLO, WHI   : linear-interpolation weights of centres j-1 and j at face j (1 <= j < ny)
+//   AC, CC     : y second-derivative weights of the lower / upper neighbour at centre j
+//                (three-point non-uniform formula, exact for quadratics; the wall neighbour
+//                 value is 0; CC = 0 at a stress-free top)
+//   AF, CF     : the same weights at interior face j (1 <= j < ny)
+//   PA, PC     : Poisson y rows 1/(dy_j hc_j) and 1/(dy_j hc_{j+1}) (zero at the boundaries)
+// ---------------------------------------------------------------------------------------------
+enum { GC_DY = 0, GC_IDY, GC_HC, GC_IHC, GC_WLO, GC_WHI, GC_AC, GC_CC, GC_AF, GC_CF, GC_PA, GC_PC,
+       NS_GC_COUNT };
+
+// RK3 constants (Sec. 2.2): gamma, zeta, alpha = gamma + zeta.
+static const double NS_GAMMA[3] = {8.0 / 15.0, 5.0 / 12.0, 3.0 / 4.0};
+static const double NS_ZETA[3] = {0.0, -17.0 / 60.0, -5.0 / 12.0};
+static const double NS_ALPHA[3] = {8.0 / 15.0, 2.0 / 15.0, 1.0 / 3.0};
+
+// ---------------------------------------------------------------------------------------------
+// Partitioned x-line solver tables (Sec. 3.2), one per sub-step, element type T.
+// P partitions of M rows; L = log2(P) reduction levels (0 for PDD).
+//   [0 .. 5MP)         : per (field f, row e, partition r) at (f*M + e)*P + r, fields
+//                        INV (1/pivot), AINV (a/pivot), CP (c/pivot) of the block Thomas
+//                        factorisation of A~, and the spikes V, W (Eq. blockAY)
+//   [5MP .. 5MP+4P)    : inverse of the final 2x2 diagonal block of interface r, [4][P]
+//   then L levels of ML [4][P] and L levels of MU [4][P]: block eliminators of the reduced
+//   system (block parallel cyclic reduction across partitions, precomputed because the
+//   matrix is the same for every line)
+// ---------------------------------------------------------------------------------------------
+enum { XT_INV = 0, XT_AINV, XT_CP, XT_V, XT_W, XT_NF };
+__host__ __device__ inline size_t xtab_count(int M, int P, int L) {
+  return (size_t)XT_NF * M * P + 4 * (size_t)P + 8 * (size_t)L * P;
+}
+
+struct ns_layout {
+  size_t off[32];
+  size_t total;
+};
+
+enum {
+  LB_RU = 0, LB_RV, LB_RW, LB_NU, LB_NV, LB_NW, LB_PHI, LB_SPEC, LB_POIS, LB_GC, LB_XTAB, LB_YTAB,
+  LB_ZTAB, LB_TWZ, LB_TWX, LB_LAMX, LB_LAMZ, LB_COUNT
+};
+
+struct ns_ctx {
+  ns_config cfg;
+  std::vector<double> yf;
+  ns_fields f;
+  cudaStream_t stream;      // caller's stream
+  cudaStream_t launch;      // where stage launches go (caller's stream, or the capture stream)
+  cudaStream_t cap_stream;  // private stream used for graph capture
+  void* ws;
+  size_t ws_bytes;
+  bool own_ws;
+  ns_layout lay;
+  int es;                   // bytes per element of r / N (8 FP64, 4 mixed)
+  int nzh;                  // nz/2 + 1
+  double dx, dz;
+  // device pointers (into ws)
+  void *ru, *rv, *rw, *nu, *nv, *nw;
+  double* phi;
+  double2* spec;
+  double2* pois;
+  double* gc;
+  void* xtab[3];
+  void* ytab[3][2];
+  void* ztab[3];
+  double2* twz;
+  double2* twx;
+  // partitioned x solver
+  int P, M, L[3];
+  int part_req;             // NS_PART_AUTO / PPT / PDD
+  int part_mode;            // resolved: NS_PART_PPT or NS_PART_PDD
+  double pdd_drop;
+  size_t xtab_stride;       // elements reserved per sub-step
+  // graph
+  cudaGraph_t graph;
+  cudaGraphExec_t gexec;
+  bool have_graph;
+  std::string err;
+};
+
+// Launchers (enqueue on ctx->launch).  Return cudaGetLastError() of the launch.
+cudaError_t launch_rhs(ns_ctx* c, int k);
+cudaError_t launch_adi_x(ns_ctx* c, int k);
+cudaError_t launch_adi_y(ns_ctx* c, int k);
+cudaError_t launch_adi_z(ns_ctx* c, int k);
+cudaError_t launch_poisson(ns_ctx* c, int k);
+cudaError_t launch_project(ns_ctx* c, int k);
+cudaError_t launch_pois_factor(ns_ctx* c, const double* lamx, const double* lamz);
+cudaError_t poisson_set_attributes();  // once per process and device, outside any capture
+
+// Host-side table builders (ns_tables.cpp-style code lives in ns_api.cu).
+size_t adi_y_tab_count(int ny);
+size_t adi_z_tab_count(int nz);
