@@ -1,0 +1,353 @@
+"""Benchmark: grid-point-steps/s of the fractional-step NS step on one GB300 (and N replicas).
+
+Default workload: the turbulent-channel-sized FP64 step, 256 x 192 x 256 cells, periodic x and z,
+tanh-stretched y with no-slip walls, Re_tau = 395 log-law field with 10 % Gaussian fluctuations
+(seeded, synthetic), dt fixed from CFL 0.5.  One step = three RK3 sub-steps, each: RHS, ADI x
+(PDD/PPT partitioned), ADI y, ADI z (+u*), divergence + z FFT, x FFT, y tridiagonal per (kx, kz),
+inverse x FFT, inverse z FFT, projection.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|mixed] [--impl ours|reference]
+
+Prints one JSON line.  N > 1 runs under torch.distributed.run: every rank advances its own
+replica (the single-instance path has no data-path exchange), value = cells*steps summed over
+ranks / max-over-ranks time.  --impl reference times the FP64 CPU oracle on the same workload
+(bounded samples of it) on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "grid-point-steps/s at 1 GB300 (FP64 vs mixed) + % HBM roofline per sweep"
+UNIT = "grid-point-steps/s"
+
+# Algorithmic work per cell per launch of each kernel (FP64 path), see the design doc section 5:
+# bytes = each input read once + each output written once; flops = floating-point operations of
+# the formulas (FMA = 2).  Complex spectral arrays have (nz/2+1)/nz of a cell each.
+def kernel_model(nx, ny, nz, es):
+    sh = (nz // 2 + 1) / nz
+    L = lambda n: math.log2(n)
+    return {
+        #                 bytes per cell                       flops per cell
+        "rhs":              (4 * 8 + 3 * es + 6 * es,        170.0),
+        "adi_x":            (6 * es,                         30.0),
+        "adi_y":            (6 * es,                         15.0),
+        "adi_z":            (3 * es + 6 * 8,                 24.0),
+        "poisson_div_fftz": (3 * 8 + sh * 16,                9.0 + 2.5 * L(nz) + 2.0),
+        "poisson_fftx_fwd": (2 * sh * 16,                    sh * 5.0 * L(nx)),
+        "poisson_tdma_y":   (3 * sh * 16,                    sh * 10.0),
+        "poisson_fftx_inv": (2 * sh * 16,                    sh * 5.0 * L(nx)),
+        "poisson_ifftz":    (sh * 16 + 8,                    2.5 * L(nz) + 2.0),
+        "project":          (8 + 8 * 8,                      11.0),
+    }
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured", float(d.get("sm_max_mhz", 2070.0))
+    except Exception:
+        return 6800.0, "fallback", 2070.0
+
+
+# FP64 ALU peak from unit counts and clock: 152 SMs x 2 FP64 FMA/clk/SM x 2 flop x f_max.
+def fp64_peak_tflops(sm_mhz):
+    return 152 * 2 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def fp32_peak_tflops(sm_mhz):
+    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+# ------------------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = str(gpu_index)
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", self.gpu, "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, pw, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                pw.append(float(parts[3]))
+            except ValueError:
+                continue
+            for n, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(pw) if pw else None, "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------------------------ oracle sample
+def oracle_sample_substep(O, g, st, k, dt, re, fx, F, part=0):
+    """One RK3 sub-step of the FP64 oracle on 1/F of every stage's work, line lengths unchanged:
+    RHS, x and y sweeps, x transforms and projection on a z-slab of nz/F planes; z sweeps and z
+    transforms on nx/F x-columns (all nz planes); y solves on the slab's nz/F spanwise modes."""
+    nz, ny, nx = g.nz, g.ny, g.nx
+    nzs = max(1, nz // F)
+    k0 = (part * nzs) % nz
+    ncol = max(1, nx // F)
+    i0 = (part * ncol) % nx
+    gs = O.Grid(nx, ny, nzs, g.lx, g.lz * nzs / nz, g.yf, g.ytop)
+    sl = slice(k0, k0 + nzs)
+    cols = slice(i0, i0 + ncol)
+    u, v, w, p = (st[q][sl] for q in ("u", "v", "w", "p"))
+    nprev = None if k == 0 else [a[sl] for a in st["nprev"]]
+    r, N = O.rhs(gs, u, v, w, p, nprev, k, dt, re, fx)
+    beta = O.RK3_ALPHA[k] * dt / (2 * re)
+    d = [O.adi_sweep(gs, r[c], 0, c, beta) for c in range(3)]
+    d = [O.adi_sweep(gs, d[c], 1, c, beta) for c in range(3)]
+    zcols = [st[q][:, :, cols] for q in ("u", "v", "w")]
+    [O.adi_sweep(g, zc, 2, c, beta) for c, zc in enumerate(zcols)]
+    us, vs, ws = u + d[0], v + d[1], w + d[2]
+    b = O.divergence(gs, us, vs, ws) / (O.RK3_ALPHA[k] * dt)
+    bh = O.dft(b.astype(np.complex128), 2)
+    O.dft(st["p"][:, :, cols].astype(np.complex128), 0)
+    a_, c_ = O.poisson_ycoeffs(g)
+    lam = O.modified_wavenumbers(nz, g.dz)[sl][:, None] + O.modified_wavenumbers(nx, g.dx)[None, :]
+    dd = np.moveaxis(bh, 1, -1)
+    B = -(a_ + c_)[None, None, :] - lam[:, :, None]
+    ph = np.moveaxis(O.thomas(a_, B, c_, dd), -1, 1)
+    O.dft(st["p"][:, :, cols].astype(np.complex128), 0, +1)
+    phi = O.dft(ph, 2, +1).real / (nx * nz)
+    O.project(gs, us, vs, ws, phi, O.RK3_ALPHA[k] * dt)
+    return N
+
+
+def oracle_baseline(case, u, v, w, p, F, nsub, warm=0):
+    """Time nsub sample sub-steps (k = 0, 1, 2, ...) of the oracle; returns (cell-steps/s, seconds)."""
+    from oracle import ns_oracle as O
+    g = O.Grid.from_case(case)
+    st = dict(u=u, v=v, w=w, p=p)
+    st["nprev"] = [np.zeros_like(u), np.zeros_like(v), np.zeros_like(w)]
+    for q in range(warm):
+        oracle_sample_substep(O, g, st, q % 3, case.dt, case.re, case.fx, F, part=q)
+    t0 = time.perf_counter()
+    for q in range(nsub):
+        oracle_sample_substep(O, g, st, q % 3, case.dt, case.re, case.fx, F, part=q)
+    t = time.perf_counter() - t0
+    # nsub sample sub-steps = nsub / (3 F) full steps of the workload
+    return case.cells() * (nsub / (3.0 * F)) / t, t
+
+
+# ------------------------------------------------------------------------------ main
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    from paper_1812_01178_gb300 import inputs as I
+    case, u0, v0, w0, p0 = I.turbulent_channel()
+    case.precision = 1 if args.precision == "mixed" else 0
+    cells = case.cells()
+    config = {"workload": "turbulent_channel_256x192x256_%s" % args.precision, "nx": case.nx, "ny": case.ny,
+              "nz": case.nz, "re_tau": case.re, "dt": case.dt, "cfl": 0.5, "bc": "periodic x,z; no-slip walls y",
+              "precision": args.precision, "l2": "inputs larger than L2 (state 0.40 GB + workspace)"}
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        import multiprocessing
+        F = 64
+        t_all0 = time.perf_counter()
+        val, t = oracle_baseline(case, u0, v0, w0, p0, F, args.steps, warm=args.warmup)
+        cores = os.cpu_count()
+        sample = ("each step: one RK3 sub-step of the FP64 numpy oracle on 1/%d of every stage's lines and "
+                  "cells of this workload (full line lengths), scaled by %d x 3" % (F, F))
+        out = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+               "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+               "data": "synthetic (seeded Re_tau 395 log-law channel field)", "config": config,
+               "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+               "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+               "gpu_launches": 0, "wall_s": time.perf_counter() - t_all0}
+        print(json.dumps(out))
+        return
+
+    # cpu baseline first, in this process, before any CUDA work
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        F = 8
+        val, t = oracle_baseline(case, u0, v0, w0, p0, F, 3)
+        cpu = {"value": val, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+               "sample": "one RK3 step (3 sub-steps) of the FP64 numpy oracle on 1/%d of every stage's lines "
+                         "and cells of this workload (full line lengths), scaled by %d; %.1f s" % (F, F, t)}
+
+    import torch
+    from paper_1812_01178_gb300 import binding as B
+    import __graft_entry__
+    __graft_entry__.build()
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    s = B.Solver(case, u0, v0, w0, p0, device=str(dev))
+    s.make_divergence_free()
+    s.step(args.warmup)
+    s.step_profiled(1)
+    s.sync()
+    P, mode, drop = s.partition()
+    config["partition_x"] = {"P": P, "mode": "PDD" if mode == B.NS_PART_PDD else "PPT", "pdd_dropped": drop}
+
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    gpu_index = vis.split(",")[local] if vis else str(local)
+    clocks = ClockSampler(gpu_index)
+    stream = s.stream
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    ev0.record(stream)
+    kms = s.step_profiled(args.steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    if dist:
+        dist.barrier()
+    t_ms = ev0.elapsed_time(ev1)
+    t_max = t_ms
+    if dist:
+        tt = torch.tensor([t_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+    value = world * cells * args.steps / (t_max * 1e-3)
+
+    # per-kernel roofline of the dominant kernel
+    hbm, hbm_kind, smax = load_peaks()
+    es = 4 if args.precision == "mixed" else 8
+    model = kernel_model(case.nx, case.ny, case.nz, es)
+    launches = 3 * args.steps
+    kern = {}
+    for name, ms in kms.items():
+        per = ms / launches
+        b, f = model[name]
+        kern[name] = {"ms_per_launch": per, "share": ms / max(sum(kms.values()), 1e-9),
+                      "GBps": b * cells / (per * 1e-3) / 1e9, "GFLOPps": f * cells / (per * 1e-3) / 1e9}
+    top = max(kms, key=kms.get)
+    b, f = model[top]
+    per = kms[top] / launches
+    fp64 = not (args.precision == "mixed" and top in ("rhs", "adi_x", "adi_y"))
+    alu_peak = (fp64_peak_tflops(smax) if fp64 else fp32_peak_tflops(smax)) * 1e12
+    t_alu = f * cells / alu_peak
+    t_mem = b * cells / (hbm * 1e9)
+    traffic = None
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic_%s.json" % config["workload"])) as fh:
+            traffic = json.load(fh).get(top)
+    except Exception:
+        traffic = None
+    if t_alu >= t_mem:
+        ach = f * cells / (per * 1e-3) / 1e12
+        roof = {"kernel": top, "bound": "alu", "achieved": ach, "peak": alu_peak / 1e12, "unit": "TFLOP/s",
+                "frac": ach / (alu_peak / 1e12), "traffic": traffic,
+                "peak_source": "derived: 152 SMs x %s FMA/clk/SM x 2 x %.0f MHz" % ("2 FP64" if fp64 else "128 FP32", smax),
+                "algorithmic_flops_per_launch": f * cells}
+    else:
+        ach = b * cells / (per * 1e-3) / 1e9
+        roof = {"kernel": top, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                "frac": ach / hbm, "traffic": traffic, "peak_source": "%s hbm_gbs" % hbm_kind,
+                "algorithmic_bytes_per_launch": b * cells}
+
+    # end to end through the host-buffer entry point (pinned host memory)
+    hu = torch.from_numpy(np.ascontiguousarray(u0)).pin_memory().numpy()
+    hv = torch.from_numpy(np.ascontiguousarray(v0)).pin_memory().numpy()
+    hw = torch.from_numpy(np.ascontiguousarray(w0)).pin_memory().numpy()
+    hp = torch.from_numpy(np.ascontiguousarray(p0)).pin_memory().numpy()
+    B.ns_step_host(s.ctx, hu, hv, hw, hp, 1)
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        B.ns_step_host(s.ctx, hu, hv, hw, hp, 1)
+    te = time.perf_counter() - t0
+    if dist:
+        tt = torch.tensor([te], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        te = float(tt.item())
+    nbytes = (hu.nbytes + hv.nbytes + hw.nbytes + hp.nbytes)
+    e2e = {"value": world * cells * args.e2e_steps / te, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+           "d2h_bytes_per_step": nbytes, "steps": args.e2e_steps,
+           "path": "ns_step_host: pinned host state -> device, one step, device -> host, sync"}
+    s.close()
+    if dist:
+        dist.destroy_process_group()
+    if rank != 0:
+        return
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f64+f32",
+           "data": "synthetic (seeded Re_tau 395 log-law channel field, 10% Gaussian fluctuations, projected)",
+           "config": config, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+           "gpu_launches": 10 * 3 * args.steps, "clocks": ck,
+           "kernels": {k: {kk: round(vv, 4) for kk, vv in d.items()} for k, d in kern.items()}}
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

@@ -132,6 +132,19 @@ ns_status ns_substep(ns_ctx* ctx, int substep);
  * The three sub-steps are captured once as a CUDA graph and replayed. */
 ns_status ns_step(ns_ctx* ctx, int nsteps);
 
+/* ns_step with per-kernel timing: replays a captured step that also records a CUDA event before
+ * every kernel (and after the last) on the context's stream, waits for each step, and adds each
+ * kernel's event-to-event time (ms) into kernel_ms[ns_kernel_name index], summed over the three
+ * sub-steps and nsteps steps.  kernel_ms: host array of at least ns_kernel_count() floats (zeroed
+ * first).  The state advances exactly as with ns_step. */
+ns_status ns_step_profiled(ns_ctx* ctx, int nsteps, float* kernel_ms, int nk);
+
+/* Number of kernels in one sub-step, and the name of kernel idx (launch order: rhs, adi_x, adi_y,
+ * adi_z, poisson_div_fftz, poisson_fftx_fwd, poisson_tdma_y, poisson_fftx_inv, poisson_ifftz,
+ * project; "" if idx is out of range). */
+int ns_kernel_count(void);
+const char* ns_kernel_name(int idx);
+
 /* End-to-end variant of ns_step for callers whose state lives in HOST memory: copies u, v, w,
  * p from the host arrays (pinned memory recommended) to the context's device fields, runs
  * nsteps steps, copies them back and synchronises.  Host arrays use the device layout. */

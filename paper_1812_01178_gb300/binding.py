@@ -24,7 +24,7 @@ STATUS_NAMES = {0: "NS_OK", 1: "NS_ERR_ARG", 2: "NS_ERR_SIZE", 3: "NS_ERR_CUDA",
 
 # Every symbol declared in include/ns.h.
 EXPORTS = ["ns_workspace_bytes", "ns_init", "ns_rhs", "ns_adi_sweep", "ns_poisson_solve", "ns_project",
-           "ns_substep", "ns_step", "ns_step_host", "ns_make_divergence_free", "ns_set_partition",
+           "ns_substep", "ns_step", "ns_step_profiled", "ns_kernel_count", "ns_kernel_name", "ns_step_host", "ns_make_divergence_free", "ns_set_partition",
            "ns_get_partition", "ns_autotune", "ns_get_buffer", "ns_sync", "ns_last_error", "ns_destroy"]
 
 
@@ -68,6 +68,10 @@ def lib(path: str = LIB_PATH):
         getattr(L, name).argtypes = [vp, i]
     L.ns_adi_sweep.argtypes = [vp, i, i]
     L.ns_step_host.argtypes = [vp, vp, vp, vp, vp, i]
+    L.ns_step_profiled.argtypes = [vp, i, P(C.c_float), i]
+    L.ns_kernel_count.argtypes = []
+    L.ns_kernel_name.argtypes = [i]
+    L.ns_kernel_name.restype = C.c_char_p
     L.ns_make_divergence_free.argtypes = [vp]
     L.ns_set_partition.argtypes = [vp, i, i, i]
     L.ns_get_partition.argtypes = [vp, i, P(i), P(i), P(d)]
@@ -79,7 +83,7 @@ def lib(path: str = LIB_PATH):
     L.ns_destroy.argtypes = [vp]
     L.ns_destroy.restype = None
     for name in EXPORTS:
-        if name not in ("ns_workspace_bytes", "ns_last_error", "ns_destroy"):
+        if name not in ("ns_workspace_bytes", "ns_last_error", "ns_destroy", "ns_kernel_name"):
             getattr(L, name).restype = i
     _LIB = L
     return L
@@ -135,6 +139,22 @@ def ns_substep(ctx, k):
 
 def ns_step(ctx, nsteps):
     _check(ctx, lib().ns_step(ctx, nsteps))
+
+
+def ns_step_profiled(ctx, nsteps):
+    """Returns {kernel name: summed ms} over nsteps steps (3 launches of each kernel per step)."""
+    n = lib().ns_kernel_count()
+    buf = (C.c_float * n)()
+    _check(ctx, lib().ns_step_profiled(ctx, nsteps, buf, n))
+    return {ns_kernel_name(q): float(buf[q]) for q in range(n)}
+
+
+def ns_kernel_count():
+    return lib().ns_kernel_count()
+
+
+def ns_kernel_name(idx):
+    return lib().ns_kernel_name(idx).decode()
 
 
 def ns_step_host(ctx, u, v, w, p, nsteps):
@@ -246,6 +266,9 @@ class Solver:
 
     def step(self, n=1):
         ns_step(self.ctx, n)
+
+    def step_profiled(self, n=1):
+        return ns_step_profiled(self.ctx, n)
 
     def make_divergence_free(self):
         ns_make_divergence_free(self.ctx)

@@ -297,29 +297,78 @@ static int z_tile(int nz) {
   return tx;
 }
 
-cudaError_t launch_poisson(ns_ctx* c, int k) {
-  const int nx = c->cfg.nx, ny = c->cfg.ny, nz = c->cfg.nz;
+namespace {
+struct PoisShape {
+  int nx, ny, nz, lnz, lnx, TX, R;
+  size_t smz, smx;
+  long nrows;
+  unsigned bx;
+};
+PoisShape pois_shape(const ns_ctx* c) {
+  PoisShape q;
+  q.nx = c->cfg.nx;
+  q.ny = c->cfg.ny;
+  q.nz = c->cfg.nz;
+  q.lnz = ilog2(q.nz);
+  q.lnx = ilog2(q.nx);
+  q.TX = min(z_tile(q.nz), q.nx);
+  q.smz = (size_t)q.TX * q.nz * sizeof(double2);  // two buffers of TX/2 sequences
+  q.nrows = (long)c->nzh * q.ny;
+  q.R = 1;
+  while (q.R < 16 && (size_t)2 * q.R * 2 * q.nx * sizeof(double2) <= 64 * 1024) q.R <<= 1;
+  q.smx = (size_t)2 * q.R * q.nx * sizeof(double2);
+  q.bx = (unsigned)((q.nrows + q.R - 1) / q.R);
+  return q;
+}
+}  // namespace
+
+// A5: divergence of u* scaled by 1/(alpha_k dt) (1 if k < 0) + forward real FFT along z
+cudaError_t launch_pois_divz(ns_ctx* c, int k) {
+  const PoisShape q = pois_shape(c);
   const double scale = (k >= 0) ? 1.0 / (NS_ALPHA[k] * c->cfg.dt) : 1.0;
-  const int lnz = ilog2(nz), lnx = ilog2(nx);
-  const int TX = min(z_tile(nz), nx);
-  size_t smz = (size_t)TX * nz * sizeof(double2);  // two buffers of TX/2 sequences
-  div_fftz_kernel<<<dim3(nx / TX, ny), 256, smz, c->launch>>>(c->f.u, c->f.v, c->f.w, c->gc, c->twz, c->spec, nx,
-                                                              ny, nz, lnz, TX, 1.0 / c->dx, 1.0 / c->dz, scale);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  const long nrows = (long)c->nzh * ny;
-  int R = 1;
-  while (R < 16 && (size_t)2 * R * 2 * nx * sizeof(double2) <= 64 * 1024) R <<= 1;
-  const size_t smx = (size_t)2 * R * nx * sizeof(double2);
-  const unsigned bx = (unsigned)((nrows + R - 1) / R);
-  fftx_kernel<-1><<<bx, 256, smx, c->launch>>>(c->spec, c->twx, nrows, nx, lnx, R, 1.0);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  tdma_y_kernel<<<dim3((nx + 127) / 128, c->nzh), 128, 0, c->launch>>>(c->spec, c->pois, c->gc, nx, ny);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  fftx_kernel<1><<<bx, 256, smx, c->launch>>>(c->spec, c->twx, nrows, nx, lnx, R, 1.0 / ((double)nx * nz));
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  ifftz_kernel<<<dim3(nx / TX, ny), 256, smz, c->launch>>>(c->spec, c->twz, c->phi, nx, ny, nz, lnz, TX, 1.0);
+  div_fftz_kernel<<<dim3(q.nx / q.TX, q.ny), 256, q.smz, c->launch>>>(c->f.u, c->f.v, c->f.w, c->gc, c->twz,
+                                                                     c->spec, q.nx, q.ny, q.nz, q.lnz, q.TX,
+                                                                     1.0 / c->dx, 1.0 / c->dz, scale);
   return cudaGetLastError();
+}
+
+// A6: forward complex FFT along x
+cudaError_t launch_pois_fftx_fwd(ns_ctx* c, int) {
+  const PoisShape q = pois_shape(c);
+  fftx_kernel<-1><<<q.bx, 256, q.smx, c->launch>>>(c->spec, c->twx, q.nrows, q.nx, q.lnx, q.R, 1.0);
+  return cudaGetLastError();
+}
+
+// A7: complex tridiagonal solve along y per (kx, kz)
+cudaError_t launch_pois_tdma(ns_ctx* c, int) {
+  const PoisShape q = pois_shape(c);
+  tdma_y_kernel<<<dim3((q.nx + 127) / 128, c->nzh), 128, 0, c->launch>>>(c->spec, c->pois, c->gc, q.nx, q.ny);
+  return cudaGetLastError();
+}
+
+// A8: inverse complex FFT along x, scaled by 1/(nx nz)
+cudaError_t launch_pois_fftx_inv(ns_ctx* c, int) {
+  const PoisShape q = pois_shape(c);
+  fftx_kernel<1><<<q.bx, 256, q.smx, c->launch>>>(c->spec, c->twx, q.nrows, q.nx, q.lnx, q.R,
+                                                   1.0 / ((double)q.nx * q.nz));
+  return cudaGetLastError();
+}
+
+// A9: inverse real FFT along z -> phi
+cudaError_t launch_pois_ifftz(ns_ctx* c, int) {
+  const PoisShape q = pois_shape(c);
+  ifftz_kernel<<<dim3(q.nx / q.TX, q.ny), 256, q.smz, c->launch>>>(c->spec, c->twz, c->phi, q.nx, q.ny, q.nz,
+                                                                  q.lnz, q.TX, 1.0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_poisson(ns_ctx* c, int k) {
+  cudaError_t e;
+  if ((e = launch_pois_divz(c, k)) != cudaSuccess) return e;
+  if ((e = launch_pois_fftx_fwd(c, k)) != cudaSuccess) return e;
+  if ((e = launch_pois_tdma(c, k)) != cudaSuccess) return e;
+  if ((e = launch_pois_fftx_inv(c, k)) != cudaSuccess) return e;
+  return launch_pois_ifftz(c, k);
 }
 
 cudaError_t launch_project(ns_ctx* c, int k) {

@@ -273,6 +273,11 @@ void drop_graph(ns_ctx* c) {
     cudaGraphDestroy(c->graph);
     c->have_graph = false;
   }
+  if (c->have_pgraph) {
+    cudaGraphExecDestroy(c->pgexec);
+    cudaGraphDestroy(c->pgraph);
+    c->have_pgraph = false;
+  }
 }
 
 ns_status fail(ns_ctx* c, ns_status s, const std::string& msg) {
@@ -291,14 +296,58 @@ bool capturing(ns_ctx* c) {
   return st != cudaStreamCaptureStatusNone;
 }
 
-ns_status run_substep(ns_ctx* c, int k) {
-  cudaError_t e;
-  if ((e = launch_rhs(c, k)) != cudaSuccess) return cuda_fail(c, e, "rhs");
-  if ((e = launch_adi_x(c, k)) != cudaSuccess) return cuda_fail(c, e, "adi_x");
-  if ((e = launch_adi_y(c, k)) != cudaSuccess) return cuda_fail(c, e, "adi_y");
-  if ((e = launch_adi_z(c, k)) != cudaSuccess) return cuda_fail(c, e, "adi_z");
-  if ((e = launch_poisson(c, k)) != cudaSuccess) return cuda_fail(c, e, "poisson");
-  if ((e = launch_project(c, k)) != cudaSuccess) return cuda_fail(c, e, "project");
+// The kernels of one sub-step, in launch order (one launch each).
+struct Stage {
+  const char* name;
+  cudaError_t (*fn)(ns_ctx*, int);
+};
+const Stage STAGES[] = {
+    {"rhs", launch_rhs},                      // A1
+    {"adi_x", launch_adi_x},                  // A2
+    {"adi_y", launch_adi_y},                  // A3
+    {"adi_z", launch_adi_z},                  // A4
+    {"poisson_div_fftz", launch_pois_divz},   // A5
+    {"poisson_fftx_fwd", launch_pois_fftx_fwd},  // A6
+    {"poisson_tdma_y", launch_pois_tdma},     // A7
+    {"poisson_fftx_inv", launch_pois_fftx_inv},  // A8
+    {"poisson_ifftz", launch_pois_ifftz},     // A9
+    {"project", launch_project},              // A10
+};
+const int NSTAGES = (int)(sizeof(STAGES) / sizeof(STAGES[0]));
+
+ns_status run_substep(ns_ctx* c, int k, cudaEvent_t* ev = nullptr) {
+  for (int q = 0; q < NSTAGES; ++q) {
+    if (ev) cudaEventRecordWithFlags(ev[q], c->launch, cudaEventRecordExternal);
+    cudaError_t e = STAGES[q].fn(c, k);
+    if (e != cudaSuccess) return cuda_fail(c, e, STAGES[q].name);
+  }
+  return NS_OK;
+}
+
+// Capture the three sub-steps of one time step into a graph (optionally with event nodes).
+ns_status capture_step(ns_ctx* c, bool profiled, cudaGraph_t* graph, cudaGraphExec_t* exec) {
+  c->launch = c->cap_stream;
+  cudaError_t e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) {
+    c->launch = c->stream;
+    return cuda_fail(c, e, "begin capture");
+  }
+  ns_status s = NS_OK;
+  for (int k = 0; k < 3 && s == NS_OK; ++k) s = run_substep(c, k, profiled ? c->pev + k * NSTAGES : nullptr);
+  if (s == NS_OK && profiled) cudaEventRecordWithFlags(c->pev[3 * NSTAGES], c->cap_stream, cudaEventRecordExternal);
+  cudaGraph_t g = nullptr;
+  e = cudaStreamEndCapture(c->cap_stream, &g);
+  c->launch = c->stream;
+  if (s != NS_OK) {
+    if (g) cudaGraphDestroy(g);
+    return s;
+  }
+  if (e != cudaSuccess) return cuda_fail(c, e, "end capture");
+  if ((e = cudaGraphInstantiate(exec, g, 0)) != cudaSuccess) {
+    cudaGraphDestroy(g);
+    return cuda_fail(c, e, "graph instantiate");
+  }
+  *graph = g;
   return NS_OK;
 }
 
@@ -352,6 +401,8 @@ ns_status ns_init(ns_ctx** out, const ns_config* cfg, const ns_fields* fields, v
   c->dz = cfg->lz / cfg->nz;
   c->lay = make_layout(cfg);
   c->have_graph = false;
+  c->have_pgraph = false;
+  c->npev = 0;
   cudaError_t e;
   if (workspace) {
     if (ws_bytes < c->lay.total || (uintptr_t)workspace % 256 != 0) {
@@ -606,34 +657,50 @@ ns_status ns_step(ns_ctx* c, int nsteps) {
   if (nsteps < 0) return fail(c, NS_ERR_ARG, "nsteps must be >= 0");
   if (nsteps == 0) return NS_OK;
   if (capturing(c)) return fail(c, NS_ERR_STATE, "ns_step called while its stream is being captured");
-  cudaError_t e;
   if (!c->have_graph) {
-    c->launch = c->cap_stream;
-    if ((e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) {
-      c->launch = c->stream;
-      return cuda_fail(c, e, "begin capture");
-    }
-    ns_status s = NS_OK;
-    for (int k = 0; k < 3 && s == NS_OK; ++k) s = run_substep(c, k);
-    cudaGraph_t g = nullptr;
-    e = cudaStreamEndCapture(c->cap_stream, &g);
-    c->launch = c->stream;
-    if (s != NS_OK) {
-      if (g) cudaGraphDestroy(g);
-      return s;
-    }
-    if (e != cudaSuccess) return cuda_fail(c, e, "end capture");
-    if ((e = cudaGraphInstantiate(&c->gexec, g, 0)) != cudaSuccess) {
-      cudaGraphDestroy(g);
-      return cuda_fail(c, e, "graph instantiate");
-    }
-    c->graph = g;
+    ns_status s = capture_step(c, false, &c->graph, &c->gexec);
+    if (s != NS_OK) return s;
     c->have_graph = true;
   }
+  cudaError_t e;
   for (int s = 0; s < nsteps; ++s)
     if ((e = cudaGraphLaunch(c->gexec, c->stream)) != cudaSuccess) return cuda_fail(c, e, "graph launch");
   return NS_OK;
 }
+
+ns_status ns_step_profiled(ns_ctx* c, int nsteps, float* kernel_ms, int nk) {
+  if (!c || !kernel_ms) return NS_ERR_ARG;
+  if (nk < NSTAGES) return fail(c, NS_ERR_ARG, "kernel_ms needs ns_kernel_count() entries");
+  if (nsteps < 0) return fail(c, NS_ERR_ARG, "nsteps must be >= 0");
+  if (capturing(c)) return fail(c, NS_ERR_STATE, "ns_step_profiled during capture");
+  for (int q = 0; q < NSTAGES; ++q) kernel_ms[q] = 0.0f;
+  cudaError_t e;
+  if (!c->have_pgraph) {
+    if (c->npev == 0) {
+      for (int q = 0; q <= 3 * NSTAGES; ++q)
+        if ((e = cudaEventCreate(&c->pev[q])) != cudaSuccess) return cuda_fail(c, e, "event create");
+      c->npev = 3 * NSTAGES + 1;
+    }
+    ns_status s = capture_step(c, true, &c->pgraph, &c->pgexec);
+    if (s != NS_OK) return s;
+    c->have_pgraph = true;
+  }
+  for (int s = 0; s < nsteps; ++s) {
+    if ((e = cudaGraphLaunch(c->pgexec, c->stream)) != cudaSuccess) return cuda_fail(c, e, "graph launch");
+    if ((e = cudaEventSynchronize(c->pev[3 * NSTAGES])) != cudaSuccess) return cuda_fail(c, e, "profiled step");
+    for (int q = 0; q < 3 * NSTAGES; ++q) {
+      float ms = 0.0f;
+      if ((e = cudaEventElapsedTime(&ms, c->pev[q], c->pev[q + 1])) != cudaSuccess)
+        return cuda_fail(c, e, "event time");
+      kernel_ms[q % NSTAGES] += ms;
+    }
+  }
+  return NS_OK;
+}
+
+int ns_kernel_count(void) { return NSTAGES; }
+
+const char* ns_kernel_name(int idx) { return (idx >= 0 && idx < NSTAGES) ? STAGES[idx].name : ""; }
 
 ns_status ns_step_host(ns_ctx* c, double* u, double* v, double* w, double* p, int nsteps) {
   if (!c || !u || !v || !w || !p) return NS_ERR_ARG;
@@ -768,6 +835,7 @@ void ns_destroy(ns_ctx* c) {
   if (!c) return;
   cudaStreamSynchronize(c->stream);
   drop_graph(c);
+  for (int q = 0; q < c->npev; ++q) cudaEventDestroy(c->pev[q]);
   cudaStreamDestroy(c->cap_stream);
   if (c->own_ws) cudaFree(c->ws);
   delete c;

@@ -89,6 +89,13 @@ struct ns_ctx {
   cudaGraph_t graph;
   cudaGraphExec_t gexec;
   bool have_graph;
+  // profiled graph: the same launches with an event recorded before each kernel and after the
+  // last one
+  cudaGraph_t pgraph;
+  cudaGraphExec_t pgexec;
+  bool have_pgraph;
+  cudaEvent_t pev[64];
+  int npev;
   std::string err;
 };
 
@@ -97,7 +104,12 @@ cudaError_t launch_rhs(ns_ctx* c, int k);
 cudaError_t launch_adi_x(ns_ctx* c, int k);
 cudaError_t launch_adi_y(ns_ctx* c, int k);
 cudaError_t launch_adi_z(ns_ctx* c, int k);
-cudaError_t launch_poisson(ns_ctx* c, int k);
+cudaError_t launch_poisson(ns_ctx* c, int k);   // the five kernels below, in order
+cudaError_t launch_pois_divz(ns_ctx* c, int k);
+cudaError_t launch_pois_fftx_fwd(ns_ctx* c, int k);
+cudaError_t launch_pois_tdma(ns_ctx* c, int k);
+cudaError_t launch_pois_fftx_inv(ns_ctx* c, int k);
+cudaError_t launch_pois_ifftz(ns_ctx* c, int k);
 cudaError_t launch_project(ns_ctx* c, int k);
 cudaError_t launch_pois_factor(ns_ctx* c, const double* lamx, const double* lamz);
 cudaError_t poisson_set_attributes();  // once per process and device, outside any capture
