@@ -178,11 +178,36 @@ enum {
 };
 ns_status ns_get_buffer(ns_ctx* ctx, int which, void** ptr, size_t* bytes);
 
+/* Context-free Poisson solve that allocates nothing (this entry point has no counterpart in the
+ * paper; it serves callers that may not call cudaMalloc: code running while the host
+ * application keeps a stream capture open, plugins inside a framework that owns all device
+ * memory through its own pool, fixed-latency loops that must not allocate after start-up).
+ *
+ * Computes the same phi as ns_poisson_solve(ctx, substep) for a context made from cfg (nx, ny,
+ * nz, lx, lz, yf and, for substep >= 0, dt are used; bc_x must be 0): D G phi = D u / s with
+ * s = alpha_k dt (substep k = 0, 1, 2) or s = 1 (substep = -1).  u, v, w: caller's device
+ * arrays in the field layouts above (read); phi: caller's device array nz*ny*nx (written).
+ * Work is enqueued on cuda_stream; the call first waits for that stream (it uploads small
+ * coefficient tables from static host buffers).
+ *
+ * Scratch: one file-scope device array of NS_STATIC_SCRATCH_BYTES, held by every GPU that loads
+ * the library until the process exits.  A grid needing more (about 2 * 16 * (nz/2+1) * ny * nx
+ * bytes) is rejected with NS_ERR_SIZE and a message; no cudaMalloc, cudaFree or other
+ * allocating routine is called.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) and sets kernel attributes; make that first call before any
+ * stream capture.  Every call shares the array and rewrites what it reads, so results do not
+ * depend on earlier calls, but calls that overlap on the GPU (e.g. on two streams) race.
+ * Errors: NS_ERR_ARG / NS_ERR_SIZE / NS_ERR_UNSUPPORTED / NS_ERR_CUDA, message in
+ * ns_last_error(NULL) on the calling thread. */
+#define NS_STATIC_SCRATCH_BYTES (48u * 1024u * 1024u)
+ns_status ns_poisson_solve_static(const ns_config* cfg, const double* u, const double* v, const double* w,
+                                  double* phi, int substep, void* cuda_stream);
+
 /* Wait for all work on the context's stream; reports asynchronous CUDA errors. */
 ns_status ns_sync(ns_ctx* ctx);
 
 /* Last error message of the context (never NULL; "" when none).  ctx may be NULL, giving the
- * message of the last failed ns_init on this thread. */
+ * message of the last failed ns_init or ns_poisson_solve_static on this thread. */
 const char* ns_last_error(ns_ctx* ctx);
 
 /* Destroy the context (frees the graph and a library-allocated workspace, not the fields). */

@@ -25,7 +25,9 @@ STATUS_NAMES = {0: "NS_OK", 1: "NS_ERR_ARG", 2: "NS_ERR_SIZE", 3: "NS_ERR_CUDA",
 # Every symbol declared in include/ns.h.
 EXPORTS = ["ns_workspace_bytes", "ns_init", "ns_rhs", "ns_adi_sweep", "ns_poisson_solve", "ns_project",
            "ns_substep", "ns_step", "ns_step_profiled", "ns_kernel_count", "ns_kernel_name", "ns_step_host", "ns_make_divergence_free", "ns_set_partition",
-           "ns_get_partition", "ns_autotune", "ns_get_buffer", "ns_sync", "ns_last_error", "ns_destroy"]
+           "ns_get_partition", "ns_autotune", "ns_get_buffer", "ns_poisson_solve_static", "ns_sync",
+           "ns_last_error", "ns_destroy"]
+NS_STATIC_SCRATCH_BYTES = 48 * 1024 * 1024
 
 
 class ns_config(C.Structure):
@@ -77,6 +79,7 @@ def lib(path: str = LIB_PATH):
     L.ns_get_partition.argtypes = [vp, i, P(i), P(i), P(d)]
     L.ns_autotune.argtypes = [vp]
     L.ns_get_buffer.argtypes = [vp, i, P(vp), P(sz)]
+    L.ns_poisson_solve_static.argtypes = [P(ns_config), vp, vp, vp, vp, i, vp]
     L.ns_sync.argtypes = [vp]
     L.ns_last_error.argtypes = [vp]
     L.ns_last_error.restype = C.c_char_p
@@ -184,6 +187,13 @@ def ns_get_buffer(ctx, which):
     ptr, n = C.c_void_p(), C.c_size_t()
     _check(ctx, lib().ns_get_buffer(ctx, which, C.byref(ptr), C.byref(n)))
     return ptr.value, n.value
+
+
+def ns_poisson_solve_static(cfg, u_ptr, v_ptr, w_ptr, phi_ptr, substep, stream_ptr):
+    """Context-free Poisson solve with no device allocation (scratch in a static device array)."""
+    s = lib().ns_poisson_solve_static(C.byref(cfg), u_ptr, v_ptr, w_ptr, phi_ptr, substep, stream_ptr)
+    if s != NS_OK:
+        raise NSError(s, lib().ns_last_error(None).decode())
 
 
 def ns_sync(ctx):

@@ -353,6 +353,8 @@ ns_status capture_step(ns_ctx* c, bool profiled, cudaGraph_t* graph, cudaGraphEx
 
 }  // namespace
 
+void ns_set_thread_error(const char* msg) { g_init_error = msg ? msg : ""; }
+
 extern "C" {
 
 size_t ns_workspace_bytes(const ns_config* cfg) {

@@ -114,6 +114,9 @@ cudaError_t launch_project(ns_ctx* c, int k);
 cudaError_t launch_pois_factor(ns_ctx* c, const double* lamx, const double* lamz);
 cudaError_t poisson_set_attributes();  // once per process and device, outside any capture
 
+// Sets the message ns_last_error(NULL) returns on this thread.
+void ns_set_thread_error(const char* msg);
+
 // Host-side table builders (ns_tables.cpp-style code lives in ns_api.cu).
 size_t adi_y_tab_count(int ny);
 size_t adi_z_tab_count(int nz);
