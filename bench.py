@@ -72,6 +72,23 @@ def fp32_peak_tflops(sm_mhz):
     return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
 
 
+def load_traffic(workload, kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu capture of this workload, or None
+    if there is none or the kernel's source file changed since the counters were taken."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic_%s.json" % workload)) as fh:
+            rec = json.load(fh).get(kernel)
+        if rec is None:
+            return None
+        with open(os.path.join(ROOT, rec["source"]), "rb") as fh:
+            if hashlib.sha256(fh.read()).hexdigest()[:16] != rec["source_sha256_16"]:
+                return None
+        return rec["bytes_per_launch"]
+    except Exception:
+        return None
+
+
 # ------------------------------------------------------------------------------ clocks
 class ClockSampler:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -187,6 +204,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--no-mixed", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -296,12 +314,7 @@ def main():
     alu_peak = (fp64_peak_tflops(smax) if fp64 else fp32_peak_tflops(smax)) * 1e12
     t_alu = f * cells / alu_peak
     t_mem = b * cells / (hbm * 1e9)
-    traffic = None
-    try:
-        with open(os.path.join(ROOT, "profiles", "traffic_%s.json" % config["workload"])) as fh:
-            traffic = json.load(fh).get(top)
-    except Exception:
-        traffic = None
+    traffic = load_traffic(config["workload"], top)
     if t_alu >= t_mem:
         ach = f * cells / (per * 1e-3) / 1e12
         roof = {"kernel": top, "bound": "alu", "achieved": ach, "peak": alu_peak / 1e12, "unit": "TFLOP/s",
@@ -314,26 +327,65 @@ def main():
                 "frac": ach / hbm, "traffic": traffic, "peak_source": "%s hbm_gbs" % hbm_kind,
                 "algorithmic_bytes_per_launch": b * cells}
 
+    # mixed precision on the same workload: throughput, speedup, and difference from FP64
+    mixed = None
+    if args.precision == "fp64" and not args.no_mixed:
+        sm = B.Solver(case, u0, v0, w0, p0, precision=B.NS_MIXED, device=str(dev))
+        sm.make_divergence_free()
+        sm.step(args.warmup)
+        sm.sync()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        ev0.record(sm.stream)
+        sm.step(args.steps)
+        ev1.record(sm.stream)
+        torch.cuda.synchronize()
+        tm = ev0.elapsed_time(ev1)
+        sm.close()
+        # accuracy: both forms from the same projected state, 10 steps
+        sa = B.Solver(case, u0, v0, w0, p0, device=str(dev))
+        sb = B.Solver(case, u0, v0, w0, p0, precision=B.NS_MIXED, device=str(dev))
+        sa.make_divergence_free()
+        sb.make_divergence_free()
+        sa.step(10)
+        sb.step(10)
+        sa.sync()
+        sb.sync()
+        vel = math.sqrt(sum(float(torch.linalg.vector_norm(t)) ** 2 for t in (sa.u, sa.v, sa.w)))
+        err = {n: float(torch.linalg.vector_norm(getattr(sb, n) - getattr(sa, n))) / vel for n in ("u", "v", "w")}
+        pa = sa.p - sa.p.mean()
+        pb = sb.p - sb.p.mean()
+        err["p"] = float(torch.linalg.vector_norm(pb - pa)) / max(float(torch.linalg.vector_norm(pa)),
+                                                                  vel * vel / math.sqrt(pa.numel()))
+        sa.close()
+        sb.close()
+        mixed = {"value": world * cells * args.steps / (tm * 1e-3), "ms_per_step": tm / args.steps,
+                 "speedup_vs_fp64": t_max / tm, "rel_l2_vs_fp64_after_10_steps": err,
+                 "dtype": "f32 increments (rhs, adi) on f64 state; f64 divergence/poisson/projection"}
+
     # end to end through the host-buffer entry point (pinned host memory)
     hu = torch.from_numpy(np.ascontiguousarray(u0)).pin_memory().numpy()
     hv = torch.from_numpy(np.ascontiguousarray(v0)).pin_memory().numpy()
     hw = torch.from_numpy(np.ascontiguousarray(w0)).pin_memory().numpy()
     hp = torch.from_numpy(np.ascontiguousarray(p0)).pin_memory().numpy()
-    B.ns_step_host(s.ctx, hu, hv, hw, hp, 1)
-    if dist:
-        dist.barrier()
-    t0 = time.perf_counter()
-    for _ in range(args.e2e_steps):
+    e2e = None
+    if args.e2e_steps > 0:
         B.ns_step_host(s.ctx, hu, hv, hw, hp, 1)
-    te = time.perf_counter() - t0
-    if dist:
-        tt = torch.tensor([te], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        te = float(tt.item())
-    nbytes = (hu.nbytes + hv.nbytes + hw.nbytes + hp.nbytes)
-    e2e = {"value": world * cells * args.e2e_steps / te, "unit": UNIT, "h2d_bytes_per_step": nbytes,
-           "d2h_bytes_per_step": nbytes, "steps": args.e2e_steps,
-           "path": "ns_step_host: pinned host state -> device, one step, device -> host, sync"}
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            B.ns_step_host(s.ctx, hu, hv, hw, hp, 1)
+        te = time.perf_counter() - t0
+        if dist:
+            tt = torch.tensor([te], device=dev, dtype=torch.float64)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            te = float(tt.item())
+        nbytes = (hu.nbytes + hv.nbytes + hw.nbytes + hp.nbytes)
+        e2e = {"value": world * cells * args.e2e_steps / te, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+               "d2h_bytes_per_step": nbytes, "steps": args.e2e_steps,
+               "path": "ns_step_host: pinned host state -> device, one step, device -> host, sync"}
     s.close()
     if dist:
         dist.destroy_process_group()
@@ -344,7 +396,7 @@ def main():
            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f64+f32",
            "data": "synthetic (seeded Re_tau 395 log-law channel field, 10% Gaussian fluctuations, projected)",
            "config": config, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
-           "gpu_launches": 10 * 3 * args.steps, "clocks": ck,
+           "gpu_launches": 10 * 3 * args.steps, "clocks": ck, "mixed": mixed,
            "kernels": {k: {kk: round(vv, 4) for kk, vv in d.items()} for k, d in kern.items()}}
     print(json.dumps(out))
 
