@@ -6,7 +6,7 @@
 //   for every (kx, kz): complex tridiagonal solve in y with rows
 //     a_j phi_{j-1} - (a_j + c_j + lam_x + lam_z) phi_j + c_j phi_{j+1} = b_j
 //   (zero normal gradient at both y boundaries; for (0,0) row 0 is replaced by phi_0 = 0)
-//   phi = IFFT_z IFFT_x phi^ / (nx nz)
+//   phi = IFFT_z IFFT_x phi^ / (nx nz)   (the 1/(nx nz) is applied to b before the transforms)
 //   u = u* - alpha_k dt G phi,  p = p + phi
 //
 // FFTs are radix-2 Stockham autosort transforms in shared memory with a precomputed twiddle
@@ -75,7 +75,9 @@ __global__ void __launch_bounds__(256) div_fftz_kernel(const double* __restrict_
   double2* B = A + nseq * nz;
   const int i0 = blockIdx.x * TX;
   const int j = blockIdx.y;
-  const double idy = __ldg(gc + GC_IDY * (ny + 1) + j);
+  const double idy = __ldg(gc + GC_IDY * (ny + 1) + j) * scale;
+  idx *= scale;
+  idz *= scale;
   const long pl = (long)ny * nx, plv = (long)(ny + 1) * nx;
   for (int q = threadIdx.x; q < TX * nz; q += blockDim.x) {
     const int il = q % TX;
@@ -87,7 +89,7 @@ __global__ void __launch_bounds__(256) div_fftz_kernel(const double* __restrict_
     const double du = __ldg(u + c + ip) - __ldg(u + c + i);
     const double dv = __ldg(v + k * plv + (long)(j + 1) * nx + i) - __ldg(v + k * plv + (long)j * nx + i);
     const double dw = __ldg(w + kp * pl + (long)j * nx + i) - __ldg(w + c + i);
-    const double b = (du * idx + dv * idy + dw * idz) * scale;
+    const double b = fma(du, idx, fma(dv, idy, dw * idz));  // scale folded into idx, idy, idz
     double* slot = reinterpret_cast<double*>(A + (il >> 1) * nz + k);
     slot[il & 1] = b;
   }
@@ -126,9 +128,13 @@ __global__ void __launch_bounds__(256) fftx_kernel(double2* __restrict__ spec, c
   for (int q = nr * nx + threadIdx.x; q < R * nx; q += blockDim.x) A[q] = make_double2(0.0, 0.0);
   __syncthreads();
   double2* Rb = stockham<SIGN>(A, B, nx, lnx, R, twx);
-  for (int q = threadIdx.x; q < nr * nx; q += blockDim.x) {
-    const double2 t = Rb[q];
-    g[q] = make_double2(t.x * scale, t.y * scale);
+  if (scale == 1.0) {
+    for (int q = threadIdx.x; q < nr * nx; q += blockDim.x) g[q] = Rb[q];
+  } else {
+    for (int q = threadIdx.x; q < nr * nx; q += blockDim.x) {
+      const double2 t = Rb[q];
+      g[q] = make_double2(t.x * scale, t.y * scale);
+    }
   }
 }
 
@@ -203,7 +209,8 @@ __global__ void __launch_bounds__(256) ifftz_kernel(const double2* __restrict__ 
     const int il = q % TX;
     const int k = q / TX;
     const double2 t = R[(il >> 1) * nz + k];
-    phi[k * pl + (long)j * nx + i0 + il] = ((il & 1) ? t.y : t.x) * scale;
+    const double val = (il & 1) ? t.y : t.x;
+    phi[k * pl + (long)j * nx + i0 + il] = (scale == 1.0) ? val : val * scale;
   }
 }
 
@@ -325,7 +332,8 @@ PoisShape pois_shape(const ns_ctx* c) {
 // A5: divergence of u* scaled by 1/(alpha_k dt) (1 if k < 0) + forward real FFT along z
 cudaError_t launch_pois_divz(ns_ctx* c, int k) {
   const PoisShape q = pois_shape(c);
-  const double scale = (k >= 0) ? 1.0 / (NS_ALPHA[k] * c->cfg.dt) : 1.0;
+  // 1/(alpha_k dt) of the right-hand side and 1/(nx nz) of the inverse transforms, applied once
+  const double scale = ((k >= 0) ? 1.0 / (NS_ALPHA[k] * c->cfg.dt) : 1.0) / ((double)q.nx * q.nz);
   div_fftz_kernel<<<dim3(q.nx / q.TX, q.ny), 256, q.smz, c->launch>>>(c->f.u, c->f.v, c->f.w, c->gc, c->twz,
                                                                      c->spec, q.nx, q.ny, q.nz, q.lnz, q.TX,
                                                                      1.0 / c->dx, 1.0 / c->dz, scale);
@@ -349,8 +357,7 @@ cudaError_t launch_pois_tdma(ns_ctx* c, int) {
 // A8: inverse complex FFT along x, scaled by 1/(nx nz)
 cudaError_t launch_pois_fftx_inv(ns_ctx* c, int) {
   const PoisShape q = pois_shape(c);
-  fftx_kernel<1><<<q.bx, 256, q.smx, c->launch>>>(c->spec, c->twx, q.nrows, q.nx, q.lnx, q.R,
-                                                   1.0 / ((double)q.nx * q.nz));
+  fftx_kernel<1><<<q.bx, 256, q.smx, c->launch>>>(c->spec, c->twx, q.nrows, q.nx, q.lnx, q.R, 1.0);
   return cudaGetLastError();
 }
 

@@ -5,8 +5,9 @@
 // distance-weighted linear interpolation in y.  L is the viscous operator (uniform second
 // differences in x and z, the three-point non-uniform formula in y).  G is the pressure gradient.
 //
-// One thread per (i, j) of one z-plane, j = 0..ny (row ny only writes the v wall row).  T is the
-// arithmetic type (double, or float for the mixed form), TR the storage type of r and N.
+// rhs_kernel: one thread per (i, j) of one z-plane, j = 0..ny (row ny only writes the v wall row),
+// used when nx is not a multiple of 32 or nz not a multiple of 8; rhs_tiled_kernel otherwise.
+// T is the arithmetic type (double, or float for the mixed form), TR the storage type of r and N.
 #include "ns_internal.cuh"
 
 namespace {
@@ -23,6 +24,7 @@ struct RhsArgs {
   void* nv;
   void* nw;
   const double* __restrict__ gc;
+  const double* __restrict__ rt;  // per-j assembly coefficients of this sub-step (RT_* rows)
   int nx, ny, nz;
   double idx, idz, idx2, idz2;
   double dt, gam, zet, alp, inv_re, fx;
@@ -154,7 +156,211 @@ __global__ void __launch_bounds__(128) rhs_kernel(RhsArgs a) {
   }
 }
 
+// ---------------------------------------------------------------------------------------------
+// Tiled form of the same right-hand side.  A block of TX x TZ threads owns a TX (x) by TZ (z)
+// column of cells and marches along y over [jb, je).  Four rolling planes of u, v, w, p (with a
+// one-cell halo in x and z, periodic wrap) sit in shared memory.  Every product the
+// divergence-form convection needs is computed once per tile and then differenced:
+//   centre squares  Q1 = (u_i + u_{i+1})^2, Q2 = (v_j + v_{j+1})^2, Q3 = (w_k + w_{k+1})^2
+//   edge fluxes     Fuv = u(yf_j) (v_{i-1} + v_i)       at (xf_i, yf_j)
+//                   Fuw = (u_{k-1} + u_k)(w_{i-1} + w_i) at (xf_i, zf_k)
+//                   Fvw = (v_{k-1} + v_k) w(yf_j)       at (yf_j, zf_k)
+// (factors 1/2, 1/4 of the averages are folded into the difference weights).  y-face fluxes of
+// face j+1 become those of face j in the next step; Q2 of centre j is kept in a register.
+// ---------------------------------------------------------------------------------------------
+constexpr int RT_X = 32;
+constexpr int RT_Z = 8;
+constexpr int RT_PX = RT_X + 2;   // plane pitch (x halo on both sides)
+constexpr int RT_PZ = RT_Z + 2;
+constexpr int RT_PLANE = RT_PX * RT_PZ;
+constexpr int RT_NPL = 4;         // rolling planes per field
+
+template <typename T>
+struct RhsTile {
+  T pl[4][RT_NPL][RT_PLANE];                 // u, v, w, p planes (j mod 4), index (kk+1)*RT_PX + (ii+1)
+  T fuv[2][RT_Z][RT_X + 1];                  // Fuv on y-face (parity), x = i0 .. i0+TX
+  T fvw[2][RT_Z + 1][RT_X];                  // Fvw on y-face (parity), z = k0 .. k0+TZ
+  T q1[RT_Z][RT_X + 1];                      // x = i0-1 .. i0+TX-1
+  T q3[RT_Z + 1][RT_X];                      // z = k0-1 .. k0+TZ-1
+  T fuw[RT_Z + 1][RT_X + 1];                 // x = i0 .. i0+TX, z = k0 .. k0+TZ
+};
+
+template <typename T, typename TR>
+__global__ void __launch_bounds__(RT_X * RT_Z) rhs_tiled_kernel(RhsArgs a, int jchunk) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  RhsTile<T>& S = *reinterpret_cast<RhsTile<T>*>(smem_raw);
+  const int nx = a.nx, ny = a.ny, nz = a.nz, ny1 = ny + 1, G = ny + 1;
+  const int tx = threadIdx.x, tz = threadIdx.y, tid = tz * RT_X + tx;
+  const int i0 = blockIdx.x * RT_X, k0 = blockIdx.y * RT_Z;
+  const int jb = blockIdx.z * jchunk;
+  const int je = min(jb + jchunk, ny);
+  const int jlast = (je == ny) ? ny : je - 1;  // v rows: the last chunk also writes face ny
+
+  auto C = [&](int f, int jj) -> T { return (T)__ldg(a.gc + f * G + jj); };
+  auto P = [&](int f, int j, int kk, int ii) -> T& { return S.pl[f][j & 3][(kk + 1) * RT_PX + ii + 1]; };
+
+  // load plane j of every field (centres for u, w, p; face j for v) with halo; zero outside
+  auto load_plane = [&](int j) {
+    for (int q = tid; q < 4 * RT_PLANE; q += RT_X * RT_Z) {
+      const int f = q / RT_PLANE, e = q - f * RT_PLANE;
+      const int kk = e / RT_PX - 1, ii = e % RT_PX - 1;
+      int gi = i0 + ii, gk = k0 + kk;
+      gi = gi < 0 ? gi + nx : (gi >= nx ? gi - nx : gi);
+      gk = gk < 0 ? gk + nz : (gk >= nz ? gk - nz : gk);
+      T val = (T)0;
+      if (f == 1) {
+        if (j >= 0 && j <= ny) val = (T)__ldg(a.v + ((long)gk * ny1 + j) * nx + gi);
+      } else if (j >= 0 && j < ny) {
+        const double* src = f == 0 ? a.u : (f == 2 ? a.w : a.p);
+        val = (T)__ldg(src + ((long)gk * ny + j) * nx + gi);
+      }
+      S.pl[f][j & 3][e] = val;
+    }
+  };
+  // y-face fluxes on face jf (Fuv, Fvw), zero on the walls
+  auto face_fluxes = [&](int jf) {
+    const bool inner = jf >= 1 && jf <= ny - 1;
+    const T wl = inner ? C(GC_WLO, jf) : (T)0, wh = inner ? C(GC_WHI, jf) : (T)0;
+    for (int q = tid; q < RT_Z * (RT_X + 1); q += RT_X * RT_Z) {
+      const int kk = q / (RT_X + 1), ii = q % (RT_X + 1);
+      T f = 0;
+      if (inner)
+        f = (wl * P(0, jf - 1, kk, ii) + wh * P(0, jf, kk, ii)) * (P(1, jf, kk, ii - 1) + P(1, jf, kk, ii));
+      S.fuv[jf & 1][kk][ii] = f;
+    }
+    for (int q = tid; q < (RT_Z + 1) * RT_X; q += RT_X * RT_Z) {
+      const int kk = q / RT_X, ii = q % RT_X;
+      T f = 0;
+      if (inner)
+        f = (P(1, jf, kk - 1, ii) + P(1, jf, kk, ii)) * (wl * P(2, jf - 1, kk, ii) + wh * P(2, jf, kk, ii));
+      S.fvw[jf & 1][kk][ii] = f;
+    }
+  };
+  // centre-plane products of plane j (Q1, Q3, Fuw)
+  auto centre_products = [&](int j) {
+    for (int q = tid; q < RT_Z * (RT_X + 1); q += RT_X * RT_Z) {
+      const int kk = q / (RT_X + 1), ii = q % (RT_X + 1) - 1;
+      const T s = P(0, j, kk, ii) + P(0, j, kk, ii + 1);
+      S.q1[kk][ii + 1] = s * s;
+    }
+    for (int q = tid; q < (RT_Z + 1) * RT_X; q += RT_X * RT_Z) {
+      const int kk = q / RT_X - 1, ii = q % RT_X;
+      const T s = P(2, j, kk, ii) + P(2, j, kk + 1, ii);
+      S.q3[kk + 1][ii] = s * s;
+    }
+    for (int q = tid; q < (RT_Z + 1) * (RT_X + 1); q += RT_X * RT_Z) {
+      const int kk = q / (RT_X + 1), ii = q % (RT_X + 1);
+      S.fuw[kk][ii] = (P(0, j, kk - 1, ii) + P(0, j, kk, ii)) * (P(2, j, kk, ii - 1) + P(2, j, kk, ii));
+    }
+  };
+
+  // r = cn N + cp N_prev + cgx (p_i - p_{i-1}) + cx (f_{i+1} + f_{i-1}) + cz (f_{k+1} + f_{k-1})
+  //     + cA f_{j-1} + cC f_{j+1} + cD f (+ cb for u), with every constant pre-multiplied by dt
+  const T qidx = (T)(0.25 * a.idx), qidz = (T)(0.25 * a.idz), hidx = (T)(0.5 * a.idx), hidz = (T)(0.5 * a.idz);
+  const T cn = (T)(-a.dt * a.gam), cp = (T)(-a.dt * a.zet);
+  const T cgx = (T)(-a.dt * a.alp * a.idx), cgz = (T)(-a.dt * a.alp * a.idz);
+  const T cl = (T)(a.dt * a.alp * a.inv_re);
+  const T cx = cl * (T)a.idx2, cz = cl * (T)a.idz2;
+  const T cb = (T)(a.dt * a.alp * a.fx);
+  const bool use_prev = a.zet != 0.0;
+  auto R = [&](int f, int jj) -> T { return (T)__ldg(a.rt + f * G + jj); };
+  TR* ru = (TR*)a.ru;
+  TR* rv = (TR*)a.rv;
+  TR* rw = (TR*)a.rw;
+  TR* nu = (TR*)a.nu;
+  TR* nv = (TR*)a.nv;
+  TR* nw = (TR*)a.nw;
+  const int i = i0 + tx, k = k0 + tz;
+
+  // prologue: planes jb-1, jb, jb+1; fluxes of face jb; Q2 of centre jb-1
+  load_plane(jb - 1);
+  load_plane(jb);
+  __syncthreads();
+  face_fluxes(jb);
+  T q2prev = 0;
+  {
+    const T s = P(1, jb - 1, tz, tx) + P(1, jb, tz, tx);
+    q2prev = (jb >= 1) ? s * s : (T)0;
+  }
+  for (int j = jb; j <= jlast; ++j) {
+    load_plane(j + 1);
+    __syncthreads();
+    face_fluxes(j + 1);
+    centre_products(j);
+    __syncthreads();
+    // ---------------- v at face j
+    {
+      const long cf = ((long)k * ny1 + j) * nx + i;
+      const T sv = P(1, j, tz, tx) + P(1, j + 1, tz, tx);
+      const T q2 = sv * sv;  // Q2 of centre j (zero planes beyond the top)
+      if (j == 0 || j == ny) {
+        rv[cf] = (TR)0;
+        nv[cf] = (TR)0;
+      } else {
+        const T n = (S.fuv[j & 1][tz][tx + 1] - S.fuv[j & 1][tz][tx]) * hidx + (q2 - q2prev) * R(RT_QIHC, j) +
+                    (S.fvw[j & 1][tz + 1][tx] - S.fvw[j & 1][tz][tx]) * hidz;
+        const T v0 = P(1, j, tz, tx);
+        T r = cn * n + R(RT_CGY, j) * (P(3, j, tz, tx) - P(3, j - 1, tz, tx));
+        r += cx * (P(1, j, tz, tx + 1) + P(1, j, tz, tx - 1));
+        r += cz * (P(1, j, tz + 1, tx) + P(1, j, tz - 1, tx));
+        r += R(RT_AF, j) * P(1, j - 1, tz, tx) + R(RT_CF, j) * P(1, j + 1, tz, tx) + R(RT_DF, j) * v0;
+        if (use_prev) r += cp * (T)nv[cf];
+        rv[cf] = (TR)r;
+        nv[cf] = (TR)n;
+      }
+      q2prev = q2;
+    }
+    if (j < ny) {
+      const long cc = ((long)k * ny + j) * nx + i;
+      const T hidy = R(RT_HIDY, j);
+      const T cA = R(RT_AC, j), cC = R(RT_CC, j), cD = R(RT_DC, j);
+      // ---------------- u at (xf_i, yc_j, zc_k)
+      {
+        const T u0 = P(0, j, tz, tx);
+        const T n = (S.q1[tz][tx + 1] - S.q1[tz][tx]) * qidx +
+                    (S.fuv[(j + 1) & 1][tz][tx] - S.fuv[j & 1][tz][tx]) * hidy +
+                    (S.fuw[tz + 1][tx] - S.fuw[tz][tx]) * qidz;
+        T r = cn * n + cb + cgx * (P(3, j, tz, tx) - P(3, j, tz, tx - 1));
+        r += cx * (P(0, j, tz, tx + 1) + P(0, j, tz, tx - 1));
+        r += cz * (P(0, j, tz + 1, tx) + P(0, j, tz - 1, tx));
+        r += cA * P(0, j - 1, tz, tx) + cC * P(0, j + 1, tz, tx) + cD * u0;
+        if (use_prev) r += cp * (T)nu[cc];
+        ru[cc] = (TR)r;
+        nu[cc] = (TR)n;
+      }
+      // ---------------- w at (xc_i, yc_j, zf_k)
+      {
+        const T w0 = P(2, j, tz, tx);
+        const T n = (S.fuw[tz][tx + 1] - S.fuw[tz][tx]) * qidx +
+                    (S.fvw[(j + 1) & 1][tz][tx] - S.fvw[j & 1][tz][tx]) * hidy +
+                    (S.q3[tz + 1][tx] - S.q3[tz][tx]) * qidz;
+        T r = cn * n + cgz * (P(3, j, tz, tx) - P(3, j, tz - 1, tx));
+        r += cx * (P(2, j, tz, tx + 1) + P(2, j, tz, tx - 1));
+        r += cz * (P(2, j, tz + 1, tx) + P(2, j, tz - 1, tx));
+        r += cA * P(2, j - 1, tz, tx) + cC * P(2, j + 1, tz, tx) + cD * w0;
+        if (use_prev) r += cp * (T)nw[cc];
+        rw[cc] = (TR)r;
+        nw[cc] = (TR)n;
+      }
+    }
+  }
+}
+
 }  // namespace
+
+cudaError_t rhs_set_attributes(int* bps_fp64, int* bps_fp32) {
+  cudaError_t e = cudaFuncSetAttribute(rhs_tiled_kernel<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)sizeof(RhsTile<double>));
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(rhs_tiled_kernel<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)sizeof(RhsTile<float>));
+  if (e != cudaSuccess) return e;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps_fp64, rhs_tiled_kernel<double, double>, RT_X * RT_Z,
+                                                    sizeof(RhsTile<double>));
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps_fp32, rhs_tiled_kernel<float, float>, RT_X * RT_Z,
+                                                       sizeof(RhsTile<float>));
+}
 
 cudaError_t launch_rhs(ns_ctx* c, int k) {
   RhsArgs a;
@@ -182,6 +388,33 @@ cudaError_t launch_rhs(ns_ctx* c, int k) {
   a.alp = NS_ALPHA[k];
   a.inv_re = c->cfg.re > 0 ? 1.0 / c->cfg.re : 0.0;
   a.fx = c->cfg.fx;
+  a.rt = c->rtab[k];
+  if (a.nx % RT_X == 0 && a.nz % RT_Z == 0) {
+    // split y into chunks (each re-derives one face and two planes) so that the blocks fill
+    // whole waves of the resident capacity: minimise waves * (planes per chunk + prologue)
+    const int tiles = (a.nx / RT_X) * (a.nz / RT_Z);
+    const int resident = c->num_sms * (c->cfg.precision == NS_MIXED ? c->rhs_bps[1] : c->rhs_bps[0]);
+    int best_nch = 1;
+    double best = 1e300;
+    for (int nch = 1; nch <= (a.ny + 5) / 6 && nch <= 64; ++nch) {
+      const int jc = (a.ny + nch - 1) / nch;
+      const long nb = (long)tiles * ((a.ny + jc - 1) / jc);
+      const long waves = (nb + resident - 1) / resident;
+      const double cost = (double)waves * (jc + 2.0);
+      if (cost < best - 1e-9) {
+        best = cost;
+        best_nch = nch;
+      }
+    }
+    const int jchunk = (a.ny + best_nch - 1) / best_nch;
+    const int nch = (a.ny + jchunk - 1) / jchunk;
+    dim3 grid(a.nx / RT_X, a.nz / RT_Z, nch), block(RT_X, RT_Z);
+    if (c->cfg.precision == NS_MIXED)
+      rhs_tiled_kernel<float, float><<<grid, block, sizeof(RhsTile<float>), c->launch>>>(a, jchunk);
+    else
+      rhs_tiled_kernel<double, double><<<grid, block, sizeof(RhsTile<double>), c->launch>>>(a, jchunk);
+    return cudaGetLastError();
+  }
   const long plane = (long)a.nx * (a.ny + 1);
   dim3 grid((unsigned)((plane + 127) / 128), (unsigned)a.nz);
   if (c->cfg.precision == NS_MIXED)

@@ -64,6 +64,7 @@ ns_layout make_layout(const ns_config* c) {
   sz[LB_TWX] = (nx / 2) * 16;
   sz[LB_LAMX] = nx * 8;
   sz[LB_LAMZ] = nzh * 8;
+  sz[LB_RTAB] = 3 * al256((size_t)RT_COUNT * (ny + 1) * 8);
   size_t o = 0;
   for (int b = 0; b < LB_COUNT; ++b) {
     L.off[b] = o;
@@ -490,6 +491,36 @@ ns_status ns_init(ns_ctx** out, const ns_config* cfg, const ns_fields* fields, v
   ns_status st = NS_OK;
   if (upload_d(c, c->gc, gc) != cudaSuccess) st = NS_ERR_CUDA;
 
+  // ---------------- RHS assembly coefficients per sub-step (tiled kernel)
+  {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    c->num_sms = 152;
+    cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev);
+    c->rhs_bps[0] = c->rhs_bps[1] = 1;
+  }
+  for (int k = 0; k < 3 && st == NS_OK; ++k) {
+    c->rtab[k] = (double*)(base + c->lay.off[LB_RTAB] + k * al256((size_t)RT_COUNT * G * 8));
+    const double inv_re = cfg->re > 0 ? 1.0 / cfg->re : 0.0;
+    const double cl = cfg->dt * NS_ALPHA[k] * inv_re;
+    const double dd = 2.0 / (c->dx * c->dx) + 2.0 / (c->dz * c->dz);
+    std::vector<double> rt((size_t)RT_COUNT * G, 0.0);
+    auto RT = [&](int f, int j) -> double& { return rt[(size_t)f * G + j]; };
+    for (int j = 0; j < ny; ++j) {
+      RT(RT_AC, j) = cl * GCv(GC_AC, j);
+      RT(RT_CC, j) = cl * GCv(GC_CC, j);
+      RT(RT_DC, j) = -cl * (dd + GCv(GC_AC, j) + GCv(GC_CC, j));
+      RT(RT_HIDY, j) = 0.5 * GCv(GC_IDY, j);
+    }
+    for (int j = 1; j < ny; ++j) {
+      RT(RT_AF, j) = cl * GCv(GC_AF, j);
+      RT(RT_CF, j) = cl * GCv(GC_CF, j);
+      RT(RT_DF, j) = -cl * (dd + GCv(GC_AF, j) + GCv(GC_CF, j));
+      RT(RT_CGY, j) = -cfg->dt * NS_ALPHA[k] * GCv(GC_IHC, j);
+      RT(RT_QIHC, j) = 0.25 * GCv(GC_IHC, j);
+    }
+    if (upload_d(c, c->rtab[k], rt) != cudaSuccess) st = NS_ERR_CUDA;
+  }
   // ---------------- ADI y and z factors per sub-step
   for (int k = 0; k < 3 && st == NS_OK; ++k) {
     const double beta = beta_of(c, k);
@@ -586,6 +617,7 @@ ns_status ns_init(ns_ctx** out, const ns_config* cfg, const ns_fields* fields, v
     if (upload_d(c, lamx_d, lx) != cudaSuccess) st = NS_ERR_CUDA;
     if (upload_d(c, lamz_d, lz) != cudaSuccess) st = NS_ERR_CUDA;
     if (st == NS_OK && poisson_set_attributes() != cudaSuccess) st = NS_ERR_CUDA;
+    if (st == NS_OK && rhs_set_attributes(&c->rhs_bps[0], &c->rhs_bps[1]) != cudaSuccess) st = NS_ERR_CUDA;
     if (st == NS_OK && launch_pois_factor(c, lamx_d, lamz_d) != cudaSuccess) st = NS_ERR_CUDA;
     if (st == NS_OK && cudaStreamSynchronize(c->stream) != cudaSuccess) st = NS_ERR_CUDA;
   }

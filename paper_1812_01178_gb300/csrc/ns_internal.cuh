@@ -23,6 +23,14 @@
 enum { GC_DY = 0, GC_IDY, GC_HC, GC_IHC, GC_WLO, GC_WHI, GC_AC, GC_CC, GC_AF, GC_CF, GC_PA, GC_PC,
        NS_GC_COUNT };
 
+// Per-(sub-step, j) assembly coefficients of the tiled RHS (double, RT_COUNT rows of ny + 1),
+// every factor pre-multiplied by dt: with cl = dt alpha_k / Re,
+//   AC/CC/DC : cl A_j, cl C_j, -cl (2/dx^2 + 2/dz^2 + A_j + C_j) at centres (AC, CC of GC_*)
+//   AF/CF/DF : the same at interior faces (AF, CF of GC_*)
+//   CGY      : -dt alpha_k / hc_j (pressure gradient at face j)
+//   HIDY     : 1 / (2 dy_j),   QIHC : 1 / (4 hc_j)
+enum { RT_AC = 0, RT_CC, RT_DC, RT_AF, RT_CF, RT_DF, RT_CGY, RT_HIDY, RT_QIHC, RT_COUNT };
+
 // RK3 constants (Sec. 2.2): gamma, zeta, alpha = gamma + zeta.
 static const double NS_GAMMA[3] = {8.0 / 15.0, 5.0 / 12.0, 3.0 / 4.0};
 static const double NS_ZETA[3] = {0.0, -17.0 / 60.0, -5.0 / 12.0};
@@ -51,7 +59,7 @@ struct ns_layout {
 
 enum {
   LB_RU = 0, LB_RV, LB_RW, LB_NU, LB_NV, LB_NW, LB_PHI, LB_SPEC, LB_POIS, LB_GC, LB_XTAB, LB_YTAB,
-  LB_ZTAB, LB_TWZ, LB_TWX, LB_LAMX, LB_LAMZ, LB_COUNT
+  LB_ZTAB, LB_TWZ, LB_TWX, LB_LAMX, LB_LAMZ, LB_RTAB, LB_COUNT
 };
 
 struct ns_ctx {
@@ -79,6 +87,9 @@ struct ns_ctx {
   void* ztab[3];
   double2* twz;
   double2* twx;
+  double* rtab[3];
+  int num_sms;
+  int rhs_bps[2];           // resident blocks per SM of the tiled RHS (FP64, FP32)
   // partitioned x solver
   int P, M, L[3];
   int part_req;             // NS_PART_AUTO / PPT / PDD
@@ -101,6 +112,7 @@ struct ns_ctx {
 
 // Launchers (enqueue on ctx->launch).  Return cudaGetLastError() of the launch.
 cudaError_t launch_rhs(ns_ctx* c, int k);
+cudaError_t rhs_set_attributes(int* bps_fp64, int* bps_fp32);  // once per device, outside any capture
 cudaError_t launch_adi_x(ns_ctx* c, int k);
 cudaError_t launch_adi_y(ns_ctx* c, int k);
 cudaError_t launch_adi_z(ns_ctx* c, int k);
