@@ -154,7 +154,7 @@ ns_status ns_step_host(ns_ctx* ctx, double* u, double* v, double* w, double* p, 
 ns_status ns_make_divergence_free(ns_ctx* ctx);
 
 /* Partitioning of the x-line solver (Sec. 3.2): P partitions per line (a power of two from
- * 1 to 32 dividing nx, with nx/P <= 16), mode 0 = automatic (PDD when the coupling PDD drops
+ * 1 to 32 dividing nx, with nx/P <= 16, or P = 32 with nx/P = 32 or 64 for long lines), mode 0 = automatic (PDD when the coupling PDD drops
  * is below its tolerance for every sub-step, else PPT), 1 = PPT, 2 = PDD.  Rebuilds the tables
  * and drops the captured graph.  dir must be 0. */
 enum { NS_PART_AUTO = 0, NS_PART_PPT = 1, NS_PART_PDD = 2 };

@@ -153,6 +153,93 @@ __global__ void __launch_bounds__(256) adi_x_kernel(AdiXArgs<T> a) {
 }
 
 // ----------------------------------------------------------------------------------------------
+// x, long lines (M = 32 or 64 rows per partition, P = 32): the same algebra with each warp's line
+// staged in shared memory at stride M+1 per partition (conflict-free for 8-byte elements), the
+// per-partition tables read through L1.  One warp per line, four warps per block.
+// ----------------------------------------------------------------------------------------------
+template <typename T, int M>
+__global__ void __launch_bounds__(128) adi_x_long_kernel(AdiXArgs<T> a) {
+  constexpr int P = 32;
+  constexpr int LS = P * (M + 1);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* line_buf = reinterpret_cast<T*>(smem_raw) + (threadIdx.x >> 5) * LS;
+  const int r = threadIdx.x & 31;
+  const int L = a.L;
+  const T* INV = a.tab + XT_INV * M * P;
+  const T* AINV = a.tab + XT_AINV * M * P;
+  const T* CP = a.tab + XT_CP * M * P;
+  const T* SV = a.tab + XT_V * M * P;
+  const T* SW = a.tab + XT_W * M * P;
+  const T* DINV = a.tab + XT_NF * M * P;
+  const T* ML = DINV + 4 * P;
+  const T* MU = ML + 4 * L * P;
+  const int nx = a.nx, ny = a.ny;
+  const long Lu = (long)a.nz * ny;
+  const long Lv = (long)a.nz * (ny - 1);
+  const long warp = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long nwarps = ((long)gridDim.x * blockDim.x) >> 5;
+  T* my = line_buf + r * (M + 1);
+  for (long line = warp; line < a.nlines; line += nwarps) {
+    T* row;
+    if (line < Lu) {
+      row = a.r[0] + line * nx;
+    } else if (line < Lu + Lv) {
+      const long q = line - Lu;
+      const long kk = q / (ny - 1);
+      const long jj = 1 + (q - kk * (ny - 1));
+      row = a.r[1] + (kk * (ny + 1) + jj) * nx;
+    } else {
+      row = a.r[2] + (line - Lu - Lv) * nx;
+    }
+    // coalesced load: element g = q*32 + lane goes to partition g / M, row g % M
+#pragma unroll 4
+    for (int q = 0; q < M; ++q) {
+      const int g = q * 32 + r;
+      line_buf[(g / M) * (M + 1) + (g % M)] = row[g];
+    }
+    __syncwarp();
+    // A~ x~ = d on partition r
+    T prev = my[0] * __ldg(INV + r);
+    my[0] = prev;
+    for (int e = 1; e < M; ++e) {
+      prev = my[e] * __ldg(INV + e * P + r) - __ldg(AINV + e * P + r) * prev;
+      my[e] = prev;
+    }
+    T next = prev;
+    for (int e = M - 2; e >= 0; --e) {
+      next = my[e] - __ldg(CP + e * P + r) * next;
+      my[e] = next;
+    }
+    T g0 = prev;
+    T g1 = __shfl_sync(NS_FULL_MASK, next, r + 1, P);
+    for (int lv = 0, s = 1; lv < L; ++lv, s <<= 1) {
+      const T h0 = __shfl_sync(NS_FULL_MASK, g0, r - s + P, P);
+      const T h1 = __shfl_sync(NS_FULL_MASK, g1, r - s + P, P);
+      const T k0 = __shfl_sync(NS_FULL_MASK, g0, r + s, P);
+      const T k1 = __shfl_sync(NS_FULL_MASK, g1, r + s, P);
+      const T* ml = ML + 4 * lv * P;
+      const T* mu = MU + 4 * lv * P;
+      const T n0 = g0 - __ldg(ml + r) * h0 - __ldg(ml + P + r) * h1 - __ldg(mu + r) * k0 - __ldg(mu + P + r) * k1;
+      const T n1 = g1 - __ldg(ml + 2 * P + r) * h0 - __ldg(ml + 3 * P + r) * h1 - __ldg(mu + 2 * P + r) * k0 -
+                   __ldg(mu + 3 * P + r) * k1;
+      g0 = n0;
+      g1 = n1;
+    }
+    const T y0 = __ldg(DINV + r) * g0 + __ldg(DINV + P + r) * g1;
+    const T y1 = __ldg(DINV + 2 * P + r) * g0 + __ldg(DINV + 3 * P + r) * g1;
+    const T left = __shfl_sync(NS_FULL_MASK, y0, r - 1 + P, P);
+    for (int e = 0; e < M; ++e) my[e] = my[e] - __ldg(SV + e * P + r) * left - __ldg(SW + e * P + r) * y1;
+    __syncwarp();
+#pragma unroll 4
+    for (int q = 0; q < M; ++q) {
+      const int g = q * 32 + r;
+      row[g] = line_buf[(g / M) * (M + 1) + (g % M)];
+    }
+    __syncwarp();
+  }
+}
+
+// ----------------------------------------------------------------------------------------------
 // y: one thread per line, Thomas with precomputed factors [INV, AINV, CP][n]
 // ----------------------------------------------------------------------------------------------
 template <typename T>
@@ -262,8 +349,30 @@ cudaError_t launch_x_t(ns_ctx* c, int k) {
   return cudaGetLastError();
 }
 
+template <typename T, int M>
+cudaError_t launch_x_long_t(ns_ctx* c, int k) {
+  AdiXArgs<T> a;
+  a.tab = (const T*)c->xtab[k];
+  a.r[0] = (T*)c->ru;
+  a.r[1] = (T*)c->rv;
+  a.r[2] = (T*)c->rw;
+  a.nx = c->cfg.nx;
+  a.ny = c->cfg.ny;
+  a.nz = c->cfg.nz;
+  a.P = c->P;
+  a.L = c->L[k];
+  a.nlines = (long)a.nz * a.ny * 2 + (long)a.nz * (a.ny - 1);
+  const size_t smem = (size_t)4 * 32 * (M + 1) * sizeof(T);
+  long blocks = (a.nlines + 3) / 4;
+  if (blocks > 152L * 16) blocks = 152L * 16;
+  adi_x_long_kernel<T, M><<<(unsigned)blocks, 128, smem, c->launch>>>(a);
+  return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_x_m(ns_ctx* c, int k) {
+  if (c->P == 32 && c->M == 32) return launch_x_long_t<T, 32>(c, k);
+  if (c->P == 32 && c->M == 64) return launch_x_long_t<T, 64>(c, k);
   switch (c->M) {
     case 1: return launch_x_t<T, 1>(c, k);
     case 2: return launch_x_t<T, 2>(c, k);
@@ -305,6 +414,21 @@ cudaError_t launch_adi_z(ns_ctx* c, int k) {
     adi_z_kernel<double><<<grid, 128, 0, c->launch>>>((double*)c->ru, (double*)c->rv, (double*)c->rw, c->f.u,
                                                       c->f.v, c->f.w, (const double*)c->ztab[k], nx, ny, nz);
   return cudaGetLastError();
+}
+
+cudaError_t adi_set_attributes() {
+  cudaError_t e;
+  if ((e = cudaFuncSetAttribute(adi_x_long_kernel<double, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                4 * 32 * 65 * 8)) != cudaSuccess)
+    return e;
+  if ((e = cudaFuncSetAttribute(adi_x_long_kernel<double, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                4 * 32 * 33 * 8)) != cudaSuccess)
+    return e;
+  if ((e = cudaFuncSetAttribute(adi_x_long_kernel<float, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                4 * 32 * 65 * 4)) != cudaSuccess)
+    return e;
+  return cudaFuncSetAttribute(adi_x_long_kernel<float, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              4 * 32 * 33 * 4);
 }
 
 size_t adi_y_tab_count(int ny) { return 3 * (size_t)ny; }

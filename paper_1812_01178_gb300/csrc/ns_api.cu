@@ -587,9 +587,9 @@ ns_status ns_init(ns_ctx** out, const ns_config* cfg, const ns_fields* fields, v
     if (P > 32) P = 32;
     c->P = P;
     c->M = nx / P;
-    if (st == NS_OK && (c->M > 16 || P > 32)) {
+    if (st == NS_OK && !(c->M <= 16 || (P == 32 && (c->M == 32 || c->M == 64)))) {
       st = NS_ERR_SIZE;
-      c->err = "nx too large for the partitioned x solver (nx/32 > 16)";
+      c->err = "nx too large for the partitioned x solver (nx/32 > 64)";
     }
   }
   if (st == NS_OK) st = build_x_tables(c);
@@ -618,6 +618,7 @@ ns_status ns_init(ns_ctx** out, const ns_config* cfg, const ns_fields* fields, v
     if (upload_d(c, lamz_d, lz) != cudaSuccess) st = NS_ERR_CUDA;
     if (st == NS_OK && poisson_set_attributes() != cudaSuccess) st = NS_ERR_CUDA;
     if (st == NS_OK && rhs_set_attributes(&c->rhs_bps[0], &c->rhs_bps[1]) != cudaSuccess) st = NS_ERR_CUDA;
+    if (st == NS_OK && adi_set_attributes() != cudaSuccess) st = NS_ERR_CUDA;
     if (st == NS_OK && launch_pois_factor(c, lamx_d, lamz_d) != cudaSuccess) st = NS_ERR_CUDA;
     if (st == NS_OK && cudaStreamSynchronize(c->stream) != cudaSuccess) st = NS_ERR_CUDA;
   }
@@ -760,7 +761,8 @@ ns_status ns_set_partition(ns_ctx* c, int dir, int P, int mode) {
   if (!c) return NS_ERR_ARG;
   if (dir != 0) return fail(c, NS_ERR_UNSUPPORTED, "only dir 0 (x) is partitioned");
   const int nx = c->cfg.nx;
-  if (!is_pow2(P) || P > 32 || nx % P != 0 || nx / P > 16) return fail(c, NS_ERR_ARG, "invalid partition count");
+  const int M = is_pow2(P) && P <= 32 && nx % P == 0 ? nx / P : 0;
+  if (M == 0 || !(M <= 16 || (P == 32 && (M == 32 || M == 64)))) return fail(c, NS_ERR_ARG, "invalid partition count");
   if (mode != NS_PART_AUTO && mode != NS_PART_PPT && mode != NS_PART_PDD)
     return fail(c, NS_ERR_ARG, "invalid partition mode");
   if (capturing(c)) return fail(c, NS_ERR_STATE, "ns_set_partition during capture");
@@ -806,7 +808,8 @@ ns_status ns_autotune(ns_ctx* c) {
   int bestP = c->P, bestMode = c->part_req;
   float best = 1e30f;
   for (int P = 1; P <= 32; P <<= 1) {
-    if (nx % P || nx / P > 16 || nx / P < 1) continue;
+    if (nx % P || nx / P < 1) continue;
+    if (!(nx / P <= 16 || (P == 32 && (nx / P == 32 || nx / P == 64)))) continue;
     for (int mode : {NS_PART_AUTO, NS_PART_PPT}) {
       if (ns_set_partition(c, 0, P, mode) != NS_OK) continue;
       if (mode == NS_PART_PPT && c->part_mode != NS_PART_PPT) continue;

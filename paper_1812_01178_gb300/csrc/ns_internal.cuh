@@ -114,6 +114,7 @@ struct ns_ctx {
 cudaError_t launch_rhs(ns_ctx* c, int k);
 cudaError_t rhs_set_attributes(int* bps_fp64, int* bps_fp32);  // once per device, outside any capture
 cudaError_t launch_adi_x(ns_ctx* c, int k);
+cudaError_t adi_set_attributes();  // once per device, outside any capture
 cudaError_t launch_adi_y(ns_ctx* c, int k);
 cudaError_t launch_adi_z(ns_ctx* c, int k);
 cudaError_t launch_poisson(ns_ctx* c, int k);   // the five kernels below, in order

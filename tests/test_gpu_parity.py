@@ -226,3 +226,42 @@ def test_make_divergence_free():
     assert np.abs(O.divergence(g, gu, gv, gw)).max() < 1e-11 * np.abs(O.divergence(g, u, v, w)).max()
     assert np.array_equal(gp, p)
     s.close()
+
+
+@pytest.mark.parametrize("nx", [1024, 2048])
+@pytest.mark.parametrize("mode", [B.NS_PART_PPT, B.NS_PART_PDD])
+def test_adi_x_long_lines_parity(nx, mode):
+    """Long x-lines (32 partitions of 32 or 64 rows, lines staged in shared memory)."""
+    case, u, v, w, p = _case(nx, 6, 8)
+    case.re = 1.0
+    case.dt = 0.02
+    g = O.Grid.from_case(case)
+    s = B.Solver(case, u, v, w, p)
+    s.set_partition(32, mode)
+    P, gotmode, drop = s.partition()
+    r3 = _rand_r(case, 21)
+    for k in (0, 2):
+        beta = O.RK3_ALPHA[k] * case.dt / (2 * case.re)
+        _load_r(s, r3)
+        s.adi(0, k)
+        for q, bi in enumerate([B.NS_BUF_RU, B.NS_BUF_RV, B.NS_BUF_RW]):
+            ref = O.adi_sweep(g, r3[q], 0, q, beta)
+            err = np.abs(to_np(s.buffer(bi)) - ref).max() / np.abs(ref).max()
+            assert err < (1e-13 if mode == B.NS_PART_PPT else max(1e-13, 50 * drop)), (k, q, err, drop)
+    s.close()
+
+
+def test_long_line_steps_parity():
+    """Full FP64 steps on a grid with 1024-long x-lines (long-line x solver, tiled RHS, long x FFT)."""
+    case, u, v, w, p = _case(1024, 12, 16)
+    case.dt = 1e-3
+    g = O.Grid.from_case(case)
+    u, v, w = O.make_divergence_free(g, u, v, w)
+    ref = O.step(g, dict(u=u, v=v, w=w, p=p), case.dt, case.re, case.fx, nsteps=2)
+    s = B.Solver(case, u, v, w, p)
+    assert s.partition()[0] == 32
+    s.step(2)
+    errs = field_rel_errors(s.state(), (ref["u"], ref["v"], ref["w"], ref["p"]))
+    for name in ("u", "v", "w", "p"):
+        assert errs[name] < 1e-11, (name, errs)
+    s.close()
