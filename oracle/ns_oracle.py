@@ -575,3 +575,271 @@ def step(g, state, dt, re, fx, nsteps=1):
         for k in range(3):
             s = substep(g, s, k, dt, re, fx)
     return s
+
+
+# ----------------------------------------------------------------------------
+# Inflow / convective outflow in x (the flat-plate configuration of Sec. 2.1)
+# ----------------------------------------------------------------------------
+# Readings (the paper gives the boundary conditions in words only, Sec. 2.1):
+# * u is stored on faces 0..nx-1 (face 0 = inflow, fixed); the outflow face nx lives in the
+#   plane bl["u_out"] (nz, ny).  v and w keep their values on the inflow / outflow faces in
+#   bl["v_in"], bl["v_out"] (nz, ny+1) and bl["w_in"], bl["w_out"] (nz, ny).
+# * v and w see the boundary faces through linear ghost cells, f_ghost = 2 f_b - f_adjacent,
+#   so every interior stencil keeps its form (the face average of ghost and neighbour is f_b).
+# * Convective outflow df/dt + U_c df/dx = 0: one first-order upwind step of alpha_k dt per
+#   sub-step, with the interior neighbour at distance dx (u) or dx/2 (v, w).
+# * Before the Poisson solve the outflow u is shifted uniformly so that the outflow volume flux
+#   equals the inflow flux (no flux through the walls / stress-free top), which makes the pure
+#   Neumann problem compatible.
+# * The Poisson operator has zero normal gradient at x = 0 and x = Lx as well: it is
+#   diagonalised by the DCT-II in x (the half-range cosine transform of Sec. 2.2).
+
+def _xnext_u(u, bl):
+    """u at face i+1 (face nx from the outflow plane)."""
+    return np.concatenate([u[:, :, 1:], bl["u_out"][:, :, None]], axis=2)
+
+
+def _xprev_u(u):
+    """u at face i-1 (face -1 does not exist: 0, never used for an unknown)."""
+    return np.concatenate([np.zeros_like(u[:, :, :1]), u[:, :, :-1]], axis=2)
+
+
+def _xnext_c(f, f_out):
+    """Centre value at i+1 with the outflow ghost 2 f_out - f_{nx-1}."""
+    return np.concatenate([f[:, :, 1:], (2.0 * f_out - f[:, :, -1])[:, :, None]], axis=2)
+
+
+def _xprev_c(f, f_in):
+    """Centre value at i-1 with the inflow ghost 2 f_in - f_0."""
+    return np.concatenate([(2.0 * f_in - f[:, :, 0])[:, :, None], f[:, :, :-1]], axis=2)
+
+
+def convection_bl(g, u, v, w, bl):
+    """Divergence-form convection with inflow / outflow in x (same stencils as convection())."""
+    dx, dz = g.dx, g.dz
+    dy = g.dy[None, :, None]
+    hc = g.hc[None, :, None]
+    ux = _xnext_u(u, bl)
+    uc = 0.5 * (u + ux)                                        # u at centres 0..nx-1
+    nux = (uc * uc - _xprev_c(uc, np.zeros_like(uc[:, :, 0])) ** 2) / dx
+    u_yf = _centre_to_yface(g, u)
+    v_xf = 0.5 * (_xprev_c(v, bl["v_in"]) + v)                  # v at x-faces 0..nx-1
+    fuv = u_yf * v_xf
+    nuy = (fuv[:, 1:, :] - fuv[:, :-1, :]) / dy
+    u_zf = 0.5 * (_zm(u) + u)
+    w_xf = 0.5 * (_xprev_c(w, bl["w_in"]) + w)
+    fuw = u_zf * w_xf
+    nuz = (_zp(fuw) - fuw) / dz
+    Nu = nux + nuy + nuz
+    Nu[:, :, 0] = 0.0                                           # inflow face: fixed
+    # edge fluxes on the outflow face nx
+    uo_yf = _centre_to_yface(g, bl["u_out"][:, :, None])[:, :, 0]
+    fuv_out = uo_yf * bl["v_out"]
+    uo_zf = 0.5 * (_zm(bl["u_out"]) + bl["u_out"])
+    fuw_out = uo_zf * bl["w_out"]
+    fuv_n = np.concatenate([fuv[:, :, 1:], fuv_out[:, :, None]], axis=2)
+    fuw_n = np.concatenate([fuw[:, :, 1:], fuw_out[:, :, None]], axis=2)
+    nvx = (fuv_n - fuv) / dx
+    vc = 0.5 * (v[:, :-1, :] + v[:, 1:, :])
+    nvy = np.zeros_like(v)
+    nvy[:, 1:-1, :] = (vc[:, 1:, :] ** 2 - vc[:, :-1, :] ** 2) / hc
+    v_zf = 0.5 * (_zm(v) + v)
+    w_yf = _centre_to_yface(g, w)
+    fvw = v_zf * w_yf
+    nvz = (_zp(fvw) - fvw) / dz
+    Nv = nvx + nvy + nvz
+    Nv[:, 0, :] = 0.0
+    Nv[:, -1, :] = 0.0
+    nwx = (fuw_n - fuw) / dx
+    nwy = (fvw[:, 1:, :] - fvw[:, :-1, :]) / dy
+    wc = 0.5 * (w + _zp(w))
+    nwz = (wc * wc - _zm(wc) * _zm(wc)) / dz
+    Nw = nwx + nwy + nwz
+    return Nu, Nv, Nw
+
+
+def gradient_bl(g, p):
+    """G p with no correction on the inflow face (u fixed there)."""
+    gx = (p - _xm(p)) / g.dx
+    gx[:, :, 0] = 0.0
+    gy = np.zeros((g.nz, g.ny + 1, g.nx))
+    gy[:, 1:-1, :] = (p[:, 1:, :] - p[:, :-1, :]) / g.hc[None, :, None]
+    gz = (p - _zm(p)) / g.dz
+    return gx, gy, gz
+
+
+def divergence_bl(g, u, v, w, bl):
+    return ((_xnext_u(u, bl) - u) / g.dx
+            + (v[:, 1:, :] - v[:, :-1, :]) / g.dy[None, :, None]
+            + (_zp(w) - w) / g.dz)
+
+
+def laplacian_bl(g, u, v, w, bl):
+    def dzz(f):
+        return (_zp(f) - 2.0 * f + _zm(f)) / (g.dz * g.dz)
+    h2 = g.dx * g.dx
+    Lu = (_xnext_u(u, bl) - 2.0 * u + _xprev_u(u)) / h2 + _dyy_centre(g, u) + dzz(u)
+    Lu[:, :, 0] = 0.0
+    Lv = (_xnext_c(v, bl["v_out"]) - 2.0 * v + _xprev_c(v, bl["v_in"])) / h2 + _dyy_face(g, v) + dzz(v)
+    Lv[:, 0, :] = 0.0
+    Lv[:, -1, :] = 0.0
+    Lw = (_xnext_c(w, bl["w_out"]) - 2.0 * w + _xprev_c(w, bl["w_in"])) / h2 + _dyy_centre(g, w) + dzz(w)
+    return Lu, Lv, Lw
+
+
+def rhs_bl(g, u, v, w, p, nprev, bl, k, dt, re, fx):
+    """rhs() with inflow / outflow in x: the inflow face of u gets r = 0."""
+    gam, zet, alp = RK3_GAMMA[k], RK3_ZETA[k], RK3_ALPHA[k]
+    N = convection_bl(g, u, v, w, bl)
+    G = gradient_bl(g, p)
+    L = laplacian_bl(g, u, v, w, bl)
+    inv_re = 0.0 if not np.isfinite(re) else 1.0 / re
+    r = []
+    for comp in range(3):
+        t = -gam * N[comp] - alp * G[comp] + (alp * inv_re) * L[comp]
+        if zet != 0.0:
+            t = t - zet * nprev[comp]
+        if comp == 0:
+            t = t + alp * fx
+        t = dt * t
+        if comp == 0:
+            t[:, :, 0] = 0.0
+        if comp == 1:
+            t[:, 0, :] = 0.0
+            t[:, -1, :] = 0.0
+        r.append(t)
+    return r, N
+
+
+def outflow_update(g, u, v, w, bl, scale, u_conv):
+    """One upwind step (scale = alpha_k dt) of df/dt + U_c df/dx = 0 on the outflow planes.
+    Returns the new planes and their increments."""
+    new = dict(bl)
+    c = scale * u_conv
+    new["u_out"] = bl["u_out"] - c * (bl["u_out"] - u[:, :, -1]) / g.dx
+    new["v_out"] = bl["v_out"] - c * (bl["v_out"] - v[:, :, -1]) / (0.5 * g.dx)
+    new["w_out"] = bl["w_out"] - c * (bl["w_out"] - w[:, :, -1]) / (0.5 * g.dx)
+    new["v_out"][:, 0] = 0.0
+    new["v_out"][:, -1] = 0.0
+    inc = {q: new[q] - bl[q] for q in ("u_out", "v_out", "w_out")}
+    return new, inc
+
+
+def adi_rows_x_bl(g, comp, beta):
+    """Rows of (I - beta delta_xx) with inflow / outflow.  u: faces 0..nx-1, row 0 is the fixed
+    inflow face (identity).  v, w: centres with ghost rows at both ends (b = 1 + 3r)."""
+    n = g.nx
+    r = beta / (g.dx * g.dx)
+    a = np.full(n, -r)
+    b = np.full(n, 1.0 + 2.0 * r)
+    c = np.full(n, -r)
+    if comp == 0:
+        a[0], b[0], c[0] = 0.0, 1.0, 0.0
+    else:
+        b[0] = 1.0 + 3.0 * r
+        b[-1] = 1.0 + 3.0 * r
+    a[0] = 0.0
+    c[-1] = 0.0
+    return a, b, c
+
+
+def adi_sweep_x_bl(g, rr, comp, beta, inc_out):
+    """x sweep with inflow / outflow: the outflow increment enters the last row's right-hand side
+    (coefficient r for u, 2r for the ghost of v, w; the inflow increment is zero)."""
+    a, b, c = adi_rows_x_bl(g, comp, beta)
+    r = beta / (g.dx * g.dx)
+    d = rr.copy()
+    d[:, :, -1] += (r if comp == 0 else 2.0 * r) * inc_out
+    return thomas(a, b, c, d)
+
+
+def flux_correct_outflow(g, u_in, u_out):
+    """Shift u_out uniformly so that its volume flux equals the inflow flux."""
+    area = (g.yf[-1] - g.yf[0]) * g.lz
+    w = g.dy[None, :] * g.dz
+    q_in = float((u_in * w).sum())
+    q_out = float((u_out * w).sum())
+    return u_out + (q_in - q_out) / area
+
+
+def dct2_matrix(n):
+    """DCT-II: X_l = sum_i x_i cos(pi l (2 i + 1) / (2 n))."""
+    l = np.arange(n)[:, None]
+    i = np.arange(n)[None, :]
+    return np.cos(math.pi * l * (2 * i + 1) / (2 * n))
+
+
+def dct3_inverse_matrix(n):
+    """Inverse of dct2_matrix: x_i = (X_0 + 2 sum_{l>0} X_l cos(pi l (2 i + 1)/(2 n))) / n."""
+    C = dct2_matrix(n).T.copy()
+    C[:, 1:] *= 2.0
+    return C / n
+
+
+def poisson_solve_bl(g, rhs):
+    """D G phi = rhs with zero normal gradient on all non-periodic boundaries: DCT-II in x,
+    DFT in z, tridiagonal in y, inverses; (0, 0) mode gauged by phi_0 = 0."""
+    Cx = dct2_matrix(g.nx)
+    bh = dft(np.moveaxis(np.moveaxis(rhs, 2, -1) @ Cx.T, -1, 2).astype(np.complex128), 0)
+    a, c = poisson_ycoeffs(g)
+    lx = (2.0 / (g.dx * g.dx)) * (1.0 - np.cos(math.pi * np.arange(g.nx) / g.nx))
+    lz = modified_wavenumbers(g.nz, g.dz)
+    lam = lz[:, None] + lx[None, :]
+    d = np.moveaxis(bh, 1, -1)
+    A = np.broadcast_to(a, d.shape).copy()
+    C = np.broadcast_to(c, d.shape).copy()
+    B = np.array(np.broadcast_to(-(a + c)[None, None, :] - lam[:, :, None], d.shape))
+    B[0, 0, 0] = 1.0
+    C[0, 0, 0] = 0.0
+    d = d.copy()
+    d[0, 0, 0] = 0.0
+    ph = np.moveaxis(thomas(A, B, C, d), -1, 1)
+    ph = dft(ph, 0, +1) / g.nz
+    Ci = dct3_inverse_matrix(g.nx)
+    phi = np.moveaxis(np.moveaxis(ph, 2, -1) @ Ci.T, -1, 2)
+    return phi.real.copy()
+
+
+def project_bl(g, u, v, w, phi, scale):
+    gx, gy, gz = gradient_bl(g, phi)
+    return u - scale * gx, v - scale * gy, w - scale * gz
+
+
+def make_divergence_free_bl(g, u, v, w, bl):
+    """Flux-correct the outflow plane, then project (scale 1)."""
+    bl = dict(bl)
+    bl["u_out"] = flux_correct_outflow(g, u[:, :, 0], bl["u_out"])
+    phi = poisson_solve_bl(g, divergence_bl(g, u, v, w, bl))
+    u2, v2, w2 = project_bl(g, u, v, w, phi, 1.0)
+    return u2, v2, w2, bl
+
+
+def substep_bl(g, state, k, dt, re, fx, u_conv=1.0):
+    """One RK3 sub-step with inflow / convective outflow in x.  Order: RHS (boundary planes of the
+    previous level), outflow update, ADI x (outflow increment on the last row) / y / z,
+    u* = u + delta, outflow flux correction, Poisson, projection of interior faces, p += phi."""
+    u, v, w, p, bl = state["u"], state["v"], state["w"], state["p"], state["bl"]
+    r, N = rhs_bl(g, u, v, w, p, state.get("nprev"), bl, k, dt, re, fx)
+    scale = RK3_ALPHA[k] * dt
+    bl_new, inc = outflow_update(g, u, v, w, bl, scale, u_conv)
+    inv_re = 0.0 if not np.isfinite(re) else 1.0 / re
+    beta = scale * inv_re / 2.0
+    out = []
+    for comp, (rc, ic) in enumerate(zip(r, (inc["u_out"], inc["v_out"], inc["w_out"]))):
+        x = adi_sweep_x_bl(g, rc, comp, beta, ic)
+        x = adi_sweep(g, x, 1, comp, beta)
+        x = adi_sweep(g, x, 2, comp, beta)
+        out.append(x)
+    us, vs, ws = u + out[0], v + out[1], w + out[2]
+    bl_new["u_out"] = flux_correct_outflow(g, u[:, :, 0], bl_new["u_out"])
+    phi = poisson_solve_bl(g, divergence_bl(g, us, vs, ws, bl_new) / scale)
+    un, vn, wn = project_bl(g, us, vs, ws, phi, scale)
+    return dict(u=un, v=vn, w=wn, p=p + phi, nprev=N, phi=phi, bl=bl_new)
+
+
+def step_bl(g, state, dt, re, fx, nsteps=1, u_conv=1.0):
+    s = dict(state)
+    for _ in range(nsteps):
+        for k in range(3):
+            s = substep_bl(g, s, k, dt, re, fx, u_conv)
+    return s

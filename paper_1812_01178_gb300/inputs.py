@@ -14,8 +14,10 @@ inputs the method is run on:
   channel-shaped field, boundary-layer-shaped field) and their sizes.
 
 Arrays use the device layout: x fastest, then y, then z, i.e. numpy shape
-(nz, ny_or_ny+1, nx_or_nx+1).  u lives on x-faces, v on y-faces (ny+1 rows,
-rows 0 and ny are walls), w on z-faces, p at cell centres (Sec. 2.1).
+(nz, ny or ny+1, nx).  u lives on x-faces, v on y-faces (ny+1 rows, rows 0 and
+ny are walls), w on z-faces, p at cell centres (Sec. 2.1).  With inflow /
+outflow in x, u holds faces 0..nx-1 (face 0 is the inflow) and the outflow face
+and the inflow / outflow values of v, w are separate planes.
 """
 from __future__ import annotations
 
@@ -171,8 +173,7 @@ def turbulent_channel(nx=256, ny=192, nz=256, beta=2.0, re_tau=395.0, rms=0.1,
 
 def field_shapes(case: Case):
     """numpy shapes of u, v, w, p for a case (x fastest, then y, then z)."""
-    nxu = case.nx + (1 if case.bc_x == 1 else 0)
-    return ((case.nz, case.ny, nxu), (case.nz, case.ny + 1, case.nx),
+    return ((case.nz, case.ny, case.nx), (case.nz, case.ny + 1, case.nx),
             (case.nz, case.ny, case.nx), (case.nz, case.ny, case.nx))
 
 
@@ -191,3 +192,43 @@ def small_channel(nx, ny, nz, seed=7, amp=0.1, re=100.0, dt=2e-3, beta=1.5,
     w = amp * normal(seed + 2, n, 0).reshape(nz, ny, nx)
     p = amp * normal(seed + 3, n, 0).reshape(nz, ny, nx)
     return case, u, v, w, p
+
+
+def boundary_layer(nx=1024, ny=256, nz=512, beta=2.0, re=1000.0, amp=1e-2, cfl=0.5, steps=50, seed=1812,
+                   lx=None, ly=None, lz=None, precision=0):
+    """Boundary-layer-shaped field with inflow / convective outflow in x.
+
+    Units: inlet thickness and free-stream speed.  Domain Lx = 200, Ly = 20, Lz = 30 by default
+    (scaled down for small grids).  Inflow u = tanh(2 y) plus seeded perturbations of amplitude
+    amp on u, v, w (time-invariant); the interior starts from the same profile plus its own
+    perturbations; the outflow planes start as the last interior column.  No-slip wall at y = 0,
+    stress-free top, periodic z, U_c = 1.  Returns (case, u, v, w, p, bl) with u holding faces
+    0..nx-1 (face 0 = inflow) and bl the boundary planes u_out, v_in, v_out, w_in, w_out.
+    """
+    lx = lx if lx is not None else (200.0 if nx >= 256 else 0.2 * nx)
+    ly = ly if ly is not None else (20.0 if ny >= 64 else 0.3 * ny)
+    lz = lz if lz is not None else (30.0 if nz >= 128 else 0.25 * nz)
+    yf = boundary_layer_faces(ny, beta, ly)
+    yc = _centres(yf)
+    case = Case("boundary_layer_%dx%dx%d" % (nx, ny, nz), nx, ny, nz, lx, lz, yf, re=re, fx=0.0,
+                steps=steps, bc_x=1, bc_ytop=1, precision=precision, u_conv=1.0)
+    n = nx * ny * nz
+    prof = np.tanh(2.0 * yc)
+    u = prof[None, :, None] + amp * normal(seed, n, 0).reshape(nz, ny, nx)
+    v = amp * normal(seed + 1, nz * (ny + 1) * nx, 0).reshape(nz, ny + 1, nx)
+    v[:, 0, :] = 0.0
+    v[:, ny, :] = 0.0
+    w = amp * normal(seed + 2, n, 0).reshape(nz, ny, nx)
+    # inflow planes (face 0 of u; v, w on the inflow face), fixed in time
+    u[:, :, 0] = prof[None, :] + amp * normal(seed + 3, nz * ny, 0).reshape(nz, ny)
+    v_in = amp * normal(seed + 4, nz * (ny + 1), 0).reshape(nz, ny + 1)
+    v_in[:, 0] = 0.0
+    v_in[:, ny] = 0.0
+    w_in = amp * normal(seed + 5, nz * ny, 0).reshape(nz, ny)
+    bl = dict(u_out=u[:, :, -1].copy(), v_in=v_in, v_out=v[:, :, -1].copy(), w_in=w_in, w_out=w[:, :, -1].copy())
+    p = np.zeros((nz, ny, nx))
+    dx, dz = lx / nx, lz / nz
+    dy = np.diff(yf)
+    c = (np.abs(u) / dx + np.abs(0.5 * (v[:, :-1] + v[:, 1:])) / dy[None, :, None] + np.abs(w) / dz)
+    case.dt = cfl / float(c.max())
+    return case, u, v, w, p, bl
