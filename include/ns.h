@@ -5,7 +5,7 @@
  *   Sec. 2.1  incompressible NS, Eq. (NScontinuity) and Eq. (NSmomentum), on a staggered grid:
  *             u on x-faces, v on y-faces, w on z-faces, p at cell centres; uniform x and z,
  *             wall-clustered y; no-slip wall at the bottom, no-slip or stress-free top;
- *             periodic z (and periodic x for channel flow).
+ *             periodic z; x periodic (channel) or inflow / convective outflow (flat plate).
  *   Sec. 2.2  semi-implicit fractional step: low-storage RK3 (convection) + Crank-Nicolson
  *             (viscous), ADI factorisation into tridiagonal solves along x, y and z, Poisson
  *             equation by Fourier transforms in x and z plus tridiagonal solves in y, projection
@@ -19,7 +19,15 @@
  *                          walls and hold 0
  *   w : nz * ny     * nx   (x-centre i, y-centre j, z-face k)
  *   p : nz * ny     * nx   (cell centres)
- * Element (i, j, k) of u is u[(k * ny + j) * nx + i].  All device pointers must be 256-byte
+ * Element (i, j, k) of u is u[(k * ny + j) * nx + i].  With inflow / outflow in x (bc_x = 1)
+ * u holds faces i = 0..nx-1, face 0 being the inflow (fixed in time), and five boundary planes
+ * complete the state (x fastest within a plane is not used: index k * rows + j):
+ *   u_out : nz * ny      u on the outflow face x = Lx (advanced by the convective condition
+ *                        dU/dt + U_c dU/dx = 0 and shifted so the outflow flux equals the inflow
+ *                        flux before every Poisson solve)
+ *   v_in, v_out : nz * (ny+1)   v on the inflow / outflow face (inflow fixed, outflow convected)
+ *   w_in, w_out : nz * ny       w on the inflow / outflow face (same)
+ * v and w see these faces through linear ghost cells (ghost = 2 f_face - f_adjacent).  All device pointers must be 256-byte
  * aligned (cudaMalloc / torch allocations are).  nx must be even, and nx and nz must be
  * powers of two in [8, 4096].  ny is in [4, 1024].
  *
@@ -71,13 +79,13 @@ typedef struct {
   double lx, lz;         /* domain lengths in the periodic directions */
   const double* yf;      /* ny+1 strictly increasing y-face coordinates, HOST memory, read
                             only during ns_init (Sec. 2.1: wall-clustered y grid) */
-  int bc_x;              /* 0: periodic x.  1 (inflow / convective outflow) is not built:
-                            NS_ERR_UNSUPPORTED */
+  int bc_x;              /* 0: periodic x; 1: inflow at x = 0, convective outflow at x = Lx */
   int bc_ytop;           /* 0: no-slip top wall, 1: stress-free top (v = 0, du/dy = dw/dy = 0) */
   double re;             /* Reynolds number of Eq. (NSmomentum); re <= 0 means inviscid */
   double fx;             /* constant body force along x (drives channel flow) */
   double dt;             /* time step, fixed for the lifetime of the context */
   int precision;         /* NS_FP64 or NS_MIXED */
+  double u_conv;         /* convection speed U_c of the outflow condition (bc_x = 1 only) */
 } ns_config;
 
 typedef struct {
@@ -85,6 +93,11 @@ typedef struct {
   double* v;
   double* w;
   double* p;
+  double* u_out;         /* boundary planes (bc_x = 1 only, else ignored and may be NULL) */
+  double* v_in;
+  double* v_out;
+  double* w_in;
+  double* w_out;
 } ns_fields;
 
 /* Workspace bytes needed by ns_init for this configuration (0 if cfg is invalid). */
@@ -125,7 +138,8 @@ ns_status ns_poisson_solve(ns_ctx* ctx, int substep);
  * substep = -1 projects with scale 1 and leaves p unchanged. */
 ns_status ns_project(ns_ctx* ctx, int substep);
 
-/* One full RK3 sub-step: ns_rhs, ns_adi_sweep x/y/z, ns_poisson_solve, ns_project. */
+/* One full RK3 sub-step: ns_rhs, (outflow update), ns_adi_sweep x/y/z, (outflow mass-flux
+ * correction), ns_poisson_solve, ns_project; the bracketed stages run only with bc_x = 1. */
 ns_status ns_substep(ns_ctx* ctx, int substep);
 
 /* nsteps time steps of three sub-steps each (Table 1 counts one step = three sub-steps).
@@ -139,9 +153,11 @@ ns_status ns_step(ns_ctx* ctx, int nsteps);
  * first).  The state advances exactly as with ns_step. */
 ns_status ns_step_profiled(ns_ctx* ctx, int nsteps, float* kernel_ms, int nk);
 
-/* Number of kernels in one sub-step, and the name of kernel idx (launch order: rhs, adi_x, adi_y,
- * adi_z, poisson_div_fftz, poisson_fftx_fwd, poisson_tdma_y, poisson_fftx_inv, poisson_ifftz,
- * project; "" if idx is out of range). */
+/* Number of kernel slots in one sub-step, and the name of slot idx, in launch order: rhs, outflow,
+ * adi_x, adi_y, adi_z, flux_correct, poisson_div_fftz, poisson_x_fwd, poisson_tdma_y,
+ * poisson_x_inv, poisson_ifftz, project ("" if idx is out of range).  outflow and flux_correct
+ * launch only with bc_x = 1 (else their time is 0); poisson_x_* are FFTs for periodic x and
+ * cosine transforms (DCT-II / its inverse) for inflow / outflow. */
 int ns_kernel_count(void);
 const char* ns_kernel_name(int idx);
 
@@ -150,7 +166,8 @@ const char* ns_kernel_name(int idx);
  * nsteps steps, copies them back and synchronises.  Host arrays use the device layout. */
 ns_status ns_step_host(ns_ctx* ctx, double* u, double* v, double* w, double* p, int nsteps);
 
-/* Make the current velocity discretely divergence-free (ns_poisson_solve(-1) + ns_project(-1)). */
+/* Make the current velocity discretely divergence-free (with bc_x = 1: outflow mass-flux
+ * correction first; then ns_poisson_solve(-1) + ns_project(-1)). */
 ns_status ns_make_divergence_free(ns_ctx* ctx);
 
 /* Partitioning of the x-line solver (Sec. 3.2): P partitions per line (a power of two from

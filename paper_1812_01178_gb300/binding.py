@@ -36,11 +36,13 @@ class ns_config(C.Structure):
                 ("yf", C.POINTER(C.c_double)),
                 ("bc_x", C.c_int), ("bc_ytop", C.c_int),
                 ("re", C.c_double), ("fx", C.c_double), ("dt", C.c_double),
-                ("precision", C.c_int)]
+                ("precision", C.c_int), ("u_conv", C.c_double)]
 
 
 class ns_fields(C.Structure):
-    _fields_ = [("u", C.c_void_p), ("v", C.c_void_p), ("w", C.c_void_p), ("p", C.c_void_p)]
+    _fields_ = [("u", C.c_void_p), ("v", C.c_void_p), ("w", C.c_void_p), ("p", C.c_void_p),
+                ("u_out", C.c_void_p), ("v_in", C.c_void_p), ("v_out", C.c_void_p),
+                ("w_in", C.c_void_p), ("w_out", C.c_void_p)]
 
 
 class NSError(RuntimeError):
@@ -97,7 +99,8 @@ def make_config(case, precision=None):
     yf = np.ascontiguousarray(case.yf, dtype=np.float64)
     cfg = ns_config(case.nx, case.ny, case.nz, case.lx, case.lz,
                     yf.ctypes.data_as(C.POINTER(C.c_double)), case.bc_x, case.bc_ytop,
-                    case.re, case.fx, case.dt, case.precision if precision is None else precision)
+                    case.re, case.fx, case.dt, case.precision if precision is None else precision,
+                    getattr(case, "u_conv", 1.0))
     cfg._yf_keep = yf
     return cfg
 
@@ -216,7 +219,8 @@ class Solver:
     C ABI; nothing is computed in Python or PyTorch.
     """
 
-    def __init__(self, case, u=None, v=None, w=None, p=None, precision=None, device="cuda:0", stream=None):
+    def __init__(self, case, u=None, v=None, w=None, p=None, precision=None, device="cuda:0", stream=None,
+                 bl=None):
         import torch
         self.torch = torch
         self.case = case
@@ -240,7 +244,16 @@ class Solver:
             raise NSError(NS_ERR_SIZE, "invalid configuration")
         self.ws = torch.empty(nbytes, dtype=torch.uint8, device=dev)
         self.stream = stream if stream is not None else torch.cuda.current_stream(dev)
-        self.fields = ns_fields(self.u.data_ptr(), self.v.data_ptr(), self.w.data_ptr(), self.p.data_ptr())
+        self.bl = None
+        bptr = [None] * 5
+        if case.bc_x == 1:
+            names = ("u_out", "v_in", "v_out", "w_in", "w_out")
+            shapes = {"u_out": (nz, ny), "v_in": (nz, ny + 1), "v_out": (nz, ny + 1), "w_in": (nz, ny),
+                      "w_out": (nz, ny)}
+            bl = bl or {}
+            self.bl = {q: put(bl.get(q), shapes[q]) for q in names}
+            bptr = [self.bl[q].data_ptr() for q in names]
+        self.fields = ns_fields(self.u.data_ptr(), self.v.data_ptr(), self.w.data_ptr(), self.p.data_ptr(), *bptr)
         self.ctx = ns_init(self.cfg, self.fields, self.ws.data_ptr(), nbytes, self.stream.cuda_stream)
         self.es = 4 if self.cfg.precision == NS_MIXED else 8
 
@@ -298,6 +311,10 @@ class Solver:
     def state(self):
         self.sync()
         return tuple(t.cpu().numpy() for t in (self.u, self.v, self.w, self.p))
+
+    def boundary(self):
+        self.sync()
+        return {q: t.cpu().numpy() for q, t in (self.bl or {}).items()}
 
     def close(self):
         if getattr(self, "ctx", None) is not None:

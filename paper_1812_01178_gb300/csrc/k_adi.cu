@@ -21,11 +21,40 @@ namespace {
 // ----------------------------------------------------------------------------------------------
 template <typename T>
 struct AdiXArgs {
-  const T* __restrict__ tab;
+  const T* __restrict__ tab[2];  // table of the u lines [0] and of the v, w lines [1]
   T* r[3];
   int nx, ny, nz, P, L;
   long nlines;  // nz*ny (u) + nz*(ny-1) (v) + nz*ny (w)
+  // inflow / outflow in x: the outflow-plane increment of component c enters the last row as
+  // + coef[c] * dout[c][k * rows + j]
+  int bl;
+  const double* __restrict__ dout[3];
+  T coef[3];
 };
+
+// component, boundary-plane index and row pointer of x-line number `line`
+template <typename T>
+__device__ __forceinline__ T* x_line(const AdiXArgs<T>& a, long line, int* comp, long* plane) {
+  const int nx = a.nx, ny = a.ny;
+  const long Lu = (long)a.nz * ny;
+  const long Lv = (long)a.nz * (ny - 1);
+  if (line < Lu) {
+    *comp = 0;
+    *plane = line;
+    return a.r[0] + line * nx;
+  }
+  if (line < Lu + Lv) {
+    const long q = line - Lu;
+    const long kk = q / (ny - 1);
+    const long jj = 1 + (q - kk * (ny - 1));
+    *comp = 1;
+    *plane = kk * (ny + 1) + jj;
+    return a.r[1] + *plane * nx;
+  }
+  *comp = 2;
+  *plane = line - Lu - Lv;
+  return a.r[2] + *plane * nx;
+}
 
 template <typename T, int M>
 __device__ __forceinline__ void load_part(const T* __restrict__ src, T (&d)[M]) {
@@ -75,25 +104,14 @@ __global__ void __launch_bounds__(256) adi_x_kernel(AdiXArgs<T> a) {
   T* st = reinterpret_cast<T*>(smem_raw);
   const int P = a.P, L = a.L;
   const int ntab = (int)xtab_count(M, P, L);
-  for (int q = threadIdx.x; q < ntab; q += blockDim.x) st[q] = a.tab[q];
+  const int ncls = a.bl ? 2 : 1;
+  for (int q = threadIdx.x; q < ntab * ncls; q += blockDim.x) st[q] = a.tab[q / ntab][q % ntab];
   __syncthreads();
 
   const int lane = threadIdx.x & 31;
   const int r = lane & (P - 1);
   const int team = lane / P;
   const int teams = 32 / P;
-  const T* INV = st + XT_INV * M * P;
-  const T* AINV = st + XT_AINV * M * P;
-  const T* CP = st + XT_CP * M * P;
-  const T* SV = st + XT_V * M * P;
-  const T* SW = st + XT_W * M * P;
-  const T* DINV = st + XT_NF * M * P;
-  const T* ML = DINV + 4 * P;
-  const T* MU = ML + 4 * L * P;
-
-  const int nx = a.nx, ny = a.ny;
-  const long Lu = (long)a.nz * ny;
-  const long Lv = (long)a.nz * (ny - 1);
   const long warp = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const long nwarps = ((long)gridDim.x * blockDim.x) >> 5;
 
@@ -101,21 +119,22 @@ __global__ void __launch_bounds__(256) adi_x_kernel(AdiXArgs<T> a) {
     const long line = l0 + team;
     const bool valid = line < a.nlines;
     T* row = nullptr;
-    if (valid) {
-      if (line < Lu) {
-        row = a.r[0] + line * nx;
-      } else if (line < Lu + Lv) {
-        const long q = line - Lu;
-        const long kk = q / (ny - 1);
-        const long jj = 1 + (q - kk * (ny - 1));
-        row = a.r[1] + (kk * (ny + 1) + jj) * nx;
-      } else {
-        row = a.r[2] + (line - Lu - Lv) * nx;
-      }
-    }
+    int comp = 0;
+    long plane = 0;
+    if (valid) row = x_line(a, line, &comp, &plane);
+    const T* tb = st + (a.bl && comp != 0 ? ntab : 0);
+    const T* INV = tb + XT_INV * M * P;
+    const T* AINV = tb + XT_AINV * M * P;
+    const T* CP = tb + XT_CP * M * P;
+    const T* SV = tb + XT_V * M * P;
+    const T* SW = tb + XT_W * M * P;
+    const T* DINV = tb + XT_NF * M * P;
+    const T* ML = DINV + 4 * P;
+    const T* MU = ML + 4 * L * P;
     T d[M];
     if (valid) {
       load_part<T, M>(row + r * M, d);
+      if (a.bl && r == P - 1) d[M - 1] += a.coef[comp] * (T)__ldg(a.dout[comp] + plane);
     } else {
 #pragma unroll
       for (int e = 0; e < M; ++e) d[e] = (T)0;
@@ -165,32 +184,22 @@ __global__ void __launch_bounds__(128) adi_x_long_kernel(AdiXArgs<T> a) {
   T* line_buf = reinterpret_cast<T*>(smem_raw) + (threadIdx.x >> 5) * LS;
   const int r = threadIdx.x & 31;
   const int L = a.L;
-  const T* INV = a.tab + XT_INV * M * P;
-  const T* AINV = a.tab + XT_AINV * M * P;
-  const T* CP = a.tab + XT_CP * M * P;
-  const T* SV = a.tab + XT_V * M * P;
-  const T* SW = a.tab + XT_W * M * P;
-  const T* DINV = a.tab + XT_NF * M * P;
-  const T* ML = DINV + 4 * P;
-  const T* MU = ML + 4 * L * P;
-  const int nx = a.nx, ny = a.ny;
-  const long Lu = (long)a.nz * ny;
-  const long Lv = (long)a.nz * (ny - 1);
   const long warp = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const long nwarps = ((long)gridDim.x * blockDim.x) >> 5;
   T* my = line_buf + r * (M + 1);
   for (long line = warp; line < a.nlines; line += nwarps) {
-    T* row;
-    if (line < Lu) {
-      row = a.r[0] + line * nx;
-    } else if (line < Lu + Lv) {
-      const long q = line - Lu;
-      const long kk = q / (ny - 1);
-      const long jj = 1 + (q - kk * (ny - 1));
-      row = a.r[1] + (kk * (ny + 1) + jj) * nx;
-    } else {
-      row = a.r[2] + (line - Lu - Lv) * nx;
-    }
+    int comp;
+    long plane;
+    T* row = x_line(a, line, &comp, &plane);
+    const T* tb = a.tab[a.bl && comp != 0 ? 1 : 0];
+    const T* INV = tb + XT_INV * M * P;
+    const T* AINV = tb + XT_AINV * M * P;
+    const T* CP = tb + XT_CP * M * P;
+    const T* SV = tb + XT_V * M * P;
+    const T* SW = tb + XT_W * M * P;
+    const T* DINV = tb + XT_NF * M * P;
+    const T* ML = DINV + 4 * P;
+    const T* MU = ML + 4 * L * P;
     // coalesced load: element g = q*32 + lane goes to partition g / M, row g % M
 #pragma unroll 4
     for (int q = 0; q < M; ++q) {
@@ -198,6 +207,7 @@ __global__ void __launch_bounds__(128) adi_x_long_kernel(AdiXArgs<T> a) {
       line_buf[(g / M) * (M + 1) + (g % M)] = row[g];
     }
     __syncwarp();
+    if (a.bl && r == P - 1) my[M - 1] += a.coef[comp] * (T)__ldg(a.dout[comp] + plane);
     // A~ x~ = d on partition r
     T prev = my[0] * __ldg(INV + r);
     my[0] = prev;
@@ -327,10 +337,23 @@ __global__ void __launch_bounds__(128) adi_z_kernel(T* __restrict__ ru, T* __res
   }
 }
 
+template <typename T>
+void fill_x_args(ns_ctx* c, int k, AdiXArgs<T>& a) {
+  a.tab[0] = (const T*)c->xtab[k][0];
+  a.tab[1] = (const T*)c->xtab[k][1];
+  a.bl = c->bl;
+  const double inv_re = c->cfg.re > 0 ? 1.0 / c->cfg.re : 0.0;
+  const double rx = NS_ALPHA[k] * c->cfg.dt * inv_re / 2.0 / (c->dx * c->dx);
+  a.coef[0] = (T)rx;          // u: the outflow face is the neighbour of the last unknown face
+  a.coef[1] = (T)(2.0 * rx);  // v, w: linear ghost 2 f_out - f_last
+  a.coef[2] = (T)(2.0 * rx);
+  for (int q = 0; q < 3; ++q) a.dout[q] = c->dout[q];
+}
+
 template <typename T, int M>
 cudaError_t launch_x_t(ns_ctx* c, int k) {
   AdiXArgs<T> a;
-  a.tab = (const T*)c->xtab[k];
+  fill_x_args(c, k, a);
   a.r[0] = (T*)c->ru;
   a.r[1] = (T*)c->rv;
   a.r[2] = (T*)c->rw;
@@ -340,11 +363,10 @@ cudaError_t launch_x_t(ns_ctx* c, int k) {
   a.P = c->P;
   a.L = c->L[k];
   a.nlines = (long)a.nz * a.ny * 2 + (long)a.nz * (a.ny - 1);
-  const size_t smem = xtab_count(M, a.P, a.L) * sizeof(T);
+  const size_t smem = xtab_count(M, a.P, a.L) * sizeof(T) * (a.bl ? 2 : 1);
   const long teams_per_block = 8L * (32 / a.P);
   long blocks = (a.nlines + teams_per_block - 1) / teams_per_block;
   if (blocks > 152L * 16) blocks = 152L * 16;
-  if (smem > 48 * 1024) cudaFuncSetAttribute(adi_x_kernel<T, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   adi_x_kernel<T, M><<<(unsigned)blocks, 256, smem, c->launch>>>(a);
   return cudaGetLastError();
 }
@@ -352,7 +374,7 @@ cudaError_t launch_x_t(ns_ctx* c, int k) {
 template <typename T, int M>
 cudaError_t launch_x_long_t(ns_ctx* c, int k) {
   AdiXArgs<T> a;
-  a.tab = (const T*)c->xtab[k];
+  fill_x_args(c, k, a);
   a.r[0] = (T*)c->ru;
   a.r[1] = (T*)c->rv;
   a.r[2] = (T*)c->rw;
@@ -416,8 +438,19 @@ cudaError_t launch_adi_z(ns_ctx* c, int k) {
   return cudaGetLastError();
 }
 
+template <typename T, int M>
+cudaError_t short_attr() {
+  return cudaFuncSetAttribute(adi_x_kernel<T, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 48 * 1024);
+}
+
 cudaError_t adi_set_attributes() {
   cudaError_t e;
+  if ((e = short_attr<double, 1>()) != cudaSuccess || (e = short_attr<double, 2>()) != cudaSuccess ||
+      (e = short_attr<double, 4>()) != cudaSuccess || (e = short_attr<double, 8>()) != cudaSuccess ||
+      (e = short_attr<double, 16>()) != cudaSuccess || (e = short_attr<float, 1>()) != cudaSuccess ||
+      (e = short_attr<float, 2>()) != cudaSuccess || (e = short_attr<float, 4>()) != cudaSuccess ||
+      (e = short_attr<float, 8>()) != cudaSuccess || (e = short_attr<float, 16>()) != cudaSuccess)
+    return e;
   if ((e = cudaFuncSetAttribute(adi_x_long_kernel<double, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 4 * 32 * 65 * 8)) != cudaSuccess)
     return e;

@@ -68,7 +68,7 @@ __global__ void __launch_bounds__(256) div_fftz_kernel(const double* __restrict_
                                                        const double* __restrict__ w, const double* __restrict__ gc,
                                                        const double2* __restrict__ twz, double2* __restrict__ spec,
                                                        int nx, int ny, int nz, int lnz, int TX, double idx,
-                                                       double idz, double scale) {
+                                                       double idz, double scale, const double* __restrict__ u_out) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int nseq = TX >> 1;
   double2* A = reinterpret_cast<double2*>(smem_raw);
@@ -86,7 +86,9 @@ __global__ void __launch_bounds__(256) div_fftz_kernel(const double* __restrict_
     const int ip = (i + 1 == nx) ? 0 : i + 1;
     const int kp = (k + 1 == nz) ? 0 : k + 1;
     const long c = k * pl + (long)j * nx;
-    const double du = __ldg(u + c + ip) - __ldg(u + c + i);
+    // u on face i+1: periodic wrap, or the outflow plane (u_out != NULL) for the last cell
+    const double uip = (u_out && i + 1 == nx) ? __ldg(u_out + (long)k * ny + j) : __ldg(u + c + ip);
+    const double du = uip - __ldg(u + c + i);
     const double dv = __ldg(v + k * plv + (long)(j + 1) * nx + i) - __ldg(v + k * plv + (long)j * nx + i);
     const double dw = __ldg(w + kp * pl + (long)j * nx + i) - __ldg(w + c + i);
     const double b = fma(du, idx, fma(dv, idy, dw * idz));  // scale folded into idx, idy, idz
@@ -222,7 +224,7 @@ __global__ void __launch_bounds__(128) project_kernel(double* __restrict__ u, do
                                                       double* __restrict__ w, double* __restrict__ p,
                                                       const double* __restrict__ phi, const double* __restrict__ gc,
                                                       int nx, int ny, int nz, double sx, double sz, int update_p,
-                                                      double s) {
+                                                      double s, int bl) {
   const long plane = (long)nx * (ny + 1);
   const long q = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= plane) return;
@@ -235,7 +237,7 @@ __global__ void __launch_bounds__(128) project_kernel(double* __restrict__ u, do
   if (j < ny) {
     const long cc = k * pl + (long)j * nx + i;
     const double f0 = __ldg(phi + cc);
-    u[cc] -= sx * (f0 - __ldg(phi + k * pl + (long)j * nx + im));
+    if (!(bl && i == 0)) u[cc] -= sx * (f0 - __ldg(phi + k * pl + (long)j * nx + im));  // inflow face fixed
     w[cc] -= sz * (f0 - __ldg(phi + km * pl + (long)j * nx + i));
     if (update_p) p[cc] += f0;
   }
@@ -244,6 +246,132 @@ __global__ void __launch_bounds__(128) project_kernel(double* __restrict__ u, do
     const long cc = k * pl + (long)j * nx + i;
     v[(long)k * (ny + 1) * nx + (long)j * nx + i] -= s * ihc * (__ldg(phi + cc) - __ldg(phi + cc - nx));
   }
+}
+
+// ------------------------------------------------------------------------------------------
+// cosine transform along x (inflow / outflow): DCT-II  X_l = sum_i x_i cos(pi l (2i+1) / (2N)) of
+// each complex row (real and imaginary parts independently), by one complex FFT of length N
+// (Makhoul 1980): v = (x_0, x_2, ..., x_3, x_1), V = FFT(v); with V_a, V_b the transforms of
+// the real and imaginary parts of v (separated through V_{N-l}), X_l = Re(w_l V_a) + i Re(w_l V_b),
+// w_l = exp(-i pi l / (2N)).  Inverse (unnormalised, N times the DCT-III inverse):
+// V_l = conj(w_l) (X_l - i X_{N-l}) (X_N = 0), v = IFFT(V), x_{2n} = v_n, x_{2n+1} = v_{N-1-n}.
+// ------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) dctx_fwd_kernel(double2* __restrict__ spec, const double2* __restrict__ twx,
+                                                       const double2* __restrict__ twd, long nrows, int nx, int lnx,
+                                                       int R) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double2* A = reinterpret_cast<double2*>(smem_raw);
+  double2* B = A + R * nx;
+  const long row0 = (long)blockIdx.x * R;
+  const int nr = (int)min((long)R, nrows - row0);
+  double2* g = spec + row0 * nx;
+  for (int q = threadIdx.x; q < R * nx; q += blockDim.x) {
+    const int rr = q / nx, i = q - rr * nx;
+    const int dst = (i & 1) ? nx - 1 - (i >> 1) : (i >> 1);
+    A[rr * nx + dst] = rr < nr ? g[q] : make_double2(0.0, 0.0);
+  }
+  __syncthreads();
+  const double2* V = stockham<-1>(A, B, nx, lnx, R, twx);
+  for (int q = threadIdx.x; q < nr * nx; q += blockDim.x) {
+    const int rr = q / nx, l = q - rr * nx;
+    const double2 vl = V[rr * nx + l];
+    const double2 vn = V[rr * nx + ((nx - l) & (nx - 1))];
+    const double2 w = __ldg(twd + l);
+    const double ax = 0.5 * (vl.x + vn.x), ay = 0.5 * (vl.y - vn.y);
+    const double bx = 0.5 * (vl.y + vn.y), by = 0.5 * (vn.x - vl.x);
+    g[q] = make_double2(fma(w.x, ax, -w.y * ay), fma(w.x, bx, -w.y * by));
+  }
+}
+
+__global__ void __launch_bounds__(256) dctx_inv_kernel(double2* __restrict__ spec, const double2* __restrict__ twx,
+                                                       const double2* __restrict__ twd, long nrows, int nx, int lnx,
+                                                       int R) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double2* A = reinterpret_cast<double2*>(smem_raw);
+  double2* B = A + R * nx;
+  const long row0 = (long)blockIdx.x * R;
+  const int nr = (int)min((long)R, nrows - row0);
+  double2* g = spec + row0 * nx;
+  for (int q = threadIdx.x; q < R * nx; q += blockDim.x) {
+    const int rr = q / nx, l = q - rr * nx;
+    double2 v = make_double2(0.0, 0.0);
+    if (rr < nr) {
+      const double2 xl = g[q];
+      const double2 xn = l == 0 ? make_double2(0.0, 0.0) : g[rr * nx + nx - l];
+      const double2 w = __ldg(twd + l);
+      const double ax = xl.x + xn.y, ay = xl.y - xn.x;  // X_l - i X_{N-l}
+      v = make_double2(fma(w.x, ax, w.y * ay), fma(w.x, ay, -w.y * ax));  // conj(w) (..)
+    }
+    A[q] = v;
+  }
+  __syncthreads();
+  const double2* X = stockham<1>(A, B, nx, lnx, R, twx);
+  for (int q = threadIdx.x; q < nr * nx; q += blockDim.x) {
+    const int rr = q / nx, i = q - rr * nx;
+    const int src = (i & 1) ? nx - 1 - (i >> 1) : (i >> 1);
+    g[q] = X[rr * nx + src];
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// convective outflow dF/dt + U_c dF/dx = 0 on the outflow planes: one upwind step of
+// alpha_k dt; the interior neighbour is the last u face (distance dx) or the last v, w centre
+// (distance dx/2).  Writes the new planes and their increments.
+// ------------------------------------------------------------------------------------------
+__global__ void outflow_kernel(const double* __restrict__ u, const double* __restrict__ v,
+                               const double* __restrict__ w, double* __restrict__ u_out, double* __restrict__ v_out,
+                               double* __restrict__ w_out, double* __restrict__ du, double* __restrict__ dv,
+                               double* __restrict__ dw, int nx, int ny, int nz, double cu, double cv) {
+  const long nu = (long)nz * ny, nv = (long)nz * (ny + 1);
+  for (long q = (long)blockIdx.x * blockDim.x + threadIdx.x; q < 2 * nu + nv; q += (long)gridDim.x * blockDim.x) {
+    if (q < nu) {
+      const double old = u_out[q];
+      const double nb = __ldg(u + q * nx + nx - 1);  // plane index q = k * ny + j
+      const double nw = old - cu * (old - nb);
+      du[q] = nw - old;
+      u_out[q] = nw;
+    } else if (q < nu + nv) {
+      const long e = q - nu;
+      const int j = (int)(e % (ny + 1));
+      const double old = v_out[e];
+      double nw = 0.0;
+      if (j > 0 && j < ny) nw = old - cv * (old - __ldg(v + e * nx + nx - 1));
+      dv[e] = nw - old;
+      v_out[e] = nw;
+    } else {
+      const long e = q - nu - nv;
+      const double old = w_out[e];
+      const double nw = old - cv * (old - __ldg(w + e * nx + nx - 1));
+      dw[e] = nw - old;
+      w_out[e] = nw;
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// outflow mass-flux correction: u_out += (Q_in - Q_out) / (Ly Lz) with Q = sum u dy_j dz over the
+// inflow face (face 0 of u) and the outflow plane.  One block, fixed reduction order.
+// ------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024) flux_correct_kernel(const double* __restrict__ u, double* __restrict__ u_out,
+                                                            const double* __restrict__ gc, int nx, int ny, int nz,
+                                                            double dz_over_area, double* __restrict__ flux) {
+  __shared__ double red[1024];
+  const double* dy = gc + GC_DY * (ny + 1);
+  const long n = (long)nz * ny;
+  double acc = 0.0;
+  for (long q = threadIdx.x; q < n; q += blockDim.x) {
+    const int j = (int)(q % ny);
+    acc += (__ldg(u + q * nx) - u_out[q]) * __ldg(dy + j);
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s2 = blockDim.x / 2; s2 > 0; s2 >>= 1) {
+    if (threadIdx.x < s2) red[threadIdx.x] += red[threadIdx.x + s2];
+    __syncthreads();
+  }
+  const double corr = red[0] * dz_over_area;
+  for (long q = threadIdx.x; q < n; q += blockDim.x) u_out[q] += corr;
+  if (threadIdx.x == 0 && flux) flux[1] = corr;
 }
 
 // ------------------------------------------------------------------------------------------
@@ -288,6 +416,8 @@ cudaError_t poisson_set_attributes() {
   cudaFuncSetAttribute(ifftz_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   cudaFuncSetAttribute(fftx_kernel<-1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   cudaFuncSetAttribute(fftx_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaFuncSetAttribute(dctx_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaFuncSetAttribute(dctx_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   return cudaGetLastError();
 }
 
@@ -336,13 +466,18 @@ cudaError_t launch_pois_divz(ns_ctx* c, int k) {
   const double scale = ((k >= 0) ? 1.0 / (NS_ALPHA[k] * c->cfg.dt) : 1.0) / ((double)q.nx * q.nz);
   div_fftz_kernel<<<dim3(q.nx / q.TX, q.ny), 256, q.smz, c->launch>>>(c->f.u, c->f.v, c->f.w, c->gc, c->twz,
                                                                      c->spec, q.nx, q.ny, q.nz, q.lnz, q.TX,
-                                                                     1.0 / c->dx, 1.0 / c->dz, scale);
+                                                                     1.0 / c->dx, 1.0 / c->dz, scale,
+                                                                     c->bl ? c->f.u_out : nullptr);
   return cudaGetLastError();
 }
 
 // A6: forward complex FFT along x
 cudaError_t launch_pois_fftx_fwd(ns_ctx* c, int) {
   const PoisShape q = pois_shape(c);
+  if (c->bl) {
+    dctx_fwd_kernel<<<q.bx, 256, q.smx, c->launch>>>(c->spec, c->twx, c->twd, q.nrows, q.nx, q.lnx, q.R);
+    return cudaGetLastError();
+  }
   fftx_kernel<-1><<<q.bx, 256, q.smx, c->launch>>>(c->spec, c->twx, q.nrows, q.nx, q.lnx, q.R, 1.0);
   return cudaGetLastError();
 }
@@ -357,6 +492,10 @@ cudaError_t launch_pois_tdma(ns_ctx* c, int) {
 // A8: inverse complex FFT along x, scaled by 1/(nx nz)
 cudaError_t launch_pois_fftx_inv(ns_ctx* c, int) {
   const PoisShape q = pois_shape(c);
+  if (c->bl) {
+    dctx_inv_kernel<<<q.bx, 256, q.smx, c->launch>>>(c->spec, c->twx, c->twd, q.nrows, q.nx, q.lnx, q.R);
+    return cudaGetLastError();
+  }
   fftx_kernel<1><<<q.bx, 256, q.smx, c->launch>>>(c->spec, c->twx, q.nrows, q.nx, q.lnx, q.R, 1.0);
   return cudaGetLastError();
 }
@@ -384,6 +523,27 @@ cudaError_t launch_project(ns_ctx* c, int k) {
   const long plane = (long)nx * (ny + 1);
   dim3 grid((unsigned)((plane + 127) / 128), nz);
   project_kernel<<<grid, 128, 0, c->launch>>>(c->f.u, c->f.v, c->f.w, c->f.p, c->phi, c->gc, nx, ny, nz, s / c->dx,
-                                              s / c->dz, k >= 0 ? 1 : 0, s);
+                                              s / c->dz, k >= 0 ? 1 : 0, s, c->bl);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_outflow(ns_ctx* c, int k) {
+  if (!c->bl) return cudaSuccess;
+  const int nx = c->cfg.nx, ny = c->cfg.ny, nz = c->cfg.nz;
+  const double step = NS_ALPHA[k] * c->cfg.dt * c->cfg.u_conv;
+  const long n = 2L * nz * ny + (long)nz * (ny + 1);
+  const unsigned blocks = (unsigned)min((n + 255) / 256, 4096L);
+  outflow_kernel<<<blocks, 256, 0, c->launch>>>(c->f.u, c->f.v, c->f.w, c->f.u_out, c->f.v_out, c->f.w_out,
+                                                c->dout[0], c->dout[1], c->dout[2], nx, ny, nz, step / c->dx,
+                                                step / (0.5 * c->dx));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_flux_correct(ns_ctx* c, int) {
+  if (!c->bl) return cudaSuccess;
+  const int ny = c->cfg.ny;
+  const double area = (c->yf[ny] - c->yf[0]) * c->cfg.lz;
+  flux_correct_kernel<<<1, 1024, 0, c->launch>>>(c->f.u, c->f.u_out, c->gc, c->cfg.nx, ny, c->cfg.nz,
+                                                 c->dz / area, c->flux);
   return cudaGetLastError();
 }

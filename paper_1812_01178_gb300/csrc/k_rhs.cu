@@ -25,6 +25,13 @@ struct RhsArgs {
   void* nw;
   const double* __restrict__ gc;
   const double* __restrict__ rt;  // per-j assembly coefficients of this sub-step (RT_* rows)
+  // inflow / outflow in x (bl = 1): boundary planes, index k * rows + j
+  int bl;
+  const double* __restrict__ u_out;
+  const double* __restrict__ v_in;
+  const double* __restrict__ v_out;
+  const double* __restrict__ w_in;
+  const double* __restrict__ w_out;
   int nx, ny, nz;
   double idx, idz, idx2, idz2;
   double dt, gam, zet, alp, inv_re, fx;
@@ -46,10 +53,28 @@ __global__ void __launch_bounds__(128) rhs_kernel(RhsArgs a) {
   const int ny1 = ny + 1;
   const int G = ny + 1;  // stride of the coefficient arrays
 
-  auto U = [&](int ii, int jj, int kk) -> T { return (T)__ldg(a.u + ((long)kk * ny + jj) * nx + ii); };
-  auto V = [&](int ii, int jj, int kk) -> T { return (T)__ldg(a.v + ((long)kk * ny1 + jj) * nx + ii); };
-  auto W = [&](int ii, int jj, int kk) -> T { return (T)__ldg(a.w + ((long)kk * ny + jj) * nx + ii); };
-  auto Pp = [&](int ii, int jj, int kk) -> T { return (T)__ldg(a.p + ((long)kk * ny + jj) * nx + ii); };
+  // x-neighbours: periodic wrap, or (bl) the outflow plane / linear ghosts of the boundary faces
+  const bool bl = a.bl != 0;
+  const int ipx = bl ? i + 1 : ip, imx = bl ? i - 1 : im;
+  auto U = [&](int ii, int jj, int kk) -> T {
+    if (ii == nx) return (T)__ldg(a.u_out + (long)kk * ny + jj);
+    if (ii < 0) return (T)0;
+    return (T)__ldg(a.u + ((long)kk * ny + jj) * nx + ii);
+  };
+  auto V = [&](int ii, int jj, int kk) -> T {
+    if (ii == nx) return (T)(2.0 * __ldg(a.v_out + (long)kk * ny1 + jj) - __ldg(a.v + ((long)kk * ny1 + jj) * nx + nx - 1));
+    if (ii < 0) return (T)(2.0 * __ldg(a.v_in + (long)kk * ny1 + jj) - __ldg(a.v + ((long)kk * ny1 + jj) * nx));
+    return (T)__ldg(a.v + ((long)kk * ny1 + jj) * nx + ii);
+  };
+  auto W = [&](int ii, int jj, int kk) -> T {
+    if (ii == nx) return (T)(2.0 * __ldg(a.w_out + (long)kk * ny + jj) - __ldg(a.w + ((long)kk * ny + jj) * nx + nx - 1));
+    if (ii < 0) return (T)(2.0 * __ldg(a.w_in + (long)kk * ny + jj) - __ldg(a.w + ((long)kk * ny + jj) * nx));
+    return (T)__ldg(a.w + ((long)kk * ny + jj) * nx + ii);
+  };
+  auto Pp = [&](int ii, int jj, int kk) -> T {
+    if (ii < 0 || ii == nx) return (T)0;
+    return (T)__ldg(a.p + ((long)kk * ny + jj) * nx + ii);
+  };
   auto C = [&](int f, int jj) -> T { return (T)__ldg(a.gc + f * G + jj); };
 
   const T idx = (T)a.idx, idz = (T)a.idz, idx2 = (T)a.idx2, idz2 = (T)a.idz2;
@@ -69,7 +94,7 @@ __global__ void __launch_bounds__(128) rhs_kernel(RhsArgs a) {
     const T idy = C(GC_IDY, j);
     // ---------------- u at (xf_i, yc_j, zc_k)
     {
-      const T u0 = U(i, j, k), uxp = U(ip, j, k), uxm = U(im, j, k);
+      const T u0 = U(i, j, k), uxp = U(ipx, j, k), uxm = U(imx, j, k);
       const T uzp = U(i, j, kp), uzm = U(i, j, km);
       const T uyp = (j + 1 < ny) ? U(i, j + 1, k) : (T)0;
       const T uym = (j > 0) ? U(i, j - 1, k) : (T)0;
@@ -78,32 +103,33 @@ __global__ void __launch_bounds__(128) rhs_kernel(RhsArgs a) {
       T ft = 0, fb = 0;
       if (j + 1 < ny) {
         const T ut = C(GC_WLO, j + 1) * u0 + C(GC_WHI, j + 1) * uyp;
-        ft = ut * (V(im, j + 1, k) + V(i, j + 1, k));
+        ft = ut * (V(imx, j + 1, k) + V(i, j + 1, k));
       }
       if (j > 0) {
         const T ub = C(GC_WLO, j) * uym + C(GC_WHI, j) * u0;
-        fb = ub * (V(im, j, k) + V(i, j, k));
+        fb = ub * (V(imx, j, k) + V(i, j, k));
       }
       const T nuy = (ft - fb) * (half * idy);
-      const T nuz = ((u0 + uzp) * (W(im, j, kp) + W(i, j, kp)) - (uzm + u0) * (W(im, j, k) + W(i, j, k))) *
+      const T nuz = ((u0 + uzp) * (W(imx, j, kp) + W(i, j, kp)) - (uzm + u0) * (W(imx, j, k) + W(i, j, k))) *
                     (quarter * idz);
       const T n = nux + nuy + nuz;
       const T ac = C(GC_AC, j), cy = C(GC_CC, j);
       const T lap = (uxp - two * u0 + uxm) * idx2 + (uzp - two * u0 + uzm) * idz2 + ac * uym -
                     (ac + cy) * u0 + cy * uyp;
-      const T gp = (Pp(i, j, k) - Pp(im, j, k)) * idx;
+      const T gp = (Pp(i, j, k) - Pp(imx, j, k)) * idx;
       T r = -gam * n - alp * gp + avis * lap + (T)(a.alp * a.fx);
       if (a.zet != 0.0) r -= zet * (T)nu[cc];
-      ru[cc] = (TR)(dt * r);
-      nu[cc] = (TR)n;
+      const bool fixed = bl && i == 0;  // inflow face
+      ru[cc] = fixed ? (TR)0 : (TR)(dt * r);
+      nu[cc] = fixed ? (TR)0 : (TR)n;
     }
     // ---------------- w at (xc_i, yc_j, zf_k)
     {
-      const T w0 = W(i, j, k), wxp = W(ip, j, k), wxm = W(im, j, k);
+      const T w0 = W(i, j, k), wxp = W(ipx, j, k), wxm = W(imx, j, k);
       const T wzp = W(i, j, kp), wzm = W(i, j, km);
       const T wyp = (j + 1 < ny) ? W(i, j + 1, k) : (T)0;
       const T wym = (j > 0) ? W(i, j - 1, k) : (T)0;
-      const T fr = (U(ip, j, km) + U(ip, j, k)) * (w0 + wxp);
+      const T fr = (U(ipx, j, km) + U(ipx, j, k)) * (w0 + wxp);
       const T fl = (U(i, j, km) + U(i, j, k)) * (wxm + w0);
       const T nwx = (fr - fl) * (quarter * idx);
       T gt = 0, gb = 0;
@@ -131,11 +157,11 @@ __global__ void __launch_bounds__(128) rhs_kernel(RhsArgs a) {
       nv[cf] = (TR)0;
       return;
     }
-    const T v0 = V(i, j, k), vxp = V(ip, j, k), vxm = V(im, j, k);
+    const T v0 = V(i, j, k), vxp = V(ipx, j, k), vxm = V(imx, j, k);
     const T vzp = V(i, j, kp), vzm = V(i, j, km);
     const T vyp = V(i, j + 1, k), vym = V(i, j - 1, k);
     const T wl = C(GC_WLO, j), wh = C(GC_WHI, j);
-    const T fr = (wl * U(ip, j - 1, k) + wh * U(ip, j, k)) * (v0 + vxp);
+    const T fr = (wl * U(ipx, j - 1, k) + wh * U(ipx, j, k)) * (v0 + vxp);
     const T fl = (wl * U(i, j - 1, k) + wh * U(i, j, k)) * (vxm + v0);
     const T nvx = (fr - fl) * (half * idx);
     const T ct = v0 + vyp, cb = vym + v0;
@@ -205,14 +231,32 @@ __global__ void __launch_bounds__(RT_X * RT_Z) rhs_tiled_kernel(RhsArgs a, int j
       const int f = q / RT_PLANE, e = q - f * RT_PLANE;
       const int kk = e / RT_PX - 1, ii = e % RT_PX - 1;
       int gi = i0 + ii, gk = k0 + kk;
-      gi = gi < 0 ? gi + nx : (gi >= nx ? gi - nx : gi);
       gk = gk < 0 ? gk + nz : (gk >= nz ? gk - nz : gk);
       T val = (T)0;
-      if (f == 1) {
-        if (j >= 0 && j <= ny) val = (T)__ldg(a.v + ((long)gk * ny1 + j) * nx + gi);
-      } else if (j >= 0 && j < ny) {
-        const double* src = f == 0 ? a.u : (f == 2 ? a.w : a.p);
-        val = (T)__ldg(src + ((long)gk * ny + j) * nx + gi);
+      if (a.bl && (gi < 0 || gi >= nx)) {
+        // x-boundary halo: outflow plane of u, linear ghosts of v and w, nothing for p
+        const bool out = gi >= nx;
+        if (f == 0) {
+          if (out && j >= 0 && j < ny) val = (T)__ldg(a.u_out + (long)gk * ny + j);
+        } else if (f == 1) {
+          if (j >= 0 && j <= ny) {
+            const double b = __ldg((out ? a.v_out : a.v_in) + (long)gk * ny1 + j);
+            val = (T)(2.0 * b - __ldg(a.v + ((long)gk * ny1 + j) * nx + (out ? nx - 1 : 0)));
+          }
+        } else if (f == 2) {
+          if (j >= 0 && j < ny) {
+            const double b = __ldg((out ? a.w_out : a.w_in) + (long)gk * ny + j);
+            val = (T)(2.0 * b - __ldg(a.w + ((long)gk * ny + j) * nx + (out ? nx - 1 : 0)));
+          }
+        }
+      } else {
+        gi = gi < 0 ? gi + nx : (gi >= nx ? gi - nx : gi);
+        if (f == 1) {
+          if (j >= 0 && j <= ny) val = (T)__ldg(a.v + ((long)gk * ny1 + j) * nx + gi);
+        } else if (j >= 0 && j < ny) {
+          const double* src = f == 0 ? a.u : (f == 2 ? a.w : a.p);
+          val = (T)__ldg(src + ((long)gk * ny + j) * nx + gi);
+        }
       }
       S.pl[f][j & 3][e] = val;
     }
@@ -325,8 +369,9 @@ __global__ void __launch_bounds__(RT_X * RT_Z) rhs_tiled_kernel(RhsArgs a, int j
         r += cz * (P(0, j, tz + 1, tx) + P(0, j, tz - 1, tx));
         r += cA * P(0, j - 1, tz, tx) + cC * P(0, j + 1, tz, tx) + cD * u0;
         if (use_prev) r += cp * (T)nu[cc];
-        ru[cc] = (TR)r;
-        nu[cc] = (TR)n;
+        const bool fixed = a.bl && i == 0;  // inflow face of u
+        ru[cc] = fixed ? (TR)0 : (TR)r;
+        nu[cc] = fixed ? (TR)0 : (TR)n;
       }
       // ---------------- w at (xc_i, yc_j, zf_k)
       {
@@ -389,6 +434,12 @@ cudaError_t launch_rhs(ns_ctx* c, int k) {
   a.inv_re = c->cfg.re > 0 ? 1.0 / c->cfg.re : 0.0;
   a.fx = c->cfg.fx;
   a.rt = c->rtab[k];
+  a.bl = c->bl;
+  a.u_out = c->f.u_out;
+  a.v_in = c->f.v_in;
+  a.v_out = c->f.v_out;
+  a.w_in = c->f.w_in;
+  a.w_out = c->f.w_out;
   if (a.nx % RT_X == 0 && a.nz % RT_Z == 0) {
     // split y into chunks (each re-derives one face and two planes) so that the blocks fill
     // whole waves of the resident capacity: minimise waves * (planes per chunk + prologue)

@@ -23,10 +23,7 @@ std::string check_cfg(const ns_config* c, ns_status* kind = nullptr) {
   k = NS_ERR_ARG;
   if (!c) return "cfg is NULL";
   if (!c->yf) return "cfg->yf is NULL";
-  if (c->bc_x != 0) {
-    k = NS_ERR_UNSUPPORTED;
-    return "bc_x = 1 (inflow / convective outflow) is not built";
-  }
+  if (c->bc_x != 0 && c->bc_x != 1) return "bc_x must be 0 or 1";
   if (c->bc_ytop != 0 && c->bc_ytop != 1) return "bc_ytop must be 0 or 1";
   if (c->precision != NS_FP64 && c->precision != NS_MIXED) return "precision must be NS_FP64 or NS_MIXED";
   k = NS_ERR_SIZE;
@@ -57,7 +54,7 @@ ns_layout make_layout(const ns_config* c) {
   sz[LB_SPEC] = nzh * ny * nx * 16;
   sz[LB_POIS] = nzh * ny * nx * 16;
   sz[LB_GC] = NS_GC_COUNT * (ny + 1) * 8;
-  sz[LB_XTAB] = 3 * al256((5 * nx + 4 * 32 + 8 * 5 * 32) * es);
+  sz[LB_XTAB] = 6 * al256((5 * nx + 4 * 32 + 8 * 5 * 32) * es);
   sz[LB_YTAB] = 6 * al256(3 * ny * es);
   sz[LB_ZTAB] = 3 * al256((4 * nz + 2) * es);
   sz[LB_TWZ] = (nz / 2) * 16;
@@ -65,6 +62,8 @@ ns_layout make_layout(const ns_config* c) {
   sz[LB_LAMX] = nx * 8;
   sz[LB_LAMZ] = nzh * 8;
   sz[LB_RTAB] = 3 * al256((size_t)RT_COUNT * (ny + 1) * 8);
+  sz[LB_DOUT] = 3 * al256((ny + 1) * nz * 8) + 256;
+  sz[LB_TWD] = nx * 16;
   size_t o = 0;
   for (int b = 0; b < LB_COUNT; ++b) {
     L.off[b] = o;
@@ -119,34 +118,56 @@ M2 minv(M2 x) {
 }
 M2 mzero() { return {0, 0, 0, 0}; }
 
-// Partitioned x solver tables for constant rows (lo, di, up) on a periodic line of n = P*M rows
-// (Sec. 3.2).  mode: NS_PART_PDD or NS_PART_PPT.  Returns the table (doubles), its number of
-// reduction levels and the largest coupling PDD drops.
-std::vector<double> build_xtab(double lo, double di, double up, int n, int P, int mode, int* levels,
+// Partitioned x solver tables (Sec. 3.2) for the rows (a, b, c) of one x-line of n = P*M rows,
+// periodic (cyclic) or not.  mode: NS_PART_PDD or NS_PART_PPT.  Per partition r: the block
+// Thomas factors of A~ (couplings to the neighbouring partitions cut), the spikes v^(r), w^(r)
+// of Eq. (blockAY) (zero where no coupling was cut: the ends of a non-periodic line), and the
+// 2x2-block reduced system Z of Eq. (Zpdd) over the interfaces (r, r+1):
+//   L_r Y_{r-1} + D_r Y_r + U_r Y_{r+1} = (x~^(r)_m, x~^(r+1)_1),
+//   D_r = [[1, w^(r)_m], [v^(r+1)_1, 1]], L_r = [[v^(r)_m, 0], [0, 0]], U_r = [[0, 0], [0, w^(r+1)_1]];
+// a non-periodic line has P-1 interfaces and a decoupled identity row in slot P-1.  PDD keeps D_r;
+// PPT eliminates L, U by block parallel cyclic reduction (multipliers stored per level).
+// Returns the table, the number of reduction levels and the largest coupling PDD drops.
+std::vector<double> build_xtab(const std::vector<double>& A, const std::vector<double>& Bv,
+                               const std::vector<double>& Cv, int P, bool cyclic, int mode, int* levels,
                                double* dropped) {
+  const int n = (int)Bv.size();
   const int M = n / P;
   int L = 0;
   while ((1 << L) < P) ++L;
-  // block Thomas factors of one partition of A~ (couplings to the neighbours cut)
-  std::vector<double> a(M, lo), b(M, di), c(M, up);
-  std::vector<double> inv, ainv, cp;
-  thomas_factors(a, b, c, inv, ainv, cp);
-  // spikes: A~ v = lo e_1, A~ w = up e_M  (Eq. blockAY, V columns of the cut couplings)
-  std::vector<double> e1(M, 0.0), em(M, 0.0);
-  e1[0] = lo;
-  em[M - 1] = up;
-  std::vector<double> sv = thomas_apply(inv, ainv, cp, e1);
-  std::vector<double> sw = thomas_apply(inv, ainv, cp, em);
-  // interface r couples partition r (last row) and r+1 (first row), cyclically.
-  // Z block row r: L_r Y_{r-1} + D_r Y_r + U_r Y_{r+1} = (x~^{(r)}_m, x~^{(r+1)}_1)
-  std::vector<M2> Lb(P), Db(P), Ub(P);
+  std::vector<double> inv(n), ainv(n), cp(n), sv(n, 0.0), sw(n, 0.0);
   for (int r = 0; r < P; ++r) {
-    Db[r] = {1.0, sw[M - 1], sv[0], 1.0};
-    Lb[r] = {sv[M - 1], 0.0, 0.0, 0.0};
-    Ub[r] = {0.0, 0.0, 0.0, sw[0]};
+    const int o = r * M;
+    std::vector<double> a(A.begin() + o, A.begin() + o + M), b(Bv.begin() + o, Bv.begin() + o + M),
+        c(Cv.begin() + o, Cv.begin() + o + M), i1, i2, i3;
+    thomas_factors(a, b, c, i1, i2, i3);  // a[0], c[M-1] (the cut couplings) are ignored
+    std::copy(i1.begin(), i1.end(), inv.begin() + o);
+    std::copy(i2.begin(), i2.end(), ainv.begin() + o);
+    std::copy(i3.begin(), i3.end(), cp.begin() + o);
+    std::vector<double> e1(M, 0.0), em(M, 0.0);
+    if (cyclic || r > 0) e1[0] = A[o];                 // a of the first row couples partition r-1
+    if (cyclic || r < P - 1) em[M - 1] = Cv[o + M - 1];  // c of the last row couples partition r+1
+    const std::vector<double> v1 = thomas_apply(i1, i2, i3, e1), w1 = thomas_apply(i1, i2, i3, em);
+    std::copy(v1.begin(), v1.end(), sv.begin() + o);
+    std::copy(w1.begin(), w1.end(), sw.begin() + o);
   }
+  auto V = [&](int r, int e) { return sv[r * M + e]; };
+  auto W = [&](int r, int e) { return sw[r * M + e]; };
+  std::vector<M2> Lb(P), Db(P), Ub(P);
   double drop = 0.0;
-  for (int r = 0; r < P; ++r) drop = std::fmax(drop, std::fmax(std::fabs(Lb[r].a), std::fabs(Ub[r].d)));
+  for (int r = 0; r < P; ++r) {
+    const int rn = (r + 1) % P;
+    if (!cyclic && r == P - 1) {
+      Db[r] = {1.0, 0.0, 0.0, 1.0};
+      Lb[r] = mzero();
+      Ub[r] = mzero();
+      continue;
+    }
+    Db[r] = {1.0, W(r, M - 1), V(rn, 0), 1.0};
+    Lb[r] = {V(r, M - 1), 0.0, 0.0, 0.0};
+    Ub[r] = {0.0, 0.0, 0.0, W(rn, 0)};
+    drop = std::fmax(drop, std::fmax(std::fabs(Lb[r].a), std::fabs(Ub[r].d)));
+  }
   *dropped = drop;
   std::vector<M2> MLs, MUs;  // per level, per r
   if (mode == NS_PART_PPT && P == 1) {
@@ -154,10 +175,10 @@ std::vector<double> build_xtab(double lo, double di, double up, int n, int P, in
     Db[0] = madd(Db[0], madd(Lb[0], Ub[0]));
   }
   if (mode == NS_PART_PPT) {
-    for (int lv = 0, s = 1; lv < L; ++lv, s <<= 1) {
+    for (int lv = 0, st = 1; lv < L; ++lv, st <<= 1) {
       std::vector<M2> nL(P), nD(P), nU(P);
       for (int r = 0; r < P; ++r) {
-        const int rm = ((r - s) % P + P) % P, rp = (r + s) % P;
+        const int rm = ((r - st) % P + P) % P, rp = (r + st) % P;
         M2 ml, mu;
         if (rm == rp) {
           ml = mmul(madd(Lb[r], Ub[r]), minv(Db[rm]));
@@ -169,7 +190,7 @@ std::vector<double> build_xtab(double lo, double di, double up, int n, int P, in
           ml = mmul(Lb[r], minv(Db[rm]));
           mu = mmul(Ub[r], minv(Db[rp]));
           nD[r] = msub(msub(Db[r], mmul(ml, Ub[rm])), mmul(mu, Lb[rp]));
-          // new couplings at distance 2s; when they coincide (4s = P) the next level folds them
+          // new couplings at distance 2 st; when they coincide (4 st = P) the next level folds them
           nL[r] = msub(mzero(), mmul(ml, Lb[rm]));
           nU[r] = msub(mzero(), mmul(mu, Ub[rp]));
         }
@@ -186,11 +207,11 @@ std::vector<double> build_xtab(double lo, double di, double up, int n, int P, in
   std::vector<double> t(xtab_count(M, P, L), 0.0);
   for (int r = 0; r < P; ++r)
     for (int e = 0; e < M; ++e) {
-      t[(XT_INV * M + e) * P + r] = inv[e];
-      t[(XT_AINV * M + e) * P + r] = ainv[e];
-      t[(XT_CP * M + e) * P + r] = cp[e];
-      t[(XT_V * M + e) * P + r] = sv[e];
-      t[(XT_W * M + e) * P + r] = sw[e];
+      t[(XT_INV * M + e) * P + r] = inv[r * M + e];
+      t[(XT_AINV * M + e) * P + r] = ainv[r * M + e];
+      t[(XT_CP * M + e) * P + r] = cp[r * M + e];
+      t[(XT_V * M + e) * P + r] = V(r, e);
+      t[(XT_W * M + e) * P + r] = W(r, e);
     }
   const size_t d0 = (size_t)XT_NF * M * P;
   for (int r = 0; r < P; ++r) {
@@ -240,20 +261,46 @@ double beta_of(const ns_ctx* c, int k) {
   return NS_ALPHA[k] * c->cfg.dt * inv_re / 2.0;
 }
 
-// x-solver tables for every sub-step with the context's P and requested mode.
-ns_status build_x_tables(ns_ctx* c) {
+// Rows of (I - beta_k delta_xx) on one x-line (Sec. 2.2) for the u lines (cls 0) and the v, w
+// lines (cls 1).  Periodic: every row (-r, 1 + 2r, -r), cyclic.  Inflow / outflow: the u line
+// holds faces 0..nx-1 with face 0 fixed (identity row) and the outflow face as the neighbour of
+// the last row (its increment enters the right-hand side); v, w lines are cell centres whose
+// first and last rows see linear ghosts of the boundary faces: b = 1 + 3r there.
+void x_rows(const ns_ctx* c, int k, int cls, std::vector<double>& a, std::vector<double>& b,
+            std::vector<double>& cc) {
   const int nx = c->cfg.nx;
+  const double r = beta_of(c, k) / (c->dx * c->dx);
+  a.assign(nx, -r);
+  b.assign(nx, 1.0 + 2.0 * r);
+  cc.assign(nx, -r);
+  if (!c->bl) return;
+  a[0] = 0.0;
+  cc[nx - 1] = 0.0;
+  if (cls == 0) {
+    b[0] = 1.0;
+    cc[0] = 0.0;
+  } else {
+    b[0] = 1.0 + 3.0 * r;
+    b[nx - 1] = 1.0 + 3.0 * r;
+  }
+}
+
+// x-solver tables for every sub-step and line class with the context's P and requested mode.
+ns_status build_x_tables(ns_ctx* c) {
   const double tol = c->es == 8 ? 1e-15 : 1e-8;
   double drop_max = 0.0;
-  std::vector<double> tabs[3][2];
+  std::vector<double> tabs[3][2][2];
   int levs[3][2];
-  for (int k = 0; k < 3; ++k) {
-    const double r = beta_of(c, k) / (c->dx * c->dx);
-    double d0, d1;
-    tabs[k][0] = build_xtab(-r, 1.0 + 2.0 * r, -r, nx, c->P, NS_PART_PDD, &levs[k][0], &d0);
-    tabs[k][1] = build_xtab(-r, 1.0 + 2.0 * r, -r, nx, c->P, NS_PART_PPT, &levs[k][1], &d1);
-    drop_max = std::fmax(drop_max, d0);
-  }
+  const bool cyclic = !c->bl;
+  for (int k = 0; k < 3; ++k)
+    for (int cls = 0; cls < 2; ++cls) {
+      std::vector<double> a, b, cc;
+      x_rows(c, k, cls, a, b, cc);
+      double d0, d1;
+      tabs[k][cls][0] = build_xtab(a, b, cc, c->P, cyclic, NS_PART_PDD, &levs[k][0], &d0);
+      tabs[k][cls][1] = build_xtab(a, b, cc, c->P, cyclic, NS_PART_PPT, &levs[k][1], &d1);
+      drop_max = std::fmax(drop_max, d0);
+    }
   int mode = c->part_req;
   if (mode == NS_PART_AUTO) mode = drop_max <= tol ? NS_PART_PDD : NS_PART_PPT;
   c->part_mode = mode;
@@ -261,8 +308,10 @@ ns_status build_x_tables(ns_ctx* c) {
   const int sel = mode == NS_PART_PDD ? 0 : 1;
   for (int k = 0; k < 3; ++k) {
     c->L[k] = levs[k][sel];
-    if (tabs[k][sel].size() > c->xtab_stride) return NS_ERR_SIZE;
-    if (upload(c, c->xtab[k], tabs[k][sel]) != cudaSuccess) return NS_ERR_CUDA;
+    for (int cls = 0; cls < 2; ++cls) {
+      if (tabs[k][cls][sel].size() > c->xtab_stride) return NS_ERR_SIZE;
+      if (upload(c, c->xtab[k][cls], tabs[k][cls][sel]) != cudaSuccess) return NS_ERR_CUDA;
+    }
   }
   if (cudaStreamSynchronize(c->stream) != cudaSuccess) return NS_ERR_CUDA;
   return NS_OK;
@@ -304,13 +353,15 @@ struct Stage {
 };
 const Stage STAGES[] = {
     {"rhs", launch_rhs},                      // A1
+    {"outflow", launch_outflow},              // A10 (convective outflow; inflow / outflow only)
     {"adi_x", launch_adi_x},                  // A2
     {"adi_y", launch_adi_y},                  // A3
     {"adi_z", launch_adi_z},                  // A4
+    {"flux_correct", launch_flux_correct},    // A10 (outflow mass flux; inflow / outflow only)
     {"poisson_div_fftz", launch_pois_divz},   // A5
-    {"poisson_fftx_fwd", launch_pois_fftx_fwd},  // A6
+    {"poisson_x_fwd", launch_pois_fftx_fwd},  // A6 (FFT, or DCT-II for inflow / outflow)
     {"poisson_tdma_y", launch_pois_tdma},     // A7
-    {"poisson_fftx_inv", launch_pois_fftx_inv},  // A8
+    {"poisson_x_inv", launch_pois_fftx_inv},  // A8
     {"poisson_ifftz", launch_pois_ifftz},     // A9
     {"project", launch_project},              // A10
 };
@@ -381,6 +432,10 @@ ns_status ns_init(ns_ctx** out, const ns_config* cfg, const ns_fields* fields, v
     g_init_error = "fields or a field pointer is NULL";
     return NS_ERR_ARG;
   }
+  if (cfg->bc_x == 1 && (!fields->u_out || !fields->v_in || !fields->v_out || !fields->w_in || !fields->w_out)) {
+    g_init_error = "inflow / outflow in x needs the five boundary planes in fields";
+    return NS_ERR_ARG;
+  }
   const void* ptrs[4] = {fields->u, fields->v, fields->w, fields->p};
   for (const void* p : ptrs)
     if ((uintptr_t)p % 256 != 0) {
@@ -393,6 +448,7 @@ ns_status ns_init(ns_ctx** out, const ns_config* cfg, const ns_fields* fields, v
     return NS_ERR_ARG;
   }
   c->cfg = *cfg;
+  c->bl = cfg->bc_x == 1;
   c->yf.assign(cfg->yf, cfg->yf + cfg->ny + 1);
   c->cfg.yf = c->yf.data();
   c->f = *fields;
@@ -444,13 +500,17 @@ ns_status ns_init(ns_ctx** out, const ns_config* cfg, const ns_fields* fields, v
   const int nx = cfg->nx, ny = cfg->ny, nz = cfg->nz;
   c->xtab_stride = (5 * (size_t)nx + 4 * 32 + 8 * 5 * 32);
   for (int k = 0; k < 3; ++k) {
-    c->xtab[k] = base + c->lay.off[LB_XTAB] + k * al256(c->xtab_stride * c->es);
+    for (int cls = 0; cls < 2; ++cls)
+      c->xtab[k][cls] = base + c->lay.off[LB_XTAB] + (2 * k + cls) * al256(c->xtab_stride * c->es);
     for (int q = 0; q < 2; ++q) c->ytab[k][q] = base + c->lay.off[LB_YTAB] + (2 * k + q) * al256(3 * ny * c->es);
     c->ztab[k] = base + c->lay.off[LB_ZTAB] + k * al256((4 * nz + 2) * c->es);
   }
   c->twz = (double2*)(base + c->lay.off[LB_TWZ]);
   c->twx = (double2*)(base + c->lay.off[LB_TWX]);
   double* lamx_d = (double*)(base + c->lay.off[LB_LAMX]);
+  for (int q = 0; q < 3; ++q) c->dout[q] = (double*)(base + c->lay.off[LB_DOUT] + q * al256((size_t)(ny + 1) * nz * 8));
+  c->flux = (double*)(base + c->lay.off[LB_DOUT] + 3 * al256((size_t)(ny + 1) * nz * 8));
+  c->twd = (double2*)(base + c->lay.off[LB_TWD]);
   double* lamz_d = (double*)(base + c->lay.off[LB_LAMZ]);
 
   // ---------------- grid coefficients (Sec. 2.1 / 2.2 readings)
@@ -610,9 +670,19 @@ ns_status ns_init(ns_ctx** out, const ns_config* cfg, const ns_fields* fields, v
     if (upload_d(c, c->twx, tx) != cudaSuccess) st = NS_ERR_CUDA;
     std::vector<double> lx(nx), lz(c->nzh);
     for (int q = 0; q < nx; ++q) {
-      const int qq = q <= nx - q ? q : nx - q;
-      lx[q] = (2.0 / (c->dx * c->dx)) * (1.0 - std::cos(2.0 * PI * qq / nx));
+      if (c->bl) {  // DCT-II modes (zero gradient at x = 0 and x = Lx)
+        lx[q] = (2.0 / (c->dx * c->dx)) * (1.0 - std::cos(PI * q / nx));
+      } else {
+        const int qq = q <= nx - q ? q : nx - q;
+        lx[q] = (2.0 / (c->dx * c->dx)) * (1.0 - std::cos(2.0 * PI * qq / nx));
+      }
     }
+    std::vector<double> td(2 * nx);
+    for (int q = 0; q < nx; ++q) {
+      td[2 * q] = std::cos(PI * q / (2.0 * nx));
+      td[2 * q + 1] = -std::sin(PI * q / (2.0 * nx));
+    }
+    if (upload_d(c, c->twd, td) != cudaSuccess) st = NS_ERR_CUDA;
     for (int q = 0; q < c->nzh; ++q) lz[q] = (2.0 / (c->dz * c->dz)) * (1.0 - std::cos(2.0 * PI * q / nz));
     if (upload_d(c, lamx_d, lx) != cudaSuccess) st = NS_ERR_CUDA;
     if (upload_d(c, lamz_d, lz) != cudaSuccess) st = NS_ERR_CUDA;
@@ -627,6 +697,9 @@ ns_status ns_init(ns_ctx** out, const ns_config* cfg, const ns_fields* fields, v
     for (int b = LB_NU; b <= LB_NW; ++b)
       if (cudaMemsetAsync(base + c->lay.off[b], 0, c->lay.off[b + 1] - c->lay.off[b], c->stream) != cudaSuccess)
         st = NS_ERR_CUDA;
+    if (cudaMemsetAsync(base + c->lay.off[LB_DOUT], 0, c->lay.off[LB_DOUT + 1] - c->lay.off[LB_DOUT], c->stream) !=
+        cudaSuccess)
+      st = NS_ERR_CUDA;
     if (cudaStreamSynchronize(c->stream) != cudaSuccess) st = NS_ERR_CUDA;
   }
   if (st != NS_OK) {
@@ -682,6 +755,10 @@ ns_status ns_substep(ns_ctx* c, int k) {
 
 ns_status ns_make_divergence_free(ns_ctx* c) {
   if (!c) return NS_ERR_ARG;
+  if (c->bl) {
+    cudaError_t e = launch_flux_correct(c, -1);
+    if (e != cudaSuccess) return cuda_fail(c, e, "flux_correct");
+  }
   ns_status s = ns_poisson_solve(c, -1);
   if (s != NS_OK) return s;
   return ns_project(c, -1);

@@ -59,7 +59,7 @@ struct ns_layout {
 
 enum {
   LB_RU = 0, LB_RV, LB_RW, LB_NU, LB_NV, LB_NW, LB_PHI, LB_SPEC, LB_POIS, LB_GC, LB_XTAB, LB_YTAB,
-  LB_ZTAB, LB_TWZ, LB_TWX, LB_LAMX, LB_LAMZ, LB_RTAB, LB_COUNT
+  LB_ZTAB, LB_TWZ, LB_TWX, LB_LAMX, LB_LAMZ, LB_RTAB, LB_DOUT, LB_TWD, LB_COUNT
 };
 
 struct ns_ctx {
@@ -82,12 +82,17 @@ struct ns_ctx {
   double2* spec;
   double2* pois;
   double* gc;
-  void* xtab[3];
+  void* xtab[3][2];         // x-solver tables per sub-step: [0] u-class, [1] v/w-class (same when
+                            // periodic; differ at the inflow / outflow rows otherwise)
   void* ytab[3][2];
   void* ztab[3];
   double2* twz;
   double2* twx;
   double* rtab[3];
+  int bl;                   // inflow / convective outflow in x
+  double* dout[3];          // outflow-plane increments of the current sub-step (u, v, w)
+  double2* twd;             // exp(-i pi l / (2 nx)), l < nx: post-twiddles of the x cosine transform
+  double* flux;             // [0]: inflow flux, [1]: last outflow correction (diagnostics)
   int num_sms;
   int rhs_bps[2];           // resident blocks per SM of the tiled RHS (FP64, FP32)
   // partitioned x solver
@@ -119,11 +124,13 @@ cudaError_t launch_adi_y(ns_ctx* c, int k);
 cudaError_t launch_adi_z(ns_ctx* c, int k);
 cudaError_t launch_poisson(ns_ctx* c, int k);   // the five kernels below, in order
 cudaError_t launch_pois_divz(ns_ctx* c, int k);
-cudaError_t launch_pois_fftx_fwd(ns_ctx* c, int k);
+cudaError_t launch_pois_fftx_fwd(ns_ctx* c, int k);   // x FFT (periodic) or DCT-II (inflow / outflow)
 cudaError_t launch_pois_tdma(ns_ctx* c, int k);
 cudaError_t launch_pois_fftx_inv(ns_ctx* c, int k);
 cudaError_t launch_pois_ifftz(ns_ctx* c, int k);
 cudaError_t launch_project(ns_ctx* c, int k);
+cudaError_t launch_outflow(ns_ctx* c, int k);        // convective outflow update + increments
+cudaError_t launch_flux_correct(ns_ctx* c, int k);   // outflow volume flux := inflow flux
 cudaError_t launch_pois_factor(ns_ctx* c, const double* lamx, const double* lamz);
 cudaError_t poisson_set_attributes();  // once per process and device, outside any capture
 

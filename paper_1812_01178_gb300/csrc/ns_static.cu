@@ -152,8 +152,9 @@ extern "C" ns_status ns_poisson_solve_static(const ns_config* cfg, const double*
   if ((e = cudaStreamSynchronize(st)) != cudaSuccess)
     return fail(NS_ERR_CUDA, std::string("table upload: ") + cudaGetErrorString(e));
 
-  ns_ctx c;
+  ns_ctx c{};  // value-initialised: every member not set below is zero
   c.cfg = *cfg;
+  c.bl = 0;
   c.launch = st;
   c.stream = st;
   c.nzh = nz / 2 + 1;
