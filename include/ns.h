@@ -220,6 +220,43 @@ ns_status ns_get_buffer(ns_ctx* ctx, int which, void** ptr, size_t* bytes);
 ns_status ns_poisson_solve_static(const ns_config* cfg, const double* u, const double* v, const double* w,
                                   double* phi, int substep, void* cuda_stream);
 
+/* ---------------------------------------------------------------------------------------------
+ * Batched ensembles: n independent instances (periodic x, one precision, any sizes) advanced
+ * together.  Each stage of a sub-step is one persistent launch for the whole ensemble (per kernel
+ * variant): its blocks walk the blocks of every instance, reading each instance's arguments from a
+ * device table; one time step is one captured CUDA graph.  cfgs[i] / fields[i] describe instance
+ * i exactly as for ns_init.  The workspace (caller-owned, or library-owned if NULL) holds every
+ * instance's workspace plus the launch tables.
+ * ------------------------------------------------------------------------------------------- */
+typedef struct ns_batch ns_batch;
+
+/* Workspace bytes for the ensemble (0 if any cfg is invalid, not periodic in x, or the
+ * precisions differ). */
+size_t ns_batch_workspace_bytes(const ns_config* cfgs, int n);
+
+ns_status ns_batch_init(ns_batch** out, const ns_config* cfgs, const ns_fields* fields, int n,
+                        void* workspace, size_t ws_bytes, void* cuda_stream);
+
+/* nsteps time steps of every instance (graph captured on first use and replayed). */
+ns_status ns_batch_step(ns_batch* b, int nsteps);
+
+/* Number of kernel launches in one batched time step (3 sub-steps x stages x kernel variants). */
+int ns_batch_launches_per_step(ns_batch* b);
+
+/* Pick each instance's x partitioning by timing (ns_autotune per instance), then re-plan. */
+ns_status ns_batch_autotune(ns_batch* b);
+
+/* Set instance i's x partitioning (as ns_set_partition) and re-plan. */
+ns_status ns_batch_set_partition(ns_batch* b, int i, int P, int mode);
+
+/* The context of instance i (for its buffers, partition query or single-instance calls on the
+ * batch's stream), NULL if out of range.  Owned by the batch. */
+ns_ctx* ns_batch_instance(ns_batch* b, int i);
+
+ns_status ns_batch_sync(ns_batch* b);
+const char* ns_batch_last_error(ns_batch* b);
+void ns_batch_destroy(ns_batch* b);
+
 /* Wait for all work on the context's stream; reports asynchronous CUDA errors. */
 ns_status ns_sync(ns_ctx* ctx);
 

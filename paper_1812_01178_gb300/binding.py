@@ -26,7 +26,9 @@ STATUS_NAMES = {0: "NS_OK", 1: "NS_ERR_ARG", 2: "NS_ERR_SIZE", 3: "NS_ERR_CUDA",
 EXPORTS = ["ns_workspace_bytes", "ns_init", "ns_rhs", "ns_adi_sweep", "ns_poisson_solve", "ns_project",
            "ns_substep", "ns_step", "ns_step_profiled", "ns_kernel_count", "ns_kernel_name", "ns_step_host", "ns_make_divergence_free", "ns_set_partition",
            "ns_get_partition", "ns_autotune", "ns_get_buffer", "ns_poisson_solve_static", "ns_sync",
-           "ns_last_error", "ns_destroy"]
+           "ns_last_error", "ns_destroy", "ns_batch_workspace_bytes", "ns_batch_init", "ns_batch_step",
+           "ns_batch_launches_per_step", "ns_batch_autotune", "ns_batch_set_partition", "ns_batch_instance",
+           "ns_batch_sync", "ns_batch_last_error", "ns_batch_destroy"]
 NS_STATIC_SCRATCH_BYTES = 48 * 1024 * 1024
 
 
@@ -87,8 +89,23 @@ def lib(path: str = LIB_PATH):
     L.ns_last_error.restype = C.c_char_p
     L.ns_destroy.argtypes = [vp]
     L.ns_destroy.restype = None
+    L.ns_batch_workspace_bytes.argtypes = [P(ns_config), i]
+    L.ns_batch_workspace_bytes.restype = sz
+    L.ns_batch_init.argtypes = [P(vp), P(ns_config), P(ns_fields), i, vp, sz, vp]
+    L.ns_batch_step.argtypes = [vp, i]
+    L.ns_batch_launches_per_step.argtypes = [vp]
+    L.ns_batch_autotune.argtypes = [vp]
+    L.ns_batch_set_partition.argtypes = [vp, i, i, i]
+    L.ns_batch_instance.argtypes = [vp, i]
+    L.ns_batch_instance.restype = vp
+    L.ns_batch_sync.argtypes = [vp]
+    L.ns_batch_last_error.argtypes = [vp]
+    L.ns_batch_last_error.restype = C.c_char_p
+    L.ns_batch_destroy.argtypes = [vp]
+    L.ns_batch_destroy.restype = None
     for name in EXPORTS:
-        if name not in ("ns_workspace_bytes", "ns_last_error", "ns_destroy", "ns_kernel_name"):
+        if name not in ("ns_workspace_bytes", "ns_last_error", "ns_destroy", "ns_kernel_name",
+                        "ns_batch_workspace_bytes", "ns_batch_instance", "ns_batch_last_error", "ns_batch_destroy"):
             getattr(L, name).restype = i
     _LIB = L
     return L
@@ -320,6 +337,86 @@ class Solver:
         if getattr(self, "ctx", None) is not None:
             ns_destroy(self.ctx)
             self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Owns the device fields of n instances and one batch context (include/ns.h, ns_batch_*)."""
+
+    def __init__(self, cases, fields=None, precision=None, device="cuda:0"):
+        import torch
+        self.torch = torch
+        dev = torch.device(device)
+        self.cases = cases
+        self.n = len(cases)
+        self.cfgs = (ns_config * self.n)()
+        self._keep = []
+        self.t = []
+        flds = (ns_fields * self.n)()
+        for q, case in enumerate(cases):
+            cfg = make_config(case, precision)
+            self._keep.append(cfg)
+            self.cfgs[q] = cfg
+            nx, ny, nz = case.nx, case.ny, case.nz
+            src = fields[q] if fields is not None else (None, None, None, None)
+            ts = []
+            for a, shape in zip(src, ((nz, ny, nx), (nz, ny + 1, nx), (nz, ny, nx), (nz, ny, nx))):
+                if a is None:
+                    ts.append(torch.zeros(shape, dtype=torch.float64, device=dev))
+                else:
+                    ts.append(torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64)).to(dev).contiguous())
+            self.t.append(ts)
+            flds[q] = ns_fields(*[x.data_ptr() for x in ts], None, None, None, None, None)
+        nbytes = lib().ns_batch_workspace_bytes(self.cfgs, self.n)
+        if nbytes == 0:
+            raise NSError(NS_ERR_ARG, "invalid batch configuration")
+        self.ws = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+        self.stream = torch.cuda.current_stream(dev)
+        self.b = C.c_void_p()
+        s = lib().ns_batch_init(C.byref(self.b), self.cfgs, flds, self.n, self.ws.data_ptr(), nbytes,
+                                self.stream.cuda_stream)
+        if s != NS_OK:
+            raise NSError(s, lib().ns_last_error(None).decode())
+
+    def _chk(self, s):
+        if s != NS_OK:
+            raise NSError(s, lib().ns_batch_last_error(self.b).decode())
+
+    def step(self, n=1):
+        self._chk(lib().ns_batch_step(self.b, n))
+
+    def autotune(self):
+        self._chk(lib().ns_batch_autotune(self.b))
+
+    def set_partition(self, i, P, mode=NS_PART_AUTO):
+        self._chk(lib().ns_batch_set_partition(self.b, i, P, mode))
+
+    def launches_per_step(self):
+        return lib().ns_batch_launches_per_step(self.b)
+
+    def instance(self, i):
+        return C.c_void_p(lib().ns_batch_instance(self.b, i))
+
+    def make_divergence_free(self):
+        for q in range(self.n):
+            ns_make_divergence_free(self.instance(q))
+
+    def sync(self):
+        self._chk(lib().ns_batch_sync(self.b))
+
+    def state(self, i):
+        self.sync()
+        return tuple(x.cpu().numpy() for x in self.t[i])
+
+    def close(self):
+        if getattr(self, "b", None) is not None and self.b.value:
+            lib().ns_batch_destroy(self.b)
+            self.b = C.c_void_p()
 
     def __del__(self):
         try:

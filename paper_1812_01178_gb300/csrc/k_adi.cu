@@ -99,7 +99,15 @@ __device__ __forceinline__ void store_part(T* __restrict__ dst, const T (&d)[M])
 }
 
 template <typename T, int M>
-__global__ void __launch_bounds__(256) adi_x_kernel(AdiXArgs<T> a) {
+struct AdiXK {
+  struct Args {
+    AdiXArgs<T> a;
+  };
+  static constexpr int kThreads = 256;
+  static Args make(AdiXArgs<T> a) { return Args{a}; }
+  static __device__ __forceinline__ void run(const Args& a_, const dim3 bid_, const dim3 gdim_) {
+    const AdiXArgs<T>& a = a_.a;
+
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* st = reinterpret_cast<T*>(smem_raw);
   const int P = a.P, L = a.L;
@@ -112,8 +120,8 @@ __global__ void __launch_bounds__(256) adi_x_kernel(AdiXArgs<T> a) {
   const int r = lane & (P - 1);
   const int team = lane / P;
   const int teams = 32 / P;
-  const long warp = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const long nwarps = ((long)gridDim.x * blockDim.x) >> 5;
+  const long warp = ((long)bid_.x * blockDim.x + threadIdx.x) >> 5;
+  const long nwarps = ((long)gdim_.x * blockDim.x) >> 5;
 
   for (long l0 = warp * teams; l0 < a.nlines; l0 += nwarps * teams) {
     const long line = l0 + team;
@@ -169,7 +177,9 @@ __global__ void __launch_bounds__(256) adi_x_kernel(AdiXArgs<T> a) {
     for (int e = 0; e < M; ++e) d[e] = d[e] - SV[e * P + r] * left - SW[e * P + r] * y1;
     if (valid) store_part<T, M>(row + r * M, d);
   }
-}
+
+  }
+};
 
 // ----------------------------------------------------------------------------------------------
 // x, long lines (M = 32 or 64 rows per partition, P = 32): the same algebra with each warp's line
@@ -177,15 +187,23 @@ __global__ void __launch_bounds__(256) adi_x_kernel(AdiXArgs<T> a) {
 // per-partition tables read through L1.  One warp per line, four warps per block.
 // ----------------------------------------------------------------------------------------------
 template <typename T, int M>
-__global__ void __launch_bounds__(128) adi_x_long_kernel(AdiXArgs<T> a) {
+struct AdiXLongK {
+  struct Args {
+    AdiXArgs<T> a;
+  };
+  static constexpr int kThreads = 128;
+  static Args make(AdiXArgs<T> a) { return Args{a}; }
+  static __device__ __forceinline__ void run(const Args& a_, const dim3 bid_, const dim3 gdim_) {
+    const AdiXArgs<T>& a = a_.a;
+
   constexpr int P = 32;
   constexpr int LS = P * (M + 1);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* line_buf = reinterpret_cast<T*>(smem_raw) + (threadIdx.x >> 5) * LS;
   const int r = threadIdx.x & 31;
   const int L = a.L;
-  const long warp = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const long nwarps = ((long)gridDim.x * blockDim.x) >> 5;
+  const long warp = ((long)bid_.x * blockDim.x + threadIdx.x) >> 5;
+  const long nwarps = ((long)gdim_.x * blockDim.x) >> 5;
   T* my = line_buf + r * (M + 1);
   for (long line = warp; line < a.nlines; line += nwarps) {
     int comp;
@@ -247,18 +265,40 @@ __global__ void __launch_bounds__(128) adi_x_long_kernel(AdiXArgs<T> a) {
     }
     __syncwarp();
   }
-}
+
+  }
+};
 
 // ----------------------------------------------------------------------------------------------
 // y: one thread per line, Thomas with precomputed factors [INV, AINV, CP][n]
 // ----------------------------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(128) adi_y_kernel(T* __restrict__ ru, T* __restrict__ rv, T* __restrict__ rw,
-                                                    const T* __restrict__ tc, const T* __restrict__ tf, int nx,
-                                                    int ny, int nz) {
-  const int comp = blockIdx.z;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int k = blockIdx.y;
+struct AdiYK {
+  struct Args {
+    T* ru;
+    T* rv;
+    T* rw;
+    const T* tc;
+    const T* tf;
+    int nx;
+    int ny;
+    int nz;
+  };
+  static constexpr int kThreads = 128;
+  static Args make(T* ru, T* rv, T* rw, const T* tc, const T* tf, int nx, int ny, int nz) { return Args{ru, rv, rw, tc, tf, nx, ny, nz}; }
+  static __device__ __forceinline__ void run(const Args& a_, const dim3 bid_, const dim3 gdim_) {
+    T* __restrict__ ru = a_.ru;
+    T* __restrict__ rv = a_.rv;
+    T* __restrict__ rw = a_.rw;
+    const T* __restrict__ tc = a_.tc;
+    const T* __restrict__ tf = a_.tf;
+    int nx = a_.nx;
+    int ny = a_.ny;
+    int nz = a_.nz;
+
+  const int comp = bid_.z;
+  const int i = bid_.x * blockDim.x + threadIdx.x;
+  const int k = bid_.y;
   if (i >= nx) return;
   T* line;
   const T* tab;
@@ -288,20 +328,45 @@ __global__ void __launch_bounds__(128) adi_y_kernel(T* __restrict__ ru, T* __res
     next = line[o] - __ldg(CP + j) * next;
     line[o] = next;
   }
-}
+
+  }
+};
 
 // ----------------------------------------------------------------------------------------------
 // z: one thread per line, cyclic (Sherman-Morrison), then u* = u + delta.
 // table: [INV, AINV, CP, Q][nz] then (FAC, BG)
 // ----------------------------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(128) adi_z_kernel(T* __restrict__ ru, T* __restrict__ rv, T* __restrict__ rw,
-                                                    double* __restrict__ u, double* __restrict__ v,
-                                                    double* __restrict__ w, const T* __restrict__ tab, int nx,
-                                                    int ny, int nz) {
-  const int comp = blockIdx.z;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y + (comp == 1 ? 1 : 0);
+struct AdiZK {
+  struct Args {
+    T* ru;
+    T* rv;
+    T* rw;
+    double* u;
+    double* v;
+    double* w;
+    const T* tab;
+    int nx;
+    int ny;
+    int nz;
+  };
+  static constexpr int kThreads = 128;
+  static Args make(T* ru, T* rv, T* rw, double* u, double* v, double* w, const T* tab, int nx, int ny, int nz) { return Args{ru, rv, rw, u, v, w, tab, nx, ny, nz}; }
+  static __device__ __forceinline__ void run(const Args& a_, const dim3 bid_, const dim3 gdim_) {
+    T* __restrict__ ru = a_.ru;
+    T* __restrict__ rv = a_.rv;
+    T* __restrict__ rw = a_.rw;
+    double* __restrict__ u = a_.u;
+    double* __restrict__ v = a_.v;
+    double* __restrict__ w = a_.w;
+    const T* __restrict__ tab = a_.tab;
+    int nx = a_.nx;
+    int ny = a_.ny;
+    int nz = a_.nz;
+
+  const int comp = bid_.z;
+  const int i = bid_.x * blockDim.x + threadIdx.x;
+  const int j = bid_.y + (comp == 1 ? 1 : 0);
   if (i >= nx) return;
   if (comp == 1 && j > ny - 1) return;
   const int rows = comp == 1 ? ny + 1 : ny;
@@ -335,7 +400,9 @@ __global__ void __launch_bounds__(128) adi_z_kernel(T* __restrict__ ru, T* __res
     const T x = line[o] - corr * __ldg(Q + kk);
     f[o] = f[o] + (double)x;
   }
-}
+
+  }
+};
 
 template <typename T>
 void fill_x_args(ns_ctx* c, int k, AdiXArgs<T>& a) {
@@ -351,7 +418,8 @@ void fill_x_args(ns_ctx* c, int k, AdiXArgs<T>& a) {
 }
 
 template <typename T, int M>
-cudaError_t launch_x_t(ns_ctx* c, int k) {
+cudaError_t launch_x_t(LaunchSink& s, int k) {
+  ns_ctx* c = s.c;
   AdiXArgs<T> a;
   fill_x_args(c, k, a);
   a.r[0] = (T*)c->ru;
@@ -367,12 +435,12 @@ cudaError_t launch_x_t(ns_ctx* c, int k) {
   const long teams_per_block = 8L * (32 / a.P);
   long blocks = (a.nlines + teams_per_block - 1) / teams_per_block;
   if (blocks > 152L * 16) blocks = 152L * 16;
-  adi_x_kernel<T, M><<<(unsigned)blocks, 256, smem, c->launch>>>(a);
-  return cudaGetLastError();
+  return emit<AdiXK<T, M>>(s, AdiXK<T, M>::make(a), dim3((unsigned)blocks), dim3(256), smem);
 }
 
 template <typename T, int M>
-cudaError_t launch_x_long_t(ns_ctx* c, int k) {
+cudaError_t launch_x_long_t(LaunchSink& s, int k) {
+  ns_ctx* c = s.c;
   AdiXArgs<T> a;
   fill_x_args(c, k, a);
   a.r[0] = (T*)c->ru;
@@ -387,60 +455,74 @@ cudaError_t launch_x_long_t(ns_ctx* c, int k) {
   const size_t smem = (size_t)4 * 32 * (M + 1) * sizeof(T);
   long blocks = (a.nlines + 3) / 4;
   if (blocks > 152L * 16) blocks = 152L * 16;
-  adi_x_long_kernel<T, M><<<(unsigned)blocks, 128, smem, c->launch>>>(a);
-  return cudaGetLastError();
+  return emit<AdiXLongK<T, M>>(s, AdiXLongK<T, M>::make(a), dim3((unsigned)blocks), dim3(128), smem);
 }
 
 template <typename T>
-cudaError_t launch_x_m(ns_ctx* c, int k) {
-  if (c->P == 32 && c->M == 32) return launch_x_long_t<T, 32>(c, k);
-  if (c->P == 32 && c->M == 64) return launch_x_long_t<T, 64>(c, k);
+cudaError_t launch_x_m(LaunchSink& s, int k) {
+  ns_ctx* c = s.c;
+  if (c->P == 32 && c->M == 32) return launch_x_long_t<T, 32>(s, k);
+  if (c->P == 32 && c->M == 64) return launch_x_long_t<T, 64>(s, k);
   switch (c->M) {
-    case 1: return launch_x_t<T, 1>(c, k);
-    case 2: return launch_x_t<T, 2>(c, k);
-    case 4: return launch_x_t<T, 4>(c, k);
-    case 8: return launch_x_t<T, 8>(c, k);
-    case 16: return launch_x_t<T, 16>(c, k);
+    case 1: return launch_x_t<T, 1>(s, k);
+    case 2: return launch_x_t<T, 2>(s, k);
+    case 4: return launch_x_t<T, 4>(s, k);
+    case 8: return launch_x_t<T, 8>(s, k);
+    case 16: return launch_x_t<T, 16>(s, k);
     default: return cudaErrorInvalidValue;
   }
 }
 
 }  // namespace
 
-cudaError_t launch_adi_x(ns_ctx* c, int k) {
-  if (c->cfg.precision == NS_MIXED) return launch_x_m<float>(c, k);
-  return launch_x_m<double>(c, k);
+cudaError_t stage_adi_x(LaunchSink& s, int k) {
+  if (s.c->cfg.precision == NS_MIXED) return launch_x_m<float>(s, k);
+  return launch_x_m<double>(s, k);
 }
 
-cudaError_t launch_adi_y(ns_ctx* c, int k) {
+cudaError_t stage_adi_y(LaunchSink& s, int k) {
+  ns_ctx* c = s.c;
   const int nx = c->cfg.nx, ny = c->cfg.ny, nz = c->cfg.nz;
   dim3 grid((nx + 127) / 128, nz, 3);
   if (c->cfg.precision == NS_MIXED)
-    adi_y_kernel<float><<<grid, 128, 0, c->launch>>>((float*)c->ru, (float*)c->rv, (float*)c->rw,
-                                                     (const float*)c->ytab[k][0], (const float*)c->ytab[k][1], nx,
-                                                     ny, nz);
-  else
-    adi_y_kernel<double><<<grid, 128, 0, c->launch>>>((double*)c->ru, (double*)c->rv, (double*)c->rw,
-                                                      (const double*)c->ytab[k][0], (const double*)c->ytab[k][1],
-                                                      nx, ny, nz);
-  return cudaGetLastError();
+    return emit<AdiYK<float>>(s, AdiYK<float>::make((float*)c->ru, (float*)c->rv, (float*)c->rw,
+                                                    (const float*)c->ytab[k][0], (const float*)c->ytab[k][1], nx,
+                                                    ny, nz), grid, 128, 0);
+  return emit<AdiYK<double>>(s, AdiYK<double>::make((double*)c->ru, (double*)c->rv, (double*)c->rw,
+                                                    (const double*)c->ytab[k][0], (const double*)c->ytab[k][1],
+                                                    nx, ny, nz), grid, 128, 0);
 }
 
-cudaError_t launch_adi_z(ns_ctx* c, int k) {
+cudaError_t stage_adi_z(LaunchSink& s, int k) {
+  ns_ctx* c = s.c;
   const int nx = c->cfg.nx, ny = c->cfg.ny, nz = c->cfg.nz;
   dim3 grid((nx + 127) / 128, ny, 3);
   if (c->cfg.precision == NS_MIXED)
-    adi_z_kernel<float><<<grid, 128, 0, c->launch>>>((float*)c->ru, (float*)c->rv, (float*)c->rw, c->f.u, c->f.v,
-                                                     c->f.w, (const float*)c->ztab[k], nx, ny, nz);
-  else
-    adi_z_kernel<double><<<grid, 128, 0, c->launch>>>((double*)c->ru, (double*)c->rv, (double*)c->rw, c->f.u,
-                                                      c->f.v, c->f.w, (const double*)c->ztab[k], nx, ny, nz);
-  return cudaGetLastError();
+    return emit<AdiZK<float>>(s, AdiZK<float>::make((float*)c->ru, (float*)c->rv, (float*)c->rw, c->f.u, c->f.v,
+                                                    c->f.w, (const float*)c->ztab[k], nx, ny, nz), grid, 128, 0);
+  return emit<AdiZK<double>>(s, AdiZK<double>::make((double*)c->ru, (double*)c->rv, (double*)c->rw, c->f.u,
+                                                    c->f.v, c->f.w, (const double*)c->ztab[k], nx, ny, nz),
+                             grid, 128, 0);
+}
+
+cudaError_t launch_adi_x(ns_ctx* c, int k) {
+  LaunchSink s{c, nullptr};
+  return stage_adi_x(s, k);
+}
+
+cudaError_t launch_adi_y(ns_ctx* c, int k) {
+  LaunchSink s{c, nullptr};
+  return stage_adi_y(s, k);
+}
+
+cudaError_t launch_adi_z(ns_ctx* c, int k) {
+  LaunchSink s{c, nullptr};
+  return stage_adi_z(s, k);
 }
 
 template <typename T, int M>
 cudaError_t short_attr() {
-  return cudaFuncSetAttribute(adi_x_kernel<T, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 48 * 1024);
+  return set_smem_limit<AdiXK<T, M>>(2 * 48 * 1024);
 }
 
 cudaError_t adi_set_attributes() {
@@ -451,17 +533,13 @@ cudaError_t adi_set_attributes() {
       (e = short_attr<float, 2>()) != cudaSuccess || (e = short_attr<float, 4>()) != cudaSuccess ||
       (e = short_attr<float, 8>()) != cudaSuccess || (e = short_attr<float, 16>()) != cudaSuccess)
     return e;
-  if ((e = cudaFuncSetAttribute(adi_x_long_kernel<double, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                4 * 32 * 65 * 8)) != cudaSuccess)
+  if ((e = set_smem_limit<AdiXLongK<double, 64>>(4 * 32 * 65 * 8)) != cudaSuccess)
     return e;
-  if ((e = cudaFuncSetAttribute(adi_x_long_kernel<double, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                4 * 32 * 33 * 8)) != cudaSuccess)
+  if ((e = set_smem_limit<AdiXLongK<double, 32>>(4 * 32 * 33 * 8)) != cudaSuccess)
     return e;
-  if ((e = cudaFuncSetAttribute(adi_x_long_kernel<float, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                4 * 32 * 65 * 4)) != cudaSuccess)
+  if ((e = set_smem_limit<AdiXLongK<float, 64>>(4 * 32 * 65 * 4)) != cudaSuccess)
     return e;
-  return cudaFuncSetAttribute(adi_x_long_kernel<float, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              4 * 32 * 33 * 4);
+  return set_smem_limit<AdiXLongK<float, 32>>(4 * 32 * 33 * 4);
 }
 
 size_t adi_y_tab_count(int ny) { return 3 * (size_t)ny; }

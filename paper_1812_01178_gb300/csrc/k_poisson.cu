@@ -64,17 +64,49 @@ __device__ double2* stockham(double2* A, double2* B, int N, int LN, int nseq, co
 // ------------------------------------------------------------------------------------------
 // divergence + forward z FFT.  Block = (x-tile of TX columns, row j).  Output spec[kz][j][i].
 // ------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) div_fftz_kernel(const double* __restrict__ u, const double* __restrict__ v,
-                                                       const double* __restrict__ w, const double* __restrict__ gc,
-                                                       const double2* __restrict__ twz, double2* __restrict__ spec,
-                                                       int nx, int ny, int nz, int lnz, int TX, double idx,
-                                                       double idz, double scale, const double* __restrict__ u_out) {
+struct DivzK {
+  struct Args {
+    const double* u;
+    const double* v;
+    const double* w;
+    const double* gc;
+    const double2* twz;
+    double2* spec;
+    int nx;
+    int ny;
+    int nz;
+    int lnz;
+    int TX;
+    double idx;
+    double idz;
+    double scale;
+    const double* u_out;
+  };
+  static constexpr int kThreads = 256;
+  static Args make(const double* u, const double* v, const double* w, const double* gc, const double2* twz, double2* spec, int nx, int ny, int nz, int lnz, int TX, double idx, double idz, double scale, const double* u_out) { return Args{u, v, w, gc, twz, spec, nx, ny, nz, lnz, TX, idx, idz, scale, u_out}; }
+  static __device__ __forceinline__ void run(const Args& a_, const dim3 bid_, const dim3 gdim_) {
+    const double* __restrict__ u = a_.u;
+    const double* __restrict__ v = a_.v;
+    const double* __restrict__ w = a_.w;
+    const double* __restrict__ gc = a_.gc;
+    const double2* __restrict__ twz = a_.twz;
+    double2* __restrict__ spec = a_.spec;
+    int nx = a_.nx;
+    int ny = a_.ny;
+    int nz = a_.nz;
+    int lnz = a_.lnz;
+    int TX = a_.TX;
+    double idx = a_.idx;
+    double idz = a_.idz;
+    double scale = a_.scale;
+    const double* __restrict__ u_out = a_.u_out;
+
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int nseq = TX >> 1;
   double2* A = reinterpret_cast<double2*>(smem_raw);
   double2* B = A + nseq * nz;
-  const int i0 = blockIdx.x * TX;
-  const int j = blockIdx.y;
+  const int i0 = bid_.x * TX;
+  const int j = bid_.y;
   const double idy = __ldg(gc + GC_IDY * (ny + 1) + j) * scale;
   idx *= scale;
   idz *= scale;
@@ -112,18 +144,39 @@ __global__ void __launch_bounds__(256) div_fftz_kernel(const double* __restrict_
       X = make_double2(0.5 * (zm.y + zn.y), 0.5 * (zn.x - zm.x));
     spec[((long)m * ny + j) * nx + i0 + il] = X;
   }
-}
+
+  }
+};
 
 // ------------------------------------------------------------------------------------------
 // complex FFT along x of R rows per block (rows are contiguous, length nx), in place.
 // ------------------------------------------------------------------------------------------
 template <int SIGN>
-__global__ void __launch_bounds__(256) fftx_kernel(double2* __restrict__ spec, const double2* __restrict__ twx,
-                                                   long nrows, int nx, int lnx, int R, double scale) {
+struct FftxK {
+  struct Args {
+    double2* spec;
+    const double2* twx;
+    long nrows;
+    int nx;
+    int lnx;
+    int R;
+    double scale;
+  };
+  static constexpr int kThreads = 256;
+  static Args make(double2* spec, const double2* twx, long nrows, int nx, int lnx, int R, double scale) { return Args{spec, twx, nrows, nx, lnx, R, scale}; }
+  static __device__ __forceinline__ void run(const Args& a_, const dim3 bid_, const dim3 gdim_) {
+    double2* __restrict__ spec = a_.spec;
+    const double2* __restrict__ twx = a_.twx;
+    long nrows = a_.nrows;
+    int nx = a_.nx;
+    int lnx = a_.lnx;
+    int R = a_.R;
+    double scale = a_.scale;
+
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double2* A = reinterpret_cast<double2*>(smem_raw);
   double2* B = A + R * nx;
-  const long row0 = (long)blockIdx.x * R;
+  const long row0 = (long)bid_.x * R;
   const int nr = (int)min((long)R, nrows - row0);
   double2* g = spec + row0 * nx;
   for (int q = threadIdx.x; q < nr * nx; q += blockDim.x) A[q] = g[q];
@@ -138,15 +191,32 @@ __global__ void __launch_bounds__(256) fftx_kernel(double2* __restrict__ spec, c
       g[q] = make_double2(t.x * scale, t.y * scale);
     }
   }
-}
+
+  }
+};
 
 // ------------------------------------------------------------------------------------------
 // y tridiagonal per (kx, kz), one thread per line, factors (1/pivot, c/pivot) precomputed.
 // ------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(128) tdma_y_kernel(double2* __restrict__ spec, const double2* __restrict__ fac,
-                                                     const double* __restrict__ gc, int nx, int ny) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int kz = blockIdx.y;
+struct TdmaK {
+  struct Args {
+    double2* spec;
+    const double2* fac;
+    const double* gc;
+    int nx;
+    int ny;
+  };
+  static constexpr int kThreads = 128;
+  static Args make(double2* spec, const double2* fac, const double* gc, int nx, int ny) { return Args{spec, fac, gc, nx, ny}; }
+  static __device__ __forceinline__ void run(const Args& a_, const dim3 bid_, const dim3 gdim_) {
+    double2* __restrict__ spec = a_.spec;
+    const double2* __restrict__ fac = a_.fac;
+    const double* __restrict__ gc = a_.gc;
+    int nx = a_.nx;
+    int ny = a_.ny;
+
+  const int i = bid_.x * blockDim.x + threadIdx.x;
+  const int kz = bid_.y;
   if (i >= nx) return;
   const long base = (long)kz * ny * nx + i;
   double2* d = spec + base;
@@ -174,20 +244,44 @@ __global__ void __launch_bounds__(128) tdma_y_kernel(double2* __restrict__ spec,
     next = make_double2(fma(-cp, next.x, dj.x), fma(-cp, next.y, dj.y));
     d[o] = next;
   }
-}
+
+  }
+};
 
 // ------------------------------------------------------------------------------------------
 // inverse z FFT (complex-to-real on the half spectrum) -> phi.  Block = (x-tile, row j).
 // ------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) ifftz_kernel(const double2* __restrict__ spec, const double2* __restrict__ twz,
-                                                    double* __restrict__ phi, int nx, int ny, int nz, int lnz,
-                                                    int TX, double scale) {
+struct IfftzK {
+  struct Args {
+    const double2* spec;
+    const double2* twz;
+    double* phi;
+    int nx;
+    int ny;
+    int nz;
+    int lnz;
+    int TX;
+    double scale;
+  };
+  static constexpr int kThreads = 256;
+  static Args make(const double2* spec, const double2* twz, double* phi, int nx, int ny, int nz, int lnz, int TX, double scale) { return Args{spec, twz, phi, nx, ny, nz, lnz, TX, scale}; }
+  static __device__ __forceinline__ void run(const Args& a_, const dim3 bid_, const dim3 gdim_) {
+    const double2* __restrict__ spec = a_.spec;
+    const double2* __restrict__ twz = a_.twz;
+    double* __restrict__ phi = a_.phi;
+    int nx = a_.nx;
+    int ny = a_.ny;
+    int nz = a_.nz;
+    int lnz = a_.lnz;
+    int TX = a_.TX;
+    double scale = a_.scale;
+
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int nseq = TX >> 1;
   double2* A = reinterpret_cast<double2*>(smem_raw);
   double2* B = A + nseq * nz;
-  const int i0 = blockIdx.x * TX;
-  const int j = blockIdx.y;
+  const int i0 = bid_.x * TX;
+  const int j = bid_.y;
   const int nh = nz >> 1;
   // Z[m] = Xa[m] + i Xb[m] (m <= nz/2), Z[nz-m] = conj(Xa[m]) + i conj(Xb[m]); the m = 0 and
   // m = nz/2 coefficients of a real sequence are real, so only their real parts are used.
@@ -214,23 +308,55 @@ __global__ void __launch_bounds__(256) ifftz_kernel(const double2* __restrict__ 
     const double val = (il & 1) ? t.y : t.x;
     phi[k * pl + (long)j * nx + i0 + il] = (scale == 1.0) ? val : val * scale;
   }
-}
+
+  }
+};
 
 // ------------------------------------------------------------------------------------------
 // projection u = u* - s G phi; p += phi (if update_p).  One thread per (i, j) of a z-plane,
 // j = 0..ny.
 // ------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(128) project_kernel(double* __restrict__ u, double* __restrict__ v,
-                                                      double* __restrict__ w, double* __restrict__ p,
-                                                      const double* __restrict__ phi, const double* __restrict__ gc,
-                                                      int nx, int ny, int nz, double sx, double sz, int update_p,
-                                                      double s, int bl) {
+struct ProjectK {
+  struct Args {
+    double* u;
+    double* v;
+    double* w;
+    double* p;
+    const double* phi;
+    const double* gc;
+    int nx;
+    int ny;
+    int nz;
+    double sx;
+    double sz;
+    int update_p;
+    double s;
+    int bl;
+  };
+  static constexpr int kThreads = 128;
+  static Args make(double* u, double* v, double* w, double* p, const double* phi, const double* gc, int nx, int ny, int nz, double sx, double sz, int update_p, double s, int bl) { return Args{u, v, w, p, phi, gc, nx, ny, nz, sx, sz, update_p, s, bl}; }
+  static __device__ __forceinline__ void run(const Args& a_, const dim3 bid_, const dim3 gdim_) {
+    double* __restrict__ u = a_.u;
+    double* __restrict__ v = a_.v;
+    double* __restrict__ w = a_.w;
+    double* __restrict__ p = a_.p;
+    const double* __restrict__ phi = a_.phi;
+    const double* __restrict__ gc = a_.gc;
+    int nx = a_.nx;
+    int ny = a_.ny;
+    int nz = a_.nz;
+    double sx = a_.sx;
+    double sz = a_.sz;
+    int update_p = a_.update_p;
+    double s = a_.s;
+    int bl = a_.bl;
+
   const long plane = (long)nx * (ny + 1);
-  const long q = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long q = (long)bid_.x * blockDim.x + threadIdx.x;
   if (q >= plane) return;
   const int j = (int)(q / nx);
   const int i = (int)(q - (long)j * nx);
-  const int k = blockIdx.y;
+  const int k = bid_.y;
   const int im = (i == 0) ? nx - 1 : i - 1;
   const int km = (k == 0) ? nz - 1 : k - 1;
   const long pl = (long)ny * nx;
@@ -246,7 +372,9 @@ __global__ void __launch_bounds__(128) project_kernel(double* __restrict__ u, do
     const long cc = k * pl + (long)j * nx + i;
     v[(long)k * (ny + 1) * nx + (long)j * nx + i] -= s * ihc * (__ldg(phi + cc) - __ldg(phi + cc - nx));
   }
-}
+
+  }
+};
 
 // ------------------------------------------------------------------------------------------
 // cosine transform along x (inflow / outflow): DCT-II  X_l = sum_i x_i cos(pi l (2i+1) / (2N)) of
@@ -412,10 +540,10 @@ int ilog2(int n) {
 }  // namespace
 
 cudaError_t poisson_set_attributes() {
-  cudaFuncSetAttribute(div_fftz_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  cudaFuncSetAttribute(ifftz_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  cudaFuncSetAttribute(fftx_kernel<-1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  cudaFuncSetAttribute(fftx_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  set_smem_limit<DivzK>(200 * 1024);
+  set_smem_limit<IfftzK>(200 * 1024);
+  set_smem_limit<FftxK<-1>>(200 * 1024);
+  set_smem_limit<FftxK<1>>(200 * 1024);
   cudaFuncSetAttribute(dctx_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   cudaFuncSetAttribute(dctx_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   return cudaGetLastError();
@@ -457,56 +585,88 @@ PoisShape pois_shape(const ns_ctx* c) {
   q.bx = (unsigned)((q.nrows + q.R - 1) / q.R);
   return q;
 }
+void single_kernel_dct_fwd(ns_ctx* c, unsigned bx, size_t smx, long nrows, int nx, int lnx, int R) {
+  dctx_fwd_kernel<<<bx, 256, smx, c->launch>>>(c->spec, c->twx, c->twd, nrows, nx, lnx, R);
+}
+void single_kernel_dct_inv(ns_ctx* c, unsigned bx, size_t smx, long nrows, int nx, int lnx, int R) {
+  dctx_inv_kernel<<<bx, 256, smx, c->launch>>>(c->spec, c->twx, c->twd, nrows, nx, lnx, R);
+}
 }  // namespace
 
 // A5: divergence of u* scaled by 1/(alpha_k dt) (1 if k < 0) + forward real FFT along z
-cudaError_t launch_pois_divz(ns_ctx* c, int k) {
+cudaError_t stage_pois_divz(LaunchSink& s, int k) {
+  ns_ctx* c = s.c;
   const PoisShape q = pois_shape(c);
   // 1/(alpha_k dt) of the right-hand side and 1/(nx nz) of the inverse transforms, applied once
   const double scale = ((k >= 0) ? 1.0 / (NS_ALPHA[k] * c->cfg.dt) : 1.0) / ((double)q.nx * q.nz);
-  div_fftz_kernel<<<dim3(q.nx / q.TX, q.ny), 256, q.smz, c->launch>>>(c->f.u, c->f.v, c->f.w, c->gc, c->twz,
-                                                                     c->spec, q.nx, q.ny, q.nz, q.lnz, q.TX,
-                                                                     1.0 / c->dx, 1.0 / c->dz, scale,
-                                                                     c->bl ? c->f.u_out : nullptr);
-  return cudaGetLastError();
+  return emit<DivzK>(s, DivzK::make(c->f.u, c->f.v, c->f.w, c->gc, c->twz, c->spec, q.nx, q.ny, q.nz, q.lnz, q.TX,
+                                    1.0 / c->dx, 1.0 / c->dz, scale, c->bl ? c->f.u_out : nullptr),
+                     dim3(q.nx / q.TX, q.ny), dim3(256), q.smz);
 }
 
-// A6: forward complex FFT along x
-cudaError_t launch_pois_fftx_fwd(ns_ctx* c, int) {
+// A6: forward complex FFT along x (periodic) or DCT-II (inflow / outflow; single instance only)
+cudaError_t stage_pois_x_fwd(LaunchSink& s, int) {
+  ns_ctx* c = s.c;
   const PoisShape q = pois_shape(c);
   if (c->bl) {
-    dctx_fwd_kernel<<<q.bx, 256, q.smx, c->launch>>>(c->spec, c->twx, c->twd, q.nrows, q.nx, q.lnx, q.R);
+    single_kernel_dct_fwd(c, q.bx, q.smx, q.nrows, q.nx, q.lnx, q.R);
     return cudaGetLastError();
   }
-  fftx_kernel<-1><<<q.bx, 256, q.smx, c->launch>>>(c->spec, c->twx, q.nrows, q.nx, q.lnx, q.R, 1.0);
-  return cudaGetLastError();
+  return emit<FftxK<-1>>(s, FftxK<-1>::make(c->spec, c->twx, q.nrows, q.nx, q.lnx, q.R, 1.0), dim3(q.bx), dim3(256),
+                         q.smx);
 }
 
 // A7: complex tridiagonal solve along y per (kx, kz)
-cudaError_t launch_pois_tdma(ns_ctx* c, int) {
+cudaError_t stage_pois_tdma(LaunchSink& s, int) {
+  ns_ctx* c = s.c;
   const PoisShape q = pois_shape(c);
-  tdma_y_kernel<<<dim3((q.nx + 127) / 128, c->nzh), 128, 0, c->launch>>>(c->spec, c->pois, c->gc, q.nx, q.ny);
-  return cudaGetLastError();
+  return emit<TdmaK>(s, TdmaK::make(c->spec, c->pois, c->gc, q.nx, q.ny), dim3((q.nx + 127) / 128, c->nzh), dim3(128), 0);
 }
 
-// A8: inverse complex FFT along x, scaled by 1/(nx nz)
-cudaError_t launch_pois_fftx_inv(ns_ctx* c, int) {
+// A8: inverse complex FFT along x (the 1/(nx nz) was applied to the right-hand side)
+cudaError_t stage_pois_x_inv(LaunchSink& s, int) {
+  ns_ctx* c = s.c;
   const PoisShape q = pois_shape(c);
   if (c->bl) {
-    dctx_inv_kernel<<<q.bx, 256, q.smx, c->launch>>>(c->spec, c->twx, c->twd, q.nrows, q.nx, q.lnx, q.R);
+    single_kernel_dct_inv(c, q.bx, q.smx, q.nrows, q.nx, q.lnx, q.R);
     return cudaGetLastError();
   }
-  fftx_kernel<1><<<q.bx, 256, q.smx, c->launch>>>(c->spec, c->twx, q.nrows, q.nx, q.lnx, q.R, 1.0);
-  return cudaGetLastError();
+  return emit<FftxK<1>>(s, FftxK<1>::make(c->spec, c->twx, q.nrows, q.nx, q.lnx, q.R, 1.0), dim3(q.bx), dim3(256),
+                        q.smx);
 }
 
 // A9: inverse real FFT along z -> phi
-cudaError_t launch_pois_ifftz(ns_ctx* c, int) {
+cudaError_t stage_pois_ifftz(LaunchSink& s, int) {
+  ns_ctx* c = s.c;
   const PoisShape q = pois_shape(c);
-  ifftz_kernel<<<dim3(q.nx / q.TX, q.ny), 256, q.smz, c->launch>>>(c->spec, c->twz, c->phi, q.nx, q.ny, q.nz,
-                                                                  q.lnz, q.TX, 1.0);
-  return cudaGetLastError();
+  return emit<IfftzK>(s, IfftzK::make(c->spec, c->twz, c->phi, q.nx, q.ny, q.nz, q.lnz, q.TX, 1.0),
+                      dim3(q.nx / q.TX, q.ny), dim3(256), q.smz);
 }
+
+// A10: projection u = u* - alpha_k dt G phi, p += phi
+cudaError_t stage_project(LaunchSink& s, int k) {
+  ns_ctx* c = s.c;
+  const int nx = c->cfg.nx, ny = c->cfg.ny, nz = c->cfg.nz;
+  const double sc = (k >= 0) ? NS_ALPHA[k] * c->cfg.dt : 1.0;
+  const long plane = (long)nx * (ny + 1);
+  dim3 grid((unsigned)((plane + 127) / 128), nz);
+  return emit<ProjectK>(s, ProjectK::make(c->f.u, c->f.v, c->f.w, c->f.p, c->phi, c->gc, nx, ny, nz, sc / c->dx,
+                                          sc / c->dz, k >= 0 ? 1 : 0, sc, c->bl),
+                        grid, dim3(128), 0);
+}
+
+#define NS_SINGLE_LAUNCH(name, stage)   \
+  cudaError_t name(ns_ctx* c, int k) {  \
+    LaunchSink s{c, nullptr};           \
+    return stage(s, k);                 \
+  }
+NS_SINGLE_LAUNCH(launch_pois_divz, stage_pois_divz)
+NS_SINGLE_LAUNCH(launch_pois_fftx_fwd, stage_pois_x_fwd)
+NS_SINGLE_LAUNCH(launch_pois_tdma, stage_pois_tdma)
+NS_SINGLE_LAUNCH(launch_pois_fftx_inv, stage_pois_x_inv)
+NS_SINGLE_LAUNCH(launch_pois_ifftz, stage_pois_ifftz)
+NS_SINGLE_LAUNCH(launch_project, stage_project)
+#undef NS_SINGLE_LAUNCH
 
 cudaError_t launch_poisson(ns_ctx* c, int k) {
   cudaError_t e;
@@ -515,16 +675,6 @@ cudaError_t launch_poisson(ns_ctx* c, int k) {
   if ((e = launch_pois_tdma(c, k)) != cudaSuccess) return e;
   if ((e = launch_pois_fftx_inv(c, k)) != cudaSuccess) return e;
   return launch_pois_ifftz(c, k);
-}
-
-cudaError_t launch_project(ns_ctx* c, int k) {
-  const int nx = c->cfg.nx, ny = c->cfg.ny, nz = c->cfg.nz;
-  const double s = (k >= 0) ? NS_ALPHA[k] * c->cfg.dt : 1.0;
-  const long plane = (long)nx * (ny + 1);
-  dim3 grid((unsigned)((plane + 127) / 128), nz);
-  project_kernel<<<grid, 128, 0, c->launch>>>(c->f.u, c->f.v, c->f.w, c->f.p, c->phi, c->gc, nx, ny, nz, s / c->dx,
-                                              s / c->dz, k >= 0 ? 1 : 0, s, c->bl);
-  return cudaGetLastError();
 }
 
 cudaError_t launch_outflow(ns_ctx* c, int k) {

@@ -38,14 +38,22 @@ struct RhsArgs {
 };
 
 template <typename T, typename TR>
-__global__ void __launch_bounds__(128) rhs_kernel(RhsArgs a) {
+struct RhsK {
+  struct Args {
+    RhsArgs a;
+  };
+  static constexpr int kThreads = 128;
+  static Args make(RhsArgs a) { return Args{a}; }
+  static __device__ __forceinline__ void run(const Args& a_, const dim3 bid_, const dim3 gdim_) {
+    const RhsArgs& a = a_.a;
+
   const int nx = a.nx, ny = a.ny, nz = a.nz;
   const long plane = (long)nx * (ny + 1);
-  const long q = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long q = (long)bid_.x * blockDim.x + threadIdx.x;
   if (q >= plane) return;
   const int j = (int)(q / nx);
   const int i = (int)(q - (long)j * nx);
-  const int k = blockIdx.y;
+  const int k = bid_.y;
   const int ip = (i + 1 == nx) ? 0 : i + 1;
   const int im = (i == 0) ? nx - 1 : i - 1;
   const int kp = (k + 1 == nz) ? 0 : k + 1;
@@ -180,7 +188,9 @@ __global__ void __launch_bounds__(128) rhs_kernel(RhsArgs a) {
     rv[cf] = (TR)(dt * r);
     nv[cf] = (TR)n;
   }
-}
+
+  }
+};
 
 // ---------------------------------------------------------------------------------------------
 // Tiled form of the same right-hand side.  A block of TX x TZ threads owns a TX (x) by TZ (z)
@@ -212,13 +222,23 @@ struct RhsTile {
 };
 
 template <typename T, typename TR>
-__global__ void __launch_bounds__(RT_X * RT_Z) rhs_tiled_kernel(RhsArgs a, int jchunk) {
+struct RhsTiledK {
+  struct Args {
+    RhsArgs a;
+    int jchunk;
+  };
+  static constexpr int kThreads = RT_X * RT_Z;
+  static Args make(RhsArgs a, int jchunk) { return Args{a, jchunk}; }
+  static __device__ __forceinline__ void run(const Args& a_, const dim3 bid_, const dim3 gdim_) {
+    const RhsArgs& a = a_.a;
+    int jchunk = a_.jchunk;
+
   extern __shared__ __align__(16) unsigned char smem_raw[];
   RhsTile<T>& S = *reinterpret_cast<RhsTile<T>*>(smem_raw);
   const int nx = a.nx, ny = a.ny, nz = a.nz, ny1 = ny + 1, G = ny + 1;
   const int tx = threadIdx.x, tz = threadIdx.y, tid = tz * RT_X + tx;
-  const int i0 = blockIdx.x * RT_X, k0 = blockIdx.y * RT_Z;
-  const int jb = blockIdx.z * jchunk;
+  const int i0 = bid_.x * RT_X, k0 = bid_.y * RT_Z;
+  const int jb = bid_.z * jchunk;
   const int je = min(jb + jchunk, ny);
   const int jlast = (je == ny) ? ny : je - 1;  // v rows: the last chunk also writes face ny
 
@@ -389,25 +409,31 @@ __global__ void __launch_bounds__(RT_X * RT_Z) rhs_tiled_kernel(RhsArgs a, int j
       }
     }
   }
-}
+
+  }
+};
 
 }  // namespace
 
 cudaError_t rhs_set_attributes(int* bps_fp64, int* bps_fp32) {
-  cudaError_t e = cudaFuncSetAttribute(rhs_tiled_kernel<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)sizeof(RhsTile<double>));
+  cudaError_t e = set_smem_limit<RhsTiledK<double, double>>((int)sizeof(RhsTile<double>));
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(rhs_tiled_kernel<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)sizeof(RhsTile<float>));
+  e = set_smem_limit<RhsTiledK<float, float>>((int)sizeof(RhsTile<float>));
   if (e != cudaSuccess) return e;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps_fp64, rhs_tiled_kernel<double, double>, RT_X * RT_Z,
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps_fp64, single_kernel<RhsTiledK<double, double>>, RT_X * RT_Z,
                                                     sizeof(RhsTile<double>));
   if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps_fp32, rhs_tiled_kernel<float, float>, RT_X * RT_Z,
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps_fp32, single_kernel<RhsTiledK<float, float>>, RT_X * RT_Z,
                                                        sizeof(RhsTile<float>));
 }
 
 cudaError_t launch_rhs(ns_ctx* c, int k) {
+  LaunchSink s{c, nullptr};
+  return stage_rhs(s, k);
+}
+
+cudaError_t stage_rhs(LaunchSink& s, int k) {
+  ns_ctx* c = s.c;
   RhsArgs a;
   a.u = c->f.u;
   a.v = c->f.v;
@@ -461,16 +487,13 @@ cudaError_t launch_rhs(ns_ctx* c, int k) {
     const int nch = (a.ny + jchunk - 1) / jchunk;
     dim3 grid(a.nx / RT_X, a.nz / RT_Z, nch), block(RT_X, RT_Z);
     if (c->cfg.precision == NS_MIXED)
-      rhs_tiled_kernel<float, float><<<grid, block, sizeof(RhsTile<float>), c->launch>>>(a, jchunk);
-    else
-      rhs_tiled_kernel<double, double><<<grid, block, sizeof(RhsTile<double>), c->launch>>>(a, jchunk);
-    return cudaGetLastError();
+      return emit<RhsTiledK<float, float>>(s, RhsTiledK<float, float>::make(a, jchunk), grid, block,
+                                           sizeof(RhsTile<float>));
+    return emit<RhsTiledK<double, double>>(s, RhsTiledK<double, double>::make(a, jchunk), grid, block,
+                                           sizeof(RhsTile<double>));
   }
   const long plane = (long)a.nx * (a.ny + 1);
   dim3 grid((unsigned)((plane + 127) / 128), (unsigned)a.nz);
-  if (c->cfg.precision == NS_MIXED)
-    rhs_kernel<float, float><<<grid, 128, 0, c->launch>>>(a);
-  else
-    rhs_kernel<double, double><<<grid, 128, 0, c->launch>>>(a);
-  return cudaGetLastError();
+  if (c->cfg.precision == NS_MIXED) return emit<RhsK<float, float>>(s, RhsK<float, float>::make(a), grid, 128, 0);
+  return emit<RhsK<double, double>>(s, RhsK<double, double>::make(a), grid, 128, 0);
 }

@@ -115,7 +115,140 @@ struct ns_ctx {
   std::string err;
 };
 
-// Launchers (enqueue on ctx->launch).  Return cudaGetLastError() of the launch.
+// ---------------------------------------------------------------------------------------------
+// Kernels are written as functors K with `using Args`, `static constexpr int kThreads` and
+// `static __device__ void run(const Args&, dim3 block, dim3 grid)` (block / grid replace
+// blockIdx / gridDim).  single_kernel<K> runs one instance.  batched_kernel<K> runs many: the
+// blocks of every instance are numbered consecutively (first[i] = index of instance i's first
+// block, first[n] = total) and a persistent grid walks them; each item decodes its instance by
+// binary search, rebuilds its local block index and runs the same body with that instance's
+// arguments.  One launch per stage and variant serves the whole ensemble.
+// ---------------------------------------------------------------------------------------------
+struct BatchMap {
+  const int* first;   // n + 1 prefix offsets
+  const uint3* grid;  // per-instance grid shape
+  int n;
+  int total;
+};
+
+template <typename K>
+__global__ void __launch_bounds__(K::kThreads) single_kernel(const typename K::Args a) {
+  K::run(a, blockIdx, gridDim);
+}
+
+template <typename K>
+__global__ void __launch_bounds__(K::kThreads) batched_kernel(const typename K::Args* __restrict__ args,
+                                                              const BatchMap m) {
+  for (int item = blockIdx.x; item < m.total; item += gridDim.x) {
+    int lo = 0, hi = m.n;
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (__ldg(m.first + mid) <= item) lo = mid; else hi = mid;
+    }
+    const uint3 g = m.grid[lo];
+    const int local = item - __ldg(m.first + lo);
+    const dim3 b(local % g.x, (local / g.x) % g.y, local / (g.x * g.y));
+    const typename K::Args a = args[lo];
+    K::run(a, b, dim3(g.x, g.y, g.z));
+    __syncthreads();  // shared memory of this item is reused by the next
+  }
+}
+
+// Dynamic shared-memory limit of both launch forms of functor K.
+template <typename K>
+cudaError_t set_smem_limit(int bytes) {
+  cudaError_t e = cudaFuncSetAttribute(single_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(batched_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Launch sink.  Every stage is written once as `stage(LaunchSink&, substep)` and emits its kernel
+// with emit<K>(sink, args, grid, block, smem): a single-instance sink launches at once on the
+// context's stream; a batch sink hands the launch to a planner that groups the instances of a
+// stage by functor type K and later launches each group as one persistent batched_kernel<K>.
+// ---------------------------------------------------------------------------------------------
+struct BatchGroup {
+  const void* key;                      // identifies K
+  size_t arg_size;
+  std::vector<unsigned char> args;      // packed K::Args, one per instance of the group
+  std::vector<int> first;               // block prefix, first[0] = 0
+  std::vector<uint3> grid;              // per-instance grid
+  dim3 block;
+  size_t smem;                          // largest dynamic shared memory of the group
+  cudaError_t (*enqueue)(const void* dargs, const BatchMap& m, unsigned grid, dim3 block, size_t smem,
+                         cudaStream_t s);
+  int (*blocks_per_sm)(int threads, size_t smem);
+};
+
+struct BatchPlanner {
+  std::vector<BatchGroup> groups;
+  template <typename K>
+  static cudaError_t enqueue_k(const void* dargs, const BatchMap& m, unsigned grid, dim3 block, size_t smem,
+                               cudaStream_t s) {
+    batched_kernel<K><<<grid, block, smem, s>>>((const typename K::Args*)dargs, m);
+    return cudaGetLastError();
+  }
+  template <typename K>
+  static int bps_k(int threads, size_t smem) {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batched_kernel<K>, threads, smem) != cudaSuccess) n = 1;
+    return n > 0 ? n : 1;
+  }
+  template <typename K>
+  cudaError_t collect(const typename K::Args& a, dim3 grid, dim3 block, size_t smem) {
+    static const char key = 0;
+    BatchGroup* g = nullptr;
+    for (auto& q : groups)
+      if (q.key == &key) g = &q;
+    if (!g) {
+      groups.emplace_back();
+      g = &groups.back();
+      g->key = &key;
+      g->arg_size = sizeof(typename K::Args);
+      g->first.push_back(0);
+      g->block = block;
+      g->smem = 0;
+      g->enqueue = &enqueue_k<K>;
+      g->blocks_per_sm = &bps_k<K>;
+    }
+    const unsigned char* p = reinterpret_cast<const unsigned char*>(&a);
+    g->args.insert(g->args.end(), p, p + sizeof(a));
+    g->grid.push_back(make_uint3(grid.x, grid.y, grid.z));
+    g->first.push_back(g->first.back() + (int)(grid.x * grid.y * grid.z));
+    if (smem > g->smem) g->smem = smem;
+    return cudaSuccess;
+  }
+};
+
+struct LaunchSink {
+  ns_ctx* c;            // the instance (its stream is used in single mode)
+  BatchPlanner* plan;   // non-null: collect instead of launching
+};
+
+template <typename K>
+cudaError_t emit(LaunchSink& s, const typename K::Args& a, dim3 grid, dim3 block, size_t smem);
+
+template <typename K>
+cudaError_t emit(LaunchSink& s, const typename K::Args& a, dim3 grid, dim3 block, size_t smem) {
+  if (s.plan) return s.plan->collect<K>(a, grid, block, smem);
+  single_kernel<K><<<grid, block, smem, s.c->launch>>>(a);
+  return cudaGetLastError();
+}
+
+// Stage functions (emit one kernel through the sink) ...
+cudaError_t stage_rhs(LaunchSink& s, int k);
+cudaError_t stage_adi_x(LaunchSink& s, int k);
+cudaError_t stage_adi_y(LaunchSink& s, int k);
+cudaError_t stage_adi_z(LaunchSink& s, int k);
+cudaError_t stage_pois_divz(LaunchSink& s, int k);
+cudaError_t stage_pois_x_fwd(LaunchSink& s, int k);
+cudaError_t stage_pois_tdma(LaunchSink& s, int k);
+cudaError_t stage_pois_x_inv(LaunchSink& s, int k);
+cudaError_t stage_pois_ifftz(LaunchSink& s, int k);
+cudaError_t stage_project(LaunchSink& s, int k);
+
+// ... and their single-instance launchers (enqueue on ctx->launch; return the launch error).
 cudaError_t launch_rhs(ns_ctx* c, int k);
 cudaError_t rhs_set_attributes(int* bps_fp64, int* bps_fp32);  // once per device, outside any capture
 cudaError_t launch_adi_x(ns_ctx* c, int k);

@@ -232,3 +232,22 @@ def boundary_layer(nx=1024, ny=256, nz=512, beta=2.0, re=1000.0, amp=1e-2, cfl=0
     c = (np.abs(u) / dx + np.abs(0.5 * (v[:, :-1] + v[:, 1:])) / dy[None, :, None] + np.abs(w) / dz)
     case.dt = cfl / float(c.max())
     return case, u, v, w, p, bl
+
+
+def ensemble(n=64, seed=1812, amp=1e-3, steps=10, sizes_x=(32, 64, 128), sizes_y=(32, 48, 64, 96),
+             re_range=(1000.0, 5000.0), beta=2.0, dt=2e-3):
+    """Uneven laminar-channel instances (32x32x32 up to 128x96x128): instance i draws nx, nz from
+    sizes_x, ny from sizes_y and Re_b uniformly from re_range with seed + i.  Returns a list of
+    (case, u, v, w, p)."""
+    out = []
+    for i in range(n):
+        r = uniform01(seed + i, 4)
+        nx = sizes_x[int(r[0] * len(sizes_x))]
+        nz = sizes_x[int(r[1] * len(sizes_x))]
+        ny = sizes_y[int(r[2] * len(sizes_y))]
+        re_b = re_range[0] + (re_range[1] - re_range[0]) * float(r[3])
+        case, u, v, w, p = laminar_channel(nx, ny, nz, beta=beta, re_b=re_b, amp=amp, dt=dt, steps=steps,
+                                           seed=seed + 1000 + i)
+        case.name = "ensemble_%d_%dx%dx%d" % (i, nx, ny, nz)
+        out.append((case, u, v, w, p))
+    return out
