@@ -197,6 +197,54 @@ def oracle_baseline(case, u, v, w, p, F, nsub, warm=0):
     return case.cells() * (nsub / (3.0 * F)) / t, t
 
 
+def bench_ensemble(B, torch, dev, args):
+    """64 uneven channel instances: batched (one persistent launch per stage, one graph per step)
+    against the same instances stepped one context at a time; FP64 and mixed."""
+    from paper_1812_01178_gb300 import inputs as I
+    ens = I.ensemble(64)
+    cells = sum(e[0].cells() for e in ens)
+    out = {"workload": "ensemble_64_channels_32^3_to_128x96x128", "instances": len(ens), "cells": cells}
+    steps = max(5, args.steps // 5)
+    for prec, tag in ((0, "fp64"), (1, "mixed")):
+        for e in ens:
+            e[0].precision = prec
+        b = B.Batch([e[0] for e in ens], [e[1:] for e in ens], device=str(dev))
+        b.autotune()
+        b.make_divergence_free()
+        b.step(args.warmup)
+        b.sync()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(b.stream)
+        b.step(steps)
+        e1.record(b.stream)
+        torch.cuda.synchronize()
+        tb = e0.elapsed_time(e1)
+        launches = b.launches_per_step()
+        parts = [B.ns_get_partition(b.instance(q))[:2] for q in range(len(ens))]
+        b.close()
+        solvers = [B.Solver(e[0], *e[1:], device=str(dev)) for e in ens]
+        for s, pm in zip(solvers, parts):
+            s.set_partition(*pm)
+            s.make_divergence_free()
+            s.step(args.warmup)
+        torch.cuda.synchronize()
+        e0.record(solvers[0].stream)
+        for _ in range(steps):
+            for s in solvers:
+                s.step(1)
+        e1.record(solvers[0].stream)
+        torch.cuda.synchronize()
+        ts = e0.elapsed_time(e1)
+        for s in solvers:
+            s.close()
+        out[tag] = {"value": cells * steps / (tb * 1e-3), "ms_per_step": tb / steps,
+                    "batched_launches_per_step": launches, "sequential_value": cells * steps / (ts * 1e-3),
+                    "sequential_launches_per_step": 30 * len(ens), "speedup_vs_sequential": ts / tb}
+    out["mixed_speedup_vs_fp64"] = out["fp64"]["ms_per_step"] / out["mixed"]["ms_per_step"]
+    return out
+
+
 # ------------------------------------------------------------------------------ main
 def main():
     ap = argparse.ArgumentParser()
@@ -208,6 +256,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-ensemble", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -347,6 +396,7 @@ def main():
         ev1.record(sm.stream)
         torch.cuda.synchronize()
         tm = ev0.elapsed_time(ev1)
+        kmix = sm.step_profiled(max(3, args.steps // 5))
         sm.close()
         # accuracy: both forms from the same projected state, 10 steps
         sa = B.Solver(case, u0, v0, w0, p0, device=str(dev))
@@ -367,7 +417,13 @@ def main():
         sb.close()
         mixed = {"value": world * cells * args.steps / (tm * 1e-3), "ms_per_step": tm / args.steps,
                  "speedup_vs_fp64": t_max / tm, "rel_l2_vs_fp64_after_10_steps": err,
-                 "dtype": "f32 increments (rhs, adi) on f64 state; f64 divergence/poisson/projection"}
+                 "dtype": "f32 increments (rhs, adi) on f64 state; f64 divergence/poisson/projection",
+                 "kernel_ms_per_step": {k: v / max(3, args.steps // 5) for k, v in kmix.items() if v > 0}}
+
+    # batched ensemble of uneven instances (64 laminar channels, 32^3 .. 128x96x128)
+    ensemble = None
+    if not args.no_ensemble:
+        ensemble = bench_ensemble(B, torch, dev, args)
 
     # end to end through the host-buffer entry point (pinned host memory)
     hu = torch.from_numpy(np.ascontiguousarray(u0)).pin_memory().numpy()
@@ -401,7 +457,7 @@ def main():
            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f64+f32",
            "data": "synthetic (seeded Re_tau 395 log-law channel field, 10% Gaussian fluctuations, projected)",
            "config": config, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
-           "gpu_launches": len(kern) * 3 * args.steps, "clocks": ck, "mixed": mixed,
+           "gpu_launches": len(kern) * 3 * args.steps, "clocks": ck, "mixed": mixed, "ensemble": ensemble,
            "kernels": {k: {kk: round(vv, 4) for kk, vv in d.items()} for k, d in kern.items()}}
     print(json.dumps(out))
 

@@ -32,6 +32,14 @@ struct AdiXArgs {
   T coef[3];
 };
 
+// coef[comp] * dout[comp][plane] without indexing the argument struct at run time
+template <typename T>
+__device__ __forceinline__ T outflow_term(const AdiXArgs<T>& a, int comp, long plane) {
+  const double* d = comp == 0 ? a.dout[0] : (comp == 1 ? a.dout[1] : a.dout[2]);
+  const T cf = comp == 0 ? a.coef[0] : (comp == 1 ? a.coef[1] : a.coef[2]);
+  return cf * (T)__ldg(d + plane);
+}
+
 // component, boundary-plane index and row pointer of x-line number `line`
 template <typename T>
 __device__ __forceinline__ T* x_line(const AdiXArgs<T>& a, long line, int* comp, long* plane) {
@@ -104,6 +112,7 @@ struct AdiXK {
     AdiXArgs<T> a;
   };
   static constexpr int kThreads = 256;
+  static constexpr int kMinBlocks = 2;
   static Args make(AdiXArgs<T> a) { return Args{a}; }
   static __device__ __forceinline__ void run(const Args& a_, const dim3 bid_, const dim3 gdim_) {
     const AdiXArgs<T>& a = a_.a;
@@ -113,7 +122,7 @@ struct AdiXK {
   const int P = a.P, L = a.L;
   const int ntab = (int)xtab_count(M, P, L);
   const int ncls = a.bl ? 2 : 1;
-  for (int q = threadIdx.x; q < ntab * ncls; q += blockDim.x) st[q] = a.tab[q / ntab][q % ntab];
+  for (int q = threadIdx.x; q < ntab * ncls; q += blockDim.x) st[q] = q < ntab ? a.tab[0][q] : a.tab[1][q - ntab];
   __syncthreads();
 
   const int lane = threadIdx.x & 31;
@@ -142,7 +151,7 @@ struct AdiXK {
     T d[M];
     if (valid) {
       load_part<T, M>(row + r * M, d);
-      if (a.bl && r == P - 1) d[M - 1] += a.coef[comp] * (T)__ldg(a.dout[comp] + plane);
+      if (a.bl && r == P - 1) d[M - 1] += outflow_term(a, comp, plane);
     } else {
 #pragma unroll
       for (int e = 0; e < M; ++e) d[e] = (T)0;
@@ -192,6 +201,7 @@ struct AdiXLongK {
     AdiXArgs<T> a;
   };
   static constexpr int kThreads = 128;
+  static constexpr int kMinBlocks = 8;
   static Args make(AdiXArgs<T> a) { return Args{a}; }
   static __device__ __forceinline__ void run(const Args& a_, const dim3 bid_, const dim3 gdim_) {
     const AdiXArgs<T>& a = a_.a;
@@ -209,7 +219,7 @@ struct AdiXLongK {
     int comp;
     long plane;
     T* row = x_line(a, line, &comp, &plane);
-    const T* tb = a.tab[a.bl && comp != 0 ? 1 : 0];
+    const T* tb = (a.bl && comp != 0) ? a.tab[1] : a.tab[0];
     const T* INV = tb + XT_INV * M * P;
     const T* AINV = tb + XT_AINV * M * P;
     const T* CP = tb + XT_CP * M * P;
@@ -225,7 +235,7 @@ struct AdiXLongK {
       line_buf[(g / M) * (M + 1) + (g % M)] = row[g];
     }
     __syncwarp();
-    if (a.bl && r == P - 1) my[M - 1] += a.coef[comp] * (T)__ldg(a.dout[comp] + plane);
+    if (a.bl && r == P - 1) my[M - 1] += outflow_term(a, comp, plane);
     // A~ x~ = d on partition r
     T prev = my[0] * __ldg(INV + r);
     my[0] = prev;
@@ -285,6 +295,7 @@ struct AdiYK {
     int nz;
   };
   static constexpr int kThreads = 128;
+  static constexpr int kMinBlocks = 16;
   static Args make(T* ru, T* rv, T* rw, const T* tc, const T* tf, int nx, int ny, int nz) { return Args{ru, rv, rw, tc, tf, nx, ny, nz}; }
   static __device__ __forceinline__ void run(const Args& a_, const dim3 bid_, const dim3 gdim_) {
     T* __restrict__ ru = a_.ru;
@@ -351,6 +362,7 @@ struct AdiZK {
     int nz;
   };
   static constexpr int kThreads = 128;
+  static constexpr int kMinBlocks = 12;
   static Args make(T* ru, T* rv, T* rw, double* u, double* v, double* w, const T* tab, int nx, int ny, int nz) { return Args{ru, rv, rw, u, v, w, tab, nx, ny, nz}; }
   static __device__ __forceinline__ void run(const Args& a_, const dim3 bid_, const dim3 gdim_) {
     T* __restrict__ ru = a_.ru;

@@ -83,6 +83,7 @@ struct DivzK {
     const double* u_out;
   };
   static constexpr int kThreads = 256;
+  static constexpr int kMinBlocks = 5;
   static Args make(const double* u, const double* v, const double* w, const double* gc, const double2* twz, double2* spec, int nx, int ny, int nz, int lnz, int TX, double idx, double idz, double scale, const double* u_out) { return Args{u, v, w, gc, twz, spec, nx, ny, nz, lnz, TX, idx, idz, scale, u_out}; }
   static __device__ __forceinline__ void run(const Args& a_, const dim3 bid_, const dim3 gdim_) {
     const double* __restrict__ u = a_.u;
@@ -163,6 +164,7 @@ struct FftxK {
     double scale;
   };
   static constexpr int kThreads = 256;
+  static constexpr int kMinBlocks = 8;
   static Args make(double2* spec, const double2* twx, long nrows, int nx, int lnx, int R, double scale) { return Args{spec, twx, nrows, nx, lnx, R, scale}; }
   static __device__ __forceinline__ void run(const Args& a_, const dim3 bid_, const dim3 gdim_) {
     double2* __restrict__ spec = a_.spec;
@@ -207,6 +209,7 @@ struct TdmaK {
     int ny;
   };
   static constexpr int kThreads = 128;
+  static constexpr int kMinBlocks = 16;
   static Args make(double2* spec, const double2* fac, const double* gc, int nx, int ny) { return Args{spec, fac, gc, nx, ny}; }
   static __device__ __forceinline__ void run(const Args& a_, const dim3 bid_, const dim3 gdim_) {
     double2* __restrict__ spec = a_.spec;
@@ -264,6 +267,7 @@ struct IfftzK {
     double scale;
   };
   static constexpr int kThreads = 256;
+  static constexpr int kMinBlocks = 8;
   static Args make(const double2* spec, const double2* twz, double* phi, int nx, int ny, int nz, int lnz, int TX, double scale) { return Args{spec, twz, phi, nx, ny, nz, lnz, TX, scale}; }
   static __device__ __forceinline__ void run(const Args& a_, const dim3 bid_, const dim3 gdim_) {
     const double2* __restrict__ spec = a_.spec;
@@ -334,6 +338,7 @@ struct ProjectK {
     int bl;
   };
   static constexpr int kThreads = 128;
+  static constexpr int kMinBlocks = 16;
   static Args make(double* u, double* v, double* w, double* p, const double* phi, const double* gc, int nx, int ny, int nz, double sx, double sz, int update_p, double s, int bl) { return Args{u, v, w, p, phi, gc, nx, ny, nz, sx, sz, update_p, s, bl}; }
   static __device__ __forceinline__ void run(const Args& a_, const dim3 bid_, const dim3 gdim_) {
     double* __restrict__ u = a_.u;

@@ -43,6 +43,7 @@ struct RhsK {
     RhsArgs a;
   };
   static constexpr int kThreads = 128;
+  static constexpr int kMinBlocks = 7;
   static Args make(RhsArgs a) { return Args{a}; }
   static __device__ __forceinline__ void run(const Args& a_, const dim3 bid_, const dim3 gdim_) {
     const RhsArgs& a = a_.a;
@@ -228,6 +229,8 @@ struct RhsTiledK {
     int jchunk;
   };
   static constexpr int kThreads = RT_X * RT_Z;
+  // FP64: shared memory allows 3 resident blocks, so up to 85 registers cost nothing; FP32 fits more
+  static constexpr int kMinBlocks = sizeof(T) == 8 ? 3 : 5;
   static Args make(RhsArgs a, int jchunk) { return Args{a, jchunk}; }
   static __device__ __forceinline__ void run(const Args& a_, const dim3 bid_, const dim3 gdim_) {
     const RhsArgs& a = a_.a;

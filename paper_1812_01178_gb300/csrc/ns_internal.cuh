@@ -116,7 +116,7 @@ struct ns_ctx {
 };
 
 // ---------------------------------------------------------------------------------------------
-// Kernels are written as functors K with `using Args`, `static constexpr int kThreads` and
+// Kernels are written as functors K with `Args`, `kThreads` / `kMinBlocks` (launch bounds) and
 // `static __device__ void run(const Args&, dim3 block, dim3 grid)` (block / grid replace
 // blockIdx / gridDim).  single_kernel<K> runs one instance.  batched_kernel<K> runs many: the
 // blocks of every instance are numbered consecutively (first[i] = index of instance i's first
@@ -132,12 +132,12 @@ struct BatchMap {
 };
 
 template <typename K>
-__global__ void __launch_bounds__(K::kThreads) single_kernel(const typename K::Args a) {
+__global__ void __launch_bounds__(K::kThreads, K::kMinBlocks) single_kernel(const __grid_constant__ typename K::Args a) {
   K::run(a, blockIdx, gridDim);
 }
 
 template <typename K>
-__global__ void __launch_bounds__(K::kThreads) batched_kernel(const typename K::Args* __restrict__ args,
+__global__ void __launch_bounds__(K::kThreads, K::kMinBlocks) batched_kernel(const typename K::Args* __restrict__ args,
                                                               const BatchMap m) {
   for (int item = blockIdx.x; item < m.total; item += gridDim.x) {
     int lo = 0, hi = m.n;
@@ -148,8 +148,7 @@ __global__ void __launch_bounds__(K::kThreads) batched_kernel(const typename K::
     const uint3 g = m.grid[lo];
     const int local = item - __ldg(m.first + lo);
     const dim3 b(local % g.x, (local / g.x) % g.y, local / (g.x * g.y));
-    const typename K::Args a = args[lo];
-    K::run(a, b, dim3(g.x, g.y, g.z));
+    K::run(args[lo], b, dim3(g.x, g.y, g.z));
     __syncthreads();  // shared memory of this item is reused by the next
   }
 }

@@ -1,0 +1,153 @@
+"""Full-size workloads in the bench's launch configuration: sampled outputs the oracle computes
+exactly (RHS on z-slabs, individual ADI lines) and properties that hold at any size (divergence
+after projection, outflow mass balance).  The device-side divergence below is test-only
+bookkeeping with torch; every step of the solver runs in the library's kernels."""
+import math
+
+import numpy as np
+import pytest
+
+from tests.gpu_common import B, O, need_gpu, to_np, torch
+from paper_1812_01178_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    need_gpu()
+
+
+def _host_mem_gb():
+    try:
+        with open("/proc/meminfo") as fh:
+            for line in fh:
+                if line.startswith("MemAvailable"):
+                    return int(line.split()[1]) / 1e6
+    except OSError:
+        pass
+    return 0.0
+
+
+def _device_divergence(s, case):
+    """max |D u| over all cells, evaluated on the device (periodic or inflow/outflow x)."""
+    dx, dz = case.lx / case.nx, case.lz / case.nz
+    dy = torch.as_tensor(np.diff(case.yf), device=s.u.device)[None, :, None]
+    if case.bc_x == 1:
+        ux = torch.cat([s.u[:, :, 1:], s.bl["u_out"][:, :, None]], dim=2)
+    else:
+        ux = torch.roll(s.u, -1, dims=2)
+    d = (ux - s.u) / dx + (s.v[:, 1:] - s.v[:, :-1]) / dy + (torch.roll(s.w, -1, dims=0) - s.w) / dz
+    torch.cuda.synchronize()
+    return float(d.abs().max())
+
+
+def _slab(a, k):
+    """Planes k-1, k, k+1 (periodic in z) of a (nz, ...) array."""
+    nz = a.shape[0]
+    return a[[(k - 1) % nz, k, (k + 1) % nz]]
+
+
+def _check_rhs_planes(s, case, u, v, w, p, bl=None, planes=(0, 7)):
+    s.rhs(0)
+    got = [to_np(s.buffer(b)) for b in (B.NS_BUF_RU, B.NS_BUF_RV, B.NS_BUF_RW)]
+    for k in planes:
+        g3 = O.Grid(case.nx, case.ny, 3, case.lx, case.lz * 3 / case.nz, case.yf, case.bc_ytop)
+        if bl is None:
+            r, _ = O.rhs(g3, _slab(u, k), _slab(v, k), _slab(w, k), _slab(p, k), None, 0, case.dt, case.re, case.fx)
+        else:
+            bl3 = {q: _slab(a, k) for q, a in bl.items()}
+            r, _ = O.rhs_bl(g3, _slab(u, k), _slab(v, k), _slab(w, k), _slab(p, k), None, bl3, 0, case.dt, case.re,
+                            case.fx)
+        for q in range(3):
+            ref = r[q][1]
+            tol = (1e-12 if case.precision == 0 else 2e-5) * np.abs(ref).max()
+            np.testing.assert_allclose(got[q][k], ref, rtol=0, atol=tol)
+
+
+def _check_adi_lines(s, case, lines=((3, 5), (17, 0))):
+    """Random r, one sweep per direction, sampled lines vs the oracle's Thomas on those lines."""
+    g = O.Grid.from_case(case)
+    rng = np.random.default_rng(5)
+    dtype = np.float32 if case.precision == 1 else np.float64
+    rr = [rng.standard_normal((case.nz, case.ny + (1 if q == 1 else 0), case.nx)) for q in range(3)]
+    for q in range(3):
+        if q == 1:
+            rr[q][:, 0] = 0
+            rr[q][:, -1] = 0
+        if q == 0 and case.bc_x == 1:
+            rr[q][:, :, 0] = 0
+    tol = 1e-13 if case.precision == 0 else 1e-5
+    k = 0
+    beta = O.RK3_ALPHA[k] * case.dt / (2 * case.re)
+    for d in (0, 1):
+        for q, b in enumerate((B.NS_BUF_RU, B.NS_BUF_RV, B.NS_BUF_RW)):
+            s.buffer(b).copy_(torch.as_tensor(rr[q].astype(dtype), device=s.u.device))
+        s.adi(d, k)
+        for q, b in enumerate((B.NS_BUF_RU, B.NS_BUF_RV, B.NS_BUF_RW)):
+            got = to_np(s.buffer(b))
+            for (jj, kk) in lines:
+                jj = max(1, jj % (case.ny - 1)) if q == 1 else jj % case.ny
+                kk = kk % case.nz
+                if d == 0:
+                    if case.bc_x == 1:
+                        ref = O.adi_sweep_x_bl(g, rr[q][kk:kk + 1, jj:jj + 1, :], q, beta,
+                                               np.zeros((1, 1)))[0, 0]
+                    else:
+                        a, bb, c = O.adi_rows(g, 0, q, beta)
+                        ref = O.thomas_cyclic(a, bb, c, rr[q][kk, jj, :])
+                    np.testing.assert_allclose(got[kk, jj, :], ref, rtol=0, atol=tol * np.abs(ref).max())
+                else:
+                    ii = (7 * jj + 3) % case.nx
+                    col = rr[q][kk:kk + 1, :, ii:ii + 1]
+                    ref = O.adi_sweep(g, col, 1, q, beta)[0, :, 0]
+                    np.testing.assert_allclose(got[kk, :, ii], ref, rtol=0, atol=tol * np.abs(ref).max())
+
+
+def test_turbulent_channel_256x192x256_fp64():
+    case, u, v, w, p = I.turbulent_channel()
+    s = B.Solver(case, u, v, w, p)
+    assert s.partition()[0] == 32
+    _check_rhs_planes(s, case, u, v, w, p)
+    _check_adi_lines(s, case)
+    s.close()
+    s = B.Solver(case, u, v, w, p)
+    s.make_divergence_free()
+    for _ in range(3):
+        s.step(1)
+        assert _device_divergence(s, case) < 1e-10
+    s.close()
+
+
+def test_boundary_layer_1024x256x512_mixed():
+    if _host_mem_gb() < 40:
+        pytest.skip("needs ~40 GB of host memory for the seeded fields")
+    case, u, v, w, p, bl = I.boundary_layer(1024, 256, 512, precision=1)
+    s = B.Solver(case, u, v, w, p, bl=bl)
+    _check_rhs_planes(s, case, u, v, w, p, bl=bl)
+    _check_adi_lines(s, case)
+    s.close()
+    s = B.Solver(case, u, v, w, p, bl=bl)
+    s.make_divergence_free()
+    dy = torch.as_tensor(np.diff(case.yf), device=s.u.device)[None, :]
+    for _ in range(2):
+        s.step(1)
+        assert _device_divergence(s, case) < 1e-10
+        q_in = float((s.u[:, :, 0] * dy).sum())
+        q_out = float((s.bl["u_out"] * dy).sum())
+        assert abs(q_in - q_out) < 1e-10 * abs(q_in)
+    s.close()
+
+
+def test_boundary_layer_2048x288x1024_mixed():
+    """The largest workload (604M cells, 2048-long x-lines): steps hold divergence at round-off."""
+    if _host_mem_gb() < 160:
+        pytest.skip("needs ~160 GB of host memory for the seeded fields")
+    case, u, v, w, p, bl = I.boundary_layer(2048, 288, 1024, precision=1)
+    s = B.Solver(case, u, v, w, p, bl=bl)
+    del u, v, w, p
+    assert s.partition()[0] == 32
+    s.make_divergence_free()
+    s.step(1)
+    assert _device_divergence(s, case) < 1e-10
+    s.close()
