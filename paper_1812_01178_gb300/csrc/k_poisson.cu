@@ -9,8 +9,8 @@
 //   phi = IFFT_z IFFT_x phi^ / (nx nz)   (the 1/(nx nz) is applied to b before the transforms)
 //   u = u* - alpha_k dt G phi,  p = p + phi
 //
-// FFTs are radix-2 Stockham autosort transforms in shared memory with a precomputed twiddle
-// table W_N^k = exp(-2 pi i k / N), k < N/2.  The y factors (1/pivot, c/pivot) of every (kx, kz)
+// FFTs are mixed radix-4/2 Stockham autosort transforms in shared memory with a precomputed
+// twiddle table W_N^k = exp(-2 pi i k / N), k < N.  The y factors (1/pivot, c/pivot) of every (kx, kz)
 // system are precomputed once by pois_factor_kernel (the operator does not change).
 #include "ns_internal.cuh"
 
@@ -22,41 +22,83 @@ __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
   return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
 }
 
-// Stockham radix-2 on nseq sequences of length N = 2^LN stored contiguously in A ([seq][N]);
-// B is scratch of the same size.  SIGN = -1 forward, +1 inverse (unscaled).  Returns the
-// buffer that holds the result.  All threads of the block take part.
+// Stockham autosort FFT on nseq sequences of length N = 2^LN stored contiguously in A ([seq][N]);
+// B is scratch of the same size.  SIGN = -1 forward, +1 inverse (unscaled).  One radix-2 stage
+// when LN is odd, then radix-4 stages (decimation in frequency): with m = n/4 and the inputs
+// a, b, c, d at p, p+m, p+2m, p+3m of the current sub-transform of length n (stride s),
+//   y_{4p+0} = (a+c) + (b+d),              y_{4p+2} = ((a+c) - (b+d)) w^{2p},
+//   y_{4p+1} = ((a-c) - i(b-d)) w^{p},      y_{4p+3} = ((a-c) + i(b-d)) w^{3p}
+// (forward signs; w = exp(-2 pi i / n) = tw[s k]).  tw holds exp(-2 pi i k / N) for k < N.
+// Returns the buffer that holds the result.  All threads of the block take part.
 template <int SIGN>
 __device__ double2* stockham(double2* A, double2* B, int N, int LN, int nseq, const double2* __restrict__ tw) {
-  const int half = N >> 1;
-  const int total = nseq * half;
   int s = 1;
   int ls = 0;  // log2(s)
-  for (int st = 0; st < LN; ++st) {
-    const int m = half >> ls;   // n/2 with n = N/s
+  if (LN & 1) {  // radix-2 stage: n = N
+    const int half = N >> 1;
+    const int total = nseq * half;
     for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
       const int sq = idx >> (LN - 1);
-      const int b = idx & (half - 1);
-      const int p = b >> ls;
-      const int q = b & (s - 1);
+      const int p = idx & (half - 1);
       const double2* X = A + sq * N;
       double2* Y = B + sq * N;
-      const double2 x0 = X[q + s * p];
-      const double2 x1 = X[q + s * (p + m)];
-      Y[q + 2 * s * p] = cadd(x0, x1);
+      const double2 x0 = X[p];
+      const double2 x1 = X[p + half];
+      Y[2 * p] = cadd(x0, x1);
       double2 dlt = csub(x0, x1);
-      if (m > 1) {
-        double2 wv = __ldg(tw + p * s);
+      if (half > 1) {
+        double2 wv = __ldg(tw + p);
         if (SIGN > 0) wv.y = -wv.y;
         dlt = cmul(dlt, wv);
       }
-      Y[q + s * (2 * p + 1)] = dlt;
+      Y[2 * p + 1] = dlt;
     }
     __syncthreads();
     double2* t = A;
     A = B;
     B = t;
-    s <<= 1;
-    ++ls;
+    s = 2;
+    ls = 1;
+  }
+  const int quarter = N >> 2;
+  const int total = nseq * quarter;
+  for (int st = ls; st < LN; st += 2) {
+    const int m = quarter >> ls;  // n/4 with n = N/s
+    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+      const int sq = idx / quarter;
+      const int bi = idx - sq * quarter;
+      const int p = bi >> ls;
+      const int q = bi & (s - 1);
+      const double2* X = A + sq * N + q;
+      double2* Y = B + sq * N + q;
+      const double2 a = X[s * p], b = X[s * (p + m)], c = X[s * (p + 2 * m)], d = X[s * (p + 3 * m)];
+      const double2 t0 = cadd(a, c), t1 = csub(a, c), t2 = cadd(b, d), t3 = csub(b, d);
+      // -i t3 (forward) or +i t3 (inverse)
+      const double2 r3 = SIGN < 0 ? make_double2(t3.y, -t3.x) : make_double2(-t3.y, t3.x);
+      double2 y1 = cadd(t1, r3), y2 = csub(t0, t2), y3 = csub(t1, r3);
+      if (m > 1) {
+        double2 w1 = __ldg(tw + p * s), w2 = __ldg(tw + 2 * p * s), w3 = __ldg(tw + 3 * p * s);
+        if (SIGN > 0) {
+          w1.y = -w1.y;
+          w2.y = -w2.y;
+          w3.y = -w3.y;
+        }
+        y1 = cmul(y1, w1);
+        y2 = cmul(y2, w2);
+        y3 = cmul(y3, w3);
+      }
+      const int o = s * 4 * p;
+      Y[o] = cadd(t0, t2);
+      Y[o + s] = y1;
+      Y[o + 2 * s] = y2;
+      Y[o + 3 * s] = y3;
+    }
+    __syncthreads();
+    double2* t = A;
+    A = B;
+    B = t;
+    s <<= 2;
+    ls += 2;
   }
   return A;
 }
@@ -83,7 +125,7 @@ struct DivzK {
     const double* u_out;
   };
   static constexpr int kThreads = 256;
-  static constexpr int kMinBlocks = 5;
+  static constexpr int kMinBlocks = 4;  // shared memory limits residency to ~3 blocks anyway
   static Args make(const double* u, const double* v, const double* w, const double* gc, const double2* twz, double2* spec, int nx, int ny, int nz, int lnz, int TX, double idx, double idz, double scale, const double* u_out) { return Args{u, v, w, gc, twz, spec, nx, ny, nz, lnz, TX, idx, idz, scale, u_out}; }
   static __device__ __forceinline__ void run(const Args& a_, const dim3 bid_, const dim3 gdim_) {
     const double* __restrict__ u = a_.u;
@@ -164,7 +206,7 @@ struct FftxK {
     double scale;
   };
   static constexpr int kThreads = 256;
-  static constexpr int kMinBlocks = 8;
+  static constexpr int kMinBlocks = 4;  // shared memory limits residency to ~3 blocks anyway
   static Args make(double2* spec, const double2* twx, long nrows, int nx, int lnx, int R, double scale) { return Args{spec, twx, nrows, nx, lnx, R, scale}; }
   static __device__ __forceinline__ void run(const Args& a_, const dim3 bid_, const dim3 gdim_) {
     double2* __restrict__ spec = a_.spec;
@@ -267,7 +309,7 @@ struct IfftzK {
     double scale;
   };
   static constexpr int kThreads = 256;
-  static constexpr int kMinBlocks = 8;
+  static constexpr int kMinBlocks = 4;  // shared memory limits residency to ~3 blocks anyway
   static Args make(const double2* spec, const double2* twz, double* phi, int nx, int ny, int nz, int lnz, int TX, double scale) { return Args{spec, twz, phi, nx, ny, nz, lnz, TX, scale}; }
   static __device__ __forceinline__ void run(const Args& a_, const dim3 bid_, const dim3 gdim_) {
     const double2* __restrict__ spec = a_.spec;
