@@ -295,7 +295,7 @@ struct AdiYK {
     int nz;
   };
   static constexpr int kThreads = 128;
-  static constexpr int kMinBlocks = 16;
+  static constexpr int kMinBlocks = 12;  // room for the rows fetched ahead
   static Args make(T* ru, T* rv, T* rw, const T* tc, const T* tf, int nx, int ny, int nz) { return Args{ru, rv, rw, tc, tf, nx, ny, nz}; }
   static __device__ __forceinline__ void run(const Args& a_, const dim3 bid_, const dim3 gdim_) {
     T* __restrict__ ru = a_.ru;
@@ -326,20 +326,34 @@ struct AdiYK {
   const T* INV = tab;
   const T* AINV = tab + n;
   const T* CP = tab + 2 * n;
-  T prev = line[0] * __ldg(INV);
-  line[0] = prev;
-  for (int j = 1; j < n; ++j) {
-    const long o = (long)j * nx;
-    prev = line[o] * __ldg(INV + j) - __ldg(AINV + j) * prev;
-    line[o] = prev;
+  // rows are fetched U at a time ahead of the dependent recurrence (memory-level parallelism)
+  constexpr int U = 4;
+  T prev = (T)0;
+  for (int j0 = 0; j0 < n; j0 += U) {
+    T dv[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (j0 + u < n) dv[u] = line[(long)(j0 + u) * nx];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (j0 + u < n) {
+        prev = dv[u] * __ldg(INV + j0 + u) - __ldg(AINV + j0 + u) * prev;  // AINV[0] = 0
+        line[(long)(j0 + u) * nx] = prev;
+      }
   }
   T next = prev;
-  for (int j = n - 2; j >= 0; --j) {
-    const long o = (long)j * nx;
-    next = line[o] - __ldg(CP + j) * next;
-    line[o] = next;
+  for (int j1 = n - 2; j1 >= 0; j1 -= U) {
+    T dv[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (j1 - u >= 0) dv[u] = line[(long)(j1 - u) * nx];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (j1 - u >= 0) {
+        next = dv[u] - __ldg(CP + j1 - u) * next;
+        line[(long)(j1 - u) * nx] = next;
+      }
   }
-
   }
 };
 
@@ -362,7 +376,7 @@ struct AdiZK {
     int nz;
   };
   static constexpr int kThreads = 128;
-  static constexpr int kMinBlocks = 12;
+  static constexpr int kMinBlocks = 10;  // room for the rows fetched ahead
   static Args make(T* ru, T* rv, T* rw, double* u, double* v, double* w, const T* tab, int nx, int ny, int nz) { return Args{ru, rv, rw, u, v, w, tab, nx, ny, nz}; }
   static __device__ __forceinline__ void run(const Args& a_, const dim3 bid_, const dim3 gdim_) {
     T* __restrict__ ru = a_.ru;
@@ -392,27 +406,56 @@ struct AdiZK {
   const T* Q = tab + 3 * nz;
   const T fac = __ldg(tab + 4 * nz);
   const T bg = __ldg(tab + 4 * nz + 1);
-  T prev = line[0] * __ldg(INV);
-  line[0] = prev;
-  for (int kk = 1; kk < nz; ++kk) {
-    const long o = kk * stride;
-    prev = line[o] * __ldg(INV + kk) - __ldg(AINV + kk) * prev;
-    line[o] = prev;
+  // Thomas on the Sherman-Morrison-modified matrix, rows fetched U at a time ahead
+  constexpr int U = 4;
+  T prev = (T)0;
+  for (int k0 = 0; k0 < nz; k0 += U) {
+    T dv[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (k0 + u < nz) dv[u] = line[(long)(k0 + u) * stride];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (k0 + u < nz) {
+        prev = dv[u] * __ldg(INV + k0 + u) - __ldg(AINV + k0 + u) * prev;
+        line[(long)(k0 + u) * stride] = prev;
+      }
   }
   const T ylast = prev;
   T next = prev;
-  for (int kk = nz - 2; kk >= 0; --kk) {
-    const long o = kk * stride;
-    next = line[o] - __ldg(CP + kk) * next;
-    line[o] = next;
+  for (int k1 = nz - 2; k1 >= 0; k1 -= U) {
+    T dv[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (k1 - u >= 0) dv[u] = line[(long)(k1 - u) * stride];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (k1 - u >= 0) {
+        next = dv[u] - __ldg(CP + k1 - u) * next;
+        line[(long)(k1 - u) * stride] = next;
+      }
   }
+  // rank-one correction, then u* = u + delta in FP64
   const T corr = (next + bg * ylast) * fac;
-  for (int kk = 0; kk < nz; ++kk) {
-    const long o = kk * stride;
-    const T x = line[o] - corr * __ldg(Q + kk);
-    f[o] = f[o] + (double)x;
+  for (int k0 = 0; k0 < nz; k0 += U) {
+    T yv[U];
+    double fv[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (k0 + u < nz) {
+        yv[u] = line[(long)(k0 + u) * stride];
+        fv[u] = f[(long)(k0 + u) * stride];
+      }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (k0 + u < nz) {
+        const T x = yv[u] - corr * __ldg(Q + k0 + u);
+        double xd;
+        if constexpr (sizeof(T) == 4) xd = f2d(x);
+        else xd = x;
+        f[(long)(k0 + u) * stride] = fv[u] + xd;
+      }
   }
-
   }
 };
 

@@ -251,7 +251,7 @@ struct TdmaK {
     int ny;
   };
   static constexpr int kThreads = 128;
-  static constexpr int kMinBlocks = 16;
+  static constexpr int kMinBlocks = 8;  // nx*(nz/2+1) lines: occupancy is set by the line count, not registers
   static Args make(double2* spec, const double2* fac, const double* gc, int nx, int ny) { return Args{spec, fac, gc, nx, ny}; }
   static __device__ __forceinline__ void run(const Args& a_, const dim3 bid_, const dim3 gdim_) {
     double2* __restrict__ spec = a_.spec;
@@ -267,29 +267,46 @@ struct TdmaK {
   double2* d = spec + base;
   const double2* f = fac + base;
   const double* pa = gc + GC_PA * (ny + 1);
-  double2 prev = d[0];
-  if (i == 0 && kz == 0) prev = make_double2(0.0, 0.0);  // gauge row of the (0,0) mode
-  double2 ff = __ldg(f);
-  prev.x *= ff.x;
-  prev.y *= ff.x;
-  d[0] = prev;
-  for (int j = 1; j < ny; ++j) {
-    const long o = (long)j * nx;
-    const double aj = __ldg(pa + j);
-    const double2 dj = d[o];
-    ff = __ldg(f + o);
-    prev = make_double2(fma(-aj, prev.x, dj.x) * ff.x, fma(-aj, prev.y, dj.y) * ff.x);
-    d[o] = prev;
+  // the (0,0) mode's row 0 is the gauge phi_0 = 0 (its factor row is 1, 0)
+  const bool gauge = (i == 0 && kz == 0);
+  constexpr int U = 4;
+  double2 prev = make_double2(0.0, 0.0);
+  for (int j0 = 0; j0 < ny; j0 += U) {
+    double2 dv[U], fv[U];
+    double av[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (j0 + u < ny) {
+        dv[u] = d[(long)(j0 + u) * nx];
+        fv[u] = __ldg(f + (long)(j0 + u) * nx);
+        av[u] = __ldg(pa + j0 + u);  // a_0 = 0
+      }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (j0 + u < ny) {
+        double2 dj = dv[u];
+        if (gauge && j0 + u == 0) dj = make_double2(0.0, 0.0);
+        prev = make_double2(fma(-av[u], prev.x, dj.x) * fv[u].x, fma(-av[u], prev.y, dj.y) * fv[u].x);
+        d[(long)(j0 + u) * nx] = prev;
+      }
   }
   double2 next = prev;
-  for (int j = ny - 2; j >= 0; --j) {
-    const long o = (long)j * nx;
-    const double cp = __ldg(f + o).y;
-    const double2 dj = d[o];
-    next = make_double2(fma(-cp, next.x, dj.x), fma(-cp, next.y, dj.y));
-    d[o] = next;
+  for (int j1 = ny - 2; j1 >= 0; j1 -= U) {
+    double2 dv[U];
+    double cv[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (j1 - u >= 0) {
+        dv[u] = d[(long)(j1 - u) * nx];
+        cv[u] = __ldg(f + (long)(j1 - u) * nx).y;
+      }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (j1 - u >= 0) {
+        next = make_double2(fma(-cv[u], next.x, dv[u].x), fma(-cv[u], next.y, dv[u].y));
+        d[(long)(j1 - u) * nx] = next;
+      }
   }
-
   }
 };
 

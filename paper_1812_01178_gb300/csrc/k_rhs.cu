@@ -25,6 +25,7 @@ struct RhsArgs {
   void* nw;
   const double* __restrict__ gc;
   const double* __restrict__ rt;  // per-j assembly coefficients of this sub-step (RT_* rows)
+  const float* __restrict__ rtf;  // the same rows in float (read by the FP32 form)
   // inflow / outflow in x (bl = 1): boundary planes, index k * rows + j
   int bl;
   const double* __restrict__ u_out;
@@ -66,25 +67,25 @@ struct RhsK {
   const bool bl = a.bl != 0;
   const int ipx = bl ? i + 1 : ip, imx = bl ? i - 1 : im;
   auto U = [&](int ii, int jj, int kk) -> T {
-    if (ii == nx) return (T)__ldg(a.u_out + (long)kk * ny + jj);
+    if (ii == nx) return from_double<T>(__ldg(a.u_out + (long)kk * ny + jj));
     if (ii < 0) return (T)0;
-    return (T)__ldg(a.u + ((long)kk * ny + jj) * nx + ii);
+    return from_double<T>(__ldg(a.u + ((long)kk * ny + jj) * nx + ii));
   };
   auto V = [&](int ii, int jj, int kk) -> T {
-    if (ii == nx) return (T)(2.0 * __ldg(a.v_out + (long)kk * ny1 + jj) - __ldg(a.v + ((long)kk * ny1 + jj) * nx + nx - 1));
-    if (ii < 0) return (T)(2.0 * __ldg(a.v_in + (long)kk * ny1 + jj) - __ldg(a.v + ((long)kk * ny1 + jj) * nx));
-    return (T)__ldg(a.v + ((long)kk * ny1 + jj) * nx + ii);
+    if (ii == nx) return from_double<T>(2.0 * __ldg(a.v_out + (long)kk * ny1 + jj) - __ldg(a.v + ((long)kk * ny1 + jj) * nx + nx - 1));
+    if (ii < 0) return from_double<T>(2.0 * __ldg(a.v_in + (long)kk * ny1 + jj) - __ldg(a.v + ((long)kk * ny1 + jj) * nx));
+    return from_double<T>(__ldg(a.v + ((long)kk * ny1 + jj) * nx + ii));
   };
   auto W = [&](int ii, int jj, int kk) -> T {
-    if (ii == nx) return (T)(2.0 * __ldg(a.w_out + (long)kk * ny + jj) - __ldg(a.w + ((long)kk * ny + jj) * nx + nx - 1));
-    if (ii < 0) return (T)(2.0 * __ldg(a.w_in + (long)kk * ny + jj) - __ldg(a.w + ((long)kk * ny + jj) * nx));
-    return (T)__ldg(a.w + ((long)kk * ny + jj) * nx + ii);
+    if (ii == nx) return from_double<T>(2.0 * __ldg(a.w_out + (long)kk * ny + jj) - __ldg(a.w + ((long)kk * ny + jj) * nx + nx - 1));
+    if (ii < 0) return from_double<T>(2.0 * __ldg(a.w_in + (long)kk * ny + jj) - __ldg(a.w + ((long)kk * ny + jj) * nx));
+    return from_double<T>(__ldg(a.w + ((long)kk * ny + jj) * nx + ii));
   };
   auto Pp = [&](int ii, int jj, int kk) -> T {
     if (ii < 0 || ii == nx) return (T)0;
-    return (T)__ldg(a.p + ((long)kk * ny + jj) * nx + ii);
+    return from_double<T>(__ldg(a.p + ((long)kk * ny + jj) * nx + ii));
   };
-  auto C = [&](int f, int jj) -> T { return (T)__ldg(a.gc + f * G + jj); };
+  auto C = [&](int f, int jj) -> T { return from_double<T>(__ldg(a.gc + f * G + jj)); };
 
   const T idx = (T)a.idx, idz = (T)a.idz, idx2 = (T)a.idx2, idz2 = (T)a.idz2;
   const T dt = (T)a.dt, gam = (T)a.gam, zet = (T)a.zet, alp = (T)a.alp;
@@ -245,7 +246,7 @@ struct RhsTiledK {
   const int je = min(jb + jchunk, ny);
   const int jlast = (je == ny) ? ny : je - 1;  // v rows: the last chunk also writes face ny
 
-  auto C = [&](int f, int jj) -> T { return (T)__ldg(a.gc + f * G + jj); };
+  auto C = [&](int f, int jj) -> T { return from_double<T>(__ldg(a.gc + f * G + jj)); };
   auto P = [&](int f, int j, int kk, int ii) -> T& { return S.pl[f][j & 3][(kk + 1) * RT_PX + ii + 1]; };
 
   // load plane j of every field (centres for u, w, p; face j for v) with halo; zero outside
@@ -260,25 +261,25 @@ struct RhsTiledK {
         // x-boundary halo: outflow plane of u, linear ghosts of v and w, nothing for p
         const bool out = gi >= nx;
         if (f == 0) {
-          if (out && j >= 0 && j < ny) val = (T)__ldg(a.u_out + (long)gk * ny + j);
+          if (out && j >= 0 && j < ny) val = from_double<T>(__ldg(a.u_out + (long)gk * ny + j));
         } else if (f == 1) {
           if (j >= 0 && j <= ny) {
             const double b = __ldg((out ? a.v_out : a.v_in) + (long)gk * ny1 + j);
-            val = (T)(2.0 * b - __ldg(a.v + ((long)gk * ny1 + j) * nx + (out ? nx - 1 : 0)));
+            val = from_double<T>(2.0 * b - __ldg(a.v + ((long)gk * ny1 + j) * nx + (out ? nx - 1 : 0)));
           }
         } else if (f == 2) {
           if (j >= 0 && j < ny) {
             const double b = __ldg((out ? a.w_out : a.w_in) + (long)gk * ny + j);
-            val = (T)(2.0 * b - __ldg(a.w + ((long)gk * ny + j) * nx + (out ? nx - 1 : 0)));
+            val = from_double<T>(2.0 * b - __ldg(a.w + ((long)gk * ny + j) * nx + (out ? nx - 1 : 0)));
           }
         }
       } else {
         gi = gi < 0 ? gi + nx : (gi >= nx ? gi - nx : gi);
         if (f == 1) {
-          if (j >= 0 && j <= ny) val = (T)__ldg(a.v + ((long)gk * ny1 + j) * nx + gi);
+          if (j >= 0 && j <= ny) val = from_double<T>(__ldg(a.v + ((long)gk * ny1 + j) * nx + gi));
         } else if (j >= 0 && j < ny) {
           const double* src = f == 0 ? a.u : (f == 2 ? a.w : a.p);
-          val = (T)__ldg(src + ((long)gk * ny + j) * nx + gi);
+          val = from_double<T>(__ldg(src + ((long)gk * ny + j) * nx + gi));
         }
       }
       S.pl[f][j & 3][e] = val;
@@ -330,7 +331,10 @@ struct RhsTiledK {
   const T cx = cl * (T)a.idx2, cz = cl * (T)a.idz2;
   const T cb = (T)(a.dt * a.alp * a.fx);
   const bool use_prev = a.zet != 0.0;
-  auto R = [&](int f, int jj) -> T { return (T)__ldg(a.rt + f * G + jj); };
+  auto R = [&](int f, int jj) -> T {
+    if constexpr (sizeof(T) == 4) return __ldg(a.rtf + f * G + jj);
+    else return (T)__ldg(a.rt + f * G + jj);
+  };
   TR* ru = (TR*)a.ru;
   TR* rv = (TR*)a.rv;
   TR* rw = (TR*)a.rw;
@@ -463,6 +467,7 @@ cudaError_t stage_rhs(LaunchSink& s, int k) {
   a.inv_re = c->cfg.re > 0 ? 1.0 / c->cfg.re : 0.0;
   a.fx = c->cfg.fx;
   a.rt = c->rtab[k];
+  a.rtf = c->rtabf[k];
   a.bl = c->bl;
   a.u_out = c->f.u_out;
   a.v_in = c->f.v_in;

@@ -61,7 +61,7 @@ ns_layout make_layout(const ns_config* c) {
   sz[LB_TWX] = nx * 16;
   sz[LB_LAMX] = nx * 8;
   sz[LB_LAMZ] = nzh * 8;
-  sz[LB_RTAB] = 3 * al256((size_t)RT_COUNT * (ny + 1) * 8);
+  sz[LB_RTAB] = 3 * al256((size_t)RT_COUNT * (ny + 1) * 8) + 3 * al256((size_t)RT_COUNT * (ny + 1) * 4);
   sz[LB_DOUT] = 3 * al256((ny + 1) * nz * 8) + 256;
   sz[LB_TWD] = nx * 16;
   size_t o = 0;
@@ -580,6 +580,12 @@ ns_status ns_init(ns_ctx** out, const ns_config* cfg, const ns_fields* fields, v
       RT(RT_QIHC, j) = 0.25 * GCv(GC_IHC, j);
     }
     if (upload_d(c, c->rtab[k], rt) != cudaSuccess) st = NS_ERR_CUDA;
+    c->rtabf[k] = (float*)(base + c->lay.off[LB_RTAB] + 3 * al256((size_t)RT_COUNT * G * 8) +
+                           k * al256((size_t)RT_COUNT * G * 4));
+    {
+      std::vector<float> rf(rt.begin(), rt.end());
+      if (cudaMemcpy(c->rtabf[k], rf.data(), rf.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess) st = NS_ERR_CUDA;
+    }
   }
   // ---------------- ADI y and z factors per sub-step
   for (int k = 0; k < 3 && st == NS_OK; ++k) {

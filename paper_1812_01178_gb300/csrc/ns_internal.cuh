@@ -89,6 +89,7 @@ struct ns_ctx {
   double2* twz;
   double2* twx;
   double* rtab[3];
+  float* rtabf[3];          // float copies of rtab for the FP32 form
   int bl;                   // inflow / convective outflow in x
   double* dout[3];          // outflow-plane increments of the current sub-step (u, v, w)
   double2* twd;             // exp(-i pi l / (2 nx)), l < nx: post-twiddles of the x cosine transform
@@ -114,6 +115,41 @@ struct ns_ctx {
   int npev;
   std::string err;
 };
+
+// ---------------------------------------------------------------------------------------------
+// FP64 <-> FP32 conversions on the integer pipe (IEEE 754 binary64 / binary32 field layouts).
+// The mixed form converts every state value it reads; the hardware conversion occupies the
+// FP64 pipe, which is the scarce unit here.  d2f rounds to nearest even; results below the
+// smallest normal float flush to +-0 and overflow gives +-inf (state values are finite and far
+// from both limits).  f2d is exact for normal floats and zero.
+// ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ float d2f_rn(double x) {
+  const unsigned hi = (unsigned)__double2hiint(x);
+  const unsigned lo = (unsigned)__double2loint(x);
+  const unsigned sign = hi & 0x80000000u;
+  const unsigned e = (hi >> 20) & 0x7FFu;                    // biased binary64 exponent
+  const unsigned mant = ((hi & 0xFFFFFu) << 3) | (lo >> 29);  // top 23 fraction bits
+  const unsigned rem = lo & 0x1FFFFFFFu;                      // 29 dropped bits
+  unsigned bits = ((e - 896u) << 23) | mant;                  // binary32 exponent = e - 1023 + 127
+  bits += (unsigned)(rem > 0x10000000u) | ((unsigned)(rem == 0x10000000u) & (mant & 1u));
+  bits = (e <= 896u) ? 0u : ((e >= 1151u) ? 0x7F800000u : bits);
+  return __uint_as_float(sign | bits);
+}
+
+__device__ __forceinline__ double f2d(float f) {
+  const unsigned b = __float_as_uint(f);
+  const unsigned sign = b & 0x80000000u, e = (b >> 23) & 0xFFu, m = b & 0x7FFFFFu;
+  const unsigned hi = (e == 0u) ? sign : (sign | ((e + 896u) << 20) | (m >> 3));
+  const unsigned lo = (e == 0u) ? 0u : (m << 29);
+  return __hiloint2double((int)hi, (int)lo);
+}
+
+// value of a double in the arithmetic type T of a kernel
+template <typename T>
+__device__ __forceinline__ T from_double(double x) {
+  if constexpr (sizeof(T) == 4) return d2f_rn(x);
+  else return (T)x;
+}
 
 // ---------------------------------------------------------------------------------------------
 // Kernels are written as functors K with `Args`, `kThreads` / `kMinBlocks` (launch bounds) and
