@@ -92,6 +92,21 @@ def load_traffic(workload, kernel):
         return None
 
 
+def nvtx_push(torch, name):
+    """Marks a timed region, so that an ncu launch list can be restricted to it (--nvtx-include)."""
+    try:
+        torch.cuda.nvtx.range_push(name)
+    except Exception:
+        pass
+
+
+def nvtx_pop(torch):
+    try:
+        torch.cuda.nvtx.range_pop()
+    except Exception:
+        pass
+
+
 # ------------------------------------------------------------------------------ clocks
 class ClockSampler:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -333,10 +348,12 @@ def main():
     torch.cuda.synchronize()
     clocks.start()
     time.sleep(0.3)
+    nvtx_push(torch, "bench_timed")
     ev0.record(stream)
     kms = s.step_profiled(args.steps)
     ev1.record(stream)
     torch.cuda.synchronize()
+    nvtx_pop(torch)
     ck = clocks.stop()
     if dist:
         dist.barrier()
@@ -391,10 +408,12 @@ def main():
         if dist:
             dist.barrier()
         torch.cuda.synchronize()
+        nvtx_push(torch, "bench_timed_mixed")
         ev0.record(sm.stream)
         sm.step(args.steps)
         ev1.record(sm.stream)
         torch.cuda.synchronize()
+        nvtx_pop(torch)
         tm = ev0.elapsed_time(ev1)
         kmix = sm.step_profiled(max(3, args.steps // 5))
         sm.close()

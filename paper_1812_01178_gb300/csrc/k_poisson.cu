@@ -9,8 +9,8 @@
 //   phi = IFFT_z IFFT_x phi^ / (nx nz)   (the 1/(nx nz) is applied to b before the transforms)
 //   u = u* - alpha_k dt G phi,  p = p + phi
 //
-// FFTs are mixed radix-4/2 Stockham autosort transforms in shared memory with a precomputed
-// twiddle table W_N^k = exp(-2 pi i k / N), k < N.  The y factors (1/pivot, c/pivot) of every (kx, kz)
+// FFTs are mixed radix-2/4 Stockham autosort transforms (decimation in time) in shared memory
+// with a precomputed table of FMA-form twiddles (fft_twiddles).  The y factors (1/pivot, c/pivot) of every (kx, kz)
 // system are precomputed once by pois_factor_kernel (the operator does not change).
 #include "ns_internal.cuh"
 
@@ -23,82 +23,91 @@ __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
 }
 
 // Stockham autosort FFT on nseq sequences of length N = 2^LN stored contiguously in A ([seq][N]);
-// B is scratch of the same size.  SIGN = -1 forward, +1 inverse (unscaled).  One radix-2 stage
-// when LN is odd, then radix-4 stages (decimation in frequency): with m = n/4 and the inputs
-// a, b, c, d at p, p+m, p+2m, p+3m of the current sub-transform of length n (stride s),
-//   y_{4p+0} = (a+c) + (b+d),              y_{4p+2} = ((a+c) - (b+d)) w^{2p},
-//   y_{4p+1} = ((a-c) - i(b-d)) w^{p},      y_{4p+3} = ((a-c) + i(b-d)) w^{3p}
-// (forward signs; w = exp(-2 pi i / n) = tw[s k]).  tw holds exp(-2 pi i k / N) for k < N.
-// Returns the buffer that holds the result.  All threads of the block take part.
+// B is scratch of the same size.  SIGN = -1 forward, +1 inverse (unscaled).  Decimation in time:
+// one twiddle-free radix-2 stage first when LN is odd, then radix-4 stages.  A stage that has
+// already combined sub-transforms of length Ns reads, for j < N/4 and k = j mod Ns, the inputs
+// a, b, c, d at j, j + N/4, j + N/2, j + 3N/4, multiplies b, c, d by w^k, w^2k, w^3k
+// (w = exp(-2 pi i / 4Ns), conjugated for the inverse), takes the 4-point DFT and writes it to
+// (j / Ns) 4 Ns + k + r Ns, r = 0..3.
+//
+// The FP64 pipe is the bound here, so the twiddled butterfly uses the tangent factorisation of
+// Goedecker (SIAM J. Sci. Comput. 18, 1997): b w = cos(th) (b.x + tan(th) b.y, b.y - tan(th) b.x)
+// costs two FMAs, the cosines are folded into the following additions, and w^k, w^3k share one
+// scale through cos(3th)/cos(th).  The butterfly is 22 FMAs instead of 12 for three complex
+// products plus 16 additions.  tw holds, at entry Ns + k, {tan th, cos th}, {tan 2th, cos 2th},
+// {tan 3th, cos 3th / cos th} with th = 2 pi k / (4 Ns) (fft_twiddles).  cos th > 0 on every entry
+// (th < pi / 2), and cos 2th, cos 3th are never exactly zero in floating point, so every factor is
+// finite.  Returns the buffer that holds the result.  All threads of the block take part.
 template <int SIGN>
 __device__ double2* stockham(double2* A, double2* B, int N, int LN, int nseq, const double2* __restrict__ tw) {
-  int s = 1;
-  int ls = 0;  // log2(s)
-  if (LN & 1) {  // radix-2 stage: n = N
+  int Ns = 1;
+  int ls = 0;  // log2(Ns)
+  if (LN & 1) {  // radix-2, Ns = 1: no twiddles
     const int half = N >> 1;
     const int total = nseq * half;
     for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
       const int sq = idx >> (LN - 1);
-      const int p = idx & (half - 1);
+      const int j = idx & (half - 1);
       const double2* X = A + sq * N;
       double2* Y = B + sq * N;
-      const double2 x0 = X[p];
-      const double2 x1 = X[p + half];
-      Y[2 * p] = cadd(x0, x1);
-      double2 dlt = csub(x0, x1);
-      if (half > 1) {
-        double2 wv = __ldg(tw + p);
-        if (SIGN > 0) wv.y = -wv.y;
-        dlt = cmul(dlt, wv);
-      }
-      Y[2 * p + 1] = dlt;
+      const double2 a = X[j], b = X[j + half];
+      Y[2 * j] = cadd(a, b);
+      Y[2 * j + 1] = csub(a, b);
     }
     __syncthreads();
     double2* t = A;
     A = B;
     B = t;
-    s = 2;
+    Ns = 2;
     ls = 1;
   }
   const int quarter = N >> 2;
   const int total = nseq * quarter;
-  for (int st = ls; st < LN; st += 2) {
-    const int m = quarter >> ls;  // n/4 with n = N/s
+  for (; Ns < N; Ns <<= 2, ls += 2) {
     for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-      const int sq = idx / quarter;
-      const int bi = idx - sq * quarter;
-      const int p = bi >> ls;
-      const int q = bi & (s - 1);
-      const double2* X = A + sq * N + q;
-      double2* Y = B + sq * N + q;
-      const double2 a = X[s * p], b = X[s * (p + m)], c = X[s * (p + 2 * m)], d = X[s * (p + 3 * m)];
-      const double2 t0 = cadd(a, c), t1 = csub(a, c), t2 = cadd(b, d), t3 = csub(b, d);
-      // -i t3 (forward) or +i t3 (inverse)
-      const double2 r3 = SIGN < 0 ? make_double2(t3.y, -t3.x) : make_double2(-t3.y, t3.x);
-      double2 y1 = cadd(t1, r3), y2 = csub(t0, t2), y3 = csub(t1, r3);
-      if (m > 1) {
-        double2 w1 = __ldg(tw + p * s), w2 = __ldg(tw + 2 * p * s), w3 = __ldg(tw + 3 * p * s);
-        if (SIGN > 0) {
-          w1.y = -w1.y;
-          w2.y = -w2.y;
-          w3.y = -w3.y;
-        }
-        y1 = cmul(y1, w1);
-        y2 = cmul(y2, w2);
-        y3 = cmul(y3, w3);
+      const int sq = idx >> (LN - 2);
+      const int j = idx & (quarter - 1);
+      const int k = j & (Ns - 1);
+      const double2* X = A + sq * N + j;
+      double2* Y = B + sq * N + ((j >> ls) << (ls + 2)) + k;
+      const double2 a = X[0], b = X[quarter], c = X[2 * quarter], d = X[3 * quarter];
+      double2 y0, y1, y2, y3;
+      if (Ns == 1) {
+        const double2 t0 = cadd(a, c), t1 = csub(a, c), t2 = cadd(b, d), t3 = csub(b, d);
+        // -i t3 (forward) or +i t3 (inverse)
+        const double2 r3 = SIGN < 0 ? make_double2(t3.y, -t3.x) : make_double2(-t3.y, t3.x);
+        y0 = cadd(t0, t2);
+        y2 = csub(t0, t2);
+        y1 = cadd(t1, r3);
+        y3 = csub(t1, r3);
+      } else {
+        const double2 e1 = __ldg(tw + 3 * (Ns + k)), e2 = __ldg(tw + 3 * (Ns + k) + 1), e3 = __ldg(tw + 3 * (Ns + k) + 2);
+        const double t1 = SIGN < 0 ? e1.x : -e1.x, t2 = SIGN < 0 ? e2.x : -e2.x, t3 = SIGN < 0 ? e3.x : -e3.x;
+        const double c1 = e1.y, c2 = e2.y, r = e3.y;
+        // b, c, d times their twiddles, each up to its cosine
+        const double2 bb = make_double2(fma(t1, b.y, b.x), fma(-t1, b.x, b.y));
+        const double2 cc = make_double2(fma(t2, c.y, c.x), fma(-t2, c.x, c.y));
+        const double2 dd = make_double2(fma(t3, d.y, d.x), fma(-t3, d.x, d.y));
+        const double2 T0 = make_double2(fma(c2, cc.x, a.x), fma(c2, cc.y, a.y));    // a + c w^2k
+        const double2 T1 = make_double2(fma(-c2, cc.x, a.x), fma(-c2, cc.y, a.y));  // a - c w^2k
+        const double2 S = make_double2(fma(r, dd.x, bb.x), fma(r, dd.y, bb.y));    // (b w^k + d w^3k) / cos th
+        const double2 D = make_double2(fma(-r, dd.x, bb.x), fma(-r, dd.y, bb.y));  // (b w^k - d w^3k) / cos th
+        y0 = make_double2(fma(c1, S.x, T0.x), fma(c1, S.y, T0.y));
+        y2 = make_double2(fma(-c1, S.x, T0.x), fma(-c1, S.y, T0.y));
+        // y1 = T1 - i (v1 - v3), y3 = T1 + i (v1 - v3) forward; signs of i swap for the inverse
+        const double s1 = SIGN < 0 ? c1 : -c1;
+        y1 = make_double2(fma(s1, D.y, T1.x), fma(-s1, D.x, T1.y));
+        y3 = make_double2(fma(-s1, D.y, T1.x), fma(s1, D.x, T1.y));
       }
-      const int o = s * 4 * p;
-      Y[o] = cadd(t0, t2);
-      Y[o + s] = y1;
-      Y[o + 2 * s] = y2;
-      Y[o + 3 * s] = y3;
+      Y[0] = y0;
+      Y[Ns] = y1;
+      Y[2 * Ns] = y2;
+      Y[3 * Ns] = y3;
     }
     __syncthreads();
     double2* t = A;
     A = B;
     B = t;
-    s <<= 2;
-    ls += 2;
   }
   return A;
 }
@@ -150,9 +159,11 @@ struct DivzK {
   double2* B = A + nseq * nz;
   const int i0 = bid_.x * TX;
   const int j = bid_.y;
-  const double idy = __ldg(gc + GC_IDY * (ny + 1) + j) * scale;
-  idx *= scale;
-  idz *= scale;
+  // the 1/2 of the two-real-sequence unpack below is folded into the scale here
+  const double hs = 0.5 * scale;
+  const double idy = __ldg(gc + GC_IDY * (ny + 1) + j) * hs;
+  idx *= hs;
+  idz *= hs;
   const long pl = (long)ny * nx, plv = (long)(ny + 1) * nx;
   for (int q = threadIdx.x; q < TX * nz; q += blockDim.x) {
     const int il = q % TX;
@@ -182,9 +193,9 @@ struct DivzK {
     const double2 zn = R[c * nz + ((nz - m) & (nz - 1))];
     double2 X;
     if ((il & 1) == 0)
-      X = make_double2(0.5 * (zm.x + zn.x), 0.5 * (zm.y - zn.y));
+      X = make_double2(zm.x + zn.x, zm.y - zn.y);
     else
-      X = make_double2(0.5 * (zm.y + zn.y), 0.5 * (zn.x - zm.x));
+      X = make_double2(zm.y + zn.y, zn.x - zm.x);
     spec[((long)m * ny + j) * nx + i0 + il] = X;
   }
 

@@ -57,8 +57,8 @@ ns_layout make_layout(const ns_config* c) {
   sz[LB_XTAB] = 6 * al256((5 * nx + 4 * 32 + 8 * 5 * 32) * es);
   sz[LB_YTAB] = 6 * al256(3 * ny * es);
   sz[LB_ZTAB] = 3 * al256((4 * nz + 2) * es);
-  sz[LB_TWZ] = nz * 16;
-  sz[LB_TWX] = nx * 16;
+  sz[LB_TWZ] = nz * 24;  // fft_twiddles: 3 N doubles
+  sz[LB_TWX] = nx * 24;
   sz[LB_LAMX] = nx * 8;
   sz[LB_LAMZ] = nzh * 8;
   sz[LB_RTAB] = 3 * al256((size_t)RT_COUNT * (ny + 1) * 8) + 3 * al256((size_t)RT_COUNT * (ny + 1) * 4);
@@ -662,17 +662,10 @@ ns_status ns_init(ns_ctx** out, const ns_config* cfg, const ns_fields* fields, v
   // ---------------- FFT twiddles, modified wavenumbers, Poisson y factors
   if (st == NS_OK) {
     const double PI = 3.14159265358979323846;
-    std::vector<double> tw(2 * nz);  // exp(-2 pi i q / nz), q < nz
-    for (int q = 0; q < nz; ++q) {
-      tw[2 * q] = std::cos(2.0 * PI * q / nz);
-      tw[2 * q + 1] = -std::sin(2.0 * PI * q / nz);
-    }
+    std::vector<double> tw(3 * nz), tx(3 * nx);
+    fft_twiddles(nz, tw.data());
+    fft_twiddles(nx, tx.data());
     if (upload_d(c, c->twz, tw) != cudaSuccess) st = NS_ERR_CUDA;
-    std::vector<double> tx(2 * nx);  // exp(-2 pi i q / nx), q < nx
-    for (int q = 0; q < nx; ++q) {
-      tx[2 * q] = std::cos(2.0 * PI * q / nx);
-      tx[2 * q + 1] = -std::sin(2.0 * PI * q / nx);
-    }
     if (upload_d(c, c->twx, tx) != cudaSuccess) st = NS_ERR_CUDA;
     std::vector<double> lx(nx), lz(c->nzh);
     for (int q = 0; q < nx; ++q) {

@@ -1,11 +1,36 @@
 // Internal declarations shared by the CUDA translation units of the library.
 #pragma once
+#include <cmath>
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string>
 #include <vector>
 
 #include "../../include/ns.h"
+
+// Twiddles of the radix-4 DIT stages of the shared-memory FFT in FMA form (Goedecker's tangent
+// factorisation): for every stage that has combined sub-transforms of length Ns (Ns = 1, 4, ...
+// for even log2 N; 2, 8, ... for odd) and k < Ns, entry Ns + k holds the three pairs
+// {tan th, cos th}, {tan 2th, cos 2th}, {tan 3th, cos 3th / cos th} with th = 2 pi k / (4 Ns).
+// out has room for 3 N doubles (N / 2 entries of six); unused entries are zero.
+inline void fft_twiddles(int N, double* out) {
+  const double PI = 3.14159265358979323846;
+  for (int q = 0; q < 3 * N; ++q) out[q] = 0.0;
+  int ln = 0;
+  while ((1 << ln) < N) ++ln;
+  for (int Ns = (ln & 1) ? 2 : 4; Ns < N; Ns <<= 2)
+    for (int k = 0; k < Ns; ++k) {
+      const double th = 2.0 * PI * k / (4.0 * Ns);
+      const double c1 = std::cos(th), c2 = std::cos(2.0 * th), c3 = std::cos(3.0 * th);
+      double* e = out + 6 * (Ns + k);
+      e[0] = std::tan(th);
+      e[1] = c1;
+      e[2] = std::tan(2.0 * th);
+      e[3] = c2;
+      e[4] = std::tan(3.0 * th);
+      e[5] = c3 / c1;
+    }
+}
 
 #define NS_FULL_MASK 0xffffffffu
 

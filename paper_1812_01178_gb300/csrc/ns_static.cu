@@ -28,8 +28,8 @@ void* g_scratch[kMaxDevices] = {};  // device address of g_ns_static_scratch, pe
 
 // host staging for the small tables (static: no allocation at call time); guarded by g_mu
 double h_gc[NS_GC_COUNT * 1025];
-double h_twz[8192];
-double h_twx[8192];
+double h_twz[3 * 4096];
+double h_twx[3 * 4096];
 double h_lamx[4096];
 double h_lamz[2049];
 
@@ -51,9 +51,9 @@ Regions regions(int nx, int ny, int nz) {
   r.gc = o;
   o += al256((size_t)NS_GC_COUNT * (ny + 1) * 8);
   r.twz = o;
-  o += al256((size_t)nz * 16);
+  o += al256((size_t)nz * 24);
   r.twx = o;
-  o += al256((size_t)nx * 16);
+  o += al256((size_t)nx * 24);
   r.lamx = o;
   o += al256((size_t)nx * 8);
   r.lamz = o;
@@ -123,14 +123,8 @@ extern "C" ns_status ns_poisson_solve_static(const ns_config* cfg, const double*
   for (int j = 0; j + 1 < ny; ++j) GC(GC_PC, j) = 1.0 / ((yf[j + 1] - yf[j]) * (yc(j + 1) - yc(j)));
   const double PI = 3.14159265358979323846;
   const double dx = cfg->lx / nx, dz = cfg->lz / nz;
-  for (int q = 0; q < nz; ++q) {
-    h_twz[2 * q] = std::cos(2.0 * PI * q / nz);
-    h_twz[2 * q + 1] = -std::sin(2.0 * PI * q / nz);
-  }
-  for (int q = 0; q < nx; ++q) {
-    h_twx[2 * q] = std::cos(2.0 * PI * q / nx);
-    h_twx[2 * q + 1] = -std::sin(2.0 * PI * q / nx);
-  }
+  fft_twiddles(nz, h_twz);
+  fft_twiddles(nx, h_twx);
   for (int q = 0; q < nx; ++q) {
     const int qq = q <= nx - q ? q : nx - q;
     h_lamx[q] = (2.0 / (dx * dx)) * (1.0 - std::cos(2.0 * PI * qq / nx));
@@ -142,8 +136,8 @@ extern "C" ns_status ns_poisson_solve_static(const ns_config* cfg, const double*
     size_t off;
     const void* src;
     size_t bytes;
-  } up[] = {{R.gc, h_gc, (size_t)NS_GC_COUNT * G * 8}, {R.twz, h_twz, (size_t)nz * 16},
-            {R.twx, h_twx, (size_t)nx * 16},           {R.lamx, h_lamx, (size_t)nx * 8},
+  } up[] = {{R.gc, h_gc, (size_t)NS_GC_COUNT * G * 8}, {R.twz, h_twz, (size_t)nz * 24},
+            {R.twx, h_twx, (size_t)nx * 24},           {R.lamx, h_lamx, (size_t)nx * 8},
             {R.lamz, h_lamz, (size_t)(nz / 2 + 1) * 8}};
   for (const auto& q : up)
     if ((e = cudaMemcpyAsync(base + q.off, q.src, q.bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess)
