@@ -33,7 +33,7 @@ sys.path.insert(0, ROOT)
 METRIC = "grid-point-steps/s at 1 GB300 (FP64 vs mixed) + % HBM roofline per sweep"
 UNIT = "grid-point-steps/s"
 
-# Algorithmic work per cell per launch of each kernel (FP64 path), see the design doc section 5:
+# Algorithmic work per cell per launch of each kernel (FP64 path):
 # bytes = each input read once + each output written once; flops = floating-point operations of
 # the formulas (FMA = 2).  Complex spectral arrays have (nz/2+1)/nz of a cell each.
 def kernel_model(nx, ny, nz, es):
@@ -90,6 +90,21 @@ def load_traffic(workload, kernel):
         return rec["bytes_per_launch"]
     except Exception:
         return None
+
+
+def max_over_ranks(torch, dist, seconds, device="cpu"):
+    """The slowest rank's time: every rank passes its own, every rank gets the maximum.  With
+    dist None (one process) it is the time itself."""
+    if dist is None:
+        return seconds
+    t = torch.tensor([seconds], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world, cells, steps, seconds):
+    """Whole-job grid-point-steps/s: every rank advances its own replica of `cells` cells."""
+    return world * cells * steps / seconds
 
 
 def nvtx_push(torch, name):
@@ -279,6 +294,8 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference" and rank != 0:
+        return  # the reference arm runs on rank 0 alone; the other ranks exit without work
 
     from paper_1812_01178_gb300 import inputs as I
     case, u0, v0, w0, p0 = I.turbulent_channel()
@@ -289,8 +306,6 @@ def main():
               "precision": args.precision, "l2": "inputs larger than L2 (state 0.40 GB + workspace)"}
 
     if args.impl == "reference":
-        if rank != 0:
-            return
         import multiprocessing
         F = 64
         t_all0 = time.perf_counter()
@@ -358,12 +373,8 @@ def main():
     if dist:
         dist.barrier()
     t_ms = ev0.elapsed_time(ev1)
-    t_max = t_ms
-    if dist:
-        tt = torch.tensor([t_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt.item())
-    value = world * cells * args.steps / (t_max * 1e-3)
+    t_max = max_over_ranks(torch, dist, t_ms, dev)
+    value = job_throughput(world, cells, args.steps, t_max * 1e-3)
 
     # per-kernel roofline of the dominant kernel
     hbm, hbm_kind, smax = load_peaks()
@@ -414,7 +425,7 @@ def main():
         ev1.record(sm.stream)
         torch.cuda.synchronize()
         nvtx_pop(torch)
-        tm = ev0.elapsed_time(ev1)
+        tm = max_over_ranks(torch, dist, ev0.elapsed_time(ev1), dev)
         kmix = sm.step_profiled(max(3, args.steps // 5))
         sm.close()
         # accuracy: both forms from the same projected state, 10 steps
@@ -434,7 +445,7 @@ def main():
                                                                   vel * vel / math.sqrt(pa.numel()))
         sa.close()
         sb.close()
-        mixed = {"value": world * cells * args.steps / (tm * 1e-3), "ms_per_step": tm / args.steps,
+        mixed = {"value": job_throughput(world, cells, args.steps, tm * 1e-3), "ms_per_step": tm / args.steps,
                  "speedup_vs_fp64": t_max / tm, "rel_l2_vs_fp64_after_10_steps": err,
                  "dtype": "f32 increments (rhs, adi) on f64 state; f64 divergence/poisson/projection",
                  "kernel_ms_per_step": {k: v / max(3, args.steps // 5) for k, v in kmix.items() if v > 0}}
@@ -457,13 +468,9 @@ def main():
         t0 = time.perf_counter()
         for _ in range(args.e2e_steps):
             B.ns_step_host(s.ctx, hu, hv, hw, hp, 1)
-        te = time.perf_counter() - t0
-        if dist:
-            tt = torch.tensor([te], device=dev, dtype=torch.float64)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            te = float(tt.item())
+        te = max_over_ranks(torch, dist, time.perf_counter() - t0, dev)
         nbytes = (hu.nbytes + hv.nbytes + hw.nbytes + hp.nbytes)
-        e2e = {"value": world * cells * args.e2e_steps / te, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+        e2e = {"value": job_throughput(world, cells, args.e2e_steps, te), "unit": UNIT, "h2d_bytes_per_step": nbytes,
                "d2h_bytes_per_step": nbytes, "steps": args.e2e_steps,
                "path": "ns_step_host: pinned host state -> device, one step, device -> host, sync"}
     s.close()

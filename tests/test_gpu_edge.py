@@ -1,0 +1,92 @@
+"""Edge and degenerate cases of the CUDA path through the C ABI: zero steps, the quiescent state,
+the smallest accepted grid, a single partition, and arguments the host rejects before any launch."""
+import numpy as np
+import pytest
+
+from tests.gpu_common import B, O, field_rel_errors, need_gpu, torch
+from paper_1812_01178_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    need_gpu()
+
+
+def test_zero_steps_is_a_no_op():
+    case, u, v, w, p = I.small_channel(32, 20, 16, seed=3)
+    s = B.Solver(case, u, v, w, p)
+    before = s.state()
+    s.step(0)
+    for a, b in zip(before, s.state()):
+        assert np.array_equal(a, b)
+    s.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_quiescent_fluid_stays_exactly_at_rest(precision):
+    """u = v = w = p = 0 with no body force is a fixed point of the scheme: every stage maps
+    zeros to zeros (the Poisson gauge included), in both precisions."""
+    case, u, v, w, p = I.small_channel(32, 20, 16, seed=3)
+    case.fx = 0.0
+    case.precision = precision
+    z = [np.zeros_like(a) for a in (u, v, w, p)]
+    s = B.Solver(case, *z)
+    s.step(3)
+    for a in s.state():
+        assert not np.any(a)
+    s.close()
+
+
+def test_smallest_grid_steps_parity():
+    """8x4x8, the smallest grid the library accepts (one FFT stage of each radix, ny = 4)."""
+    case, u, v, w, p = I.small_channel(8, 4, 8, seed=11)
+    case.dt = 1e-3
+    g = O.Grid.from_case(case)
+    u, v, w = O.make_divergence_free(g, u, v, w)
+    ref = O.step(g, dict(u=u, v=v, w=w, p=p), case.dt, case.re, case.fx, nsteps=2)
+    s = B.Solver(case, u, v, w, p)
+    s.step(2)
+    errs = field_rel_errors(s.state(), (ref["u"], ref["v"], ref["w"], ref["p"]))
+    for name in ("u", "v", "w", "p"):
+        assert errs[name] < 1e-11, (name, errs)
+    s.close()
+
+
+@pytest.mark.parametrize("mode", [B.NS_PART_PPT, B.NS_PART_PDD])
+def test_single_partition_is_plain_thomas(mode):
+    """P = 1: no reduced system; PDD and PPT both reduce to the whole-line solve."""
+    case, u, v, w, p = I.small_channel(16, 9, 8, seed=5)
+    g = O.Grid.from_case(case)
+    s = B.Solver(case, u, v, w, p)
+    s.set_partition(1, mode)
+    assert s.partition()[0] == 1
+    rng = np.random.default_rng(2)
+    rr = [rng.standard_normal((case.nz, case.ny + (1 if q == 1 else 0), case.nx)) for q in range(3)]
+    rr[1][:, 0] = 0
+    rr[1][:, -1] = 0
+    for q, b in enumerate((B.NS_BUF_RU, B.NS_BUF_RV, B.NS_BUF_RW)):
+        s.buffer(b).copy_(torch.as_tensor(rr[q], device=s.u.device))
+    s.adi(0, 1)
+    beta = O.RK3_ALPHA[1] * case.dt / (2 * case.re)
+    for q, b in enumerate((B.NS_BUF_RU, B.NS_BUF_RV, B.NS_BUF_RW)):
+        ref = O.adi_sweep(g, rr[q], 0, q, beta)
+        got = s.buffer(b).double().cpu().numpy()
+        assert np.abs(got - ref).max() <= 1e-13 * np.abs(ref).max()
+    s.close()
+
+
+def test_invalid_arguments_are_rejected_on_the_host():
+    case, u, v, w, p = I.small_channel(16, 9, 8, seed=5)
+    s = B.Solver(case, u, v, w, p)
+    L = B.lib()
+    assert L.ns_adi_sweep(s.ctx, 3, 0) == B.NS_ERR_ARG
+    assert L.ns_adi_sweep(s.ctx, 0, 3) == B.NS_ERR_ARG
+    assert L.ns_rhs(s.ctx, -1) == B.NS_ERR_ARG
+    assert L.ns_step(s.ctx, -1) == B.NS_ERR_ARG
+    assert L.ns_set_partition(s.ctx, 0, 3, B.NS_PART_PPT) != B.NS_OK  # P must divide nx
+    # the context is still usable after the rejected calls
+    s.step(1)
+    s.sync()
+    s.close()
