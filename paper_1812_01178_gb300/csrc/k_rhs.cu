@@ -36,7 +36,31 @@ struct RhsArgs {
   int nx, ny, nz;
   double idx, idz, idx2, idz2;
   double dt, gam, zet, alp, inv_re, fx;
+  // the tiled kernel's sub-step constants, formed once on the host in each arithmetic type
+  double kd[11];
+  float kf[11];
 };
+
+// indexes into RhsArgs::kd / kf
+enum { RK_QIDX, RK_QIDZ, RK_HIDX, RK_HIDZ, RK_CN, RK_CP, RK_CGX, RK_CGZ, RK_CX, RK_CZ, RK_CB };
+
+// The constants of RhsTiledK, each rounded to double (kd) and to float (kf) exactly as the
+// expressions would be in that type: the products of the double inputs are rounded once to the
+// type, and cx, cz are then formed in the type itself.
+void rhs_constants(RhsArgs& a) {
+  const double d[11] = {0.25 * a.idx, 0.25 * a.idz, 0.5 * a.idx, 0.5 * a.idz, -a.dt * a.gam, -a.dt * a.zet,
+                        -a.dt * a.alp * a.idx, -a.dt * a.alp * a.idz, 0.0, 0.0, a.dt * a.alp * a.fx};
+  const double cl = a.dt * a.alp * a.inv_re;
+  for (int q = 0; q < 11; ++q) {
+    a.kd[q] = d[q];
+    a.kf[q] = (float)d[q];
+  }
+  a.kd[RK_CX] = cl * a.idx2;
+  a.kd[RK_CZ] = cl * a.idz2;
+  const float clf = (float)cl;
+  a.kf[RK_CX] = clf * (float)a.idx2;
+  a.kf[RK_CZ] = clf * (float)a.idz2;
+}
 
 template <typename T, typename TR>
 struct RhsK {
@@ -249,40 +273,73 @@ struct RhsTiledK {
   auto C = [&](int f, int jj) -> T { return from_double<T>(__ldg(a.gc + f * G + jj)); };
   auto P = [&](int f, int j, int kk, int ii) -> T& { return S.pl[f][j & 3][(kk + 1) * RT_PX + ii + 1]; };
 
-  // load plane j of every field (centres for u, w, p; face j for v) with halo; zero outside
-  auto load_plane = [&](int j) {
-    for (int q = tid; q < 4 * RT_PLANE; q += RT_X * RT_Z) {
-      const int f = q / RT_PLANE, e = q - f * RT_PLANE;
+  // Plane loads.  Each thread owns up to two positions of the (RT_PZ x RT_PX) halo plane and
+  // loads all four fields there, so the index arithmetic (wrap, offsets) is done once per thread
+  // and only j changes between planes.  u, w, p share the offset of a centre; v has its own.
+  // Positions on the x boundary of an inflow / outflow domain take the boundary planes instead.
+  constexpr int kPos = (RT_PLANE + RT_X * RT_Z - 1) / (RT_X * RT_Z);
+  long oc[kPos], ov[kPos];
+  int pos[kPos];  // plane index e, -1 if unused, or -(e + 2) for an x-boundary halo position
+#pragma unroll
+  for (int r = 0; r < kPos; ++r) {
+    const int e = tid + r * RT_X * RT_Z;
+    pos[r] = -1;
+    oc[r] = 0;
+    ov[r] = 0;
+    if (e < RT_PLANE) {
       const int kk = e / RT_PX - 1, ii = e % RT_PX - 1;
       int gi = i0 + ii, gk = k0 + kk;
       gk = gk < 0 ? gk + nz : (gk >= nz ? gk - nz : gk);
-      T val = (T)0;
       if (a.bl && (gi < 0 || gi >= nx)) {
-        // x-boundary halo: outflow plane of u, linear ghosts of v and w, nothing for p
-        const bool out = gi >= nx;
-        if (f == 0) {
-          if (out && j >= 0 && j < ny) val = from_double<T>(__ldg(a.u_out + (long)gk * ny + j));
-        } else if (f == 1) {
-          if (j >= 0 && j <= ny) {
-            const double b = __ldg((out ? a.v_out : a.v_in) + (long)gk * ny1 + j);
-            val = from_double<T>(2.0 * b - __ldg(a.v + ((long)gk * ny1 + j) * nx + (out ? nx - 1 : 0)));
-          }
-        } else if (f == 2) {
-          if (j >= 0 && j < ny) {
-            const double b = __ldg((out ? a.w_out : a.w_in) + (long)gk * ny + j);
-            val = from_double<T>(2.0 * b - __ldg(a.w + ((long)gk * ny + j) * nx + (out ? nx - 1 : 0)));
-          }
-        }
+        pos[r] = -(e + 2);
+        oc[r] = gk;
       } else {
         gi = gi < 0 ? gi + nx : (gi >= nx ? gi - nx : gi);
-        if (f == 1) {
-          if (j >= 0 && j <= ny) val = from_double<T>(__ldg(a.v + ((long)gk * ny1 + j) * nx + gi));
-        } else if (j >= 0 && j < ny) {
-          const double* src = f == 0 ? a.u : (f == 2 ? a.w : a.p);
-          val = from_double<T>(__ldg(src + ((long)gk * ny + j) * nx + gi));
-        }
+        pos[r] = e;
+        oc[r] = (long)gk * ny * nx + gi;
+        ov[r] = (long)gk * ny1 * nx + gi;
       }
-      S.pl[f][j & 3][e] = val;
+    }
+  }
+  auto load_plane = [&](int j) {
+    const bool jc = j >= 0 && j < ny, jv = j >= 0 && j <= ny;
+    const long jo = (long)j * nx;
+#pragma unroll
+    for (int r = 0; r < kPos; ++r) {
+      if (pos[r] >= 0) {
+        const int e = pos[r];
+        const long o = oc[r] + jo, q = ov[r] + jo;
+        T vu = (T)0, vv = (T)0, vw = (T)0, vp = (T)0;
+        if (jc) {
+          vu = from_double<T>(__ldg(a.u + o));
+          vw = from_double<T>(__ldg(a.w + o));
+          vp = from_double<T>(__ldg(a.p + o));
+        }
+        if (jv) vv = from_double<T>(__ldg(a.v + q));
+        S.pl[0][j & 3][e] = vu;
+        S.pl[1][j & 3][e] = vv;
+        S.pl[2][j & 3][e] = vw;
+        S.pl[3][j & 3][e] = vp;
+      } else if (pos[r] < -1) {
+        // x-boundary halo: outflow plane of u, linear ghosts of v and w, nothing for p
+        const int e = -pos[r] - 2;
+        const int gk = (int)oc[r];
+        const bool out = i0 + e % RT_PX - 1 >= nx;
+        T vu = (T)0, vv = (T)0, vw = (T)0;
+        if (out && jc) vu = from_double<T>(__ldg(a.u_out + (long)gk * ny + j));
+        if (jv) {
+          const double b = __ldg((out ? a.v_out : a.v_in) + (long)gk * ny1 + j);
+          vv = from_double<T>(2.0 * b - __ldg(a.v + ((long)gk * ny1 + j) * nx + (out ? nx - 1 : 0)));
+        }
+        if (jc) {
+          const double b = __ldg((out ? a.w_out : a.w_in) + (long)gk * ny + j);
+          vw = from_double<T>(2.0 * b - __ldg(a.w + ((long)gk * ny + j) * nx + (out ? nx - 1 : 0)));
+        }
+        S.pl[0][j & 3][e] = vu;
+        S.pl[1][j & 3][e] = vv;
+        S.pl[2][j & 3][e] = vw;
+        S.pl[3][j & 3][e] = (T)0;
+      }
     }
   };
   // y-face fluxes on face jf (Fuv, Fvw), zero on the walls
@@ -324,12 +381,13 @@ struct RhsTiledK {
 
   // r = cn N + cp N_prev + cgx (p_i - p_{i-1}) + cx (f_{i+1} + f_{i-1}) + cz (f_{k+1} + f_{k-1})
   //     + cA f_{j-1} + cC f_{j+1} + cD f (+ cb for u), with every constant pre-multiplied by dt
-  const T qidx = (T)(0.25 * a.idx), qidz = (T)(0.25 * a.idz), hidx = (T)(0.5 * a.idx), hidz = (T)(0.5 * a.idz);
-  const T cn = (T)(-a.dt * a.gam), cp = (T)(-a.dt * a.zet);
-  const T cgx = (T)(-a.dt * a.alp * a.idx), cgz = (T)(-a.dt * a.alp * a.idz);
-  const T cl = (T)(a.dt * a.alp * a.inv_re);
-  const T cx = cl * (T)a.idx2, cz = cl * (T)a.idz2;
-  const T cb = (T)(a.dt * a.alp * a.fx);
+  auto K = [&](int q) -> T {
+    if constexpr (sizeof(T) == 4) return a.kf[q];
+    else return a.kd[q];
+  };
+  const T qidx = K(RK_QIDX), qidz = K(RK_QIDZ), hidx = K(RK_HIDX), hidz = K(RK_HIDZ);
+  const T cn = K(RK_CN), cp = K(RK_CP), cgx = K(RK_CGX), cgz = K(RK_CGZ), cx = K(RK_CX), cz = K(RK_CZ);
+  const T cb = K(RK_CB);
   const bool use_prev = a.zet != 0.0;
   auto R = [&](int f, int jj) -> T {
     if constexpr (sizeof(T) == 4) return __ldg(a.rtf + f * G + jj);
@@ -474,6 +532,7 @@ cudaError_t stage_rhs(LaunchSink& s, int k) {
   a.v_out = c->f.v_out;
   a.w_in = c->f.w_in;
   a.w_out = c->f.w_out;
+  rhs_constants(a);
   if (a.nx % RT_X == 0 && a.nz % RT_Z == 0) {
     // split y into chunks (each re-derives one face and two planes) so that the blocks fill
     // whole waves of the resident capacity: minimise waves * (planes per chunk + prologue)
