@@ -28,8 +28,10 @@
  *   v_in, v_out : nz * (ny+1)   v on the inflow / outflow face (inflow fixed, outflow convected)
  *   w_in, w_out : nz * ny       w on the inflow / outflow face (same)
  * v and w see these faces through linear ghost cells (ghost = 2 f_face - f_adjacent).  All device pointers must be 256-byte
- * aligned (cudaMalloc / torch allocations are).  nx must be even, and nx and nz must be
- * powers of two in [8, 4096].  ny is in [4, 1024].
+ * aligned (cudaMalloc / torch allocations are).  nx and nz are 2^a 3^b with a >= 3 (the
+ * mixed radix-2/4/3 FFT of Sec. 2.2; multiples of 8) in [8, 4096], and nx must admit a partition
+ * shape of the x solver (ns_set_partition).  ny is in [4, 1024].  Other sizes give NS_ERR_SIZE
+ * (ns_workspace_bytes returns 0 for them).
  *
  * Ownership.  Fields and the workspace are allocated by the caller (device memory) and are
  * never freed by the library.  The library owns only the opaque context (host memory) and the
@@ -170,10 +172,12 @@ ns_status ns_step_host(ns_ctx* ctx, double* u, double* v, double* w, double* p, 
  * correction first; then ns_poisson_solve(-1) + ns_project(-1)). */
 ns_status ns_make_divergence_free(ns_ctx* ctx);
 
-/* Partitioning of the x-line solver (Sec. 3.2): P partitions per line (a power of two from
- * 1 to 32 dividing nx, with nx/P <= 16, or P = 32 with nx/P = 32 or 64 for long lines), mode 0 = automatic (PDD when the coupling PDD drops
- * is below its tolerance for every sub-step, else PPT), 1 = PPT, 2 = PDD.  Rebuilds the tables
- * and drops the captured graph.  dir must be 0. */
+/* Partitioning of the x-line solver (Sec. 3.2): P partitions of M = nx/P rows per line, P a
+ * power of two from 1 to 32, M in {1, 2, 3, 4, 6, 8, 9, 12, 16} (rows held in registers) or, at
+ * P = 32, M in {24, 32, 48, 64} (long lines staged in shared memory); other P give NS_ERR_ARG.
+ * mode 0 = automatic (PDD when the coupling PDD drops is below its tolerance for every sub-step,
+ * else PPT), 1 = PPT, 2 = PDD.  Rebuilds the tables and drops the captured graph.  dir must be
+ * 0.  The default P is the largest admissible one with at least 8 rows per partition. */
 enum { NS_PART_AUTO = 0, NS_PART_PPT = 1, NS_PART_PDD = 2 };
 ns_status ns_set_partition(ns_ctx* ctx, int dir, int P, int mode);
 

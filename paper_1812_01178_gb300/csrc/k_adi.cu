@@ -516,14 +516,21 @@ cudaError_t launch_x_long_t(LaunchSink& s, int k) {
 template <typename T>
 cudaError_t launch_x_m(LaunchSink& s, int k) {
   ns_ctx* c = s.c;
-  if (c->P == 32 && c->M == 32) return launch_x_long_t<T, 32>(s, k);
-  if (c->P == 32 && c->M == 64) return launch_x_long_t<T, 64>(s, k);
+  if (!x_partition_ok(c->P, c->M)) return cudaErrorInvalidValue;
   switch (c->M) {
     case 1: return launch_x_t<T, 1>(s, k);
     case 2: return launch_x_t<T, 2>(s, k);
+    case 3: return launch_x_t<T, 3>(s, k);
     case 4: return launch_x_t<T, 4>(s, k);
+    case 6: return launch_x_t<T, 6>(s, k);
     case 8: return launch_x_t<T, 8>(s, k);
+    case 9: return launch_x_t<T, 9>(s, k);
+    case 12: return launch_x_t<T, 12>(s, k);
     case 16: return launch_x_t<T, 16>(s, k);
+    case 24: return launch_x_long_t<T, 24>(s, k);
+    case 32: return launch_x_long_t<T, 32>(s, k);
+    case 48: return launch_x_long_t<T, 48>(s, k);
+    case 64: return launch_x_long_t<T, 64>(s, k);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -580,21 +587,26 @@ cudaError_t short_attr() {
   return set_smem_limit<AdiXK<T, M>>(2 * 48 * 1024);
 }
 
-cudaError_t adi_set_attributes() {
+template <typename T>
+cudaError_t x_attributes() {
   cudaError_t e;
-  if ((e = short_attr<double, 1>()) != cudaSuccess || (e = short_attr<double, 2>()) != cudaSuccess ||
-      (e = short_attr<double, 4>()) != cudaSuccess || (e = short_attr<double, 8>()) != cudaSuccess ||
-      (e = short_attr<double, 16>()) != cudaSuccess || (e = short_attr<float, 1>()) != cudaSuccess ||
-      (e = short_attr<float, 2>()) != cudaSuccess || (e = short_attr<float, 4>()) != cudaSuccess ||
-      (e = short_attr<float, 8>()) != cudaSuccess || (e = short_attr<float, 16>()) != cudaSuccess)
+  if ((e = short_attr<T, 1>()) != cudaSuccess || (e = short_attr<T, 2>()) != cudaSuccess ||
+      (e = short_attr<T, 3>()) != cudaSuccess || (e = short_attr<T, 4>()) != cudaSuccess ||
+      (e = short_attr<T, 6>()) != cudaSuccess || (e = short_attr<T, 8>()) != cudaSuccess ||
+      (e = short_attr<T, 9>()) != cudaSuccess || (e = short_attr<T, 12>()) != cudaSuccess ||
+      (e = short_attr<T, 16>()) != cudaSuccess)
     return e;
-  if ((e = set_smem_limit<AdiXLongK<double, 64>>(4 * 32 * 65 * 8)) != cudaSuccess)
+  if ((e = set_smem_limit<AdiXLongK<T, 24>>(4 * 32 * 25 * (int)sizeof(T))) != cudaSuccess ||
+      (e = set_smem_limit<AdiXLongK<T, 32>>(4 * 32 * 33 * (int)sizeof(T))) != cudaSuccess ||
+      (e = set_smem_limit<AdiXLongK<T, 48>>(4 * 32 * 49 * (int)sizeof(T))) != cudaSuccess)
     return e;
-  if ((e = set_smem_limit<AdiXLongK<double, 32>>(4 * 32 * 33 * 8)) != cudaSuccess)
-    return e;
-  if ((e = set_smem_limit<AdiXLongK<float, 64>>(4 * 32 * 65 * 4)) != cudaSuccess)
-    return e;
-  return set_smem_limit<AdiXLongK<float, 32>>(4 * 32 * 33 * 4);
+  return set_smem_limit<AdiXLongK<T, 64>>(4 * 32 * 65 * (int)sizeof(T));
+}
+
+cudaError_t adi_set_attributes() {
+  cudaError_t e = x_attributes<double>();
+  if (e != cudaSuccess) return e;
+  return x_attributes<float>();
 }
 
 size_t adi_y_tab_count(int ny) { return 3 * (size_t)ny; }

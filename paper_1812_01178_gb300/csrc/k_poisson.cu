@@ -9,8 +9,8 @@
 //   phi = IFFT_z IFFT_x phi^ / (nx nz)   (the 1/(nx nz) is applied to b before the transforms)
 //   u = u* - alpha_k dt G phi,  p = p + phi
 //
-// FFTs are mixed radix-2/4 Stockham autosort transforms (decimation in time) in shared memory
-// with a precomputed table of FMA-form twiddles (fft_twiddles).  The y factors (1/pivot, c/pivot) of every (kx, kz)
+// FFTs are mixed radix-2/4/3 Stockham autosort transforms (decimation in time) in shared memory
+// with a precomputed table of FMA-form twiddles (fft_twiddles); nx and nz are 2^a 3^b.  The y factors (1/pivot, c/pivot) of every (kx, kz)
 // system are precomputed once by pois_factor_kernel (the operator does not change).
 #include "ns_internal.cuh"
 
@@ -18,36 +18,36 @@ namespace {
 
 __device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
-__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
-  return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
-}
 
-// Stockham autosort FFT on nseq sequences of length N = 2^LN stored contiguously in A ([seq][N]);
-// B is scratch of the same size.  SIGN = -1 forward, +1 inverse (unscaled).  Decimation in time:
-// one twiddle-free radix-2 stage first when LN is odd, then radix-4 stages.  A stage that has
-// already combined sub-transforms of length Ns reads, for j < N/4 and k = j mod Ns, the inputs
-// a, b, c, d at j, j + N/4, j + N/2, j + 3N/4, multiplies b, c, d by w^k, w^2k, w^3k
-// (w = exp(-2 pi i / 4Ns), conjugated for the inverse), takes the 4-point DFT and writes it to
-// (j / Ns) 4 Ns + k + r Ns, r = 0..3.
+// Stockham autosort FFT on nseq sequences of length N = 2^a 3^b stored contiguously in A
+// ([seq][N]); plan = a | (b << 8) (fft_plan).  B is scratch of the same size.  SIGN = -1 forward,
+// +1 inverse (unscaled).  Decimation in time: one twiddle-free radix-2 stage first when a is odd,
+// then a/2 radix-4 stages, then b radix-3 stages.  A radix-R stage that follows stages combining
+// sub-transforms of length Ns reads, for j < N/R and k = j mod Ns, the R inputs at j + r N/R,
+// multiplies input r by w^(r k) (w = exp(-2 pi i / (R Ns)), conjugated for the inverse), takes the
+// R-point DFT and writes output r to (j / Ns) R Ns + k + r Ns.
 //
-// The FP64 pipe is the bound here, so the twiddled butterfly uses the tangent factorisation of
+// The FP64 pipe is the bound here, so the twiddled butterflies use the tangent factorisation of
 // Goedecker (SIAM J. Sci. Comput. 18, 1997): b w = cos(th) (b.x + tan(th) b.y, b.y - tan(th) b.x)
-// costs two FMAs, the cosines are folded into the following additions, and w^k, w^3k share one
-// scale through cos(3th)/cos(th).  The butterfly is 22 FMAs instead of 12 for three complex
-// products plus 16 additions.  tw holds, at entry Ns + k, {tan th, cos th}, {tan 2th, cos 2th},
-// {tan 3th, cos 3th / cos th} with th = 2 pi k / (4 Ns) (fft_twiddles).  cos th > 0 on every entry
-// (th < pi / 2), and cos 2th, cos 3th are never exactly zero in floating point, so every factor is
-// finite.  Returns the buffer that holds the result.  All threads of the block take part.
+// costs two FMAs, and the cosine is folded into the following additions; inputs 1 and 3 (radix
+// 4) or 1 and 2 (radix 3) share one scale through the ratio of their cosines.  A twiddled radix-4
+// butterfly is 22 FMAs (instead of 28 instructions), a radix-3 one 16.  tw holds six doubles per
+// entry Ns + k (fft_twiddles): radix 4, th = 2 pi k / (4 Ns): {tan th, cos th}, {tan 2th, cos 2th},
+// {tan 3th, cos 3th / cos th}; radix 3, th = 2 pi k / (3 Ns): {tan th, cos th},
+// {tan 2th, cos 2th / cos th}, {cos th / 2, (sqrt 3 / 2) cos th}.  cos th is never exactly zero in
+// floating point, so every factor is finite.  Returns the buffer that holds the result.  All
+// threads of the block take part.
 template <int SIGN>
-__device__ double2* stockham(double2* A, double2* B, int N, int LN, int nseq, const double2* __restrict__ tw) {
+__device__ double2* stockham(double2* A, double2* B, int N, int plan, int nseq, const double2* __restrict__ tw) {
+  const int a2 = plan & 0xff, b3 = plan >> 8;
+  const bool p2 = b3 == 0;  // N a power of two: index arithmetic by shifts
   int Ns = 1;
-  int ls = 0;  // log2(Ns)
-  if (LN & 1) {  // radix-2, Ns = 1: no twiddles
+  if (a2 & 1) {  // radix-2, Ns = 1: no twiddles
     const int half = N >> 1;
     const int total = nseq * half;
     for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-      const int sq = idx >> (LN - 1);
-      const int j = idx & (half - 1);
+      const int sq = p2 ? idx >> (a2 - 1) : idx / half;
+      const int j = idx - sq * half;
       const double2* X = A + sq * N;
       double2* Y = B + sq * N;
       const double2 a = X[j], b = X[j + half];
@@ -59,14 +59,14 @@ __device__ double2* stockham(double2* A, double2* B, int N, int LN, int nseq, co
     A = B;
     B = t;
     Ns = 2;
-    ls = 1;
   }
   const int quarter = N >> 2;
-  const int total = nseq * quarter;
-  for (; Ns < N; Ns <<= 2, ls += 2) {
+  for (int st = 0; st < (a2 >> 1); ++st, Ns <<= 2) {
+    const int ls = __ffs(Ns) - 1;  // Ns is a power of two in the radix-4 stages
+    const int total = nseq * quarter;
     for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-      const int sq = idx >> (LN - 2);
-      const int j = idx & (quarter - 1);
+      const int sq = p2 ? idx >> (a2 - 2) : idx / quarter;
+      const int j = idx - sq * quarter;
       const int k = j & (Ns - 1);
       const double2* X = A + sq * N + j;
       double2* Y = B + sq * N + ((j >> ls) << (ls + 2)) + k;
@@ -109,6 +109,48 @@ __device__ double2* stockham(double2* A, double2* B, int N, int LN, int nseq, co
     A = B;
     B = t;
   }
+  const int third = N / 3;
+  constexpr double kS3 = 0.86602540378443864676;  // sqrt(3) / 2
+  for (int st = 0; st < b3; ++st, Ns *= 3) {
+    const int total = nseq * third;
+    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+      const int sq = idx / third;
+      const int j = idx - sq * third;
+      const int g = j / Ns;
+      const int k = j - g * Ns;
+      const double2* X = A + sq * N + j;
+      double2* Y = B + sq * N + g * 3 * Ns + k;
+      const double2 a = X[0], b = X[third], c = X[2 * third];
+      double2 S, D, y0, T;
+      double gs;
+      if (Ns == 1) {
+        S = cadd(b, c);
+        D = csub(b, c);
+        y0 = cadd(a, S);
+        T = make_double2(fma(-0.5, S.x, a.x), fma(-0.5, S.y, a.y));
+        gs = SIGN < 0 ? kS3 : -kS3;
+      } else {
+        const double2 e1 = __ldg(tw + 3 * (Ns + k)), e2 = __ldg(tw + 3 * (Ns + k) + 1), e3 = __ldg(tw + 3 * (Ns + k) + 2);
+        const double t1 = SIGN < 0 ? e1.x : -e1.x, t2 = SIGN < 0 ? e2.x : -e2.x;
+        const double c1 = e1.y, r = e2.y, h = e3.x;
+        const double2 bb = make_double2(fma(t1, b.y, b.x), fma(-t1, b.x, b.y));
+        const double2 cc = make_double2(fma(t2, c.y, c.x), fma(-t2, c.x, c.y));
+        S = make_double2(fma(r, cc.x, bb.x), fma(r, cc.y, bb.y));    // (b w^k + c w^2k) / cos th
+        D = make_double2(fma(-r, cc.x, bb.x), fma(-r, cc.y, bb.y));  // (b w^k - c w^2k) / cos th
+        y0 = make_double2(fma(c1, S.x, a.x), fma(c1, S.y, a.y));
+        T = make_double2(fma(-h, S.x, a.x), fma(-h, S.y, a.y));      // a - (v1 + v2) / 2
+        gs = SIGN < 0 ? e3.y : -e3.y;                                // (sqrt 3 / 2) cos th
+      }
+      // y1 = T - i (sqrt 3 / 2)(v1 - v2), y2 = T + i (sqrt 3 / 2)(v1 - v2) forward
+      Y[0] = y0;
+      Y[Ns] = make_double2(fma(gs, D.y, T.x), fma(-gs, D.x, T.y));
+      Y[2 * Ns] = make_double2(fma(-gs, D.y, T.x), fma(gs, D.x, T.y));
+    }
+    __syncthreads();
+    double2* t = A;
+    A = B;
+    B = t;
+  }
   return A;
 }
 
@@ -126,7 +168,7 @@ struct DivzK {
     int nx;
     int ny;
     int nz;
-    int lnz;
+    int pz;  // fft_plan(nz)
     int TX;
     double idx;
     double idz;
@@ -135,7 +177,7 @@ struct DivzK {
   };
   static constexpr int kThreads = 256;
   static constexpr int kMinBlocks = 4;  // shared memory limits residency to ~3 blocks anyway
-  static Args make(const double* u, const double* v, const double* w, const double* gc, const double2* twz, double2* spec, int nx, int ny, int nz, int lnz, int TX, double idx, double idz, double scale, const double* u_out) { return Args{u, v, w, gc, twz, spec, nx, ny, nz, lnz, TX, idx, idz, scale, u_out}; }
+  static Args make(const double* u, const double* v, const double* w, const double* gc, const double2* twz, double2* spec, int nx, int ny, int nz, int pz, int TX, double idx, double idz, double scale, const double* u_out) { return Args{u, v, w, gc, twz, spec, nx, ny, nz, pz, TX, idx, idz, scale, u_out}; }
   static __device__ __forceinline__ void run(const Args& a_, const dim3 bid_, const dim3 gdim_) {
     const double* __restrict__ u = a_.u;
     const double* __restrict__ v = a_.v;
@@ -146,7 +188,7 @@ struct DivzK {
     int nx = a_.nx;
     int ny = a_.ny;
     int nz = a_.nz;
-    int lnz = a_.lnz;
+    int pz = a_.pz;
     int TX = a_.TX;
     double idx = a_.idx;
     double idz = a_.idz;
@@ -182,7 +224,7 @@ struct DivzK {
     slot[il & 1] = b;
   }
   __syncthreads();
-  double2* R = stockham<-1>(A, B, nz, lnz, nseq, twz);
+  double2* R = stockham<-1>(A, B, nz, pz, nseq, twz);
   // unpack the two real transforms of each packed pair; write kz = 0..nz/2
   const int nh = (nz >> 1) + 1;
   for (int q = threadIdx.x; q < nh * TX; q += blockDim.x) {
@@ -190,7 +232,7 @@ struct DivzK {
     const int m = q / TX;
     const int c = il >> 1;
     const double2 zm = R[c * nz + m];
-    const double2 zn = R[c * nz + ((nz - m) & (nz - 1))];
+    const double2 zn = R[c * nz + (m == 0 ? 0 : nz - m)];
     double2 X;
     if ((il & 1) == 0)
       X = make_double2(zm.x + zn.x, zm.y - zn.y);
@@ -212,19 +254,19 @@ struct FftxK {
     const double2* twx;
     long nrows;
     int nx;
-    int lnx;
+    int px;  // fft_plan(nx)
     int R;
     double scale;
   };
   static constexpr int kThreads = 256;
   static constexpr int kMinBlocks = 4;  // shared memory limits residency to ~3 blocks anyway
-  static Args make(double2* spec, const double2* twx, long nrows, int nx, int lnx, int R, double scale) { return Args{spec, twx, nrows, nx, lnx, R, scale}; }
+  static Args make(double2* spec, const double2* twx, long nrows, int nx, int px, int R, double scale) { return Args{spec, twx, nrows, nx, px, R, scale}; }
   static __device__ __forceinline__ void run(const Args& a_, const dim3 bid_, const dim3 gdim_) {
     double2* __restrict__ spec = a_.spec;
     const double2* __restrict__ twx = a_.twx;
     long nrows = a_.nrows;
     int nx = a_.nx;
-    int lnx = a_.lnx;
+    int px = a_.px;
     int R = a_.R;
     double scale = a_.scale;
 
@@ -237,7 +279,7 @@ struct FftxK {
   for (int q = threadIdx.x; q < nr * nx; q += blockDim.x) A[q] = g[q];
   for (int q = nr * nx + threadIdx.x; q < R * nx; q += blockDim.x) A[q] = make_double2(0.0, 0.0);
   __syncthreads();
-  double2* Rb = stockham<SIGN>(A, B, nx, lnx, R, twx);
+  double2* Rb = stockham<SIGN>(A, B, nx, px, R, twx);
   if (scale == 1.0) {
     for (int q = threadIdx.x; q < nr * nx; q += blockDim.x) g[q] = Rb[q];
   } else {
@@ -332,13 +374,13 @@ struct IfftzK {
     int nx;
     int ny;
     int nz;
-    int lnz;
+    int pz;  // fft_plan(nz)
     int TX;
     double scale;
   };
   static constexpr int kThreads = 256;
   static constexpr int kMinBlocks = 4;  // shared memory limits residency to ~3 blocks anyway
-  static Args make(const double2* spec, const double2* twz, double* phi, int nx, int ny, int nz, int lnz, int TX, double scale) { return Args{spec, twz, phi, nx, ny, nz, lnz, TX, scale}; }
+  static Args make(const double2* spec, const double2* twz, double* phi, int nx, int ny, int nz, int pz, int TX, double scale) { return Args{spec, twz, phi, nx, ny, nz, pz, TX, scale}; }
   static __device__ __forceinline__ void run(const Args& a_, const dim3 bid_, const dim3 gdim_) {
     const double2* __restrict__ spec = a_.spec;
     const double2* __restrict__ twz = a_.twz;
@@ -346,7 +388,7 @@ struct IfftzK {
     int nx = a_.nx;
     int ny = a_.ny;
     int nz = a_.nz;
-    int lnz = a_.lnz;
+    int pz = a_.pz;
     int TX = a_.TX;
     double scale = a_.scale;
 
@@ -373,7 +415,7 @@ struct IfftzK {
     if (m > 0 && m < nh) A[c * nz + nz - m] = make_double2(xa.x + xb.y, xb.x - xa.y);
   }
   __syncthreads();
-  const double2* R = stockham<1>(A, B, nz, lnz, nseq, twz);
+  const double2* R = stockham<1>(A, B, nz, pz, nseq, twz);
   const long pl = (long)ny * nx;
   for (int q = threadIdx.x; q < TX * nz; q += blockDim.x) {
     const int il = q % TX;
@@ -460,7 +502,7 @@ struct ProjectK {
 // V_l = conj(w_l) (X_l - i X_{N-l}) (X_N = 0), v = IFFT(V), x_{2n} = v_n, x_{2n+1} = v_{N-1-n}.
 // ------------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) dctx_fwd_kernel(double2* __restrict__ spec, const double2* __restrict__ twx,
-                                                       const double2* __restrict__ twd, long nrows, int nx, int lnx,
+                                                       const double2* __restrict__ twd, long nrows, int nx, int px,
                                                        int R) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double2* A = reinterpret_cast<double2*>(smem_raw);
@@ -474,11 +516,11 @@ __global__ void __launch_bounds__(256) dctx_fwd_kernel(double2* __restrict__ spe
     A[rr * nx + dst] = rr < nr ? g[q] : make_double2(0.0, 0.0);
   }
   __syncthreads();
-  const double2* V = stockham<-1>(A, B, nx, lnx, R, twx);
+  const double2* V = stockham<-1>(A, B, nx, px, R, twx);
   for (int q = threadIdx.x; q < nr * nx; q += blockDim.x) {
     const int rr = q / nx, l = q - rr * nx;
     const double2 vl = V[rr * nx + l];
-    const double2 vn = V[rr * nx + ((nx - l) & (nx - 1))];
+    const double2 vn = V[rr * nx + (l == 0 ? 0 : nx - l)];
     const double2 w = __ldg(twd + l);
     const double ax = 0.5 * (vl.x + vn.x), ay = 0.5 * (vl.y - vn.y);
     const double bx = 0.5 * (vl.y + vn.y), by = 0.5 * (vn.x - vl.x);
@@ -487,7 +529,7 @@ __global__ void __launch_bounds__(256) dctx_fwd_kernel(double2* __restrict__ spe
 }
 
 __global__ void __launch_bounds__(256) dctx_inv_kernel(double2* __restrict__ spec, const double2* __restrict__ twx,
-                                                       const double2* __restrict__ twd, long nrows, int nx, int lnx,
+                                                       const double2* __restrict__ twd, long nrows, int nx, int px,
                                                        int R) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double2* A = reinterpret_cast<double2*>(smem_raw);
@@ -508,7 +550,7 @@ __global__ void __launch_bounds__(256) dctx_inv_kernel(double2* __restrict__ spe
     A[q] = v;
   }
   __syncthreads();
-  const double2* X = stockham<1>(A, B, nx, lnx, R, twx);
+  const double2* X = stockham<1>(A, B, nx, px, R, twx);
   for (int q = threadIdx.x; q < nr * nx; q += blockDim.x) {
     const int rr = q / nx, i = q - rr * nx;
     const int src = (i & 1) ? nx - 1 - (i >> 1) : (i >> 1);
@@ -606,12 +648,6 @@ __global__ void pois_factor_kernel(double2* __restrict__ fac, const double* __re
   }
 }
 
-int ilog2(int n) {
-  int l = 0;
-  while ((1 << l) < n) ++l;
-  return l;
-}
-
 }  // namespace
 
 cudaError_t poisson_set_attributes() {
@@ -639,7 +675,7 @@ static int z_tile(int nz) {
 
 namespace {
 struct PoisShape {
-  int nx, ny, nz, lnz, lnx, TX, R;
+  int nx, ny, nz, pz, px, TX, R;
   size_t smz, smx;
   long nrows;
   unsigned bx;
@@ -649,9 +685,10 @@ PoisShape pois_shape(const ns_ctx* c) {
   q.nx = c->cfg.nx;
   q.ny = c->cfg.ny;
   q.nz = c->cfg.nz;
-  q.lnz = ilog2(q.nz);
-  q.lnx = ilog2(q.nx);
-  q.TX = min(z_tile(q.nz), q.nx);
+  q.pz = fft_plan(q.nz);
+  q.px = fft_plan(q.nx);
+  q.TX = z_tile(q.nz);
+  while (q.nx % q.TX) q.TX >>= 1;  // TX divides nx (nx is a multiple of 8)
   q.smz = (size_t)q.TX * q.nz * sizeof(double2);  // two buffers of TX/2 sequences
   q.nrows = (long)c->nzh * q.ny;
   q.R = 1;
@@ -660,11 +697,11 @@ PoisShape pois_shape(const ns_ctx* c) {
   q.bx = (unsigned)((q.nrows + q.R - 1) / q.R);
   return q;
 }
-void single_kernel_dct_fwd(ns_ctx* c, unsigned bx, size_t smx, long nrows, int nx, int lnx, int R) {
-  dctx_fwd_kernel<<<bx, 256, smx, c->launch>>>(c->spec, c->twx, c->twd, nrows, nx, lnx, R);
+void single_kernel_dct_fwd(ns_ctx* c, unsigned bx, size_t smx, long nrows, int nx, int px, int R) {
+  dctx_fwd_kernel<<<bx, 256, smx, c->launch>>>(c->spec, c->twx, c->twd, nrows, nx, px, R);
 }
-void single_kernel_dct_inv(ns_ctx* c, unsigned bx, size_t smx, long nrows, int nx, int lnx, int R) {
-  dctx_inv_kernel<<<bx, 256, smx, c->launch>>>(c->spec, c->twx, c->twd, nrows, nx, lnx, R);
+void single_kernel_dct_inv(ns_ctx* c, unsigned bx, size_t smx, long nrows, int nx, int px, int R) {
+  dctx_inv_kernel<<<bx, 256, smx, c->launch>>>(c->spec, c->twx, c->twd, nrows, nx, px, R);
 }
 }  // namespace
 
@@ -674,7 +711,7 @@ cudaError_t stage_pois_divz(LaunchSink& s, int k) {
   const PoisShape q = pois_shape(c);
   // 1/(alpha_k dt) of the right-hand side and 1/(nx nz) of the inverse transforms, applied once
   const double scale = ((k >= 0) ? 1.0 / (NS_ALPHA[k] * c->cfg.dt) : 1.0) / ((double)q.nx * q.nz);
-  return emit<DivzK>(s, DivzK::make(c->f.u, c->f.v, c->f.w, c->gc, c->twz, c->spec, q.nx, q.ny, q.nz, q.lnz, q.TX,
+  return emit<DivzK>(s, DivzK::make(c->f.u, c->f.v, c->f.w, c->gc, c->twz, c->spec, q.nx, q.ny, q.nz, q.pz, q.TX,
                                     1.0 / c->dx, 1.0 / c->dz, scale, c->bl ? c->f.u_out : nullptr),
                      dim3(q.nx / q.TX, q.ny), dim3(256), q.smz);
 }
@@ -684,10 +721,10 @@ cudaError_t stage_pois_x_fwd(LaunchSink& s, int) {
   ns_ctx* c = s.c;
   const PoisShape q = pois_shape(c);
   if (c->bl) {
-    single_kernel_dct_fwd(c, q.bx, q.smx, q.nrows, q.nx, q.lnx, q.R);
+    single_kernel_dct_fwd(c, q.bx, q.smx, q.nrows, q.nx, q.px, q.R);
     return cudaGetLastError();
   }
-  return emit<FftxK<-1>>(s, FftxK<-1>::make(c->spec, c->twx, q.nrows, q.nx, q.lnx, q.R, 1.0), dim3(q.bx), dim3(256),
+  return emit<FftxK<-1>>(s, FftxK<-1>::make(c->spec, c->twx, q.nrows, q.nx, q.px, q.R, 1.0), dim3(q.bx), dim3(256),
                          q.smx);
 }
 
@@ -703,10 +740,10 @@ cudaError_t stage_pois_x_inv(LaunchSink& s, int) {
   ns_ctx* c = s.c;
   const PoisShape q = pois_shape(c);
   if (c->bl) {
-    single_kernel_dct_inv(c, q.bx, q.smx, q.nrows, q.nx, q.lnx, q.R);
+    single_kernel_dct_inv(c, q.bx, q.smx, q.nrows, q.nx, q.px, q.R);
     return cudaGetLastError();
   }
-  return emit<FftxK<1>>(s, FftxK<1>::make(c->spec, c->twx, q.nrows, q.nx, q.lnx, q.R, 1.0), dim3(q.bx), dim3(256),
+  return emit<FftxK<1>>(s, FftxK<1>::make(c->spec, c->twx, q.nrows, q.nx, q.px, q.R, 1.0), dim3(q.bx), dim3(256),
                         q.smx);
 }
 
@@ -714,7 +751,7 @@ cudaError_t stage_pois_x_inv(LaunchSink& s, int) {
 cudaError_t stage_pois_ifftz(LaunchSink& s, int) {
   ns_ctx* c = s.c;
   const PoisShape q = pois_shape(c);
-  return emit<IfftzK>(s, IfftzK::make(c->spec, c->twz, c->phi, q.nx, q.ny, q.nz, q.lnz, q.TX, 1.0),
+  return emit<IfftzK>(s, IfftzK::make(c->spec, c->twz, c->phi, q.nx, q.ny, q.nz, q.pz, q.TX, 1.0),
                       dim3(q.nx / q.TX, q.ny), dim3(256), q.smz);
 }
 

@@ -12,7 +12,6 @@ namespace {
 
 thread_local std::string g_init_error;
 
-bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
 
 size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 
@@ -27,8 +26,11 @@ std::string check_cfg(const ns_config* c, ns_status* kind = nullptr) {
   if (c->bc_ytop != 0 && c->bc_ytop != 1) return "bc_ytop must be 0 or 1";
   if (c->precision != NS_FP64 && c->precision != NS_MIXED) return "precision must be NS_FP64 or NS_MIXED";
   k = NS_ERR_SIZE;
-  if (!is_pow2(c->nx) || c->nx < 8 || c->nx > 4096) return "nx must be a power of two in [8, 4096]";
-  if (!is_pow2(c->nz) || c->nz < 8 || c->nz > 4096) return "nz must be a power of two in [8, 4096]";
+  if (fft_plan(c->nx) < 0 || c->nx % 8 || c->nx < 8 || c->nx > 4096)
+    return "nx must be 2^a 3^b with a >= 3, in [8, 4096]";
+  if (fft_plan(c->nz) < 0 || c->nz % 8 || c->nz < 8 || c->nz > 4096)
+    return "nz must be 2^a 3^b with a >= 3, in [8, 4096]";
+  if (x_default_partition(c->nx) == 0) return "nx has no partition shape of the x solver (P <= 32 lanes, M rows)";
   if (c->ny < 4 || c->ny > 1024) return "ny must be in [4, 1024]";
   k = NS_ERR_ARG;
   if (!(c->lx > 0) || !(c->lz > 0) || !(c->dt > 0)) return "lx, lz and dt must be positive";
@@ -57,8 +59,8 @@ ns_layout make_layout(const ns_config* c) {
   sz[LB_XTAB] = 6 * al256((5 * nx + 4 * 32 + 8 * 5 * 32) * es);
   sz[LB_YTAB] = 6 * al256(3 * ny * es);
   sz[LB_ZTAB] = 3 * al256((4 * nz + 2) * es);
-  sz[LB_TWZ] = nz * 24;  // fft_twiddles: 3 N doubles
-  sz[LB_TWX] = nx * 24;
+  sz[LB_TWZ] = fft_twiddle_doubles((int)nz) * 8;
+  sz[LB_TWX] = fft_twiddle_doubles((int)nx) * 8;
   sz[LB_LAMX] = nx * 8;
   sz[LB_LAMZ] = nzh * 8;
   sz[LB_RTAB] = 3 * al256((size_t)RT_COUNT * (ny + 1) * 8) + 3 * al256((size_t)RT_COUNT * (ny + 1) * 4);
@@ -647,22 +649,20 @@ ns_status ns_init(ns_ctx** out, const ns_config* cfg, const ns_fields* fields, v
   // ---------------- x partitioned solver: default P
   c->part_req = NS_PART_AUTO;
   {
-    // default: partitions of 8 rows (at most 32 per line, one per lane)
-    int P = nx / 8;
-    if (P < 1) P = 1;
-    if (P > 32) P = 32;
-    c->P = P;
-    c->M = nx / P;
-    if (st == NS_OK && !(c->M <= 16 || (P == 32 && (c->M == 32 || c->M == 64)))) {
+    // default: partitions of about 8 rows (at most 32 per line, one per lane)
+    const int P = x_default_partition(nx);
+    c->P = P > 0 ? P : 1;
+    c->M = nx / c->P;
+    if (st == NS_OK && P == 0) {
       st = NS_ERR_SIZE;
-      c->err = "nx too large for the partitioned x solver (nx/32 > 64)";
+      c->err = "nx has no partition shape of the x solver";
     }
   }
   if (st == NS_OK) st = build_x_tables(c);
   // ---------------- FFT twiddles, modified wavenumbers, Poisson y factors
   if (st == NS_OK) {
     const double PI = 3.14159265358979323846;
-    std::vector<double> tw(3 * nz), tx(3 * nx);
+    std::vector<double> tw(fft_twiddle_doubles(nz)), tx(fft_twiddle_doubles(nx));
     fft_twiddles(nz, tw.data());
     fft_twiddles(nx, tx.data());
     if (upload_d(c, c->twz, tw) != cudaSuccess) st = NS_ERR_CUDA;
@@ -844,8 +844,8 @@ ns_status ns_set_partition(ns_ctx* c, int dir, int P, int mode) {
   if (!c) return NS_ERR_ARG;
   if (dir != 0) return fail(c, NS_ERR_UNSUPPORTED, "only dir 0 (x) is partitioned");
   const int nx = c->cfg.nx;
-  const int M = is_pow2(P) && P <= 32 && nx % P == 0 ? nx / P : 0;
-  if (M == 0 || !(M <= 16 || (P == 32 && (M == 32 || M == 64)))) return fail(c, NS_ERR_ARG, "invalid partition count");
+  if (P < 1 || P > 32 || nx % P != 0 || !x_partition_ok(P, nx / P))
+    return fail(c, NS_ERR_ARG, "invalid partition count");
   if (mode != NS_PART_AUTO && mode != NS_PART_PPT && mode != NS_PART_PDD)
     return fail(c, NS_ERR_ARG, "invalid partition mode");
   if (capturing(c)) return fail(c, NS_ERR_STATE, "ns_set_partition during capture");
@@ -891,8 +891,7 @@ ns_status ns_autotune(ns_ctx* c) {
   int bestP = c->P, bestMode = c->part_req;
   float best = 1e30f;
   for (int P = 1; P <= 32; P <<= 1) {
-    if (nx % P || nx / P < 1) continue;
-    if (!(nx / P <= 16 || (P == 32 && (nx / P == 32 || nx / P == 64)))) continue;
+    if (nx % P || !x_partition_ok(P, nx / P)) continue;
     for (int mode : {NS_PART_AUTO, NS_PART_PPT}) {
       if (ns_set_partition(c, 0, P, mode) != NS_OK) continue;
       if (mode == NS_PART_PPT && c->part_mode != NS_PART_PPT) continue;

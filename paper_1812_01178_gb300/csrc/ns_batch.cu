@@ -181,7 +181,7 @@ ns_status ns_batch_init(ns_batch** out, const ns_config* cfgs, const ns_fields* 
   } else {
     if ((e = cudaMalloc(&b->ws, need)) != cudaSuccess) {
       delete b;
-      ns_set_thread_error("batch: cudaMalloc workspace failed");
+      ns_set_thread_error((std::string("batch: cudaMalloc workspace failed: ") + cudaGetErrorString(e)).c_str());
       return NS_ERR_CUDA;
     }
     b->own_ws = true;

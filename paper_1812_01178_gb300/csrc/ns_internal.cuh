@@ -8,21 +8,40 @@
 
 #include "../../include/ns.h"
 
-// Twiddles of the radix-4 DIT stages of the shared-memory FFT in FMA form (Goedecker's tangent
-// factorisation): for every stage that has combined sub-transforms of length Ns (Ns = 1, 4, ...
-// for even log2 N; 2, 8, ... for odd) and k < Ns, entry Ns + k holds the three pairs
-// {tan th, cos th}, {tan 2th, cos 2th}, {tan 3th, cos 3th / cos th} with th = 2 pi k / (4 Ns).
-// out has room for 3 N doubles (N / 2 entries of six); unused entries are zero.
+// FFT plan of a length N = 2^a 3^b: a | (b << 8), or -1 for any other N.
+inline __host__ __device__ int fft_plan(int N) {
+  if (N < 1) return -1;
+  int a = 0, b = 0;
+  while (N % 2 == 0) N /= 2, ++a;
+  while (N % 3 == 0) N /= 3, ++b;
+  return N == 1 ? (a | (b << 8)) : -1;
+}
+
+// Doubles in the twiddle table of a length-N FFT (fft_twiddles): six per entry, N entries.
+inline size_t fft_twiddle_doubles(int N) { return 6 * (size_t)N; }
+
+// Twiddles of the DIT stages of the shared-memory FFT in FMA form (Goedecker's tangent
+// factorisation), one entry of six doubles per (stage, k), at index Ns + k, where Ns is the
+// length of the sub-transforms the stage combines and k < Ns.  The stage order is a radix-2
+// stage (Ns = 1, no twiddles) when a is odd, a/2 radix-4 stages, then b radix-3 stages; the index
+// ranges [Ns, 2 Ns) of the stages are disjoint and end below 2N/3.
+//   radix 4, th = 2 pi k / (4 Ns): {tan th, cos th}, {tan 2th, cos 2th}, {tan 3th, cos 3th / cos th}
+//   radix 3, th = 2 pi k / (3 Ns): {tan th, cos th}, {tan 2th, cos 2th / cos th},
+//                                  {cos th / 2, (sqrt 3 / 2) cos th}
+// out has room for fft_twiddle_doubles(N); unused entries are zero.
 inline void fft_twiddles(int N, double* out) {
   const double PI = 3.14159265358979323846;
-  for (int q = 0; q < 3 * N; ++q) out[q] = 0.0;
-  int ln = 0;
-  while ((1 << ln) < N) ++ln;
-  for (int Ns = (ln & 1) ? 2 : 4; Ns < N; Ns <<= 2)
-    for (int k = 0; k < Ns; ++k) {
+  const double S3 = 0.86602540378443864676;
+  for (size_t q = 0; q < fft_twiddle_doubles(N); ++q) out[q] = 0.0;
+  const int plan = fft_plan(N);
+  if (plan < 0) return;
+  const int a = plan & 0xff, b = plan >> 8;
+  int Ns = (a & 1) ? 2 : 1;
+  for (int s = 0; s < (a >> 1); ++s, Ns *= 4)
+    for (int k = 0; k < Ns && Ns > 1; ++k) {
       const double th = 2.0 * PI * k / (4.0 * Ns);
       const double c1 = std::cos(th), c2 = std::cos(2.0 * th), c3 = std::cos(3.0 * th);
-      double* e = out + 6 * (Ns + k);
+      double* e = out + 6 * (size_t)(Ns + k);
       e[0] = std::tan(th);
       e[1] = c1;
       e[2] = std::tan(2.0 * th);
@@ -30,6 +49,40 @@ inline void fft_twiddles(int N, double* out) {
       e[4] = std::tan(3.0 * th);
       e[5] = c3 / c1;
     }
+  for (int s = 0; s < b; ++s, Ns *= 3)
+    for (int k = 0; k < Ns && Ns > 1; ++k) {
+      const double th = 2.0 * PI * k / (3.0 * Ns);
+      const double c1 = std::cos(th), c2 = std::cos(2.0 * th);
+      double* e = out + 6 * (size_t)(Ns + k);
+      e[0] = std::tan(th);
+      e[1] = c1;
+      e[2] = std::tan(2.0 * th);
+      e[3] = c2 / c1;
+      e[4] = 0.5 * c1;
+      e[5] = S3 * c1;
+    }
+}
+
+// Partition shapes the x solver is built for: P lanes (a power of two <= 32) of M rows, with
+// M <= 16 from {1, 2, 3, 4, 6, 8, 9, 12, 16} (rows in registers) or, at P = 32, the long-line
+// shapes M in {24, 32, 48, 64} (lines staged in shared memory).
+inline bool x_partition_ok(int P, int M) {
+  if (P < 1 || P > 32 || (P & (P - 1)) != 0) return false;
+  switch (M) {
+    case 1: case 2: case 3: case 4: case 6: case 8: case 9: case 12: case 16: return true;
+    case 24: case 32: case 48: case 64: return P == 32;
+    default: return false;
+  }
+}
+
+// Default partition count of an x line of nx rows: the largest admissible P with at least 8 rows
+// per partition, else the smallest admissible P; 0 if none is admissible.
+inline int x_default_partition(int nx) {
+  for (int P = 32; P >= 1; P >>= 1)
+    if (nx % P == 0 && nx / P >= 8 && x_partition_ok(P, nx / P)) return P;
+  for (int P = 1; P <= 32; P <<= 1)
+    if (nx % P == 0 && x_partition_ok(P, nx / P)) return P;
+  return 0;
 }
 
 #define NS_FULL_MASK 0xffffffffu

@@ -28,13 +28,12 @@ void* g_scratch[kMaxDevices] = {};  // device address of g_ns_static_scratch, pe
 
 // host staging for the small tables (static: no allocation at call time); guarded by g_mu
 double h_gc[NS_GC_COUNT * 1025];
-double h_twz[3 * 4096];
-double h_twx[3 * 4096];
+double h_twz[6 * 4096];
+double h_twx[6 * 4096];
 double h_lamx[4096];
 double h_lamz[2049];
 
 size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
-bool pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
 
 struct Regions {
   size_t spec, pois, gc, twz, twx, lamx, lamz, total;
@@ -51,9 +50,9 @@ Regions regions(int nx, int ny, int nz) {
   r.gc = o;
   o += al256((size_t)NS_GC_COUNT * (ny + 1) * 8);
   r.twz = o;
-  o += al256((size_t)nz * 24);
+  o += al256(fft_twiddle_doubles(nz) * 8);
   r.twx = o;
-  o += al256((size_t)nx * 24);
+  o += al256(fft_twiddle_doubles(nx) * 8);
   r.lamx = o;
   o += al256((size_t)nx * 8);
   r.lamz = o;
@@ -74,8 +73,9 @@ extern "C" ns_status ns_poisson_solve_static(const ns_config* cfg, const double*
   ns_set_thread_error("");
   if (!cfg || !cfg->yf || !u || !v || !w || !phi) return fail(NS_ERR_ARG, "NULL argument");
   const int nx = cfg->nx, ny = cfg->ny, nz = cfg->nz;
-  if (!pow2(nx) || nx < 8 || nx > 4096 || !pow2(nz) || nz < 8 || nz > 4096 || ny < 4 || ny > 1024)
-    return fail(NS_ERR_SIZE, "nx, nz must be powers of two in [8, 4096] and ny in [4, 1024]");
+  if (fft_plan(nx) < 0 || nx % 8 || nx < 8 || nx > 4096 || fft_plan(nz) < 0 || nz % 8 || nz < 8 || nz > 4096 ||
+      ny < 4 || ny > 1024)
+    return fail(NS_ERR_SIZE, "nx, nz must be 2^a 3^b (a >= 3) in [8, 4096] and ny in [4, 1024]");
   if (cfg->bc_x != 0) return fail(NS_ERR_UNSUPPORTED, "only periodic x is built");
   if (substep < -1 || substep > 2) return fail(NS_ERR_ARG, "substep must be -1, 0, 1 or 2");
   if (!(cfg->lx > 0) || !(cfg->lz > 0) || (substep >= 0 && !(cfg->dt > 0)))
@@ -136,8 +136,8 @@ extern "C" ns_status ns_poisson_solve_static(const ns_config* cfg, const double*
     size_t off;
     const void* src;
     size_t bytes;
-  } up[] = {{R.gc, h_gc, (size_t)NS_GC_COUNT * G * 8}, {R.twz, h_twz, (size_t)nz * 24},
-            {R.twx, h_twx, (size_t)nx * 24},           {R.lamx, h_lamx, (size_t)nx * 8},
+  } up[] = {{R.gc, h_gc, (size_t)NS_GC_COUNT * G * 8}, {R.twz, h_twz, fft_twiddle_doubles(nz) * 8},
+            {R.twx, h_twx, fft_twiddle_doubles(nx) * 8},           {R.lamx, h_lamx, (size_t)nx * 8},
             {R.lamz, h_lamz, (size_t)(nz / 2 + 1) * 8}};
   for (const auto& q : up)
     if ((e = cudaMemcpyAsync(base + q.off, q.src, q.bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess)

@@ -35,10 +35,20 @@ def test_library_exports_every_declared_symbol(libpath):
         assert hasattr(lib, name), name
 
 
-def test_invalid_config_rejected_without_gpu(libpath):
+@pytest.mark.parametrize("nx,nz,ok", [
+    (64, 32, True), (48, 32, True), (96, 24, True), (72, 216, True), (384, 96, True), (768, 8, True),
+    (1536, 48, True), (2048, 1024, True),
+    (40, 32, False),    # factor 5: not 2^a 3^b
+    (12, 32, False),    # a < 3
+    (64, 36, False),    # nz = 4 * 9: a < 3
+    (216, 32, False),   # 8 * 27: no partition shape (P <= 32 lanes of M rows)
+    (1152, 32, False),  # 128 * 9: M = 36 at P = 32 is not a built shape
+    (6144, 32, False),  # beyond 4096
+])
+def test_grid_sizes_accepted_and_rejected_without_gpu(libpath, nx, nz, ok):
+    """nx and nz are 2^a 3^b with a >= 3 (the mixed radix-2/4/3 FFT), and nx admits a partition
+    shape of the x solver; the check runs on the host (no device call)."""
     from paper_1812_01178_gb300 import inputs as I
     case, *_ = I.small_channel(64, 20, 32)
-    cfg = B.make_config(case)
-    assert B.ns_workspace_bytes(cfg) > 0
-    case.nx = 48  # not a power of two
-    assert B.ns_workspace_bytes(B.make_config(case)) == 0
+    case.nx, case.nz = nx, nz
+    assert (B.ns_workspace_bytes(B.make_config(case)) > 0) == ok
