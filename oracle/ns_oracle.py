@@ -549,12 +549,23 @@ def rhs(g, u, v, w, p, nprev, k, dt, re, fx):
     return r, N
 
 
-def substep(g, state, k, dt, re, fx):
+def pressure_update(p, phi, lap_phi, beta, pressure):
+    """p = p + phi (pressure="delta"), or the Kim & Moin (J. Comput. Phys. 59, 1985) form
+    p = p + phi - beta_k L phi with L = D G, the operator of the Poisson solve
+    (pressure="kim_moin")."""
+    if pressure == "delta":
+        return p + phi
+    if pressure == "kim_moin":
+        return p + phi - beta * lap_phi
+    raise ValueError(pressure)
+
+
+def substep(g, state, k, dt, re, fx, pressure="delta"):
     """One RK3 sub-step: RHS, ADI (x, y, z), u* = u + delta, Poisson, projection.
 
     state = dict(u, v, w, p, nprev); returns a new dict.  beta_k = alpha_k dt/(2 Re);
     the Poisson right-hand side is D u* / (alpha_k dt); u = u* - alpha_k dt G phi;
-    p = p + phi.
+    p = p + phi (or the Kim-Moin form, pressure_update).
     """
     u, v, w, p = state["u"], state["v"], state["w"], state["p"]
     r, N = rhs(g, u, v, w, p, state.get("nprev"), k, dt, re, fx)
@@ -565,16 +576,47 @@ def substep(g, state, k, dt, re, fx):
     scale = RK3_ALPHA[k] * dt
     phi = poisson_solve(g, divergence(g, us, vs, ws) / scale)
     un, vn, wn = project(g, us, vs, ws, phi, scale)
-    return dict(u=un, v=vn, w=wn, p=p + phi, nprev=N, phi=phi)
+    lap = divergence(g, *gradient(g, phi)) if pressure != "delta" else None
+    return dict(u=un, v=vn, w=wn, p=pressure_update(p, phi, lap, beta, pressure), nprev=N, phi=phi)
 
 
-def step(g, state, dt, re, fx, nsteps=1):
+def step(g, state, dt, re, fx, nsteps=1, pressure="delta"):
     """nsteps full time steps of three RK3 sub-steps each."""
     s = dict(state)
     for _ in range(nsteps):
         for k in range(3):
-            s = substep(g, s, k, dt, re, fx)
+            s = substep(g, s, k, dt, re, fx, pressure)
     return s
+
+
+# ----------------------------------------------------------------------------
+# Time step at a fixed CFL number (the paper's runs hold CFL = 1.0, Sec. 4)
+# ----------------------------------------------------------------------------
+# Reading: the paper gives no formula for its CFL number.  Here it is the convective one,
+# dt max over cells of |u|/dx + |v_c|/dy_j + |w|/dz, with u and w the values on the cell's lower
+# x and z faces and v_c the average of its two y faces; dt is set before every step from the
+# velocity at the start of the step and held for the three sub-steps.
+
+def convective_rate(g, u, v, w):
+    """max over cells of |u|/dx + |v_c|/dy_j + |w|/dz (so that CFL = dt * rate)."""
+    vc = 0.5 * (v[:, :-1, :] + v[:, 1:, :])
+    c = np.abs(u) / g.dx + np.abs(vc) / g.dy[None, :, None] + np.abs(w) / g.dz
+    return float(c.max())
+
+
+def step_cfl(g, state, cfl, re, fx, nsteps=1, pressure="delta", bl=False, u_conv=1.0):
+    """nsteps steps, each with dt = cfl / convective_rate(velocity at the start of the step).
+    Returns (state, list of the dt of each step)."""
+    s = dict(state)
+    dts = []
+    for _ in range(nsteps):
+        dt = cfl / convective_rate(g, s["u"], s["v"], s["w"])
+        dts.append(dt)
+        if bl:
+            s = step_bl(g, s, dt, re, fx, 1, u_conv, pressure)
+        else:
+            s = step(g, s, dt, re, fx, 1, pressure)
+    return s, dts
 
 
 # ----------------------------------------------------------------------------
@@ -814,7 +856,7 @@ def make_divergence_free_bl(g, u, v, w, bl):
     return u2, v2, w2, bl
 
 
-def substep_bl(g, state, k, dt, re, fx, u_conv=1.0):
+def substep_bl(g, state, k, dt, re, fx, u_conv=1.0, pressure="delta"):
     """One RK3 sub-step with inflow / convective outflow in x.  Order: RHS (boundary planes of the
     previous level), outflow update, ADI x (outflow increment on the last row) / y / z,
     u* = u + delta, outflow flux correction, Poisson, projection of interior faces, p += phi."""
@@ -834,12 +876,15 @@ def substep_bl(g, state, k, dt, re, fx, u_conv=1.0):
     bl_new["u_out"] = flux_correct_outflow(g, u[:, :, 0], bl_new["u_out"])
     phi = poisson_solve_bl(g, divergence_bl(g, us, vs, ws, bl_new) / scale)
     un, vn, wn = project_bl(g, us, vs, ws, phi, scale)
-    return dict(u=un, v=vn, w=wn, p=p + phi, nprev=N, phi=phi, bl=bl_new)
+    lap = None
+    if pressure != "delta":  # D G phi with zero normal gradient at the inflow and outflow faces
+        lap = divergence_bl(g, *gradient_bl(g, phi), dict(u_out=np.zeros((g.nz, g.ny))))
+    return dict(u=un, v=vn, w=wn, p=pressure_update(p, phi, lap, beta, pressure), nprev=N, phi=phi, bl=bl_new)
 
 
-def step_bl(g, state, dt, re, fx, nsteps=1, u_conv=1.0):
+def step_bl(g, state, dt, re, fx, nsteps=1, u_conv=1.0, pressure="delta"):
     s = dict(state)
     for _ in range(nsteps):
         for k in range(3):
-            s = substep_bl(g, s, k, dt, re, fx, u_conv)
+            s = substep_bl(g, s, k, dt, re, fx, u_conv, pressure)
     return s
