@@ -88,7 +88,17 @@ typedef struct {
   double dt;             /* time step, fixed for the lifetime of the context */
   int precision;         /* NS_FP64 or NS_MIXED */
   double u_conv;         /* convection speed U_c of the outflow condition (bc_x = 1 only) */
+  int pressure_update;   /* NS_PRESSURE_DELTA or NS_PRESSURE_KIM_MOIN */
 } ns_config;
+
+/* Pressure update of each sub-step after the projection (the paper names only the
+ * pseudo-pressure phi, Sec. 2.2):
+ *   NS_PRESSURE_DELTA    : p = p + phi.
+ *   NS_PRESSURE_KIM_MOIN : p = p + phi - beta_k L phi, beta_k = alpha_k dt / (2 Re), L = D G the
+ *                          operator of the Poisson solve (Kim & Moin, J. Comput. Phys. 59, 1985),
+ *                          which makes the pressure consistent to second order in time.
+ * The velocities are the same under both. */
+enum { NS_PRESSURE_DELTA = 0, NS_PRESSURE_KIM_MOIN = 1 };
 
 typedef struct {
   double* u;             /* device pointers, layouts above; updated in place */
@@ -147,6 +157,26 @@ ns_status ns_substep(ns_ctx* ctx, int substep);
 /* nsteps time steps of three sub-steps each (Table 1 counts one step = three sub-steps).
  * The three sub-steps are captured once as a CUDA graph and replayed. */
 ns_status ns_step(ns_ctx* ctx, int nsteps);
+
+/* Time step at a fixed CFL number (the paper's runs hold CFL = 1.0, Sec. 4).
+ *
+ * ns_convective_rate: *rate = max over cells of |u|/dx + |v_c|/dy_j + |w|/dz of the current
+ * fields, with u and w the values on the cell's lower x and z faces and v_c the average of its two
+ * y faces, so that the convective CFL number is dt * rate.  One device max-reduction on the
+ * context's stream, then a synchronising 8-byte read.  NS_ERR_STATE if the fields hold a
+ * non-finite value.
+ *
+ * ns_set_dt: make dt the time step of the following sub-steps.  Rebuilds every table that
+ * depends on dt (RHS rows, ADI factors and PDD/PPT tables, with the PDD admissibility test of the
+ * automatic mode redone) and drops the captured graphs; the next ns_step captures again.  dt must
+ * be positive and finite (NS_ERR_ARG).  Synchronises the stream.
+ *
+ * ns_step_cfl: nsteps steps, each preceded by dt = cfl / rate of the velocity at its start
+ * (ns_convective_rate, then ns_set_dt when dt changes).  dts, if not NULL, receives the nsteps
+ * values of dt (host array).  cfl must be positive and finite.  One host round trip per step. */
+ns_status ns_convective_rate(ns_ctx* ctx, double* rate);
+ns_status ns_set_dt(ns_ctx* ctx, double dt);
+ns_status ns_step_cfl(ns_ctx* ctx, int nsteps, double cfl, double* dts);
 
 /* ns_step with per-kernel timing: replays a captured step that also records a CUDA event before
  * every kernel (and after the last) on the context's stream, waits for each step, and adds each

@@ -17,6 +17,7 @@ LIB_PATH = os.path.join(HERE, "_lib", "libns_gb300.so")
 NS_OK, NS_ERR_ARG, NS_ERR_SIZE, NS_ERR_CUDA, NS_ERR_TIMEOUT, NS_ERR_STATE, NS_ERR_UNSUPPORTED = range(7)
 NS_FP64, NS_MIXED = 0, 1
 NS_PART_AUTO, NS_PART_PPT, NS_PART_PDD = 0, 1, 2
+NS_PRESSURE_DELTA, NS_PRESSURE_KIM_MOIN = 0, 1
 NS_BUF_RU, NS_BUF_RV, NS_BUF_RW, NS_BUF_NU, NS_BUF_NV, NS_BUF_NW, NS_BUF_PHI, NS_BUF_SPEC = range(8)
 
 STATUS_NAMES = {0: "NS_OK", 1: "NS_ERR_ARG", 2: "NS_ERR_SIZE", 3: "NS_ERR_CUDA", 4: "NS_ERR_TIMEOUT",
@@ -24,7 +25,7 @@ STATUS_NAMES = {0: "NS_OK", 1: "NS_ERR_ARG", 2: "NS_ERR_SIZE", 3: "NS_ERR_CUDA",
 
 # Every symbol declared in include/ns.h.
 EXPORTS = ["ns_workspace_bytes", "ns_init", "ns_rhs", "ns_adi_sweep", "ns_poisson_solve", "ns_project",
-           "ns_substep", "ns_step", "ns_step_profiled", "ns_kernel_count", "ns_kernel_name", "ns_step_host", "ns_make_divergence_free", "ns_set_partition",
+           "ns_substep", "ns_step", "ns_convective_rate", "ns_set_dt", "ns_step_cfl", "ns_step_profiled", "ns_kernel_count", "ns_kernel_name", "ns_step_host", "ns_make_divergence_free", "ns_set_partition",
            "ns_get_partition", "ns_autotune", "ns_get_buffer", "ns_poisson_solve_static", "ns_sync",
            "ns_last_error", "ns_destroy", "ns_batch_workspace_bytes", "ns_batch_init", "ns_batch_step",
            "ns_batch_launches_per_step", "ns_batch_autotune", "ns_batch_set_partition", "ns_batch_instance",
@@ -38,7 +39,7 @@ class ns_config(C.Structure):
                 ("yf", C.POINTER(C.c_double)),
                 ("bc_x", C.c_int), ("bc_ytop", C.c_int),
                 ("re", C.c_double), ("fx", C.c_double), ("dt", C.c_double),
-                ("precision", C.c_int), ("u_conv", C.c_double)]
+                ("precision", C.c_int), ("u_conv", C.c_double), ("pressure_update", C.c_int)]
 
 
 class ns_fields(C.Structure):
@@ -73,6 +74,9 @@ def lib(path: str = LIB_PATH):
     for name in ("ns_rhs", "ns_poisson_solve", "ns_project", "ns_substep", "ns_step"):
         getattr(L, name).argtypes = [vp, i]
     L.ns_adi_sweep.argtypes = [vp, i, i]
+    L.ns_convective_rate.argtypes = [vp, P(d)]
+    L.ns_set_dt.argtypes = [vp, d]
+    L.ns_step_cfl.argtypes = [vp, i, d, P(d)]
     L.ns_step_host.argtypes = [vp, vp, vp, vp, vp, i]
     L.ns_step_profiled.argtypes = [vp, i, P(C.c_float), i]
     L.ns_kernel_count.argtypes = []
@@ -117,7 +121,7 @@ def make_config(case, precision=None):
     cfg = ns_config(case.nx, case.ny, case.nz, case.lx, case.lz,
                     yf.ctypes.data_as(C.POINTER(C.c_double)), case.bc_x, case.bc_ytop,
                     case.re, case.fx, case.dt, case.precision if precision is None else precision,
-                    getattr(case, "u_conv", 1.0))
+                    getattr(case, "u_conv", 1.0), getattr(case, "pressure_update", NS_PRESSURE_DELTA))
     cfg._yf_keep = yf
     return cfg
 
@@ -162,6 +166,22 @@ def ns_substep(ctx, k):
 
 def ns_step(ctx, nsteps):
     _check(ctx, lib().ns_step(ctx, nsteps))
+
+
+def ns_convective_rate(ctx):
+    r = C.c_double()
+    _check(ctx, lib().ns_convective_rate(ctx, C.byref(r)))
+    return r.value
+
+
+def ns_set_dt(ctx, dt):
+    _check(ctx, lib().ns_set_dt(ctx, dt))
+
+
+def ns_step_cfl(ctx, nsteps, cfl):
+    dts = (C.c_double * max(nsteps, 1))()
+    _check(ctx, lib().ns_step_cfl(ctx, nsteps, cfl, dts))
+    return list(dts)[:nsteps]
 
 
 def ns_step_profiled(ctx, nsteps):
@@ -309,6 +329,15 @@ class Solver:
 
     def step_profiled(self, n=1):
         return ns_step_profiled(self.ctx, n)
+
+    def convective_rate(self):
+        return ns_convective_rate(self.ctx)
+
+    def set_dt(self, dt):
+        ns_set_dt(self.ctx, dt)
+
+    def step_cfl(self, n, cfl):
+        return ns_step_cfl(self.ctx, n, cfl)
 
     def make_divergence_free(self):
         ns_make_divergence_free(self.ctx)

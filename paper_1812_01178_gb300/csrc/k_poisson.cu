@@ -448,10 +448,12 @@ struct ProjectK {
     int update_p;
     double s;
     int bl;
+    double beta_p;  // beta_k of the Kim-Moin pressure update (0: p += phi)
+    double idx2, idz2;
   };
   static constexpr int kThreads = 128;
   static constexpr int kMinBlocks = 16;
-  static Args make(double* u, double* v, double* w, double* p, const double* phi, const double* gc, int nx, int ny, int nz, double sx, double sz, int update_p, double s, int bl) { return Args{u, v, w, p, phi, gc, nx, ny, nz, sx, sz, update_p, s, bl}; }
+  static Args make(double* u, double* v, double* w, double* p, const double* phi, const double* gc, int nx, int ny, int nz, double sx, double sz, int update_p, double s, int bl, double beta_p, double idx2, double idz2) { return Args{u, v, w, p, phi, gc, nx, ny, nz, sx, sz, update_p, s, bl, beta_p, idx2, idz2}; }
   static __device__ __forceinline__ void run(const Args& a_, const dim3 bid_, const dim3 gdim_) {
     double* __restrict__ u = a_.u;
     double* __restrict__ v = a_.v;
@@ -482,7 +484,30 @@ struct ProjectK {
     const double f0 = __ldg(phi + cc);
     if (!(bl && i == 0)) u[cc] -= sx * (f0 - __ldg(phi + k * pl + (long)j * nx + im));  // inflow face fixed
     w[cc] -= sz * (f0 - __ldg(phi + km * pl + (long)j * nx + i));
-    if (update_p) p[cc] += f0;
+    if (update_p) {
+      double dp = f0;
+      if (a_.beta_p != 0.0) {
+        // Kim-Moin: p += phi - beta_k (D G phi), with G phi = 0 on the walls (PA_0 = PC_{ny-1} = 0)
+        // and, with inflow / outflow, on the x = 0 and x = Lx faces
+        const long row = k * pl + (long)j * nx;
+        double lx;
+        if (bl) {
+          const double ge = (i + 1 < nx) ? __ldg(phi + row + i + 1) - f0 : 0.0;
+          const double gw = (i > 0) ? f0 - __ldg(phi + row + i - 1) : 0.0;
+          lx = (ge - gw) * a_.idx2;
+        } else {
+          const int ip = (i + 1 == nx) ? 0 : i + 1;
+          lx = ((__ldg(phi + row + ip) - f0) - (f0 - __ldg(phi + row + im))) * a_.idx2;
+        }
+        const double ly = (j > 0 ? __ldg(gc + GC_PA * (ny + 1) + j) * (__ldg(phi + cc - nx) - f0) : 0.0) +
+                          (j + 1 < ny ? __ldg(gc + GC_PC * (ny + 1) + j) * (__ldg(phi + cc + nx) - f0) : 0.0);
+        const int kp = (k + 1 == nz) ? 0 : k + 1;
+        const double lz = ((__ldg(phi + kp * pl + (long)j * nx + i) - f0) - (f0 - __ldg(phi + km * pl + (long)j * nx + i))) *
+                          a_.idz2;
+        dp = f0 - a_.beta_p * (lx + ly + lz);
+      }
+      p[cc] += dp;
+    }
   }
   if (j >= 1 && j < ny) {
     const double ihc = __ldg(gc + GC_IHC * (ny + 1) + j);
@@ -620,6 +645,52 @@ __global__ void __launch_bounds__(1024) flux_correct_kernel(const double* __rest
 }
 
 // ------------------------------------------------------------------------------------------
+// convective rate max over cells of |u|/dx + |v_c|/dy_j + |w|/dz (u, w on the cell's lower faces,
+// v_c the mean of its two y faces), the measure of the fixed-CFL time step.  Values are >= 0, so
+// their bit patterns order like the values and one atomicMax on the bits combines the blocks in
+// any order with the same result.  A non-finite value stores the bits of a NaN (above every
+// finite value) so that the host sees it.
+// ------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) rate_kernel(const double* __restrict__ u, const double* __restrict__ v,
+                                                   const double* __restrict__ w, const double* __restrict__ gc,
+                                                   int nx, int ny, int nz, double dx, double dz,
+                                                   unsigned long long* __restrict__ out) {
+  const long n = (long)nx * ny * nz;
+  const double* dy = gc + GC_DY * (ny + 1);
+  double m = 0.0;
+  bool bad = false;
+  for (long q = (long)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (long)gridDim.x * blockDim.x) {
+    const long kj = q / nx;
+    const int i = (int)(q - kj * nx);
+    const int k = (int)(kj / ny);
+    const int j = (int)(kj - (long)k * ny);
+    const long vq = ((long)k * (ny + 1) + j) * nx + i;
+    const double vc = 0.5 * (__ldg(v + vq) + __ldg(v + vq + nx));
+    const double r = fabs(__ldg(u + q)) / dx + fabs(vc) / __ldg(dy + j) + fabs(__ldg(w + q)) / dz;
+    bad |= !(r <= 1.7976931348623157e308);
+    m = fmax(m, r);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    m = fmax(m, __shfl_xor_sync(NS_FULL_MASK, m, o));
+    bad |= __shfl_xor_sync(NS_FULL_MASK, (int)bad, o) != 0;
+  }
+  __shared__ double sm[8];
+  __shared__ int sb[8];
+  if ((threadIdx.x & 31) == 0) {
+    sm[threadIdx.x >> 5] = m;
+    sb[threadIdx.x >> 5] = bad;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int q = 1; q < (int)(blockDim.x >> 5); ++q) {
+      m = fmax(m, sm[q]);
+      bad |= sb[q] != 0;
+    }
+    atomicMax(out, bad ? 0x7FF8000000000000ull : (unsigned long long)__double_as_longlong(m));
+  }
+}
+
+// ------------------------------------------------------------------------------------------
 // factor table of the y systems: per (kx, kz, j): (1/pivot_j, c_j/pivot_j).  Init only.
 // ------------------------------------------------------------------------------------------
 __global__ void pois_factor_kernel(double2* __restrict__ fac, const double* __restrict__ gc,
@@ -657,6 +728,14 @@ cudaError_t poisson_set_attributes() {
   set_smem_limit<FftxK<1>>(200 * 1024);
   cudaFuncSetAttribute(dctx_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   cudaFuncSetAttribute(dctx_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_convective_rate(ns_ctx* c) {
+  cudaError_t e = cudaMemsetAsync(c->rate, 0, sizeof(unsigned long long), c->launch);
+  if (e != cudaSuccess) return e;
+  rate_kernel<<<4 * c->num_sms, 256, 0, c->launch>>>(c->f.u, c->f.v, c->f.w, c->gc, c->cfg.nx, c->cfg.ny, c->cfg.nz,
+                                                     c->dx, c->dz, c->rate);
   return cudaGetLastError();
 }
 
@@ -762,8 +841,11 @@ cudaError_t stage_project(LaunchSink& s, int k) {
   const double sc = (k >= 0) ? NS_ALPHA[k] * c->cfg.dt : 1.0;
   const long plane = (long)nx * (ny + 1);
   dim3 grid((unsigned)((plane + 127) / 128), nz);
+  const double inv_re = c->cfg.re > 0 ? 1.0 / c->cfg.re : 0.0;
+  const double beta_p = (k >= 0 && c->cfg.pressure_update == NS_PRESSURE_KIM_MOIN) ? sc * inv_re / 2.0 : 0.0;
   return emit<ProjectK>(s, ProjectK::make(c->f.u, c->f.v, c->f.w, c->f.p, c->phi, c->gc, nx, ny, nz, sc / c->dx,
-                                          sc / c->dz, k >= 0 ? 1 : 0, sc, c->bl),
+                                          sc / c->dz, k >= 0 ? 1 : 0, sc, c->bl, beta_p, 1.0 / (c->dx * c->dx),
+                                          1.0 / (c->dz * c->dz)),
                         grid, dim3(128), 0);
 }
 

@@ -25,6 +25,8 @@ std::string check_cfg(const ns_config* c, ns_status* kind = nullptr) {
   if (c->bc_x != 0 && c->bc_x != 1) return "bc_x must be 0 or 1";
   if (c->bc_ytop != 0 && c->bc_ytop != 1) return "bc_ytop must be 0 or 1";
   if (c->precision != NS_FP64 && c->precision != NS_MIXED) return "precision must be NS_FP64 or NS_MIXED";
+  if (c->pressure_update != NS_PRESSURE_DELTA && c->pressure_update != NS_PRESSURE_KIM_MOIN)
+    return "pressure_update must be NS_PRESSURE_DELTA or NS_PRESSURE_KIM_MOIN";
   k = NS_ERR_SIZE;
   if (fft_plan(c->nx) < 0 || c->nx % 8 || c->nx < 8 || c->nx > 4096)
     return "nx must be 2^a 3^b with a >= 3, in [8, 4096]";
@@ -319,6 +321,103 @@ ns_status build_x_tables(ns_ctx* c) {
   return NS_OK;
 }
 
+// Tables that depend on dt: the RHS rows pre-multiplied by the sub-step constants (FP64 and an
+// FP32 copy) and the ADI y and z factors of every sub-step.  The x tables are build_x_tables.
+ns_status build_dt_tables(ns_ctx* c) {
+  const int ny = c->cfg.ny, nz = c->cfg.nz;
+  const int G = ny + 1;
+  char* base = (char*)c->ws;
+  auto GCv = [&](int f, int j) -> double { return c->gc_h[(size_t)f * G + j]; };
+  ns_status st = NS_OK;
+  for (int k = 0; k < 3 && st == NS_OK; ++k) {
+    c->rtab[k] = (double*)(base + c->lay.off[LB_RTAB] + k * al256((size_t)RT_COUNT * G * 8));
+    const double inv_re = c->cfg.re > 0 ? 1.0 / c->cfg.re : 0.0;
+    const double cl = c->cfg.dt * NS_ALPHA[k] * inv_re;
+    const double dd = 2.0 / (c->dx * c->dx) + 2.0 / (c->dz * c->dz);
+    std::vector<double> rt((size_t)RT_COUNT * G, 0.0);
+    auto RT = [&](int f, int j) -> double& { return rt[(size_t)f * G + j]; };
+    for (int j = 0; j < ny; ++j) {
+      RT(RT_AC, j) = cl * GCv(GC_AC, j);
+      RT(RT_CC, j) = cl * GCv(GC_CC, j);
+      RT(RT_DC, j) = -cl * (dd + GCv(GC_AC, j) + GCv(GC_CC, j));
+      RT(RT_HIDY, j) = 0.5 * GCv(GC_IDY, j);
+    }
+    for (int j = 1; j < ny; ++j) {
+      RT(RT_AF, j) = cl * GCv(GC_AF, j);
+      RT(RT_CF, j) = cl * GCv(GC_CF, j);
+      RT(RT_DF, j) = -cl * (dd + GCv(GC_AF, j) + GCv(GC_CF, j));
+      RT(RT_CGY, j) = -c->cfg.dt * NS_ALPHA[k] * GCv(GC_IHC, j);
+      RT(RT_QIHC, j) = 0.25 * GCv(GC_IHC, j);
+    }
+    if (upload_d(c, c->rtab[k], rt) != cudaSuccess) st = NS_ERR_CUDA;
+    c->rtabf[k] = (float*)(base + c->lay.off[LB_RTAB] + 3 * al256((size_t)RT_COUNT * G * 8) +
+                           k * al256((size_t)RT_COUNT * G * 4));
+    {
+      std::vector<float> rf(rt.begin(), rt.end());
+      if (cudaMemcpy(c->rtabf[k], rf.data(), rf.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess) st = NS_ERR_CUDA;
+    }
+  }
+  // ADI y and z factors per sub-step
+  for (int k = 0; k < 3 && st == NS_OK; ++k) {
+    const double beta = beta_of(c, k);
+    {  // centres (u, w): rows j = 0..ny-1
+      std::vector<double> a(ny), b(ny), cc(ny), inv, ainv, cp;
+      for (int j = 0; j < ny; ++j) {
+        a[j] = -beta * GCv(GC_AC, j);
+        cc[j] = -beta * GCv(GC_CC, j);
+        b[j] = 1.0 + beta * (GCv(GC_AC, j) + GCv(GC_CC, j));
+      }
+      thomas_factors(a, b, cc, inv, ainv, cp);
+      std::vector<double> t;
+      t.insert(t.end(), inv.begin(), inv.end());
+      t.insert(t.end(), ainv.begin(), ainv.end());
+      t.insert(t.end(), cp.begin(), cp.end());
+      if (upload(c, c->ytab[k][0], t) != cudaSuccess) st = NS_ERR_CUDA;
+    }
+    {  // faces (v): rows j = 1..ny-1
+      const int n = ny - 1;
+      std::vector<double> a(n), b(n), cc(n), inv, ainv, cp;
+      for (int q = 0; q < n; ++q) {
+        const int j = q + 1;
+        a[q] = -beta * GCv(GC_AF, j);
+        cc[q] = -beta * GCv(GC_CF, j);
+        b[q] = 1.0 + beta * (GCv(GC_AF, j) + GCv(GC_CF, j));
+      }
+      thomas_factors(a, b, cc, inv, ainv, cp);
+      std::vector<double> t;
+      t.insert(t.end(), inv.begin(), inv.end());
+      t.insert(t.end(), ainv.begin(), ainv.end());
+      t.insert(t.end(), cp.begin(), cp.end());
+      if (upload(c, c->ytab[k][1], t) != cudaSuccess) st = NS_ERR_CUDA;
+    }
+    {  // z: cyclic rows (-r, 1 + 2r, -r) by Sherman-Morrison
+      const double r = beta / (c->dz * c->dz);
+      const double lo = -r, di = 1.0 + 2.0 * r, up = -r;
+      const double gam = -di, alpha = up /* A[n-1][0] */, bet = lo /* A[0][n-1] */;
+      std::vector<double> a(nz, lo), b(nz, di), cc(nz, up), inv, ainv, cp;
+      b[0] = di - gam;
+      b[nz - 1] = di - alpha * bet / gam;
+      thomas_factors(a, b, cc, inv, ainv, cp);
+      std::vector<double> s(nz, 0.0);
+      s[0] = gam;
+      s[nz - 1] = alpha;
+      std::vector<double> q = thomas_apply(inv, ainv, cp, s);
+      const double bg = bet / gam;
+      const double fac = 1.0 / (1.0 + q[0] + bg * q[nz - 1]);
+      std::vector<double> t;
+      t.insert(t.end(), inv.begin(), inv.end());
+      t.insert(t.end(), ainv.begin(), ainv.end());
+      t.insert(t.end(), cp.begin(), cp.end());
+      t.insert(t.end(), q.begin(), q.end());
+      t.push_back(fac);
+      t.push_back(bg);
+      if (upload(c, c->ztab[k], t) != cudaSuccess) st = NS_ERR_CUDA;
+    }
+  }
+  if (st == NS_OK && cudaStreamSynchronize(c->stream) != cudaSuccess) st = NS_ERR_CUDA;
+  return st;
+}
+
 void drop_graph(ns_ctx* c) {
   if (c->have_graph) {
     cudaGraphExecDestroy(c->gexec);
@@ -512,6 +611,7 @@ ns_status ns_init(ns_ctx** out, const ns_config* cfg, const ns_fields* fields, v
   double* lamx_d = (double*)(base + c->lay.off[LB_LAMX]);
   for (int q = 0; q < 3; ++q) c->dout[q] = (double*)(base + c->lay.off[LB_DOUT] + q * al256((size_t)(ny + 1) * nz * 8));
   c->flux = (double*)(base + c->lay.off[LB_DOUT] + 3 * al256((size_t)(ny + 1) * nz * 8));
+  c->rate = (unsigned long long*)(c->flux + 4);
   c->twd = (double2*)(base + c->lay.off[LB_TWD]);
   double* lamz_d = (double*)(base + c->lay.off[LB_LAMZ]);
 
@@ -551,6 +651,7 @@ ns_status ns_init(ns_ctx** out, const ns_config* cfg, const ns_fields* fields, v
   for (int j = 1; j < ny; ++j) GCv(GC_PA, j) = 1.0 / (dy[j] * (yc[j] - yc[j - 1]));
   for (int j = 0; j + 1 < ny; ++j) GCv(GC_PC, j) = 1.0 / (dy[j] * (yc[j + 1] - yc[j]));
   ns_status st = NS_OK;
+  c->gc_h = gc;
   if (upload_d(c, c->gc, gc) != cudaSuccess) st = NS_ERR_CUDA;
 
   // ---------------- RHS assembly coefficients per sub-step (tiled kernel)
@@ -561,91 +662,7 @@ ns_status ns_init(ns_ctx** out, const ns_config* cfg, const ns_fields* fields, v
     cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev);
     c->rhs_bps[0] = c->rhs_bps[1] = 1;
   }
-  for (int k = 0; k < 3 && st == NS_OK; ++k) {
-    c->rtab[k] = (double*)(base + c->lay.off[LB_RTAB] + k * al256((size_t)RT_COUNT * G * 8));
-    const double inv_re = cfg->re > 0 ? 1.0 / cfg->re : 0.0;
-    const double cl = cfg->dt * NS_ALPHA[k] * inv_re;
-    const double dd = 2.0 / (c->dx * c->dx) + 2.0 / (c->dz * c->dz);
-    std::vector<double> rt((size_t)RT_COUNT * G, 0.0);
-    auto RT = [&](int f, int j) -> double& { return rt[(size_t)f * G + j]; };
-    for (int j = 0; j < ny; ++j) {
-      RT(RT_AC, j) = cl * GCv(GC_AC, j);
-      RT(RT_CC, j) = cl * GCv(GC_CC, j);
-      RT(RT_DC, j) = -cl * (dd + GCv(GC_AC, j) + GCv(GC_CC, j));
-      RT(RT_HIDY, j) = 0.5 * GCv(GC_IDY, j);
-    }
-    for (int j = 1; j < ny; ++j) {
-      RT(RT_AF, j) = cl * GCv(GC_AF, j);
-      RT(RT_CF, j) = cl * GCv(GC_CF, j);
-      RT(RT_DF, j) = -cl * (dd + GCv(GC_AF, j) + GCv(GC_CF, j));
-      RT(RT_CGY, j) = -cfg->dt * NS_ALPHA[k] * GCv(GC_IHC, j);
-      RT(RT_QIHC, j) = 0.25 * GCv(GC_IHC, j);
-    }
-    if (upload_d(c, c->rtab[k], rt) != cudaSuccess) st = NS_ERR_CUDA;
-    c->rtabf[k] = (float*)(base + c->lay.off[LB_RTAB] + 3 * al256((size_t)RT_COUNT * G * 8) +
-                           k * al256((size_t)RT_COUNT * G * 4));
-    {
-      std::vector<float> rf(rt.begin(), rt.end());
-      if (cudaMemcpy(c->rtabf[k], rf.data(), rf.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess) st = NS_ERR_CUDA;
-    }
-  }
-  // ---------------- ADI y and z factors per sub-step
-  for (int k = 0; k < 3 && st == NS_OK; ++k) {
-    const double beta = beta_of(c, k);
-    {  // centres (u, w): rows j = 0..ny-1
-      std::vector<double> a(ny), b(ny), cc(ny), inv, ainv, cp;
-      for (int j = 0; j < ny; ++j) {
-        a[j] = -beta * GCv(GC_AC, j);
-        cc[j] = -beta * GCv(GC_CC, j);
-        b[j] = 1.0 + beta * (GCv(GC_AC, j) + GCv(GC_CC, j));
-      }
-      thomas_factors(a, b, cc, inv, ainv, cp);
-      std::vector<double> t;
-      t.insert(t.end(), inv.begin(), inv.end());
-      t.insert(t.end(), ainv.begin(), ainv.end());
-      t.insert(t.end(), cp.begin(), cp.end());
-      if (upload(c, c->ytab[k][0], t) != cudaSuccess) st = NS_ERR_CUDA;
-    }
-    {  // faces (v): rows j = 1..ny-1
-      const int n = ny - 1;
-      std::vector<double> a(n), b(n), cc(n), inv, ainv, cp;
-      for (int q = 0; q < n; ++q) {
-        const int j = q + 1;
-        a[q] = -beta * GCv(GC_AF, j);
-        cc[q] = -beta * GCv(GC_CF, j);
-        b[q] = 1.0 + beta * (GCv(GC_AF, j) + GCv(GC_CF, j));
-      }
-      thomas_factors(a, b, cc, inv, ainv, cp);
-      std::vector<double> t;
-      t.insert(t.end(), inv.begin(), inv.end());
-      t.insert(t.end(), ainv.begin(), ainv.end());
-      t.insert(t.end(), cp.begin(), cp.end());
-      if (upload(c, c->ytab[k][1], t) != cudaSuccess) st = NS_ERR_CUDA;
-    }
-    {  // z: cyclic rows (-r, 1 + 2r, -r) by Sherman-Morrison
-      const double r = beta / (c->dz * c->dz);
-      const double lo = -r, di = 1.0 + 2.0 * r, up = -r;
-      const double gam = -di, alpha = up /* A[n-1][0] */, bet = lo /* A[0][n-1] */;
-      std::vector<double> a(nz, lo), b(nz, di), cc(nz, up), inv, ainv, cp;
-      b[0] = di - gam;
-      b[nz - 1] = di - alpha * bet / gam;
-      thomas_factors(a, b, cc, inv, ainv, cp);
-      std::vector<double> s(nz, 0.0);
-      s[0] = gam;
-      s[nz - 1] = alpha;
-      std::vector<double> q = thomas_apply(inv, ainv, cp, s);
-      const double bg = bet / gam;
-      const double fac = 1.0 / (1.0 + q[0] + bg * q[nz - 1]);
-      std::vector<double> t;
-      t.insert(t.end(), inv.begin(), inv.end());
-      t.insert(t.end(), ainv.begin(), ainv.end());
-      t.insert(t.end(), cp.begin(), cp.end());
-      t.insert(t.end(), q.begin(), q.end());
-      t.push_back(fac);
-      t.push_back(bg);
-      if (upload(c, c->ztab[k], t) != cudaSuccess) st = NS_ERR_CUDA;
-    }
-  }
+  if (st == NS_OK) st = build_dt_tables(c);
   // ---------------- x partitioned solver: default P
   c->part_req = NS_PART_AUTO;
   {
@@ -776,6 +793,58 @@ ns_status ns_step(ns_ctx* c, int nsteps) {
   cudaError_t e;
   for (int s = 0; s < nsteps; ++s)
     if ((e = cudaGraphLaunch(c->gexec, c->stream)) != cudaSuccess) return cuda_fail(c, e, "graph launch");
+  return NS_OK;
+}
+
+ns_status ns_convective_rate(ns_ctx* c, double* rate) {
+  if (!c || !rate) return NS_ERR_ARG;
+  if (capturing(c)) return fail(c, NS_ERR_STATE, "ns_convective_rate during capture");
+  cudaError_t e = launch_convective_rate(c);
+  if (e != cudaSuccess) return cuda_fail(c, e, "convective rate");
+  unsigned long long bits = 0;
+  if ((e = cudaMemcpyAsync(&bits, c->rate, sizeof(bits), cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(c->stream)) != cudaSuccess)
+    return cuda_fail(c, e, "convective rate read");
+  double r;
+  memcpy(&r, &bits, sizeof(r));
+  if (!std::isfinite(r)) return fail(c, NS_ERR_STATE, "the velocity field holds a non-finite value");
+  *rate = r;
+  return NS_OK;
+}
+
+ns_status ns_set_dt(ns_ctx* c, double dt) {
+  if (!c) return NS_ERR_ARG;
+  if (!(dt > 0.0) || !std::isfinite(dt)) return fail(c, NS_ERR_ARG, "dt must be positive and finite");
+  if (capturing(c)) return fail(c, NS_ERR_STATE, "ns_set_dt during capture");
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return fail(c, NS_ERR_CUDA, "sync");
+  const double old = c->cfg.dt;
+  c->cfg.dt = dt;
+  ns_status s = build_dt_tables(c);
+  if (s == NS_OK) s = build_x_tables(c);
+  drop_graph(c);
+  if (s != NS_OK) {
+    c->cfg.dt = old;
+    build_dt_tables(c);
+    build_x_tables(c);
+    return fail(c, s, "rebuilding the dt tables failed");
+  }
+  return NS_OK;
+}
+
+ns_status ns_step_cfl(ns_ctx* c, int nsteps, double cfl, double* dts) {
+  if (!c) return NS_ERR_ARG;
+  if (nsteps < 0) return fail(c, NS_ERR_ARG, "nsteps must be >= 0");
+  if (!(cfl > 0.0) || !std::isfinite(cfl)) return fail(c, NS_ERR_ARG, "cfl must be positive and finite");
+  for (int n = 0; n < nsteps; ++n) {
+    double rate = 0.0;
+    ns_status s = ns_convective_rate(c, &rate);
+    if (s != NS_OK) return s;
+    if (!(rate > 0.0)) return fail(c, NS_ERR_STATE, "fluid at rest: no convective time step");
+    const double dt = cfl / rate;
+    if (dt != c->cfg.dt && (s = ns_set_dt(c, dt)) != NS_OK) return s;
+    if (dts) dts[n] = dt;
+    if ((s = ns_step(c, 1)) != NS_OK) return s;
+  }
   return NS_OK;
 }
 

@@ -172,6 +172,8 @@ struct ns_ctx {
   double* dout[3];          // outflow-plane increments of the current sub-step (u, v, w)
   double2* twd;             // exp(-i pi l / (2 nx)), l < nx: post-twiddles of the x cosine transform
   double* flux;             // [0]: inflow flux, [1]: last outflow correction (diagnostics)
+  unsigned long long* rate; // bits of the convective rate of ns_convective_rate (in the flux block)
+  std::vector<double> gc_h; // host copy of the grid coefficients (tables are rebuilt when dt changes)
   int num_sms;
   int rhs_bps[2];           // resident blocks per SM of the tiled RHS (FP64, FP32)
   // partitioned x solver
@@ -378,6 +380,7 @@ cudaError_t launch_project(ns_ctx* c, int k);
 cudaError_t launch_outflow(ns_ctx* c, int k);        // convective outflow update + increments
 cudaError_t launch_flux_correct(ns_ctx* c, int k);   // outflow volume flux := inflow flux
 cudaError_t launch_pois_factor(ns_ctx* c, const double* lamx, const double* lamz);
+cudaError_t launch_convective_rate(ns_ctx* c);  // max-reduction into c->rate (zeroed first)
 cudaError_t poisson_set_attributes();  // once per process and device, outside any capture
 
 // Sets the message ns_last_error(NULL) returns on this thread.

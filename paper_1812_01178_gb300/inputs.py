@@ -98,6 +98,7 @@ class Case:
     bc_ytop: int = 0       # 0 no-slip wall, 1 stress-free
     precision: int = 0     # 0 FP64, 1 mixed
     u_conv: float = 1.0
+    pressure_update: int = 0  # 0: p += phi; 1: Kim-Moin form
 
     def cells(self) -> int:
         return self.nx * self.ny * self.nz

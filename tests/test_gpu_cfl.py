@@ -1,0 +1,143 @@
+"""Fixed-CFL time step (convective rate reduction, dt changes) and the Kim-Moin pressure update:
+the CUDA path through the C ABI against the FP64 oracle."""
+import ctypes
+import math
+
+import numpy as np
+import pytest
+
+from tests.gpu_common import B, O, field_rel_errors, need_gpu, torch
+from paper_1812_01178_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    need_gpu()
+
+
+def _projected(shape, seed, **kw):
+    case, u, v, w, p = I.small_channel(*shape, seed=seed, **kw)
+    g = O.Grid.from_case(case)
+    u, v, w = O.make_divergence_free(g, u, v, w)
+    return case, g, u, v, w, p
+
+
+@pytest.mark.parametrize("shape", [(64, 37, 32), (96, 20, 24), (8, 5, 8)])
+def test_convective_rate_equals_the_oracle(shape):
+    """A max of per-cell values computed with the same operations: equal to the last bit."""
+    case, g, u, v, w, p = _projected(shape, 3)
+    s = B.Solver(case, u, v, w, p)
+    assert s.convective_rate() == O.convective_rate(g, u, v, w)
+    s.close()
+
+
+def test_convective_rate_boundary_layer():
+    case, u, v, w, p, bl = I.boundary_layer(64, 20, 16, amp=0.05, seed=3, re=200.0)
+    g = O.Grid.from_case(case)
+    s = B.Solver(case, u, v, w, p, bl=bl)
+    assert s.convective_rate() == O.convective_rate(g, u, v, w)
+    s.close()
+
+
+def test_set_dt_then_steps_match_the_oracle():
+    case, g, u, v, w, p = _projected((32, 20, 16), 4)
+    s = B.Solver(case, u, v, w, p)
+    s.step(1)
+    ref = O.step(g, dict(u=u, v=v, w=w, p=p), case.dt, case.re, case.fx, 1)
+    dt2 = 0.37 * case.dt
+    s.set_dt(dt2)
+    s.step(2)
+    ref = O.step(g, ref, dt2, case.re, case.fx, 2)
+    errs = field_rel_errors(s.state(), (ref["u"], ref["v"], ref["w"], ref["p"]))
+    for name in ("u", "v", "w", "p"):
+        assert errs[name] < 1e-11, (name, errs)
+    s.close()
+
+
+@pytest.mark.parametrize("prec,bound", [(B.NS_FP64, 1e-11), (B.NS_MIXED, 1e-6)])
+def test_step_cfl_matches_the_oracle(prec, bound):
+    case, g, u, v, w, p = _projected((64, 20, 32), 5)
+    s = B.Solver(case, u, v, w, p, precision=prec)
+    dts = s.step_cfl(3, 0.5)
+    ref, rdts = O.step_cfl(g, dict(u=u, v=v, w=w, p=p), 0.5, case.re, case.fx, 3)
+    assert dts[0] == rdts[0]  # the first rate is taken from identical fields
+    np.testing.assert_allclose(dts, rdts, rtol=1e-10 if prec == B.NS_FP64 else 1e-5)
+    assert len(set(dts)) == 3
+    errs = field_rel_errors(s.state(), (ref["u"], ref["v"], ref["w"], ref["p"]))
+    for name in ("u", "v", "w", "p"):
+        assert errs[name] < bound, (name, errs)
+    s.close()
+
+
+def test_step_cfl_boundary_layer():
+    case, u, v, w, p, bl = I.boundary_layer(64, 16, 16, amp=0.05, seed=7, re=200.0)
+    g = O.Grid.from_case(case)
+    u, v, w, bl = O.make_divergence_free_bl(g, u, v, w, bl)
+    s = B.Solver(case, u, v, w, p, bl=bl)
+    dts = s.step_cfl(2, 0.8)
+    ref, rdts = O.step_cfl(g, dict(u=u, v=v, w=w, p=p, bl=bl), 0.8, case.re, case.fx, 2, bl=True,
+                           u_conv=case.u_conv)
+    np.testing.assert_allclose(dts, rdts, rtol=1e-10)
+    errs = field_rel_errors(s.state(), (ref["u"], ref["v"], ref["w"], ref["p"]))
+    for name in ("u", "v", "w", "p"):
+        assert errs[name] < 1e-11, (name, errs)
+    s.close()
+
+
+@pytest.mark.parametrize("shape", [(64, 37, 32), (96, 13, 24)])
+def test_kim_moin_steps_match_the_oracle(shape):
+    case, g, u, v, w, p = _projected(shape, 6, re=40.0)
+    case.pressure_update = B.NS_PRESSURE_KIM_MOIN
+    s = B.Solver(case, u, v, w, p)
+    s.step(2)
+    ref = O.step(g, dict(u=u, v=v, w=w, p=p), case.dt, case.re, case.fx, 2, pressure="kim_moin")
+    errs = field_rel_errors(s.state(), (ref["u"], ref["v"], ref["w"], ref["p"]))
+    for name in ("u", "v", "w", "p"):
+        assert errs[name] < 1e-11, (name, errs)
+    s.close()
+    # within one sub-step the velocities are those of the plain update and only p differs (the
+    # pressure enters the velocity through the next sub-step's -alpha_k G p)
+    s1 = B.Solver(case, u, v, w, p)
+    case.pressure_update = B.NS_PRESSURE_DELTA
+    s2 = B.Solver(case, u, v, w, p)
+    s1.substep(0)
+    s2.substep(0)
+    a, b = s1.state(), s2.state()
+    for q in range(3):
+        assert np.array_equal(a[q], b[q])
+    assert not np.array_equal(a[3], b[3])
+    s1.close()
+    s2.close()
+
+
+def test_kim_moin_boundary_layer():
+    case, u, v, w, p, bl = I.boundary_layer(64, 16, 16, amp=0.05, seed=8, re=100.0)
+    case.pressure_update = B.NS_PRESSURE_KIM_MOIN
+    g = O.Grid.from_case(case)
+    u, v, w, bl = O.make_divergence_free_bl(g, u, v, w, bl)
+    s = B.Solver(case, u, v, w, p, bl=bl)
+    s.step(2)
+    ref = O.step_bl(g, dict(u=u, v=v, w=w, p=p, bl=bl), case.dt, case.re, case.fx, 2, case.u_conv,
+                    pressure="kim_moin")
+    errs = field_rel_errors(s.state(), (ref["u"], ref["v"], ref["w"], ref["p"]))
+    for name in ("u", "v", "w", "p"):
+        assert errs[name] < 1e-11, (name, errs)
+    s.close()
+
+
+def test_invalid_dt_cfl_and_non_finite_fields_are_reported():
+    case, g, u, v, w, p = _projected((16, 9, 8), 2)
+    s = B.Solver(case, u, v, w, p)
+    L = B.lib()
+    for bad in (0.0, -1.0, math.inf, math.nan):
+        assert L.ns_set_dt(s.ctx, bad) == B.NS_ERR_ARG
+        assert L.ns_step_cfl(s.ctx, 1, bad, None) == B.NS_ERR_ARG
+    s.u[1, 2, 3] = float("nan")
+    r = ctypes.c_double()
+    assert L.ns_convective_rate(s.ctx, ctypes.byref(r)) == B.NS_ERR_STATE
+    s.u[1, 2, 3] = 0.0
+    s.step(1)  # still usable
+    s.sync()
+    s.close()
