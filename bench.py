@@ -227,6 +227,32 @@ def oracle_baseline(case, u, v, w, p, F, nsub, warm=0):
     return case.cells() * (nsub / (3.0 * F)) / t, t
 
 
+def bench_cfl(B, dev, case, u0, v0, w0, p0, steps, cells):
+    """Steps at a fixed CFL number of 1.0 (the paper's runs): each step reads the convective rate
+    back, rebuilds the dt tables when dt changes and updates the captured graph in place.  Host
+    wall clock with a device synchronisation on both sides, since the per-step read-back is part
+    of the cost."""
+    s = B.Solver(case, u0, v0, w0, p0, device=str(dev))
+    s.make_divergence_free()
+    s.step_cfl(3, 1.0)
+    s.sync()
+    t0 = time.perf_counter()
+    dts = s.step_cfl(steps, 1.0)
+    s.sync()
+    t = time.perf_counter() - t0
+    # the same number of steps at a fixed dt (the last one), same clock
+    s.step(1)
+    s.sync()
+    t1 = time.perf_counter()
+    s.step(steps)
+    s.sync()
+    tf = time.perf_counter() - t1
+    s.close()
+    return {"cfl": 1.0, "steps": steps, "value": cells * steps / t, "unit": UNIT, "ms_per_step": 1e3 * t / steps,
+            "fixed_dt_ms_per_step_same_clock": 1e3 * tf / steps, "dt_min": min(dts), "dt_max": max(dts),
+            "timing": "host wall clock around synchronised steps (per-step rate read-back included)"}
+
+
 def bench_ensemble(B, torch, dev, args):
     """64 uneven channel instances: batched (one persistent launch per stage, one graph per step)
     against the same instances stepped one context at a time; FP64 and mixed."""
@@ -287,6 +313,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true")
+    ap.add_argument("--no-cfl", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -450,6 +477,11 @@ def main():
                  "dtype": "f32 increments (rhs, adi) on f64 state; f64 divergence/poisson/projection",
                  "kernel_ms_per_step": {k: v / max(3, args.steps // 5) for k, v in kmix.items() if v > 0}}
 
+    # fixed-CFL stepping (dt from a device max-reduction before every step)
+    cflsec = None
+    if args.precision == "fp64" and not args.no_cfl:
+        cflsec = bench_cfl(B, dev, case, u0, v0, w0, p0, min(args.steps, 20), cells)
+
     # batched ensemble of uneven instances (64 laminar channels, 32^3 .. 128x96x128)
     ensemble = None
     if not args.no_ensemble:
@@ -483,7 +515,7 @@ def main():
            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f64+f32",
            "data": "synthetic (seeded Re_tau 395 log-law channel field, 10% Gaussian fluctuations, projected)",
            "config": config, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
-           "gpu_launches": len(kern) * 3 * args.steps, "clocks": ck, "mixed": mixed, "ensemble": ensemble,
+           "gpu_launches": len(kern) * 3 * args.steps, "clocks": ck, "mixed": mixed, "fixed_cfl": cflsec, "ensemble": ensemble,
            "kernels": {k: {kk: round(vv, 4) for kk, vv in d.items()} for k, d in kern.items()}}
     print(json.dumps(out))
 

@@ -478,11 +478,18 @@ ns_status run_substep(ns_ctx* c, int k, cudaEvent_t* ev = nullptr) {
 }
 
 // Capture the three sub-steps of one time step into a graph (optionally with event nodes).
-ns_status capture_step(ns_ctx* c, bool profiled, cudaGraph_t* graph, cudaGraphExec_t* exec) {
+// Captures one step (3 sub-steps) into *graph and instantiates it into *exec; with update, *exec
+// holds an instantiated graph of the same stages, which is updated in place when possible.
+ns_status capture_step(ns_ctx* c, bool profiled, cudaGraph_t* graph, cudaGraphExec_t* exec, bool update = false) {
+  // on failure with update, *exec is destroyed (the caller drops the graph)
+  auto drop_exec = [&]() {
+    if (update) cudaGraphExecDestroy(*exec);
+  };
   c->launch = c->cap_stream;
   cudaError_t e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) {
     c->launch = c->stream;
+    drop_exec();
     return cuda_fail(c, e, "begin capture");
   }
   ns_status s = NS_OK;
@@ -493,9 +500,23 @@ ns_status capture_step(ns_ctx* c, bool profiled, cudaGraph_t* graph, cudaGraphEx
   c->launch = c->stream;
   if (s != NS_OK) {
     if (g) cudaGraphDestroy(g);
+    drop_exec();
     return s;
   }
-  if (e != cudaSuccess) return cuda_fail(c, e, "end capture");
+  if (e != cudaSuccess) {
+    drop_exec();
+    return cuda_fail(c, e, "end capture");
+  }
+  if (update) {
+    // same stages, new kernel arguments (a new dt): update the instantiated graph in place
+    cudaGraphExecUpdateResultInfo info;
+    if (cudaGraphExecUpdate(*exec, g, &info) == cudaSuccess) {
+      *graph = g;
+      return NS_OK;
+    }
+    cudaGetLastError();
+    cudaGraphExecDestroy(*exec);
+  }
   if ((e = cudaGraphInstantiate(exec, g, 0)) != cudaSuccess) {
     cudaGraphDestroy(g);
     return cuda_fail(c, e, "graph instantiate");
@@ -785,10 +806,21 @@ ns_status ns_step(ns_ctx* c, int nsteps) {
   if (nsteps < 0) return fail(c, NS_ERR_ARG, "nsteps must be >= 0");
   if (nsteps == 0) return NS_OK;
   if (capturing(c)) return fail(c, NS_ERR_STATE, "ns_step called while its stream is being captured");
+  if (c->have_graph && c->graph_stale) {
+    cudaGraph_t old = c->graph;
+    ns_status s = capture_step(c, false, &c->graph, &c->gexec, true);
+    cudaGraphDestroy(old);
+    c->graph_stale = false;
+    if (s != NS_OK) {
+      c->have_graph = false;
+      return s;
+    }
+  }
   if (!c->have_graph) {
     ns_status s = capture_step(c, false, &c->graph, &c->gexec);
     if (s != NS_OK) return s;
     c->have_graph = true;
+    c->graph_stale = false;
   }
   cudaError_t e;
   for (int s = 0; s < nsteps; ++s)
@@ -821,7 +853,22 @@ ns_status ns_set_dt(ns_ctx* c, double dt) {
   c->cfg.dt = dt;
   ns_status s = build_dt_tables(c);
   if (s == NS_OK) s = build_x_tables(c);
+  // the step graph is re-captured and updated in place by the next ns_step; the profiled one is
+  // dropped
+  const bool keep = c->have_graph;
+  const cudaGraph_t g = c->graph;
+  const cudaGraphExec_t x = c->gexec;
+  c->have_graph = false;
   drop_graph(c);
+  if (keep && s == NS_OK) {
+    c->graph = g;
+    c->gexec = x;
+    c->have_graph = true;
+    c->graph_stale = true;
+  } else if (keep) {
+    cudaGraphExecDestroy(x);
+    cudaGraphDestroy(g);
+  }
   if (s != NS_OK) {
     c->cfg.dt = old;
     build_dt_tables(c);

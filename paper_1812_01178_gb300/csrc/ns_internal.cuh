@@ -186,6 +186,7 @@ struct ns_ctx {
   cudaGraph_t graph;
   cudaGraphExec_t gexec;
   bool have_graph;
+  bool graph_stale = false;  // kernel arguments changed (ns_set_dt): update gexec before launching
   // profiled graph: the same launches with an event recorded before each kernel and after the
   // last one
   cudaGraph_t pgraph;
