@@ -888,3 +888,116 @@ def step_bl(g, state, dt, re, fx, nsteps=1, u_conv=1.0, pressure="delta"):
         for k in range(3):
             s = substep_bl(g, s, k, dt, re, fx, u_conv, pressure)
     return s
+
+
+# ----------------------------------------------------------------------------
+# Recycling inflow (Sec. 2.1: turbulent inflow by the recycling method of Lund, Wu & Squires,
+# J. Comput. Phys. 140, 1998), restated from that method's description.
+# ----------------------------------------------------------------------------
+# Readings (the paper cites the method only):
+# * The recycle plane is the u face i_r (1 <= i_r < nx); v and w there are the averages of the
+#   centres i_r - 1 and i_r.  Means are spanwise averages of that plane at the current step (no
+#   running time average); fluctuations are the plane minus its means.
+# * delta_rec: the first y where the recycled mean U reaches 0.99 U_inf (linear between centres;
+#   the top centre if never reached).  The friction velocities enter only through their ratio,
+#   gamma = u_tau,inl / u_tau,rec = (delta_rec / delta_inl)^(1/8) (the 1/5 power law:
+#   delta ~ x^(4/5), u_tau ~ x^(-1/10)).
+# * Inlet row at height y takes the recycled profiles at y gamma (inner: same y+) and at
+#   y delta_rec / delta_inl (outer: same eta = y / delta), by linear interpolation in y over the
+#   plane's points with the wall value (u, w: 0 at y = 0; v: its face values) and the top value
+#   held above.  Inner mean U: gamma U_rec; outer: gamma U_rec + (1 - gamma) U_inf; mean V
+#   unscaled; mean W = 0; fluctuations times gamma.  Blend (1 - W) inner + W outer with
+#   W(eta) = (1 + tanh(a (eta - b) / ((1 - 2b) eta + b)) / tanh a) / 2, a = 4, b = 0.2, W = 1 for
+#   eta > 1.
+# * The inflow planes (u on face 0, v_in, w_in) are set this way once at the start of every step.
+
+def lund_weight(eta, a=4.0, b=0.2):
+    eta = np.asarray(eta, dtype=np.float64)
+    wgt = 0.5 * (1.0 + np.tanh(a * (eta - b) / ((1.0 - 2.0 * b) * eta + b)) / math.tanh(a))
+    return np.where(eta > 1.0, 1.0, wgt)
+
+
+def _interp_rows(yq, ys, f):
+    """Linear interpolation along axis 1 of f (nz, n) given at ys (increasing), at heights yq;
+    values beyond the ends are the end values."""
+    out = np.empty((f.shape[0], yq.size))
+    for k in range(f.shape[0]):
+        out[k] = np.interp(yq, ys, f[k])
+    return out
+
+
+def delta99(yc, U, u_inf=1.0):
+    """First height where U reaches 0.99 u_inf (linear between centres); yc[-1] if never."""
+    target = 0.99 * u_inf
+    for j in range(len(U)):
+        if U[j] >= target:
+            if j == 0:
+                return yc[0] * target / U[0]
+            return yc[j - 1] + (target - U[j - 1]) * (yc[j] - yc[j - 1]) / (U[j] - U[j - 1])
+    return yc[-1]
+
+
+def rescale_inflow(g, u_r, v_r, w_r, gamma, delta_rec, delta_inl, u_inf=1.0):
+    """Inlet planes from recycle-plane values u_r (nz, ny) at centres, v_r (nz, ny+1) at faces,
+    w_r (nz, ny) at centres, given gamma and the two thicknesses."""
+    yc, yf = g.yc, g.yf
+    # sample points with the wall value: centres plus y = 0 for u, w; faces for v
+    ys_c = np.concatenate([[yf[0]], yc])
+    U = u_r.mean(axis=0)
+    V = v_r.mean(axis=0)
+    Wm = w_r.mean(axis=0)
+    up = u_r - U[None, :]
+    vp = v_r - V[None, :]
+    wp = w_r - Wm[None, :]
+    def sample_c(f2d, yq):
+        z1 = np.zeros((f2d.shape[0], 1))
+        return _interp_rows(yq, ys_c, np.concatenate([z1, f2d], axis=1))
+
+    def blend(inner, outer, y):
+        wgt = lund_weight(y / delta_inl)[None, :]
+        return (1.0 - wgt) * inner + wgt * outer
+
+    r = delta_rec / delta_inl
+    # u (centres)
+    Ui = gamma * sample_c(U[None, :], gamma * yc)
+    Uo = gamma * sample_c(U[None, :], r * yc) + (1.0 - gamma) * u_inf
+    ui = gamma * sample_c(up, gamma * yc)
+    uo = gamma * sample_c(up, r * yc)
+    u_in = blend(Ui + ui, Uo + uo, yc)
+    # w (centres; mean W = 0 at the inlet)
+    w_in = blend(gamma * sample_c(wp, gamma * yc), gamma * sample_c(wp, r * yc), yc)
+    # v (faces, wall and top rows kept at 0)
+    Vi = _interp_rows(gamma * yf, yf, V[None, :])
+    Vo = _interp_rows(r * yf, yf, V[None, :])
+    vi = gamma * _interp_rows(gamma * yf, yf, vp)
+    vo = gamma * _interp_rows(r * yf, yf, vp)
+    v_in = blend(Vi + vi, Vo + vo, yf)
+    v_in[:, 0] = 0.0
+    v_in[:, -1] = 0.0
+    return u_in, v_in, w_in
+
+
+def recycle_inflow(g, u, v, w, i_r, delta_inl, re, u_inf=1.0):
+    """The inflow planes (u face 0, v_in, w_in) recycled from the u face i_r."""
+    u_r = u[:, :, i_r]
+    v_r = 0.5 * (v[:, :, i_r - 1] + v[:, :, i_r])
+    w_r = 0.5 * (w[:, :, i_r - 1] + w[:, :, i_r])
+    U = u_r.mean(axis=0)
+    delta_rec = delta99(g.yc, U, u_inf)
+    gamma = (delta_rec / delta_inl) ** 0.125
+    return rescale_inflow(g, u_r, v_r, w_r, gamma, delta_rec, delta_inl, u_inf)
+
+
+def step_bl_recycled(g, state, dt, re, fx, i_r, delta_inl, nsteps=1, u_conv=1.0, pressure="delta"):
+    """step_bl with the inflow planes recycled from face i_r at the start of every step."""
+    s = dict(state)
+    for _ in range(nsteps):
+        u_in, v_in, w_in = recycle_inflow(g, s["u"], s["v"], s["w"], i_r, delta_inl, re, u_conv)
+        u = s["u"].copy()
+        u[:, :, 0] = u_in
+        bl = dict(s["bl"])
+        bl["v_in"] = v_in
+        bl["w_in"] = w_in
+        s = dict(s, u=u, bl=bl)
+        s = step_bl(g, s, dt, re, fx, 1, u_conv, pressure)
+    return s

@@ -1,0 +1,91 @@
+"""Pins of the oracle's recycling inflow (the rescaling method of Lund, Wu & Squires 1998)."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import ns_oracle as O
+from paper_1812_01178_gb300 import inputs as I
+
+
+def _grid(nx=16, ny=24, nz=8):
+    case, u, v, w, p, bl = I.boundary_layer(nx, ny, nz, amp=0.05, seed=2, re=300.0)
+    return case, O.Grid.from_case(case), u, v, w, p, bl
+
+
+def test_weight_function_ends_and_monotone():
+    assert O.lund_weight(0.0) == 0.0
+    assert O.lund_weight(1.0) == 1.0
+    assert O.lund_weight(3.0) == 1.0
+    eta = np.linspace(0, 1, 201)
+    assert np.all(np.diff(O.lund_weight(eta)) >= 0)
+    assert O.lund_weight(0.2) == pytest.approx(0.5)   # the inflection point b
+
+
+def test_identity_when_the_thicknesses_agree():
+    """gamma = 1 and delta_rec = delta_inl: both rescalings sample the plane at its own heights,
+    so the inflow planes are the recycle plane (v with its wall and top rows)."""
+    case, g, u, v, w, p, bl = _grid()
+    rng = np.random.default_rng(1)
+    u_r = rng.standard_normal((g.nz, g.ny))
+    v_r = rng.standard_normal((g.nz, g.ny + 1))
+    v_r[:, 0] = 0
+    v_r[:, -1] = 0
+    w_r = rng.standard_normal((g.nz, g.ny))
+    ui, vi, wi = O.rescale_inflow(g, u_r, v_r, w_r, 1.0, 2.5, 2.5)
+    np.testing.assert_allclose(ui, u_r, rtol=0, atol=1e-14)
+    np.testing.assert_allclose(vi, v_r, rtol=0, atol=1e-14)
+    np.testing.assert_allclose(wi, w_r - w_r.mean(axis=0), rtol=0, atol=1e-14)
+
+
+def test_linear_mean_profile_closed_form():
+    """U_rec = a y, spanwise uniform (no fluctuations): linear interpolation is exact, so the inlet
+    mean is (1 - W) gamma^2 a y + W (gamma a y delta_rec / delta_inl + 1 - gamma) in closed form
+    wherever the sampled heights stay below the top centre."""
+    case, g, u, v, w, p, bl = _grid(ny=32)
+    a = 0.05
+    u_r = np.broadcast_to(a * g.yc, (g.nz, g.ny)).copy()
+    v_r = np.zeros((g.nz, g.ny + 1))
+    w_r = np.zeros((g.nz, g.ny))
+    gamma, drec, dinl = 1.03, 3.0, 2.4
+    ui, vi, wi = O.rescale_inflow(g, u_r, v_r, w_r, gamma, drec, dinl)
+    y = g.yc
+    ok = (gamma * y <= g.yc[-1]) & (drec / dinl * y <= g.yc[-1])
+    W = O.lund_weight(y / dinl)
+    expect = (1 - W) * gamma * gamma * a * y + W * (gamma * a * y * drec / dinl + 1 - gamma)
+    np.testing.assert_allclose(ui[:, ok], np.broadcast_to(expect[ok], (g.nz, ok.sum())), rtol=0, atol=1e-14)
+    assert not np.any(wi) and not np.any(vi)
+
+
+def test_delta99_of_a_tanh_profile():
+    yc = np.linspace(0.01, 5.0, 400)
+    s = 1.3
+    d = O.delta99(yc, np.tanh(s * yc))
+    assert d == pytest.approx(math.atanh(0.99) / s, rel=1e-4)
+
+
+def test_fluctuations_scale_with_gamma_in_the_outer_layer():
+    """Above delta_inl (W = 1) the inlet fluctuation is gamma times the plane's fluctuation sampled
+    at y delta_rec / delta_inl."""
+    case, g, u, v, w, p, bl = _grid(ny=40)
+    rng = np.random.default_rng(3)
+    u_r = 1.0 + 0.1 * rng.standard_normal((g.nz, g.ny))
+    v_r = np.zeros((g.nz, g.ny + 1))
+    w_r = 0.1 * rng.standard_normal((g.nz, g.ny))
+    gamma, drec, dinl = 0.97, 1.0, 1.0
+    ui, vi, wi = O.rescale_inflow(g, u_r, v_r, w_r, gamma, drec, dinl)
+    top = g.yc > dinl
+    wp = w_r - w_r.mean(axis=0)
+    np.testing.assert_allclose(wi[:, top], gamma * wp[:, top], rtol=0, atol=1e-14)
+    up = u_r - u_r.mean(axis=0)
+    np.testing.assert_allclose(ui[:, top] - ui[:, top].mean(axis=0), gamma * up[:, top], rtol=0, atol=1e-13)
+
+
+def test_recycled_steps_keep_divergence_and_mass_balance():
+    case, g, u, v, w, p, bl = _grid(16, 12, 8)
+    u, v, w, bl = O.make_divergence_free_bl(g, u, v, w, bl)
+    s = O.step_bl_recycled(g, dict(u=u, v=v, w=w, p=p, bl=bl), case.dt, case.re, case.fx, 10, 1.0, nsteps=2)
+    assert np.abs(O.divergence_bl(g, s["u"], s["v"], s["w"], s["bl"])).max() < 1e-11
+    wgt = g.dy[None, :] * g.dz
+    assert abs((s["u"][:, :, 0] * wgt).sum() - (s["bl"]["u_out"] * wgt).sum()) < 1e-11
+    assert not np.array_equal(s["u"][:, :, 0], u[:, :, 0])
