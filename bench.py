@@ -52,6 +52,7 @@ def kernel_model(nx, ny, nz, es):
         # boundary-plane stages (inflow / outflow only): per cell of the volume they are tiny
         "outflow":          (8 * 3.0 * 5 / nx,               8.0 / nx),
         "flux_correct":     (8 * 3.0 / nx,                   3.0 / nx),
+        "recycle":          (8 * 3.0 * 4 / nx,               40.0 / nx),
         "poisson_ifftz":    (sh * 16 + 8,                    2.5 * L(nz) + 2.0),
         "project":          (8 + 8 * 8,                      11.0),
     }

@@ -89,7 +89,22 @@ typedef struct {
   int precision;         /* NS_FP64 or NS_MIXED */
   double u_conv;         /* convection speed U_c of the outflow condition (bc_x = 1 only) */
   int pressure_update;   /* NS_PRESSURE_DELTA or NS_PRESSURE_KIM_MOIN */
+  int recycle_i;         /* 0: fixed inflow planes; else the u face 1..nx-1 recycled to the inflow */
+  double delta_in;       /* inlet boundary-layer thickness of the recycling (recycle_i != 0) */
 } ns_config;
+
+/* Recycling inflow (Sec. 2.1 names the method of Lund, Wu & Squires, J. Comput. Phys. 140,
+ * 1998).  With bc_x = 1 and recycle_i != 0, every time step first rewrites the inflow planes
+ * (u on face 0, v_in, w_in) from the u face recycle_i, with v and w there averaged from the
+ * centres recycle_i - 1 and recycle_i:
+ *   means U, V, W are spanwise averages of that plane, fluctuations the plane minus them;
+ *   delta_rec is the first height where U reaches 0.99 u_conv (linear between centres);
+ *   gamma = (delta_rec / delta_in)^(1/8) is the inlet-to-recycle friction-velocity ratio;
+ *   the row at height y takes mean and fluctuation at y gamma (inner) and y delta_rec / delta_in
+ *   (outer) by linear interpolation (0 at the wall for u, w), inner mean gamma U, outer
+ *   gamma U + (1 - gamma) u_conv, mean V unscaled, mean W zero, fluctuations times gamma, blended
+ *   by W(y / delta_in) = (1 + tanh(4 (eta - 0.2) / (0.6 eta + 0.2)) / tanh 4) / 2 (1 above 1).
+ * recycle_i outside [1, nx-1], delta_in <= 0, or recycle_i != 0 with bc_x = 0 give NS_ERR_ARG. */
 
 /* Pressure update of each sub-step after the projection (the paper names only the
  * pseudo-pressure phi, Sec. 2.2):
@@ -185,11 +200,12 @@ ns_status ns_step_cfl(ns_ctx* ctx, int nsteps, double cfl, double* dts);
  * first).  The state advances exactly as with ns_step. */
 ns_status ns_step_profiled(ns_ctx* ctx, int nsteps, float* kernel_ms, int nk);
 
-/* Number of kernel slots in one sub-step, and the name of slot idx, in launch order: rhs, outflow,
- * adi_x, adi_y, adi_z, flux_correct, poisson_div_fftz, poisson_x_fwd, poisson_tdma_y,
- * poisson_x_inv, poisson_ifftz, project ("" if idx is out of range).  outflow and flux_correct
- * launch only with bc_x = 1 (else their time is 0); poisson_x_* are FFTs for periodic x and
- * cosine transforms (DCT-II / its inverse) for inflow / outflow. */
+/* Number of kernel slots in one sub-step, and the name of slot idx, in launch order: recycle,
+ * rhs, outflow, adi_x, adi_y, adi_z, flux_correct, poisson_div_fftz, poisson_x_fwd,
+ * poisson_tdma_y, poisson_x_inv, poisson_ifftz, project ("" if idx is out of range).  recycle
+ * launches only in sub-step 0 with recycle_i != 0; outflow and flux_correct only with bc_x = 1
+ * (else their time is 0); poisson_x_* are FFTs for periodic x and cosine transforms (DCT-II / its
+ * inverse) for inflow / outflow. */
 int ns_kernel_count(void);
 const char* ns_kernel_name(int idx);
 

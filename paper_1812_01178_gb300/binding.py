@@ -39,7 +39,8 @@ class ns_config(C.Structure):
                 ("yf", C.POINTER(C.c_double)),
                 ("bc_x", C.c_int), ("bc_ytop", C.c_int),
                 ("re", C.c_double), ("fx", C.c_double), ("dt", C.c_double),
-                ("precision", C.c_int), ("u_conv", C.c_double), ("pressure_update", C.c_int)]
+                ("precision", C.c_int), ("u_conv", C.c_double), ("pressure_update", C.c_int),
+                ("recycle_i", C.c_int), ("delta_in", C.c_double)]
 
 
 class ns_fields(C.Structure):
@@ -121,7 +122,8 @@ def make_config(case, precision=None):
     cfg = ns_config(case.nx, case.ny, case.nz, case.lx, case.lz,
                     yf.ctypes.data_as(C.POINTER(C.c_double)), case.bc_x, case.bc_ytop,
                     case.re, case.fx, case.dt, case.precision if precision is None else precision,
-                    getattr(case, "u_conv", 1.0), getattr(case, "pressure_update", NS_PRESSURE_DELTA))
+                    getattr(case, "u_conv", 1.0), getattr(case, "pressure_update", NS_PRESSURE_DELTA),
+                    getattr(case, "recycle_i", 0), getattr(case, "delta_in", 0.0))
     cfg._yf_keep = yf
     return cfg
 

@@ -27,6 +27,11 @@ std::string check_cfg(const ns_config* c, ns_status* kind = nullptr) {
   if (c->precision != NS_FP64 && c->precision != NS_MIXED) return "precision must be NS_FP64 or NS_MIXED";
   if (c->pressure_update != NS_PRESSURE_DELTA && c->pressure_update != NS_PRESSURE_KIM_MOIN)
     return "pressure_update must be NS_PRESSURE_DELTA or NS_PRESSURE_KIM_MOIN";
+  if (c->recycle_i != 0) {
+    if (c->bc_x != 1) return "recycling needs inflow / outflow in x (bc_x = 1)";
+    if (c->recycle_i < 1 || c->recycle_i >= c->nx) return "recycle_i must be in [1, nx - 1]";
+    if (!(c->delta_in > 0.0) || !std::isfinite(c->delta_in)) return "delta_in must be positive and finite";
+  }
   k = NS_ERR_SIZE;
   if (fft_plan(c->nx) < 0 || c->nx % 8 || c->nx < 8 || c->nx > 4096)
     return "nx must be 2^a 3^b with a >= 3, in [8, 4096]";
@@ -68,6 +73,7 @@ ns_layout make_layout(const ns_config* c) {
   sz[LB_RTAB] = 3 * al256((size_t)RT_COUNT * (ny + 1) * 8) + 3 * al256((size_t)RT_COUNT * (ny + 1) * 4);
   sz[LB_DOUT] = 3 * al256((ny + 1) * nz * 8) + 256;
   sz[LB_TWD] = nx * 16;
+  sz[LB_RCY] = recycle_block_doubles((int)ny) * 8;
   size_t o = 0;
   for (int b = 0; b < LB_COUNT; ++b) {
     L.off[b] = o;
@@ -453,6 +459,7 @@ struct Stage {
   cudaError_t (*fn)(ns_ctx*, int);
 };
 const Stage STAGES[] = {
+    {"recycle", launch_recycle},              // inflow planes from the recycle plane (sub-step 0 only)
     {"rhs", launch_rhs},                      // A1
     {"outflow", launch_outflow},              // A10 (convective outflow; inflow / outflow only)
     {"adi_x", launch_adi_x},                  // A2
@@ -633,6 +640,7 @@ ns_status ns_init(ns_ctx** out, const ns_config* cfg, const ns_fields* fields, v
   for (int q = 0; q < 3; ++q) c->dout[q] = (double*)(base + c->lay.off[LB_DOUT] + q * al256((size_t)(ny + 1) * nz * 8));
   c->flux = (double*)(base + c->lay.off[LB_DOUT] + 3 * al256((size_t)(ny + 1) * nz * 8));
   c->rate = (unsigned long long*)(c->flux + 4);
+  c->rcy = (double*)(base + c->lay.off[LB_RCY]);
   c->twd = (double2*)(base + c->lay.off[LB_TWD]);
   double* lamz_d = (double*)(base + c->lay.off[LB_LAMZ]);
 
@@ -673,6 +681,7 @@ ns_status ns_init(ns_ctx** out, const ns_config* cfg, const ns_fields* fields, v
   for (int j = 0; j + 1 < ny; ++j) GCv(GC_PC, j) = 1.0 / (dy[j] * (yc[j + 1] - yc[j]));
   ns_status st = NS_OK;
   c->gc_h = gc;
+  if (c->cfg.recycle_i && recycle_upload_grid(c) != cudaSuccess) st = NS_ERR_CUDA;
   if (upload_d(c, c->gc, gc) != cudaSuccess) st = NS_ERR_CUDA;
 
   // ---------------- RHS assembly coefficients per sub-step (tiled kernel)
@@ -897,6 +906,7 @@ ns_status ns_step_cfl(ns_ctx* c, int nsteps, double cfl, double* dts) {
 
 // Stages that launch nothing in this configuration (the boundary-plane stages of periodic x).
 bool stage_idle(const ns_ctx* c, int q) {
+  if (STAGES[q].fn == launch_recycle) return !c->cfg.recycle_i;
   return !c->bl && (STAGES[q].fn == launch_outflow || STAGES[q].fn == launch_flux_correct);
 }
 

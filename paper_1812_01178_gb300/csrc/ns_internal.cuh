@@ -137,7 +137,7 @@ struct ns_layout {
 
 enum {
   LB_RU = 0, LB_RV, LB_RW, LB_NU, LB_NV, LB_NW, LB_PHI, LB_SPEC, LB_POIS, LB_GC, LB_XTAB, LB_YTAB,
-  LB_ZTAB, LB_TWZ, LB_TWX, LB_LAMX, LB_LAMZ, LB_RTAB, LB_DOUT, LB_TWD, LB_COUNT
+  LB_ZTAB, LB_TWZ, LB_TWX, LB_LAMX, LB_LAMZ, LB_RTAB, LB_DOUT, LB_TWD, LB_RCY, LB_COUNT
 };
 
 struct ns_ctx {
@@ -174,6 +174,7 @@ struct ns_ctx {
   double* flux;             // [0]: inflow flux, [1]: last outflow correction (diagnostics)
   unsigned long long* rate; // bits of the convective rate of ns_convective_rate (in the flux block)
   std::vector<double> gc_h; // host copy of the grid coefficients (tables are rebuilt when dt changes)
+  double* rcy;              // recycling inflow: sample heights, plane means, gamma (k_recycle.cu)
   int num_sms;
   int rhs_bps[2];           // resident blocks per SM of the tiled RHS (FP64, FP32)
   // partitioned x solver
@@ -382,6 +383,9 @@ cudaError_t launch_outflow(ns_ctx* c, int k);        // convective outflow updat
 cudaError_t launch_flux_correct(ns_ctx* c, int k);   // outflow volume flux := inflow flux
 cudaError_t launch_pois_factor(ns_ctx* c, const double* lamx, const double* lamz);
 cudaError_t launch_convective_rate(ns_ctx* c);  // max-reduction into c->rate (zeroed first)
+cudaError_t launch_recycle(ns_ctx* c, int k);    // recycled inflow planes (sub-step 0, if enabled)
+size_t recycle_block_doubles(int ny);
+cudaError_t recycle_upload_grid(ns_ctx* c);
 cudaError_t poisson_set_attributes();  // once per process and device, outside any capture
 
 // Sets the message ns_last_error(NULL) returns on this thread.

@@ -99,6 +99,8 @@ class Case:
     precision: int = 0     # 0 FP64, 1 mixed
     u_conv: float = 1.0
     pressure_update: int = 0  # 0: p += phi; 1: Kim-Moin form
+    recycle_i: int = 0        # u face recycled to the inflow (0: fixed inflow planes)
+    delta_in: float = 0.0     # inlet boundary-layer thickness of the recycling
 
     def cells(self) -> int:
         return self.nx * self.ny * self.nz

@@ -52,3 +52,21 @@ def test_grid_sizes_accepted_and_rejected_without_gpu(libpath, nx, nz, ok):
     case, *_ = I.small_channel(64, 20, 32)
     case.nx, case.nz = nx, nz
     assert (B.ns_workspace_bytes(B.make_config(case)) > 0) == ok
+
+
+@pytest.mark.parametrize("bc_x,ir,delta_in,ok", [
+    (1, 5, 1.0, True), (1, 0, 0.0, True), (0, 5, 1.0, False), (1, 64, 1.0, False), (1, -1, 1.0, False),
+    (1, 5, 0.0, False), (1, 5, float("inf"), False)])
+def test_recycling_options_checked_without_gpu(libpath, bc_x, ir, delta_in, ok):
+    from paper_1812_01178_gb300 import inputs as I
+    case, *_ = I.boundary_layer(64, 12, 16)
+    case.bc_x, case.recycle_i, case.delta_in = bc_x, ir, delta_in
+    assert (B.ns_workspace_bytes(B.make_config(case)) > 0) == ok
+
+
+@pytest.mark.parametrize("pu,ok", [(0, True), (1, True), (2, False), (-1, False)])
+def test_pressure_update_option_checked_without_gpu(libpath, pu, ok):
+    from paper_1812_01178_gb300 import inputs as I
+    case, *_ = I.small_channel(32, 12, 16)
+    case.pressure_update = pu
+    assert (B.ns_workspace_bytes(B.make_config(case)) > 0) == ok
