@@ -415,8 +415,14 @@ def main():
             continue  # stage not launched in this configuration
         per = ms / launches
         b, f = model[name]
+        gbps = b * cells / (per * 1e-3) / 1e9
         kern[name] = {"ms_per_launch": per, "share": ms / max(sum(kms.values()), 1e-9),
-                      "GBps": b * cells / (per * 1e-3) / 1e9, "GFLOPps": f * cells / (per * 1e-3) / 1e9}
+                      "GBps": gbps, "GFLOPps": f * cells / (per * 1e-3) / 1e9,
+                      # % of the HBM roofline: algorithmic bytes, and the ncu DRAM bytes of the
+                      # committed capture (null once the kernel's source has changed)
+                      "hbm_frac_algorithmic": gbps / hbm}
+        tr = load_traffic(config["workload"], name)
+        kern[name]["hbm_frac_measured"] = (tr / (per * 1e-3) / 1e9 / hbm) if tr else None
     top = max(kms, key=kms.get)
     b, f = model[top]
     per = kms[top] / launches
@@ -517,7 +523,8 @@ def main():
            "data": "synthetic (seeded Re_tau 395 log-law channel field, 10% Gaussian fluctuations, projected)",
            "config": config, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
            "gpu_launches": len(kern) * 3 * args.steps, "clocks": ck, "mixed": mixed, "fixed_cfl": cflsec, "ensemble": ensemble,
-           "kernels": {k: {kk: round(vv, 4) for kk, vv in d.items()} for k, d in kern.items()}}
+           "kernels": {k: {kk: (round(vv, 4) if vv is not None else None) for kk, vv in d.items()}
+                       for k, d in kern.items()}}
     print(json.dumps(out))
 
 
