@@ -594,13 +594,14 @@ def step(g, state, dt, re, fx, nsteps=1, pressure="delta"):
 # ----------------------------------------------------------------------------
 # Reading: the paper gives no formula for its CFL number.  Here it is the convective one,
 # dt max over cells of |u|/dx + |v_c|/dy_j + |w|/dz, with u and w the values on the cell's lower
-# x and z faces and v_c the average of its two y faces; dt is set before every step from the
-# velocity at the start of the step and held for the three sub-steps.
+# x and z faces and v_c the average of its two y faces, each term formed as the magnitude times
+# the reciprocal spacing; dt is set before every step from the velocity at the start of the step
+# and held for the three sub-steps.
 
 def convective_rate(g, u, v, w):
-    """max over cells of |u|/dx + |v_c|/dy_j + |w|/dz (so that CFL = dt * rate)."""
+    """max over cells of |u| (1/dx) + |v_c| (1/dy_j) + |w| (1/dz) (so that CFL = dt * rate)."""
     vc = 0.5 * (v[:, :-1, :] + v[:, 1:, :])
-    c = np.abs(u) / g.dx + np.abs(vc) / g.dy[None, :, None] + np.abs(w) / g.dz
+    c = np.abs(u) * (1.0 / g.dx) + np.abs(vc) * (1.0 / g.dy)[None, :, None] + np.abs(w) * (1.0 / g.dz)
     return float(c.max())
 
 
