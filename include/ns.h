@@ -175,7 +175,7 @@ ns_status ns_step(ns_ctx* ctx, int nsteps);
 
 /* Time step at a fixed CFL number (the paper's runs hold CFL = 1.0, Sec. 4).
  *
- * ns_convective_rate: *rate = max over cells of |u|/dx + |v_c|/dy_j + |w|/dz of the current
+ * ns_convective_rate: *rate = max over cells of |u| (1/dx) + |v_c| (1/dy_j) + |w| (1/dz) of the current
  * fields, with u and w the values on the cell's lower x and z faces and v_c the average of its two
  * y faces, so that the convective CFL number is dt * rate.  One device max-reduction on the
  * context's stream, then a synchronising 8-byte read.  NS_ERR_STATE if the fields hold a

@@ -23,20 +23,22 @@ template <typename T>
 struct AdiXArgs {
   const T* __restrict__ tab[2];  // table of the u lines [0] and of the v, w lines [1]
   T* r[3];
-  int nx, ny, nz, P, L;
+  int nx, ny, nz, P;
   long nlines;  // nz*ny (u) + nz*(ny-1) (v) + nz*ny (w)
   // inflow / outflow in x: the outflow-plane increment of component c enters the last row as
-  // + coef[c] * dout[c][k * rows + j]
+  // + sk->xcf[c] * dout[c][k * rows + j]
   int bl;
   const double* __restrict__ dout[3];
-  T coef[3];
+  const StepK* sk;  // reduction levels L (0: PDD) and the outflow weights of this sub-step
 };
 
-// coef[comp] * dout[comp][plane] without indexing the argument struct at run time
+// xcf[comp] * dout[comp][plane] in the arithmetic type
 template <typename T>
 __device__ __forceinline__ T outflow_term(const AdiXArgs<T>& a, int comp, long plane) {
   const double* d = comp == 0 ? a.dout[0] : (comp == 1 ? a.dout[1] : a.dout[2]);
-  const T cf = comp == 0 ? a.coef[0] : (comp == 1 ? a.coef[1] : a.coef[2]);
+  T cf;
+  if constexpr (sizeof(T) == 4) cf = a.sk->xcff[comp];
+  else cf = a.sk->xcf[comp];
   return cf * (T)__ldg(d + plane);
 }
 
@@ -119,7 +121,7 @@ struct AdiXK {
 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* st = reinterpret_cast<T*>(smem_raw);
-  const int P = a.P, L = a.L;
+  const int P = a.P, L = a.sk->L;
   const int ntab = (int)xtab_count(M, P, L);
   const int ncls = a.bl ? 2 : 1;
   for (int q = threadIdx.x; q < ntab * ncls; q += blockDim.x) st[q] = q < ntab ? a.tab[0][q] : a.tab[1][q - ntab];
@@ -211,7 +213,7 @@ struct AdiXLongK {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* line_buf = reinterpret_cast<T*>(smem_raw) + (threadIdx.x >> 5) * LS;
   const int r = threadIdx.x & 31;
-  const int L = a.L;
+  const int L = a.sk->L;
   const long warp = ((long)bid_.x * blockDim.x + threadIdx.x) >> 5;
   const long nwarps = ((long)gdim_.x * blockDim.x) >> 5;
   T* my = line_buf + r * (M + 1);
@@ -464,11 +466,7 @@ void fill_x_args(ns_ctx* c, int k, AdiXArgs<T>& a) {
   a.tab[0] = (const T*)c->xtab[k][0];
   a.tab[1] = (const T*)c->xtab[k][1];
   a.bl = c->bl;
-  const double inv_re = c->cfg.re > 0 ? 1.0 / c->cfg.re : 0.0;
-  const double rx = NS_ALPHA[k] * c->cfg.dt * inv_re / 2.0 / (c->dx * c->dx);
-  a.coef[0] = (T)rx;          // u: the outflow face is the neighbour of the last unknown face
-  a.coef[1] = (T)(2.0 * rx);  // v, w: linear ghost 2 f_out - f_last
-  a.coef[2] = (T)(2.0 * rx);
+  a.sk = c->stepk + k;
   for (int q = 0; q < 3; ++q) a.dout[q] = c->dout[q];
 }
 
@@ -484,9 +482,11 @@ cudaError_t launch_x_t(LaunchSink& s, int k) {
   a.ny = c->cfg.ny;
   a.nz = c->cfg.nz;
   a.P = c->P;
-  a.L = c->L[k];
   a.nlines = (long)a.nz * a.ny * 2 + (long)a.nz * (a.ny - 1);
-  const size_t smem = xtab_count(M, a.P, a.L) * sizeof(T) * (a.bl ? 2 : 1);
+  // room for the PPT tables: the levels are read from device memory and follow the mode in use
+  int lmax = 0;
+  while ((1 << lmax) < a.P) ++lmax;
+  const size_t smem = xtab_count(M, a.P, lmax) * sizeof(T) * (a.bl ? 2 : 1);
   const long teams_per_block = 8L * (32 / a.P);
   long blocks = (a.nlines + teams_per_block - 1) / teams_per_block;
   if (blocks > 152L * 16) blocks = 152L * 16;
@@ -505,7 +505,6 @@ cudaError_t launch_x_long_t(LaunchSink& s, int k) {
   a.ny = c->cfg.ny;
   a.nz = c->cfg.nz;
   a.P = c->P;
-  a.L = c->L[k];
   a.nlines = (long)a.nz * a.ny * 2 + (long)a.nz * (a.ny - 1);
   const size_t smem = (size_t)4 * 32 * (M + 1) * sizeof(T);
   long blocks = (a.nlines + 3) / 4;

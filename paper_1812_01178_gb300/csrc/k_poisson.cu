@@ -172,12 +172,12 @@ struct DivzK {
     int TX;
     double idx;
     double idz;
-    double scale;
+    const StepK* sk;  // pscale = 1 / (alpha_k dt nx nz)
     const double* u_out;
   };
   static constexpr int kThreads = 256;
   static constexpr int kMinBlocks = 4;  // shared memory limits residency to ~3 blocks anyway
-  static Args make(const double* u, const double* v, const double* w, const double* gc, const double2* twz, double2* spec, int nx, int ny, int nz, int pz, int TX, double idx, double idz, double scale, const double* u_out) { return Args{u, v, w, gc, twz, spec, nx, ny, nz, pz, TX, idx, idz, scale, u_out}; }
+  static Args make(const double* u, const double* v, const double* w, const double* gc, const double2* twz, double2* spec, int nx, int ny, int nz, int pz, int TX, double idx, double idz, const StepK* sk, const double* u_out) { return Args{u, v, w, gc, twz, spec, nx, ny, nz, pz, TX, idx, idz, sk, u_out}; }
   static __device__ __forceinline__ void run(const Args& a_, const dim3 bid_, const dim3 gdim_) {
     const double* __restrict__ u = a_.u;
     const double* __restrict__ v = a_.v;
@@ -192,7 +192,7 @@ struct DivzK {
     int TX = a_.TX;
     double idx = a_.idx;
     double idz = a_.idz;
-    double scale = a_.scale;
+    const double scale = a_.sk->pscale;
     const double* __restrict__ u_out = a_.u_out;
 
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -432,6 +432,9 @@ struct IfftzK {
 // projection u = u* - s G phi; p += phi (if update_p).  One thread per (i, j) of a z-plane,
 // j = 0..ny.
 // ------------------------------------------------------------------------------------------
+// Dyn: sx, sz, s, beta_p from device memory, else from the arguments; KM: the Kim-Moin pressure
+// update (compiled only into the variants that use it)
+template <bool Dyn, bool KM>
 struct ProjectK {
   struct Args {
     double* u;
@@ -443,17 +446,15 @@ struct ProjectK {
     int nx;
     int ny;
     int nz;
-    double sx;
-    double sz;
+    const StepK* sk;  // sx, sz, s and the Kim-Moin beta_p (0: p += phi)
+    double sx, sz, s, beta_p;  // the same as arguments
     int update_p;
-    double s;
     int bl;
-    double beta_p;  // beta_k of the Kim-Moin pressure update (0: p += phi)
     double idx2, idz2;
   };
   static constexpr int kThreads = 128;
-  static constexpr int kMinBlocks = 16;
-  static Args make(double* u, double* v, double* w, double* p, const double* phi, const double* gc, int nx, int ny, int nz, double sx, double sz, int update_p, double s, int bl, double beta_p, double idx2, double idz2) { return Args{u, v, w, p, phi, gc, nx, ny, nz, sx, sz, update_p, s, bl, beta_p, idx2, idz2}; }
+  static constexpr int kMinBlocks = (Dyn || KM) ? 12 : 16;
+  static Args make(double* u, double* v, double* w, double* p, const double* phi, const double* gc, int nx, int ny, int nz, const StepK* sk, const StepK& kc, int update_p, int bl, double idx2, double idz2) { return Args{u, v, w, p, phi, gc, nx, ny, nz, sk, kc.sx, kc.sz, kc.s, kc.beta_p, update_p, bl, idx2, idz2}; }
   static __device__ __forceinline__ void run(const Args& a_, const dim3 bid_, const dim3 gdim_) {
     double* __restrict__ u = a_.u;
     double* __restrict__ v = a_.v;
@@ -464,10 +465,11 @@ struct ProjectK {
     int nx = a_.nx;
     int ny = a_.ny;
     int nz = a_.nz;
-    double sx = a_.sx;
-    double sz = a_.sz;
+    const double sx = Dyn ? a_.sk->sx : a_.sx;
+    const double sz = Dyn ? a_.sk->sz : a_.sz;
     int update_p = a_.update_p;
-    double s = a_.s;
+    const double s = Dyn ? a_.sk->s : a_.s;
+    const double beta_p = Dyn ? a_.sk->beta_p : a_.beta_p;
     int bl = a_.bl;
 
   const long plane = (long)nx * (ny + 1);
@@ -486,7 +488,7 @@ struct ProjectK {
     w[cc] -= sz * (f0 - __ldg(phi + km * pl + (long)j * nx + i));
     if (update_p) {
       double dp = f0;
-      if (a_.beta_p != 0.0) {
+      if (KM && beta_p != 0.0) {
         // Kim-Moin: p += phi - beta_k (D G phi), with G phi = 0 on the walls (PA_0 = PC_{ny-1} = 0)
         // and, with inflow / outflow, on the x = 0 and x = Lx faces
         const long row = k * pl + (long)j * nx;
@@ -504,7 +506,7 @@ struct ProjectK {
         const int kp = (k + 1 == nz) ? 0 : k + 1;
         const double lz = ((__ldg(phi + kp * pl + (long)j * nx + i) - f0) - (f0 - __ldg(phi + km * pl + (long)j * nx + i))) *
                           a_.idz2;
-        dp = f0 - a_.beta_p * (lx + ly + lz);
+        dp = f0 - beta_p * (lx + ly + lz);
       }
       p[cc] += dp;
     }
@@ -591,7 +593,8 @@ __global__ void __launch_bounds__(256) dctx_inv_kernel(double2* __restrict__ spe
 __global__ void outflow_kernel(const double* __restrict__ u, const double* __restrict__ v,
                                const double* __restrict__ w, double* __restrict__ u_out, double* __restrict__ v_out,
                                double* __restrict__ w_out, double* __restrict__ du, double* __restrict__ dv,
-                               double* __restrict__ dw, int nx, int ny, int nz, double cu, double cv) {
+                               double* __restrict__ dw, int nx, int ny, int nz, const StepK* __restrict__ sk) {
+  const double cu = sk->cu, cv = sk->cv;
   const long nu = (long)nz * ny, nv = (long)nz * (ny + 1);
   for (long q = (long)blockIdx.x * blockDim.x + threadIdx.x; q < 2 * nu + nv; q += (long)gridDim.x * blockDim.x) {
     if (q < nu) {
@@ -645,37 +648,39 @@ __global__ void __launch_bounds__(1024) flux_correct_kernel(const double* __rest
 }
 
 // ------------------------------------------------------------------------------------------
-// convective rate max over cells of |u|/dx + |v_c|/dy_j + |w|/dz (u, w on the cell's lower faces,
-// v_c the mean of its two y faces), the measure of the fixed-CFL time step.  Values are >= 0, so
-// their bit patterns order like the values and one atomicMax on the bits combines the blocks in
-// any order with the same result.  A non-finite value stores the bits of a NaN (above every
-// finite value) so that the host sees it.
+// convective rate max over cells of |u| (1/dx) + |v_c| (1/dy_j) + |w| (1/dz) (u, w on the cell's
+// lower faces, v_c the mean of its two y faces), the measure of the fixed-CFL time step.  Each
+// block walks (j, k) rows; the products and sums are rounded one by one (no contraction), so the
+// value of every cell, and the maximum, equal the plain definition.  Values are >= 0, so their
+// bit patterns order like the values and one atomicMax per block on the bits combines the blocks
+// in any order.  A non-finite value stores the bits of a NaN (above every finite value).
 // ------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) rate_kernel(const double* __restrict__ u, const double* __restrict__ v,
+__global__ void __launch_bounds__(128) rate_kernel(const double* __restrict__ u, const double* __restrict__ v,
                                                    const double* __restrict__ w, const double* __restrict__ gc,
-                                                   int nx, int ny, int nz, double dx, double dz,
+                                                   int nx, int ny, int nz, double ix, double iz,
                                                    unsigned long long* __restrict__ out) {
-  const long n = (long)nx * ny * nz;
-  const double* dy = gc + GC_DY * (ny + 1);
+  // ix = 1/dx, iz = 1/dz and the rows 1/dy_j (GC_IDY) are rounded on the host
   double m = 0.0;
   bool bad = false;
-  for (long q = (long)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (long)gridDim.x * blockDim.x) {
-    const long kj = q / nx;
-    const int i = (int)(q - kj * nx);
-    const int k = (int)(kj / ny);
-    const int j = (int)(kj - (long)k * ny);
-    const long vq = ((long)k * (ny + 1) + j) * nx + i;
-    const double vc = 0.5 * (__ldg(v + vq) + __ldg(v + vq + nx));
-    const double r = fabs(__ldg(u + q)) / dx + fabs(vc) / __ldg(dy + j) + fabs(__ldg(w + q)) / dz;
-    bad |= !(r <= 1.7976931348623157e308);
-    m = fmax(m, r);
+  for (int row = blockIdx.x; row < ny * nz; row += gridDim.x) {
+    const int k = row / ny, j = row - k * ny;
+    const double iy = __ldg(gc + GC_IDY * (ny + 1) + j);
+    const long c0 = ((long)k * ny + j) * nx;
+    const long v0 = ((long)k * (ny + 1) + j) * nx;
+    for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+      const double au = fabs(__ldg(u + c0 + i)), aw = fabs(__ldg(w + c0 + i));
+      const double av = fabs(__dmul_rn(0.5, __dadd_rn(__ldg(v + v0 + i), __ldg(v + v0 + nx + i))));
+      const double r = __dadd_rn(__dadd_rn(__dmul_rn(au, ix), __dmul_rn(av, iy)), __dmul_rn(aw, iz));
+      bad |= !(r <= 1.7976931348623157e308);
+      m = fmax(m, r);
+    }
   }
   for (int o = 16; o > 0; o >>= 1) {
     m = fmax(m, __shfl_xor_sync(NS_FULL_MASK, m, o));
     bad |= __shfl_xor_sync(NS_FULL_MASK, (int)bad, o) != 0;
   }
-  __shared__ double sm[8];
-  __shared__ int sb[8];
+  __shared__ double sm[4];
+  __shared__ int sb[4];
   if ((threadIdx.x & 31) == 0) {
     sm[threadIdx.x >> 5] = m;
     sb[threadIdx.x >> 5] = bad;
@@ -734,8 +739,10 @@ cudaError_t poisson_set_attributes() {
 cudaError_t launch_convective_rate(ns_ctx* c) {
   cudaError_t e = cudaMemsetAsync(c->rate, 0, sizeof(unsigned long long), c->launch);
   if (e != cudaSuccess) return e;
-  rate_kernel<<<4 * c->num_sms, 256, 0, c->launch>>>(c->f.u, c->f.v, c->f.w, c->gc, c->cfg.nx, c->cfg.ny, c->cfg.nz,
-                                                     c->dx, c->dz, c->rate);
+  const int rows = c->cfg.ny * c->cfg.nz;
+  const int blocks = rows < 16 * c->num_sms ? rows : 16 * c->num_sms;
+  rate_kernel<<<blocks, 128, 0, c->launch>>>(c->f.u, c->f.v, c->f.w, c->gc, c->cfg.nx, c->cfg.ny, c->cfg.nz,
+                                             1.0 / c->dx, 1.0 / c->dz, c->rate);
   return cudaGetLastError();
 }
 
@@ -789,9 +796,10 @@ cudaError_t stage_pois_divz(LaunchSink& s, int k) {
   ns_ctx* c = s.c;
   const PoisShape q = pois_shape(c);
   // 1/(alpha_k dt) of the right-hand side and 1/(nx nz) of the inverse transforms, applied once
-  const double scale = ((k >= 0) ? 1.0 / (NS_ALPHA[k] * c->cfg.dt) : 1.0) / ((double)q.nx * q.nz);
+  // (StepK::pscale)
   return emit<DivzK>(s, DivzK::make(c->f.u, c->f.v, c->f.w, c->gc, c->twz, c->spec, q.nx, q.ny, q.nz, q.pz, q.TX,
-                                    1.0 / c->dx, 1.0 / c->dz, scale, c->bl ? c->f.u_out : nullptr),
+                                    1.0 / c->dx, 1.0 / c->dz, c->stepk + stepk_index(k),
+                                    c->bl ? c->f.u_out : nullptr),
                      dim3(q.nx / q.TX, q.ny), dim3(256), q.smz);
 }
 
@@ -834,19 +842,25 @@ cudaError_t stage_pois_ifftz(LaunchSink& s, int) {
                       dim3(q.nx / q.TX, q.ny), dim3(256), q.smz);
 }
 
-// A10: projection u = u* - alpha_k dt G phi, p += phi
-cudaError_t stage_project(LaunchSink& s, int k) {
+template <bool Dyn, bool KM>
+cudaError_t emit_project(LaunchSink& s, int q, int k) {
   ns_ctx* c = s.c;
   const int nx = c->cfg.nx, ny = c->cfg.ny, nz = c->cfg.nz;
-  const double sc = (k >= 0) ? NS_ALPHA[k] * c->cfg.dt : 1.0;
   const long plane = (long)nx * (ny + 1);
   dim3 grid((unsigned)((plane + 127) / 128), nz);
-  const double inv_re = c->cfg.re > 0 ? 1.0 / c->cfg.re : 0.0;
-  const double beta_p = (k >= 0 && c->cfg.pressure_update == NS_PRESSURE_KIM_MOIN) ? sc * inv_re / 2.0 : 0.0;
-  return emit<ProjectK>(s, ProjectK::make(c->f.u, c->f.v, c->f.w, c->f.p, c->phi, c->gc, nx, ny, nz, sc / c->dx,
-                                          sc / c->dz, k >= 0 ? 1 : 0, sc, c->bl, beta_p, 1.0 / (c->dx * c->dx),
-                                          1.0 / (c->dz * c->dz)),
-                        grid, dim3(128), 0);
+  return emit<ProjectK<Dyn, KM>>(s, ProjectK<Dyn, KM>::make(c->f.u, c->f.v, c->f.w, c->f.p, c->phi, c->gc, nx, ny, nz,
+                                                            c->stepk + q, c->stepk_h[q], k >= 0 ? 1 : 0, c->bl,
+                                                            1.0 / (c->dx * c->dx), 1.0 / (c->dz * c->dz)),
+                                 grid, dim3(128), 0);
+}
+
+// A10: projection u = u* - alpha_k dt G phi, p += phi (or the Kim-Moin form)
+cudaError_t stage_project(LaunchSink& s, int k) {
+  ns_ctx* c = s.c;
+  const int q = stepk_index(k);
+  const bool km = c->cfg.pressure_update == NS_PRESSURE_KIM_MOIN;
+  if (c->dyn_consts) return km ? emit_project<true, true>(s, q, k) : emit_project<true, false>(s, q, k);
+  return km ? emit_project<false, true>(s, q, k) : emit_project<false, false>(s, q, k);
 }
 
 #define NS_SINGLE_LAUNCH(name, stage)   \
@@ -874,12 +888,10 @@ cudaError_t launch_poisson(ns_ctx* c, int k) {
 cudaError_t launch_outflow(ns_ctx* c, int k) {
   if (!c->bl) return cudaSuccess;
   const int nx = c->cfg.nx, ny = c->cfg.ny, nz = c->cfg.nz;
-  const double step = NS_ALPHA[k] * c->cfg.dt * c->cfg.u_conv;
   const long n = 2L * nz * ny + (long)nz * (ny + 1);
   const unsigned blocks = (unsigned)min((n + 255) / 256, 4096L);
   outflow_kernel<<<blocks, 256, 0, c->launch>>>(c->f.u, c->f.v, c->f.w, c->f.u_out, c->f.v_out, c->f.w_out,
-                                                c->dout[0], c->dout[1], c->dout[2], nx, ny, nz, step / c->dx,
-                                                step / (0.5 * c->dx));
+                                                c->dout[0], c->dout[1], c->dout[2], nx, ny, nz, c->stepk + k);
   return cudaGetLastError();
 }
 

@@ -36,33 +36,41 @@ struct RhsArgs {
   int nx, ny, nz;
   double idx, idz, idx2, idz2;
   double dt, gam, zet, alp, inv_re, fx;
-  // the tiled kernel's sub-step constants, formed once on the host in each arithmetic type
-  double kd[11];
-  float kf[11];
+  const StepK* sk;  // dt-dependent constants of this sub-step (device; read by the Dyn variants)
+  StepK kc;         // the same values as kernel arguments (read by the fixed-dt variants)
 };
 
 // indexes into RhsArgs::kd / kf
 enum { RK_QIDX, RK_QIDZ, RK_HIDX, RK_HIDZ, RK_CN, RK_CP, RK_CGX, RK_CGZ, RK_CX, RK_CZ, RK_CB };
 
-// The constants of RhsTiledK, each rounded to double (kd) and to float (kf) exactly as the
-// expressions would be in that type: the products of the double inputs are rounded once to the
-// type, and cx, cz are then formed in the type itself.
-void rhs_constants(RhsArgs& a) {
-  const double d[11] = {0.25 * a.idx, 0.25 * a.idz, 0.5 * a.idx, 0.5 * a.idz, -a.dt * a.gam, -a.dt * a.zet,
-                        -a.dt * a.alp * a.idx, -a.dt * a.alp * a.idz, 0.0, 0.0, a.dt * a.alp * a.fx};
-  const double cl = a.dt * a.alp * a.inv_re;
+}  // namespace
+
+// The constants of RhsTiledK for sub-step k, each rounded to double (kd) and to float (kf)
+// exactly as the expressions would be in that type: the products of the double inputs are
+// rounded once to the type, and cx, cz are then formed in the type itself.
+void rhs_fill_step(const ns_ctx* c, int k, StepK& sk) {
+  const double dt = c->cfg.dt, gam = NS_GAMMA[k], zet = NS_ZETA[k], alp = NS_ALPHA[k];
+  const double idx = 1.0 / c->dx, idz = 1.0 / c->dz, idx2 = idx * idx, idz2 = idz * idz;
+  const double inv_re = c->cfg.re > 0 ? 1.0 / c->cfg.re : 0.0;
+  const double d[11] = {0.25 * idx, 0.25 * idz, 0.5 * idx, 0.5 * idz, -dt * gam, -dt * zet,
+                        -dt * alp * idx, -dt * alp * idz, 0.0, 0.0, dt * alp * c->cfg.fx};
+  const double cl = dt * alp * inv_re;
   for (int q = 0; q < 11; ++q) {
-    a.kd[q] = d[q];
-    a.kf[q] = (float)d[q];
+    sk.kd[q] = d[q];
+    sk.kf[q] = (float)d[q];
   }
-  a.kd[RK_CX] = cl * a.idx2;
-  a.kd[RK_CZ] = cl * a.idz2;
+  sk.kd[RK_CX] = cl * idx2;
+  sk.kd[RK_CZ] = cl * idz2;
   const float clf = (float)cl;
-  a.kf[RK_CX] = clf * (float)a.idx2;
-  a.kf[RK_CZ] = clf * (float)a.idz2;
+  sk.kf[RK_CX] = clf * (float)idx2;
+  sk.kf[RK_CZ] = clf * (float)idz2;
 }
 
-template <typename T, typename TR>
+namespace {
+
+// Dyn: the sub-step constants are read from device memory (a step graph that outlives changes of
+// dt); otherwise from the kernel arguments, where they cost no registers.
+template <typename T, typename TR, bool Dyn>
 struct RhsK {
   struct Args {
     RhsArgs a;
@@ -112,7 +120,7 @@ struct RhsK {
   auto C = [&](int f, int jj) -> T { return from_double<T>(__ldg(a.gc + f * G + jj)); };
 
   const T idx = (T)a.idx, idz = (T)a.idz, idx2 = (T)a.idx2, idz2 = (T)a.idz2;
-  const T dt = (T)a.dt, gam = (T)a.gam, zet = (T)a.zet, alp = (T)a.alp;
+  const T dt = (T)(Dyn ? a.sk->dt : a.kc.dt), gam = (T)a.gam, zet = (T)a.zet, alp = (T)a.alp;
   const T avis = (T)(a.alp * a.inv_re);
   const T half = (T)0.5, quarter = (T)0.25, two = (T)2;
 
@@ -247,15 +255,16 @@ struct RhsTile {
   T fuw[RT_Z + 1][RT_X + 1];                 // x = i0 .. i0+TX, z = k0 .. k0+TZ
 };
 
-template <typename T, typename TR>
+template <typename T, typename TR, bool Dyn>
 struct RhsTiledK {
   struct Args {
     RhsArgs a;
     int jchunk;
   };
   static constexpr int kThreads = RT_X * RT_Z;
-  // FP64: shared memory allows 3 resident blocks, so up to 85 registers cost nothing; FP32 fits more
-  static constexpr int kMinBlocks = sizeof(T) == 8 ? 3 : 5;
+  // FP64: shared memory allows 3 resident blocks, so up to 85 registers cost nothing; FP32: 5 blocks,
+  // or 4 of up to 64 registers when the sub-step constants come from device memory
+  static constexpr int kMinBlocks = sizeof(T) == 8 ? 3 : (Dyn ? 4 : 5);
   static Args make(RhsArgs a, int jchunk) { return Args{a, jchunk}; }
   static __device__ __forceinline__ void run(const Args& a_, const dim3 bid_, const dim3 gdim_) {
     const RhsArgs& a = a_.a;
@@ -382,8 +391,9 @@ struct RhsTiledK {
   // r = cn N + cp N_prev + cgx (p_i - p_{i-1}) + cx (f_{i+1} + f_{i-1}) + cz (f_{k+1} + f_{k-1})
   //     + cA f_{j-1} + cC f_{j+1} + cD f (+ cb for u), with every constant pre-multiplied by dt
   auto K = [&](int q) -> T {
-    if constexpr (sizeof(T) == 4) return a.kf[q];
-    else return a.kd[q];
+    const StepK& sk = Dyn ? *a.sk : a.kc;
+    if constexpr (sizeof(T) == 4) return sk.kf[q];
+    else return sk.kd[q];
   };
   const T qidx = K(RK_QIDX), qidz = K(RK_QIDZ), hidx = K(RK_HIDX), hidz = K(RK_HIDZ);
   const T cn = K(RK_CN), cp = K(RK_CP), cgx = K(RK_CGX), cgz = K(RK_CGZ), cx = K(RK_CX), cz = K(RK_CZ);
@@ -481,20 +491,27 @@ struct RhsTiledK {
 }  // namespace
 
 cudaError_t rhs_set_attributes(int* bps_fp64, int* bps_fp32) {
-  cudaError_t e = set_smem_limit<RhsTiledK<double, double>>((int)sizeof(RhsTile<double>));
+  cudaError_t e;
+  if ((e = set_smem_limit<RhsTiledK<double, double, false>>((int)sizeof(RhsTile<double>))) != cudaSuccess ||
+      (e = set_smem_limit<RhsTiledK<double, double, true>>((int)sizeof(RhsTile<double>))) != cudaSuccess ||
+      (e = set_smem_limit<RhsTiledK<float, float, false>>((int)sizeof(RhsTile<float>))) != cudaSuccess ||
+      (e = set_smem_limit<RhsTiledK<float, float, true>>((int)sizeof(RhsTile<float>))) != cudaSuccess)
+    return e;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps_fp64, single_kernel<RhsTiledK<double, double, false>>,
+                                                    RT_X * RT_Z, sizeof(RhsTile<double>));
   if (e != cudaSuccess) return e;
-  e = set_smem_limit<RhsTiledK<float, float>>((int)sizeof(RhsTile<float>));
-  if (e != cudaSuccess) return e;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps_fp64, single_kernel<RhsTiledK<double, double>>, RT_X * RT_Z,
-                                                    sizeof(RhsTile<double>));
-  if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps_fp32, single_kernel<RhsTiledK<float, float>>, RT_X * RT_Z,
-                                                       sizeof(RhsTile<float>));
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps_fp32, single_kernel<RhsTiledK<float, float, false>>,
+                                                       RT_X * RT_Z, sizeof(RhsTile<float>));
 }
 
 cudaError_t launch_rhs(ns_ctx* c, int k) {
   LaunchSink s{c, nullptr};
   return stage_rhs(s, k);
+}
+
+template <typename T, bool Dyn>
+cudaError_t emit_tiled(LaunchSink& s, const RhsArgs& a, int jchunk, dim3 grid, dim3 block) {
+  return emit<RhsTiledK<T, T, Dyn>>(s, RhsTiledK<T, T, Dyn>::make(a, jchunk), grid, block, sizeof(RhsTile<T>));
 }
 
 cudaError_t stage_rhs(LaunchSink& s, int k) {
@@ -532,7 +549,8 @@ cudaError_t stage_rhs(LaunchSink& s, int k) {
   a.v_out = c->f.v_out;
   a.w_in = c->f.w_in;
   a.w_out = c->f.w_out;
-  rhs_constants(a);
+  a.sk = c->stepk + k;
+  a.kc = c->stepk_h[k];
   if (a.nx % RT_X == 0 && a.nz % RT_Z == 0) {
     // split y into chunks (each re-derives one face and two planes) so that the blocks fill
     // whole waves of the resident capacity: minimise waves * (planes per chunk + prologue)
@@ -554,13 +572,17 @@ cudaError_t stage_rhs(LaunchSink& s, int k) {
     const int nch = (a.ny + jchunk - 1) / jchunk;
     dim3 grid(a.nx / RT_X, a.nz / RT_Z, nch), block(RT_X, RT_Z);
     if (c->cfg.precision == NS_MIXED)
-      return emit<RhsTiledK<float, float>>(s, RhsTiledK<float, float>::make(a, jchunk), grid, block,
-                                           sizeof(RhsTile<float>));
-    return emit<RhsTiledK<double, double>>(s, RhsTiledK<double, double>::make(a, jchunk), grid, block,
-                                           sizeof(RhsTile<double>));
+      return c->dyn_consts ? emit_tiled<float, true>(s, a, jchunk, grid, block)
+                           : emit_tiled<float, false>(s, a, jchunk, grid, block);
+    // FP64 always reads them from device memory: the register allocation of that variant (80)
+    // is faster than the one with constant-bank operands (64) on this kernel
+    return emit_tiled<double, true>(s, a, jchunk, grid, block);
   }
   const long plane = (long)a.nx * (a.ny + 1);
   dim3 grid((unsigned)((plane + 127) / 128), (unsigned)a.nz);
-  if (c->cfg.precision == NS_MIXED) return emit<RhsK<float, float>>(s, RhsK<float, float>::make(a), grid, 128, 0);
-  return emit<RhsK<double, double>>(s, RhsK<double, double>::make(a), grid, 128, 0);
+  if (c->cfg.precision == NS_MIXED)
+    return c->dyn_consts ? emit<RhsK<float, float, true>>(s, RhsK<float, float, true>::make(a), grid, 128, 0)
+                         : emit<RhsK<float, float, false>>(s, RhsK<float, float, false>::make(a), grid, 128, 0);
+  return c->dyn_consts ? emit<RhsK<double, double, true>>(s, RhsK<double, double, true>::make(a), grid, 128, 0)
+                       : emit<RhsK<double, double, false>>(s, RhsK<double, double, false>::make(a), grid, 128, 0);
 }

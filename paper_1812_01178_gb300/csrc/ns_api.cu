@@ -74,6 +74,7 @@ ns_layout make_layout(const ns_config* c) {
   sz[LB_DOUT] = 3 * al256((ny + 1) * nz * 8) + 256;
   sz[LB_TWD] = nx * 16;
   sz[LB_RCY] = recycle_block_doubles((int)ny) * 8;
+  sz[LB_STEPK] = NS_STEPK * sizeof(StepK);
   size_t o = 0;
   for (int b = 0; b < LB_COUNT; ++b) {
     L.off[b] = o;
@@ -252,18 +253,74 @@ cudaError_t upload_d(ns_ctx* c, void* dst, const std::vector<double>& src);
 
 // Copy a host table to the device in the context's element type (double or float).  Waits for
 // the copy, so the host vector may be released afterwards.
-cudaError_t upload(ns_ctx* c, void* dst, const std::vector<double>& src) {
-  if (c->es == 8) return upload_d(c, dst, src);
-  std::vector<float> f(src.begin(), src.end());
-  cudaError_t e = cudaMemcpyAsync(dst, f.data(), f.size() * 4, cudaMemcpyHostToDevice, c->stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);  // f is a temporary
+// Host -> workspace copy of a table.  While c->staging, the bytes go to the pinned mirror and
+// the range is recorded (flush_staging copies it); otherwise a copy followed by a stream sync.
+cudaError_t upload_raw(ns_ctx* c, void* dst, const void* src, size_t bytes) {
+  const size_t off = (size_t)((char*)dst - (char*)c->ws);
+  if (c->staging && c->pin && off >= c->pin_lo && off + bytes <= c->pin_hi) {
+    memcpy(c->pin + (off - c->pin_lo), src, bytes);
+    c->dirty.emplace_back(off, bytes);
+    return cudaSuccess;
+  }
+  cudaError_t e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   return e;
 }
 
+cudaError_t upload(ns_ctx* c, void* dst, const std::vector<double>& src) {
+  if (c->es == 8) return upload_d(c, dst, src);
+  std::vector<float> f(src.begin(), src.end());
+  return upload_raw(c, dst, f.data(), f.size() * 4);
+}
+
 cudaError_t upload_d(ns_ctx* c, void* dst, const std::vector<double>& src) {
-  cudaError_t e = cudaMemcpyAsync(dst, src.data(), src.size() * 8, cudaMemcpyHostToDevice, c->stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  return upload_raw(c, dst, src.data(), src.size() * 8);
+}
+
+// Asynchronous copies of the staged ranges (pinned source: nothing waits).
+cudaError_t flush_staging(ns_ctx* c) {
+  cudaError_t e = cudaSuccess;
+  for (const auto& r : c->dirty)
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync((char*)c->ws + r.first, c->pin + (r.first - c->pin_lo), r.second, cudaMemcpyHostToDevice,
+                          c->stream);
+  c->dirty.clear();
   return e;
+}
+
+// The dt-dependent kernel constants of every sub-step (StepK) from cfg.dt and the x-solver levels.
+cudaError_t upload_step_constants(ns_ctx* c) {
+  const double dt = c->cfg.dt, nxz = (double)c->cfg.nx * c->cfg.nz;
+  const double inv_re = c->cfg.re > 0 ? 1.0 / c->cfg.re : 0.0;
+  for (int k = 0; k < 3; ++k) {
+    StepK& sk = c->stepk_h[k];
+    memset(&sk, 0, sizeof(sk));
+    rhs_fill_step(c, k, sk);
+    const double sc = NS_ALPHA[k] * dt;
+    sk.dt = dt;
+    sk.pscale = 1.0 / sc / nxz;
+    sk.sx = sc / c->dx;
+    sk.sz = sc / c->dz;
+    sk.s = sc;
+    sk.beta_p = c->cfg.pressure_update == NS_PRESSURE_KIM_MOIN ? sc * inv_re / 2.0 : 0.0;
+    const double step = sc * c->cfg.u_conv;
+    sk.cu = step / c->dx;
+    sk.cv = step / (0.5 * c->dx);
+    const double rx = NS_ALPHA[k] * dt * inv_re / 2.0 / (c->dx * c->dx);
+    sk.xcf[0] = rx;  // u: the outflow face is the neighbour of the last unknown face
+    sk.xcf[1] = 2.0 * rx;  // v, w: linear ghost 2 f_out - f_last
+    sk.xcf[2] = 2.0 * rx;
+    for (int q = 0; q < 3; ++q) sk.xcff[q] = (float)sk.xcf[q];
+    sk.L = c->L[k];
+  }
+  StepK& s3 = c->stepk_h[3];  // projection of an initial field: scale 1
+  memset(&s3, 0, sizeof(s3));
+  s3.dt = dt;
+  s3.pscale = 1.0 / nxz;
+  s3.sx = 1.0 / c->dx;
+  s3.sz = 1.0 / c->dz;
+  s3.s = 1.0;
+  return upload_raw(c, c->stepk, c->stepk_h, sizeof(c->stepk_h));
 }
 
 double beta_of(const ns_ctx* c, int k) {
@@ -323,7 +380,8 @@ ns_status build_x_tables(ns_ctx* c) {
       if (upload(c, c->xtab[k][cls], tabs[k][cls][sel]) != cudaSuccess) return NS_ERR_CUDA;
     }
   }
-  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return NS_ERR_CUDA;
+  if (upload_step_constants(c) != cudaSuccess) return NS_ERR_CUDA;
+  if (!c->staging && cudaStreamSynchronize(c->stream) != cudaSuccess) return NS_ERR_CUDA;
   return NS_OK;
 }
 
@@ -360,7 +418,7 @@ ns_status build_dt_tables(ns_ctx* c) {
                            k * al256((size_t)RT_COUNT * G * 4));
     {
       std::vector<float> rf(rt.begin(), rt.end());
-      if (cudaMemcpy(c->rtabf[k], rf.data(), rf.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess) st = NS_ERR_CUDA;
+      if (upload_raw(c, c->rtabf[k], rf.data(), rf.size() * 4) != cudaSuccess) st = NS_ERR_CUDA;
     }
   }
   // ADI y and z factors per sub-step
@@ -420,7 +478,7 @@ ns_status build_dt_tables(ns_ctx* c) {
       if (upload(c, c->ztab[k], t) != cudaSuccess) st = NS_ERR_CUDA;
     }
   }
-  if (st == NS_OK && cudaStreamSynchronize(c->stream) != cudaSuccess) st = NS_ERR_CUDA;
+  if (st == NS_OK && !c->staging && cudaStreamSynchronize(c->stream) != cudaSuccess) st = NS_ERR_CUDA;
   return st;
 }
 
@@ -484,19 +542,13 @@ ns_status run_substep(ns_ctx* c, int k, cudaEvent_t* ev = nullptr) {
   return NS_OK;
 }
 
-// Capture the three sub-steps of one time step into a graph (optionally with event nodes).
-// Captures one step (3 sub-steps) into *graph and instantiates it into *exec; with update, *exec
-// holds an instantiated graph of the same stages, which is updated in place when possible.
-ns_status capture_step(ns_ctx* c, bool profiled, cudaGraph_t* graph, cudaGraphExec_t* exec, bool update = false) {
-  // on failure with update, *exec is destroyed (the caller drops the graph)
-  auto drop_exec = [&]() {
-    if (update) cudaGraphExecDestroy(*exec);
-  };
+// Capture the three sub-steps of one time step into a graph (optionally with event nodes) and
+// instantiate it.
+ns_status capture_step(ns_ctx* c, bool profiled, cudaGraph_t* graph, cudaGraphExec_t* exec) {
   c->launch = c->cap_stream;
   cudaError_t e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) {
     c->launch = c->stream;
-    drop_exec();
     return cuda_fail(c, e, "begin capture");
   }
   ns_status s = NS_OK;
@@ -507,23 +559,9 @@ ns_status capture_step(ns_ctx* c, bool profiled, cudaGraph_t* graph, cudaGraphEx
   c->launch = c->stream;
   if (s != NS_OK) {
     if (g) cudaGraphDestroy(g);
-    drop_exec();
     return s;
   }
-  if (e != cudaSuccess) {
-    drop_exec();
-    return cuda_fail(c, e, "end capture");
-  }
-  if (update) {
-    // same stages, new kernel arguments (a new dt): update the instantiated graph in place
-    cudaGraphExecUpdateResultInfo info;
-    if (cudaGraphExecUpdate(*exec, g, &info) == cudaSuccess) {
-      *graph = g;
-      return NS_OK;
-    }
-    cudaGetLastError();
-    cudaGraphExecDestroy(*exec);
-  }
+  if (e != cudaSuccess) return cuda_fail(c, e, "end capture");
   if ((e = cudaGraphInstantiate(exec, g, 0)) != cudaSuccess) {
     cudaGraphDestroy(g);
     return cuda_fail(c, e, "graph instantiate");
@@ -641,6 +679,7 @@ ns_status ns_init(ns_ctx** out, const ns_config* cfg, const ns_fields* fields, v
   c->flux = (double*)(base + c->lay.off[LB_DOUT] + 3 * al256((size_t)(ny + 1) * nz * 8));
   c->rate = (unsigned long long*)(c->flux + 4);
   c->rcy = (double*)(base + c->lay.off[LB_RCY]);
+  c->stepk = (StepK*)(base + c->lay.off[LB_STEPK]);
   c->twd = (double2*)(base + c->lay.off[LB_TWD]);
   double* lamz_d = (double*)(base + c->lay.off[LB_LAMZ]);
 
@@ -815,21 +854,10 @@ ns_status ns_step(ns_ctx* c, int nsteps) {
   if (nsteps < 0) return fail(c, NS_ERR_ARG, "nsteps must be >= 0");
   if (nsteps == 0) return NS_OK;
   if (capturing(c)) return fail(c, NS_ERR_STATE, "ns_step called while its stream is being captured");
-  if (c->have_graph && c->graph_stale) {
-    cudaGraph_t old = c->graph;
-    ns_status s = capture_step(c, false, &c->graph, &c->gexec, true);
-    cudaGraphDestroy(old);
-    c->graph_stale = false;
-    if (s != NS_OK) {
-      c->have_graph = false;
-      return s;
-    }
-  }
   if (!c->have_graph) {
     ns_status s = capture_step(c, false, &c->graph, &c->gexec);
     if (s != NS_OK) return s;
     c->have_graph = true;
-    c->graph_stale = false;
   }
   cudaError_t e;
   for (int s = 0; s < nsteps; ++s)
@@ -857,33 +885,39 @@ ns_status ns_set_dt(ns_ctx* c, double dt) {
   if (!c) return NS_ERR_ARG;
   if (!(dt > 0.0) || !std::isfinite(dt)) return fail(c, NS_ERR_ARG, "dt must be positive and finite");
   if (capturing(c)) return fail(c, NS_ERR_STATE, "ns_set_dt during capture");
+  // the staging mirror may still feed copies of the previous call
   if (cudaStreamSynchronize(c->stream) != cudaSuccess) return fail(c, NS_ERR_CUDA, "sync");
+  if (!c->pin) {
+    // workspace bytes of the dt tables and the step constants
+    c->pin_lo = c->lay.off[LB_XTAB];
+    c->pin_hi = c->lay.off[LB_STEPK] + NS_STEPK * sizeof(StepK);
+    if (cudaMallocHost(&c->pin, c->pin_hi - c->pin_lo) != cudaSuccess) {
+      c->pin = nullptr;
+      return fail(c, NS_ERR_CUDA, "pinned staging buffer");
+    }
+  }
   const double old = c->cfg.dt;
   c->cfg.dt = dt;
+  c->staging = true;
+  c->dirty.clear();
   ns_status s = build_dt_tables(c);
   if (s == NS_OK) s = build_x_tables(c);
-  // the step graph is re-captured and updated in place by the next ns_step; the profiled one is
-  // dropped
-  const bool keep = c->have_graph;
-  const cudaGraph_t g = c->graph;
-  const cudaGraphExec_t x = c->gexec;
-  c->have_graph = false;
-  drop_graph(c);
-  if (keep && s == NS_OK) {
-    c->graph = g;
-    c->gexec = x;
-    c->have_graph = true;
-    c->graph_stale = true;
-  } else if (keep) {
-    cudaGraphExecDestroy(x);
-    cudaGraphDestroy(g);
-  }
+  c->staging = false;
   if (s != NS_OK) {
+    c->dirty.clear();
     c->cfg.dt = old;
     build_dt_tables(c);
     build_x_tables(c);
     return fail(c, s, "rebuilding the dt tables failed");
   }
+  // from now on every kernel reads the sub-step constants from the workspace, so the step graph,
+  // captured once more here, stays valid across later changes of dt
+  if (!c->dyn_consts) {
+    c->dyn_consts = true;
+    drop_graph(c);
+  }
+  cudaError_t e = flush_staging(c);
+  if (e != cudaSuccess) return cuda_fail(c, e, "dt table copies");
   return NS_OK;
 }
 
@@ -1082,6 +1116,7 @@ void ns_destroy(ns_ctx* c) {
   drop_graph(c);
   for (int q = 0; q < c->npev; ++q) cudaEventDestroy(c->pev[q]);
   cudaStreamDestroy(c->cap_stream);
+  if (c->pin) cudaFreeHost(c->pin);
   if (c->own_ws) cudaFree(c->ws);
   delete c;
 }

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/ns.h"
@@ -137,8 +138,26 @@ struct ns_layout {
 
 enum {
   LB_RU = 0, LB_RV, LB_RW, LB_NU, LB_NV, LB_NW, LB_PHI, LB_SPEC, LB_POIS, LB_GC, LB_XTAB, LB_YTAB,
-  LB_ZTAB, LB_TWZ, LB_TWX, LB_LAMX, LB_LAMZ, LB_RTAB, LB_DOUT, LB_TWD, LB_RCY, LB_COUNT
+  LB_ZTAB, LB_TWZ, LB_TWX, LB_LAMX, LB_LAMZ, LB_RTAB, LB_DOUT, LB_TWD, LB_RCY, LB_STEPK, LB_COUNT
 };
+
+// dt-dependent constants of one RK3 sub-step (entries 0..2) and of the projection of an initial
+// field (entry 3).  They live in device memory, so a new dt reaches every kernel of a captured
+// step without capturing it again.
+struct StepK {
+  double dt;          // the time step
+  double kd[11];      // tiled RHS constants in double (RhsTiledK)
+  float kf[12];       // the same rounded to float (11 used)
+  double pscale;      // divergence scale 1 / (alpha_k dt nx nz) (1 / (nx nz) for entry 3)
+  double sx, sz, s;   // projection: alpha_k dt / dx, alpha_k dt / dz, alpha_k dt
+  double beta_p;      // Kim-Moin beta_k (0 with the plain pressure update)
+  double cu, cv;      // convective outflow: alpha_k dt U_c / dx and / (dx / 2)
+  double xcf[3];      // outflow increment weights of the x sweep (u, v, w): r, 2r, 2r, r = beta_k / dx^2
+  float xcff[4];      // the same in float (3 used)
+  int L;              // reduction levels of the x solve (0: PDD)
+  int pad;
+};
+constexpr int NS_STEPK = 4;
 
 struct ns_ctx {
   ns_config cfg;
@@ -175,6 +194,15 @@ struct ns_ctx {
   unsigned long long* rate; // bits of the convective rate of ns_convective_rate (in the flux block)
   std::vector<double> gc_h; // host copy of the grid coefficients (tables are rebuilt when dt changes)
   double* rcy;              // recycling inflow: sample heights, plane means, gamma (k_recycle.cu)
+  StepK* stepk;             // device: dt-dependent constants per sub-step (NS_STEPK entries)
+  StepK stepk_h[NS_STEPK];  // host image of stepk
+  // ns_set_dt stages the rebuilt tables in pinned host memory (a mirror of the workspace bytes
+  // [pin_lo, pin_hi)) and copies the written ranges asynchronously
+  char* pin = nullptr;
+  size_t pin_lo = 0, pin_hi = 0;
+  bool staging = false;
+  bool dyn_consts = false;  // set by ns_set_dt: kernels read the sub-step constants from stepk
+  std::vector<std::pair<size_t, size_t>> dirty;  // (workspace offset, bytes) written while staging
   int num_sms;
   int rhs_bps[2];           // resident blocks per SM of the tiled RHS (FP64, FP32)
   // partitioned x solver
@@ -187,7 +215,6 @@ struct ns_ctx {
   cudaGraph_t graph;
   cudaGraphExec_t gexec;
   bool have_graph;
-  bool graph_stale = false;  // kernel arguments changed (ns_set_dt): update gexec before launching
   // profiled graph: the same launches with an event recorded before each kernel and after the
   // last one
   cudaGraph_t pgraph;
@@ -383,6 +410,8 @@ cudaError_t launch_outflow(ns_ctx* c, int k);        // convective outflow updat
 cudaError_t launch_flux_correct(ns_ctx* c, int k);   // outflow volume flux := inflow flux
 cudaError_t launch_pois_factor(ns_ctx* c, const double* lamx, const double* lamz);
 cudaError_t launch_convective_rate(ns_ctx* c);  // max-reduction into c->rate (zeroed first)
+void rhs_fill_step(const ns_ctx* c, int k, StepK& sk);  // RHS part of StepK (k_rhs.cu)
+inline int stepk_index(int k) { return k < 0 ? 3 : k; }
 cudaError_t launch_recycle(ns_ctx* c, int k);    // recycled inflow planes (sub-step 0, if enabled)
 size_t recycle_block_doubles(int ny);
 cudaError_t recycle_upload_grid(ns_ctx* c);

@@ -32,11 +32,12 @@ double h_twz[6 * 4096];
 double h_twx[6 * 4096];
 double h_lamx[4096];
 double h_lamz[2049];
+StepK h_stepk[NS_STEPK];
 
 size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Regions {
-  size_t spec, pois, gc, twz, twx, lamx, lamz, total;
+  size_t spec, pois, gc, twz, twx, lamx, lamz, stepk, total;
 };
 
 Regions regions(int nx, int ny, int nz) {
@@ -57,6 +58,8 @@ Regions regions(int nx, int ny, int nz) {
   o += al256((size_t)nx * 8);
   r.lamz = o;
   o += al256(nzh * 8);
+  r.stepk = o;
+  o += al256(NS_STEPK * sizeof(StepK));
   r.total = o;
   return r;
 }
@@ -131,6 +134,10 @@ extern "C" ns_status ns_poisson_solve_static(const ns_config* cfg, const double*
   }
   for (int q = 0; q <= nz / 2; ++q) h_lamz[q] = (2.0 / (dz * dz)) * (1.0 - std::cos(2.0 * PI * q / nz));
 
+  // divergence scale of the requested sub-step (the only dt-dependent constant of the solve)
+  for (int q = 0; q < NS_STEPK; ++q) h_stepk[q] = StepK{};
+  h_stepk[stepk_index(substep)].pscale =
+      ((substep >= 0) ? 1.0 / (NS_ALPHA[substep] * cfg->dt) : 1.0) / ((double)nx * nz);
   cudaStream_t st = (cudaStream_t)cuda_stream;
   const struct {
     size_t off;
@@ -138,7 +145,7 @@ extern "C" ns_status ns_poisson_solve_static(const ns_config* cfg, const double*
     size_t bytes;
   } up[] = {{R.gc, h_gc, (size_t)NS_GC_COUNT * G * 8}, {R.twz, h_twz, fft_twiddle_doubles(nz) * 8},
             {R.twx, h_twx, fft_twiddle_doubles(nx) * 8},           {R.lamx, h_lamx, (size_t)nx * 8},
-            {R.lamz, h_lamz, (size_t)(nz / 2 + 1) * 8}};
+            {R.lamz, h_lamz, (size_t)(nz / 2 + 1) * 8}, {R.stepk, h_stepk, sizeof(h_stepk)}};
   for (const auto& q : up)
     if ((e = cudaMemcpyAsync(base + q.off, q.src, q.bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess)
       return fail(NS_ERR_CUDA, std::string("table upload: ") + cudaGetErrorString(e));
@@ -164,6 +171,7 @@ extern "C" ns_status ns_poisson_solve_static(const ns_config* cfg, const double*
   c.gc = (double*)(base + R.gc);
   c.twz = (double2*)(base + R.twz);
   c.twx = (double2*)(base + R.twx);
+  c.stepk = (StepK*)(base + R.stepk);
   if ((e = launch_pois_factor(&c, (const double*)(base + R.lamx), (const double*)(base + R.lamz))) != cudaSuccess)
     return fail(NS_ERR_CUDA, std::string("factor table: ") + cudaGetErrorString(e));
   if ((e = launch_poisson(&c, substep)) != cudaSuccess)
