@@ -282,6 +282,129 @@ struct AdiXLongK {
 };
 
 // ----------------------------------------------------------------------------------------------
+// y and z lines of the mixed form, partitioned (Sec. 3.2, the paper's own use of PDD/PPT on the
+// wall-normal lines): a block holds 32 consecutive lines (x) by P partitions of M rows, and
+// thread (tx, r) keeps rows rM .. rM+M-1 of line tx in registers.  Each element is loaded and
+// stored once, coalesced across tx, instead of the forward sweep's write and the back sweep's
+// re-read of the thread-per-line solver.  The P interfaces of a line form the same 2x2-block
+// reduced system as on x-lines (Eq. Zpdd); it is solved through shared memory, by block PCR
+// (L levels) or, when its dropped coupling is negligible, by its diagonal blocks (PDD, L = 0).
+// Tables: the x-solver layout (xtab_count) built by the host for the rows of each direction:
+// y centres (u, w), y faces (v; the wall row 0 enters as an identity row), z (cyclic).  The z
+// lines end with u* = u + delta in FP64.
+// ----------------------------------------------------------------------------------------------
+template <int P, int M, bool ZDIR>
+struct AdiLinePK {
+  struct Args {
+    float* r[3];
+    double* f[3];
+    const float* tab[2];  // y: [0] centres, [1] faces; z: [0]
+    const StepK* sk;      // levels Ly / Lz of this sub-step
+    int nx, ny, nz;
+  };
+  static constexpr int kThreads = 32 * P;
+  static constexpr int kMinBlocks = 1;
+  static Args make(float* ru, float* rv, float* rw, double* u, double* v, double* w, const float* t0, const float* t1,
+                   const StepK* sk, int nx, int ny, int nz) {
+    return Args{{ru, rv, rw}, {u, v, w}, {t0, t1}, sk, nx, ny, nz};
+  }
+  static __device__ __forceinline__ void run(const Args& a, const dim3 bid_, const dim3 gdim_) {
+    constexpr int LMAX = P == 8 ? 3 : (P == 16 ? 4 : 5);
+    const int nx = a.nx, ny = a.ny;
+    const int comp = bid_.z;
+    const int tx = threadIdx.x & 31, r = threadIdx.x >> 5;
+    const int i = bid_.x * 32 + tx;
+    int L;
+    long base, stride;
+    const float* gtab;
+    if constexpr (ZDIR) {
+      const int j = bid_.y + (comp == 1 ? 1 : 0);
+      if (comp == 1 && j > ny - 1) return;  // uniform over the block
+      base = (long)j * nx + i;
+      stride = (long)(comp == 1 ? ny + 1 : ny) * nx;
+      gtab = a.tab[0];
+      L = a.sk->Lz;
+    } else {
+      const int k = bid_.y;
+      base = (long)k * (comp == 1 ? ny + 1 : ny) * nx + i;
+      stride = nx;
+      gtab = a.tab[comp == 1 ? 1 : 0];
+      L = a.sk->Ly;
+    }
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float* st = reinterpret_cast<float*>(smem_raw);
+    float* ex0 = st + xtab_count(M, P, LMAX);  // [P][32]
+    float* ex1 = ex0 + P * 32;
+    const int ntab = (int)xtab_count(M, P, L);
+    for (int q = threadIdx.x; q < ntab; q += blockDim.x) st[q] = __ldg(gtab + q);
+    float* line = (comp == 0 ? a.r[0] : comp == 1 ? a.r[1] : a.r[2]) + base;
+    float d[M];
+#pragma unroll
+    for (int e = 0; e < M; ++e) d[e] = line[(long)(r * M + e) * stride];
+    __syncthreads();
+    const float* INV = st + XT_INV * M * P;
+    const float* AINV = st + XT_AINV * M * P;
+    const float* CP = st + XT_CP * M * P;
+    const float* SV = st + XT_V * M * P;
+    const float* SW = st + XT_W * M * P;
+    const float* DINV = st + XT_NF * M * P;
+    const float* ML = DINV + 4 * P;
+    const float* MU = ML + 4 * L * P;
+    // A~ x~ = d on this partition
+    d[0] = d[0] * INV[r];
+#pragma unroll
+    for (int e = 1; e < M; ++e) d[e] = d[e] * INV[e * P + r] - AINV[e * P + r] * d[e - 1];
+#pragma unroll
+    for (int e = M - 2; e >= 0; --e) d[e] = d[e] - CP[e * P + r] * d[e + 1];
+    // interface r: g = (x~^{(r)}_m, x~^{(r+1)}_1)
+    ex0[r * 32 + tx] = d[0];
+    __syncthreads();
+    float g0 = d[M - 1];
+    float g1 = ex0[((r + 1) % P) * 32 + tx];
+    for (int lv = 0, sd = 1; lv < L; ++lv, sd <<= 1) {
+      __syncthreads();
+      ex0[r * 32 + tx] = g0;
+      ex1[r * 32 + tx] = g1;
+      __syncthreads();
+      const int rm = (r - sd + P) % P, rp = (r + sd) % P;
+      const float h0 = ex0[rm * 32 + tx], h1 = ex1[rm * 32 + tx];
+      const float k0 = ex0[rp * 32 + tx], k1 = ex1[rp * 32 + tx];
+      const float* ml = ML + 4 * lv * P;
+      const float* mu = MU + 4 * lv * P;
+      const float n0 = g0 - ml[r] * h0 - ml[P + r] * h1 - mu[r] * k0 - mu[P + r] * k1;
+      const float n1 = g1 - ml[2 * P + r] * h0 - ml[3 * P + r] * h1 - mu[2 * P + r] * k0 - mu[3 * P + r] * k1;
+      g0 = n0;
+      g1 = n1;
+    }
+    const float y0 = DINV[r] * g0 + DINV[P + r] * g1;          // x^{(r)}_m
+    const float y1 = DINV[2 * P + r] * g0 + DINV[3 * P + r] * g1;  // x^{(r+1)}_1
+    __syncthreads();
+    ex0[r * 32 + tx] = y0;
+    __syncthreads();
+    const float left = ex0[((r + P - 1) % P) * 32 + tx];  // x^{(r-1)}_m
+#pragma unroll
+    for (int e = 0; e < M; ++e) d[e] = d[e] - SV[e * P + r] * left - SW[e * P + r] * y1;
+    if constexpr (ZDIR) {
+      double* f = (comp == 0 ? a.f[0] : comp == 1 ? a.f[1] : a.f[2]) + base;
+      constexpr int U = 8;  // u rows in flight at a time (bounds the registers of the FP64 values)
+#pragma unroll
+      for (int e0 = 0; e0 < M; e0 += U) {
+        double fv[U];
+#pragma unroll
+        for (int q = 0; q < U; ++q)
+          if (e0 + q < M) fv[q] = f[(long)(r * M + e0 + q) * stride];
+#pragma unroll
+        for (int q = 0; q < U; ++q)
+          if (e0 + q < M) f[(long)(r * M + e0 + q) * stride] = fv[q] + f2d(d[e0 + q]);
+      }
+    } else {
+#pragma unroll
+      for (int e = 0; e < M; ++e) line[(long)(r * M + e) * stride] = d[e];
+    }
+  }
+};
+
+// ----------------------------------------------------------------------------------------------
 // y: one thread per line, Thomas with precomputed factors [INV, AINV, CP][n]
 // ----------------------------------------------------------------------------------------------
 template <typename T>
@@ -541,9 +664,44 @@ cudaError_t stage_adi_x(LaunchSink& s, int k) {
   return launch_x_m<double>(s, k);
 }
 
+template <int P, int M, bool ZDIR>
+cudaError_t emit_line_part(LaunchSink& s, int k) {
+  ns_ctx* c = s.c;
+  const int nx = c->cfg.nx, ny = c->cfg.ny, nz = c->cfg.nz;
+  constexpr int LMAX = P == 8 ? 3 : (P == 16 ? 4 : 5);
+  const size_t smem = (xtab_count(M, P, LMAX) + 2 * P * 32) * sizeof(float);
+  const dim3 grid(nx / 32, ZDIR ? ny : nz, 3);
+  const float* t0 = (const float*)c->ptab[k][ZDIR ? 2 : 0];
+  const float* t1 = (const float*)c->ptab[k][ZDIR ? 2 : 1];
+  return emit<AdiLinePK<P, M, ZDIR>>(s, AdiLinePK<P, M, ZDIR>::make((float*)c->ru, (float*)c->rv, (float*)c->rw,
+                                                                    c->f.u, c->f.v, c->f.w, t0, t1, c->stepk + k, nx,
+                                                                    ny, nz),
+                                     grid, dim3(32 * P), smem);
+}
+
+// the partitioned y / z line solver of shape (P, n / P), if one is built
+template <bool ZDIR>
+cudaError_t launch_line_part(LaunchSink& s, int k, int P, int n) {
+  const int M = n / P;
+  switch (P * 1000 + M) {
+    case 8004: return emit_line_part<8, 4, ZDIR>(s, k);
+    case 8006: return emit_line_part<8, 6, ZDIR>(s, k);
+    case 8008: return emit_line_part<8, 8, ZDIR>(s, k);
+    case 8012: return emit_line_part<8, 12, ZDIR>(s, k);
+    case 8016: return emit_line_part<8, 16, ZDIR>(s, k);
+    case 8024: return emit_line_part<8, 24, ZDIR>(s, k);
+    case 8032: return emit_line_part<8, 32, ZDIR>(s, k);
+    case 16018: return emit_line_part<16, 18, ZDIR>(s, k);
+    case 16032: return emit_line_part<16, 32, ZDIR>(s, k);
+    case 32032: return emit_line_part<32, 32, ZDIR>(s, k);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 cudaError_t stage_adi_y(LaunchSink& s, int k) {
   ns_ctx* c = s.c;
   const int nx = c->cfg.nx, ny = c->cfg.ny, nz = c->cfg.nz;
+  if (c->yP) return launch_line_part<false>(s, k, c->yP, ny);
   dim3 grid((nx + 127) / 128, nz, 3);
   if (c->cfg.precision == NS_MIXED)
     return emit<AdiYK<float>>(s, AdiYK<float>::make((float*)c->ru, (float*)c->rv, (float*)c->rw,
@@ -557,6 +715,7 @@ cudaError_t stage_adi_y(LaunchSink& s, int k) {
 cudaError_t stage_adi_z(LaunchSink& s, int k) {
   ns_ctx* c = s.c;
   const int nx = c->cfg.nx, ny = c->cfg.ny, nz = c->cfg.nz;
+  if (c->zP) return launch_line_part<true>(s, k, c->zP, nz);
   dim3 grid((nx + 127) / 128, ny, 3);
   if (c->cfg.precision == NS_MIXED)
     return emit<AdiZK<float>>(s, AdiZK<float>::make((float*)c->ru, (float*)c->rv, (float*)c->rw, c->f.u, c->f.v,
@@ -602,9 +761,24 @@ cudaError_t x_attributes() {
   return set_smem_limit<AdiXLongK<T, 64>>(4 * 32 * 65 * (int)sizeof(T));
 }
 
+template <int P, int M>
+cudaError_t line_attr() {
+  constexpr int LMAX = P == 8 ? 3 : (P == 16 ? 4 : 5);
+  const int bytes = (int)((xtab_count(M, P, LMAX) + 2 * P * 32) * sizeof(float));
+  cudaError_t e = set_smem_limit<AdiLinePK<P, M, false>>(bytes);
+  if (e != cudaSuccess) return e;
+  return set_smem_limit<AdiLinePK<P, M, true>>(bytes);
+}
+
 cudaError_t adi_set_attributes() {
   cudaError_t e = x_attributes<double>();
   if (e != cudaSuccess) return e;
+  if ((e = line_attr<8, 4>()) != cudaSuccess || (e = line_attr<8, 6>()) != cudaSuccess ||
+      (e = line_attr<8, 8>()) != cudaSuccess || (e = line_attr<8, 12>()) != cudaSuccess ||
+      (e = line_attr<8, 16>()) != cudaSuccess || (e = line_attr<8, 24>()) != cudaSuccess ||
+      (e = line_attr<8, 32>()) != cudaSuccess || (e = line_attr<16, 18>()) != cudaSuccess ||
+      (e = line_attr<16, 32>()) != cudaSuccess || (e = line_attr<32, 32>()) != cudaSuccess)
+    return e;
   return x_attributes<float>();
 }
 

@@ -1,4 +1,5 @@
 // C ABI entry points, workspace layout, coefficient tables and graph capture.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -46,6 +47,28 @@ std::string check_cfg(const ns_config* c, ns_status* kind = nullptr) {
   return "";
 }
 
+int ilog2i(int n) {
+  int l = 0;
+  while ((1 << l) < n) ++l;
+  return l;
+}
+
+// Partitioned y / z lines are used by the mixed form when x is a multiple of 32 (one block holds
+// 32 lines) and the line length has a built shape.
+int line_P(const ns_config* c, int n) {
+  if (c->precision != NS_MIXED || c->nx % 32 != 0) return 0;
+  return line_partition(n);
+}
+
+// floats of one partitioned-line table (the larger of the y and z shapes, PPT levels included)
+size_t line_table_floats(const ns_config* c) {
+  size_t m = 0;
+  const int py = line_P(c, c->ny), pz = line_P(c, c->nz);
+  if (py) m = std::max(m, xtab_count(c->ny / py, py, ilog2i(py)));
+  if (pz) m = std::max(m, xtab_count(c->nz / pz, pz, ilog2i(pz)));
+  return m;
+}
+
 ns_layout make_layout(const ns_config* c) {
   ns_layout L;
   memset(&L, 0, sizeof(L));
@@ -75,6 +98,7 @@ ns_layout make_layout(const ns_config* c) {
   sz[LB_TWD] = nx * 16;
   sz[LB_RCY] = recycle_block_doubles((int)ny) * 8;
   sz[LB_STEPK] = NS_STEPK * sizeof(StepK);
+  sz[LB_PTAB] = 9 * al256(line_table_floats(c) * 4);
   size_t o = 0;
   for (int b = 0; b < LB_COUNT; ++b) {
     L.off[b] = o;
@@ -312,6 +336,8 @@ cudaError_t upload_step_constants(ns_ctx* c) {
     sk.xcf[2] = 2.0 * rx;
     for (int q = 0; q < 3; ++q) sk.xcff[q] = (float)sk.xcf[q];
     sk.L = c->L[k];
+    sk.Ly = c->yL[k];
+    sk.Lz = c->zL[k];
   }
   StepK& s3 = c->stepk_h[3];  // projection of an initial field: scale 1
   memset(&s3, 0, sizeof(s3));
@@ -352,6 +378,69 @@ void x_rows(const ns_ctx* c, int k, int cls, std::vector<double>& a, std::vector
   }
 }
 
+// Tables of the partitioned y and z lines of the mixed form (AdiLinePK), every sub-step: the rows
+// of the thread-per-line solvers, split into P partitions by build_xtab.  y centres (u, w) and y
+// faces (v, with the wall row 0 as an identity row) are not periodic; z is.  PDD when the
+// coupling it drops stays below the FP32 tolerance for every sub-step of the direction, else PPT.
+ns_status build_line_tables(ns_ctx* c) {
+  if (!c->yP && !c->zP) return NS_OK;
+  const int ny = c->cfg.ny, nz = c->cfg.nz, G = ny + 1;
+  auto GCv = [&](int f, int j) -> double { return c->gc_h[(size_t)f * G + j]; };
+  const double tol = 1e-8;
+  std::vector<double> tabs[3][3][2];
+  int levs[3][3][2];
+  double ydrop = 0.0, zdrop = 0.0;
+  for (int k = 0; k < 3; ++k) {
+    const double beta = beta_of(c, k);
+    if (c->yP) {
+      std::vector<double> a(ny), b(ny), cc(ny);
+      for (int j = 0; j < ny; ++j) {
+        a[j] = -beta * GCv(GC_AC, j);
+        cc[j] = -beta * GCv(GC_CC, j);
+        b[j] = 1.0 + beta * (GCv(GC_AC, j) + GCv(GC_CC, j));
+      }
+      double d0, d1;
+      tabs[k][0][0] = build_xtab(a, b, cc, c->yP, false, NS_PART_PDD, &levs[k][0][0], &d0);
+      tabs[k][0][1] = build_xtab(a, b, cc, c->yP, false, NS_PART_PPT, &levs[k][0][1], &d1);
+      ydrop = std::fmax(ydrop, d0);
+      a.assign(ny, 0.0);
+      b.assign(ny, 1.0);
+      cc.assign(ny, 0.0);
+      for (int j = 1; j < ny; ++j) {
+        a[j] = -beta * GCv(GC_AF, j);
+        cc[j] = -beta * GCv(GC_CF, j);
+        b[j] = 1.0 + beta * (GCv(GC_AF, j) + GCv(GC_CF, j));
+      }
+      a[1] = 0.0;  // row 0 is the wall (v = 0, identity row)
+      tabs[k][1][0] = build_xtab(a, b, cc, c->yP, false, NS_PART_PDD, &levs[k][1][0], &d0);
+      tabs[k][1][1] = build_xtab(a, b, cc, c->yP, false, NS_PART_PPT, &levs[k][1][1], &d1);
+      ydrop = std::fmax(ydrop, d0);
+    }
+    if (c->zP) {
+      const double r = beta / (c->dz * c->dz);
+      std::vector<double> a(nz, -r), b(nz, 1.0 + 2.0 * r), cc(nz, -r);
+      double d0, d1;
+      tabs[k][2][0] = build_xtab(a, b, cc, c->zP, true, NS_PART_PDD, &levs[k][2][0], &d0);
+      tabs[k][2][1] = build_xtab(a, b, cc, c->zP, true, NS_PART_PPT, &levs[k][2][1], &d1);
+      zdrop = std::fmax(zdrop, d0);
+    }
+  }
+  c->ypdd_drop = ydrop;
+  c->zpdd_drop = zdrop;
+  const int ysel = ydrop <= tol ? 0 : 1, zsel = zdrop <= tol ? 0 : 1;
+  for (int k = 0; k < 3; ++k) {
+    for (int q = 0; q < 3; ++q) {
+      const bool on = q < 2 ? c->yP != 0 : c->zP != 0;
+      if (!on) continue;
+      const int sel = q < 2 ? ysel : zsel;
+      if (upload(c, c->ptab[k][q], tabs[k][q][sel]) != cudaSuccess) return NS_ERR_CUDA;
+    }
+    c->yL[k] = c->yP ? levs[k][0][ysel] : 0;
+    c->zL[k] = c->zP ? levs[k][2][zsel] : 0;
+  }
+  return NS_OK;
+}
+
 // x-solver tables for every sub-step and line class with the context's P and requested mode.
 ns_status build_x_tables(ns_ctx* c) {
   const double tol = c->es == 8 ? 1e-15 : 1e-8;
@@ -380,6 +469,8 @@ ns_status build_x_tables(ns_ctx* c) {
       if (upload(c, c->xtab[k][cls], tabs[k][cls][sel]) != cudaSuccess) return NS_ERR_CUDA;
     }
   }
+  const ns_status ls = build_line_tables(c);
+  if (ls != NS_OK) return ls;
   if (upload_step_constants(c) != cudaSuccess) return NS_ERR_CUDA;
   if (!c->staging && cudaStreamSynchronize(c->stream) != cudaSuccess) return NS_ERR_CUDA;
   return NS_OK;
@@ -680,6 +771,11 @@ ns_status ns_init(ns_ctx** out, const ns_config* cfg, const ns_fields* fields, v
   c->rate = (unsigned long long*)(c->flux + 4);
   c->rcy = (double*)(base + c->lay.off[LB_RCY]);
   c->stepk = (StepK*)(base + c->lay.off[LB_STEPK]);
+  c->yP = line_P(cfg, cfg->ny);
+  c->zP = line_P(cfg, cfg->nz);
+  for (int k = 0; k < 3; ++k)
+    for (int q = 0; q < 3; ++q)
+      c->ptab[k][q] = base + c->lay.off[LB_PTAB] + (3 * k + q) * al256(line_table_floats(cfg) * 4);
   c->twd = (double2*)(base + c->lay.off[LB_TWD]);
   double* lamz_d = (double*)(base + c->lay.off[LB_LAMZ]);
 
@@ -890,7 +986,7 @@ ns_status ns_set_dt(ns_ctx* c, double dt) {
   if (!c->pin) {
     // workspace bytes of the dt tables and the step constants
     c->pin_lo = c->lay.off[LB_XTAB];
-    c->pin_hi = c->lay.off[LB_STEPK] + NS_STEPK * sizeof(StepK);
+    c->pin_hi = c->lay.total;  // through LB_PTAB, the last block
     if (cudaMallocHost(&c->pin, c->pin_hi - c->pin_lo) != cudaSuccess) {
       c->pin = nullptr;
       return fail(c, NS_ERR_CUDA, "pinned staging buffer");

@@ -76,6 +76,20 @@ inline bool x_partition_ok(int P, int M) {
   }
 }
 
+// (P, M) shapes built for the partitioned y and z lines of the mixed form (AdiLinePK): n = P M
+// rows, P partitions of M rows held in registers by a block of 32 lines x P.
+inline bool line_part_ok(int P, int M) {
+  if (P == 8) return M == 4 || M == 6 || M == 8 || M == 12 || M == 16 || M == 24 || M == 32;
+  if (P == 16) return M == 18 || M == 32;
+  if (P == 32) return M == 32;
+  return false;
+}
+inline int line_partition(int n) {
+  for (int P = 8; P <= 32; P <<= 1)
+    if (n % P == 0 && line_part_ok(P, n / P)) return P;
+  return 0;
+}
+
 // Default partition count of an x line of nx rows: the largest admissible P with at least 8 rows
 // per partition, else the smallest admissible P; 0 if none is admissible.
 inline int x_default_partition(int nx) {
@@ -138,7 +152,7 @@ struct ns_layout {
 
 enum {
   LB_RU = 0, LB_RV, LB_RW, LB_NU, LB_NV, LB_NW, LB_PHI, LB_SPEC, LB_POIS, LB_GC, LB_XTAB, LB_YTAB,
-  LB_ZTAB, LB_TWZ, LB_TWX, LB_LAMX, LB_LAMZ, LB_RTAB, LB_DOUT, LB_TWD, LB_RCY, LB_STEPK, LB_COUNT
+  LB_ZTAB, LB_TWZ, LB_TWX, LB_LAMX, LB_LAMZ, LB_RTAB, LB_DOUT, LB_TWD, LB_RCY, LB_STEPK, LB_PTAB, LB_COUNT
 };
 
 // dt-dependent constants of one RK3 sub-step (entries 0..2) and of the projection of an initial
@@ -155,7 +169,7 @@ struct StepK {
   double xcf[3];      // outflow increment weights of the x sweep (u, v, w): r, 2r, 2r, r = beta_k / dx^2
   float xcff[4];      // the same in float (3 used)
   int L;              // reduction levels of the x solve (0: PDD)
-  int pad;
+  int Ly, Lz;         // the same for the partitioned y and z lines of the mixed form
 };
 constexpr int NS_STEPK = 4;
 
@@ -183,6 +197,12 @@ struct ns_ctx {
                             // periodic; differ at the inflow / outflow rows otherwise)
   void* ytab[3][2];
   void* ztab[3];
+  // partitioned y and z lines of the mixed form (0: thread per line): P per direction, the
+  // levels per sub-step, and the tables [k][0 y centres, 1 y faces, 2 z]
+  int yP = 0, zP = 0;
+  int yL[3] = {0, 0, 0}, zL[3] = {0, 0, 0};
+  void* ptab[3][3] = {};
+  double ypdd_drop = 0.0, zpdd_drop = 0.0;
   double2* twz;
   double2* twx;
   double* rtab[3];
