@@ -114,7 +114,7 @@ struct AdiXK {
     AdiXArgs<T> a;
   };
   static constexpr int kThreads = 256;
-  static constexpr int kMinBlocks = 2;
+  static constexpr int kMinBlocks = sizeof(T) == 4 ? 3 : 2;  // FP32 is bandwidth-bound: occupancy
   static Args make(AdiXArgs<T> a) { return Args{a}; }
   static __device__ __forceinline__ void run(const Args& a_, const dim3 bid_, const dim3 gdim_) {
     const AdiXArgs<T>& a = a_.a;
