@@ -293,7 +293,8 @@ struct FftxK {
 };
 
 // ------------------------------------------------------------------------------------------
-// y tridiagonal per (kx, kz), one thread per line, factors (1/pivot, c/pivot) precomputed.
+// y tridiagonal per (kx, kz), two threads per line (real, imaginary part), factors 1/pivot and
+// c/pivot precomputed in two planes (each sweep reads only the one it uses).
 // ------------------------------------------------------------------------------------------
 struct TdmaK {
   struct Args {
@@ -302,10 +303,11 @@ struct TdmaK {
     const double* gc;
     int nx;
     int ny;
+    int nzh;
   };
   static constexpr int kThreads = 128;
   static constexpr int kMinBlocks = 8;  // nx*(nz/2+1) lines: occupancy is set by the line count, not registers
-  static Args make(double2* spec, const double2* fac, const double* gc, int nx, int ny) { return Args{spec, fac, gc, nx, ny}; }
+  static Args make(double2* spec, const double2* fac, const double* gc, int nx, int ny, int nzh) { return Args{spec, fac, gc, nx, ny, nzh}; }
   static __device__ __forceinline__ void run(const Args& a_, const dim3 bid_, const dim3 gdim_) {
     double2* __restrict__ spec = a_.spec;
     const double2* __restrict__ fac = a_.fac;
@@ -313,51 +315,54 @@ struct TdmaK {
     int nx = a_.nx;
     int ny = a_.ny;
 
-  const int i = bid_.x * blockDim.x + threadIdx.x;
+  // two threads per (kx, kz) line: the real and the imaginary part are independent systems
+  // with the same real matrix (twice the parallelism of a thread per line, same traffic)
+  const int t = bid_.x * blockDim.x + threadIdx.x;
+  const int i = t >> 1, part = t & 1;
   const int kz = bid_.y;
   if (i >= nx) return;
   const long base = (long)kz * ny * nx + i;
-  double2* d = spec + base;
-  const double2* f = fac + base;
+  double* d = reinterpret_cast<double*>(spec + base) + part;
+  const long sd = 2L * nx;  // row stride in doubles
+  // factor planes: 1/pivot, then c/pivot (pois_factor_kernel), nzh * ny * nx doubles each
+  const double* finv = reinterpret_cast<const double*>(fac) + base;
+  const double* fcp = finv + (long)a_.nzh * ny * nx;
   const double* pa = gc + GC_PA * (ny + 1);
   // the (0,0) mode's row 0 is the gauge phi_0 = 0 (its factor row is 1, 0)
   const bool gauge = (i == 0 && kz == 0);
   constexpr int U = 4;
-  double2 prev = make_double2(0.0, 0.0);
+  double prev = 0.0;
   for (int j0 = 0; j0 < ny; j0 += U) {
-    double2 dv[U], fv[U];
-    double av[U];
+    double dv[U], fx[U], av[U];
 #pragma unroll
     for (int u = 0; u < U; ++u)
       if (j0 + u < ny) {
-        dv[u] = d[(long)(j0 + u) * nx];
-        fv[u] = __ldg(f + (long)(j0 + u) * nx);
+        dv[u] = d[(long)(j0 + u) * sd];
+        fx[u] = __ldg(finv + (long)(j0 + u) * nx);
         av[u] = __ldg(pa + j0 + u);  // a_0 = 0
       }
 #pragma unroll
     for (int u = 0; u < U; ++u)
       if (j0 + u < ny) {
-        double2 dj = dv[u];
-        if (gauge && j0 + u == 0) dj = make_double2(0.0, 0.0);
-        prev = make_double2(fma(-av[u], prev.x, dj.x) * fv[u].x, fma(-av[u], prev.y, dj.y) * fv[u].x);
-        d[(long)(j0 + u) * nx] = prev;
+        const double dj = (gauge && j0 + u == 0) ? 0.0 : dv[u];
+        prev = fma(-av[u], prev, dj) * fx[u];
+        d[(long)(j0 + u) * sd] = prev;
       }
   }
-  double2 next = prev;
+  double next = prev;
   for (int j1 = ny - 2; j1 >= 0; j1 -= U) {
-    double2 dv[U];
-    double cv[U];
+    double dv[U], cv[U];
 #pragma unroll
     for (int u = 0; u < U; ++u)
       if (j1 - u >= 0) {
-        dv[u] = d[(long)(j1 - u) * nx];
-        cv[u] = __ldg(f + (long)(j1 - u) * nx).y;
+        dv[u] = d[(long)(j1 - u) * sd];
+        cv[u] = __ldg(fcp + (long)(j1 - u) * nx);
       }
 #pragma unroll
     for (int u = 0; u < U; ++u)
       if (j1 - u >= 0) {
-        next = make_double2(fma(-cv[u], next.x, dv[u].x), fma(-cv[u], next.y, dv[u].y));
-        d[(long)(j1 - u) * nx] = next;
+        next = fma(-cv[u], next, dv[u]);
+        d[(long)(j1 - u) * sd] = next;
       }
   }
   }
@@ -720,7 +725,11 @@ __global__ void pois_factor_kernel(double2* __restrict__ fac, const double* __re
     const double piv = b - a * cprev;
     const double ip = 1.0 / piv;
     cprev = c * ip;
-    fac[((long)kz * ny + j) * nx + i] = make_double2(ip, cprev);
+    // two planes of one double each: 1/pivot (forward sweep) and c/pivot (back sweep)
+    double* f = reinterpret_cast<double*>(fac);
+    const long q = ((long)kz * ny + j) * nx + i;
+    f[q] = ip;
+    f[(long)nzh * ny * nx + q] = cprev;
   }
 }
 
@@ -819,7 +828,8 @@ cudaError_t stage_pois_x_fwd(LaunchSink& s, int) {
 cudaError_t stage_pois_tdma(LaunchSink& s, int) {
   ns_ctx* c = s.c;
   const PoisShape q = pois_shape(c);
-  return emit<TdmaK>(s, TdmaK::make(c->spec, c->pois, c->gc, q.nx, q.ny), dim3((q.nx + 127) / 128, c->nzh), dim3(128), 0);
+  return emit<TdmaK>(s, TdmaK::make(c->spec, c->pois, c->gc, q.nx, q.ny, c->nzh), dim3((2 * q.nx + 127) / 128, c->nzh),
+                     dim3(128), 0);
 }
 
 // A8: inverse complex FFT along x (the 1/(nx nz) was applied to the right-hand side)
