@@ -90,3 +90,23 @@ def test_invalid_arguments_are_rejected_on_the_host():
     s.step(1)
     s.sync()
     s.close()
+
+
+@pytest.mark.parametrize("pinned", [True, False])
+def test_step_host_equals_device_step(pinned):
+    """ns_step_host: host state in (pinned or pageable memory), one captured step, state out:
+    bitwise equal to the same step on device fields."""
+    case, u, v, w, p = I.small_channel(64, 20, 32, seed=13)
+    s1 = B.Solver(case, u, v, w, p)
+    s1.step(1)
+    ref = s1.state()
+    s1.close()
+    s2 = B.Solver(case)
+    host = []
+    for a in (u, v, w, p):
+        t = torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64).copy())
+        host.append((t.pin_memory() if pinned else t).numpy())
+    B.ns_step_host(s2.ctx, *host, 1)
+    for got, want in zip(host, ref):
+        assert np.array_equal(got, want)
+    s2.close()
