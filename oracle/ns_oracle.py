@@ -911,6 +911,8 @@ def step_bl(g, state, dt, re, fx, nsteps=1, u_conv=1.0, pressure="delta"):
 #   W(eta) = (1 + tanh(a (eta - b) / ((1 - 2b) eta + b)) / tanh a) / 2, a = 4, b = 0.2, W = 1 for
 #   eta > 1.
 # * The inflow planes (u on face 0, v_in, w_in) are set this way once at the start of every step.
+# * Parity unpinned: the blending constant a = 4 (b = 0.2 is pinned through the weight's
+#   inflection point); no independent value of a is available.
 
 def lund_weight(eta, a=4.0, b=0.2):
     eta = np.asarray(eta, dtype=np.float64)

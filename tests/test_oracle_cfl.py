@@ -107,3 +107,12 @@ def test_kim_moin_is_the_plain_update_without_viscosity():
     a = O.step(g, st, case.dt, float("inf"), case.fx, 1)
     b = O.step(g, st, case.dt, float("inf"), case.fx, 1, pressure="kim_moin")
     assert np.array_equal(a["p"], b["p"])
+
+
+def test_rate_of_a_uniform_stream_in_minus_x():
+    """u = -U everywhere (v = w = 0): the rate is |U| / dx whatever the sign."""
+    case, g = _grid(8, 6, 4)
+    u = np.full((g.nz, g.ny, g.nx), -2.5)
+    v = np.zeros((g.nz, g.ny + 1, g.nx))
+    w = np.zeros((g.nz, g.ny, g.nx))
+    assert O.convective_rate(g, u, v, w) == pytest.approx(2.5 / g.dx, rel=1e-15)

@@ -89,3 +89,44 @@ def test_recycled_steps_keep_divergence_and_mass_balance():
     wgt = g.dy[None, :] * g.dz
     assert abs((s["u"][:, :, 0] * wgt).sum() - (s["bl"]["u_out"] * wgt).sum()) < 1e-11
     assert not np.array_equal(s["u"][:, :, 0], u[:, :, 0])
+
+
+def test_recycle_face_values_of_v_and_w_are_centre_averages():
+    """v and w live at x-centres; on the recycle face x = i_r dx they are the averages of the centres
+    i_r - 1 and i_r.  With v = x_c (linear in x, exact under averaging), equal thicknesses
+    (gamma = 1) and a spanwise-uniform plane, the inflow v is i_r dx on the interior faces."""
+    case, g, u, v, w, p, bl = _grid(16, 12, 4)
+    ir = 7
+    u = np.broadcast_to(np.tanh(2.0 * g.yc)[None, :, None], u.shape).copy()
+    xc = (np.arange(g.nx) + 0.5) * g.dx
+    v = np.broadcast_to(xc[None, None, :], v.shape).copy()
+    w = np.broadcast_to(xc[None, None, :], w.shape).copy()
+    d = O.delta99(g.yc, u[0, :, ir])
+    ui, vi, wi = O.recycle_inflow(g, u, v, w, ir, d, case.re)
+    np.testing.assert_allclose(vi[:, 1:-1], ir * g.dx, rtol=1e-13)
+    np.testing.assert_allclose(wi, 0.0, atol=1e-13)  # uniform plane: no fluctuation, mean W dropped
+
+
+def test_gamma_follows_the_power_law_in_x():
+    """With delta ~ x^(4/5) and u_tau ~ x^(-1/10) (the 1/5 power law), the friction-velocity ratio
+    of an inlet at x_in and a recycle plane at x_rec is (x_rec / x_in)^(1/10).  The outer-layer
+    fluctuation of the recycled inflow is gamma times the plane's: recover gamma from it."""
+    case, g, u, v, w, p, bl = _grid(16, 64, 8)
+    x_in, x_rec = 1.0, 3.0
+    d_in, d_rec = 0.3 * x_in ** 0.8, 0.3 * x_rec ** 0.8
+    s = math.atanh(0.99) / d_rec
+    ir = 5
+    u = np.broadcast_to(np.tanh(s * g.yc)[None, :, None], u.shape).copy()
+    rng = np.random.default_rng(9)
+    w = 0.01 * rng.standard_normal(w.shape)
+    ui, vi, wi = O.recycle_inflow(g, u, v, w, ir, d_in, case.re)
+    w_r = 0.5 * (w[:, :, ir - 1] + w[:, :, ir])
+    wp = w_r - w_r.mean(axis=0)
+    # a row above delta_in (weight 1: outer layer only); its source height uses the measured
+    # thickness of the plane (delta99, pinned above), which is d_rec to interpolation accuracy
+    ratio = O.delta99(g.yc, u[0, :, ir]) / d_in
+    j = int(np.searchsorted(g.yc, 1.2 * d_in))
+    src = np.array([np.interp(g.yc[j] * ratio, np.concatenate([[0.0], g.yc]), np.concatenate([[0.0], wp[k]]))
+                    for k in range(g.nz)])
+    gamma = float(np.dot(wi[:, j], src) / np.dot(src, src))
+    assert gamma == pytest.approx((x_rec / x_in) ** 0.1, rel=2e-3)
