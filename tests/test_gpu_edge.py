@@ -110,3 +110,30 @@ def test_step_host_equals_device_step(pinned):
     for got, want in zip(host, ref):
         assert np.array_equal(got, want)
     s2.close()
+
+
+@pytest.mark.parametrize("bl", [False, True])
+def test_checkpoint_at_a_step_boundary_resumes_bitwise(bl):
+    """At a step boundary the state is the caller's fields (and the boundary planes): sub-step 0
+    does not read N_prev.  Stepping 1 + 2 steps through a copy equals 3 steps without a stop."""
+    if bl:
+        case, u, v, w, p, planes = I.boundary_layer(64, 12, 16, amp=0.05, seed=4, re=200.0)
+    else:
+        case, u, v, w, p = I.small_channel(64, 20, 16, seed=4)
+        planes = None
+    a = B.Solver(case, u, v, w, p, bl=planes)
+    a.step(3)
+    b = B.Solver(case, u, v, w, p, bl=planes)
+    b.step(1)
+    snap = b.state()
+    snap_bl = b.boundary() if bl else None
+    b.close()
+    c = B.Solver(case, *snap, bl=snap_bl)
+    c.step(2)
+    for x, y in zip(a.state(), c.state()):
+        assert np.array_equal(x, y)
+    if bl:
+        for q, t in a.boundary().items():
+            assert np.array_equal(t, c.boundary()[q])
+    a.close()
+    c.close()
