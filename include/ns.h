@@ -183,12 +183,20 @@ ns_status ns_step(ns_ctx* ctx, int nsteps);
  *
  * ns_set_dt: make dt the time step of the following sub-steps.  Rebuilds every table that
  * depends on dt (RHS rows, ADI factors and PDD/PPT tables, with the PDD admissibility test of the
- * automatic mode redone) and drops the captured graphs; the next ns_step captures again.  dt must
- * be positive and finite (NS_ERR_ARG).  Synchronises the stream.
+ * automatic mode redone, and the sub-step constants) on the host and copies them to the workspace
+ * asynchronously.  The first call switches the kernels to reading the sub-step constants from the
+ * workspace and drops the captured graphs once (the next ns_step captures again); later calls
+ * keep them.  dt must be positive and finite (NS_ERR_ARG).  Synchronises the stream on entry.
  *
- * ns_step_cfl: nsteps steps, each preceded by dt = cfl / rate of the velocity at its start
- * (ns_convective_rate, then ns_set_dt when dt changes).  dts, if not NULL, receives the nsteps
- * values of dt (host array).  cfl must be positive and finite.  One host round trip per step. */
+ * ns_step_cfl: nsteps steps, each preceded by dt = cfl / rate of the velocity at its start.  The
+ * rate, dt and every dt-dependent table are computed on the device inside the captured step graph
+ * (rate reduction, then two kernels that build the same tables as ns_set_dt, with the same
+ * operations and roundings, so the steps are bitwise those of ns_convective_rate + ns_set_dt +
+ * ns_step); the host reads the dt log back once per 1024 steps.  dts, if not NULL, receives the
+ * nsteps values of dt (host array).  cfl must be positive and finite (NS_ERR_ARG).  A rate that is
+ * not positive and finite (a non-finite field, or fluid at rest) keeps the previous dt for that
+ * step and makes the call return NS_ERR_STATE after the run of steps it fell in (the message names
+ * the step); the fields are then not a solution.  Synchronises the stream. */
 ns_status ns_convective_rate(ns_ctx* ctx, double* rate);
 ns_status ns_set_dt(ns_ctx* ctx, double dt);
 ns_status ns_step_cfl(ns_ctx* ctx, int nsteps, double cfl, double* dts);

@@ -19,6 +19,9 @@ LIB = os.path.join(OUT, "libns_gb300.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2",
                      "-I", os.path.join(ROOT, "include")]
+# Per-file flags.  k_dt.cu builds the dt tables on the host and on the device from the same
+# functions; without contraction on either side both round alike and the tables agree bitwise.
+FILE_FLAGS = {"k_dt.cu": ["-fmad=false", "-Xcompiler", "-ffp-contract=off"]}
 
 
 def _nvcc():
@@ -47,7 +50,7 @@ def build(verbose: bool = False, ptxas_verbose: bool = False) -> str:
         o = os.path.join(OUT, os.path.basename(s)[:-3] + ".o")
         objs.append(o)
         if ptxas_verbose or _stale(o, [s] + hdrs):
-            jobs.append([nvcc] + NVCC_FLAGS + extra + ["-c", s, "-o", o])
+            jobs.append([nvcc] + NVCC_FLAGS + FILE_FLAGS.get(os.path.basename(s), []) + extra + ["-c", s, "-o", o])
 
     def run(cmd):
         r = subprocess.run(cmd, capture_output=True, text=True)

@@ -654,30 +654,81 @@ __global__ void __launch_bounds__(1024) flux_correct_kernel(const double* __rest
 
 // ------------------------------------------------------------------------------------------
 // convective rate max over cells of |u| (1/dx) + |v_c| (1/dy_j) + |w| (1/dz) (u, w on the cell's
-// lower faces, v_c the mean of its two y faces), the measure of the fixed-CFL time step.  Each
-// block walks (j, k) rows; the products and sums are rounded one by one (no contraction), so the
-// value of every cell, and the maximum, equal the plain definition.  Values are >= 0, so their
+// lower faces, v_c the mean of its two y faces), the measure of the fixed-CFL time step.  The
+// value of a cell that can be the maximum is computed with its products and sums rounded one by
+// one (no contraction), so the maximum equals the plain definition.  Values are >= 0, so their
 // bit patterns order like the values and one atomicMax per block on the bits combines the blocks
 // in any order.  A non-finite value stores the bits of a NaN (above every finite value).
+//
+// Screening: the FP64 pipe is the scarce unit, so each cell first gets an upper bound of its
+// value on the integer and FP32 pipes, from the high words of the doubles (every magnitude
+// truncated to 20 fraction bits as a float, a lower bound within 2^-20; magnitudes below 2^-126
+// as 0, above 2^128 or non-finite as inf).  The bound adds the slack of those truncations and of
+// the float and double roundings with a margin (a factor 1 + 2^-14 and 1e-30).  A cell whose bound
+// is below an exact value already found (the running maximum of the block) cannot be the maximum
+// and skips the exact evaluation; a warp evaluates exactly only when one of its lanes needs it.
 // ------------------------------------------------------------------------------------------
+__device__ __forceinline__ float trunc_mag(unsigned hi) {  // |x| from the high word, truncated
+  const unsigned h = hi & 0x7FFFFFFFu;
+  unsigned b = (h - 0x38000000u) << 3;  // binary64 exponent e -> binary32 exponent e - 896
+  b = h < 0x38100000u ? 0u : b;         // |x| < 2^-126
+  b = h >= 0x47F00000u ? 0x7F800000u : b;  // |x| >= 2^128, inf, NaN
+  return __uint_as_float(b);
+}
+
 __global__ void __launch_bounds__(128) rate_kernel(const double* __restrict__ u, const double* __restrict__ v,
                                                    const double* __restrict__ w, const double* __restrict__ gc,
                                                    int nx, int ny, int nz, double ix, double iz,
                                                    unsigned long long* __restrict__ out) {
   // ix = 1/dx, iz = 1/dz and the rows 1/dy_j (GC_IDY) are rounded on the host
+  __shared__ unsigned long long s_max;  // bits of the block's running maximum
+  if (threadIdx.x == 0) s_max = 0ull;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const float ixf = trunc_mag((unsigned)__double2hiint(ix)), izf = trunc_mag((unsigned)__double2hiint(iz));
   double m = 0.0;
+  float mf = 0.0f;  // a float <= m
   bool bad = false;
   for (int row = blockIdx.x; row < ny * nz; row += gridDim.x) {
     const int k = row / ny, j = row - k * ny;
     const double iy = __ldg(gc + GC_IDY * (ny + 1) + j);
+    const float iyf = trunc_mag((unsigned)__double2hiint(iy));
     const long c0 = ((long)k * ny + j) * nx;
     const long v0 = ((long)k * (ny + 1) + j) * nx;
-    for (int i = threadIdx.x; i < nx; i += blockDim.x) {
-      const double au = fabs(__ldg(u + c0 + i)), aw = fabs(__ldg(w + c0 + i));
-      const double av = fabs(__dmul_rn(0.5, __dadd_rn(__ldg(v + v0 + i), __ldg(v + v0 + nx + i))));
-      const double r = __dadd_rn(__dadd_rn(__dmul_rn(au, ix), __dmul_rn(av, iy)), __dmul_rn(aw, iz));
-      bad |= !(r <= 1.7976931348623157e308);
-      m = fmax(m, r);
+    const unsigned long long bm = *(volatile unsigned long long*)&s_max;
+    if (bm > (unsigned long long)__double_as_longlong(m)) {
+      m = __longlong_as_double((long long)bm);
+      mf = __double2float_rd(m);
+    }
+    for (int i0 = warp * 32; i0 < nx; i0 += blockDim.x) {
+      const int i = i0 + lane;
+      const bool in = i < nx;
+      double du = 0.0, dw = 0.0, dv0 = 0.0, dv1 = 0.0;
+      if (in) {
+        du = __ldg(u + c0 + i);
+        dw = __ldg(w + c0 + i);
+        dv0 = __ldg(v + v0 + i);
+        dv1 = __ldg(v + v0 + nx + i);
+      }
+      const unsigned h0 = (unsigned)__double2hiint(dv0), h1 = (unsigned)__double2hiint(dv1);
+      const float f0 = __uint_as_float(__float_as_uint(trunc_mag(h0)) | (h0 & 0x80000000u));
+      const float f1 = __uint_as_float(__float_as_uint(trunc_mag(h1)) | (h1 & 0x80000000u));
+      const float avh = fabsf(f0 + f1) + 0x1p-18f * (fabsf(f0) + fabsf(f1));
+      const float rh = (trunc_mag((unsigned)__double2hiint(du)) * ixf + 0.5f * avh * iyf +
+                        trunc_mag((unsigned)__double2hiint(dw)) * izf) * (1.0f + 0x1p-14f) + 1e-30f;
+      const bool cand = in && !(rh < mf);
+      if (__any_sync(NS_FULL_MASK, cand)) {
+        if (cand) {
+          const double au = fabs(du), aw = fabs(dw);
+          const double av = fabs(__dmul_rn(0.5, __dadd_rn(dv0, dv1)));
+          const double r = __dadd_rn(__dadd_rn(__dmul_rn(au, ix), __dmul_rn(av, iy)), __dmul_rn(aw, iz));
+          bad |= !(r <= 1.7976931348623157e308);
+          m = fmax(m, r);
+        }
+        for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(NS_FULL_MASK, m, o));
+        mf = __double2float_rd(m);
+        if (lane == 0) atomicMax(&s_max, (unsigned long long)__double_as_longlong(m));
+      }
     }
   }
   for (int o = 16; o > 0; o >>= 1) {
@@ -686,9 +737,9 @@ __global__ void __launch_bounds__(128) rate_kernel(const double* __restrict__ u,
   }
   __shared__ double sm[4];
   __shared__ int sb[4];
-  if ((threadIdx.x & 31) == 0) {
-    sm[threadIdx.x >> 5] = m;
-    sb[threadIdx.x >> 5] = bad;
+  if (lane == 0) {
+    sm[warp] = m;
+    sb[warp] = bad;
   }
   __syncthreads();
   if (threadIdx.x == 0) {

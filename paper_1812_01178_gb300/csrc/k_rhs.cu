@@ -40,31 +40,7 @@ struct RhsArgs {
   StepK kc;         // the same values as kernel arguments (read by the fixed-dt variants)
 };
 
-// indexes into RhsArgs::kd / kf
-enum { RK_QIDX, RK_QIDZ, RK_HIDX, RK_HIDZ, RK_CN, RK_CP, RK_CGX, RK_CGZ, RK_CX, RK_CZ, RK_CB };
-
 }  // namespace
-
-// The constants of RhsTiledK for sub-step k, each rounded to double (kd) and to float (kf)
-// exactly as the expressions would be in that type: the products of the double inputs are
-// rounded once to the type, and cx, cz are then formed in the type itself.
-void rhs_fill_step(const ns_ctx* c, int k, StepK& sk) {
-  const double dt = c->cfg.dt, gam = NS_GAMMA[k], zet = NS_ZETA[k], alp = NS_ALPHA[k];
-  const double idx = 1.0 / c->dx, idz = 1.0 / c->dz, idx2 = idx * idx, idz2 = idz * idz;
-  const double inv_re = c->cfg.re > 0 ? 1.0 / c->cfg.re : 0.0;
-  const double d[11] = {0.25 * idx, 0.25 * idz, 0.5 * idx, 0.5 * idz, -dt * gam, -dt * zet,
-                        -dt * alp * idx, -dt * alp * idz, 0.0, 0.0, dt * alp * c->cfg.fx};
-  const double cl = dt * alp * inv_re;
-  for (int q = 0; q < 11; ++q) {
-    sk.kd[q] = d[q];
-    sk.kf[q] = (float)d[q];
-  }
-  sk.kd[RK_CX] = cl * idx2;
-  sk.kd[RK_CZ] = cl * idz2;
-  const float clf = (float)cl;
-  sk.kf[RK_CX] = clf * (float)idx2;
-  sk.kf[RK_CZ] = clf * (float)idz2;
-}
 
 namespace {
 

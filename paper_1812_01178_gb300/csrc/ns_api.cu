@@ -1,6 +1,7 @@
 // C ABI entry points, workspace layout, coefficient tables and graph capture.
 #include <algorithm>
 #include <cmath>
+#include <cstddef>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -13,8 +14,6 @@ namespace {
 
 thread_local std::string g_init_error;
 
-
-size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // Returns "" if the configuration is valid, else a message; *kind receives the status to report.
 std::string check_cfg(const ns_config* c, ns_status* kind = nullptr) {
@@ -69,6 +68,9 @@ size_t line_table_floats(const ns_config* c) {
   return m;
 }
 
+// elements reserved per x-solver table: any admissible P <= 32 (L <= 5 levels)
+size_t x_table_elems(const ns_config* c) { return 5 * (size_t)c->nx + 4 * 32 + 8 * 5 * 32; }
+
 ns_layout make_layout(const ns_config* c) {
   ns_layout L;
   memset(&L, 0, sizeof(L));
@@ -86,7 +88,7 @@ ns_layout make_layout(const ns_config* c) {
   sz[LB_SPEC] = nzh * ny * nx * 16;
   sz[LB_POIS] = nzh * ny * nx * 16;
   sz[LB_GC] = NS_GC_COUNT * (ny + 1) * 8;
-  sz[LB_XTAB] = 6 * al256((5 * nx + 4 * 32 + 8 * 5 * 32) * es);
+  sz[LB_XTAB] = 6 * al256(x_table_elems(c) * es);
   sz[LB_YTAB] = 6 * al256(3 * ny * es);
   sz[LB_ZTAB] = 3 * al256((4 * nz + 2) * es);
   sz[LB_TWZ] = fft_twiddle_doubles((int)nz) * 8;
@@ -99,6 +101,7 @@ ns_layout make_layout(const ns_config* c) {
   sz[LB_RCY] = recycle_block_doubles((int)ny) * 8;
   sz[LB_STEPK] = NS_STEPK * sizeof(StepK);
   sz[LB_PTAB] = 9 * al256(line_table_floats(c) * 4);
+  sz[LB_DT] = al256(sizeof(DtCtl)) + 8 * dt_scratch_doubles((int)nz, x_table_elems(c), line_table_floats(c));
   size_t o = 0;
   for (int b = 0; b < LB_COUNT; ++b) {
     L.off[b] = o;
@@ -108,469 +111,8 @@ ns_layout make_layout(const ns_config* c) {
   return L;
 }
 
-// --------------------------------------------------------------------------------------------
-// tridiagonal helpers (host, double)
-// --------------------------------------------------------------------------------------------
-// Thomas factors of rows (a, b, c), a[0] and c[n-1] ignored: inv = 1/pivot, ainv = a/pivot, cp = c/pivot.
-void thomas_factors(const std::vector<double>& a, const std::vector<double>& b, const std::vector<double>& c,
-                    std::vector<double>& inv, std::vector<double>& ainv, std::vector<double>& cp) {
-  const size_t n = b.size();
-  inv.assign(n, 0.0);
-  ainv.assign(n, 0.0);
-  cp.assign(n, 0.0);
-  double cprev = 0.0;
-  for (size_t j = 0; j < n; ++j) {
-    const double aj = j > 0 ? a[j] : 0.0;
-    const double cj = j + 1 < n ? c[j] : 0.0;
-    const double piv = b[j] - aj * cprev;
-    inv[j] = 1.0 / piv;
-    ainv[j] = aj * inv[j];
-    cp[j] = cj * inv[j];
-    cprev = cp[j];
-  }
-}
-
-std::vector<double> thomas_apply(const std::vector<double>& inv, const std::vector<double>& ainv,
-                                 const std::vector<double>& cp, std::vector<double> d) {
-  const size_t n = d.size();
-  d[0] *= inv[0];
-  for (size_t j = 1; j < n; ++j) d[j] = d[j] * inv[j] - ainv[j] * d[j - 1];
-  for (size_t j = n - 1; j-- > 0;) d[j] -= cp[j] * d[j + 1];
-  return d;
-}
-
-struct M2 {
-  double a, b, c, d;  // [[a, b], [c, d]]
-};
-M2 mmul(M2 x, M2 y) {
-  return {x.a * y.a + x.b * y.c, x.a * y.b + x.b * y.d, x.c * y.a + x.d * y.c, x.c * y.b + x.d * y.d};
-}
-M2 madd(M2 x, M2 y) { return {x.a + y.a, x.b + y.b, x.c + y.c, x.d + y.d}; }
-M2 msub(M2 x, M2 y) { return {x.a - y.a, x.b - y.b, x.c - y.c, x.d - y.d}; }
-M2 minv(M2 x) {
-  const double det = x.a * x.d - x.b * x.c;
-  return {x.d / det, -x.b / det, -x.c / det, x.a / det};
-}
-M2 mzero() { return {0, 0, 0, 0}; }
-
-// Partitioned x solver tables (Sec. 3.2) for the rows (a, b, c) of one x-line of n = P*M rows,
-// periodic (cyclic) or not.  mode: NS_PART_PDD or NS_PART_PPT.  Per partition r: the block
-// Thomas factors of A~ (couplings to the neighbouring partitions cut), the spikes v^(r), w^(r)
-// of Eq. (blockAY) (zero where no coupling was cut: the ends of a non-periodic line), and the
-// 2x2-block reduced system Z of Eq. (Zpdd) over the interfaces (r, r+1):
-//   L_r Y_{r-1} + D_r Y_r + U_r Y_{r+1} = (x~^(r)_m, x~^(r+1)_1),
-//   D_r = [[1, w^(r)_m], [v^(r+1)_1, 1]], L_r = [[v^(r)_m, 0], [0, 0]], U_r = [[0, 0], [0, w^(r+1)_1]];
-// a non-periodic line has P-1 interfaces and a decoupled identity row in slot P-1.  PDD keeps D_r;
-// PPT eliminates L, U by block parallel cyclic reduction (multipliers stored per level).
-// Returns the table, the number of reduction levels and the largest coupling PDD drops.
-std::vector<double> build_xtab(const std::vector<double>& A, const std::vector<double>& Bv,
-                               const std::vector<double>& Cv, int P, bool cyclic, int mode, int* levels,
-                               double* dropped) {
-  const int n = (int)Bv.size();
-  const int M = n / P;
-  int L = 0;
-  while ((1 << L) < P) ++L;
-  std::vector<double> inv(n), ainv(n), cp(n), sv(n, 0.0), sw(n, 0.0);
-  for (int r = 0; r < P; ++r) {
-    const int o = r * M;
-    std::vector<double> a(A.begin() + o, A.begin() + o + M), b(Bv.begin() + o, Bv.begin() + o + M),
-        c(Cv.begin() + o, Cv.begin() + o + M), i1, i2, i3;
-    thomas_factors(a, b, c, i1, i2, i3);  // a[0], c[M-1] (the cut couplings) are ignored
-    std::copy(i1.begin(), i1.end(), inv.begin() + o);
-    std::copy(i2.begin(), i2.end(), ainv.begin() + o);
-    std::copy(i3.begin(), i3.end(), cp.begin() + o);
-    std::vector<double> e1(M, 0.0), em(M, 0.0);
-    if (cyclic || r > 0) e1[0] = A[o];                 // a of the first row couples partition r-1
-    if (cyclic || r < P - 1) em[M - 1] = Cv[o + M - 1];  // c of the last row couples partition r+1
-    const std::vector<double> v1 = thomas_apply(i1, i2, i3, e1), w1 = thomas_apply(i1, i2, i3, em);
-    std::copy(v1.begin(), v1.end(), sv.begin() + o);
-    std::copy(w1.begin(), w1.end(), sw.begin() + o);
-  }
-  auto V = [&](int r, int e) { return sv[r * M + e]; };
-  auto W = [&](int r, int e) { return sw[r * M + e]; };
-  std::vector<M2> Lb(P), Db(P), Ub(P);
-  double drop = 0.0;
-  for (int r = 0; r < P; ++r) {
-    const int rn = (r + 1) % P;
-    if (!cyclic && r == P - 1) {
-      Db[r] = {1.0, 0.0, 0.0, 1.0};
-      Lb[r] = mzero();
-      Ub[r] = mzero();
-      continue;
-    }
-    Db[r] = {1.0, W(r, M - 1), V(rn, 0), 1.0};
-    Lb[r] = {V(r, M - 1), 0.0, 0.0, 0.0};
-    Ub[r] = {0.0, 0.0, 0.0, W(rn, 0)};
-    drop = std::fmax(drop, std::fmax(std::fabs(Lb[r].a), std::fabs(Ub[r].d)));
-  }
-  *dropped = drop;
-  std::vector<M2> MLs, MUs;  // per level, per r
-  if (mode == NS_PART_PPT && P == 1) {
-    // one partition: both couplings of the single interface point back at itself
-    Db[0] = madd(Db[0], madd(Lb[0], Ub[0]));
-  }
-  if (mode == NS_PART_PPT) {
-    for (int lv = 0, st = 1; lv < L; ++lv, st <<= 1) {
-      std::vector<M2> nL(P), nD(P), nU(P);
-      for (int r = 0; r < P; ++r) {
-        const int rm = ((r - st) % P + P) % P, rp = (r + st) % P;
-        M2 ml, mu;
-        if (rm == rp) {
-          ml = mmul(madd(Lb[r], Ub[r]), minv(Db[rm]));
-          mu = mzero();
-          nD[r] = msub(Db[r], mmul(ml, madd(Lb[rm], Ub[rm])));
-          nL[r] = mzero();
-          nU[r] = mzero();
-        } else {
-          ml = mmul(Lb[r], minv(Db[rm]));
-          mu = mmul(Ub[r], minv(Db[rp]));
-          nD[r] = msub(msub(Db[r], mmul(ml, Ub[rm])), mmul(mu, Lb[rp]));
-          // new couplings at distance 2 st; when they coincide (4 st = P) the next level folds them
-          nL[r] = msub(mzero(), mmul(ml, Lb[rm]));
-          nU[r] = msub(mzero(), mmul(mu, Ub[rp]));
-        }
-        MLs.push_back(ml);
-        MUs.push_back(mu);
-      }
-      Lb = nL;
-      Db = nD;
-      Ub = nU;
-    }
-  } else {
-    L = 0;
-  }
-  std::vector<double> t(xtab_count(M, P, L), 0.0);
-  for (int r = 0; r < P; ++r)
-    for (int e = 0; e < M; ++e) {
-      t[(XT_INV * M + e) * P + r] = inv[r * M + e];
-      t[(XT_AINV * M + e) * P + r] = ainv[r * M + e];
-      t[(XT_CP * M + e) * P + r] = cp[r * M + e];
-      t[(XT_V * M + e) * P + r] = V(r, e);
-      t[(XT_W * M + e) * P + r] = W(r, e);
-    }
-  const size_t d0 = (size_t)XT_NF * M * P;
-  for (int r = 0; r < P; ++r) {
-    const M2 di = minv(Db[r]);
-    t[d0 + r] = di.a;
-    t[d0 + P + r] = di.b;
-    t[d0 + 2 * P + r] = di.c;
-    t[d0 + 3 * P + r] = di.d;
-  }
-  const size_t m0 = d0 + 4 * (size_t)P, u0 = m0 + 4 * (size_t)L * P;
-  for (int lv = 0; lv < L; ++lv)
-    for (int r = 0; r < P; ++r) {
-      const M2 ml = MLs[(size_t)lv * P + r], mu = MUs[(size_t)lv * P + r];
-      t[m0 + (4 * lv + 0) * P + r] = ml.a;
-      t[m0 + (4 * lv + 1) * P + r] = ml.b;
-      t[m0 + (4 * lv + 2) * P + r] = ml.c;
-      t[m0 + (4 * lv + 3) * P + r] = ml.d;
-      t[u0 + (4 * lv + 0) * P + r] = mu.a;
-      t[u0 + (4 * lv + 1) * P + r] = mu.b;
-      t[u0 + (4 * lv + 2) * P + r] = mu.c;
-      t[u0 + (4 * lv + 3) * P + r] = mu.d;
-    }
-  *levels = L;
-  return t;
-}
-
-cudaError_t upload_d(ns_ctx* c, void* dst, const std::vector<double>& src);
-
-// Copy a host table to the device in the context's element type (double or float).  Waits for
-// the copy, so the host vector may be released afterwards.
-// Host -> workspace copy of a table.  While c->staging, the bytes go to the pinned mirror and
-// the range is recorded (flush_staging copies it); otherwise a copy followed by a stream sync.
-cudaError_t upload_raw(ns_ctx* c, void* dst, const void* src, size_t bytes) {
-  const size_t off = (size_t)((char*)dst - (char*)c->ws);
-  if (c->staging && c->pin && off >= c->pin_lo && off + bytes <= c->pin_hi) {
-    memcpy(c->pin + (off - c->pin_lo), src, bytes);
-    c->dirty.emplace_back(off, bytes);
-    return cudaSuccess;
-  }
-  cudaError_t e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, c->stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-  return e;
-}
-
-cudaError_t upload(ns_ctx* c, void* dst, const std::vector<double>& src) {
-  if (c->es == 8) return upload_d(c, dst, src);
-  std::vector<float> f(src.begin(), src.end());
-  return upload_raw(c, dst, f.data(), f.size() * 4);
-}
-
 cudaError_t upload_d(ns_ctx* c, void* dst, const std::vector<double>& src) {
   return upload_raw(c, dst, src.data(), src.size() * 8);
-}
-
-// Asynchronous copies of the staged ranges (pinned source: nothing waits).
-cudaError_t flush_staging(ns_ctx* c) {
-  cudaError_t e = cudaSuccess;
-  for (const auto& r : c->dirty)
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync((char*)c->ws + r.first, c->pin + (r.first - c->pin_lo), r.second, cudaMemcpyHostToDevice,
-                          c->stream);
-  c->dirty.clear();
-  return e;
-}
-
-// The dt-dependent kernel constants of every sub-step (StepK) from cfg.dt and the x-solver levels.
-cudaError_t upload_step_constants(ns_ctx* c) {
-  const double dt = c->cfg.dt, nxz = (double)c->cfg.nx * c->cfg.nz;
-  const double inv_re = c->cfg.re > 0 ? 1.0 / c->cfg.re : 0.0;
-  for (int k = 0; k < 3; ++k) {
-    StepK& sk = c->stepk_h[k];
-    memset(&sk, 0, sizeof(sk));
-    rhs_fill_step(c, k, sk);
-    const double sc = NS_ALPHA[k] * dt;
-    sk.dt = dt;
-    sk.pscale = 1.0 / sc / nxz;
-    sk.sx = sc / c->dx;
-    sk.sz = sc / c->dz;
-    sk.s = sc;
-    sk.beta_p = c->cfg.pressure_update == NS_PRESSURE_KIM_MOIN ? sc * inv_re / 2.0 : 0.0;
-    const double step = sc * c->cfg.u_conv;
-    sk.cu = step / c->dx;
-    sk.cv = step / (0.5 * c->dx);
-    const double rx = NS_ALPHA[k] * dt * inv_re / 2.0 / (c->dx * c->dx);
-    sk.xcf[0] = rx;  // u: the outflow face is the neighbour of the last unknown face
-    sk.xcf[1] = 2.0 * rx;  // v, w: linear ghost 2 f_out - f_last
-    sk.xcf[2] = 2.0 * rx;
-    for (int q = 0; q < 3; ++q) sk.xcff[q] = (float)sk.xcf[q];
-    sk.L = c->L[k];
-    sk.Ly = c->yL[k];
-    sk.Lz = c->zL[k];
-  }
-  StepK& s3 = c->stepk_h[3];  // projection of an initial field: scale 1
-  memset(&s3, 0, sizeof(s3));
-  s3.dt = dt;
-  s3.pscale = 1.0 / nxz;
-  s3.sx = 1.0 / c->dx;
-  s3.sz = 1.0 / c->dz;
-  s3.s = 1.0;
-  return upload_raw(c, c->stepk, c->stepk_h, sizeof(c->stepk_h));
-}
-
-double beta_of(const ns_ctx* c, int k) {
-  const double inv_re = c->cfg.re > 0 ? 1.0 / c->cfg.re : 0.0;
-  return NS_ALPHA[k] * c->cfg.dt * inv_re / 2.0;
-}
-
-// Rows of (I - beta_k delta_xx) on one x-line (Sec. 2.2) for the u lines (cls 0) and the v, w
-// lines (cls 1).  Periodic: every row (-r, 1 + 2r, -r), cyclic.  Inflow / outflow: the u line
-// holds faces 0..nx-1 with face 0 fixed (identity row) and the outflow face as the neighbour of
-// the last row (its increment enters the right-hand side); v, w lines are cell centres whose
-// first and last rows see linear ghosts of the boundary faces: b = 1 + 3r there.
-void x_rows(const ns_ctx* c, int k, int cls, std::vector<double>& a, std::vector<double>& b,
-            std::vector<double>& cc) {
-  const int nx = c->cfg.nx;
-  const double r = beta_of(c, k) / (c->dx * c->dx);
-  a.assign(nx, -r);
-  b.assign(nx, 1.0 + 2.0 * r);
-  cc.assign(nx, -r);
-  if (!c->bl) return;
-  a[0] = 0.0;
-  cc[nx - 1] = 0.0;
-  if (cls == 0) {
-    b[0] = 1.0;
-    cc[0] = 0.0;
-  } else {
-    b[0] = 1.0 + 3.0 * r;
-    b[nx - 1] = 1.0 + 3.0 * r;
-  }
-}
-
-// Tables of the partitioned y and z lines of the mixed form (AdiLinePK), every sub-step: the rows
-// of the thread-per-line solvers, split into P partitions by build_xtab.  y centres (u, w) and y
-// faces (v, with the wall row 0 as an identity row) are not periodic; z is.  PDD when the
-// coupling it drops stays below the FP32 tolerance for every sub-step of the direction, else PPT.
-ns_status build_line_tables(ns_ctx* c) {
-  if (!c->yP && !c->zP) return NS_OK;
-  const int ny = c->cfg.ny, nz = c->cfg.nz, G = ny + 1;
-  auto GCv = [&](int f, int j) -> double { return c->gc_h[(size_t)f * G + j]; };
-  const double tol = 1e-8;
-  std::vector<double> tabs[3][3][2];
-  int levs[3][3][2];
-  double ydrop = 0.0, zdrop = 0.0;
-  for (int k = 0; k < 3; ++k) {
-    const double beta = beta_of(c, k);
-    if (c->yP) {
-      std::vector<double> a(ny), b(ny), cc(ny);
-      for (int j = 0; j < ny; ++j) {
-        a[j] = -beta * GCv(GC_AC, j);
-        cc[j] = -beta * GCv(GC_CC, j);
-        b[j] = 1.0 + beta * (GCv(GC_AC, j) + GCv(GC_CC, j));
-      }
-      double d0, d1;
-      tabs[k][0][0] = build_xtab(a, b, cc, c->yP, false, NS_PART_PDD, &levs[k][0][0], &d0);
-      tabs[k][0][1] = build_xtab(a, b, cc, c->yP, false, NS_PART_PPT, &levs[k][0][1], &d1);
-      ydrop = std::fmax(ydrop, d0);
-      a.assign(ny, 0.0);
-      b.assign(ny, 1.0);
-      cc.assign(ny, 0.0);
-      for (int j = 1; j < ny; ++j) {
-        a[j] = -beta * GCv(GC_AF, j);
-        cc[j] = -beta * GCv(GC_CF, j);
-        b[j] = 1.0 + beta * (GCv(GC_AF, j) + GCv(GC_CF, j));
-      }
-      a[1] = 0.0;  // row 0 is the wall (v = 0, identity row)
-      tabs[k][1][0] = build_xtab(a, b, cc, c->yP, false, NS_PART_PDD, &levs[k][1][0], &d0);
-      tabs[k][1][1] = build_xtab(a, b, cc, c->yP, false, NS_PART_PPT, &levs[k][1][1], &d1);
-      ydrop = std::fmax(ydrop, d0);
-    }
-    if (c->zP) {
-      const double r = beta / (c->dz * c->dz);
-      std::vector<double> a(nz, -r), b(nz, 1.0 + 2.0 * r), cc(nz, -r);
-      double d0, d1;
-      tabs[k][2][0] = build_xtab(a, b, cc, c->zP, true, NS_PART_PDD, &levs[k][2][0], &d0);
-      tabs[k][2][1] = build_xtab(a, b, cc, c->zP, true, NS_PART_PPT, &levs[k][2][1], &d1);
-      zdrop = std::fmax(zdrop, d0);
-    }
-  }
-  c->ypdd_drop = ydrop;
-  c->zpdd_drop = zdrop;
-  const int ysel = ydrop <= tol ? 0 : 1, zsel = zdrop <= tol ? 0 : 1;
-  for (int k = 0; k < 3; ++k) {
-    for (int q = 0; q < 3; ++q) {
-      const bool on = q < 2 ? c->yP != 0 : c->zP != 0;
-      if (!on) continue;
-      const int sel = q < 2 ? ysel : zsel;
-      if (upload(c, c->ptab[k][q], tabs[k][q][sel]) != cudaSuccess) return NS_ERR_CUDA;
-    }
-    c->yL[k] = c->yP ? levs[k][0][ysel] : 0;
-    c->zL[k] = c->zP ? levs[k][2][zsel] : 0;
-  }
-  return NS_OK;
-}
-
-// x-solver tables for every sub-step and line class with the context's P and requested mode.
-ns_status build_x_tables(ns_ctx* c) {
-  const double tol = c->es == 8 ? 1e-15 : 1e-8;
-  double drop_max = 0.0;
-  std::vector<double> tabs[3][2][2];
-  int levs[3][2];
-  const bool cyclic = !c->bl;
-  for (int k = 0; k < 3; ++k)
-    for (int cls = 0; cls < 2; ++cls) {
-      std::vector<double> a, b, cc;
-      x_rows(c, k, cls, a, b, cc);
-      double d0, d1;
-      tabs[k][cls][0] = build_xtab(a, b, cc, c->P, cyclic, NS_PART_PDD, &levs[k][0], &d0);
-      tabs[k][cls][1] = build_xtab(a, b, cc, c->P, cyclic, NS_PART_PPT, &levs[k][1], &d1);
-      drop_max = std::fmax(drop_max, d0);
-    }
-  int mode = c->part_req;
-  if (mode == NS_PART_AUTO) mode = drop_max <= tol ? NS_PART_PDD : NS_PART_PPT;
-  c->part_mode = mode;
-  c->pdd_drop = drop_max;
-  const int sel = mode == NS_PART_PDD ? 0 : 1;
-  for (int k = 0; k < 3; ++k) {
-    c->L[k] = levs[k][sel];
-    for (int cls = 0; cls < 2; ++cls) {
-      if (tabs[k][cls][sel].size() > c->xtab_stride) return NS_ERR_SIZE;
-      if (upload(c, c->xtab[k][cls], tabs[k][cls][sel]) != cudaSuccess) return NS_ERR_CUDA;
-    }
-  }
-  const ns_status ls = build_line_tables(c);
-  if (ls != NS_OK) return ls;
-  if (upload_step_constants(c) != cudaSuccess) return NS_ERR_CUDA;
-  if (!c->staging && cudaStreamSynchronize(c->stream) != cudaSuccess) return NS_ERR_CUDA;
-  return NS_OK;
-}
-
-// Tables that depend on dt: the RHS rows pre-multiplied by the sub-step constants (FP64 and an
-// FP32 copy) and the ADI y and z factors of every sub-step.  The x tables are build_x_tables.
-ns_status build_dt_tables(ns_ctx* c) {
-  const int ny = c->cfg.ny, nz = c->cfg.nz;
-  const int G = ny + 1;
-  char* base = (char*)c->ws;
-  auto GCv = [&](int f, int j) -> double { return c->gc_h[(size_t)f * G + j]; };
-  ns_status st = NS_OK;
-  for (int k = 0; k < 3 && st == NS_OK; ++k) {
-    c->rtab[k] = (double*)(base + c->lay.off[LB_RTAB] + k * al256((size_t)RT_COUNT * G * 8));
-    const double inv_re = c->cfg.re > 0 ? 1.0 / c->cfg.re : 0.0;
-    const double cl = c->cfg.dt * NS_ALPHA[k] * inv_re;
-    const double dd = 2.0 / (c->dx * c->dx) + 2.0 / (c->dz * c->dz);
-    std::vector<double> rt((size_t)RT_COUNT * G, 0.0);
-    auto RT = [&](int f, int j) -> double& { return rt[(size_t)f * G + j]; };
-    for (int j = 0; j < ny; ++j) {
-      RT(RT_AC, j) = cl * GCv(GC_AC, j);
-      RT(RT_CC, j) = cl * GCv(GC_CC, j);
-      RT(RT_DC, j) = -cl * (dd + GCv(GC_AC, j) + GCv(GC_CC, j));
-      RT(RT_HIDY, j) = 0.5 * GCv(GC_IDY, j);
-    }
-    for (int j = 1; j < ny; ++j) {
-      RT(RT_AF, j) = cl * GCv(GC_AF, j);
-      RT(RT_CF, j) = cl * GCv(GC_CF, j);
-      RT(RT_DF, j) = -cl * (dd + GCv(GC_AF, j) + GCv(GC_CF, j));
-      RT(RT_CGY, j) = -c->cfg.dt * NS_ALPHA[k] * GCv(GC_IHC, j);
-      RT(RT_QIHC, j) = 0.25 * GCv(GC_IHC, j);
-    }
-    if (upload_d(c, c->rtab[k], rt) != cudaSuccess) st = NS_ERR_CUDA;
-    c->rtabf[k] = (float*)(base + c->lay.off[LB_RTAB] + 3 * al256((size_t)RT_COUNT * G * 8) +
-                           k * al256((size_t)RT_COUNT * G * 4));
-    {
-      std::vector<float> rf(rt.begin(), rt.end());
-      if (upload_raw(c, c->rtabf[k], rf.data(), rf.size() * 4) != cudaSuccess) st = NS_ERR_CUDA;
-    }
-  }
-  // ADI y and z factors per sub-step
-  for (int k = 0; k < 3 && st == NS_OK; ++k) {
-    const double beta = beta_of(c, k);
-    {  // centres (u, w): rows j = 0..ny-1
-      std::vector<double> a(ny), b(ny), cc(ny), inv, ainv, cp;
-      for (int j = 0; j < ny; ++j) {
-        a[j] = -beta * GCv(GC_AC, j);
-        cc[j] = -beta * GCv(GC_CC, j);
-        b[j] = 1.0 + beta * (GCv(GC_AC, j) + GCv(GC_CC, j));
-      }
-      thomas_factors(a, b, cc, inv, ainv, cp);
-      std::vector<double> t;
-      t.insert(t.end(), inv.begin(), inv.end());
-      t.insert(t.end(), ainv.begin(), ainv.end());
-      t.insert(t.end(), cp.begin(), cp.end());
-      if (upload(c, c->ytab[k][0], t) != cudaSuccess) st = NS_ERR_CUDA;
-    }
-    {  // faces (v): rows j = 1..ny-1
-      const int n = ny - 1;
-      std::vector<double> a(n), b(n), cc(n), inv, ainv, cp;
-      for (int q = 0; q < n; ++q) {
-        const int j = q + 1;
-        a[q] = -beta * GCv(GC_AF, j);
-        cc[q] = -beta * GCv(GC_CF, j);
-        b[q] = 1.0 + beta * (GCv(GC_AF, j) + GCv(GC_CF, j));
-      }
-      thomas_factors(a, b, cc, inv, ainv, cp);
-      std::vector<double> t;
-      t.insert(t.end(), inv.begin(), inv.end());
-      t.insert(t.end(), ainv.begin(), ainv.end());
-      t.insert(t.end(), cp.begin(), cp.end());
-      if (upload(c, c->ytab[k][1], t) != cudaSuccess) st = NS_ERR_CUDA;
-    }
-    {  // z: cyclic rows (-r, 1 + 2r, -r) by Sherman-Morrison
-      const double r = beta / (c->dz * c->dz);
-      const double lo = -r, di = 1.0 + 2.0 * r, up = -r;
-      const double gam = -di, alpha = up /* A[n-1][0] */, bet = lo /* A[0][n-1] */;
-      std::vector<double> a(nz, lo), b(nz, di), cc(nz, up), inv, ainv, cp;
-      b[0] = di - gam;
-      b[nz - 1] = di - alpha * bet / gam;
-      thomas_factors(a, b, cc, inv, ainv, cp);
-      std::vector<double> s(nz, 0.0);
-      s[0] = gam;
-      s[nz - 1] = alpha;
-      std::vector<double> q = thomas_apply(inv, ainv, cp, s);
-      const double bg = bet / gam;
-      const double fac = 1.0 / (1.0 + q[0] + bg * q[nz - 1]);
-      std::vector<double> t;
-      t.insert(t.end(), inv.begin(), inv.end());
-      t.insert(t.end(), ainv.begin(), ainv.end());
-      t.insert(t.end(), cp.begin(), cp.end());
-      t.insert(t.end(), q.begin(), q.end());
-      t.push_back(fac);
-      t.push_back(bg);
-      if (upload(c, c->ztab[k], t) != cudaSuccess) st = NS_ERR_CUDA;
-    }
-  }
-  if (st == NS_OK && !c->staging && cudaStreamSynchronize(c->stream) != cudaSuccess) st = NS_ERR_CUDA;
-  return st;
 }
 
 void drop_graph(ns_ctx* c) {
@@ -583,6 +125,11 @@ void drop_graph(ns_ctx* c) {
     cudaGraphExecDestroy(c->pgexec);
     cudaGraphDestroy(c->pgraph);
     c->have_pgraph = false;
+  }
+  if (c->have_cgraph) {
+    cudaGraphExecDestroy(c->cgexec);
+    cudaGraphDestroy(c->cgraph);
+    c->have_cgraph = false;
   }
 }
 
@@ -624,9 +171,14 @@ const Stage STAGES[] = {
 };
 const int NSTAGES = (int)(sizeof(STAGES) / sizeof(STAGES[0]));
 
-ns_status run_substep(ns_ctx* c, int k, cudaEvent_t* ev = nullptr) {
+// join: an event the x sweep waits for (the side branch of the fixed-CFL dt update)
+ns_status run_substep(ns_ctx* c, int k, cudaEvent_t* ev = nullptr, cudaEvent_t join = nullptr) {
   for (int q = 0; q < NSTAGES; ++q) {
     if (ev) cudaEventRecordWithFlags(ev[q], c->launch, cudaEventRecordExternal);
+    if (join && STAGES[q].fn == launch_adi_x) {
+      cudaError_t e = cudaStreamWaitEvent(c->launch, join, 0);
+      if (e != cudaSuccess) return cuda_fail(c, e, "join");
+    }
     cudaError_t e = STAGES[q].fn(c, k);
     if (e != cudaSuccess) return cuda_fail(c, e, STAGES[q].name);
   }
@@ -634,8 +186,10 @@ ns_status run_substep(ns_ctx* c, int k, cudaEvent_t* ev = nullptr) {
 }
 
 // Capture the three sub-steps of one time step into a graph (optionally with event nodes) and
-// instantiate it.
-ns_status capture_step(ns_ctx* c, bool profiled, cudaGraph_t* graph, cudaGraphExec_t* exec) {
+// instantiate it.  With cfl the step is preceded by the convective rate and the device-side dt
+// update: its first part on the step's stream, the rest on a side branch that the x sweep of
+// sub-step 0 joins.
+ns_status capture_step(ns_ctx* c, bool profiled, cudaGraph_t* graph, cudaGraphExec_t* exec, bool cfl = false) {
   c->launch = c->cap_stream;
   cudaError_t e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) {
@@ -643,7 +197,19 @@ ns_status capture_step(ns_ctx* c, bool profiled, cudaGraph_t* graph, cudaGraphEx
     return cuda_fail(c, e, "begin capture");
   }
   ns_status s = NS_OK;
-  for (int k = 0; k < 3 && s == NS_OK; ++k) s = run_substep(c, k, profiled ? c->pev + k * NSTAGES : nullptr);
+  if (cfl) {
+    if ((e = launch_convective_rate(c)) == cudaSuccess && (e = launch_dt_update(c, 0)) == cudaSuccess &&
+        (e = cudaEventRecord(c->ev_fork, c->cap_stream)) == cudaSuccess &&
+        (e = cudaStreamWaitEvent(c->side_stream, c->ev_fork, 0)) == cudaSuccess) {
+      c->launch = c->side_stream;
+      e = launch_dt_update(c, 1);
+      c->launch = c->cap_stream;
+      if (e == cudaSuccess) e = cudaEventRecord(c->ev_join, c->side_stream);
+    }
+    if (e != cudaSuccess) s = cuda_fail(c, e, "dt update");
+  }
+  for (int k = 0; k < 3 && s == NS_OK; ++k)
+    s = run_substep(c, k, profiled ? c->pev + k * NSTAGES : nullptr, cfl && k == 0 ? c->ev_join : nullptr);
   if (s == NS_OK && profiled) cudaEventRecordWithFlags(c->pev[3 * NSTAGES], c->cap_stream, cudaEventRecordExternal);
   cudaGraph_t g = nullptr;
   e = cudaStreamEndCapture(c->cap_stream, &g);
@@ -756,7 +322,7 @@ ns_status ns_init(ns_ctx** out, const ns_config* cfg, const ns_fields* fields, v
   c->pois = (double2*)(base + c->lay.off[LB_POIS]);
   c->gc = (double*)(base + c->lay.off[LB_GC]);
   const int nx = cfg->nx, ny = cfg->ny, nz = cfg->nz;
-  c->xtab_stride = (5 * (size_t)nx + 4 * 32 + 8 * 5 * 32);
+  c->xtab_stride = x_table_elems(cfg);
   for (int k = 0; k < 3; ++k) {
     for (int cls = 0; cls < 2; ++cls)
       c->xtab[k][cls] = base + c->lay.off[LB_XTAB] + (2 * k + cls) * al256(c->xtab_stride * c->es);
@@ -771,6 +337,10 @@ ns_status ns_init(ns_ctx** out, const ns_config* cfg, const ns_fields* fields, v
   c->rate = (unsigned long long*)(c->flux + 4);
   c->rcy = (double*)(base + c->lay.off[LB_RCY]);
   c->stepk = (StepK*)(base + c->lay.off[LB_STEPK]);
+  c->dtctl = (DtCtl*)(base + c->lay.off[LB_DT]);
+  c->dtscr = (double*)(base + c->lay.off[LB_DT] + al256(sizeof(DtCtl)));
+  c->dt_xs = x_table_elems(cfg);
+  c->dt_ls = line_table_floats(cfg);
   c->yP = line_P(cfg, cfg->ny);
   c->zP = line_P(cfg, cfg->nz);
   for (int k = 0; k < 3; ++k)
@@ -986,7 +556,7 @@ ns_status ns_set_dt(ns_ctx* c, double dt) {
   if (!c->pin) {
     // workspace bytes of the dt tables and the step constants
     c->pin_lo = c->lay.off[LB_XTAB];
-    c->pin_hi = c->lay.total;  // through LB_PTAB, the last block
+    c->pin_hi = c->lay.off[LB_DT];  // through LB_PTAB
     if (cudaMallocHost(&c->pin, c->pin_hi - c->pin_lo) != cudaSuccess) {
       c->pin = nullptr;
       return fail(c, NS_ERR_CUDA, "pinned staging buffer");
@@ -1021,17 +591,60 @@ ns_status ns_step_cfl(ns_ctx* c, int nsteps, double cfl, double* dts) {
   if (!c) return NS_ERR_ARG;
   if (nsteps < 0) return fail(c, NS_ERR_ARG, "nsteps must be >= 0");
   if (!(cfl > 0.0) || !std::isfinite(cfl)) return fail(c, NS_ERR_ARG, "cfl must be positive and finite");
-  for (int n = 0; n < nsteps; ++n) {
-    double rate = 0.0;
-    ns_status s = ns_convective_rate(c, &rate);
-    if (s != NS_OK) return s;
-    if (!(rate > 0.0)) return fail(c, NS_ERR_STATE, "fluid at rest: no convective time step");
-    const double dt = cfl / rate;
-    if (dt != c->cfg.dt && (s = ns_set_dt(c, dt)) != NS_OK) return s;
-    if (dts) dts[n] = dt;
-    if ((s = ns_step(c, 1)) != NS_OK) return s;
+  if (capturing(c)) return fail(c, NS_ERR_STATE, "ns_step_cfl during capture");
+  if (nsteps == 0) return NS_OK;
+  // every kernel reads the sub-step constants from the workspace, where the dt update writes them
+  if (!c->dyn_consts) {
+    c->dyn_consts = true;
+    drop_graph(c);
   }
-  return NS_OK;
+  if (!c->side_stream) {
+    cudaError_t e0 = cudaStreamCreateWithFlags(&c->side_stream, cudaStreamNonBlocking);
+    if (e0 == cudaSuccess) e0 = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
+    if (e0 == cudaSuccess) e0 = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
+    if (e0 != cudaSuccess) return cuda_fail(c, e0, "side stream");
+  }
+  if (!c->have_cgraph) {
+    ns_status s = capture_step(c, false, &c->cgraph, &c->cgexec, true);
+    if (s != NS_OK) return s;
+    c->have_cgraph = true;
+  }
+  // runs of at most NS_DTLOG steps: reset the control block, launch, read the log back
+  const size_t head = offsetof(DtCtl, dts);
+  std::vector<char> hbuf(sizeof(DtCtl));
+  DtCtl* h = reinterpret_cast<DtCtl*>(hbuf.data());
+  cudaError_t e;
+  ns_status st = NS_OK;
+  for (int done = 0; done < nsteps && st == NS_OK;) {
+    const int n = std::min(nsteps - done, NS_DTLOG);
+    memset(h, 0, head);
+    h->cfl = cfl;
+    h->dt = c->cfg.dt;
+    if ((e = cudaMemcpyAsync(c->dtctl, h, head, cudaMemcpyHostToDevice, c->stream)) != cudaSuccess)
+      return cuda_fail(c, e, "dt control block");
+    for (int q = 0; q < n; ++q)
+      if ((e = cudaGraphLaunch(c->cgexec, c->stream)) != cudaSuccess) return cuda_fail(c, e, "graph launch");
+    if ((e = cudaMemcpyAsync(h, c->dtctl, head + (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, c->stream)) !=
+            cudaSuccess ||
+        (e = cudaStreamSynchronize(c->stream)) != cudaSuccess)
+      return cuda_fail(c, e, "dt log");
+    if (dts) memcpy(dts + done, h->dts, (size_t)n * sizeof(double));
+    c->cfg.dt = h->dt;
+    if (h->status)
+      st = fail(c, NS_ERR_STATE,
+                std::string(h->status == 1 ? "the velocity field holds a non-finite value"
+                                           : "fluid at rest: no convective time step") +
+                    " (step " + std::to_string(done + (int)h->fail_step) + " kept the previous dt)");
+    done += n;
+  }
+  // the host image of the tables (modes, levels, sub-step constants) at the last dt; the device
+  // already holds the same bytes
+  c->dry = true;
+  ns_status r = build_dt_tables(c);
+  if (r == NS_OK) r = build_x_tables(c);
+  c->dry = false;
+  if (st == NS_OK && r != NS_OK) st = fail(c, r, "host image of the dt tables");
+  return st;
 }
 
 // Stages that launch nothing in this configuration (the boundary-plane stages of periodic x).
@@ -1212,6 +825,9 @@ void ns_destroy(ns_ctx* c) {
   drop_graph(c);
   for (int q = 0; q < c->npev; ++q) cudaEventDestroy(c->pev[q]);
   cudaStreamDestroy(c->cap_stream);
+  if (c->side_stream) cudaStreamDestroy(c->side_stream);
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  if (c->ev_join) cudaEventDestroy(c->ev_join);
   if (c->pin) cudaFreeHost(c->pin);
   if (c->own_ws) cudaFree(c->ws);
   delete c;

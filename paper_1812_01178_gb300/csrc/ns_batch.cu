@@ -34,7 +34,6 @@ constexpr int NBATCH_STAGES = 10;
 constexpr size_t kArenaBase = 1 << 20;
 constexpr size_t kArenaPerInstance = 64 << 10;
 
-size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 }  // namespace
 

@@ -124,6 +124,12 @@ enum { GC_DY = 0, GC_IDY, GC_HC, GC_IHC, GC_WLO, GC_WHI, GC_AC, GC_CC, GC_AF, GC
 //   HIDY     : 1 / (2 dy_j),   QIHC : 1 / (4 hc_j)
 enum { RT_AC = 0, RT_CC, RT_DC, RT_AF, RT_CF, RT_DF, RT_CGY, RT_HIDY, RT_QIHC, RT_COUNT };
 
+// Constants of the tiled RHS in StepK::kd / kf: quarter and half inverse spacings in x and z, the
+// convection weights -dt gamma_k and -dt zeta_k, the pressure-gradient and viscous weights
+// -dt alpha_k / dx, -dt alpha_k / dz, dt alpha_k / (Re dx^2), dt alpha_k / (Re dz^2), and the body
+// force dt alpha_k fx.
+enum { RK_QIDX, RK_QIDZ, RK_HIDX, RK_HIDZ, RK_CN, RK_CP, RK_CGX, RK_CGZ, RK_CX, RK_CZ, RK_CB };
+
 // RK3 constants (Sec. 2.2): gamma, zeta, alpha = gamma + zeta.
 static const double NS_GAMMA[3] = {8.0 / 15.0, 5.0 / 12.0, 3.0 / 4.0};
 static const double NS_ZETA[3] = {0.0, -17.0 / 60.0, -5.0 / 12.0};
@@ -152,7 +158,7 @@ struct ns_layout {
 
 enum {
   LB_RU = 0, LB_RV, LB_RW, LB_NU, LB_NV, LB_NW, LB_PHI, LB_SPEC, LB_POIS, LB_GC, LB_XTAB, LB_YTAB,
-  LB_ZTAB, LB_TWZ, LB_TWX, LB_LAMX, LB_LAMZ, LB_RTAB, LB_DOUT, LB_TWD, LB_RCY, LB_STEPK, LB_PTAB, LB_COUNT
+  LB_ZTAB, LB_TWZ, LB_TWX, LB_LAMX, LB_LAMZ, LB_RTAB, LB_DOUT, LB_TWD, LB_RCY, LB_STEPK, LB_PTAB, LB_DT, LB_COUNT
 };
 
 // dt-dependent constants of one RK3 sub-step (entries 0..2) and of the projection of an initial
@@ -172,6 +178,20 @@ struct StepK {
   int Ly, Lz;         // the same for the partitioned y and z lines of the mixed form
 };
 constexpr int NS_STEPK = 4;
+
+inline size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Control block of the fixed-CFL steps whose dt is set on the device (k_dt.cu): the host writes
+// cfl, dt (the current one), count = status = 0 before a run of at most NS_DTLOG steps; each step
+// logs the dt it used.  status: 0, 1 (a non-finite convective rate) or 2 (a zero rate) at step
+// fail_step, which then keeps the previous dt.
+constexpr int NS_DTLOG = 1024;
+struct DtCtl {
+  double cfl;
+  double dt;
+  unsigned count, status, fail_step, pad;
+  double dts[NS_DTLOG];
+};
 
 struct ns_ctx {
   ns_config cfg;
@@ -222,6 +242,12 @@ struct ns_ctx {
   size_t pin_lo = 0, pin_hi = 0;
   bool staging = false;
   bool dyn_consts = false;  // set by ns_set_dt: kernels read the sub-step constants from stepk
+  bool dry = false;         // table builders update the host state only (upload_raw copies nothing)
+  // device-side dt update of the fixed-CFL steps: control block, FP64 scratch of the table
+  // builders, and the doubles reserved per x table (dt_xs) and per line table (dt_ls)
+  DtCtl* dtctl = nullptr;
+  double* dtscr = nullptr;
+  size_t dt_xs = 0, dt_ls = 0;
   std::vector<std::pair<size_t, size_t>> dirty;  // (workspace offset, bytes) written while staging
   int num_sms;
   int rhs_bps[2];           // resident blocks per SM of the tiled RHS (FP64, FP32)
@@ -242,6 +268,13 @@ struct ns_ctx {
   bool have_pgraph;
   cudaEvent_t pev[64];
   int npev;
+  // fixed-CFL graph: convective rate, dt update, then the step; the tables sub-step 0's RHS does not
+  // read are built on side_stream beside it (fork / join events)
+  cudaStream_t side_stream = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaGraph_t cgraph;
+  cudaGraphExec_t cgexec;
+  bool have_cgraph = false;
   std::string err;
 };
 
@@ -430,7 +463,17 @@ cudaError_t launch_outflow(ns_ctx* c, int k);        // convective outflow updat
 cudaError_t launch_flux_correct(ns_ctx* c, int k);   // outflow volume flux := inflow flux
 cudaError_t launch_pois_factor(ns_ctx* c, const double* lamx, const double* lamz);
 cudaError_t launch_convective_rate(ns_ctx* c);  // max-reduction into c->rate (zeroed first)
-void rhs_fill_step(const ns_ctx* c, int k, StepK& sk);  // RHS part of StepK (k_rhs.cu)
+// dt-dependent tables (k_dt.cu).  build_dt_tables: RHS rows, ADI y and z factors;
+// build_x_tables: x-solver and partitioned-line tables (modes chosen by the PDD drop) and the
+// sub-step constants.  launch_dt_update: the same tables on the device from dt = cfl / rate.
+ns_status build_dt_tables(ns_ctx* c);
+ns_status build_x_tables(ns_ctx* c);
+cudaError_t launch_dt_update(ns_ctx* c, int part);
+size_t dt_scratch_doubles(int nz, size_t xs, size_t ls);  // doubles of the dtscr block
+// Host -> workspace copy of a table: to the pinned mirror while c->staging (flush_staging
+// copies the recorded ranges asynchronously), nothing while c->dry, else a copy and a sync.
+cudaError_t upload_raw(ns_ctx* c, void* dst, const void* src, size_t bytes);
+cudaError_t flush_staging(ns_ctx* c);
 inline int stepk_index(int k) { return k < 0 ? 3 : k; }
 cudaError_t launch_recycle(ns_ctx* c, int k);    // recycled inflow planes (sub-step 0, if enabled)
 size_t recycle_block_doubles(int ny);

@@ -34,7 +34,6 @@ double h_lamx[4096];
 double h_lamz[2049];
 StepK h_stepk[NS_STEPK];
 
-size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Regions {
   size_t spec, pois, gc, twz, twx, lamx, lamz, stepk, total;

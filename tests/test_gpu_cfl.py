@@ -33,6 +33,31 @@ def test_convective_rate_equals_the_oracle(shape):
     s.close()
 
 
+@pytest.mark.parametrize("shape", [(64, 37, 32), (24, 9, 16)])
+def test_convective_rate_screening_edge_values(shape):
+    """The rate kernel skips cells whose cheap upper bound is below an exact value already found;
+    fields built to stress that bound: mostly zero, subnormal and tiny values, faces of v that
+    cancel to the last bits, a few spikes of either sign, and values a hair apart at the top.
+    The maximum still equals the oracle's to the last bit."""
+    case, g, u, v, w, p = _projected(shape, 11)
+    rng = np.random.default_rng(5)
+    for f in (u, v, w):
+        f *= 0.0
+        f.flat[rng.integers(0, f.size, 50)] = rng.choice([5e-324, -1e-310, 1e-300, 3e-39, -2e-38], 50)
+    nx, ny, nz = case.nx, case.ny, case.nz
+    v[:, 1:ny, :] = 0.7
+    v[:, 2:ny, ::3] = -0.7 + 1e-15  # cancellation across the two faces of a cell
+    top = 1.0 + np.arange(7) * 2.0 ** -50
+    for q, val in enumerate(top):
+        u.flat[rng.integers(0, u.size)] = val * (-1) ** q
+        w.flat[rng.integers(0, w.size)] = -val
+    s = B.Solver(case, u, v, w, p)
+    assert s.convective_rate() == O.convective_rate(g, u, v, w)
+    s.u.mul_(-1.0)
+    assert s.convective_rate() == O.convective_rate(g, -u, v, w)
+    s.close()
+
+
 def test_convective_rate_boundary_layer():
     case, u, v, w, p, bl = I.boundary_layer(64, 20, 16, amp=0.05, seed=3, re=200.0)
     g = O.Grid.from_case(case)
@@ -84,6 +109,81 @@ def test_step_cfl_boundary_layer():
     for name in ("u", "v", "w", "p"):
         assert errs[name] < 1e-11, (name, errs)
     s.close()
+
+
+def _host_cfl(s, n, cfl):
+    """Fixed-CFL steps driven from the host: read the rate, set dt (host-built tables), step."""
+    dts = []
+    for _ in range(n):
+        dt = cfl / s.convective_rate()
+        s.set_dt(dt)
+        s.step(1)
+        dts.append(dt)
+    return dts
+
+
+def _same_state(a, b):
+    for x, y, name in zip(a.state(), b.state(), "uvwp"):
+        assert np.array_equal(x, y), name
+    for q, x in a.boundary().items():
+        assert np.array_equal(x, b.boundary()[q]), q
+
+
+# (precision, shape, x partition request): FP64 and mixed; the mixed shapes have partitioned y and z
+# lines (nx a multiple of 32, ny and nz with a built line shape); PPT forced with several levels
+@pytest.mark.parametrize("prec,shape,part", [
+    (B.NS_FP64, (64, 20, 32), None),
+    (B.NS_MIXED, (64, 48, 64), None),
+    (B.NS_FP64, (64, 20, 32), (8, B.NS_PART_PPT)),
+    (B.NS_MIXED, (96, 32, 48), (32, B.NS_PART_PPT)),
+])
+def test_device_dt_update_equals_the_host_tables(prec, shape, part):
+    """ns_step_cfl computes dt and rebuilds every table on the device inside its graph; the host
+    path (rate read back, ns_set_dt, ns_step) builds them with the same functions: the dts and the
+    fields agree to the last bit."""
+    case, g, u, v, w, p = _projected(shape, 6)
+    a = B.Solver(case, u, v, w, p, precision=prec)
+    b = B.Solver(case, u, v, w, p, precision=prec)
+    if part:
+        a.set_partition(*part)
+        b.set_partition(*part)
+    d_dev = a.step_cfl(4, 0.6)
+    d_host = _host_cfl(b, 4, 0.6)
+    assert list(d_dev) == d_host
+    assert len(set(d_host)) == 4
+    _same_state(a, b)
+    assert a.partition() == b.partition()
+    a.close()
+    b.close()
+
+
+def test_device_dt_update_equals_the_host_tables_boundary_layer():
+    case, u, v, w, p, bl = I.boundary_layer(64, 16, 16, amp=0.05, seed=8, re=200.0)
+    g = O.Grid.from_case(case)
+    u, v, w, bl = O.make_divergence_free_bl(g, u, v, w, bl)
+    a = B.Solver(case, u, v, w, p, bl=bl)
+    b = B.Solver(case, u, v, w, p, bl=bl)
+    d_dev = a.step_cfl(3, 0.8)
+    d_host = _host_cfl(b, 3, 0.8)
+    assert list(d_dev) == d_host
+    _same_state(a, b)
+    a.close()
+    b.close()
+
+
+def test_step_cfl_runs_longer_than_the_dt_log():
+    """More steps than the device dt log holds: the call runs them in several launches of the
+    graph, reading the log back after each; dt then continues from the last one."""
+    case, g, u, v, w, p = _projected((16, 9, 8), 9)
+    a = B.Solver(case, u, v, w, p)
+    b = B.Solver(case, u, v, w, p)
+    n = 1030
+    d_dev = list(a.step_cfl(n, 0.5)) + list(a.step_cfl(2, 0.5))
+    d_host = _host_cfl(b, n + 2, 0.5)
+    assert d_dev == d_host
+    _same_state(a, b)
+    a.close()
+    b.close()
 
 
 @pytest.mark.parametrize("shape", [(64, 37, 32), (96, 13, 24)])
