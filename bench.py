@@ -37,9 +37,14 @@ UNIT = "grid-point-steps/s"
 # bytes = each input read once + each output written once; flops = floating-point operations of
 # the formulas (FMA = 2).  Complex spectral arrays have (nz/2+1)/nz of a cell each.
 def kernel_model(nx, ny, nz, es):
+    """(algorithmic bytes, flops) per cell of one launch of each stage.  es = 8: FP64 form, with the
+    Poisson spectra in complex128.  es = 4: the mixed form, whose Poisson transforms run in FP32 on
+    a complex64 spectrum around an FP64 right-hand side and one FP64 refinement; its Poisson flops
+    count the FP64 work only (divergence, residual, y solves), the FP32 transforms being far from
+    their pipe's bound."""
     sh = (nz // 2 + 1) / nz
     L = lambda n: math.log2(n)
-    return {
+    m = {
         #                 bytes per cell                       flops per cell
         "rhs":              (4 * 8 + 3 * es + 6 * es,        170.0),
         "adi_x":            (6 * es,                         30.0),
@@ -54,8 +59,23 @@ def kernel_model(nx, ny, nz, es):
         "flux_correct":     (8 * 3.0 / nx,                   3.0 / nx),
         "recycle":          (8 * 3.0 * 4 / nx,               40.0 / nx),
         "poisson_ifftz":    (sh * 16 + 8,                    2.5 * L(nz) + 2.0),
+        "poisson_refine":   (0.0,                            0.0),
         "project":          (8 + 8 * 8,                      11.0),
     }
+    if es == 4:
+        cs = 8  # complex64
+        m.update({
+            # u, v, w in; bs (FP64) and the spectrum out
+            "poisson_div_fftz": (3 * 8 + 8 + sh * cs,        9.0),
+            "poisson_x_fwd":    (2 * sh * cs,                0.0),
+            # spectrum in and out, the two FP64 factor planes
+            "poisson_tdma_y":   (sh * (2 * cs + 16),         sh * 10.0),
+            "poisson_x_inv":    (2 * sh * cs,                0.0),
+            "poisson_ifftz":    (sh * cs + 4,                0.0),
+            # residual (bs, phi1 in, spectrum out), the four stages again, phi = phi1 + phi2
+            "poisson_refine":   (24 + 8 * sh * cs + sh * 16, 13.0 + sh * 10.0),
+        })
+    return m
 
 
 def load_peaks():

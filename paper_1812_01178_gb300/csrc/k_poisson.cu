@@ -16,8 +16,22 @@
 
 namespace {
 
-__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+// complex arithmetic on double2 (FP64 path) and float2 (the transforms of the mixed form)
+template <typename C> struct Cplx;
+template <> struct Cplx<double2> {
+  using R = double;
+  static __device__ __forceinline__ double2 mk(double x, double y) { return make_double2(x, y); }
+};
+template <> struct Cplx<float2> {
+  using R = float;
+  static __device__ __forceinline__ float2 mk(float x, float y) { return make_float2(x, y); }
+};
+__device__ __forceinline__ double fmaT(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float fmaT(float a, float b, float c) { return fmaf(a, b, c); }
+template <typename C>
+__device__ __forceinline__ C cadd(C a, C b) { return Cplx<C>::mk(a.x + b.x, a.y + b.y); }
+template <typename C>
+__device__ __forceinline__ C csub(C a, C b) { return Cplx<C>::mk(a.x - b.x, a.y - b.y); }
 
 // Stockham autosort FFT on nseq sequences of length N = 2^a 3^b stored contiguously in A
 // ([seq][N]); plan = a | (b << 8) (fft_plan).  B is scratch of the same size.  SIGN = -1 forward,
@@ -37,8 +51,10 @@ __device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_doub
 // {tan 2th, cos 2th / cos th}, {cos th / 2, (sqrt 3 / 2) cos th}.  cos th is never exactly zero in
 // floating point, so every factor is finite.  Returns the buffer that holds the result.  All
 // threads of the block take part.
-template <int SIGN>
-__device__ double2* stockham(double2* A, double2* B, int N, int plan, int nseq, const double2* __restrict__ tw) {
+template <int SIGN, typename C = double2>
+__device__ C* stockham(C* A, C* B, int N, int plan, int nseq, const C* __restrict__ tw) {
+  using R = typename Cplx<C>::R;
+  auto mk = [](R x, R y) { return Cplx<C>::mk(x, y); };
   const int a2 = plan & 0xff, b3 = plan >> 8;
   const bool p2 = b3 == 0;  // N a power of two: index arithmetic by shifts
   int Ns = 1;
@@ -48,14 +64,14 @@ __device__ double2* stockham(double2* A, double2* B, int N, int plan, int nseq, 
     for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
       const int sq = p2 ? idx >> (a2 - 1) : idx / half;
       const int j = idx - sq * half;
-      const double2* X = A + sq * N;
-      double2* Y = B + sq * N;
-      const double2 a = X[j], b = X[j + half];
+      const C* X = A + sq * N;
+      C* Y = B + sq * N;
+      const C a = X[j], b = X[j + half];
       Y[2 * j] = cadd(a, b);
       Y[2 * j + 1] = csub(a, b);
     }
     __syncthreads();
-    double2* t = A;
+    C* t = A;
     A = B;
     B = t;
     Ns = 2;
@@ -68,36 +84,36 @@ __device__ double2* stockham(double2* A, double2* B, int N, int plan, int nseq, 
       const int sq = p2 ? idx >> (a2 - 2) : idx / quarter;
       const int j = idx - sq * quarter;
       const int k = j & (Ns - 1);
-      const double2* X = A + sq * N + j;
-      double2* Y = B + sq * N + ((j >> ls) << (ls + 2)) + k;
-      const double2 a = X[0], b = X[quarter], c = X[2 * quarter], d = X[3 * quarter];
-      double2 y0, y1, y2, y3;
+      const C* X = A + sq * N + j;
+      C* Y = B + sq * N + ((j >> ls) << (ls + 2)) + k;
+      const C a = X[0], b = X[quarter], c = X[2 * quarter], d = X[3 * quarter];
+      C y0, y1, y2, y3;
       if (Ns == 1) {
-        const double2 t0 = cadd(a, c), t1 = csub(a, c), t2 = cadd(b, d), t3 = csub(b, d);
+        const C t0 = cadd(a, c), t1 = csub(a, c), t2 = cadd(b, d), t3 = csub(b, d);
         // -i t3 (forward) or +i t3 (inverse)
-        const double2 r3 = SIGN < 0 ? make_double2(t3.y, -t3.x) : make_double2(-t3.y, t3.x);
+        const C r3 = SIGN < 0 ? mk(t3.y, -t3.x) : mk(-t3.y, t3.x);
         y0 = cadd(t0, t2);
         y2 = csub(t0, t2);
         y1 = cadd(t1, r3);
         y3 = csub(t1, r3);
       } else {
-        const double2 e1 = __ldg(tw + 3 * (Ns + k)), e2 = __ldg(tw + 3 * (Ns + k) + 1), e3 = __ldg(tw + 3 * (Ns + k) + 2);
-        const double t1 = SIGN < 0 ? e1.x : -e1.x, t2 = SIGN < 0 ? e2.x : -e2.x, t3 = SIGN < 0 ? e3.x : -e3.x;
-        const double c1 = e1.y, c2 = e2.y, r = e3.y;
+        const C e1 = __ldg(tw + 3 * (Ns + k)), e2 = __ldg(tw + 3 * (Ns + k) + 1), e3 = __ldg(tw + 3 * (Ns + k) + 2);
+        const R t1 = SIGN < 0 ? e1.x : -e1.x, t2 = SIGN < 0 ? e2.x : -e2.x, t3 = SIGN < 0 ? e3.x : -e3.x;
+        const R c1 = e1.y, c2 = e2.y, r = e3.y;
         // b, c, d times their twiddles, each up to its cosine
-        const double2 bb = make_double2(fma(t1, b.y, b.x), fma(-t1, b.x, b.y));
-        const double2 cc = make_double2(fma(t2, c.y, c.x), fma(-t2, c.x, c.y));
-        const double2 dd = make_double2(fma(t3, d.y, d.x), fma(-t3, d.x, d.y));
-        const double2 T0 = make_double2(fma(c2, cc.x, a.x), fma(c2, cc.y, a.y));    // a + c w^2k
-        const double2 T1 = make_double2(fma(-c2, cc.x, a.x), fma(-c2, cc.y, a.y));  // a - c w^2k
-        const double2 S = make_double2(fma(r, dd.x, bb.x), fma(r, dd.y, bb.y));    // (b w^k + d w^3k) / cos th
-        const double2 D = make_double2(fma(-r, dd.x, bb.x), fma(-r, dd.y, bb.y));  // (b w^k - d w^3k) / cos th
-        y0 = make_double2(fma(c1, S.x, T0.x), fma(c1, S.y, T0.y));
-        y2 = make_double2(fma(-c1, S.x, T0.x), fma(-c1, S.y, T0.y));
+        const C bb = mk(fmaT(t1, b.y, b.x), fmaT(-t1, b.x, b.y));
+        const C cc = mk(fmaT(t2, c.y, c.x), fmaT(-t2, c.x, c.y));
+        const C dd = mk(fmaT(t3, d.y, d.x), fmaT(-t3, d.x, d.y));
+        const C T0 = mk(fmaT(c2, cc.x, a.x), fmaT(c2, cc.y, a.y));    // a + c w^2k
+        const C T1 = mk(fmaT(-c2, cc.x, a.x), fmaT(-c2, cc.y, a.y));  // a - c w^2k
+        const C S = mk(fmaT(r, dd.x, bb.x), fmaT(r, dd.y, bb.y));    // (b w^k + d w^3k) / cos th
+        const C D = mk(fmaT(-r, dd.x, bb.x), fmaT(-r, dd.y, bb.y));  // (b w^k - d w^3k) / cos th
+        y0 = mk(fmaT(c1, S.x, T0.x), fmaT(c1, S.y, T0.y));
+        y2 = mk(fmaT(-c1, S.x, T0.x), fmaT(-c1, S.y, T0.y));
         // y1 = T1 - i (v1 - v3), y3 = T1 + i (v1 - v3) forward; signs of i swap for the inverse
-        const double s1 = SIGN < 0 ? c1 : -c1;
-        y1 = make_double2(fma(s1, D.y, T1.x), fma(-s1, D.x, T1.y));
-        y3 = make_double2(fma(-s1, D.y, T1.x), fma(s1, D.x, T1.y));
+        const R s1 = SIGN < 0 ? c1 : -c1;
+        y1 = mk(fmaT(s1, D.y, T1.x), fmaT(-s1, D.x, T1.y));
+        y3 = mk(fmaT(-s1, D.y, T1.x), fmaT(s1, D.x, T1.y));
       }
       Y[0] = y0;
       Y[Ns] = y1;
@@ -105,12 +121,12 @@ __device__ double2* stockham(double2* A, double2* B, int N, int plan, int nseq, 
       Y[3 * Ns] = y3;
     }
     __syncthreads();
-    double2* t = A;
+    C* t = A;
     A = B;
     B = t;
   }
   const int third = N / 3;
-  constexpr double kS3 = 0.86602540378443864676;  // sqrt(3) / 2
+  const R kS3 = (R)0.86602540378443864676;  // sqrt(3) / 2
   for (int st = 0; st < b3; ++st, Ns *= 3) {
     const int total = nseq * third;
     for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
@@ -118,36 +134,36 @@ __device__ double2* stockham(double2* A, double2* B, int N, int plan, int nseq, 
       const int j = idx - sq * third;
       const int g = j / Ns;
       const int k = j - g * Ns;
-      const double2* X = A + sq * N + j;
-      double2* Y = B + sq * N + g * 3 * Ns + k;
-      const double2 a = X[0], b = X[third], c = X[2 * third];
-      double2 S, D, y0, T;
-      double gs;
+      const C* X = A + sq * N + j;
+      C* Y = B + sq * N + g * 3 * Ns + k;
+      const C a = X[0], b = X[third], c = X[2 * third];
+      C S, D, y0, T;
+      R gs;
       if (Ns == 1) {
         S = cadd(b, c);
         D = csub(b, c);
         y0 = cadd(a, S);
-        T = make_double2(fma(-0.5, S.x, a.x), fma(-0.5, S.y, a.y));
+        T = mk(fmaT((R)-0.5, S.x, a.x), fmaT((R)-0.5, S.y, a.y));
         gs = SIGN < 0 ? kS3 : -kS3;
       } else {
-        const double2 e1 = __ldg(tw + 3 * (Ns + k)), e2 = __ldg(tw + 3 * (Ns + k) + 1), e3 = __ldg(tw + 3 * (Ns + k) + 2);
-        const double t1 = SIGN < 0 ? e1.x : -e1.x, t2 = SIGN < 0 ? e2.x : -e2.x;
-        const double c1 = e1.y, r = e2.y, h = e3.x;
-        const double2 bb = make_double2(fma(t1, b.y, b.x), fma(-t1, b.x, b.y));
-        const double2 cc = make_double2(fma(t2, c.y, c.x), fma(-t2, c.x, c.y));
-        S = make_double2(fma(r, cc.x, bb.x), fma(r, cc.y, bb.y));    // (b w^k + c w^2k) / cos th
-        D = make_double2(fma(-r, cc.x, bb.x), fma(-r, cc.y, bb.y));  // (b w^k - c w^2k) / cos th
-        y0 = make_double2(fma(c1, S.x, a.x), fma(c1, S.y, a.y));
-        T = make_double2(fma(-h, S.x, a.x), fma(-h, S.y, a.y));      // a - (v1 + v2) / 2
+        const C e1 = __ldg(tw + 3 * (Ns + k)), e2 = __ldg(tw + 3 * (Ns + k) + 1), e3 = __ldg(tw + 3 * (Ns + k) + 2);
+        const R t1 = SIGN < 0 ? e1.x : -e1.x, t2 = SIGN < 0 ? e2.x : -e2.x;
+        const R c1 = e1.y, r = e2.y, h = e3.x;
+        const C bb = mk(fmaT(t1, b.y, b.x), fmaT(-t1, b.x, b.y));
+        const C cc = mk(fmaT(t2, c.y, c.x), fmaT(-t2, c.x, c.y));
+        S = mk(fmaT(r, cc.x, bb.x), fmaT(r, cc.y, bb.y));    // (b w^k + c w^2k) / cos th
+        D = mk(fmaT(-r, cc.x, bb.x), fmaT(-r, cc.y, bb.y));  // (b w^k - c w^2k) / cos th
+        y0 = mk(fmaT(c1, S.x, a.x), fmaT(c1, S.y, a.y));
+        T = mk(fmaT(-h, S.x, a.x), fmaT(-h, S.y, a.y));      // a - (v1 + v2) / 2
         gs = SIGN < 0 ? e3.y : -e3.y;                                // (sqrt 3 / 2) cos th
       }
       // y1 = T - i (sqrt 3 / 2)(v1 - v2), y2 = T + i (sqrt 3 / 2)(v1 - v2) forward
       Y[0] = y0;
-      Y[Ns] = make_double2(fma(gs, D.y, T.x), fma(-gs, D.x, T.y));
-      Y[2 * Ns] = make_double2(fma(-gs, D.y, T.x), fma(gs, D.x, T.y));
+      Y[Ns] = mk(fmaT(gs, D.y, T.x), fmaT(-gs, D.x, T.y));
+      Y[2 * Ns] = mk(fmaT(-gs, D.y, T.x), fmaT(gs, D.x, T.y));
     }
     __syncthreads();
-    double2* t = A;
+    C* t = A;
     A = B;
     B = t;
   }
@@ -247,45 +263,46 @@ struct DivzK {
 // ------------------------------------------------------------------------------------------
 // complex FFT along x of R rows per block (rows are contiguous, length nx), in place.
 // ------------------------------------------------------------------------------------------
-template <int SIGN>
+template <int SIGN, typename C = double2>
 struct FftxK {
+  using R_ = typename Cplx<C>::R;
   struct Args {
-    double2* spec;
-    const double2* twx;
+    C* spec;
+    const C* twx;
     long nrows;
     int nx;
     int px;  // fft_plan(nx)
     int R;
-    double scale;
+    R_ scale;
   };
   static constexpr int kThreads = 256;
   static constexpr int kMinBlocks = 4;  // shared memory limits residency to ~3 blocks anyway
-  static Args make(double2* spec, const double2* twx, long nrows, int nx, int px, int R, double scale) { return Args{spec, twx, nrows, nx, px, R, scale}; }
+  static Args make(C* spec, const C* twx, long nrows, int nx, int px, int R, R_ scale) { return Args{spec, twx, nrows, nx, px, R, scale}; }
   static __device__ __forceinline__ void run(const Args& a_, const dim3 bid_, const dim3 gdim_) {
-    double2* __restrict__ spec = a_.spec;
-    const double2* __restrict__ twx = a_.twx;
+    C* __restrict__ spec = a_.spec;
+    const C* __restrict__ twx = a_.twx;
     long nrows = a_.nrows;
     int nx = a_.nx;
     int px = a_.px;
     int R = a_.R;
-    double scale = a_.scale;
+    R_ scale = a_.scale;
 
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  double2* A = reinterpret_cast<double2*>(smem_raw);
-  double2* B = A + R * nx;
+  C* A = reinterpret_cast<C*>(smem_raw);
+  C* B = A + R * nx;
   const long row0 = (long)bid_.x * R;
   const int nr = (int)min((long)R, nrows - row0);
-  double2* g = spec + row0 * nx;
+  C* g = spec + row0 * nx;
   for (int q = threadIdx.x; q < nr * nx; q += blockDim.x) A[q] = g[q];
-  for (int q = nr * nx + threadIdx.x; q < R * nx; q += blockDim.x) A[q] = make_double2(0.0, 0.0);
+  for (int q = nr * nx + threadIdx.x; q < R * nx; q += blockDim.x) A[q] = Cplx<C>::mk(0, 0);
   __syncthreads();
-  double2* Rb = stockham<SIGN>(A, B, nx, px, R, twx);
-  if (scale == 1.0) {
+  C* Rb = stockham<SIGN, C>(A, B, nx, px, R, twx);
+  if (scale == (R_)1) {
     for (int q = threadIdx.x; q < nr * nx; q += blockDim.x) g[q] = Rb[q];
   } else {
     for (int q = threadIdx.x; q < nr * nx; q += blockDim.x) {
-      const double2 t = Rb[q];
-      g[q] = make_double2(t.x * scale, t.y * scale);
+      const C t = Rb[q];
+      g[q] = Cplx<C>::mk(t.x * scale, t.y * scale);
     }
   }
 
@@ -434,6 +451,218 @@ struct IfftzK {
 };
 
 // ------------------------------------------------------------------------------------------
+// The Poisson solve of the mixed form: FP32 transforms, one FP64 refinement.
+//   pass 1: bs = D u* / (alpha_k dt nx nz) in FP64 (stored), its transforms in FP32 (complex64
+//           spectrum), the y solves in FP64 arithmetic on that spectrum, phi1 = inverse (FP32)
+//   pass 2: rs = bs - (D G phi1) / (nx nz) in FP64, with D G the operator the solve inverts
+//           (periodic or Neumann x, the PA / PC rows in y, periodic z), the same FP32 pipeline on
+//           rs, and phi = phi1 + phi2 in FP64
+// The FP32 transforms leave relative errors near 1e-6 in phi1; the residual, formed in FP64 from
+// the stored phi1, carries them into phi2, whose own FP32 error is then near 1e-12 of phi: the
+// projected divergence stays at the level of the FP64 solve.  Conversions between FP64 and FP32
+// go through the integer pipe (d2f_rn, f2d).
+// ------------------------------------------------------------------------------------------
+template <bool RES>
+struct DivzMK {
+  struct Args {
+    const double* u;
+    const double* v;
+    const double* w;
+    const double* gc;
+    const float2* twz;
+    float2* spec;
+    double* bs;         // pass 1 writes it, pass 2 reads it
+    const float* phi1;  // pass 2
+    int nx, ny, nz, pz, TX, bl;
+    double idx, idz, idx2, idz2, inv_nxnz;
+    const StepK* sk;  // pscale = 1 / (alpha_k dt nx nz)
+    const double* u_out;
+  };
+  static constexpr int kThreads = 256;
+  static constexpr int kMinBlocks = 4;
+  static __device__ __forceinline__ void run(const Args& a, const dim3 bid_, const dim3) {
+    const int nx = a.nx, ny = a.ny, nz = a.nz, TX = a.TX;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int nseq = TX >> 1;
+    float2* A = reinterpret_cast<float2*>(smem_raw);
+    float2* B = A + nseq * nz;
+    const int i0 = bid_.x * TX;
+    const int j = bid_.y;
+    const long pl = (long)ny * nx, plv = (long)(ny + 1) * nx;
+    if (!RES) {
+      const double scale = a.sk->pscale;
+      const double idy = __ldg(a.gc + GC_IDY * (ny + 1) + j) * scale, idx = a.idx * scale, idz = a.idz * scale;
+      for (int q = threadIdx.x; q < TX * nz; q += blockDim.x) {
+        const int il = q % TX, k = q / TX, i = i0 + il;
+        const int ip = (i + 1 == nx) ? 0 : i + 1;
+        const int kp = (k + 1 == nz) ? 0 : k + 1;
+        const long c = k * pl + (long)j * nx;
+        const double uip = (a.u_out && i + 1 == nx) ? __ldg(a.u_out + (long)k * ny + j) : __ldg(a.u + c + ip);
+        const double du = uip - __ldg(a.u + c + i);
+        const double dv = __ldg(a.v + k * plv + (long)(j + 1) * nx + i) - __ldg(a.v + k * plv + (long)j * nx + i);
+        const double dw = __ldg(a.w + kp * pl + (long)j * nx + i) - __ldg(a.w + c + i);
+        const double b = fma(du, idx, fma(dv, idy, dw * idz));
+        a.bs[c + i] = b;
+        reinterpret_cast<float*>(A + (il >> 1) * nz + k)[il & 1] = 0.5f * d2f_rn(b);  // 1/2 of the unpack
+      }
+    } else {
+      // rs = bs - (D G phi1) / (nx nz) with D G phi = idx2 (phi_E + phi_W) + idz2 (phi_U + phi_D)
+      //   + PA_j phi_S + PC_j phi_N - (2 idx2 + 2 idz2 + PA_j + PC_j) phi; a missing neighbour (the
+      //   Neumann x faces, the walls, where PA_0 = PC_{ny-1} = 0) takes the value phi itself.  Each
+      //   pair sum of two FP32 values is exact in FP64; the 1/(nx nz) is folded into the weights.
+      const double inv = a.inv_nxnz;
+      const double paj = __ldg(a.gc + GC_PA * (ny + 1) + j), pcj = __ldg(a.gc + GC_PC * (ny + 1) + j);
+      const double wx = a.idx2 * inv, wz = a.idz2 * inv, wa = paj * inv, wc = pcj * inv;
+      const double w0 = (2.0 * a.idx2 + 2.0 * a.idz2 + paj + pcj) * inv;
+      const float* __restrict__ f = a.phi1;
+      for (int q = threadIdx.x; q < TX * nz; q += blockDim.x) {
+        const int il = q % TX, k = q / TX, i = i0 + il;
+        const long row = k * pl + (long)j * nx, cc = row + i;
+        const float f0 = __ldg(f + cc);
+        float fe, fw;
+        if (a.bl) {
+          fe = (i + 1 < nx) ? __ldg(f + cc + 1) : f0;
+          fw = (i > 0) ? __ldg(f + cc - 1) : f0;
+        } else {
+          fe = __ldg(f + row + ((i + 1 == nx) ? 0 : i + 1));
+          fw = __ldg(f + row + ((i == 0) ? nx - 1 : i - 1));
+        }
+        const float fs = j > 0 ? __ldg(f + cc - nx) : f0;
+        const float fn = j + 1 < ny ? __ldg(f + cc + nx) : f0;
+        const int kp = (k + 1 == nz) ? 0 : k + 1, km = (k == 0) ? nz - 1 : k - 1;
+        const float fu = __ldg(f + kp * pl + (long)j * nx + i), fd = __ldg(f + km * pl + (long)j * nx + i);
+        const double sx = f2d(fe) + f2d(fw), sz = f2d(fu) + f2d(fd);
+        double r = fma(w0, f2d(f0), __ldg(a.bs + cc));
+        r = fma(-wx, sx, r);
+        r = fma(-wz, sz, r);
+        r = fma(-wa, f2d(fs), r);
+        r = fma(-wc, f2d(fn), r);
+        reinterpret_cast<float*>(A + (il >> 1) * nz + k)[il & 1] = 0.5f * d2f_rn(r);
+      }
+    }
+    __syncthreads();
+    const float2* R = stockham<-1, float2>(A, B, nz, a.pz, nseq, a.twz);
+    const int nh = (nz >> 1) + 1;
+    for (int q = threadIdx.x; q < nh * TX; q += blockDim.x) {
+      const int il = q % TX, m = q / TX, c = il >> 1;
+      const float2 zm = R[c * nz + m];
+      const float2 zn = R[c * nz + (m == 0 ? 0 : nz - m)];
+      const float2 X = (il & 1) == 0 ? make_float2(zm.x + zn.x, zm.y - zn.y) : make_float2(zm.y + zn.y, zn.x - zm.x);
+      a.spec[((long)m * ny + j) * nx + i0 + il] = X;
+    }
+  }
+};
+
+// y tridiagonal per (kx, kz) of the mixed form: complex64 spectrum, FP64 arithmetic and factors
+// (the same recurrences as TdmaK)
+struct TdmaMK {
+  struct Args {
+    float2* spec;
+    const double2* fac;
+    const double* gc;
+    int nx, ny, nzh;
+  };
+  static constexpr int kThreads = 128;
+  static constexpr int kMinBlocks = 8;
+  static __device__ __forceinline__ void run(const Args& a, const dim3 bid_, const dim3) {
+    const int nx = a.nx, ny = a.ny;
+    const int t = bid_.x * blockDim.x + threadIdx.x;
+    const int i = t >> 1, part = t & 1;
+    const int kz = bid_.y;
+    if (i >= nx) return;
+    const long base = (long)kz * ny * nx + i;
+    float* d = reinterpret_cast<float*>(a.spec + base) + part;
+    const long sd = 2L * nx;
+    const double* finv = reinterpret_cast<const double*>(a.fac) + base;
+    const double* fcp = finv + (long)a.nzh * ny * nx;
+    const double* pa = a.gc + GC_PA * (ny + 1);
+    const bool gauge = (i == 0 && kz == 0);
+    constexpr int U = 4;
+    double prev = 0.0;
+    for (int j0 = 0; j0 < ny; j0 += U) {
+      double dv[U], fx[U], av[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (j0 + u < ny) {
+          dv[u] = f2d(d[(long)(j0 + u) * sd]);
+          fx[u] = __ldg(finv + (long)(j0 + u) * nx);
+          av[u] = __ldg(pa + j0 + u);
+        }
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (j0 + u < ny) {
+          const double dj = (gauge && j0 + u == 0) ? 0.0 : dv[u];
+          prev = fma(-av[u], prev, dj) * fx[u];
+          d[(long)(j0 + u) * sd] = d2f_rn(prev);
+        }
+    }
+    double next = prev;
+    for (int j1 = ny - 2; j1 >= 0; j1 -= U) {
+      double dv[U], cv[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (j1 - u >= 0) {
+          dv[u] = f2d(d[(long)(j1 - u) * sd]);
+          cv[u] = __ldg(fcp + (long)(j1 - u) * nx);
+        }
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (j1 - u >= 0) {
+          next = fma(-cv[u], next, dv[u]);
+          d[(long)(j1 - u) * sd] = d2f_rn(next);
+        }
+    }
+  }
+};
+
+// inverse z transform of the mixed form (complex-to-real, FP32): pass 1 stores phi1 (FP32);
+// pass 2 (ACC) adds its result to phi1 in FP64 and writes phi
+template <bool ACC>
+struct IfftzMK {
+  struct Args {
+    const float2* spec;
+    const float2* twz;
+    float* phi1;
+    double* phi;
+    int nx, ny, nz, pz, TX;
+  };
+  static constexpr int kThreads = 256;
+  static constexpr int kMinBlocks = 4;
+  static __device__ __forceinline__ void run(const Args& a, const dim3 bid_, const dim3) {
+    const int nx = a.nx, ny = a.ny, nz = a.nz, TX = a.TX;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int nseq = TX >> 1;
+    float2* A = reinterpret_cast<float2*>(smem_raw);
+    float2* B = A + nseq * nz;
+    const int i0 = bid_.x * TX;
+    const int j = bid_.y;
+    const int nh = nz >> 1;
+    for (int q = threadIdx.x; q < nseq * (nh + 1); q += blockDim.x) {
+      const int c = q % nseq, m = q / nseq;
+      const long o = ((long)m * ny + j) * nx + i0 + 2 * c;
+      float2 xa = a.spec[o], xb = a.spec[o + 1];
+      if (m == 0 || m == nh) {
+        xa.y = 0.0f;
+        xb.y = 0.0f;
+      }
+      A[c * nz + m] = make_float2(xa.x - xb.y, xa.y + xb.x);
+      if (m > 0 && m < nh) A[c * nz + nz - m] = make_float2(xa.x + xb.y, xb.x - xa.y);
+    }
+    __syncthreads();
+    const float2* R = stockham<1, float2>(A, B, nz, a.pz, nseq, a.twz);
+    const long pl = (long)ny * nx;
+    for (int q = threadIdx.x; q < TX * nz; q += blockDim.x) {
+      const int il = q % TX, k = q / TX;
+      const float2 t = R[(il >> 1) * nz + k];
+      const float val = (il & 1) ? t.y : t.x;
+      const long cc = k * pl + (long)j * nx + i0 + il;
+      if (ACC) a.phi[cc] = f2d(a.phi1[cc]) + f2d(val);
+      else a.phi1[cc] = val;
+    }
+  }
+};
+
+// ------------------------------------------------------------------------------------------
 // projection u = u* - s G phi; p += phi (if update_p).  One thread per (i, j) of a z-plane,
 // j = 0..ny.
 // ------------------------------------------------------------------------------------------
@@ -533,56 +762,59 @@ struct ProjectK {
 // w_l = exp(-i pi l / (2N)).  Inverse (unnormalised, N times the DCT-III inverse):
 // V_l = conj(w_l) (X_l - i X_{N-l}) (X_N = 0), v = IFFT(V), x_{2n} = v_n, x_{2n+1} = v_{N-1-n}.
 // ------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) dctx_fwd_kernel(double2* __restrict__ spec, const double2* __restrict__ twx,
-                                                       const double2* __restrict__ twd, long nrows, int nx, int px,
+template <typename C>
+__global__ void __launch_bounds__(256) dctx_fwd_kernel(C* __restrict__ spec, const C* __restrict__ twx,
+                                                       const C* __restrict__ twd, long nrows, int nx, int px,
                                                        int R) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  double2* A = reinterpret_cast<double2*>(smem_raw);
-  double2* B = A + R * nx;
+  C* A = reinterpret_cast<C*>(smem_raw);
+  C* B = A + R * nx;
   const long row0 = (long)blockIdx.x * R;
   const int nr = (int)min((long)R, nrows - row0);
-  double2* g = spec + row0 * nx;
+  C* g = spec + row0 * nx;
   for (int q = threadIdx.x; q < R * nx; q += blockDim.x) {
     const int rr = q / nx, i = q - rr * nx;
     const int dst = (i & 1) ? nx - 1 - (i >> 1) : (i >> 1);
-    A[rr * nx + dst] = rr < nr ? g[q] : make_double2(0.0, 0.0);
+    A[rr * nx + dst] = rr < nr ? g[q] : Cplx<C>::mk(0, 0);
   }
   __syncthreads();
-  const double2* V = stockham<-1>(A, B, nx, px, R, twx);
+  const C* V = stockham<-1, C>(A, B, nx, px, R, twx);
   for (int q = threadIdx.x; q < nr * nx; q += blockDim.x) {
     const int rr = q / nx, l = q - rr * nx;
-    const double2 vl = V[rr * nx + l];
-    const double2 vn = V[rr * nx + (l == 0 ? 0 : nx - l)];
-    const double2 w = __ldg(twd + l);
-    const double ax = 0.5 * (vl.x + vn.x), ay = 0.5 * (vl.y - vn.y);
-    const double bx = 0.5 * (vl.y + vn.y), by = 0.5 * (vn.x - vl.x);
-    g[q] = make_double2(fma(w.x, ax, -w.y * ay), fma(w.x, bx, -w.y * by));
+    const C vl = V[rr * nx + l];
+    const C vn = V[rr * nx + (l == 0 ? 0 : nx - l)];
+    const C w = __ldg(twd + l);
+    using R_ = typename Cplx<C>::R;
+    const R_ ax = (R_)0.5 * (vl.x + vn.x), ay = (R_)0.5 * (vl.y - vn.y);
+    const R_ bx = (R_)0.5 * (vl.y + vn.y), by = (R_)0.5 * (vn.x - vl.x);
+    g[q] = Cplx<C>::mk(fmaT(w.x, ax, -w.y * ay), fmaT(w.x, bx, -w.y * by));
   }
 }
 
-__global__ void __launch_bounds__(256) dctx_inv_kernel(double2* __restrict__ spec, const double2* __restrict__ twx,
-                                                       const double2* __restrict__ twd, long nrows, int nx, int px,
+template <typename C>
+__global__ void __launch_bounds__(256) dctx_inv_kernel(C* __restrict__ spec, const C* __restrict__ twx,
+                                                       const C* __restrict__ twd, long nrows, int nx, int px,
                                                        int R) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  double2* A = reinterpret_cast<double2*>(smem_raw);
-  double2* B = A + R * nx;
+  C* A = reinterpret_cast<C*>(smem_raw);
+  C* B = A + R * nx;
   const long row0 = (long)blockIdx.x * R;
   const int nr = (int)min((long)R, nrows - row0);
-  double2* g = spec + row0 * nx;
+  C* g = spec + row0 * nx;
   for (int q = threadIdx.x; q < R * nx; q += blockDim.x) {
     const int rr = q / nx, l = q - rr * nx;
-    double2 v = make_double2(0.0, 0.0);
+    C v = Cplx<C>::mk(0, 0);
     if (rr < nr) {
-      const double2 xl = g[q];
-      const double2 xn = l == 0 ? make_double2(0.0, 0.0) : g[rr * nx + nx - l];
-      const double2 w = __ldg(twd + l);
-      const double ax = xl.x + xn.y, ay = xl.y - xn.x;  // X_l - i X_{N-l}
-      v = make_double2(fma(w.x, ax, w.y * ay), fma(w.x, ay, -w.y * ax));  // conj(w) (..)
+      const C xl = g[q];
+      const C xn = l == 0 ? Cplx<C>::mk(0, 0) : g[rr * nx + nx - l];
+      const C w = __ldg(twd + l);
+      const auto ax = xl.x + xn.y, ay = xl.y - xn.x;  // X_l - i X_{N-l}
+      v = Cplx<C>::mk(fmaT(w.x, ax, w.y * ay), fmaT(w.x, ay, -w.y * ax));  // conj(w) (..)
     }
     A[q] = v;
   }
   __syncthreads();
-  const double2* X = stockham<1>(A, B, nx, px, R, twx);
+  const C* X = stockham<1, C>(A, B, nx, px, R, twx);
   for (int q = threadIdx.x; q < nr * nx; q += blockDim.x) {
     const int rr = q / nx, i = q - rr * nx;
     const int src = (i & 1) ? nx - 1 - (i >> 1) : (i >> 1);
@@ -791,8 +1023,8 @@ cudaError_t poisson_set_attributes() {
   set_smem_limit<IfftzK>(200 * 1024);
   set_smem_limit<FftxK<-1>>(200 * 1024);
   set_smem_limit<FftxK<1>>(200 * 1024);
-  cudaFuncSetAttribute(dctx_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  cudaFuncSetAttribute(dctx_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaFuncSetAttribute(dctx_fwd_kernel<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaFuncSetAttribute(dctx_inv_kernel<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   return cudaGetLastError();
 }
 
@@ -843,17 +1075,85 @@ PoisShape pois_shape(const ns_ctx* c) {
   q.bx = (unsigned)((q.nrows + q.R - 1) / q.R);
   return q;
 }
+// the mixed form's FP32 pipeline: spectrum (complex64) over the dead increments r_u, r_v; phi1 in
+// r_w; the FP64 right-hand side bs in the FP64 spectrum block
+float2* sp32(const ns_ctx* c) { return reinterpret_cast<float2*>(c->ru); }
+float* phi1(const ns_ctx* c) { return reinterpret_cast<float*>(c->rw); }
+double* bs64(const ns_ctx* c) { return reinterpret_cast<double*>(c->spec); }
+
+template <bool RES>
+cudaError_t emit_divzm(LaunchSink& s, int k) {
+  ns_ctx* c = s.c;
+  const PoisShape q = pois_shape(c);
+  typename DivzMK<RES>::Args a;
+  a.u = c->f.u;
+  a.v = c->f.v;
+  a.w = c->f.w;
+  a.gc = c->gc;
+  a.twz = c->twz32;
+  a.spec = sp32(c);
+  a.bs = bs64(c);
+  a.phi1 = phi1(c);
+  a.nx = q.nx;
+  a.ny = q.ny;
+  a.nz = q.nz;
+  a.pz = q.pz;
+  a.TX = q.TX;
+  a.bl = c->bl;
+  a.idx = 1.0 / c->dx;
+  a.idz = 1.0 / c->dz;
+  a.idx2 = 1.0 / (c->dx * c->dx);
+  a.idz2 = 1.0 / (c->dz * c->dz);
+  a.inv_nxnz = 1.0 / ((double)q.nx * q.nz);
+  a.sk = c->stepk + stepk_index(k);
+  a.u_out = c->bl ? c->f.u_out : nullptr;
+  return emit<DivzMK<RES>>(s, a, dim3(q.nx / q.TX, q.ny), dim3(256), q.smz / 2);
+}
+
+cudaError_t emit_xm(LaunchSink& s, bool fwd) {
+  ns_ctx* c = s.c;
+  const PoisShape q = pois_shape(c);
+  if (c->bl) {
+    if (fwd)
+      dctx_fwd_kernel<float2><<<q.bx, 256, q.smx / 2, c->launch>>>(sp32(c), c->twx32, c->twd32, q.nrows, q.nx, q.px, q.R);
+    else
+      dctx_inv_kernel<float2><<<q.bx, 256, q.smx / 2, c->launch>>>(sp32(c), c->twx32, c->twd32, q.nrows, q.nx, q.px, q.R);
+    return cudaGetLastError();
+  }
+  if (fwd)
+    return emit<FftxK<-1, float2>>(s, FftxK<-1, float2>::make(sp32(c), c->twx32, q.nrows, q.nx, q.px, q.R, 1.0f),
+                                   dim3(q.bx), dim3(256), q.smx / 2);
+  return emit<FftxK<1, float2>>(s, FftxK<1, float2>::make(sp32(c), c->twx32, q.nrows, q.nx, q.px, q.R, 1.0f),
+                                dim3(q.bx), dim3(256), q.smx / 2);
+}
+
+cudaError_t emit_tdmam(LaunchSink& s) {
+  ns_ctx* c = s.c;
+  const PoisShape q = pois_shape(c);
+  return emit<TdmaMK>(s, TdmaMK::Args{sp32(c), c->pois, c->gc, q.nx, q.ny, c->nzh}, dim3((2 * q.nx + 127) / 128, c->nzh),
+                      dim3(128), 0);
+}
+
+template <bool ACC>
+cudaError_t emit_ifftzm(LaunchSink& s) {
+  ns_ctx* c = s.c;
+  const PoisShape q = pois_shape(c);
+  return emit<IfftzMK<ACC>>(s, typename IfftzMK<ACC>::Args{sp32(c), c->twz32, phi1(c), c->phi, q.nx, q.ny, q.nz, q.pz, q.TX},
+                            dim3(q.nx / q.TX, q.ny), dim3(256), q.smz / 2);
+}
+
 void single_kernel_dct_fwd(ns_ctx* c, unsigned bx, size_t smx, long nrows, int nx, int px, int R) {
-  dctx_fwd_kernel<<<bx, 256, smx, c->launch>>>(c->spec, c->twx, c->twd, nrows, nx, px, R);
+  dctx_fwd_kernel<double2><<<bx, 256, smx, c->launch>>>(c->spec, c->twx, c->twd, nrows, nx, px, R);
 }
 void single_kernel_dct_inv(ns_ctx* c, unsigned bx, size_t smx, long nrows, int nx, int px, int R) {
-  dctx_inv_kernel<<<bx, 256, smx, c->launch>>>(c->spec, c->twx, c->twd, nrows, nx, px, R);
+  dctx_inv_kernel<double2><<<bx, 256, smx, c->launch>>>(c->spec, c->twx, c->twd, nrows, nx, px, R);
 }
 }  // namespace
 
 // A5: divergence of u* scaled by 1/(alpha_k dt) (1 if k < 0) + forward real FFT along z
 cudaError_t stage_pois_divz(LaunchSink& s, int k) {
   ns_ctx* c = s.c;
+  if (c->pois32) return emit_divzm<false>(s, k);
   const PoisShape q = pois_shape(c);
   // 1/(alpha_k dt) of the right-hand side and 1/(nx nz) of the inverse transforms, applied once
   // (StepK::pscale)
@@ -866,6 +1166,7 @@ cudaError_t stage_pois_divz(LaunchSink& s, int k) {
 // A6: forward complex FFT along x (periodic) or DCT-II (inflow / outflow; single instance only)
 cudaError_t stage_pois_x_fwd(LaunchSink& s, int) {
   ns_ctx* c = s.c;
+  if (c->pois32) return emit_xm(s, true);
   const PoisShape q = pois_shape(c);
   if (c->bl) {
     single_kernel_dct_fwd(c, q.bx, q.smx, q.nrows, q.nx, q.px, q.R);
@@ -878,6 +1179,7 @@ cudaError_t stage_pois_x_fwd(LaunchSink& s, int) {
 // A7: complex tridiagonal solve along y per (kx, kz)
 cudaError_t stage_pois_tdma(LaunchSink& s, int) {
   ns_ctx* c = s.c;
+  if (c->pois32) return emit_tdmam(s);
   const PoisShape q = pois_shape(c);
   return emit<TdmaK>(s, TdmaK::make(c->spec, c->pois, c->gc, q.nx, q.ny, c->nzh), dim3((2 * q.nx + 127) / 128, c->nzh),
                      dim3(128), 0);
@@ -886,6 +1188,7 @@ cudaError_t stage_pois_tdma(LaunchSink& s, int) {
 // A8: inverse complex FFT along x (the 1/(nx nz) was applied to the right-hand side)
 cudaError_t stage_pois_x_inv(LaunchSink& s, int) {
   ns_ctx* c = s.c;
+  if (c->pois32) return emit_xm(s, false);
   const PoisShape q = pois_shape(c);
   if (c->bl) {
     single_kernel_dct_inv(c, q.bx, q.smx, q.nrows, q.nx, q.px, q.R);
@@ -898,9 +1201,20 @@ cudaError_t stage_pois_x_inv(LaunchSink& s, int) {
 // A9: inverse real FFT along z -> phi
 cudaError_t stage_pois_ifftz(LaunchSink& s, int) {
   ns_ctx* c = s.c;
+  if (c->pois32) return emit_ifftzm<false>(s);
   const PoisShape q = pois_shape(c);
   return emit<IfftzK>(s, IfftzK::make(c->spec, c->twz, c->phi, q.nx, q.ny, q.nz, q.pz, q.TX, 1.0),
                       dim3(q.nx / q.TX, q.ny), dim3(256), q.smz);
+}
+
+// A9b (mixed form only): the FP64 residual of phi1 and the second FP32 solve, phi = phi1 + phi2
+cudaError_t stage_pois_refine(LaunchSink& s, int k) {
+  if (!s.c->pois32) return cudaSuccess;
+  cudaError_t e;
+  if ((e = emit_divzm<true>(s, k)) != cudaSuccess || (e = emit_xm(s, true)) != cudaSuccess ||
+      (e = emit_tdmam(s)) != cudaSuccess || (e = emit_xm(s, false)) != cudaSuccess)
+    return e;
+  return emit_ifftzm<true>(s);
 }
 
 template <bool Dyn, bool KM>
@@ -934,6 +1248,7 @@ NS_SINGLE_LAUNCH(launch_pois_fftx_fwd, stage_pois_x_fwd)
 NS_SINGLE_LAUNCH(launch_pois_tdma, stage_pois_tdma)
 NS_SINGLE_LAUNCH(launch_pois_fftx_inv, stage_pois_x_inv)
 NS_SINGLE_LAUNCH(launch_pois_ifftz, stage_pois_ifftz)
+NS_SINGLE_LAUNCH(launch_pois_refine, stage_pois_refine)
 NS_SINGLE_LAUNCH(launch_project, stage_project)
 #undef NS_SINGLE_LAUNCH
 
@@ -943,7 +1258,8 @@ cudaError_t launch_poisson(ns_ctx* c, int k) {
   if ((e = launch_pois_fftx_fwd(c, k)) != cudaSuccess) return e;
   if ((e = launch_pois_tdma(c, k)) != cudaSuccess) return e;
   if ((e = launch_pois_fftx_inv(c, k)) != cudaSuccess) return e;
-  return launch_pois_ifftz(c, k);
+  if ((e = launch_pois_ifftz(c, k)) != cudaSuccess) return e;
+  return launch_pois_refine(c, k);
 }
 
 cudaError_t launch_outflow(ns_ctx* c, int k) {

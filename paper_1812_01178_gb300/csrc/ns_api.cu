@@ -101,6 +101,9 @@ ns_layout make_layout(const ns_config* c) {
   sz[LB_RCY] = recycle_block_doubles((int)ny) * 8;
   sz[LB_STEPK] = NS_STEPK * sizeof(StepK);
   sz[LB_PTAB] = 9 * al256(line_table_floats(c) * 4);
+  sz[LB_TW32] = c->precision == NS_MIXED ? al256(fft_twiddle_doubles((int)nz) * 4) + al256(fft_twiddle_doubles((int)nx) * 4) +
+                                               al256(nx * 8)
+                                         : 0;
   sz[LB_DT] = al256(sizeof(DtCtl)) + 8 * dt_scratch_doubles((int)nz, x_table_elems(c), line_table_floats(c));
   size_t o = 0;
   for (int b = 0; b < LB_COUNT; ++b) {
@@ -167,6 +170,7 @@ const Stage STAGES[] = {
     {"poisson_tdma_y", launch_pois_tdma},     // A7
     {"poisson_x_inv", launch_pois_fftx_inv},  // A8
     {"poisson_ifftz", launch_pois_ifftz},     // A9
+    {"poisson_refine", launch_pois_refine},   // A5-A9 again on the FP64 residual (mixed form only)
     {"project", launch_project},              // A10
 };
 const int NSTAGES = (int)(sizeof(STAGES) / sizeof(STAGES[0]));
@@ -347,6 +351,13 @@ ns_status ns_init(ns_ctx** out, const ns_config* cfg, const ns_fields* fields, v
     for (int q = 0; q < 3; ++q)
       c->ptab[k][q] = base + c->lay.off[LB_PTAB] + (3 * k + q) * al256(line_table_floats(cfg) * 4);
   c->twd = (double2*)(base + c->lay.off[LB_TWD]);
+  c->pois32 = cfg->precision == NS_MIXED;
+  if (c->pois32) {
+    char* t32 = base + c->lay.off[LB_TW32];
+    c->twz32 = (float2*)t32;
+    c->twx32 = (float2*)(t32 + al256(fft_twiddle_doubles(nz) * 4));
+    c->twd32 = (float2*)(t32 + al256(fft_twiddle_doubles(nz) * 4) + al256(fft_twiddle_doubles(nx) * 4));
+  }
   double* lamz_d = (double*)(base + c->lay.off[LB_LAMZ]);
 
   // ---------------- grid coefficients (Sec. 2.1 / 2.2 readings)
@@ -434,6 +445,13 @@ ns_status ns_init(ns_ctx** out, const ns_config* cfg, const ns_fields* fields, v
       td[2 * q + 1] = -std::sin(PI * q / (2.0 * nx));
     }
     if (upload_d(c, c->twd, td) != cudaSuccess) st = NS_ERR_CUDA;
+    if (c->pois32) {  // the same tables rounded to float for the FP32 transforms of the mixed form
+      const std::vector<float> fz(tw.begin(), tw.end()), fx(tx.begin(), tx.end()), fd(td.begin(), td.end());
+      if (upload_raw(c, c->twz32, fz.data(), fz.size() * 4) != cudaSuccess ||
+          upload_raw(c, c->twx32, fx.data(), fx.size() * 4) != cudaSuccess ||
+          upload_raw(c, c->twd32, fd.data(), fd.size() * 4) != cudaSuccess)
+        st = NS_ERR_CUDA;
+    }
     for (int q = 0; q < c->nzh; ++q) lz[q] = (2.0 / (c->dz * c->dz)) * (1.0 - std::cos(2.0 * PI * q / nz));
     if (upload_d(c, lamx_d, lx) != cudaSuccess) st = NS_ERR_CUDA;
     if (upload_d(c, lamz_d, lz) != cudaSuccess) st = NS_ERR_CUDA;
@@ -650,6 +668,7 @@ ns_status ns_step_cfl(ns_ctx* c, int nsteps, double cfl, double* dts) {
 // Stages that launch nothing in this configuration (the boundary-plane stages of periodic x).
 bool stage_idle(const ns_ctx* c, int q) {
   if (STAGES[q].fn == launch_recycle) return !c->cfg.recycle_i;
+  if (STAGES[q].fn == launch_pois_refine) return !c->pois32;
   return !c->bl && (STAGES[q].fn == launch_outflow || STAGES[q].fn == launch_flux_correct);
 }
 

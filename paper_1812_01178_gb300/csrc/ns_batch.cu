@@ -26,11 +26,11 @@ struct PlannedLaunch {
 typedef cudaError_t (*StageFn)(LaunchSink&, int);
 const StageFn BATCH_STAGES[] = {stage_rhs,       stage_adi_x,      stage_adi_y,     stage_adi_z,
                                 stage_pois_divz, stage_pois_x_fwd, stage_pois_tdma, stage_pois_x_inv,
-                                stage_pois_ifftz, stage_project};
+                                stage_pois_ifftz, stage_pois_refine, stage_project};
 const char* BATCH_STAGE_NAMES[] = {"rhs",           "adi_x",         "adi_y",          "adi_z",
                                    "poisson_div_fftz", "poisson_x_fwd", "poisson_tdma_y", "poisson_x_inv",
-                                   "poisson_ifftz", "project"};
-constexpr int NBATCH_STAGES = 10;
+                                   "poisson_ifftz", "poisson_refine", "project"};
+constexpr int NBATCH_STAGES = 11;
 constexpr size_t kArenaBase = 1 << 20;
 constexpr size_t kArenaPerInstance = 64 << 10;
 

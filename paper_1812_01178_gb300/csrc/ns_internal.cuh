@@ -158,7 +158,7 @@ struct ns_layout {
 
 enum {
   LB_RU = 0, LB_RV, LB_RW, LB_NU, LB_NV, LB_NW, LB_PHI, LB_SPEC, LB_POIS, LB_GC, LB_XTAB, LB_YTAB,
-  LB_ZTAB, LB_TWZ, LB_TWX, LB_LAMX, LB_LAMZ, LB_RTAB, LB_DOUT, LB_TWD, LB_RCY, LB_STEPK, LB_PTAB, LB_DT, LB_COUNT
+  LB_ZTAB, LB_TWZ, LB_TWX, LB_LAMX, LB_LAMZ, LB_RTAB, LB_DOUT, LB_TWD, LB_RCY, LB_STEPK, LB_PTAB, LB_TW32, LB_DT, LB_COUNT
 };
 
 // dt-dependent constants of one RK3 sub-step (entries 0..2) and of the projection of an initial
@@ -230,6 +230,10 @@ struct ns_ctx {
   int bl;                   // inflow / convective outflow in x
   double* dout[3];          // outflow-plane increments of the current sub-step (u, v, w)
   double2* twd;             // exp(-i pi l / (2 nx)), l < nx: post-twiddles of the x cosine transform
+  // the mixed form's Poisson solve: FP32 transforms (twiddles rounded to float) and one FP64
+  // refinement (k_poisson.cu); off for FP64 contexts
+  bool pois32 = false;
+  float2 *twz32 = nullptr, *twx32 = nullptr, *twd32 = nullptr;
   double* flux;             // [0]: inflow flux, [1]: last outflow correction (diagnostics)
   unsigned long long* rate; // bits of the convective rate of ns_convective_rate (in the flux block)
   std::vector<double> gc_h; // host copy of the grid coefficients (tables are rebuilt when dt changes)
@@ -443,6 +447,7 @@ cudaError_t stage_pois_x_fwd(LaunchSink& s, int k);
 cudaError_t stage_pois_tdma(LaunchSink& s, int k);
 cudaError_t stage_pois_x_inv(LaunchSink& s, int k);
 cudaError_t stage_pois_ifftz(LaunchSink& s, int k);
+cudaError_t stage_pois_refine(LaunchSink& s, int k);  // mixed form: FP64 residual, second FP32 solve
 cudaError_t stage_project(LaunchSink& s, int k);
 
 // ... and their single-instance launchers (enqueue on ctx->launch; return the launch error).
@@ -458,6 +463,7 @@ cudaError_t launch_pois_fftx_fwd(ns_ctx* c, int k);   // x FFT (periodic) or DCT
 cudaError_t launch_pois_tdma(ns_ctx* c, int k);
 cudaError_t launch_pois_fftx_inv(ns_ctx* c, int k);
 cudaError_t launch_pois_ifftz(ns_ctx* c, int k);
+cudaError_t launch_pois_refine(ns_ctx* c, int k);
 cudaError_t launch_project(ns_ctx* c, int k);
 cudaError_t launch_outflow(ns_ctx* c, int k);        // convective outflow update + increments
 cudaError_t launch_flux_correct(ns_ctx* c, int k);   // outflow volume flux := inflow flux
