@@ -28,6 +28,16 @@ template <> struct Cplx<float2> {
 };
 __device__ __forceinline__ double fmaT(double a, double b, double c) { return fma(a, b, c); }
 __device__ __forceinline__ float fmaT(float a, float b, float c) { return fmaf(a, b, c); }
+// error-free transformations (Knuth's TwoSum; TwoProd by one FMA): s + e = a + b, p + e = a b
+__device__ __forceinline__ void ff_two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ __forceinline__ void ff_two_prod(float a, float b, float& p, float& e) {
+  p = __fmul_rn(a, b);
+  e = __fmaf_rn(a, b, -p);
+}
 template <typename C>
 __device__ __forceinline__ C cadd(C a, C b) { return Cplx<C>::mk(a.x + b.x, a.y + b.y); }
 template <typename C>
@@ -309,6 +319,79 @@ struct FftxK {
   }
 };
 
+// The forward and backward sweeps of the y system of one (kx, kz) line (one of its real and
+// imaginary parts), rows d[j * sd], with the factor planes finv (1/pivot) and fcp (c/pivot) and the
+// sub-diagonal pa; T is the storage type of the spectrum (double, or float in the mixed form; the
+// arithmetic is FP64).  The loads of the next U rows are issued before the current U rows are
+// computed and stored (other rows, so no hazard), and their latency overlaps the recurrence.
+__device__ __forceinline__ double tdma_cv(double x) { return x; }
+__device__ __forceinline__ double tdma_cv(float x) { return f2d(x); }
+__device__ __forceinline__ void tdma_st(double* p, double x) { *p = x; }
+__device__ __forceinline__ void tdma_st(float* p, double x) { *p = d2f_rn(x); }
+
+template <typename T>
+__device__ __forceinline__ void tdma_line(T* d, long sd, const double* __restrict__ finv,
+                                          const double* __restrict__ fcp, const double* __restrict__ pa, int nx,
+                                          int ny, bool gauge) {
+  constexpr int U = 4;
+  // two register sets, A and B, take turns: no copies between them (a copy of a register whose
+  // load is in flight would wait for it)
+  // (the spectrum values stay in their storage type until used: a conversion right after the load
+  // would wait for it)
+  T Ad[U] = {}, Bd[U] = {};
+  double Af[U] = {}, Aa[U] = {}, Bf[U] = {}, Ba[U] = {};
+  auto load_f = [&](int j0, T* D, double* F, double* A) {
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (j0 + u < ny) {
+        D[u] = d[(long)(j0 + u) * sd];
+        F[u] = __ldg(finv + (long)(j0 + u) * nx);
+        A[u] = __ldg(pa + j0 + u);  // a_0 = 0
+      }
+  };
+  double prev = 0.0;
+  auto sweep_f = [&](int j0, const T* D, const double* F, const double* A) {
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (j0 + u < ny) {
+        const double dj = (gauge && j0 + u == 0) ? 0.0 : tdma_cv(D[u]);  // the gauge row phi_0 = 0
+        prev = fma(-A[u], prev, dj) * F[u];
+        tdma_st(d + (long)(j0 + u) * sd, prev);
+      }
+  };
+  load_f(0, Ad, Af, Aa);
+  for (int j0 = 0; j0 < ny; j0 += 2 * U) {
+    load_f(j0 + U, Bd, Bf, Ba);
+    sweep_f(j0, Ad, Af, Aa);
+    load_f(j0 + 2 * U, Ad, Af, Aa);
+    sweep_f(j0 + U, Bd, Bf, Ba);
+  }
+  double next = prev;
+  auto load_b = [&](int j1, T* D, double* C) {
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (j1 - u >= 0) {
+        D[u] = d[(long)(j1 - u) * sd];
+        C[u] = __ldg(fcp + (long)(j1 - u) * nx);
+      }
+  };
+  auto sweep_b = [&](int j1, const T* D, const double* C) {
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (j1 - u >= 0) {
+        next = fma(-C[u], next, tdma_cv(D[u]));
+        tdma_st(d + (long)(j1 - u) * sd, next);
+      }
+  };
+  load_b(ny - 2, Ad, Af);
+  for (int j1 = ny - 2; j1 >= 0; j1 -= 2 * U) {
+    load_b(j1 - U, Bd, Bf);
+    sweep_b(j1, Ad, Af);
+    load_b(j1 - 2 * U, Ad, Af);
+    sweep_b(j1 - U, Bd, Bf);
+  }
+}
+
 // ------------------------------------------------------------------------------------------
 // y tridiagonal per (kx, kz), two threads per line (real, imaginary part), factors 1/pivot and
 // c/pivot precomputed in two planes (each sweep reads only the one it uses).
@@ -323,7 +406,7 @@ struct TdmaK {
     int nzh;
   };
   static constexpr int kThreads = 128;
-  static constexpr int kMinBlocks = 8;  // nx*(nz/2+1) lines: occupancy is set by the line count, not registers
+  static constexpr int kMinBlocks = 4;  // nx*(nz/2+1) lines: occupancy is set by the line count, not registers
   static Args make(double2* spec, const double2* fac, const double* gc, int nx, int ny, int nzh) { return Args{spec, fac, gc, nx, ny, nzh}; }
   static __device__ __forceinline__ void run(const Args& a_, const dim3 bid_, const dim3 gdim_) {
     double2* __restrict__ spec = a_.spec;
@@ -346,42 +429,7 @@ struct TdmaK {
   const double* fcp = finv + (long)a_.nzh * ny * nx;
   const double* pa = gc + GC_PA * (ny + 1);
   // the (0,0) mode's row 0 is the gauge phi_0 = 0 (its factor row is 1, 0)
-  const bool gauge = (i == 0 && kz == 0);
-  constexpr int U = 4;
-  double prev = 0.0;
-  for (int j0 = 0; j0 < ny; j0 += U) {
-    double dv[U], fx[U], av[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u)
-      if (j0 + u < ny) {
-        dv[u] = d[(long)(j0 + u) * sd];
-        fx[u] = __ldg(finv + (long)(j0 + u) * nx);
-        av[u] = __ldg(pa + j0 + u);  // a_0 = 0
-      }
-#pragma unroll
-    for (int u = 0; u < U; ++u)
-      if (j0 + u < ny) {
-        const double dj = (gauge && j0 + u == 0) ? 0.0 : dv[u];
-        prev = fma(-av[u], prev, dj) * fx[u];
-        d[(long)(j0 + u) * sd] = prev;
-      }
-  }
-  double next = prev;
-  for (int j1 = ny - 2; j1 >= 0; j1 -= U) {
-    double dv[U], cv[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u)
-      if (j1 - u >= 0) {
-        dv[u] = d[(long)(j1 - u) * sd];
-        cv[u] = __ldg(fcp + (long)(j1 - u) * nx);
-      }
-#pragma unroll
-    for (int u = 0; u < U; ++u)
-      if (j1 - u >= 0) {
-        next = fma(-cv[u], next, dv[u]);
-        d[(long)(j1 - u) * sd] = next;
-      }
-  }
+  tdma_line(d, sd, finv, fcp, pa, nx, ny, i == 0 && kz == 0);
   }
 };
 
@@ -508,12 +556,23 @@ struct DivzMK {
     } else {
       // rs = bs - (D G phi1) / (nx nz) with D G phi = idx2 (phi_E + phi_W) + idz2 (phi_U + phi_D)
       //   + PA_j phi_S + PC_j phi_N - (2 idx2 + 2 idz2 + PA_j + PC_j) phi; a missing neighbour (the
-      //   Neumann x faces, the walls, where PA_0 = PC_{ny-1} = 0) takes the value phi itself.  Each
-      //   pair sum of two FP32 values is exact in FP64; the 1/(nx nz) is folded into the weights.
+      //   Neumann x faces, the walls, where PA_0 = PC_{ny-1} = 0) takes the value phi itself, and
+      //   the 1/(nx nz) is folded into the weights.  phi1 is FP32, so the stencil is summed in
+      //   float-float arithmetic on the FP32 pipe (pair sums exact by TwoSum, products exact by
+      //   TwoProd, weights split into two floats, error terms gathered in one float); only the
+      //   final bs + S + C is FP64.  Its error is about 2^-46 of the largest stencil term.
       const double inv = a.inv_nxnz;
       const double paj = __ldg(a.gc + GC_PA * (ny + 1) + j), pcj = __ldg(a.gc + GC_PC * (ny + 1) + j);
-      const double wx = a.idx2 * inv, wz = a.idz2 * inv, wa = paj * inv, wc = pcj * inv;
-      const double w0 = (2.0 * a.idx2 + 2.0 * a.idz2 + paj + pcj) * inv;
+      float wh[5], wl[5];
+      {
+        const double w[5] = {(2.0 * a.idx2 + 2.0 * a.idz2 + paj + pcj) * inv, a.idx2 * inv, a.idz2 * inv,
+                             paj * inv, pcj * inv};
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+          wh[q] = d2f_rn(w[q]);
+          wl[q] = d2f_rn(w[q] - f2d(wh[q]));
+        }
+      }
       const float* __restrict__ f = a.phi1;
       for (int q = threadIdx.x; q < TX * nz; q += blockDim.x) {
         const int il = q % TX, k = q / TX, i = i0 + il;
@@ -531,12 +590,30 @@ struct DivzMK {
         const float fn = j + 1 < ny ? __ldg(f + cc + nx) : f0;
         const int kp = (k + 1 == nz) ? 0 : k + 1, km = (k == 0) ? nz - 1 : k - 1;
         const float fu = __ldg(f + kp * pl + (long)j * nx + i), fd = __ldg(f + km * pl + (long)j * nx + i);
-        const double sx = f2d(fe) + f2d(fw), sz = f2d(fu) + f2d(fd);
-        double r = fma(w0, f2d(f0), __ldg(a.bs + cc));
-        r = fma(-wx, sx, r);
-        r = fma(-wz, sz, r);
-        r = fma(-wa, f2d(fs), r);
-        r = fma(-wc, f2d(fn), r);
+        float sxh, sxl, szh, szl;
+        ff_two_sum(fe, fw, sxh, sxl);
+        ff_two_sum(fu, fd, szh, szl);
+        // S + C = w0 phi - wx sx - wz sz - wa phi_S - wc phi_N
+        float S, C, p, e, t;
+        ff_two_prod(wh[0], f0, S, C);
+        C = __fmaf_rn(wl[0], f0, C);
+        ff_two_prod(wh[1], sxh, p, e);
+        e = __fmaf_rn(wh[1], sxl, __fmaf_rn(wl[1], sxh, e));
+        ff_two_sum(S, -p, S, t);
+        C = __fsub_rn(__fadd_rn(C, t), e);
+        ff_two_prod(wh[2], szh, p, e);
+        e = __fmaf_rn(wh[2], szl, __fmaf_rn(wl[2], szh, e));
+        ff_two_sum(S, -p, S, t);
+        C = __fsub_rn(__fadd_rn(C, t), e);
+        ff_two_prod(wh[3], fs, p, e);
+        e = __fmaf_rn(wl[3], fs, e);
+        ff_two_sum(S, -p, S, t);
+        C = __fsub_rn(__fadd_rn(C, t), e);
+        ff_two_prod(wh[4], fn, p, e);
+        e = __fmaf_rn(wl[4], fn, e);
+        ff_two_sum(S, -p, S, t);
+        C = __fsub_rn(__fadd_rn(C, t), e);
+        const double r = (__ldg(a.bs + cc) + f2d(S)) + f2d(C);
         reinterpret_cast<float*>(A + (il >> 1) * nz + k)[il & 1] = 0.5f * d2f_rn(r);
       }
     }
@@ -576,42 +653,7 @@ struct TdmaMK {
     const double* finv = reinterpret_cast<const double*>(a.fac) + base;
     const double* fcp = finv + (long)a.nzh * ny * nx;
     const double* pa = a.gc + GC_PA * (ny + 1);
-    const bool gauge = (i == 0 && kz == 0);
-    constexpr int U = 4;
-    double prev = 0.0;
-    for (int j0 = 0; j0 < ny; j0 += U) {
-      double dv[U], fx[U], av[U];
-#pragma unroll
-      for (int u = 0; u < U; ++u)
-        if (j0 + u < ny) {
-          dv[u] = f2d(d[(long)(j0 + u) * sd]);
-          fx[u] = __ldg(finv + (long)(j0 + u) * nx);
-          av[u] = __ldg(pa + j0 + u);
-        }
-#pragma unroll
-      for (int u = 0; u < U; ++u)
-        if (j0 + u < ny) {
-          const double dj = (gauge && j0 + u == 0) ? 0.0 : dv[u];
-          prev = fma(-av[u], prev, dj) * fx[u];
-          d[(long)(j0 + u) * sd] = d2f_rn(prev);
-        }
-    }
-    double next = prev;
-    for (int j1 = ny - 2; j1 >= 0; j1 -= U) {
-      double dv[U], cv[U];
-#pragma unroll
-      for (int u = 0; u < U; ++u)
-        if (j1 - u >= 0) {
-          dv[u] = f2d(d[(long)(j1 - u) * sd]);
-          cv[u] = __ldg(fcp + (long)(j1 - u) * nx);
-        }
-#pragma unroll
-      for (int u = 0; u < U; ++u)
-        if (j1 - u >= 0) {
-          next = fma(-cv[u], next, dv[u]);
-          d[(long)(j1 - u) * sd] = d2f_rn(next);
-        }
-    }
+    tdma_line(d, sd, finv, fcp, pa, nx, ny, i == 0 && kz == 0);
   }
 };
 
