@@ -231,6 +231,15 @@ struct RhsTile {
   T fuw[RT_Z + 1][RT_X + 1];                 // x = i0 .. i0+TX, z = k0 .. k0+TZ
 };
 
+// State values entering the FP32 tile: the hardware conversion (one instruction on the FP64
+// pipe, which the FP32 RHS leaves idle) instead of the integer-pipe d2f_rn (about a dozen
+// instructions on the issue-bound FP32 RHS).
+template <typename T>
+__device__ __forceinline__ T plane_cvt(double x) {
+  if constexpr (sizeof(T) == 4) return __double2float_rn(x);
+  else return x;
+}
+
 template <typename T, typename TR, bool Dyn>
 struct RhsTiledK {
   struct Args {
@@ -296,11 +305,11 @@ struct RhsTiledK {
         const long o = oc[r] + jo, q = ov[r] + jo;
         T vu = (T)0, vv = (T)0, vw = (T)0, vp = (T)0;
         if (jc) {
-          vu = from_double<T>(__ldg(a.u + o));
-          vw = from_double<T>(__ldg(a.w + o));
-          vp = from_double<T>(__ldg(a.p + o));
+          vu = plane_cvt<T>(__ldg(a.u + o));
+          vw = plane_cvt<T>(__ldg(a.w + o));
+          vp = plane_cvt<T>(__ldg(a.p + o));
         }
-        if (jv) vv = from_double<T>(__ldg(a.v + q));
+        if (jv) vv = plane_cvt<T>(__ldg(a.v + q));
         S.pl[0][j & 3][e] = vu;
         S.pl[1][j & 3][e] = vv;
         S.pl[2][j & 3][e] = vw;
