@@ -241,3 +241,30 @@ def test_invalid_dt_cfl_and_non_finite_fields_are_reported():
     s.step(1)  # still usable
     s.sync()
     s.close()
+
+
+def test_step_cfl_reports_rest_and_non_finite_fields():
+    """The device-side dt update cannot stop the graph it runs in: a rate that is zero (fluid at
+    rest) or non-finite keeps the previous dt for that step, and the call reports NS_ERR_STATE
+    with the step once its run of steps is done.  A valid field afterwards steps normally."""
+    case, g, u, v, w, p = _projected((16, 9, 8), 2)
+    L = B.lib()
+    s = B.Solver(case, 0.0 * u, 0.0 * v, 0.0 * w, p)
+    dts = (ctypes.c_double * 2)()
+    assert L.ns_step_cfl(s.ctx, 2, 0.5, dts) == B.NS_ERR_STATE
+    msg = L.ns_last_error(s.ctx).decode()
+    assert "rest" in msg and "step 0" in msg, msg
+    # step 0 kept the previous dt; the body force then set the fluid moving, so step 1 had a
+    # (tiny) rate and its own, large, dt
+    assert dts[0] == case.dt and dts[1] > case.dt
+    s.close()
+    s = B.Solver(case, u, v, w, p)
+    s.u[1, 2, 3] = float("nan")
+    assert L.ns_step_cfl(s.ctx, 1, 0.5, None) == B.NS_ERR_STATE
+    assert "non-finite" in L.ns_last_error(s.ctx).decode()
+    s.close()
+    s = B.Solver(case, u, v, w, p)
+    d = s.step_cfl(2, 0.5)
+    ref, rdts = O.step_cfl(g, dict(u=u, v=v, w=w, p=p), 0.5, case.re, case.fx, 2)
+    np.testing.assert_allclose(d, rdts, rtol=1e-10)
+    s.close()
