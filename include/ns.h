@@ -158,7 +158,11 @@ ns_status ns_adi_sweep(ns_ctx* ctx, int dir, int substep);
  * real FFT along z and complex FFT along x; one complex tridiagonal solve along y per (kx, kz)
  * with zero normal gradient at both y boundaries (the singular (0,0) mode is gauged by
  * phi_hat(j=0) = 0); inverse FFTs.  Writes phi into NS_BUF_PHI.  substep = -1 uses scale 1
- * (b = D u), for making an initial field divergence-free. */
+ * (b = D u), for making an initial field divergence-free.
+ * NS_MIXED: b is formed in FP64 and kept (in NS_BUF_SPEC), the transforms run in FP32 on a
+ * complex64 spectrum held over NS_BUF_RU/RV (phi1 in NS_BUF_RW: the three r buffers are scratch of
+ * the solve), the y solves keep FP64 arithmetic, and one refinement on the FP64 residual
+ * b - D G phi1 gives phi = phi1 + phi2 (FP64) at the accuracy of the FP64 solve. */
 ns_status ns_poisson_solve(ns_ctx* ctx, int substep);
 
 /* Projection of sub-step `substep` (Sec. 2.2): u = u* - alpha_k dt G phi, p = p + phi.
@@ -249,7 +253,8 @@ enum {
   NS_BUF_NU = 3, NS_BUF_NV = 4, NS_BUF_NW = 5,   /* N_prev (double, or float if NS_MIXED) */
   NS_BUF_PHI = 6,                               /* phi, double, nz*ny*nx */
   NS_BUF_SPEC = 7                               /* spectral buffer, complex double,
-                                                   (nz/2+1)*ny*nx, layout [kz][j][kx] */
+                                                   (nz/2+1)*ny*nx, layout [kz][j][kx]; NS_MIXED:
+                                                   the FP64 right-hand side of the Poisson solve */
 };
 ns_status ns_get_buffer(ns_ctx* ctx, int which, void** ptr, size_t* bytes);
 
