@@ -12,6 +12,8 @@
 // FFTs are mixed radix-2/4/3 Stockham autosort transforms (decimation in time) in shared memory
 // with a precomputed table of FMA-form twiddles (fft_twiddles); nx and nz are 2^a 3^b.  The y factors (1/pivot, c/pivot) of every (kx, kz)
 // system are precomputed once by pois_factor_kernel (the operator does not change).
+#include <algorithm>
+
 #include "ns_internal.cuh"
 
 namespace {
@@ -391,6 +393,67 @@ __device__ __forceinline__ void tdma_line(T* d, long sd, const double* __restric
     sweep_b(j1 - U, Bd, Bf);
   }
 }
+
+// ------------------------------------------------------------------------------------------
+// The FP32 x transform of the mixed form, persistent and double-buffered: each block walks
+// batches of R contiguous rows; the next batch is copied into shared memory by asynchronous
+// 16-byte copies (cp.async, waited for by cp.async.wait_group: no spin on a flag) while the
+// current batch is transformed and stored.  Rows of a batch are consecutive in the spectrum,
+// so a batch is one contiguous range (nx a multiple of 8: every row starts on 64 bytes).
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+template <int SIGN>
+struct FftxPK {
+  struct Args {
+    float2* spec;
+    const float2* twx;
+    long nrows;
+    int nx, px, R;
+    long nbatch;
+  };
+  static constexpr int kThreads = 256;
+  static constexpr int kMinBlocks = 2;
+  static __device__ __forceinline__ void run(const Args& a, const dim3 bid_, const dim3 gdim_) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int nx = a.nx, R = a.R;
+    const int rn = R * nx;  // float2 per buffer
+    float2* buf = reinterpret_cast<float2*>(smem_raw);  // [stage 0: data, scratch][stage 1: data, scratch]
+    auto issue = [&](long b, int st) {
+      if (b < a.nbatch) {
+        const long row0 = b * R;
+        const int nr = (int)min((long)R, a.nrows - row0);
+        const float4* src = reinterpret_cast<const float4*>(a.spec + row0 * nx);
+        float4* dst = reinterpret_cast<float4*>(buf + (2 * st) * rn);
+        for (int q = threadIdx.x; q < (nr * nx) / 2; q += blockDim.x) cp_async16(dst + q, src + q);
+      }
+      cp_async_commit();  // a group per call, empty or not, so that the waits count alike
+    };
+    long b = bid_.x;
+    issue(b, 0);
+    for (int it = 0; b < a.nbatch; ++it, b += gdim_.x) {
+      const int st = it & 1;
+      issue(b + gdim_.x, st ^ 1);
+      cp_async_wait<1>();  // every group but the newest: batch b has landed
+      __syncthreads();
+      const float2* X = stockham<SIGN, float2>(buf + (2 * st) * rn, buf + (2 * st + 1) * rn, nx, a.px, R, a.twx);
+      const long row0 = b * R;
+      const int nr = (int)min((long)R, a.nrows - row0);
+      float2* g = a.spec + row0 * nx;
+      for (int q = threadIdx.x; q < nr * nx; q += blockDim.x) g[q] = X[q];
+      __syncthreads();  // stage st is read out before the next iteration refills it
+    }
+    cp_async_wait<0>();
+  }
+};
 
 // ------------------------------------------------------------------------------------------
 // y tridiagonal per (kx, kz), two threads per line (real, imaginary part), factors 1/pivot and
@@ -1065,6 +1128,8 @@ cudaError_t poisson_set_attributes() {
   set_smem_limit<IfftzK>(200 * 1024);
   set_smem_limit<FftxK<-1>>(200 * 1024);
   set_smem_limit<FftxK<1>>(200 * 1024);
+  set_smem_limit<FftxPK<-1>>(200 * 1024);
+  set_smem_limit<FftxPK<1>>(200 * 1024);
   cudaFuncSetAttribute(dctx_fwd_kernel<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   cudaFuncSetAttribute(dctx_inv_kernel<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   return cudaGetLastError();
@@ -1162,11 +1227,21 @@ cudaError_t emit_xm(LaunchSink& s, bool fwd) {
       dctx_inv_kernel<float2><<<q.bx, 256, q.smx / 2, c->launch>>>(sp32(c), c->twx32, c->twd32, q.nrows, q.nx, q.px, q.R);
     return cudaGetLastError();
   }
+  // persistent, double-buffered: R rows per batch with 4 buffers of R nx float2 in shared memory
+  int R = 1;
+  while (R < 4 && (size_t)4 * 2 * R * q.nx * sizeof(float2) <= 64 * 1024) R <<= 1;
+  const long nbatch = (q.nrows + R - 1) / R;
+  const size_t smem = (size_t)4 * R * q.nx * sizeof(float2);
+  int bps = 1;
+  const cudaError_t oe = fwd ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, single_kernel<FftxPK<-1>>, 256, smem)
+                             : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, single_kernel<FftxPK<1>>, 256, smem);
+  if (oe != cudaSuccess) return oe;
+  const long blocks = std::min(nbatch, (long)std::max(bps, 1) * c->num_sms);
   if (fwd)
-    return emit<FftxK<-1, float2>>(s, FftxK<-1, float2>::make(sp32(c), c->twx32, q.nrows, q.nx, q.px, q.R, 1.0f),
-                                   dim3(q.bx), dim3(256), q.smx / 2);
-  return emit<FftxK<1, float2>>(s, FftxK<1, float2>::make(sp32(c), c->twx32, q.nrows, q.nx, q.px, q.R, 1.0f),
-                                dim3(q.bx), dim3(256), q.smx / 2);
+    return emit<FftxPK<-1>>(s, FftxPK<-1>::Args{sp32(c), c->twx32, q.nrows, q.nx, q.px, R, nbatch}, dim3((unsigned)blocks),
+                            dim3(256), smem);
+  return emit<FftxPK<1>>(s, FftxPK<1>::Args{sp32(c), c->twx32, q.nrows, q.nx, q.px, R, nbatch}, dim3((unsigned)blocks),
+                         dim3(256), smem);
 }
 
 cudaError_t emit_tdmam(LaunchSink& s) {
