@@ -503,7 +503,7 @@ def main():
         sb.close()
         mixed = {"value": job_throughput(world, cells, args.steps, tm * 1e-3), "ms_per_step": tm / args.steps,
                  "speedup_vs_fp64": t_max / tm, "rel_l2_vs_fp64_after_10_steps": err,
-                 "dtype": "f32 increments (rhs, adi) on f64 state; f64 divergence/poisson/projection",
+                 "dtype": "f32 increments (rhs, adi) on f64 state; f64 divergence, y solves and projection; f32 poisson transforms with one f64 refinement",
                  "kernel_ms_per_step": {k: v / max(3, args.steps // 5) for k, v in kmix.items() if v > 0}}
 
     # fixed-CFL stepping (dt from a device max-reduction before every step)
