@@ -1227,7 +1227,15 @@ cudaError_t emit_xm(LaunchSink& s, bool fwd) {
       dctx_inv_kernel<float2><<<q.bx, 256, q.smx / 2, c->launch>>>(sp32(c), c->twx32, c->twd32, q.nrows, q.nx, q.px, q.R);
     return cudaGetLastError();
   }
-  // persistent, double-buffered: R rows per batch with 4 buffers of R nx float2 in shared memory
+  if (s.plan) {  // batched ensembles: many small instances fill the GPU with one batch per block
+    if (fwd)
+      return emit<FftxK<-1, float2>>(s, FftxK<-1, float2>::make(sp32(c), c->twx32, q.nrows, q.nx, q.px, q.R, 1.0f),
+                                     dim3(q.bx), dim3(256), q.smx / 2);
+    return emit<FftxK<1, float2>>(s, FftxK<1, float2>::make(sp32(c), c->twx32, q.nrows, q.nx, q.px, q.R, 1.0f),
+                                  dim3(q.bx), dim3(256), q.smx / 2);
+  }
+  // single instance: persistent, double-buffered: R rows per batch with 4 buffers of R nx float2
+  // in shared memory
   int R = 1;
   while (R < 4 && (size_t)4 * 2 * R * q.nx * sizeof(float2) <= 64 * 1024) R <<= 1;
   const long nbatch = (q.nrows + R - 1) / R;
