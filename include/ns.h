@@ -214,10 +214,11 @@ ns_status ns_step_profiled(ns_ctx* ctx, int nsteps, float* kernel_ms, int nk);
 
 /* Number of kernel slots in one sub-step, and the name of slot idx, in launch order: recycle,
  * rhs, outflow, adi_x, adi_y, adi_z, flux_correct, poisson_div_fftz, poisson_x_fwd,
- * poisson_tdma_y, poisson_x_inv, poisson_ifftz, project ("" if idx is out of range).  recycle
- * launches only in sub-step 0 with recycle_i != 0; outflow and flux_correct only with bc_x = 1
- * (else their time is 0); poisson_x_* are FFTs for periodic x and cosine transforms (DCT-II / its
- * inverse) for inflow / outflow. */
+ * poisson_tdma_y, poisson_x_inv, poisson_ifftz, poisson_refine, project ("" if idx is out of
+ * range).  recycle launches only in sub-step 0 with recycle_i != 0; outflow and flux_correct only
+ * with bc_x = 1; poisson_refine (the FP64 residual and the second FP32 Poisson pass, five kernels)
+ * only with NS_MIXED (an idle slot's time is 0); poisson_x_* are FFTs for periodic x and cosine
+ * transforms (DCT-II / its inverse) for inflow / outflow. */
 int ns_kernel_count(void);
 const char* ns_kernel_name(int idx);
 
