@@ -1,8 +1,9 @@
 // The tables and constants that depend on the time step (ADI factors, PDD/PPT tables, RHS rows,
 // sub-step constants), written once for both builders: the host (ns_init, ns_set_dt) and the
-// device (dt_phase1_kernel and dt_phase2_kernel in the fixed-CFL step graph, k_dt.cu).  Every function here is a task on one
-// table or row that a host loop or a device thread runs; all arithmetic is FP64 and the tables
-// are stored in the context's element type (double, or float for the mixed form).
+// device (dt_phase1_kernel and dt_phase2_kernel in the fixed-CFL step graph, k_dt.cu).  Every
+// function here is a task on one table or row that a host loop or a device thread runs; all
+// arithmetic is FP64 and the tables are stored in the context's element type (double, or float
+// for the mixed form).
 #pragma once
 
 #include <string.h>
