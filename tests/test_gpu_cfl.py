@@ -157,12 +157,13 @@ def test_device_dt_update_equals_the_host_tables(prec, shape, part):
     b.close()
 
 
-def test_device_dt_update_equals_the_host_tables_boundary_layer():
+@pytest.mark.parametrize("prec", [B.NS_FP64, B.NS_MIXED])
+def test_device_dt_update_equals_the_host_tables_boundary_layer(prec):
     case, u, v, w, p, bl = I.boundary_layer(64, 16, 16, amp=0.05, seed=8, re=200.0)
     g = O.Grid.from_case(case)
     u, v, w, bl = O.make_divergence_free_bl(g, u, v, w, bl)
-    a = B.Solver(case, u, v, w, p, bl=bl)
-    b = B.Solver(case, u, v, w, p, bl=bl)
+    a = B.Solver(case, u, v, w, p, bl=bl, precision=prec)
+    b = B.Solver(case, u, v, w, p, bl=bl, precision=prec)
     d_dev = a.step_cfl(3, 0.8)
     d_host = _host_cfl(b, 3, 0.8)
     assert list(d_dev) == d_host
@@ -210,6 +211,21 @@ def test_kim_moin_steps_match_the_oracle(shape):
     assert not np.array_equal(a[3], b[3])
     s1.close()
     s2.close()
+
+
+def test_kim_moin_mixed_form():
+    """The Kim-Moin pressure update with the mixed form (its projection reads the refined phi)."""
+    case, g, u, v, w, p = _projected((64, 37, 32), 6, re=40.0)
+    case.pressure_update = B.NS_PRESSURE_KIM_MOIN
+    s = B.Solver(case, u, v, w, p, precision=B.NS_MIXED)
+    s.step(2)
+    ref = O.step(g, dict(u=u, v=v, w=w, p=p), case.dt, case.re, case.fx, 2, pressure="kim_moin")
+    got = s.state()
+    errs = field_rel_errors(got, (ref["u"], ref["v"], ref["w"], ref["p"]))
+    for name, bound in (("u", 1e-7), ("v", 1e-7), ("w", 1e-7), ("p", 1e-6)):
+        assert errs[name] < bound, (name, errs)
+    assert np.abs(O.divergence(g, *got[:3])).max() < 1e-10
+    s.close()
 
 
 def test_kim_moin_boundary_layer():
