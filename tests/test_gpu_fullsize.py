@@ -119,6 +119,25 @@ def test_turbulent_channel_256x192x256_fp64():
     s.close()
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_turbulent_channel_256x192x256_poisson_residual(precision):
+    """A property that holds at any size: phi of the Poisson solve satisfies the discrete equation
+    D G phi = D u (scale 1) cell by cell, checked with the oracle's divergence and gradient
+    stencils.  In the mixed form this is the FP32 transforms with their FP64 refinement at the
+    bench's size."""
+    case, u, v, w, p = I.turbulent_channel()
+    case.precision = precision
+    g = O.Grid.from_case(case)
+    s = B.Solver(case, u, v, w, p)
+    s.poisson(-1)
+    phi = to_np(s.buffer(B.NS_BUF_PHI))
+    s.close()
+    b = O.divergence(g, u, v, w)
+    b = b - (b * g.dy[None, :, None]).sum() / (g.dy.sum() * case.nx * case.nz)  # the solvable part
+    res = O.divergence(g, *O.gradient(g, phi)) - b
+    assert np.abs(res).max() < 1e-10 * np.abs(b).max(), (np.abs(res).max(), np.abs(b).max())
+
+
 def test_boundary_layer_1024x256x512_mixed():
     if _host_mem_gb() < 40:
         pytest.skip("needs ~40 GB of host memory for the seeded fields")
