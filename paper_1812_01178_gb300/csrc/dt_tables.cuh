@@ -308,6 +308,24 @@ NS_HD double xtab_drop(int n, int P, bool cyclic, const double* t) {
   return drop;
 }
 
+// Spike truncation of the x solve: the spikes decay geometrically away from the partition end
+// they start from (by about r = beta / dx^2 per row here), so the back half of v^(r) and the front
+// half of w^(r) are often below any effect on the solution.  1 if, for every partition, |v_e| and
+// |w_{M-1-e}| are at most tol for e >= M/2 (M even, M >= 2); the correction x_e -= v_e x_m^(r-1) +
+// w_e x_1^(r+1) then keeps one term per row.  tol: 1e-17 in FP64 (a hundredth of the coupling PDD
+// may drop, below the rounding of the solve itself), 1e-9 in FP32.
+NS_HD double x_half_tol(int es) { return es == 8 ? 1e-17 : 1e-9; }
+NS_HD int xtab_half(int n, int P, const double* t, double tol) {
+  const int M = n / P;
+  if (M < 2 || (M & 1)) return 0;
+  const double* SV = t + (size_t)XT_V * M * P;
+  const double* SW = t + (size_t)XT_W * M * P;
+  for (int e = M / 2; e < M; ++e)
+    for (int r = 0; r < P; ++r)
+      if (!(fabs(SV[(size_t)e * P + r]) <= tol) || !(fabs(SW[(size_t)(M - 1 - e) * P + r]) <= tol)) return 0;
+  return 1;
+}
+
 // Phase 2 in three steps, each over the partitions r independently (a device block runs them
 // with one thread per r and a barrier between levels): the blocks of interface r, one level of
 // block cyclic reduction, and the final inverse diagonal block.

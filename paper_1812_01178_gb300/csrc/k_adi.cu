@@ -183,9 +183,17 @@ struct AdiXK {
     const T y0 = DINV[r] * g0 + DINV[P + r] * g1;      // x^{(r)}_m
     const T y1 = DINV[2 * P + r] * g0 + DINV[3 * P + r] * g1;  // x^{(r+1)}_1
     const T left = __shfl_sync(NS_FULL_MASK, y0, r - 1 + P, P);  // x^{(r-1)}_m
-    // x = x~ - v x^{(r-1)}_m - w x^{(r+1)}_1
+    // x = x~ - v x^{(r-1)}_m - w x^{(r+1)}_1; when the tables say the back half of v and the front
+    // half of w are below the truncation tolerance (StepK::xhalf), each row keeps one term
+    if (a.sk->xhalf[a.bl && comp != 0 ? 1 : 0]) {
 #pragma unroll
-    for (int e = 0; e < M; ++e) d[e] = d[e] - SV[e * P + r] * left - SW[e * P + r] * y1;
+      for (int e = 0; e < M / 2; ++e) d[e] = d[e] - SV[e * P + r] * left;
+#pragma unroll
+      for (int e = M / 2; e < M; ++e) d[e] = d[e] - SW[e * P + r] * y1;
+    } else {
+#pragma unroll
+      for (int e = 0; e < M; ++e) d[e] = d[e] - SV[e * P + r] * left - SW[e * P + r] * y1;
+    }
     if (valid) store_part<T, M>(row + r * M, d);
   }
 

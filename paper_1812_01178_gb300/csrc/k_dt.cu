@@ -222,6 +222,8 @@ __global__ void __launch_bounds__(128) dt_phase2_kernel(const __grid_constant__ 
         a.stepk[k].L = Lx;
         a.stepk[k].Ly = Ly;
         a.stepk[k].Lz = Lz;
+        for (int cls = 0; cls < 2; ++cls)
+          a.stepk[k].xhalf[cls] = xtab_half(s.nx, s.P, scr_x(a, 2 * k + cls), x_half_tol(s.es));
       }
     } else if (ctl->status == 0) {
       ctl->status = isfinite(rate) ? 2u : 1u;
@@ -353,6 +355,9 @@ ns_status build_x_tables(ns_ctx* c) {
       for (int r = 0; r < P; ++r) xtab_phase1_part(nx, P, r, cyclic, row, t[k][cls].data());
       drop = std::fmax(drop, xtab_drop(nx, P, cyclic, t[k][cls].data()));
     }
+  int half[3][2];
+  for (int k = 0; k < 3; ++k)
+    for (int cls = 0; cls < 2; ++cls) half[k][cls] = xtab_half(nx, P, t[k][cls].data(), x_half_tol(c->es));
   int mode = c->part_req;
   if (mode == NS_PART_AUTO) mode = drop <= pdd_tol(c->es) ? NS_PART_PDD : NS_PART_PPT;
   c->part_mode = mode;
@@ -374,6 +379,8 @@ ns_status build_x_tables(ns_ctx* c) {
       c->stepk_h[q].L = c->L[q];
       c->stepk_h[q].Ly = c->yL[q];
       c->stepk_h[q].Lz = c->zL[q];
+      c->stepk_h[q].xhalf[0] = half[q][0];
+      c->stepk_h[q].xhalf[1] = half[q][1];
     }
   }
   if (upload_raw(c, c->stepk, c->stepk_h, sizeof(c->stepk_h)) != cudaSuccess) return NS_ERR_CUDA;

@@ -176,6 +176,9 @@ struct StepK {
   float xcff[4];      // the same in float (3 used)
   int L;              // reduction levels of the x solve (0: PDD)
   int Ly, Lz;         // the same for the partitioned y and z lines of the mixed form
+  int xhalf[2];       // x tables of class 0 (u) / 1 (v, w): 1 if every spike v^(r)_e of the back
+                      // half of a partition and w^(r)_e of the front half is below the truncation
+                      // tolerance (x_half_tol), so each row takes one correction only
 };
 constexpr int NS_STEPK = 4;
 

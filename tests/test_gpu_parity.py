@@ -120,6 +120,31 @@ def test_adi_x_partitioned_parity(shape, mode):
     s.close()
 
 
+@pytest.mark.parametrize("mode", [B.NS_PART_PPT, B.NS_PART_PDD])
+def test_adi_x_truncated_spikes(mode):
+    """Strongly dominant rows (beta / dx^2 about 1e-7): the spikes fall below the truncation
+    tolerance within half a partition, and the sweep keeps one correction per row
+    (StepK::xhalf).  The result still equals the oracle's whole-line cyclic solve to round-off,
+    both modes, every sub-step.  (The inflow / outflow class is covered by the whole-step parity
+    of the boundary layer, whose rows are as dominant.)"""
+    case, u, v, w, p = _case(128, 9, 8)
+    case.re = 1e5
+    case.dt = 1e-4
+    g = O.Grid.from_case(case)
+    s = B.Solver(case, u, v, w, p)
+    s.set_partition(16, mode)  # M = 8 rows per partition
+    r3 = _rand_r(case, 21)
+    for k in (0, 1, 2):
+        beta = O.RK3_ALPHA[k] * case.dt / (2 * case.re)
+        _load_r(s, r3)
+        s.adi(0, k)
+        for q, bi in enumerate([B.NS_BUF_RU, B.NS_BUF_RV, B.NS_BUF_RW]):
+            ref = O.adi_sweep(g, r3[q], 0, q, beta)
+            err = np.abs(to_np(s.buffer(bi)) - ref).max() / np.abs(ref).max()
+            assert err < 1e-13, (k, q, err)
+    s.close()
+
+
 @pytest.mark.parametrize("shape", SHAPES)
 def test_pdd_matches_oracle_pdd(shape):
     """PDD on the GPU reproduces the oracle's dense-matrix PDD of Sec. 3.2 when the dropped
