@@ -235,17 +235,28 @@ ns_status ns_make_divergence_free(ns_ctx* ctx);
  * power of two from 1 to 32, M in {1, 2, 3, 4, 6, 8, 9, 12, 16} (rows held in registers) or, at
  * P = 32, M in {24, 32, 48, 64} (long lines staged in shared memory); other P give NS_ERR_ARG.
  * mode 0 = automatic (PDD when the coupling PDD drops is below its tolerance for every sub-step,
- * else PPT), 1 = PPT, 2 = PDD.  Rebuilds the tables and drops the captured graph.  dir must be
- * 0.  The default P is the largest admissible one with at least 8 rows per partition. */
+ * else PPT), 1 = PPT, 2 = PDD.  Rebuilds the tables and drops the captured graph.  The default P
+ * is the largest admissible one with at least 8 rows per partition.
+ *
+ * dir 1 / 2: the y / z lines of the mixed form (NS_MIXED with nx a multiple of 32; otherwise
+ * NS_ERR_UNSUPPORTED).  P = 0 solves every line whole, one thread per line; a nonzero P must be
+ * the one partition shape the line kernels are built for (8 x {4, 6, 8, 12, 16, 24, 32},
+ * 16 x {18, 32}, 32 x 32 rows; it is the default when the line length has one), else NS_ERR_ARG.
+ * mode must be NS_PART_AUTO: PDD when the coupling it drops is below the FP32 tolerance for every
+ * sub-step, else PPT.  Other dir: NS_ERR_ARG. */
 enum { NS_PART_AUTO = 0, NS_PART_PPT = 1, NS_PART_PDD = 2 };
 ns_status ns_set_partition(ns_ctx* ctx, int dir, int P, int mode);
 
 /* Query the partitioning in use: *P, *mode (NS_PART_PPT or NS_PART_PDD) and the largest
- * coupling PDD drops over the three sub-steps (the admissibility measure). */
+ * coupling PDD drops over the three sub-steps (the admissibility measure).  dir 1 / 2 (y / z
+ * lines): *P = 0 for lines solved whole (reported as NS_PART_PPT, dropped 0). */
 ns_status ns_get_partition(ns_ctx* ctx, int dir, int* P, int* mode, double* pdd_dropped);
 
 /* Pick P and the PDD/PPT mode for the x solver by timing every admissible P on the context's
- * stream (CUDA events).  Leaves the fastest installed. */
+ * stream (CUDA events), and, in the mixed form with nx a multiple of 32, the y and z line shapes
+ * (partitioned or whole), each by timing its sweep.  Leaves the fastest installed.  The timed
+ * sweeps run on the current r buffers and velocity; both are saved to temporary device memory
+ * (cudaMalloc, freed before return) and restored.  Synchronises the stream. */
 ns_status ns_autotune(ns_ctx* ctx);
 
 /* Workspace buffers, for inspection and for stage-by-stage testing. */
@@ -307,7 +318,9 @@ ns_status ns_batch_step(ns_batch* b, int nsteps);
 /* Number of kernel launches in one batched time step (3 sub-steps x stages x kernel variants). */
 int ns_batch_launches_per_step(ns_batch* b);
 
-/* Pick each instance's x partitioning by timing (ns_autotune per instance), then re-plan. */
+/* Pick each instance's x partitioning by timing (as ns_autotune, x solver only: instances keep
+ * their default y and z line shapes, so that instances of one size share launches), then
+ * re-plan. */
 ns_status ns_batch_autotune(ns_batch* b);
 
 /* Set instance i's x partitioning (as ns_set_partition) and re-plan. */

@@ -350,6 +350,13 @@ class Solver:
     def partition(self):
         return ns_get_partition(self.ctx, 0)
 
+    def set_line_partition(self, direction, P):
+        """y (1) or z (2) lines of the mixed form: P = 0 whole lines, else the built-in shape."""
+        ns_set_partition(self.ctx, direction, P, NS_PART_AUTO)
+
+    def line_partition(self, direction):
+        return ns_get_partition(self.ctx, direction)
+
     def autotune(self):
         ns_autotune(self.ctx)
 

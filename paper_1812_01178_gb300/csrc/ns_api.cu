@@ -728,9 +728,33 @@ ns_status ns_step_host(ns_ctx* c, double* u, double* v, double* w, double* p, in
   return ns_sync(c);
 }
 
+// y (dir 1) or z (dir 2) lines of the mixed form: P = 0 solves them whole (one thread per line),
+// else P must be the partition count line_partition(n) the line kernels are built for.
+static ns_status set_line_partition(ns_ctx* c, int dir, int P, int mode) {
+  if (c->cfg.precision != NS_MIXED || c->cfg.nx % 32 != 0)
+    return fail(c, NS_ERR_UNSUPPORTED, "y and z lines are partitioned only in the mixed form with nx % 32 == 0");
+  const int n = dir == 1 ? c->cfg.ny : c->cfg.nz;
+  if (P != 0 && P != line_partition(n)) return fail(c, NS_ERR_ARG, "invalid line partition count");
+  if (mode != NS_PART_AUTO) return fail(c, NS_ERR_ARG, "y and z lines take NS_PART_AUTO");
+  if (capturing(c)) return fail(c, NS_ERR_STATE, "ns_set_partition during capture");
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return fail(c, NS_ERR_CUDA, "sync");
+  int& slot = dir == 1 ? c->yP : c->zP;
+  const int old = slot;
+  slot = P;
+  ns_status s = build_x_tables(c);
+  if (s != NS_OK) {
+    slot = old;
+    build_x_tables(c);
+    return fail(c, s, "rebuilding line tables failed");
+  }
+  drop_graph(c);
+  return NS_OK;
+}
+
 ns_status ns_set_partition(ns_ctx* c, int dir, int P, int mode) {
   if (!c) return NS_ERR_ARG;
-  if (dir != 0) return fail(c, NS_ERR_UNSUPPORTED, "only dir 0 (x) is partitioned");
+  if (dir == 1 || dir == 2) return set_line_partition(c, dir, P, mode);
+  if (dir != 0) return fail(c, NS_ERR_ARG, "dir must be 0, 1 or 2");
   const int nx = c->cfg.nx;
   if (P < 1 || P > 32 || nx % P != 0 || !x_partition_ok(P, nx / P))
     return fail(c, NS_ERR_ARG, "invalid partition count");
@@ -756,23 +780,60 @@ ns_status ns_set_partition(ns_ctx* c, int dir, int P, int mode) {
 
 ns_status ns_get_partition(ns_ctx* c, int dir, int* P, int* mode, double* dropped) {
   if (!c) return NS_ERR_ARG;
-  if (dir != 0) return fail(c, NS_ERR_UNSUPPORTED, "only dir 0 (x) is partitioned");
+  if (dir == 1 || dir == 2) {
+    const int lp = dir == 1 ? c->yP : c->zP;
+    const int L = dir == 1 ? c->yL[0] : c->zL[0];
+    if (P) *P = lp;
+    if (mode) *mode = lp && L == 0 ? NS_PART_PDD : NS_PART_PPT;
+    if (dropped) *dropped = lp ? (dir == 1 ? c->ypdd_drop : c->zpdd_drop) : 0.0;
+    return NS_OK;
+  }
+  if (dir != 0) return fail(c, NS_ERR_ARG, "dir must be 0, 1 or 2");
   if (P) *P = c->P;
   if (mode) *mode = c->part_mode;
   if (dropped) *dropped = c->pdd_drop;
   return NS_OK;
 }
 
-ns_status ns_autotune(ns_ctx* c) {
+extern "C++" {
+// mean time of five launches of one sweep (after one untimed launch), in ms; < 0 on a failure
+static float time_sweep(ns_ctx* c, int dir, cudaEvent_t e0, cudaEvent_t e1) {
+  LaunchSink s{c, nullptr};
+  auto one = [&](int k) {
+    return dir == 0 ? stage_adi_x(s, k) : (dir == 1 ? stage_adi_y(s, k) : stage_adi_z(s, k));
+  };
+  if (one(0) != cudaSuccess) return -1.0f;
+  cudaEventRecord(e0, c->stream);
+  for (int it = 0; it < 5; ++it)
+    if (one(it % 3) != cudaSuccess) return -1.0f;
+  cudaEventRecord(e1, c->stream);
+  cudaEventSynchronize(e1);
+  float ms = 0;
+  cudaEventElapsedTime(&ms, e0, e1);
+  return cudaGetLastError() == cudaSuccess ? ms / 5 : -1.0f;
+}
+
+// The x partitioning (every admissible P, automatic mode and forced PPT); with lines, also the y
+// and z lines of the mixed form (partitioned or whole).  Each candidate's sweep is timed on the
+// context's stream; the fastest stays installed.  The timed sweeps overwrite r and, in z, the
+// velocity (u* = u + delta): both are saved first and restored afterwards.
+ns_status autotune_ctx(ns_ctx* c, bool lines) {
   if (!c) return NS_ERR_ARG;
   if (capturing(c)) return fail(c, NS_ERR_STATE, "ns_autotune during capture");
   const int nx = c->cfg.nx;
-  // The timed sweeps overwrite r: keep a copy and restore it afterwards.
+  const bool tune_lines = lines && c->cfg.precision == NS_MIXED && nx % 32 == 0;
   const size_t rbytes = c->lay.off[LB_NU] - c->lay.off[LB_RU];
-  void* save = nullptr;
-  cudaError_t e = cudaMalloc(&save, rbytes);
+  const size_t cells = (size_t)nx * c->cfg.ny * c->cfg.nz, vcells = (size_t)nx * (c->cfg.ny + 1) * c->cfg.nz;
+  const size_t fbytes = tune_lines ? (2 * cells + vcells) * 8 : 0;
+  char* save = nullptr;
+  cudaError_t e = cudaMalloc((void**)&save, rbytes + fbytes);
   if (e != cudaSuccess) return cuda_fail(c, e, "autotune scratch");
   cudaMemcpyAsync(save, c->ru, rbytes, cudaMemcpyDeviceToDevice, c->stream);
+  if (tune_lines) {
+    cudaMemcpyAsync(save + rbytes, c->f.u, cells * 8, cudaMemcpyDeviceToDevice, c->stream);
+    cudaMemcpyAsync(save + rbytes + cells * 8, c->f.v, vcells * 8, cudaMemcpyDeviceToDevice, c->stream);
+    cudaMemcpyAsync(save + rbytes + (cells + vcells) * 8, c->f.w, cells * 8, cudaMemcpyDeviceToDevice, c->stream);
+  }
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
@@ -783,27 +844,46 @@ ns_status ns_autotune(ns_ctx* c) {
     for (int mode : {NS_PART_AUTO, NS_PART_PPT}) {
       if (ns_set_partition(c, 0, P, mode) != NS_OK) continue;
       if (mode == NS_PART_PPT && c->part_mode != NS_PART_PPT) continue;
-      launch_adi_x(c, 0);
-      cudaEventRecord(e0, c->stream);
-      for (int it = 0; it < 5; ++it) launch_adi_x(c, it % 3);
-      cudaEventRecord(e1, c->stream);
-      cudaEventSynchronize(e1);
-      float ms = 0;
-      cudaEventElapsedTime(&ms, e0, e1);
-      if (cudaGetLastError() == cudaSuccess && ms < best) {
+      const float ms = time_sweep(c, 0, e0, e1);
+      if (ms >= 0 && ms < best) {
         best = ms;
         bestP = P;
         bestMode = mode;
       }
     }
   }
+  ns_status st = ns_set_partition(c, 0, bestP, bestMode);
+  for (int dir = 1; dir <= 2 && tune_lines && st == NS_OK; ++dir) {
+    const int Pl = line_partition(dir == 1 ? c->cfg.ny : c->cfg.nz);
+    if (!Pl) continue;
+    int bestL = dir == 1 ? c->yP : c->zP;
+    float bl = 1e30f;
+    for (int P : {Pl, 0}) {
+      if (ns_set_partition(c, dir, P, NS_PART_AUTO) != NS_OK) continue;
+      const float ms = time_sweep(c, dir, e0, e1);
+      if (ms >= 0 && ms < bl) {
+        bl = ms;
+        bestL = P;
+      }
+    }
+    st = ns_set_partition(c, dir, bestL, NS_PART_AUTO);
+  }
   cudaMemcpyAsync(c->ru, save, rbytes, cudaMemcpyDeviceToDevice, c->stream);
+  if (tune_lines) {
+    cudaMemcpyAsync(c->f.u, save + rbytes, cells * 8, cudaMemcpyDeviceToDevice, c->stream);
+    cudaMemcpyAsync(c->f.v, save + rbytes + cells * 8, vcells * 8, cudaMemcpyDeviceToDevice, c->stream);
+    cudaMemcpyAsync(c->f.w, save + rbytes + (cells + vcells) * 8, cells * 8, cudaMemcpyDeviceToDevice, c->stream);
+  }
   cudaStreamSynchronize(c->stream);
   cudaFree(save);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  return ns_set_partition(c, 0, bestP, bestMode);
+  return st;
 }
+
+}  // extern "C++"
+
+ns_status ns_autotune(ns_ctx* c) { return autotune_ctx(c, true); }
 
 ns_status ns_get_buffer(ns_ctx* c, int which, void** ptr, size_t* bytes) {
   if (!c || !ptr) return NS_ERR_ARG;

@@ -253,7 +253,7 @@ int ns_batch_launches_per_step(ns_batch* b) {
 ns_status ns_batch_autotune(ns_batch* b) {
   if (!b) return NS_ERR_ARG;
   for (ns_ctx* c : b->inst) {
-    ns_status s = ns_autotune(c);
+    ns_status s = autotune_ctx(c, false);  // the x solver only: instances of one size keep one line shape
     if (s != NS_OK) return bfail(b, s, std::string("instance autotune: ") + ns_last_error(c));
   }
   drop_batch_graph(b);

@@ -457,6 +457,8 @@ cudaError_t stage_project(LaunchSink& s, int k);
 cudaError_t launch_rhs(ns_ctx* c, int k);
 cudaError_t rhs_set_attributes(int* bps_fp64, int* bps_fp32);  // once per device, outside any capture
 cudaError_t launch_adi_x(ns_ctx* c, int k);
+// ns_autotune; lines = false keeps the default y and z line shapes (batched instances share them)
+ns_status autotune_ctx(ns_ctx* c, bool lines);
 cudaError_t adi_set_attributes();  // once per device, outside any capture
 cudaError_t launch_adi_y(ns_ctx* c, int k);
 cudaError_t launch_adi_z(ns_ctx* c, int k);
