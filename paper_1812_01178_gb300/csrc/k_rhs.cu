@@ -247,9 +247,11 @@ struct RhsTiledK {
     int jchunk;
   };
   static constexpr int kThreads = RT_X * RT_Z;
-  // FP64: shared memory allows 3 resident blocks, so up to 85 registers cost nothing; FP32: 5 blocks,
-  // or 4 of up to 64 registers when the sub-step constants come from device memory
-  static constexpr int kMinBlocks = sizeof(T) == 8 ? 3 : (Dyn ? 4 : 5);
+  // FP64: shared memory allows 3 resident blocks, so up to 85 registers cost nothing.  FP32: 6
+  // blocks of up to 40 registers (the kernel waits on memory and shared memory, so occupancy pays
+  // more than registers: 0.314 ms at 6 blocks against 0.338 at 5, 0.352 at 4 and 0.434 at 3), or 4
+  // of up to 64 when the sub-step constants come from device memory (fewer spill)
+  static constexpr int kMinBlocks = sizeof(T) == 8 ? 3 : (Dyn ? 4 : 6);
   static Args make(RhsArgs a, int jchunk) { return Args{a, jchunk}; }
   static __device__ __forceinline__ void run(const Args& a_, const dim3 bid_, const dim3 gdim_) {
     const RhsArgs& a = a_.a;
