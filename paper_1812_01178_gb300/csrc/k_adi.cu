@@ -114,7 +114,9 @@ struct AdiXK {
     AdiXArgs<T> a;
   };
   static constexpr int kThreads = 256;
-  static constexpr int kMinBlocks = sizeof(T) == 4 ? 3 : 2;  // FP32 is bandwidth-bound: occupancy
+  // FP32 is bandwidth-bound: occupancy.  At 8 rows, 4 blocks of 64 registers (a 24-byte spill)
+  // beat 3 of 80 (0.071 -> 0.066 ms on 256-row lines)
+  static constexpr int kMinBlocks = sizeof(T) == 4 ? (M == 8 ? 4 : 3) : 2;
   static Args make(AdiXArgs<T> a) { return Args{a}; }
   static __device__ __forceinline__ void run(const Args& a_, const dim3 bid_, const dim3 gdim_) {
     const AdiXArgs<T>& a = a_.a;
