@@ -590,7 +590,7 @@ struct DivzMK {
     const double* u_out;
   };
   static constexpr int kThreads = 256;
-  static constexpr int kMinBlocks = 4;
+  static constexpr int kMinBlocks = 5;  // 48 registers: 5 blocks of 32 KB (0.173 -> 0.166 ms at 4 -> 5)
   static __device__ __forceinline__ void run(const Args& a, const dim3 bid_, const dim3) {
     const int nx = a.nx, ny = a.ny, nz = a.nz, TX = a.TX;
     extern __shared__ __align__(16) unsigned char smem_raw[];
