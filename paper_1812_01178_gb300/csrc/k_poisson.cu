@@ -768,8 +768,8 @@ struct IfftzMK {
 };
 
 // ------------------------------------------------------------------------------------------
-// projection u = u* - s G phi; p += phi (if update_p).  One thread per (i, j) of a z-plane,
-// j = 0..ny.
+// projection u = u* - s G phi; p += phi (if update_p).  One thread per (i, j) of kZ consecutive
+// z-planes, j = 0..ny.
 // ------------------------------------------------------------------------------------------
 // Dyn: sx, sz, s, beta_p from device memory, else from the arguments; KM: the Kim-Moin pressure
 // update (compiled only into the variants that use it)
@@ -792,7 +792,8 @@ struct ProjectK {
     double idx2, idz2;
   };
   static constexpr int kThreads = 128;
-  static constexpr int kMinBlocks = (Dyn || KM) ? 12 : 16;
+  static constexpr int kMinBlocks = KM ? 8 : 12;  // the Kim-Moin update reads six more neighbours
+  static constexpr int kZ = 4;  // z planes per thread (nz is a multiple of 8)
   static Args make(double* u, double* v, double* w, double* p, const double* phi, const double* gc, int nx, int ny, int nz, const StepK* sk, const StepK& kc, int update_p, int bl, double idx2, double idz2) { return Args{u, v, w, p, phi, gc, nx, ny, nz, sk, kc.sx, kc.sz, kc.s, kc.beta_p, update_p, bl, idx2, idz2}; }
   static __device__ __forceinline__ void run(const Args& a_, const dim3 bid_, const dim3 gdim_) {
     double* __restrict__ u = a_.u;
@@ -816,44 +817,46 @@ struct ProjectK {
   if (q >= plane) return;
   const int j = (int)(q / nx);
   const int i = (int)(q - (long)j * nx);
-  const int k = bid_.y;
+  if (j >= ny) return;  // the top wall row of v: nothing to update
   const int im = (i == 0) ? nx - 1 : i - 1;
-  const int km = (k == 0) ? nz - 1 : k - 1;
-  const long pl = (long)ny * nx;
-  if (j < ny) {
-    const long cc = k * pl + (long)j * nx + i;
+  const long pl = (long)ny * nx, vpl = (long)(ny + 1) * nx;
+  const long row = (long)j * nx;
+  const double sv = j >= 1 ? s * __ldg(gc + GC_IHC * (ny + 1) + j) : 0.0;  // v: s / hc_j
+  // kZ consecutive z planes per thread: phi of the plane below carries over to the w update
+  const int k0 = bid_.y * kZ;
+  double fprev = __ldg(phi + (k0 == 0 ? nz - 1 : k0 - 1) * pl + row + i);
+#pragma unroll 1
+  for (int kk = 0; kk < kZ; ++kk) {
+    const int k = k0 + kk;
+    const long cc = k * pl + row + i;
     const double f0 = __ldg(phi + cc);
-    if (!(bl && i == 0)) u[cc] -= sx * (f0 - __ldg(phi + k * pl + (long)j * nx + im));  // inflow face fixed
-    w[cc] -= sz * (f0 - __ldg(phi + km * pl + (long)j * nx + i));
+    if (!(bl && i == 0)) u[cc] -= sx * (f0 - __ldg(phi + k * pl + row + im));  // inflow face fixed
+    w[cc] -= sz * (f0 - fprev);
+    if (j >= 1) v[k * vpl + row + i] -= sv * (f0 - __ldg(phi + cc - nx));
     if (update_p) {
       double dp = f0;
       if (KM && beta_p != 0.0) {
         // Kim-Moin: p += phi - beta_k (D G phi), with G phi = 0 on the walls (PA_0 = PC_{ny-1} = 0)
         // and, with inflow / outflow, on the x = 0 and x = Lx faces
-        const long row = k * pl + (long)j * nx;
+        const long rk = k * pl + row;
         double lx;
         if (bl) {
-          const double ge = (i + 1 < nx) ? __ldg(phi + row + i + 1) - f0 : 0.0;
-          const double gw = (i > 0) ? f0 - __ldg(phi + row + i - 1) : 0.0;
+          const double ge = (i + 1 < nx) ? __ldg(phi + rk + i + 1) - f0 : 0.0;
+          const double gw = (i > 0) ? f0 - __ldg(phi + rk + i - 1) : 0.0;
           lx = (ge - gw) * a_.idx2;
         } else {
           const int ip = (i + 1 == nx) ? 0 : i + 1;
-          lx = ((__ldg(phi + row + ip) - f0) - (f0 - __ldg(phi + row + im))) * a_.idx2;
+          lx = ((__ldg(phi + rk + ip) - f0) - (f0 - __ldg(phi + rk + im))) * a_.idx2;
         }
         const double ly = (j > 0 ? __ldg(gc + GC_PA * (ny + 1) + j) * (__ldg(phi + cc - nx) - f0) : 0.0) +
                           (j + 1 < ny ? __ldg(gc + GC_PC * (ny + 1) + j) * (__ldg(phi + cc + nx) - f0) : 0.0);
         const int kp = (k + 1 == nz) ? 0 : k + 1;
-        const double lz = ((__ldg(phi + kp * pl + (long)j * nx + i) - f0) - (f0 - __ldg(phi + km * pl + (long)j * nx + i))) *
-                          a_.idz2;
+        const double lz = ((__ldg(phi + kp * pl + row + i) - f0) - (f0 - fprev)) * a_.idz2;
         dp = f0 - beta_p * (lx + ly + lz);
       }
       p[cc] += dp;
     }
-  }
-  if (j >= 1 && j < ny) {
-    const double ihc = __ldg(gc + GC_IHC * (ny + 1) + j);
-    const long cc = k * pl + (long)j * nx + i;
-    v[(long)k * (ny + 1) * nx + (long)j * nx + i] -= s * ihc * (__ldg(phi + cc) - __ldg(phi + cc - nx));
+    fprev = f0;
   }
 
   }
@@ -1347,7 +1350,7 @@ cudaError_t emit_project(LaunchSink& s, int q, int k) {
   ns_ctx* c = s.c;
   const int nx = c->cfg.nx, ny = c->cfg.ny, nz = c->cfg.nz;
   const long plane = (long)nx * (ny + 1);
-  dim3 grid((unsigned)((plane + 127) / 128), nz);
+  dim3 grid((unsigned)((plane + 127) / 128), nz / ProjectK<Dyn, KM>::kZ);
   return emit<ProjectK<Dyn, KM>>(s, ProjectK<Dyn, KM>::make(c->f.u, c->f.v, c->f.w, c->f.p, c->phi, c->gc, nx, ny, nz,
                                                             c->stepk + q, c->stepk_h[q], k >= 0 ? 1 : 0, c->bl,
                                                             1.0 / (c->dx * c->dx), 1.0 / (c->dz * c->dz)),
