@@ -70,3 +70,52 @@ def test_pressure_update_option_checked_without_gpu(libpath, pu, ok):
     case, *_ = I.small_channel(32, 12, 16)
     case.pressure_update = pu
     assert (B.ns_workspace_bytes(B.make_config(case)) > 0) == ok
+
+
+def test_null_handles_are_rejected_without_gpu(libpath):
+    """Every entry point checks its context (or batch) handle before any device call: a NULL
+    handle returns NS_ERR_ARG, and the query / teardown calls accept it."""
+    L = B.lib()
+    E = B.NS_ERR_ARG
+    null = None
+    for name, args in [("ns_rhs", (0,)), ("ns_adi_sweep", (0, 0)), ("ns_poisson_solve", (0,)),
+                       ("ns_project", (0,)), ("ns_substep", (0,)), ("ns_make_divergence_free", ()),
+                       ("ns_step", (1,)), ("ns_set_dt", (1e-3,)), ("ns_step_cfl", (1, 0.5, None)),
+                       ("ns_set_partition", (0, 8, 0)), ("ns_set_partition", (1, 0, 0)),
+                       ("ns_set_partition", (2, 0, 0)), ("ns_autotune", ()), ("ns_sync", ())]:
+        assert getattr(L, name)(null, *args) == E, name
+    P, mode, drop = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+    for d in (0, 1, 2):
+        assert L.ns_get_partition(null, d, ctypes.byref(P), ctypes.byref(mode), ctypes.byref(drop)) == E
+    rate = ctypes.c_double()
+    assert L.ns_convective_rate(null, ctypes.byref(rate)) == E
+    assert L.ns_batch_step(null, 1) == E
+    assert L.ns_batch_autotune(null) == E
+    assert L.ns_batch_set_partition(null, 0, 8, 0) == E
+    assert L.ns_batch_sync(null) == E
+    assert L.ns_batch_launches_per_step(null) == 0
+    assert L.ns_batch_instance(null, 0) is None
+    L.ns_destroy(null)
+    L.ns_batch_destroy(null)
+
+
+def test_traffic_record_is_dropped_when_its_kernel_source_changes(tmp_path, monkeypatch):
+    """bench.py reports an ncu traffic figure only while the kernel source it was captured from
+    is unchanged (the committed hash); otherwise the roofline's traffic is null."""
+    import hashlib
+    import json
+    import sys
+    sys.path.insert(0, ROOT)
+    import bench
+    src = tmp_path / "k.cu"
+    src.write_text("__global__ void k() {}\n")
+    (tmp_path / "profiles").mkdir()
+    rec = {"rhs": {"bytes_per_launch": 123.0, "source": "k.cu",
+                   "source_sha256_16": hashlib.sha256(src.read_bytes()).hexdigest()[:16]}}
+    (tmp_path / "profiles" / "traffic_w.json").write_text(json.dumps(rec))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.load_traffic("w", "rhs") == 123.0
+    assert bench.load_traffic("w", "adi_x") is None
+    assert bench.load_traffic("missing", "rhs") is None
+    src.write_text("__global__ void k() { }\n")
+    assert bench.load_traffic("w", "rhs") is None
