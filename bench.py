@@ -113,6 +113,20 @@ def load_traffic(workload, kernel):
         return None
 
 
+def host_cpu():
+    """The host CPU's model name from /proc/cpuinfo, else its architecture."""
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                key, _, val = line.partition(":")
+                if key.strip().lower() == "model name" and val.strip():
+                    return val.strip()
+    except OSError:
+        pass
+    import platform
+    return platform.machine() or "unknown"
+
+
 def max_over_ranks(torch, dist, seconds, device="cpu"):
     """The slowest rank's time: every rank passes its own, every rank gets the maximum.  With
     dist None (one process) it is the time itself."""
@@ -367,7 +381,8 @@ def main():
                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
                "data": "synthetic (seeded Re_tau 395 log-law channel field)", "config": config,
-               "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+               "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "cpu": host_cpu(), "kind": "oracle",
+                                "sample": sample},
                "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
                "gpu_launches": 0, "wall_s": time.perf_counter() - t_all0}
         print(json.dumps(out))
@@ -378,7 +393,7 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         F = 8
         val, t = oracle_baseline(case, u0, v0, w0, p0, F, 3)
-        cpu = {"value": val, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+        cpu = {"value": val, "unit": UNIT, "cores": os.cpu_count(), "cpu": host_cpu(), "kind": "oracle",
                "sample": "one RK3 step (3 sub-steps) of the FP64 numpy oracle on 1/%d of every stage's lines "
                          "and cells of this workload (full line lengths), scaled by %d; %.1f s" % (F, F, t)}
 
