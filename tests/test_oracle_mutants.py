@@ -1,0 +1,127 @@
+"""The oracle's pins catch plausible mistakes: each mutant below plants one (a dropped term, a
+wrong sign, index or constant, a transposed operand) in a copy of the oracle, and the pin tests
+that cover that part, run on the copy, must fail.  The copies live in a temporary directory; the
+oracle itself is never modified.  The mutants run as parallel subprocesses."""
+import os
+import shutil
+import subprocess
+import sys
+from concurrent.futures import ThreadPoolExecutor
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+ORACLE = os.path.join(ROOT, "oracle", "ns_oracle.py")
+
+CORE = ["tests/test_oracle_tridiag.py", "tests/test_oracle_ops.py", "tests/test_oracle_step.py"]
+BL = ["tests/test_oracle_bl.py"]
+CFL = ["tests/test_oracle_cfl.py"]
+RCY = ["tests/test_oracle_recycle.py"]
+
+# name: (text in the oracle, replacement, pin files)
+MUTANTS = {
+    # RK3, interpolation, stencils, grid metrics
+    "zeta_sign": ("RK3_ZETA = (0.0, -17.0 / 60.0, -5.0 / 12.0)", "RK3_ZETA = (0.0, 17.0 / 60.0, -5.0 / 12.0)", CORE),
+    "gamma_value": ("RK3_GAMMA = (8.0 / 15.0, 5.0 / 12.0, 3.0 / 4.0)", "RK3_GAMMA = (8.0 / 15.0, 5.0 / 12.0, 2.0 / 3.0)", CORE),
+    "interp_swap": ("wlo = 1.0 - whi ", "wlo = whi; whi = 1.0 - wlo ", CORE),
+    "wall_hm": ("hm[0] = g.yc[0] - g.yf[0]", "hm[0] = g.hc[0]", CORE),
+    "grad_y_index": ("(p[:, 1:, :] - p[:, :-1, :]) / g.hc[None, :, None]",
+                     "(p[:, 1:, :] - p[:, :-1, :]) / g.dy[None, 1:, None]", CORE),
+    "nuz_sign": ("nuz = (_zp(fuw) - fuw) / dz", "nuz = (fuw - _zm(fuw)) / dz", CORE),
+    "nvx_shift": ("nvx = (_xp(fuv) - fuv) / dx", "nvx = (fuv - _xm(fuv)) / dx", CORE),
+    # ADI, tridiagonal solvers, partitioned solve
+    "beta_factor": ("beta = RK3_ALPHA[k] * dt * inv_re / 2.0", "beta = RK3_ALPHA[k] * dt * inv_re", CORE),
+    "thomas_back_index": ("x[..., j] = dp[..., j] - cp[..., j] * x[..., j + 1]",
+                          "x[..., j] = dp[..., j] - cp[..., j + 1] * x[..., j + 1]", CORE),
+    "cyclic_corner": ("bb[..., n - 1] = b[..., n - 1] - alpha * beta / gam",
+                      "bb[..., n - 1] = b[..., n - 1] - alpha * beta * gam", CORE),
+    "ppt_perm": ("Zbar = P + E.T @ Ybar", "Zbar = np.eye(len(P)) + E.T @ Ybar", CORE),
+    # Poisson and projection
+    "dft_sign": ("return np.exp(sign * 2j * math.pi * np.outer(k, k) / n)",
+                 "return np.exp(-sign * 2j * math.pi * np.outer(k, k) / n)", CORE),
+    "pois_c": ("c[:-1] = 1.0 / (g.dy[:-1] * g.hc)", "c[:-1] = 1.0 / (g.dy[1:] * g.hc)", CORE),
+    "wavenumber_period": ("return (2.0 / (h * h)) * (1.0 - np.cos(2.0 * math.pi * l / n))",
+                          "return (2.0 / (h * h)) * (1.0 - np.cos(math.pi * l / n))", CORE),
+    "project_sign": ("    return u - scale * gx, v - scale * gy, w - scale * gz\n\n\ndef ",
+                     "    return u + scale * gx, v - scale * gy, w - scale * gz\n\n\ndef ", CORE),
+    # inflow / convective outflow
+    "ghost_coef": ("return np.concatenate([f[:, :, 1:], (2.0 * f_out - f[:, :, -1])[:, :, None]], axis=2)",
+                   "return np.concatenate([f[:, :, 1:], (1.0 * f_out)[:, :, None]], axis=2)", BL),
+    "adi_3r": ("        b[0] = 1.0 + 3.0 * r\n        b[-1] = 1.0 + 3.0 * r",
+               "        b[0] = 1.0 + 2.0 * r\n        b[-1] = 1.0 + 3.0 * r", BL),
+    "adi_inc2r": ("d[:, :, -1] += (r if comp == 0 else 2.0 * r) * inc_out", "d[:, :, -1] += r * inc_out", BL),
+    "dct_inv": ("    C[:, 1:] *= 2.0\n", "    C[:, 1:] *= 1.0\n", BL),
+    "lam_bl": ("lx = (2.0 / (g.dx * g.dx)) * (1.0 - np.cos(math.pi * np.arange(g.nx) / g.nx))",
+               "lx = (2.0 / (g.dx * g.dx)) * (1.0 - np.cos(2 * math.pi * np.arange(g.nx) / g.nx))", BL),
+    "flux_area": ("return u_out + (q_in - q_out) / area", "return u_out + (q_in - q_out) / (2 * area)", BL),
+    "fuv_out": ('fuv_out = uo_yf * bl["v_out"]', 'fuv_out = uo_yf * bl["v_in"]', BL),
+    # fixed-CFL rate and the Kim-Moin update
+    "rate_vface": ("vc = 0.5 * (v[:, :-1, :] + v[:, 1:, :])\n    c = np.abs(u) * (1.0 / g.dx)",
+                   "vc = v[:, :-1, :]\n    c = np.abs(u) * (1.0 / g.dx)", CFL),
+    "rate_dz": ("np.abs(w) * (1.0 / g.dz)\n    return float(c.max())", "np.abs(w) * (1.0 / g.dx)\n    return float(c.max())", CFL),
+    "rate_noabs": ("c = np.abs(u) * (1.0 / g.dx)", "c = u * (1.0 / g.dx)", CFL),
+    "km_sign": ("return p + phi - beta * lap_phi", "return p + phi + beta * lap_phi", CFL),
+    "km_beta2": ("return p + phi - beta * lap_phi", "return p + phi - 2.0 * beta * lap_phi", CFL),
+    # recycling inflow
+    "lund_b": ("def lund_weight(eta, a=4.0, b=0.2):", "def lund_weight(eta, a=4.0, b=0.3):", RCY),
+    "inner_outer_swap": ("    Ui = gamma * sample_c(U[None, :], gamma * yc)\n    Uo = gamma * sample_c(U[None, :], r * yc) + (1.0 - gamma) * u_inf",
+                         "    Ui = gamma * sample_c(U[None, :], r * yc)\n    Uo = gamma * sample_c(U[None, :], gamma * yc) + (1.0 - gamma) * u_inf", RCY),
+    "outer_defect": ("+ (1.0 - gamma) * u_inf\n    ui =", "+ (gamma - 1.0) * u_inf\n    ui =", RCY),
+    "fluct_nogamma": ("    uo = gamma * sample_c(up, r * yc)\n", "    uo = sample_c(up, r * yc)\n", RCY),
+    "w_mean_kept": ("    wp = w_r - Wm[None, :]\n", "    wp = w_r + 0.0 * Wm[None, :]\n", RCY),
+    "delta99_target": ("target = 0.99 * u_inf", "target = 0.95 * u_inf", RCY),
+    "gamma_exp": ("gamma = (delta_rec / delta_inl) ** 0.125", "gamma = (delta_rec / delta_inl) ** 0.1", RCY),
+    "recycle_v_avg": ("v_r = 0.5 * (v[:, :, i_r - 1] + v[:, :, i_r])", "v_r = v[:, :, i_r]", RCY),
+}
+
+
+def _copy_tree(dst):
+    """The oracle, the pin tests and the input generators (pure Python) in dst."""
+    shutil.copytree(os.path.join(ROOT, "oracle"), os.path.join(dst, "oracle"),
+                    ignore=shutil.ignore_patterns("__pycache__"))
+    os.makedirs(os.path.join(dst, "tests"))
+    for f in os.listdir(os.path.join(ROOT, "tests")):
+        if f in ("__init__.py", "conftest.py") or (f.startswith("test_oracle_") and f.endswith(".py")):
+            shutil.copy(os.path.join(ROOT, "tests", f), os.path.join(dst, "tests", f))
+    shutil.copytree(os.path.join(ROOT, "tests", "golden"), os.path.join(dst, "tests", "golden"))
+    os.makedirs(os.path.join(dst, "paper_1812_01178_gb300"))
+    for f in ("__init__.py", "inputs.py"):
+        shutil.copy(os.path.join(ROOT, "paper_1812_01178_gb300", f), os.path.join(dst, "paper_1812_01178_gb300", f))
+
+
+def _run(tmp, name):
+    a, b, files = MUTANTS[name]
+    d = os.path.join(tmp, name)
+    _copy_tree(d)
+    src = open(ORACLE).read()
+    open(os.path.join(d, "oracle", "ns_oracle.py"), "w").write(src.replace(a, b, 1))
+    env = dict(os.environ, PYTHONDONTWRITEBYTECODE="1", OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, "-m", "pytest", "-p", "no:cacheprovider", "-x", "-q", "-m", "not gpu"] + files,
+                       cwd=d, env=env, capture_output=True, text=True, timeout=600)
+    return name, r.returncode, (r.stdout.strip().splitlines() or [""])[-1]
+
+
+def test_every_mutant_text_is_in_the_oracle():
+    src = open(ORACLE).read()
+    for name, (a, b, _) in MUTANTS.items():
+        assert src.count(a) >= 1 and a != b, name
+
+
+def test_the_pins_catch_every_mutant(tmp_path):
+    names = list(MUTANTS)
+    with ThreadPoolExecutor(max_workers=max(2, min(len(names), os.cpu_count() or 2))) as ex:
+        results = list(ex.map(lambda n: _run(str(tmp_path), n), names))
+    missed = [(n, last) for n, rc, last in results if rc == 0]
+    assert not missed, missed
+    # exit code 1 = tests failed (not a collection or usage error)
+    errors = [(n, rc, last) for n, rc, last in results if rc not in (1,)]
+    assert not errors, errors
+
+
+def test_the_unmutated_copy_passes(tmp_path):
+    d = str(tmp_path / "clean")
+    _copy_tree(d)
+    r = subprocess.run([sys.executable, "-m", "pytest", "-p", "no:cacheprovider", "-x", "-q", "-m", "not gpu"]
+                       + CORE + BL + CFL + RCY, cwd=d, capture_output=True, text=True, timeout=600,
+                       env=dict(os.environ, PYTHONDONTWRITEBYTECODE="1"))
+    assert r.returncode == 0, r.stdout[-2000:]
