@@ -44,6 +44,24 @@ MUTANTS = {
                           "return (2.0 / (h * h)) * (1.0 - np.cos(math.pi * l / n))", CORE),
     "project_sign": ("    return u - scale * gx, v - scale * gy, w - scale * gz\n\n\ndef ",
                      "    return u + scale * gx, v - scale * gy, w - scale * gz\n\n\ndef ", CORE),
+    "conv_uc_neighbour": ("uc = 0.5 * (u + _xp(u))", "uc = 0.5 * (u + _xm(u))", CORE),
+    "conv_w_xface": ("w_xf = 0.5 * (_xm(w) + w)", "w_xf = w", CORE),
+    "conv_nvy_spacing": ("nvy[:, 1:-1, :] = (vc[:, 1:, :] ** 2 - vc[:, :-1, :] ** 2) / hc",
+                         "nvy[:, 1:-1, :] = (vc[:, 1:, :] ** 2 - vc[:, :-1, :] ** 2) / dy[:, 1:, :]", CORE),
+    "div_z_shift": ("+ (_zp(w) - w) / g.dz)", "+ (w - _zm(w)) / g.dz)", CORE),
+    "dxx_centre": ("return (_xp(f) - 2.0 * f + _xm(f)) / (g.dx * g.dx)", "return (_xp(f) - 1.0 * f + _xm(f)) / (g.dx * g.dx)", CORE),
+    "yrows_A": ("    A = 2.0 / (hm * (hm + hp))\n    C = 2.0 / (hp * (hm + hp))\n    if g.ytop",
+                "    A = 2.0 / (hp * (hm + hp))\n    C = 2.0 / (hp * (hm + hp))\n    if g.ytop", CORE),
+    "stress_free_top": ("    if g.ytop == 1:\n        C[-1] = 0.0", "    if g.ytop == 1:\n        C[-1] = C[-1]", CORE),
+    "rhs_force_coef": ("t = t + alp * fx", "t = t + gam * fx", CORE),
+    "rhs_visc_half": ("(alp * inv_re) * L[comp]", "(alp * inv_re / 2.0) * L[comp]", CORE),
+    "rhs_pgrad_sign": ("t = -gam * N[comp] - alp * G[comp]", "t = -gam * N[comp] + alp * G[comp]", CORE),
+    "pdd_block_offdiag": ("Zb[r:r + 2, r:r + 2] = Z[r:r + 2, r:r + 2]",
+                          "Zb[r, r] = Z[r, r]; Zb[r + 1, r + 1] = Z[r + 1, r + 1]", CORE),
+    "poisson_scale": ("phi = poisson_solve(g, divergence(g, us, vs, ws) / scale)",
+                      "phi = poisson_solve(g, divergence(g, us, vs, ws) * scale)", CORE),
+    "pois_a": ("a[1:] = 1.0 / (g.dy[1:] * g.hc)", "a[1:] = 1.0 / (g.dy[:-1] * g.hc)", CORE),
+    "adi_x_spacing": ("h = g.dx if direction == 0 else g.dz", "h = g.dz if direction == 0 else g.dz", CORE),
     # inflow / convective outflow
     "ghost_coef": ("return np.concatenate([f[:, :, 1:], (2.0 * f_out - f[:, :, -1])[:, :, None]], axis=2)",
                    "return np.concatenate([f[:, :, 1:], (1.0 * f_out)[:, :, None]], axis=2)", BL),
