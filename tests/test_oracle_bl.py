@@ -166,3 +166,31 @@ def test_bl_convection_telescopes_to_boundary_fluxes():
     expect_w = g.dz * (g.dy[None, :] * flux_w).sum()
     got_w = (Nw * g.dy[None, :, None]).sum() * g.dx * g.dz
     assert abs(got_w - expect_w) < 1e-12 * np.abs(Nw).sum() * g.dx * g.dz * 10
+
+
+def test_outflow_update_advects_a_linear_profile_exactly():
+    """The convective outflow condition df/dt + U_c df/dx = 0 (Sec. 2.1), one upwind step of
+    alpha_k dt: for a field linear in x the one-sided difference between the outflow plane
+    (x = Lx) and the last interior point is the exact slope, whatever their distance (dx from the
+    last u face, dx/2 from the last v, w centre), so each plane moves by exactly -U_c (alpha dt)
+    slope.  The wall rows of v stay zero."""
+    g = _grid()
+    a, b = 0.3, -0.7
+    xf = np.arange(g.nx) * g.dx             # u faces 0..nx-1 (face 0 the inflow)
+    xc = (np.arange(g.nx) + 0.5) * g.dx     # centres
+    lx = g.nx * g.dx
+    u = np.broadcast_to(a + b * xf, (g.nz, g.ny, g.nx)).copy()
+    v = np.broadcast_to(a + b * xc, (g.nz, g.ny + 1, g.nx)).copy()
+    w = np.broadcast_to(a + b * xc, (g.nz, g.ny, g.nx)).copy()
+    bl = dict(u_out=np.full((g.nz, g.ny), a + b * lx), v_out=np.full((g.nz, g.ny + 1), a + b * lx),
+              w_out=np.full((g.nz, g.ny), a + b * lx), v_in=np.zeros((g.nz, g.ny + 1)),
+              w_in=np.zeros((g.nz, g.ny)))
+    scale, uc = 0.013, 1.3
+    new, inc = O.outflow_update(g, u, v, w, bl, scale, uc)
+    want = a + b * lx - uc * scale * b
+    np.testing.assert_allclose(new["u_out"], want, rtol=0, atol=1e-14)
+    np.testing.assert_allclose(new["w_out"], want, rtol=0, atol=1e-14)
+    np.testing.assert_allclose(new["v_out"][:, 1:-1], want, rtol=0, atol=1e-14)
+    assert np.all(new["v_out"][:, 0] == 0) and np.all(new["v_out"][:, -1] == 0)
+    for q in ("u_out", "v_out", "w_out"):
+        np.testing.assert_array_equal(inc[q], new[q] - bl[q])

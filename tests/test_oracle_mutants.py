@@ -73,6 +73,15 @@ MUTANTS = {
                "lx = (2.0 / (g.dx * g.dx)) * (1.0 - np.cos(2 * math.pi * np.arange(g.nx) / g.nx))", BL),
     "flux_area": ("return u_out + (q_in - q_out) / area", "return u_out + (q_in - q_out) / (2 * area)", BL),
     "fuv_out": ('fuv_out = uo_yf * bl["v_out"]', 'fuv_out = uo_yf * bl["v_in"]', BL),
+    "inflow_ghost": ("return np.concatenate([(2.0 * f_in - f[:, :, 0])[:, :, None], f[:, :, :-1]], axis=2)",
+                     "return np.concatenate([(1.0 * f_in)[:, :, None], f[:, :, :-1]], axis=2)", BL),
+    "outflow_u_next": ('return np.concatenate([u[:, :, 1:], bl["u_out"][:, :, None]], axis=2)',
+                       'return np.concatenate([u[:, :, 1:], u[:, :, -1:]], axis=2)', BL),
+    "outflow_v_spacing": ('new["v_out"] = bl["v_out"] - c * (bl["v_out"] - v[:, :, -1]) / (0.5 * g.dx)',
+                          'new["v_out"] = bl["v_out"] - c * (bl["v_out"] - v[:, :, -1]) / g.dx', BL),
+    "outflow_upwind_sign": ('new["u_out"] = bl["u_out"] - c * (bl["u_out"] - u[:, :, -1]) / g.dx',
+                            'new["u_out"] = bl["u_out"] + c * (bl["u_out"] - u[:, :, -1]) / g.dx', BL),
+    "inflow_row_identity": ("        a[0], b[0], c[0] = 0.0, 1.0, 0.0\n", "        a[0], b[0], c[0] = 0.0, 1.0, -r\n", BL),
     # fixed-CFL rate and the Kim-Moin update
     "rate_vface": ("vc = 0.5 * (v[:, :-1, :] + v[:, 1:, :])\n    c = np.abs(u) * (1.0 / g.dx)",
                    "vc = v[:, :-1, :]\n    c = np.abs(u) * (1.0 / g.dx)", CFL),
