@@ -194,3 +194,79 @@ def test_outflow_update_advects_a_linear_profile_exactly():
     assert np.all(new["v_out"][:, 0] == 0) and np.all(new["v_out"][:, -1] == 0)
     for q in ("u_out", "v_out", "w_out"):
         np.testing.assert_array_equal(inc[q], new[q] - bl[q])
+
+
+def test_divergence_telescopes_to_the_boundary_fluxes():
+    """Discrete Gauss theorem: the volume sum of D u equals the net flux through the boundary,
+    the outflow plane u_out at x = Lx minus the inflow face u_0 at x = 0 (periodic z, v = 0 on
+    the walls of a channel-like box here, so only x contributes besides the y faces given)."""
+    g = _grid(12, 7, 6)
+    u, v, w, bl = _fields(g, 5)
+    d = O.divergence_bl(g, u, v, w, bl)
+    vol = g.dx * g.dy[None, :, None] * g.dz
+    wy = g.dy[None, :] * g.dz
+    net = ((bl["u_out"] - u[:, :, 0]) * wy).sum() + ((v[:, -1, :] - v[:, 0, :]) * g.dx * g.dz).sum()
+    assert abs((d * vol).sum() - net) < 1e-12 * np.abs(u).sum()
+
+
+def test_step_from_unbalanced_outflow_keeps_divergence_and_inflow():
+    """Sub-steps from a random field that is neither solenoidal nor mass-balanced: the outflow flux
+    correction makes the Poisson problem compatible, so every sub-step ends divergence-free to
+    round-off with the outflow flux equal to the inflow flux.  The inflow face of u stays fixed
+    (a Dirichlet condition) even under a body force."""
+    g = _grid(16, 10, 8)
+    u, v, w, bl = _fields(g, 9, amp=0.5)  # not projected: the first sub-step must balance it
+    p = np.zeros_like(u)
+    s = dict(u=u, v=v, w=w, p=p, bl=bl)
+    wgt = g.dy[None, :] * g.dz
+    for k in range(3):
+        s = O.substep_bl(g, s, k, 2e-3, 50.0, 0.7, 1.0)
+        assert np.abs(O.divergence_bl(g, s["u"], s["v"], s["w"], s["bl"])).max() < 1e-10
+        assert abs((s["u"][:, :, 0] * wgt).sum() - (s["bl"]["u_out"] * wgt).sum()) < 1e-11
+        assert np.array_equal(s["u"][:, :, 0], u[:, :, 0])
+
+
+def test_viscous_operator_with_ghosts_is_exact_for_linear_x_profiles():
+    """The inflow / outflow ghosts (2 f_in - f_0, 2 f_out - f_{nx-1}) extrapolate linearly, so the
+    x second difference vanishes on fields linear in x: for f = (a + b x) phi(y), the viscous
+    operator equals (a + b x) / a times its value on a phi(y), cell by cell, for u, v and w."""
+    g = _grid(12, 7, 4)
+    rng = np.random.default_rng(3)
+    pc = rng.standard_normal(g.ny)
+    pf = rng.standard_normal(g.ny + 1)
+    pf[0] = pf[-1] = 0.0
+    xf = np.arange(g.nx) * g.dx
+    xc = (np.arange(g.nx) + 0.5) * g.dx
+    lx = g.nx * g.dx
+
+    def fields(a, b):
+        u = np.broadcast_to((a + b * xf)[None, None, :] * pc[None, :, None], (g.nz, g.ny, g.nx)).copy()
+        v = np.broadcast_to((a + b * xc)[None, None, :] * pf[None, :, None], (g.nz, g.ny + 1, g.nx)).copy()
+        w = np.broadcast_to((a + b * xc)[None, None, :] * pc[None, :, None], (g.nz, g.ny, g.nx)).copy()
+        bl = dict(u_out=np.broadcast_to((a + b * lx) * pc, (g.nz, g.ny)).copy(),
+                  v_in=np.broadcast_to(a * pf, (g.nz, g.ny + 1)).copy(),
+                  v_out=np.broadcast_to((a + b * lx) * pf, (g.nz, g.ny + 1)).copy(),
+                  w_in=np.broadcast_to(a * pc, (g.nz, g.ny)).copy(),
+                  w_out=np.broadcast_to((a + b * lx) * pc, (g.nz, g.ny)).copy())
+        return u, v, w, bl
+
+    a, b = 1.5, -0.4
+    L1 = O.laplacian_bl(g, *fields(a, b))
+    L0 = O.laplacian_bl(g, *fields(a, 0.0))
+    for comp, x in ((0, xf), (1, xc), (2, xc)):
+        want = ((a + b * x) / a)[None, None, :] * L0[comp]
+        if comp == 0:
+            want[:, :, 0] = 0.0  # the inflow face of u takes no viscous term
+        np.testing.assert_allclose(L1[comp], want, rtol=0, atol=1e-10 * np.abs(L0[comp]).max())
+
+
+@pytest.mark.parametrize("bl", [False, True])
+def test_poisson_gauge_zero_mean_on_the_first_row(bl):
+    """The singular (kx, kz) = (0, 0) mode is gauged by phi_hat(j = 0) = 0: the solution's mean
+    over the first y row of cells is zero."""
+    g = _grid(8, 6, 4)
+    rng = np.random.default_rng(4)
+    rhs = rng.standard_normal((g.nz, g.ny, g.nx))
+    rhs -= (rhs * g.dy[None, :, None]).sum() / (g.dy.sum() * g.nx * g.nz)  # compatible
+    phi = O.poisson_solve_bl(g, rhs) if bl else O.poisson_solve(g, rhs)
+    assert abs(phi[:, 0, :].mean()) < 1e-12 * np.abs(phi).max()

@@ -82,6 +82,19 @@ MUTANTS = {
     "outflow_upwind_sign": ('new["u_out"] = bl["u_out"] - c * (bl["u_out"] - u[:, :, -1]) / g.dx',
                             'new["u_out"] = bl["u_out"] + c * (bl["u_out"] - u[:, :, -1]) / g.dx', BL),
     "inflow_row_identity": ("        a[0], b[0], c[0] = 0.0, 1.0, 0.0\n", "        a[0], b[0], c[0] = 0.0, 1.0, -r\n", BL),
+    "bl_v_xface": ('v_xf = 0.5 * (_xprev_c(v, bl["v_in"]) + v)', 'v_xf = 0.5 * (_xm(v) + v)', BL),
+    "bl_fuw_out": ('fuw_out = uo_zf * bl["w_out"]', 'fuw_out = uo_zf * bl["w_in"]', BL),
+    "bl_grad_inflow": ("    gx[:, :, 0] = 0.0\n    gy = np.zeros((g.nz, g.ny + 1, g.nx))\n    gy[:, 1:-1, :] = (p[:, 1:, :] - p[:, :-1, :]) / g.hc[None, :, None]\n    gz = (p - _zm(p)) / g.dz\n    return gx, gy, gz\n\n\ndef divergence_bl",
+                       "    gx[:, :, 0] = gx[:, :, 0]\n    gy = np.zeros((g.nz, g.ny + 1, g.nx))\n    gy[:, 1:-1, :] = (p[:, 1:, :] - p[:, :-1, :]) / g.hc[None, :, None]\n    gz = (p - _zm(p)) / g.dz\n    return gx, gy, gz\n\n\ndef divergence_bl", BL),
+    "bl_div_outflow": ("return ((_xnext_u(u, bl) - u) / g.dx", "return ((_xp(u) - u) / g.dx", BL),
+    "bl_lap_v_ghost": ('Lv = (_xnext_c(v, bl["v_out"]) - 2.0 * v + _xprev_c(v, bl["v_in"])) / h2',
+                       'Lv = (_xp(v) - 2.0 * v + _xprev_c(v, bl["v_in"])) / h2', BL),
+    "bl_rhs_inflow_r": ("        if comp == 0:\n            t[:, :, 0] = 0.0\n", "        if comp == 0:\n            t[:, :, 0] = t[:, :, 0]\n", BL),
+    "bl_flux_weights": ("w = g.dy[None, :] * g.dz\n", "w = g.dz\n", BL),
+    "bl_flux_before_poisson": ('    bl_new["u_out"] = flux_correct_outflow(g, u[:, :, 0], bl_new["u_out"])\n    phi = poisson_solve_bl',
+                               '    phi = poisson_solve_bl', BL),
+    "bl_ycoeff_gauge": ("    B[0, 0, 0] = 1.0\n    C[0, 0, 0] = 0.0\n    d = d.copy()\n    d[0, 0, 0] = 0.0\n    ph = np.moveaxis(thomas(A, B, C, d), -1, 1)\n    ph = dft(ph, 0, +1) / g.nz",
+                        "    B[0, 0, 0] = 1.0\n    C[0, 0, 0] = 0.0\n    d = d.copy()\n    ph = np.moveaxis(thomas(A, B, C, d), -1, 1)\n    ph = dft(ph, 0, +1) / g.nz", BL),
     # fixed-CFL rate and the Kim-Moin update
     "rate_vface": ("vc = 0.5 * (v[:, :-1, :] + v[:, 1:, :])\n    c = np.abs(u) * (1.0 / g.dx)",
                    "vc = v[:, :-1, :]\n    c = np.abs(u) * (1.0 / g.dx)", CFL),
