@@ -62,6 +62,12 @@ MUTANTS = {
                       "phi = poisson_solve(g, divergence(g, us, vs, ws) * scale)", CORE),
     "pois_a": ("a[1:] = 1.0 / (g.dy[1:] * g.hc)", "a[1:] = 1.0 / (g.dy[:-1] * g.hc)", CORE),
     "adi_x_spacing": ("h = g.dx if direction == 0 else g.dz", "h = g.dz if direction == 0 else g.dz", CORE),
+    "nprev_sign": ("t = t - zet * nprev[comp]\n        if comp == 0:\n            t = t + alp * fx\n        t = dt * t\n        if comp == 1:",
+                   "t = t + zet * nprev[comp]\n        if comp == 0:\n            t = t + alp * fx\n        t = dt * t\n        if comp == 1:", CORE),
+    "p_update_half": ("    if pressure == \"delta\":\n        return p + phi", "    if pressure == \"delta\":\n        return p + 0.5 * phi", CORE + CFL),
+    "projection_scale": ("    scale = RK3_ALPHA[k] * dt\n    phi = poisson_solve(g,", "    scale = RK3_GAMMA[k] * dt\n    phi = poisson_solve(g,", CORE + CFL),
+    "cyclic_fac_sign": ("fac = (y[..., 0] + beta / gam * y[..., n - 1])", "fac = (y[..., 0] - beta / gam * y[..., n - 1])", CORE),
+    "thomas_den": ("den = b[..., j] - a[..., j] * cp[..., j - 1]", "den = b[..., j] - c[..., j] * cp[..., j - 1]", CORE),
     # inflow / convective outflow
     "ghost_coef": ("return np.concatenate([f[:, :, 1:], (2.0 * f_out - f[:, :, -1])[:, :, None]], axis=2)",
                    "return np.concatenate([f[:, :, 1:], (1.0 * f_out)[:, :, None]], axis=2)", BL),
@@ -102,6 +108,10 @@ MUTANTS = {
     "rate_noabs": ("c = np.abs(u) * (1.0 / g.dx)", "c = u * (1.0 / g.dx)", CFL),
     "km_sign": ("return p + phi - beta * lap_phi", "return p + phi + beta * lap_phi", CFL),
     "km_beta2": ("return p + phi - beta * lap_phi", "return p + phi - 2.0 * beta * lap_phi", CFL),
+    "cfl_dt_frozen": ('dt = cfl / convective_rate(g, s["u"], s["v"], s["w"])',
+                      'dt = cfl / convective_rate(g, state["u"], state["v"], state["w"])', CFL),
+    "km_operator": ("lap = divergence(g, *gradient(g, phi)) if pressure != \"delta\" else None",
+                    "lap = laplacian(g, phi, phi, phi)[0] if pressure != \"delta\" else None", CFL),
     # recycling inflow
     "lund_b": ("def lund_weight(eta, a=4.0, b=0.2):", "def lund_weight(eta, a=4.0, b=0.3):", RCY),
     "inner_outer_swap": ("    Ui = gamma * sample_c(U[None, :], gamma * yc)\n    Uo = gamma * sample_c(U[None, :], r * yc) + (1.0 - gamma) * u_inf",

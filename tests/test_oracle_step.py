@@ -104,3 +104,27 @@ def test_divergence_after_each_substep():
         s = O.substep(g, s, k, case.dt, case.re, case.fx)
         d = O.divergence(g, s["u"], s["v"], s["w"])
         assert np.abs(d).max() < 1e-12
+
+
+@pytest.mark.parametrize("k", [1, 2])
+def test_an_irrotational_field_is_removed_and_becomes_pressure(k):
+    """Projection (Sec. 2.2): an intermediate field that is a discrete gradient, u* = G psi, is
+    removed completely by the projection u = u* - alpha_k dt G phi, and the pressure increment
+    is phi = psi / (alpha_k dt) up to a constant.  Driven through a whole inviscid sub-step from
+    u = eps G psi at rest otherwise (no force, no N_prev): the convection term is O(eps^2), so
+    the velocity left is O(eps^2) and p - mean(p) = eps (psi - mean(psi)) / (alpha_k dt) to
+    relative O(eps).  Sub-steps 1 and 2, where alpha_k differs from gamma_k."""
+    case, *_ = I.small_channel(16, 12, 8, seed=3)
+    g = O.Grid.from_case(case)
+    rng = np.random.default_rng(8)
+    psi = rng.standard_normal((g.nz, g.ny, g.nx))
+    eps, dt = 1e-6, 1e-2
+    gx, gy, gz = O.gradient(g, psi)
+    state = dict(u=eps * gx, v=eps * gy, w=eps * gz, p=np.zeros_like(psi),
+                 nprev=[np.zeros_like(gx), np.zeros_like(gy), np.zeros_like(gz)])
+    s = O.substep(g, state, k, dt, float("inf"), 0.0)
+    want = eps * (psi - psi.mean()) / (O.RK3_ALPHA[k] * dt)
+    got = s["p"] - s["p"].mean()
+    assert np.abs(got - want).max() < 1e-5 * np.abs(want).max()
+    for f in ("u", "v", "w"):
+        assert np.abs(s[f]).max() < 1e-4 * eps * np.abs(gx).max()
