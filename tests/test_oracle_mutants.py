@@ -122,6 +122,15 @@ MUTANTS = {
     "delta99_target": ("target = 0.99 * u_inf", "target = 0.95 * u_inf", RCY),
     "gamma_exp": ("gamma = (delta_rec / delta_inl) ** 0.125", "gamma = (delta_rec / delta_inl) ** 0.1", RCY),
     "recycle_v_avg": ("v_r = 0.5 * (v[:, :, i_r - 1] + v[:, :, i_r])", "v_r = v[:, :, i_r]", RCY),
+    "recycle_v_inner_scale": ("    vi = gamma * _interp_rows(gamma * yf, yf, vp)", "    vi = _interp_rows(gamma * yf, yf, vp)", RCY),
+    "recycle_v_outer_height": ("    Vo = _interp_rows(r * yf, yf, V[None, :])", "    Vo = _interp_rows(gamma * yf, yf, V[None, :])", RCY),
+    "recycle_blend_swap": ("        return (1.0 - wgt) * inner + wgt * outer", "        return wgt * inner + (1.0 - wgt) * outer", RCY),
+    "recycle_blend_eta": ("        wgt = lund_weight(y / delta_inl)[None, :]", "        wgt = lund_weight(y / delta_rec)[None, :]", RCY),
+    "recycle_wall_sample": ("        z1 = np.zeros((f2d.shape[0], 1))", "        z1 = f2d[:, :1]", RCY),
+    "recycle_w_avg": ("w_r = 0.5 * (w[:, :, i_r - 1] + w[:, :, i_r])", "w_r = w[:, :, i_r]", RCY),
+    "delta99_interp": ("return yc[j - 1] + (target - U[j - 1]) * (yc[j] - yc[j - 1]) / (U[j] - U[j - 1])",
+                       "return yc[j - 1] + (target - U[j - 1]) * (yc[j] - yc[j - 1]) / U[j]", RCY),
+    "lund_weight_top": ("    return np.where(eta > 1.0, 1.0, wgt)", "    return wgt", RCY),
 }
 
 

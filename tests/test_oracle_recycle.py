@@ -38,16 +38,18 @@ def test_identity_when_the_thicknesses_agree():
     np.testing.assert_allclose(wi, w_r - w_r.mean(axis=0), rtol=0, atol=1e-14)
 
 
-def test_linear_mean_profile_closed_form():
+@pytest.mark.parametrize("gamma,drec,dinl", [(1.03, 3.0, 2.4), (0.97, 2.0, 2.4)])
+def test_linear_mean_profile_closed_form(gamma, drec, dinl):
     """U_rec = a y, spanwise uniform (no fluctuations): linear interpolation is exact, so the inlet
     mean is (1 - W) gamma^2 a y + W (gamma a y delta_rec / delta_inl + 1 - gamma) in closed form
-    wherever the sampled heights stay below the top centre."""
+    wherever the sampled heights stay below the top centre.  With gamma < 1 and delta_rec <
+    delta_inl the rows nearest the wall sample below the first centre, between it and the wall
+    value U = 0 (no slip), where a y is still exact."""
     case, g, u, v, w, p, bl = _grid(ny=32)
     a = 0.05
     u_r = np.broadcast_to(a * g.yc, (g.nz, g.ny)).copy()
     v_r = np.zeros((g.nz, g.ny + 1))
     w_r = np.zeros((g.nz, g.ny))
-    gamma, drec, dinl = 1.03, 3.0, 2.4
     ui, vi, wi = O.rescale_inflow(g, u_r, v_r, w_r, gamma, drec, dinl)
     y = g.yc
     ok = (gamma * y <= g.yc[-1]) & (drec / dinl * y <= g.yc[-1])
@@ -130,3 +132,31 @@ def test_gamma_follows_the_power_law_in_x():
                     for k in range(g.nz)])
     gamma = float(np.dot(wi[:, j], src) / np.dot(src, src))
     assert gamma == pytest.approx((x_rec / x_in) ** 0.1, rel=2e-3)
+
+
+def test_v_mean_and_fluctuation_closed_form():
+    """v at the recycle face linear in y, v_r = (s + c_k) y with spanwise-zero-mean c_k: mean
+    V = s y, fluctuation c_k y.  The inner part samples at gamma y and scales the fluctuation by
+    gamma, the outer part samples at y delta_rec / delta_inl, mean V unscaled; so at the inlet
+    faces v = (1 - W)(s gamma y + gamma^2 c_k y) + W (s r y + gamma r c_k y), r = delta_rec /
+    delta_inl, wherever the sampled heights stay below the top face; wall and top rows 0."""
+    case, g, u, v, w, p, bl = _grid(ny=32)
+    rng = np.random.default_rng(5)
+    ck = rng.standard_normal(g.nz)
+    ck -= ck.mean()
+    sv = 0.02
+    yf = g.yf
+    v_r = (sv + ck)[:, None] * yf[None, :]
+    u_r = np.broadcast_to(0.05 * g.yc, (g.nz, g.ny)).copy()
+    w_r = np.zeros((g.nz, g.ny))
+    gamma, drec, dinl = 0.95, 2.0, 2.4
+    r = drec / dinl
+    ui, vi, wi = O.rescale_inflow(g, u_r, v_r, w_r, gamma, drec, dinl)
+    W = O.lund_weight(yf / dinl)[None, :]
+    y = yf[None, :]
+    c = ck[:, None]
+    expect = (1 - W) * (sv * gamma * y + gamma * gamma * c * y) + W * (sv * r * y + gamma * r * c * y)
+    rows = np.arange(1, g.ny)
+    ok = rows[(gamma * yf[rows] <= yf[-1]) & (r * yf[rows] <= yf[-1])]
+    np.testing.assert_allclose(vi[:, ok], expect[:, ok], rtol=0, atol=1e-14)
+    assert np.all(vi[:, 0] == 0) and np.all(vi[:, -1] == 0)
