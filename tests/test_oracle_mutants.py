@@ -122,6 +122,15 @@ MUTANTS = {
     "delta99_target": ("target = 0.99 * u_inf", "target = 0.95 * u_inf", RCY),
     "gamma_exp": ("gamma = (delta_rec / delta_inl) ** 0.125", "gamma = (delta_rec / delta_inl) ** 0.1", RCY),
     "recycle_v_avg": ("v_r = 0.5 * (v[:, :, i_r - 1] + v[:, :, i_r])", "v_r = v[:, :, i_r]", RCY),
+    "grid_hc": ("self.hc = self.yc[1:] - self.yc[:-1]", "self.hc = self.dy[1:]", CORE),
+    "grid_yc": ("self.yc = 0.5 * (self.yf[:-1] + self.yf[1:])", "self.yc = self.yf[:-1]", CORE),
+    "dense_cyclic_corner": ("        A[0, n - 1] = a[0]\n        A[n - 1, 0] = c[n - 1]", "        A[0, n - 1] = c[n - 1]\n        A[n - 1, 0] = a[0]", CORE),
+    "partition_first_row": ("        first = ((r + 1) % p) * m", "        first = (r + 1) * m - 1 if r + 1 < p else 0", CORE),
+    "partition_V_pairing": ("        V[first, 2 * r] = A[first, last]", "        V[first, 2 * r] = A[last, first]", CORE),
+    "swap_perm_identity": ("        P[r, r + 1] = 1.0\n        P[r + 1, r] = 1.0", "        P[r, r] = 1.0\n        P[r + 1, r + 1] = 1.0", CORE),
+    "adi_drops_z": ("        x = adi_sweep(g, r, 0, comp, beta)\n        x = adi_sweep(g, x, 1, comp, beta)\n        x = adi_sweep(g, x, 2, comp, beta)\n        out.append(x)\n    return out",
+                      "        x = adi_sweep(g, r, 0, comp, beta)\n        x = adi_sweep(g, x, 1, comp, beta)\n        out.append(x)\n    return out", CORE),
+    "volumes_v": ("hv[1:-1] = self.hc", "hv[1:-1] = self.dy[1:]", CORE),
     "recycle_v_inner_scale": ("    vi = gamma * _interp_rows(gamma * yf, yf, vp)", "    vi = _interp_rows(gamma * yf, yf, vp)", RCY),
     "recycle_v_outer_height": ("    Vo = _interp_rows(r * yf, yf, V[None, :])", "    Vo = _interp_rows(gamma * yf, yf, V[None, :])", RCY),
     "recycle_blend_swap": ("        return (1.0 - wgt) * inner + wgt * outer", "        return wgt * inner + (1.0 - wgt) * outer", RCY),
