@@ -131,6 +131,13 @@ MUTANTS = {
     "adi_drops_z": ("        x = adi_sweep(g, r, 0, comp, beta)\n        x = adi_sweep(g, x, 1, comp, beta)\n        x = adi_sweep(g, x, 2, comp, beta)\n        out.append(x)\n    return out",
                       "        x = adi_sweep(g, r, 0, comp, beta)\n        x = adi_sweep(g, x, 1, comp, beta)\n        out.append(x)\n    return out", CORE),
     "volumes_v": ("hv[1:-1] = self.hc", "hv[1:-1] = self.dy[1:]", CORE),
+    "yrows_face_C": ("    hp = g.dy[1:]\n    A = 2.0 / (hm * (hm + hp))\n    C = 2.0 / (hp * (hm + hp))",
+                     "    hp = g.dy[1:]\n    A = 2.0 / (hm * (hm + hp))\n    C = 2.0 / (hm * (hm + hp))", CORE),
+    "dyy_centre_shift": ("    fp[:, :-1, :] = f[:, 1:, :]", "    fp[:, :-1, :] = f[:, :-1, :]", CORE),
+    "dyy_face_shift": ("+ C[None, :, None] * f[:, 2:, :])", "+ C[None, :, None] * f[:, 1:-1, :])", CORE),
+    "pdd_drop_block": ("        Zo[r:r + 2, r:r + 2] = 0.0", "        Zo[r, r] = 0.0", CORE),
+    "dct2_half_shift": ("return np.cos(math.pi * l * (2 * i + 1) / (2 * n))", "return np.cos(math.pi * l * (2 * i) / (2 * n))", BL),
+    "recycle_not_applied": ("        u[:, :, 0] = u_in\n", "        u[:, :, 0] = u[:, :, 0]\n", RCY),
     "recycle_v_inner_scale": ("    vi = gamma * _interp_rows(gamma * yf, yf, vp)", "    vi = _interp_rows(gamma * yf, yf, vp)", RCY),
     "recycle_v_outer_height": ("    Vo = _interp_rows(r * yf, yf, V[None, :])", "    Vo = _interp_rows(gamma * yf, yf, V[None, :])", RCY),
     "recycle_blend_swap": ("        return (1.0 - wgt) * inner + wgt * outer", "        return wgt * inner + (1.0 - wgt) * outer", RCY),
