@@ -138,6 +138,14 @@ MUTANTS = {
     "pdd_drop_block": ("        Zo[r:r + 2, r:r + 2] = 0.0", "        Zo[r, r] = 0.0", CORE),
     "dct2_half_shift": ("return np.cos(math.pi * l * (2 * i + 1) / (2 * n))", "return np.cos(math.pi * l * (2 * i) / (2 * n))", BL),
     "recycle_not_applied": ("        u[:, :, 0] = u_in\n", "        u[:, :, 0] = u[:, :, 0]\n", RCY),
+    "periodic_gauge": ("    d[0, 0, 0] = 0.0\n    ph = thomas(A, B, C, d)\n    ph = np.moveaxis(ph, -1, 1)",
+                       "    ph = thomas(A, B, C, d)\n    ph = np.moveaxis(ph, -1, 1)", CORE + BL),
+    "step_two_substeps": ("    for _ in range(nsteps):\n        for k in range(3):\n            s = substep(g, s, k, dt, re, fx, pressure)",
+                          "    for _ in range(nsteps):\n        for k in range(2):\n            s = substep(g, s, k, dt, re, fx, pressure)", CORE),
+    "conv_fvw_no_interp": ("    fvw = v_zf * w_yf\n    nvz = (_zp(fvw) - fvw) / dz\n    Nv = nvx + nvy + nvz\n    Nv[:, 0, :] = 0.0\n    Nv[:, -1, :] = 0.0\n    # ---- Nw",
+                           "    fvw = v * w_yf\n    nvz = (_zp(fvw) - fvw) / dz\n    Nv = nvx + nvy + nvz\n    Nv[:, 0, :] = 0.0\n    Nv[:, -1, :] = 0.0\n    # ---- Nw", CORE),
+    "inverse_dft_norm": ("    phi = dft(dft(ph, 0, +1), 2, +1) / (g.nx * g.nz)", "    phi = dft(dft(ph, 0, +1), 2, +1) / g.nx", CORE),
+    "make_div_free_scale": ("    return project(g, u, v, w, phi, 1.0)", "    return project(g, u, v, w, phi, 0.5)", CORE),
     "recycle_v_inner_scale": ("    vi = gamma * _interp_rows(gamma * yf, yf, vp)", "    vi = _interp_rows(gamma * yf, yf, vp)", RCY),
     "recycle_v_outer_height": ("    Vo = _interp_rows(r * yf, yf, V[None, :])", "    Vo = _interp_rows(gamma * yf, yf, V[None, :])", RCY),
     "recycle_blend_swap": ("        return (1.0 - wgt) * inner + wgt * outer", "        return wgt * inner + (1.0 - wgt) * outer", RCY),
