@@ -391,7 +391,7 @@ def main():
     # cpu baseline first, in this process, before any CUDA work
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        F = 2  # half of every stage's lines: about 20 s on 16 host cores, arrays well beyond cache
+        F = 2  # half of every stage's lines: about 12 s on 16 host cores, arrays well beyond cache
         val, t = oracle_baseline(case, u0, v0, w0, p0, F, 3)
         cpu = {"value": val, "unit": UNIT, "cores": os.cpu_count(), "cpu": host_cpu(), "kind": "oracle",
                "sample": "one RK3 step (3 sub-steps) of the FP64 numpy oracle on 1/%d of every stage's lines "
