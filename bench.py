@@ -34,8 +34,11 @@ METRIC = "grid-point-steps/s at 1 GB300 (FP64 vs mixed) + % HBM roofline per swe
 UNIT = "grid-point-steps/s"
 
 # Algorithmic work per cell per launch of each kernel (FP64 path):
-# bytes = each input read once + each output written once; flops = floating-point operations of
-# the formulas (FMA = 2).  Complex spectral arrays have (nz/2+1)/nz of a cell each.
+# bytes = each input read once + each output written once; flops = the per-cell estimates of the
+# hot-path scope table (FMA = 2): RHS about 150, ADI about 5 per point per sweep for each of the
+# three components (plus the u* = u + delta add of the z sweep), FFTs 5 N log2 N per complex
+# transform of length N (2.5 log2 N per real point), the y solve about 10 per complex point, the
+# projection about 15.  Complex spectral arrays have (nz/2+1)/nz of a cell each.
 def kernel_model(nx, ny, nz, es):
     """(algorithmic bytes, flops) per cell of one launch of each stage.  es = 8: FP64 form, with the
     Poisson spectra in complex128.  es = 4: the mixed form, whose Poisson transforms run in FP32 on
@@ -46,10 +49,10 @@ def kernel_model(nx, ny, nz, es):
     L = lambda n: math.log2(n)
     m = {
         #                 bytes per cell                       flops per cell
-        "rhs":              (4 * 8 + 3 * es + 6 * es,        170.0),
-        "adi_x":            (6 * es,                         30.0),
+        "rhs":              (4 * 8 + 3 * es + 6 * es,        150.0),
+        "adi_x":            (6 * es,                         15.0),
         "adi_y":            (6 * es,                         15.0),
-        "adi_z":            (3 * es + 6 * 8,                 24.0),
+        "adi_z":            (3 * es + 6 * 8,                 18.0),
         "poisson_div_fftz": (3 * 8 + sh * 16,                9.0 + 2.5 * L(nz) + 2.0),
         "poisson_x_fwd":    (2 * sh * 16,                    sh * 5.0 * L(nx)),
         "poisson_tdma_y":   (3 * sh * 16,                    sh * 10.0),
@@ -60,7 +63,7 @@ def kernel_model(nx, ny, nz, es):
         "recycle":          (8 * 3.0 * 4 / nx,               40.0 / nx),
         "poisson_ifftz":    (sh * 16 + 8,                    2.5 * L(nz) + 2.0),
         "poisson_refine":   (0.0,                            0.0),
-        "project":          (8 + 8 * 8,                      11.0),
+        "project":          (8 + 8 * 8,                      15.0),
     }
     if es == 4:
         cs = 8  # complex64
@@ -87,18 +90,46 @@ def load_peaks():
         return 6800.0, "fallback", 2070.0
 
 
-# FP64 ALU peak from unit counts and clock: 152 SMs x 2 FP64 FMA/clk/SM x 2 flop x f_max.
+# FP64 ALU peak from unit counts and clock: 152 SMs x 2 FP64 FMA/clk/SM x 2 flop x f_max (the
+# fallback when the live measurement below is not available).
 def fp64_peak_tflops(sm_mhz):
     return 152 * 2 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def measure_fp64_peak(torch, B, dev, reps=5):
+    """FP64 FMA throughput (TFLOP/s) of this GPU: the library's probe kernel (8 independent FMA
+    chains per thread, 8 blocks of 256 threads per SM), best of `reps` launches, each timed with
+    CUDA events on the stream it runs on.  Returns (TFLOP/s, description)."""
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    nb, it = 8 * nsm, 4096
+    out = torch.empty(nb * 256, dtype=torch.float64, device=dev)
+    st = torch.cuda.Stream(dev)
+    flops = 16.0 * it * nb * 256
+    best = 0.0
+    with torch.cuda.stream(st):
+        B.ns_fp64_fma_probe(out.data_ptr(), nb, it, st.cuda_stream)  # warm-up
+        for _ in range(reps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            B.ns_fp64_fma_probe(out.data_ptr(), nb, it, st.cuda_stream)
+            e1.record(st)
+            e1.synchronize()
+            best = max(best, flops / (e0.elapsed_time(e1) * 1e-3) / 1e12)
+    if not bool(torch.isfinite(out).all()):
+        raise RuntimeError("FP64 probe produced non-finite values")
+    return best, ("measured live: ns_fp64_fma_probe, %d blocks x 256 threads x 8 chains x %d FMAs, best of %d "
+                  "(CUDA events)" % (nb, it, reps))
 
 
 def fp32_peak_tflops(sm_mhz):
     return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
 
 
-def load_traffic(workload, kernel):
-    """DRAM bytes per launch of `kernel` from the committed ncu capture of this workload, or None
-    if there is none or the kernel's source file changed since the counters were taken."""
+def load_traffic(workload, kernel, key="bytes_per_launch"):
+    """A counter figure of `kernel` from the committed ncu capture of this workload (DRAM bytes per
+    launch by default; "fp64_inst_per_cell": executed FP64 instructions per cell), or None if there
+    is none or the kernel's source file changed since the counters were taken."""
     import hashlib
     try:
         with open(os.path.join(ROOT, "profiles", "traffic_%s.json" % workload)) as fh:
@@ -108,7 +139,7 @@ def load_traffic(workload, kernel):
         with open(os.path.join(ROOT, rec["source"]), "rb") as fh:
             if hashlib.sha256(fh.read()).hexdigest()[:16] != rec["source_sha256_16"]:
                 return None
-        return rec["bytes_per_launch"]
+        return rec.get(key)
     except Exception:
         return None
 
@@ -409,6 +440,12 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
 
+    fp64_live = None
+    try:
+        fp64_live = measure_fp64_peak(torch, B, dev)
+    except Exception as exc:  # the derived figure stands in, and the line says so
+        sys.stderr.write("FP64 probe failed: %s\n" % exc)
+
     s = B.Solver(case, u0, v0, w0, p0, device=str(dev))
     s.make_divergence_free()
     s.step(args.warmup)
@@ -464,16 +501,25 @@ def main():
     b, f = model[top]
     per = kms[top] / launches
     fp64 = not (args.precision == "mixed" and top in ("rhs", "adi_x", "adi_y"))
-    alu_peak = (fp64_peak_tflops(smax) if fp64 else fp32_peak_tflops(smax)) * 1e12
+    if fp64 and fp64_live:
+        alu_peak, alu_src = fp64_live[0] * 1e12, fp64_live[1]
+    else:
+        alu_peak = (fp64_peak_tflops(smax) if fp64 else fp32_peak_tflops(smax)) * 1e12
+        alu_src = "derived: 152 SMs x %s FMA/clk/SM x 2 x %.0f MHz" % ("2 FP64" if fp64 else "128 FP32", smax)
     t_alu = f * cells / alu_peak
     t_mem = b * cells / (hbm * 1e9)
     traffic = load_traffic(config["workload"], top)
     if t_alu >= t_mem:
         ach = f * cells / (per * 1e-3) / 1e12
         roof = {"kernel": top, "bound": "alu", "achieved": ach, "peak": alu_peak / 1e12, "unit": "TFLOP/s",
-                "frac": ach / (alu_peak / 1e12), "traffic": traffic,
-                "peak_source": "derived: 152 SMs x %s FMA/clk/SM x 2 x %.0f MHz" % ("2 FP64" if fp64 else "128 FP32", smax),
-                "algorithmic_flops_per_launch": f * cells}
+                "frac": ach / (alu_peak / 1e12), "traffic": traffic, "peak_source": alu_src,
+                "algorithmic_flops_per_cell": f, "cells_per_launch": cells,
+                "algorithmic_flops_per_launch": f * cells, "ms_per_launch": per}
+        # executed FP64 instructions per cell (ncu opcode counters of the committed capture) against
+        # the pipe's instruction rate, which is half the FMA flop rate
+        ipc = load_traffic(config["workload"], top, "fp64_inst_per_cell") if fp64 else None
+        roof["fp64_inst_per_cell"] = ipc
+        roof["fp64_issue_frac"] = (ipc * cells / (per * 1e-3) / (alu_peak / 2.0)) if ipc else None
     else:
         ach = b * cells / (per * 1e-3) / 1e9
         roof = {"kernel": top, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
@@ -559,6 +605,7 @@ def main():
            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f64+f32",
            "data": "synthetic (seeded Re_tau 395 log-law channel field, 10% Gaussian fluctuations, projected)",
            "config": config, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+           "fp64_peak": ({"tflops": fp64_live[0], "source": fp64_live[1]} if fp64_live else None),
            "gpu_launches": len(kern) * 3 * args.steps, "clocks": ck, "mixed": mixed, "fixed_cfl": cflsec, "ensemble": ensemble,
            "kernels": {k: {kk: (round(vv, 4) if vv is not None else None) for kk, vv in d.items()}
                        for k, d in kern.items()}}

@@ -271,16 +271,19 @@ enum {
 ns_status ns_get_buffer(ns_ctx* ctx, int which, void** ptr, size_t* bytes);
 
 /* Context-free Poisson solve that allocates nothing (this entry point has no counterpart in the
- * paper; it serves callers that may not call cudaMalloc: code running while the host
- * application keeps a stream capture open, plugins inside a framework that owns all device
- * memory through its own pool, fixed-latency loops that must not allocate after start-up).
+ * paper).  It serves callers that may not call cudaMalloc: plugins inside a host framework that
+ * owns all device memory through its own pool allocator, and fixed-latency loops that must not
+ * allocate after start-up (an allocation can synchronise the device and take unbounded time).
  *
- * Computes the same phi as ns_poisson_solve(ctx, substep) for a context made from cfg (nx, ny,
- * nz, lx, lz, yf and, for substep >= 0, dt are used; bc_x must be 0): D G phi = D u / s with
- * s = alpha_k dt (substep k = 0, 1, 2) or s = 1 (substep = -1).  u, v, w: caller's device
- * arrays in the field layouts above (read); phi: caller's device array nz*ny*nx (written).
- * Work is enqueued on cuda_stream; the call first waits for that stream (it uploads small
- * coefficient tables from static host buffers).
+ * Computes the same phi as ns_poisson_solve(ctx, substep) for an NS_FP64 context made from cfg
+ * (nx, ny, nz, lx, lz, yf and, for substep >= 0, dt are used; bc_x must be 0): D G phi = D u / s
+ * with s = alpha_k dt (substep k = 0, 1, 2) or s = 1 (substep = -1).  The solve runs in FP64
+ * only: cfg->precision must be NS_FP64 (NS_MIXED gives NS_ERR_UNSUPPORTED, other values
+ * NS_ERR_ARG).  u, v, w: caller's device arrays in the field layouts above (read); phi: caller's
+ * device array nz*ny*nx (written); all four 256-byte aligned (else NS_ERR_ARG).
+ * Work goes on cuda_stream: the call queues the upload of small coefficient tables from static
+ * host buffers, then synchronises cuda_stream (so earlier work on that stream completes first and
+ * the host buffers may be reused), then queues the kernels and returns without waiting for them.
  *
  * Scratch: one file-scope device array of NS_STATIC_SCRATCH_BYTES, held by every GPU that loads
  * the library until the process exits.  A grid needing more (about 2 * 16 * (nz/2+1) * ny * nx
@@ -333,6 +336,16 @@ ns_ctx* ns_batch_instance(ns_batch* b, int i);
 ns_status ns_batch_sync(ns_batch* b);
 const char* ns_batch_last_error(ns_batch* b);
 void ns_batch_destroy(ns_batch* b);
+
+/* Measurement aid (no counterpart in the paper): the FP64 FMA throughput of this GPU, the
+ * denominator of the FP64-ALU roofline the solver's FP64 kernels are measured against.  Enqueues
+ * one kernel of n_blocks blocks of 256 threads on cuda_stream; every thread runs 8 independent
+ * chains of n_iter dependent FMAs (x = x * b + c), i.e. 16 * n_iter flops per thread, and writes
+ * the sum of its chains to out[block * 256 + thread] (caller's device array of n_blocks * 256
+ * doubles, written only).  Time it with CUDA events recorded on cuda_stream.  NS_ERR_ARG for a
+ * NULL out or n_blocks, n_iter < 1; NS_ERR_CUDA if the launch fails (message in
+ * ns_last_error(NULL) on the calling thread). */
+ns_status ns_fp64_fma_probe(double* out, int n_blocks, int n_iter, void* cuda_stream);
 
 /* Wait for all work on the context's stream; reports asynchronous CUDA errors. */
 ns_status ns_sync(ns_ctx* ctx);

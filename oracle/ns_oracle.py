@@ -594,14 +594,13 @@ def step(g, state, dt, re, fx, nsteps=1, pressure="delta"):
 # ----------------------------------------------------------------------------
 # Reading: the paper gives no formula for its CFL number.  Here it is the convective one,
 # dt max over cells of |u|/dx + |v_c|/dy_j + |w|/dz, with u and w the values on the cell's lower
-# x and z faces and v_c the average of its two y faces, each term formed as the magnitude times
-# the reciprocal spacing; dt is set before every step from the velocity at the start of the step
-# and held for the three sub-steps.
+# x and z faces and v_c the average of its two y faces; dt is set before every step from the
+# velocity at the start of the step and held for the three sub-steps.
 
 def convective_rate(g, u, v, w):
-    """max over cells of |u| (1/dx) + |v_c| (1/dy_j) + |w| (1/dz) (so that CFL = dt * rate)."""
+    """max over cells of |u|/dx + |v_c|/dy_j + |w|/dz (so that CFL = dt * rate)."""
     vc = 0.5 * (v[:, :-1, :] + v[:, 1:, :])
-    c = np.abs(u) * (1.0 / g.dx) + np.abs(vc) * (1.0 / g.dy)[None, :, None] + np.abs(w) * (1.0 / g.dz)
+    c = np.abs(u) / g.dx + np.abs(vc) / g.dy[None, :, None] + np.abs(w) / g.dz
     return float(c.max())
 
 
@@ -915,6 +914,10 @@ def step_bl(g, state, dt, re, fx, nsteps=1, u_conv=1.0, pressure="delta"):
 #   inflection point); no independent value of a is available.
 
 def lund_weight(eta, a=4.0, b=0.2):
+    """Weight W(eta) of the outer profile in the composite inflow of Lund, Wu & Squires
+    (J. Comput. Phys. 140, 1998): the tanh weighting function with which their rescaling blends
+    the inner and outer profiles, W(b) = 1/2 at eta = b, W = 1 above eta = 1.  a = 4 and b = 0.2
+    are the constants given with that function.  Parity unpinned for a (see the section header)."""
     eta = np.asarray(eta, dtype=np.float64)
     wgt = 0.5 * (1.0 + np.tanh(a * (eta - b) / ((1.0 - 2.0 * b) * eta + b)) / math.tanh(a))
     return np.where(eta > 1.0, 1.0, wgt)

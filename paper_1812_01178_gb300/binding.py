@@ -26,7 +26,7 @@ STATUS_NAMES = {0: "NS_OK", 1: "NS_ERR_ARG", 2: "NS_ERR_SIZE", 3: "NS_ERR_CUDA",
 # Every symbol declared in include/ns.h.
 EXPORTS = ["ns_workspace_bytes", "ns_init", "ns_rhs", "ns_adi_sweep", "ns_poisson_solve", "ns_project",
            "ns_substep", "ns_step", "ns_convective_rate", "ns_set_dt", "ns_step_cfl", "ns_step_profiled", "ns_kernel_count", "ns_kernel_name", "ns_step_host", "ns_make_divergence_free", "ns_set_partition",
-           "ns_get_partition", "ns_autotune", "ns_get_buffer", "ns_poisson_solve_static", "ns_sync",
+           "ns_get_partition", "ns_autotune", "ns_get_buffer", "ns_poisson_solve_static", "ns_fp64_fma_probe", "ns_sync",
            "ns_last_error", "ns_destroy", "ns_batch_workspace_bytes", "ns_batch_init", "ns_batch_step",
            "ns_batch_launches_per_step", "ns_batch_autotune", "ns_batch_set_partition", "ns_batch_instance",
            "ns_batch_sync", "ns_batch_last_error", "ns_batch_destroy"]
@@ -89,6 +89,7 @@ def lib(path: str = LIB_PATH):
     L.ns_autotune.argtypes = [vp]
     L.ns_get_buffer.argtypes = [vp, i, P(vp), P(sz)]
     L.ns_poisson_solve_static.argtypes = [P(ns_config), vp, vp, vp, vp, i, vp]
+    L.ns_fp64_fma_probe.argtypes = [vp, i, i, vp]
     L.ns_sync.argtypes = [vp]
     L.ns_last_error.argtypes = [vp]
     L.ns_last_error.restype = C.c_char_p
@@ -234,6 +235,13 @@ def ns_get_buffer(ctx, which):
 def ns_poisson_solve_static(cfg, u_ptr, v_ptr, w_ptr, phi_ptr, substep, stream_ptr):
     """Context-free Poisson solve with no device allocation (scratch in a static device array)."""
     s = lib().ns_poisson_solve_static(C.byref(cfg), u_ptr, v_ptr, w_ptr, phi_ptr, substep, stream_ptr)
+    if s != NS_OK:
+        raise NSError(s, lib().ns_last_error(None).decode())
+
+
+def ns_fp64_fma_probe(out_ptr, n_blocks, n_iter, stream_ptr):
+    """Enqueue the FP64 FMA throughput kernel: 16 * n_iter flops for each of n_blocks * 256 threads."""
+    s = lib().ns_fp64_fma_probe(out_ptr, n_blocks, n_iter, stream_ptr)
     if s != NS_OK:
         raise NSError(s, lib().ns_last_error(None).decode())
 

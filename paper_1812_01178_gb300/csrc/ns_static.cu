@@ -3,10 +3,10 @@
 // modified wavenumbers) lives in one file-scope __device__ array of NS_STATIC_SCRATCH_BYTES that
 // every GPU loading the library holds until the process exits.
 //
-// Some callers cannot call cudaMalloc: code that runs while the host application keeps a stream
-// capture open (allocation is not allowed then), plugins inside a host framework that owns all
-// device memory through its own pool, and fixed-latency loops that must not allocate after
-// start-up.  They pass only their inputs (u, v, w) and output (phi).
+// Some callers cannot call cudaMalloc: plugins inside a host framework that owns all device
+// memory through its own pool allocator, and fixed-latency loops that must not allocate after
+// start-up (an allocation can synchronise the device and take unbounded time).  They pass only
+// their inputs (u, v, w) and output (phi).  The solve is the FP64 one.
 //
 // The kernels are the library's own Poisson kernels; only where their scratch and tables live
 // differs.  Every call rewrites each scratch region it reads before reading it, so the contents
@@ -79,6 +79,11 @@ extern "C" ns_status ns_poisson_solve_static(const ns_config* cfg, const double*
       ny < 4 || ny > 1024)
     return fail(NS_ERR_SIZE, "nx, nz must be 2^a 3^b (a >= 3) in [8, 4096] and ny in [4, 1024]");
   if (cfg->bc_x != 0) return fail(NS_ERR_UNSUPPORTED, "only periodic x is built");
+  if (cfg->precision != NS_FP64)
+    return fail(cfg->precision == NS_MIXED ? NS_ERR_UNSUPPORTED : NS_ERR_ARG,
+                "the allocation-free solve runs in FP64 only: precision must be NS_FP64");
+  for (const void* q : {(const void*)u, (const void*)v, (const void*)w, (const void*)phi})
+    if ((size_t)q % 256) return fail(NS_ERR_ARG, "u, v, w and phi must be 256-byte aligned");
   if (substep < -1 || substep > 2) return fail(NS_ERR_ARG, "substep must be -1, 0, 1 or 2");
   if (!(cfg->lx > 0) || !(cfg->lz > 0) || (substep >= 0 && !(cfg->dt > 0)))
     return fail(NS_ERR_ARG, "lx, lz (and dt for substep >= 0) must be positive");

@@ -102,10 +102,10 @@ MUTANTS = {
     "bl_ycoeff_gauge": ("    B[0, 0, 0] = 1.0\n    C[0, 0, 0] = 0.0\n    d = d.copy()\n    d[0, 0, 0] = 0.0\n    ph = np.moveaxis(thomas(A, B, C, d), -1, 1)\n    ph = dft(ph, 0, +1) / g.nz",
                         "    B[0, 0, 0] = 1.0\n    C[0, 0, 0] = 0.0\n    d = d.copy()\n    ph = np.moveaxis(thomas(A, B, C, d), -1, 1)\n    ph = dft(ph, 0, +1) / g.nz", BL),
     # fixed-CFL rate and the Kim-Moin update
-    "rate_vface": ("vc = 0.5 * (v[:, :-1, :] + v[:, 1:, :])\n    c = np.abs(u) * (1.0 / g.dx)",
-                   "vc = v[:, :-1, :]\n    c = np.abs(u) * (1.0 / g.dx)", CFL),
-    "rate_dz": ("np.abs(w) * (1.0 / g.dz)\n    return float(c.max())", "np.abs(w) * (1.0 / g.dx)\n    return float(c.max())", CFL),
-    "rate_noabs": ("c = np.abs(u) * (1.0 / g.dx)", "c = u * (1.0 / g.dx)", CFL),
+    "rate_vface": ("vc = 0.5 * (v[:, :-1, :] + v[:, 1:, :])\n    c = np.abs(u) / g.dx",
+                   "vc = v[:, :-1, :]\n    c = np.abs(u) / g.dx", CFL),
+    "rate_dz": ("np.abs(w) / g.dz\n    return float(c.max())", "np.abs(w) / g.dx\n    return float(c.max())", CFL),
+    "rate_noabs": ("c = np.abs(u) / g.dx", "c = u / g.dx", CFL),
     "km_sign": ("return p + phi - beta * lap_phi", "return p + phi + beta * lap_phi", CFL),
     "km_beta2": ("return p + phi - beta * lap_phi", "return p + phi - 2.0 * beta * lap_phi", CFL),
     "cfl_dt_frozen": ('dt = cfl / convective_rate(g, s["u"], s["v"], s["w"])',
