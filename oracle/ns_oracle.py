@@ -39,6 +39,7 @@ Array layout: numpy shape (nz, ny, nx) with x fastest; v has ny+1 rows
 from __future__ import annotations
 
 import math
+
 import numpy as np
 
 # Low-storage RK3 (Sec. 2.2 names the scheme; constants are the standard set
@@ -257,26 +258,32 @@ def thomas(a, b, c, d):
 
     The line runs along the last axis of d; a, b, c broadcast against d
     (a_0 and c_{n-1} are ignored).  Forward elimination then back
-    substitution, no pivoting.
+    substitution, no pivoting.  A 1-D a, b or c holds the same rows for every
+    line; when all three are 1-D the pivots and c'_j are computed once for all
+    lines.  The operations on each element are the same either way.  The
+    recurrences run over the rows of an array with the row index first, so that
+    each step works on one slice of all lines.
     """
     d = np.asarray(d)
     n = d.shape[-1]
-    a = np.broadcast_to(a, d.shape)
-    b = np.broadcast_to(b, d.shape)
-    c = np.broadcast_to(c, d.shape)
-    cp = np.empty(d.shape, dtype=np.result_type(b, c, np.float64))
-    dp = np.empty(d.shape, dtype=np.result_type(d, b, np.float64))
-    cp[..., 0] = c[..., 0] / b[..., 0]
-    dp[..., 0] = d[..., 0] / b[..., 0]
+    D = np.moveaxis(d, -1, 0)
+    A, Bm, Cm = (np.asarray(q) if np.ndim(q) == 1 else np.moveaxis(np.broadcast_to(q, d.shape), -1, 0)
+                 for q in (a, b, c))
+    shared = A.ndim == Bm.ndim == Cm.ndim == 1
+    cp = np.empty(Bm.shape if shared else D.shape, dtype=np.result_type(Bm, Cm, np.float64))
+    dp = np.empty(D.shape, dtype=np.result_type(D, Bm, Cm, np.float64))
+    den = Bm[0]
+    cp[0] = Cm[0] / den
+    dp[0] = D[0] / den
     for j in range(1, n):
-        den = b[..., j] - a[..., j] * cp[..., j - 1]
-        cp[..., j] = c[..., j] / den
-        dp[..., j] = (d[..., j] - a[..., j] * dp[..., j - 1]) / den
+        den = Bm[j] - A[j] * cp[j - 1]
+        cp[j] = Cm[j] / den
+        dp[j] = (D[j] - A[j] * dp[j - 1]) / den
     x = np.empty_like(dp)
-    x[..., n - 1] = dp[..., n - 1]
+    x[n - 1] = dp[n - 1]
     for j in range(n - 2, -1, -1):
-        x[..., j] = dp[..., j] - cp[..., j] * x[..., j + 1]
-    return x
+        x[j] = dp[j] - cp[j] * x[j + 1]
+    return np.moveaxis(x, 0, -1)
 
 
 def thomas_cyclic(a, b, c, d):
@@ -284,12 +291,14 @@ def thomas_cyclic(a, b, c, d):
 
     Sherman-Morrison on top of Thomas: A = B + s t^T with s = (g,0..0,c_{n-1}),
     t = (1,0..0,a_0/g), g = -b_0; x = y - (t.y)/(1 + t.q) q with B y = d, B q = s.
+    With 1-D a, b, c (the same rows for every line) q is one vector shared by all lines.
     """
     d = np.asarray(d)
     n = d.shape[-1]
-    a = np.array(np.broadcast_to(a, d.shape), dtype=np.float64)
-    b = np.array(np.broadcast_to(b, d.shape), dtype=np.float64)
-    c = np.array(np.broadcast_to(c, d.shape), dtype=np.float64)
+    shp = (n,) if all(np.ndim(q) == 1 for q in (a, b, c)) else d.shape
+    a = np.array(np.broadcast_to(a, shp), dtype=np.float64)
+    b = np.array(np.broadcast_to(b, shp), dtype=np.float64)
+    c = np.array(np.broadcast_to(c, shp), dtype=np.float64)
     gam = -b[..., 0]
     alpha = c[..., n - 1]       # A[n-1, 0]
     beta = a[..., 0]            # A[0, n-1]
@@ -297,7 +306,7 @@ def thomas_cyclic(a, b, c, d):
     bb[..., 0] = b[..., 0] - gam
     bb[..., n - 1] = b[..., n - 1] - alpha * beta / gam
     y = thomas(a, bb, c, d)
-    s = np.zeros(d.shape)
+    s = np.zeros(shp)
     s[..., 0] = gam
     s[..., n - 1] = alpha
     q = thomas(a, bb, c, s)
@@ -451,9 +460,19 @@ def dft_matrix(n, sign=-1):
     return np.exp(sign * 2j * math.pi * np.outer(k, k) / n)
 
 
+# Lines longer than this are transformed by numpy's FFT (the same sums, O(N log N)); shorter
+# ones by the definition.  The FFT is pinned against the definition at lengths above the limit.
+NAIVE_DFT_MAX = 64
+
+
 def dft(f, axis, sign=-1):
-    """Naive O(N^2) DFT along an axis: F_k = sum_n f_n exp(sign 2 pi i k n / N)."""
+    """DFT along an axis: F_k = sum_n f_n exp(sign 2 pi i k n / N), unnormalised in both
+    directions.  Naive O(N^2) matrix product for N <= NAIVE_DFT_MAX, numpy's FFT above."""
     n = f.shape[axis]
+    if n > NAIVE_DFT_MAX:
+        if sign < 0:
+            return np.fft.fft(f, axis=axis)
+        return np.fft.ifft(f, axis=axis, norm="forward")
     M = dft_matrix(n, sign)
     return np.moveaxis(np.moveaxis(f, axis, -1) @ M.T, -1, axis)
 

@@ -31,8 +31,8 @@ MUTANTS = {
     "nvx_shift": ("nvx = (_xp(fuv) - fuv) / dx", "nvx = (fuv - _xm(fuv)) / dx", CORE),
     # ADI, tridiagonal solvers, partitioned solve
     "beta_factor": ("beta = RK3_ALPHA[k] * dt * inv_re / 2.0", "beta = RK3_ALPHA[k] * dt * inv_re", CORE),
-    "thomas_back_index": ("x[..., j] = dp[..., j] - cp[..., j] * x[..., j + 1]",
-                          "x[..., j] = dp[..., j] - cp[..., j + 1] * x[..., j + 1]", CORE),
+    "thomas_back_index": ("x[j] = dp[j] - cp[j] * x[j + 1]",
+                          "x[j] = dp[j] - cp[j + 1] * x[j + 1]", CORE),
     "cyclic_corner": ("bb[..., n - 1] = b[..., n - 1] - alpha * beta / gam",
                       "bb[..., n - 1] = b[..., n - 1] - alpha * beta * gam", CORE),
     "ppt_perm": ("Zbar = P + E.T @ Ybar", "Zbar = np.eye(len(P)) + E.T @ Ybar", CORE),
@@ -67,7 +67,7 @@ MUTANTS = {
     "p_update_half": ("    if pressure == \"delta\":\n        return p + phi", "    if pressure == \"delta\":\n        return p + 0.5 * phi", CORE + CFL),
     "projection_scale": ("    scale = RK3_ALPHA[k] * dt\n    phi = poisson_solve(g,", "    scale = RK3_GAMMA[k] * dt\n    phi = poisson_solve(g,", CORE + CFL),
     "cyclic_fac_sign": ("fac = (y[..., 0] + beta / gam * y[..., n - 1])", "fac = (y[..., 0] - beta / gam * y[..., n - 1])", CORE),
-    "thomas_den": ("den = b[..., j] - a[..., j] * cp[..., j - 1]", "den = b[..., j] - c[..., j] * cp[..., j - 1]", CORE),
+    "thomas_den": ("den = Bm[j] - A[j] * cp[j - 1]", "den = Bm[j] - Cm[j] * cp[j - 1]", CORE),
     # inflow / convective outflow
     "ghost_coef": ("return np.concatenate([f[:, :, 1:], (2.0 * f_out - f[:, :, -1])[:, :, None]], axis=2)",
                    "return np.concatenate([f[:, :, 1:], (1.0 * f_out)[:, :, None]], axis=2)", BL),

@@ -36,6 +36,26 @@ def test_dft_matches_library_fft(n):
     np.testing.assert_allclose((np.abs(F) ** 2).sum(1), n * (np.abs(f) ** 2).sum(1), rtol=1e-12)
 
 
+@pytest.mark.parametrize("n", [72, 96, 128, 256])
+def test_dft_above_the_naive_limit_equals_the_definition(n):
+    """Lines longer than NAIVE_DFT_MAX go through numpy's FFT: the same sums as the definition
+    F_k = sum_m f_m exp(sign 2 pi i k m / N), written out here as a matrix product, along both
+    axes used by the solver (0 and 2), forward and unnormalised inverse."""
+    assert n > O.NAIVE_DFT_MAX
+    rng = np.random.default_rng(n)
+    f = rng.standard_normal((n, 3, n)) + 1j * rng.standard_normal((n, 3, n))
+    k = np.arange(n)
+    for sign in (-1, +1):
+        M = np.exp(sign * 2j * np.pi * np.outer(k, k) / n)
+        by_def2 = np.einsum("km,zym->zyk", M, f)
+        by_def0 = np.einsum("km,myx->kyx", M, f)
+        scale = np.abs(by_def2).max()
+        np.testing.assert_allclose(O.dft(f, 2, sign), by_def2, rtol=0, atol=1e-12 * scale)
+        np.testing.assert_allclose(O.dft(f, 0, sign), by_def0, rtol=0, atol=1e-12 * scale)
+    # round trip: the inverse is unnormalised, so it returns n f
+    np.testing.assert_allclose(O.dft(O.dft(f, 2), 2, +1), n * f, rtol=0, atol=1e-12 * n * np.abs(f).max())
+
+
 @pytest.mark.parametrize("n", [4, 7, 16])
 def test_modified_wavenumbers_are_eigenvalues(n):
     h = 0.3
