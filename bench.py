@@ -369,6 +369,160 @@ def bench_ensemble(B, torch, dev, args):
     return out
 
 
+# ------------------------------------------------------------------------------ boundary layers
+def device_bl_fields(torch, I, dev, case, slab=8, workers=8):
+    """The boundary-layer initial field built a few z planes at a time on the host (threads; each
+    slab is bit for bit that plane range of the whole-field generator) and copied into device
+    tensors, so host memory holds a few slabs only.  Sets case.dt from CFL 0.5 on that field."""
+    from concurrent.futures import ThreadPoolExecutor
+    nx, ny, nz = case.nx, case.ny, case.nz
+    f64 = dict(dtype=torch.float64, device=dev)
+    u = torch.empty((nz, ny, nx), **f64)
+    v = torch.empty((nz, ny + 1, nx), **f64)
+    w = torch.empty((nz, ny, nx), **f64)
+    p = torch.zeros((nz, ny, nx), **f64)
+    bl = {q: torch.empty((nz, rows), **f64) for q, rows in
+          (("u_out", ny), ("v_in", ny + 1), ("v_out", ny + 1), ("w_in", ny), ("w_out", ny))}
+
+    def gen(k0):
+        k1 = min(nz, k0 + slab)
+        su, sv, sw, sbl = I.boundary_layer_slab(case, k0, k1)
+        return k0, k1, su, sv, sw, sbl, I.boundary_layer_rate(case, su, sv, sw)
+
+    rate = 0.0
+    with ThreadPoolExecutor(workers) as ex:
+        for k0, k1, su, sv, sw, sbl, r in ex.map(gen, range(0, nz, slab)):
+            rate = max(rate, r)
+            for t, a in ((u, su), (v, sv), (w, sw)):
+                t[k0:k1].copy_(torch.from_numpy(a))
+            for q, a in sbl.items():
+                bl[q][k0:k1].copy_(torch.from_numpy(a))
+    case.dt = 0.5 / rate
+    return u, v, w, p, bl
+
+
+def device_max_divergence(torch, s, case, slab=32):
+    """max over cells of |D u| (inflow / outflow x, periodic z), evaluated on the device a few z
+    planes at a time (measurement bookkeeping with torch; the solver's work is the library's)."""
+    dx, dz = case.lx / case.nx, case.lz / case.nz
+    dy = torch.as_tensor(np.diff(case.yf), device=s.u.device)[None, :, None]
+    out = 0.0
+    nz = case.nz
+    for k0 in range(0, nz, slab):
+        k1 = min(nz, k0 + slab)
+        u, v, w = s.u[k0:k1], s.v[k0:k1], s.w[k0:k1]
+        ux = torch.cat([u[:, :, 1:], s.bl["u_out"][k0:k1, :, None]], dim=2)
+        wz = s.w[[(k + 1) % nz for k in range(k0, k1)]]
+        d = (ux - u) / dx + (v[:, 1:] - v[:, :-1]) / dy + (wz - w) / dz
+        out = max(out, float(d.abs().max()))
+    return out
+
+
+def timed_steps(torch, s, start, steps, warmup, gpu_index):
+    """warmup steps (graph capture), the projected start restored, then `steps` steps timed with
+    CUDA events on the solver's stream and clocks sampled.  Returns (ms, clocks)."""
+    s.step(warmup)
+    s.sync()
+    for t, a in zip(solver_state(s), start):
+        t.copy_(a)
+    ck = ClockSampler(gpu_index)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ck.start()
+    time.sleep(0.3)
+    ev0.record(s.stream)
+    s.step(steps)
+    ev1.record(s.stream)
+    torch.cuda.synchronize()
+    return ev0.elapsed_time(ev1), ck.stop()
+
+
+def solver_state(s):
+    """Everything a step reads: u, v, w, p and the boundary planes (N_prev is not read by the
+    first sub-step, whose zeta is 0)."""
+    return [s.u, s.v, s.w, s.p] + [s.bl[q] for q in sorted(s.bl)]
+
+
+def kernel_fracs(model, kms, launches, cells, hbm):
+    out = {}
+    for name, ms in kms.items():
+        if ms <= 0.0:
+            continue
+        per = ms / launches
+        gbps = model[name][0] * cells / (per * 1e-3) / 1e9
+        out[name] = {"ms_per_launch": round(per, 4), "GBps": round(gbps, 1), "hbm_frac_algorithmic": round(gbps / hbm, 4)}
+    return out
+
+
+def bench_boundary_layer(B, torch, I, dev, gpu_index, nx, ny, nz, steps, fp64_ref, warmup=2):
+    """The paper-scale flat-plate workloads (inflow / convective outflow in x, wall and stress-free
+    top in y, periodic z), mixed form, `steps` steps timed like the headline.  With fp64_ref, the
+    FP64 form also runs the same steps from the same projected start, and the record reports the
+    per-field relative L2 difference of the mixed form from it."""
+    hbm, _, _ = load_peaks()
+    case = I.boundary_layer_case(nx, ny, nz, steps=steps)
+    cells = case.cells()
+    t0 = time.perf_counter()
+    u, v, w, p, bl = device_bl_fields(torch, I, dev, case)
+    rec = {"workload": "boundary_layer_%dx%dx%d" % (nx, ny, nz), "cells": cells, "steps": steps, "dt": case.dt,
+           "cfl": 0.5, "re": case.re, "bc": "inflow / convective outflow x; wall + stress-free top y; periodic z",
+           "inputs_s": round(time.perf_counter() - t0, 1)}
+    free0 = torch.cuda.mem_get_info(dev)[0]
+    torch.cuda.reset_peak_memory_stats(dev)
+    # the start: projected in FP64 (outflow flux corrected first), shared by both forms
+    case.precision = 0
+    sa = B.Solver(case, u, v, w, p, bl=bl, device=str(dev))
+    sa.make_divergence_free()
+    sa.sync()
+    start = [t.clone() for t in solver_state(sa)]
+    ref = None
+    if fp64_ref:
+        ms, ck = timed_steps(torch, sa, start, steps, warmup, gpu_index)
+        ref = [t.clone() for t in (sa.u, sa.v, sa.w, sa.p)]  # after exactly `steps` steps
+        rec["fp64"] = {"value": cells * steps / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / steps, "clocks": ck,
+                       "max_divergence": device_max_divergence(torch, sa, case)}
+        rec["fp64"]["kernels"] = kernel_fracs(kernel_model(nx, ny, nz, 8), sa.step_profiled(1), 3, cells, hbm)
+    sa.close()
+    del sa, u, v, w, p, bl
+    # the mixed form from the same start
+    case.precision = 1
+    sm = B.Solver(case, *[t.clone() for t in start[:4]], bl={q: t.clone() for q, t in zip(sorted(start_bl_names()), start[4:])},
+                  device=str(dev))
+    sm.autotune()
+    for t, a in zip(solver_state(sm), start):
+        t.copy_(a)
+    P, mode, drop = sm.partition()
+    rec["partition_x"] = {"P": P, "rows": nx // P, "mode": "PDD" if mode == B.NS_PART_PDD else "PPT",
+                          "pdd_dropped": drop, "chosen_by": "ns_autotune"}
+    ms, ck = timed_steps(torch, sm, start, steps, warmup, gpu_index)
+    rec["mixed"] = {"value": cells * steps / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / steps, "clocks": ck,
+                    "max_divergence": device_max_divergence(torch, sm, case)}
+    if ref is not None:
+        vel = math.sqrt(sum(float(torch.linalg.vector_norm(t)) ** 2 for t in ref[:3]))
+        err = {n: float(torch.linalg.vector_norm(getattr(sm, n) - r)) / vel for n, r in zip("uvw", ref[:3])}
+        pa = ref[3] - ref[3].mean()
+        pb = sm.p - sm.p.mean()
+        err["p"] = float(torch.linalg.vector_norm(pb - pa)) / max(float(torch.linalg.vector_norm(pa)),
+                                                                  vel * vel / math.sqrt(pa.numel()))
+        rec["rel_l2_mixed_vs_fp64_after_%d_steps" % steps] = err
+        rec["speedup_mixed_vs_fp64"] = rec["fp64"]["ms_per_step"] / rec["mixed"]["ms_per_step"]
+    rec["mixed"]["kernels"] = kernel_fracs(kernel_model(nx, ny, nz, 4), sm.step_profiled(1), 3, cells, hbm)
+    state_bytes = sum(t.numel() * 8 for t in solver_state(sm))
+    rec["footprint"] = {"state_bytes": state_bytes, "workspace_bytes": sm.ws.numel(),
+                        "torch_allocator_peak_bytes": torch.cuda.max_memory_allocated(dev),
+                        "device_used_bytes_at_end": free0 - torch.cuda.mem_get_info(dev)[0],
+                        "note": "peak includes the saved projected start and, with fp64_ref, the FP64 run"}
+    sm.close()
+    del sm, start, ref
+    torch.cuda.empty_cache()
+    return rec
+
+
+def start_bl_names():
+    return ("u_out", "v_in", "v_out", "w_in", "w_out")
+
+
 # ------------------------------------------------------------------------------ main
 def main():
     ap = argparse.ArgumentParser()
@@ -382,6 +536,7 @@ def main():
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--no-cfl", action="store_true")
+    ap.add_argument("--no-bl", action="store_true", help="skip the 134M- and 604M-cell boundary-layer records")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -422,11 +577,10 @@ def main():
     # cpu baseline first, in this process, before any CUDA work
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        F = 2  # half of every stage's lines: about 12 s on 16 host cores, arrays well beyond cache
-        val, t = oracle_baseline(case, u0, v0, w0, p0, F, 3)
+        F = 1  # the whole workload: two RK3 steps, about 18 s on 16 host cores
+        val, t = oracle_baseline(case, u0, v0, w0, p0, F, 6)
         cpu = {"value": val, "unit": UNIT, "cores": os.cpu_count(), "cpu": host_cpu(), "kind": "oracle",
-               "sample": "one RK3 step (3 sub-steps) of the FP64 numpy oracle on 1/%d of every stage's lines "
-                         "and cells of this workload (full line lengths), scaled by %d; %.1f s" % (F, F, t)}
+               "sample": "two RK3 steps (6 sub-steps) of the FP64 numpy oracle on the whole workload; %.1f s" % t}
 
     import torch
     from paper_1812_01178_gb300 import binding as B
@@ -577,6 +731,13 @@ def main():
     if not args.no_ensemble:
         ensemble = bench_ensemble(B, torch, dev, args)
 
+    # the paper-scale boundary layers (one GPU only: the records are single-GPU figures)
+    bls = None
+    if args.precision == "fp64" and not args.no_bl and world == 1:
+        from paper_1812_01178_gb300 import inputs as I
+        bls = {"1024x256x512": bench_boundary_layer(B, torch, I, dev, gpu_index, 1024, 256, 512, 50, True),
+               "2048x288x1024": bench_boundary_layer(B, torch, I, dev, gpu_index, 2048, 288, 1024, 20, False)}
+
     # end to end through the host-buffer entry point (pinned host memory)
     hu = torch.from_numpy(np.ascontiguousarray(u0)).pin_memory().numpy()
     hv = torch.from_numpy(np.ascontiguousarray(v0)).pin_memory().numpy()
@@ -606,7 +767,7 @@ def main():
            "data": "synthetic (seeded Re_tau 395 log-law channel field, 10% Gaussian fluctuations, projected)",
            "config": config, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
            "fp64_peak": ({"tflops": fp64_live[0], "source": fp64_live[1]} if fp64_live else None),
-           "gpu_launches": len(kern) * 3 * args.steps, "clocks": ck, "mixed": mixed, "fixed_cfl": cflsec, "ensemble": ensemble,
+           "gpu_launches": len(kern) * 3 * args.steps, "clocks": ck, "mixed": mixed, "fixed_cfl": cflsec, "ensemble": ensemble, "boundary_layer": bls,
            "kernels": {k: {kk: (round(vv, 4) if vv is not None else None) for kk, vv in d.items()}
                        for k, d in kern.items()}}
     print(json.dumps(out))

@@ -337,6 +337,79 @@ ns_status ns_batch_sync(ns_batch* b);
 const char* ns_batch_last_error(ns_batch* b);
 void ns_batch_destroy(ns_batch* b);
 
+/* ---------------------------------------------------------------------------------------------
+ * y-slab decomposition (Sec. 3.2, "Domain decomposition using parallel algorithms"; Algorithm 1):
+ * the domain is cut into p slabs of whole x-z planes, slab r owning the cell rows [j0, j1) of y
+ * (ns_slab_rows) and, of v, the faces j0 .. j1-1 (the last slab also the top face ny).  One slab
+ * is one GPU's share in the paper's multi-GPU method.  Everything along x and z is local to a slab;
+ * the y sweep of the ADI factorisation is split across slabs by PDD (Sec. 3.2, Eq. (Zpdd): one
+ * exchange of end values with the two neighbours, Algorithm 1) or PPT (Eq. (Zppt): all-gather of
+ * the end values), and the Poisson y solve of every (kx, kz) line by PPT.  Built for periodic x,
+ * NS_FP64 and the plain pressure update (other configurations: NS_ERR_ARG); every slab needs at
+ * least 3 rows (ny >= 3 p).
+ *
+ * Local fields.  A slab's u, w, p hold rows j0-hb .. j1+ha-1 and its v the faces j0-hb .. j1+ha,
+ * where hb = (r > 0) and ha = (r < p-1) are the halo rows below and above (layouts as above with
+ * ny replaced by the local row count nyl + hb + ha).  The caller fills the owned rows; the halo
+ * rows are filled by the exchanges.
+ *
+ * Exchanges.  A sub-step is six phases (NS_SLAB_*) with an exchange after each:
+ *   PACK (before the first sub-step only) -> HALO -> RHS -> ADIY -> ADIZ -> VSTAR -> POIS -> POIS
+ *   -> PHI -> PHI -> PROJECT -> HALO (ready for the next sub-step's RHS)
+ * where the exchange named after a phase is NS_XCH_<name>.  For exchange x every slab has a send
+ * buffer of ns_slab_slot_bytes bytes and a receive buffer of p such slots; after the phase that
+ * writes its send buffer, the caller copies slab s's send buffer into slot s of every slab r that
+ * reads it (ns_slab_slots: slots lo .. hi of slab r; the slab's own slot, where read, it writes
+ * itself).  Between GPUs that is NCCL send / receive between neighbours or an all-gather; on one
+ * GPU, device copies.  Buffers come from ns_slab_buffers.
+ * ------------------------------------------------------------------------------------------- */
+typedef struct ns_slab ns_slab;
+enum { NS_XCH_HALO = 0, NS_XCH_ADIY = 1, NS_XCH_VSTAR = 2, NS_XCH_POIS = 3, NS_XCH_PHI = 4, NS_XCH_COUNT = 5 };
+enum { NS_SLAB_PACK = 0, NS_SLAB_RHS = 1, NS_SLAB_ADIZ = 2, NS_SLAB_POIS = 3, NS_SLAB_PHI = 4,
+       NS_SLAB_PROJECT = 5 };
+
+/* Rows [*j0, *j1) of slab r of p on ny rows (as even as possible).  Host only. */
+ns_status ns_slab_rows(int ny, int p, int r, int* j0, int* j1);
+
+/* Bytes of one exchange slot of kind xch for the whole-domain cfg (0 if invalid).  Host only. */
+size_t ns_slab_slot_bytes(const ns_config* cfg, int p, int xch);
+
+/* The slots lo .. hi (inclusive) of its receive buffer that slab r reads in exchange xch; ymode is
+ * the slab's y-sweep mode (NS_PART_PDD: neighbours only; NS_PART_PPT: every slab).  Host only. */
+ns_status ns_slab_slots(int p, int r, int xch, int ymode, int* lo, int* hi);
+
+/* Workspace bytes of slab r (its sub-grid context, the slab tables and the exchange buffers); 0 if
+ * the configuration is not supported. */
+size_t ns_slab_workspace_bytes(const ns_config* cfg, int p, int r);
+
+/* Create slab r of p of the whole-domain configuration cfg on `local` fields (device pointers,
+ * 256-byte aligned, layouts above).  ymode: NS_PART_AUTO (PDD when the coupling it drops is at most
+ * 1e-15 in every sub-step, else PPT), NS_PART_PPT or NS_PART_PDD for the y sweep.  The tables of
+ * the y sweep and of the Poisson y solve (block factors, spikes, reduced-system rows) are built on
+ * the host once.  workspace: caller's device memory of ns_slab_workspace_bytes, or NULL (the
+ * library allocates it and frees it in ns_slab_destroy).  Errors: NS_ERR_ARG / NS_ERR_SIZE /
+ * NS_ERR_CUDA / NS_ERR_STATE (a singular reduced system), message in ns_last_error(NULL). */
+ns_status ns_slab_init(ns_slab** out, const ns_config* cfg, int p, int r, int ymode, const ns_fields* local,
+                       void* workspace, size_t ws_bytes, void* cuda_stream);
+
+/* Enqueue phase `phase` of RK3 sub-step `substep` on the slab's stream: it first reads the
+ * receive buffer of the exchange before it, then runs its kernels and writes the send buffer of
+ * the exchange after it. */
+ns_status ns_slab_phase(ns_slab* s, int phase, int substep);
+
+/* Send buffer, receive buffer and slot bytes of exchange xch (device pointers, slab-owned). */
+ns_status ns_slab_buffers(ns_slab* s, int xch, void** send, void** recv, size_t* slot_bytes);
+
+/* The y-sweep mode in use (NS_PART_PDD or NS_PART_PPT) and the largest coupling PDD drops. */
+ns_status ns_slab_mode(ns_slab* s, int* ymode, double* ydrop);
+
+/* The sub-grid context (for ns_get_buffer and the like); owned by the slab. */
+ns_ctx* ns_slab_context(ns_slab* s);
+
+ns_status ns_slab_sync(ns_slab* s);
+const char* ns_slab_last_error(ns_slab* s);
+void ns_slab_destroy(ns_slab* s);
+
 /* Measurement aid (no counterpart in the paper): the FP64 FMA throughput of this GPU, the
  * denominator of the FP64-ALU roofline the solver's FP64 kernels are measured against.  Enqueues
  * one kernel of n_blocks blocks of 256 threads on cuda_stream; every thread runs 8 independent

@@ -29,7 +29,10 @@ EXPORTS = ["ns_workspace_bytes", "ns_init", "ns_rhs", "ns_adi_sweep", "ns_poisso
            "ns_get_partition", "ns_autotune", "ns_get_buffer", "ns_poisson_solve_static", "ns_fp64_fma_probe", "ns_sync",
            "ns_last_error", "ns_destroy", "ns_batch_workspace_bytes", "ns_batch_init", "ns_batch_step",
            "ns_batch_launches_per_step", "ns_batch_autotune", "ns_batch_set_partition", "ns_batch_instance",
-           "ns_batch_sync", "ns_batch_last_error", "ns_batch_destroy"]
+           "ns_batch_sync", "ns_batch_last_error", "ns_batch_destroy",
+           "ns_slab_rows", "ns_slab_slot_bytes", "ns_slab_slots", "ns_slab_workspace_bytes", "ns_slab_init",
+           "ns_slab_phase", "ns_slab_buffers", "ns_slab_mode", "ns_slab_context", "ns_slab_sync",
+           "ns_slab_last_error", "ns_slab_destroy"]
 NS_STATIC_SCRATCH_BYTES = 48 * 1024 * 1024
 
 
@@ -90,6 +93,23 @@ def lib(path: str = LIB_PATH):
     L.ns_get_buffer.argtypes = [vp, i, P(vp), P(sz)]
     L.ns_poisson_solve_static.argtypes = [P(ns_config), vp, vp, vp, vp, i, vp]
     L.ns_fp64_fma_probe.argtypes = [vp, i, i, vp]
+    L.ns_slab_rows.argtypes = [i, i, i, P(i), P(i)]
+    L.ns_slab_slot_bytes.argtypes = [P(ns_config), i, i]
+    L.ns_slab_slot_bytes.restype = sz
+    L.ns_slab_slots.argtypes = [i, i, i, i, P(i), P(i)]
+    L.ns_slab_workspace_bytes.argtypes = [P(ns_config), i, i]
+    L.ns_slab_workspace_bytes.restype = sz
+    L.ns_slab_init.argtypes = [P(vp), P(ns_config), i, i, i, P(ns_fields), vp, sz, vp]
+    L.ns_slab_phase.argtypes = [vp, i, i]
+    L.ns_slab_buffers.argtypes = [vp, i, P(vp), P(vp), P(sz)]
+    L.ns_slab_mode.argtypes = [vp, P(i), P(d)]
+    L.ns_slab_context.argtypes = [vp]
+    L.ns_slab_context.restype = vp
+    L.ns_slab_sync.argtypes = [vp]
+    L.ns_slab_last_error.argtypes = [vp]
+    L.ns_slab_last_error.restype = C.c_char_p
+    L.ns_slab_destroy.argtypes = [vp]
+    L.ns_slab_destroy.restype = None
     L.ns_sync.argtypes = [vp]
     L.ns_last_error.argtypes = [vp]
     L.ns_last_error.restype = C.c_char_p
@@ -278,6 +298,11 @@ class Solver:
         def put(a, shape):
             if a is None:
                 return torch.zeros(shape, dtype=torch.float64, device=dev)
+            if isinstance(a, torch.Tensor) and a.device == dev:
+                # a device tensor of the right layout is used in place (the context updates it)
+                if a.dtype != torch.float64 or tuple(a.shape) != shape or not a.is_contiguous():
+                    raise ValueError("device field must be a contiguous float64 tensor of shape %s" % (shape,))
+                return a
             t = torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64)).to(dev)
             assert tuple(t.shape) == shape, (t.shape, shape)
             return t.contiguous()

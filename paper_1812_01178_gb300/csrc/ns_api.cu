@@ -235,6 +235,47 @@ ns_status capture_step(ns_ctx* c, bool profiled, cudaGraph_t* graph, cudaGraphEx
 
 void ns_set_thread_error(const char* msg) { g_init_error = msg ? msg : ""; }
 
+// Grid coefficient block (layout of GC_*) of a configuration, on the host.
+std::vector<double> grid_coefficients_host(const ns_config* cfg) {
+  const int ny = cfg->ny;
+  const double* yf = cfg->yf;
+  std::vector<double> yc(ny), dy(ny);
+  for (int j = 0; j < ny; ++j) {
+    yc[j] = 0.5 * (yf[j] + yf[j + 1]);
+    dy[j] = yf[j + 1] - yf[j];
+  }
+  const int G = ny + 1;
+  std::vector<double> gc((size_t)NS_GC_COUNT * G, 0.0);
+  auto GCv = [&](int f, int j) -> double& { return gc[(size_t)f * G + j]; };
+  for (int j = 0; j < ny; ++j) {
+    GCv(GC_DY, j) = dy[j];
+    GCv(GC_IDY, j) = 1.0 / dy[j];
+  }
+  for (int j = 1; j < ny; ++j) {
+    const double hc = yc[j] - yc[j - 1];
+    GCv(GC_HC, j) = hc;
+    GCv(GC_IHC, j) = 1.0 / hc;
+    const double whi = (yf[j] - yc[j - 1]) / hc;
+    GCv(GC_WHI, j) = whi;
+    GCv(GC_WLO, j) = 1.0 - whi;
+  }
+  for (int j = 0; j < ny; ++j) {
+    const double hm = j == 0 ? yc[0] - yf[0] : yc[j] - yc[j - 1];
+    const double hp = j == ny - 1 ? yf[ny] - yc[ny - 1] : yc[j + 1] - yc[j];
+    GCv(GC_AC, j) = 2.0 / (hm * (hm + hp));
+    GCv(GC_CC, j) = (j == ny - 1 && cfg->bc_ytop == 1) ? 0.0 : 2.0 / (hp * (hm + hp));
+  }
+  for (int j = 1; j < ny; ++j) {
+    const double hm = dy[j - 1], hp = dy[j];
+    GCv(GC_AF, j) = 2.0 / (hm * (hm + hp));
+    GCv(GC_CF, j) = 2.0 / (hp * (hm + hp));
+  }
+  for (int j = 1; j < ny; ++j) GCv(GC_PA, j) = 1.0 / (dy[j] * (yc[j] - yc[j - 1]));
+  for (int j = 0; j + 1 < ny; ++j) GCv(GC_PC, j) = 1.0 / (dy[j] * (yc[j + 1] - yc[j]));
+  return gc;
+}
+
+
 extern "C" {
 
 size_t ns_workspace_bytes(const ns_config* cfg) {
@@ -368,33 +409,8 @@ ns_status ns_init(ns_ctx** out, const ns_config* cfg, const ns_fields* fields, v
     dy[j] = yf[j + 1] - yf[j];
   }
   const int G = ny + 1;
-  std::vector<double> gc((size_t)NS_GC_COUNT * G, 0.0);
+  std::vector<double> gc = grid_coefficients_host(&c->cfg);
   auto GCv = [&](int f, int j) -> double& { return gc[(size_t)f * G + j]; };
-  for (int j = 0; j < ny; ++j) {
-    GCv(GC_DY, j) = dy[j];
-    GCv(GC_IDY, j) = 1.0 / dy[j];
-  }
-  for (int j = 1; j < ny; ++j) {
-    const double hc = yc[j] - yc[j - 1];
-    GCv(GC_HC, j) = hc;
-    GCv(GC_IHC, j) = 1.0 / hc;
-    const double whi = (yf[j] - yc[j - 1]) / hc;
-    GCv(GC_WHI, j) = whi;
-    GCv(GC_WLO, j) = 1.0 - whi;
-  }
-  for (int j = 0; j < ny; ++j) {
-    const double hm = j == 0 ? yc[0] - yf[0] : yc[j] - yc[j - 1];
-    const double hp = j == ny - 1 ? yf[ny] - yc[ny - 1] : yc[j + 1] - yc[j];
-    GCv(GC_AC, j) = 2.0 / (hm * (hm + hp));
-    GCv(GC_CC, j) = (j == ny - 1 && cfg->bc_ytop == 1) ? 0.0 : 2.0 / (hp * (hm + hp));
-  }
-  for (int j = 1; j < ny; ++j) {
-    const double hm = dy[j - 1], hp = dy[j];
-    GCv(GC_AF, j) = 2.0 / (hm * (hm + hp));
-    GCv(GC_CF, j) = 2.0 / (hp * (hm + hp));
-  }
-  for (int j = 1; j < ny; ++j) GCv(GC_PA, j) = 1.0 / (dy[j] * (yc[j] - yc[j - 1]));
-  for (int j = 0; j + 1 < ny; ++j) GCv(GC_PC, j) = 1.0 / (dy[j] * (yc[j + 1] - yc[j]));
   ns_status st = NS_OK;
   c->gc_h = gc;
   if (c->cfg.recycle_i && recycle_upload_grid(c) != cudaSuccess) st = NS_ERR_CUDA;

@@ -494,6 +494,9 @@ cudaError_t poisson_set_attributes();  // once per process and device, outside a
 // Sets the message ns_last_error(NULL) returns on this thread.
 void ns_set_thread_error(const char* msg);
 
+// Grid coefficient block (GC_* layout, NS_GC_COUNT arrays of ny + 1) of cfg, on the host.
+std::vector<double> grid_coefficients_host(const ns_config* cfg);
+
 // Host-side table builders (ns_tables.cpp-style code lives in ns_api.cu).
 size_t adi_y_tab_count(int ny);
 size_t adi_z_tab_count(int nz);

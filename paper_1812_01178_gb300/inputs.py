@@ -60,6 +60,14 @@ def normal(seed: int, n: int, offset: int = 0) -> np.ndarray:
     return out[:n]
 
 
+def normal_range(seed: int, e0: int, n: int) -> np.ndarray:
+    """Elements e0 .. e0+n-1 of the sequence normal(seed, N, 0) (any N >= e0 + n), without
+    generating the elements before e0: element e uses the uniforms of counters 2(e // 2) and
+    2(e // 2) + 1, so a range that starts on an even element is normal(seed, n, e0 / 2)."""
+    s = e0 - (e0 % 2)
+    return normal(seed, n + (e0 - s), s // 2)[e0 - s:]
+
+
 # ----------------------------------------------------------------------------
 # grids
 # ----------------------------------------------------------------------------
@@ -197,6 +205,50 @@ def small_channel(nx, ny, nz, seed=7, amp=0.1, re=100.0, dt=2e-3, beta=1.5,
     return case, u, v, w, p
 
 
+def boundary_layer_case(nx=1024, ny=256, nz=512, beta=2.0, re=1000.0, steps=50, lx=None, ly=None, lz=None,
+                        precision=0):
+    """The boundary-layer workload's sizes and constants (dt is set from the initial field by
+    boundary_layer / boundary_layer_dt).  Units: inlet thickness and free-stream speed; domain
+    Lx = 200, Ly = 20, Lz = 30 by default (scaled down for small grids)."""
+    lx = lx if lx is not None else (200.0 if nx >= 256 else 0.2 * nx)
+    ly = ly if ly is not None else (20.0 if ny >= 64 else 0.3 * ny)
+    lz = lz if lz is not None else (30.0 if nz >= 128 else 0.25 * nz)
+    yf = boundary_layer_faces(ny, beta, ly)
+    return Case("boundary_layer_%dx%dx%d" % (nx, ny, nz), nx, ny, nz, lx, lz, yf, re=re, fx=0.0,
+                steps=steps, bc_x=1, bc_ytop=1, precision=precision, u_conv=1.0)
+
+
+def boundary_layer_slab(case: Case, k0: int, k1: int, amp=1e-2, seed=1812):
+    """Planes k0 <= k < k1 of the boundary-layer initial field: (u, v, w, bl) with u, v, w of shape
+    (k1-k0, ny or ny+1, nx) and the boundary planes of those rows.  The planes are exactly those
+    of the whole field (every value comes from its own counter), so a field can be built slab by
+    slab with little host memory."""
+    nx, ny = case.nx, case.ny
+    nk = k1 - k0
+    prof = np.tanh(2.0 * _centres(case.yf))
+    u = prof[None, :, None] + amp * normal_range(seed, k0 * ny * nx, nk * ny * nx).reshape(nk, ny, nx)
+    v = amp * normal_range(seed + 1, k0 * (ny + 1) * nx, nk * (ny + 1) * nx).reshape(nk, ny + 1, nx)
+    v[:, 0, :] = 0.0
+    v[:, ny, :] = 0.0
+    w = amp * normal_range(seed + 2, k0 * ny * nx, nk * ny * nx).reshape(nk, ny, nx)
+    # inflow planes (face 0 of u; v, w on the inflow face), fixed in time
+    u[:, :, 0] = prof[None, :] + amp * normal_range(seed + 3, k0 * ny, nk * ny).reshape(nk, ny)
+    v_in = amp * normal_range(seed + 4, k0 * (ny + 1), nk * (ny + 1)).reshape(nk, ny + 1)
+    v_in[:, 0] = 0.0
+    v_in[:, ny] = 0.0
+    w_in = amp * normal_range(seed + 5, k0 * ny, nk * ny).reshape(nk, ny)
+    bl = dict(u_out=u[:, :, -1].copy(), v_in=v_in, v_out=v[:, :, -1].copy(), w_in=w_in, w_out=w[:, :, -1].copy())
+    return u, v, w, bl
+
+
+def boundary_layer_rate(case: Case, u, v, w) -> float:
+    """max |u|/dx + |v_c|/dy + |w|/dz of (a slab of) the initial field: the CFL recipe of dt."""
+    dx, dz = case.lx / case.nx, case.lz / case.nz
+    dy = np.diff(case.yf)
+    c = np.abs(u) / dx + np.abs(0.5 * (v[:, :-1] + v[:, 1:])) / dy[None, :, None] + np.abs(w) / dz
+    return float(c.max())
+
+
 def boundary_layer(nx=1024, ny=256, nz=512, beta=2.0, re=1000.0, amp=1e-2, cfl=0.5, steps=50, seed=1812,
                    lx=None, ly=None, lz=None, precision=0):
     """Boundary-layer-shaped field with inflow / convective outflow in x.
@@ -205,35 +257,14 @@ def boundary_layer(nx=1024, ny=256, nz=512, beta=2.0, re=1000.0, amp=1e-2, cfl=0
     (scaled down for small grids).  Inflow u = tanh(2 y) plus seeded perturbations of amplitude
     amp on u, v, w (time-invariant); the interior starts from the same profile plus its own
     perturbations; the outflow planes start as the last interior column.  No-slip wall at y = 0,
-    stress-free top, periodic z, U_c = 1.  Returns (case, u, v, w, p, bl) with u holding faces
-    0..nx-1 (face 0 = inflow) and bl the boundary planes u_out, v_in, v_out, w_in, w_out.
+    stress-free top, periodic z, U_c = 1.  dt from the CFL number on the initial field.  Returns
+    (case, u, v, w, p, bl) with u holding faces 0..nx-1 (face 0 = inflow) and bl the boundary
+    planes u_out, v_in, v_out, w_in, w_out.
     """
-    lx = lx if lx is not None else (200.0 if nx >= 256 else 0.2 * nx)
-    ly = ly if ly is not None else (20.0 if ny >= 64 else 0.3 * ny)
-    lz = lz if lz is not None else (30.0 if nz >= 128 else 0.25 * nz)
-    yf = boundary_layer_faces(ny, beta, ly)
-    yc = _centres(yf)
-    case = Case("boundary_layer_%dx%dx%d" % (nx, ny, nz), nx, ny, nz, lx, lz, yf, re=re, fx=0.0,
-                steps=steps, bc_x=1, bc_ytop=1, precision=precision, u_conv=1.0)
-    n = nx * ny * nz
-    prof = np.tanh(2.0 * yc)
-    u = prof[None, :, None] + amp * normal(seed, n, 0).reshape(nz, ny, nx)
-    v = amp * normal(seed + 1, nz * (ny + 1) * nx, 0).reshape(nz, ny + 1, nx)
-    v[:, 0, :] = 0.0
-    v[:, ny, :] = 0.0
-    w = amp * normal(seed + 2, n, 0).reshape(nz, ny, nx)
-    # inflow planes (face 0 of u; v, w on the inflow face), fixed in time
-    u[:, :, 0] = prof[None, :] + amp * normal(seed + 3, nz * ny, 0).reshape(nz, ny)
-    v_in = amp * normal(seed + 4, nz * (ny + 1), 0).reshape(nz, ny + 1)
-    v_in[:, 0] = 0.0
-    v_in[:, ny] = 0.0
-    w_in = amp * normal(seed + 5, nz * ny, 0).reshape(nz, ny)
-    bl = dict(u_out=u[:, :, -1].copy(), v_in=v_in, v_out=v[:, :, -1].copy(), w_in=w_in, w_out=w[:, :, -1].copy())
+    case = boundary_layer_case(nx, ny, nz, beta, re, steps, lx, ly, lz, precision)
+    u, v, w, bl = boundary_layer_slab(case, 0, nz, amp, seed)
     p = np.zeros((nz, ny, nx))
-    dx, dz = lx / nx, lz / nz
-    dy = np.diff(yf)
-    c = (np.abs(u) / dx + np.abs(0.5 * (v[:, :-1] + v[:, 1:])) / dy[None, :, None] + np.abs(w) / dz)
-    case.dt = cfl / float(c.max())
+    case.dt = cfl / boundary_layer_rate(case, u, v, w)
     return case, u, v, w, p, bl
 
 

@@ -62,3 +62,23 @@ def test_turbulent_channel_recipe_small():
     # the same call gives the same fields
     case2, u2, *_ = I.turbulent_channel(32, 24, 16)
     assert np.array_equal(u, u2) and case2.dt == case.dt
+
+
+def test_normal_range_is_a_window_of_the_whole_sequence():
+    whole = I.normal(99, 1001, 0)
+    for e0, n in ((0, 10), (1, 7), (2, 9), (37, 64), (500, 501)):
+        assert np.array_equal(I.normal_range(99, e0, n), whole[e0:e0 + n])
+
+
+def test_boundary_layer_built_slab_by_slab_equals_the_whole_field():
+    """The bench builds the large boundary-layer fields a few z planes at a time: the planes are
+    bit for bit those of the whole-field generator, boundary planes included (odd slab starts and
+    odd plane sizes as well)."""
+    case, u, v, w, p, bl = I.boundary_layer(96, 37, 24)
+    parts = [I.boundary_layer_slab(case, k0, min(k0 + 5, case.nz)) for k0 in range(0, case.nz, 5)]
+    for q, ref in enumerate((u, v, w)):
+        assert np.array_equal(np.concatenate([pp[q] for pp in parts]), ref)
+    for k, ref in bl.items():
+        assert np.array_equal(np.concatenate([pp[3][k] for pp in parts]), ref)
+    rate = max(I.boundary_layer_rate(case, *pp[:3]) for pp in parts)
+    assert case.dt == 0.5 / rate

@@ -1,0 +1,114 @@
+"""The exchanges of the y-slab decomposition on the host (gloo ranks, no GPU): which slots every
+slab reads (ns_slab_slots, the library's host-only query), their sizes (ns_slab_slot_bytes), the
+order of phases and exchanges of a sub-step, and that DistExchange delivers exactly slab s's send
+buffer into slot s of every slab that reads it, by point-to-point messages between neighbours or
+by an all-gather (Sec. 3.2: PDD exchanges with neighbours, PPT gathers every slab's ends)."""
+import os
+import socket
+import sys
+
+import pytest
+
+torch = pytest.importorskip("torch")
+import torch.distributed as dist  # noqa: E402
+import torch.multiprocessing as mp  # noqa: E402
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_1812_01178_gb300 import binding as B  # noqa: E402
+from paper_1812_01178_gb300 import inputs as I  # noqa: E402
+from paper_1812_01178_gb300 import slabs as S  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not os.path.exists(B.LIB_PATH):
+        from paper_1812_01178_gb300 import build
+        build.build()
+
+
+def test_slots_each_slab_reads():
+    p = 5
+    for r in range(p):
+        below, above = max(0, r - 1), min(p - 1, r + 1)
+        assert S.slots(p, r, S.NS_XCH_HALO, B.NS_PART_PDD) == (below, above)
+        assert S.slots(p, r, S.NS_XCH_ADIY, B.NS_PART_PDD) == (below, above)
+        assert S.slots(p, r, S.NS_XCH_ADIY, B.NS_PART_PPT) == (0, p - 1)
+        assert S.slots(p, r, S.NS_XCH_VSTAR, B.NS_PART_PDD) == (r, above)
+        assert S.slots(p, r, S.NS_XCH_POIS, B.NS_PART_PDD) == (0, p - 1)
+        assert S.slots(p, r, S.NS_XCH_PHI, B.NS_PART_PDD) == (below, r)
+
+
+def test_rows_and_slot_sizes():
+    case, *_ = I.small_channel(64, 37, 32)
+    cfg = B.make_config(case)
+    rows = [S.rows(37, 4, r) for r in range(4)]
+    assert rows[0][0] == 0 and rows[-1][1] == 37
+    assert all(a[1] == b[0] for a, b in zip(rows, rows[1:]))
+    assert all(3 <= j1 - j0 <= 10 for j0, j1 in rows)
+    plane = 64 * 32 * 8
+    assert S.slot_bytes(cfg, 4, S.NS_XCH_HALO) == 8 * plane      # u, w, p, v rows, both sides
+    assert S.slot_bytes(cfg, 4, S.NS_XCH_ADIY) == 6 * plane      # x~_1, x~_m of u, v, w
+    assert S.slot_bytes(cfg, 4, S.NS_XCH_VSTAR) == plane
+    assert S.slot_bytes(cfg, 4, S.NS_XCH_PHI) == plane
+    assert S.slot_bytes(cfg, 4, S.NS_XCH_POIS) == 2 * 17 * 64 * 16   # complex ends per (kx, kz)
+    assert B.lib().ns_slab_workspace_bytes(B.make_config(case), 13, 0) == 0  # fewer than 3 rows a slab
+
+
+class _FakeSlab:
+    """Stands in for a slab on the host: a phase writes a tag (slab, exchange, sub-step) into the
+    send buffer of the exchange that follows it and records itself."""
+
+    def __init__(self, r, send, log):
+        self.r, self.send, self.log = r, send, log
+        self.next = {ph: x for ph, x in S.SUBSTEP}
+        self.next[S.NS_SLAB_PACK] = S.NS_XCH_HALO
+
+    def phase(self, ph, k):
+        self.log.append((ph, k))
+        x = self.next[ph]
+        self.send[x].copy_(torch.full_like(self.send[x], (self.r * 16 + x * 3 + k) % 256))
+
+
+def _worker(rank, world, port, ymode):
+    sys.path.insert(0, ROOT)
+    dist.init_process_group("gloo", init_method="tcp://127.0.0.1:%d" % port, rank=rank, world_size=world)
+    try:
+        case, *_ = I.small_channel(16, 3 * world + 2, 8)
+        cfg = B.make_config(case)
+        sizes = [S.slot_bytes(cfg, world, x) for x in range(S.NS_XCH_COUNT)]
+        send = [torch.zeros(n, dtype=torch.uint8) for n in sizes]
+        recv = [torch.full((world, n), 255, dtype=torch.uint8) for n in sizes]
+        log = []
+        slab = _FakeSlab(rank, send, log)
+        ex = S.DistExchange(dist, world, rank, ymode, send, recv)
+        seen = []
+
+        def exchange(x):
+            ex(x)
+            lo, hi = S.slots(world, rank, x, ymode)
+            k = log[-1][1]
+            for s in range(lo, hi + 1):
+                if s != rank:
+                    assert int(recv[x][s].min()) == int(recv[x][s].max()) == (s * 16 + x * 3 + k) % 256, (x, s)
+            seen.append(x)
+
+        S.run_steps([slab], exchange, 1)
+        # PACK, HALO, then per sub-step RHS/ADIY, ADIZ/VSTAR, POIS/POIS, PHI/PHI, PROJECT/HALO
+        assert [ph for ph, _ in log] == [S.NS_SLAB_PACK] + [ph for _ in range(3) for ph, _ in S.SUBSTEP]
+        assert seen == [S.NS_XCH_HALO] + [x for _ in range(3) for _, x in S.SUBSTEP]
+    finally:
+        dist.destroy_process_group()
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+@pytest.mark.parametrize("world,ymode", [(2, B.NS_PART_PDD), (3, B.NS_PART_PDD), (3, B.NS_PART_PPT)])
+def test_gloo_ranks_exchange_what_each_slab_reads(world, ymode):
+    mp.start_processes(_worker, args=(world, _free_port(), ymode), nprocs=world, join=True, start_method="spawn")
