@@ -228,6 +228,33 @@ NS_HD void dt_ztab(const DtSpec& s, int k, void* out, double* scratch) {
   for (int j = 0; j < nz; ++j) put_es(out, 3 * (size_t)nz + j, q[j], es);
   put_es(out, 4 * (size_t)nz, fac, es);
   put_es(out, 4 * (size_t)nz + 1, bg, es);
+  // The same rows are circulant (uniform, periodic z) and factor exactly as
+  //   A = alpha (I - lam S)(I - lam S^-1),  S the cyclic shift, (S x)_j = x_{j-1},
+  // with lam = 2r / (1 + 2r + sqrt(1 + 4r)) (the root below 1 of lam + 1/lam = (1 + 2r) / r) and
+  // alpha = r / lam, so A x = d is two first-order cyclic recurrences (t_j = d_j + lam t_{j-1},
+  // then x_j = t_j + lam x_{j+1}, x = result / alpha).  Each starts from its periodic sum,
+  // t_0 = sum_k lam^k d_{-k}, truncated after the K terms with lam^(K+1) > 1e-17 (the spike
+  // truncation tolerance of the x solve).  use = 0 (the Thomas path) in the float table, or when
+  // K exceeds NS_ZF_KMAX or the line.
+  const double lam = 2.0 * r / (1.0 + 2.0 * r + sqrt(1.0 + 4.0 * r));
+  const double ialpha = r > 0.0 ? lam / r : 1.0;
+  int K = 0;
+  double pw = lam;  // lam^(K+1)
+  while (pw > 1e-17 && K <= NS_ZF_KMAX) {
+    ++K;
+    pw *= lam;
+  }
+  const bool use = es == 8 && K <= NS_ZF_KMAX && K + 1 < nz;
+  const size_t z0 = 4 * (size_t)nz + 2;
+  put_es(out, z0, lam, es);
+  put_es(out, z0 + 1, ialpha, es);
+  put_es(out, z0 + 2, use ? 1.0 : 0.0, es);
+  put_es(out, z0 + 3, (double)(use ? K : 0), es);
+  double lk = lam;
+  for (int q = 0; q < NS_ZF_KMAX; ++q) {
+    put_es(out, z0 + 4 + q, use && q < K ? lk : 0.0, es);
+    lk *= lam;
+  }
 }
 
 // ---------------------------------------------------------------------------------------------

@@ -538,6 +538,57 @@ struct AdiZK {
   const long base = (long)j * nx + i;
   T* line = (comp == 0 ? ru : comp == 1 ? rv : rw) + base;
   double* f = (comp == 0 ? u : comp == 1 ? v : w) + base;
+  constexpr int U = 4;
+  if constexpr (sizeof(T) == 8) {
+    const T* Z = tab + 4 * nz + 2;
+    if (__ldg(Z + 2) != 0.0) {  // uniform over the grid: the factorised circulant form (dt_ztab)
+      const double lam = __ldg(Z), ia = __ldg(Z + 1);
+      const int K = (int)__ldg(Z + 3);
+      const T* LP = Z + 4;  // lam^1 .. lam^KMAX
+      // forward recurrence t_j = d_j + lam t_{j-1} from t_0 = d_0 + sum_k lam^k d_{nz-k}
+      double t = line[0];
+#pragma unroll
+      for (int q = 1; q <= NS_ZF_KMAX; ++q)
+        if (q <= K) t = fma(__ldg(LP + q - 1), line[(long)(nz - q) * stride], t);
+      line[0] = t;
+      for (int k0 = 1; k0 < nz; k0 += U) {
+        double dv[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+          if (k0 + u < nz) dv[u] = line[(long)(k0 + u) * stride];
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+          if (k0 + u < nz) {
+            t = fma(lam, t, dv[u]);
+            line[(long)(k0 + u) * stride] = t;
+          }
+      }
+      // backward recurrence x_j = t_j + lam x_{j+1} from x_{nz-1} = t_{nz-1} + sum_k lam^k t_{k-1};
+      // u* = u + x / alpha
+      // (t_0 .. t_{K-1} are read back from the line: this thread wrote them)
+      double x = t;
+#pragma unroll
+      for (int q = 1; q <= NS_ZF_KMAX; ++q)
+        if (q <= K) x = fma(__ldg(LP + q - 1), line[(long)(q - 1) * stride], x);
+      f[(long)(nz - 1) * stride] = fma(x, ia, f[(long)(nz - 1) * stride]);
+      for (int k1 = nz - 2; k1 >= 0; k1 -= U) {
+        double dv[U], fv[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+          if (k1 - u >= 0) {
+            dv[u] = line[(long)(k1 - u) * stride];
+            fv[u] = f[(long)(k1 - u) * stride];
+          }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+          if (k1 - u >= 0) {
+            x = fma(lam, x, dv[u]);
+            f[(long)(k1 - u) * stride] = fma(x, ia, fv[u]);
+          }
+      }
+      return;
+    }
+  }
   const T* INV = tab;
   const T* AINV = tab + nz;
   const T* CP = tab + 2 * nz;
@@ -545,7 +596,6 @@ struct AdiZK {
   const T fac = __ldg(tab + 4 * nz);
   const T bg = __ldg(tab + 4 * nz + 1);
   // Thomas on the Sherman-Morrison-modified matrix, rows fetched U at a time ahead
-  constexpr int U = 4;
   T prev = (T)0;
   for (int k0 = 0; k0 < nz; k0 += U) {
     T dv[U];
@@ -796,4 +846,4 @@ cudaError_t adi_set_attributes() {
 }
 
 size_t adi_y_tab_count(int ny) { return 3 * (size_t)ny; }
-size_t adi_z_tab_count(int nz) { return 4 * (size_t)nz + 2; }
+size_t adi_z_tab_count(int nz) { return ztab_entries(nz); }

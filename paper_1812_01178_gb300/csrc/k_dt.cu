@@ -331,7 +331,7 @@ ns_status build_dt_tables(ns_ctx* c) {
       dt_ytab(s, k, cls, buf.data());
       if (upload_raw(c, c->ytab[k][cls], buf.data(), buf.size()) != cudaSuccess) st = NS_ERR_CUDA;
     }
-    buf.assign((4 * (size_t)nz + 2) * s.es, 0);
+    buf.assign(ztab_entries(nz) * s.es, 0);
     dt_ztab(s, k, buf.data(), scr.data());
     if (st == NS_OK && upload_raw(c, c->ztab[k], buf.data(), buf.size()) != cudaSuccess) st = NS_ERR_CUDA;
   }

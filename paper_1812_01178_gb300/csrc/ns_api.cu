@@ -90,7 +90,7 @@ ns_layout make_layout(const ns_config* c) {
   sz[LB_GC] = NS_GC_COUNT * (ny + 1) * 8;
   sz[LB_XTAB] = 6 * al256(x_table_elems(c) * es);
   sz[LB_YTAB] = 6 * al256(3 * ny * es);
-  sz[LB_ZTAB] = 3 * al256((4 * nz + 2) * es);
+  sz[LB_ZTAB] = 3 * al256(ztab_entries(nz) * es);
   sz[LB_TWZ] = fft_twiddle_doubles((int)nz) * 8;
   sz[LB_TWX] = fft_twiddle_doubles((int)nx) * 8;
   sz[LB_LAMX] = nx * 8;
@@ -372,7 +372,7 @@ ns_status ns_init(ns_ctx** out, const ns_config* cfg, const ns_fields* fields, v
     for (int cls = 0; cls < 2; ++cls)
       c->xtab[k][cls] = base + c->lay.off[LB_XTAB] + (2 * k + cls) * al256(c->xtab_stride * c->es);
     for (int q = 0; q < 2; ++q) c->ytab[k][q] = base + c->lay.off[LB_YTAB] + (2 * k + q) * al256(3 * ny * c->es);
-    c->ztab[k] = base + c->lay.off[LB_ZTAB] + k * al256((4 * nz + 2) * c->es);
+    c->ztab[k] = base + c->lay.off[LB_ZTAB] + k * al256(ztab_entries(nz) * c->es);
   }
   c->twz = (double2*)(base + c->lay.off[LB_TWZ]);
   c->twx = (double2*)(base + c->lay.off[LB_TWX]);

@@ -500,3 +500,9 @@ std::vector<double> grid_coefficients_host(const ns_config* cfg);
 // Host-side table builders (ns_tables.cpp-style code lives in ns_api.cu).
 size_t adi_y_tab_count(int ny);
 size_t adi_z_tab_count(int nz);
+
+// Entries of a z-sweep table (dt_ztab): the Sherman-Morrison Thomas factors INV, AINV, CP and the
+// vector Q (nz each), fac, bg, then the factorised circulant form: lambda, 1/alpha, use (1 or 0),
+// K, lambda^1 .. lambda^NS_ZF_KMAX.
+constexpr int NS_ZF_KMAX = 8;
+inline size_t ztab_entries(int nz) { return 4 * (size_t)nz + 2 + 4 + NS_ZF_KMAX; }
