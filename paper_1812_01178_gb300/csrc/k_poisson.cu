@@ -1128,6 +1128,10 @@ __global__ void pois_factor_kernel(double2* __restrict__ fac, const double* __re
 
 cudaError_t poisson_set_attributes() {
   set_smem_limit<DivzK>(200 * 1024);
+  set_smem_limit<DivzMK<false>>(200 * 1024);
+  set_smem_limit<DivzMK<true>>(200 * 1024);
+  set_smem_limit<IfftzMK<false>>(200 * 1024);
+  set_smem_limit<IfftzMK<true>>(200 * 1024);
   set_smem_limit<IfftzK>(200 * 1024);
   set_smem_limit<FftxK<-1>>(200 * 1024);
   set_smem_limit<FftxK<1>>(200 * 1024);
@@ -1163,7 +1167,7 @@ static int z_tile(int nz) {
 
 namespace {
 struct PoisShape {
-  int nx, ny, nz, pz, px, TX, R;
+  int nx, ny, nz, pz, px, TX, R, TXm;
   size_t smz, smx;
   long nrows;
   unsigned bx;
@@ -1178,6 +1182,14 @@ PoisShape pois_shape(const ns_ctx* c) {
   q.TX = z_tile(q.nz);
   while (q.nx % q.TX) q.TX >>= 1;  // TX divides nx (nx is a multiple of 8)
   q.smz = (size_t)q.TX * q.nz * sizeof(double2);  // two buffers of TX/2 sequences
+  // the FP32 z transforms of the mixed form (complex64): TX nz 8 bytes <= 32 KB, but at least 8
+  // columns while that stays within 160 KB; 4-column tiles of long lines leave those kernels far
+  // from their bounds (2048x288x1024 divergence + z FFT 15.9 -> 8.4 ms at 8 columns; wider tiles
+  // are slower at every size measured)
+  q.TXm = 16;
+  while (q.TXm > 2 && (size_t)q.TXm * q.nz * 8 > 32 * 1024) q.TXm >>= 1;
+  if (q.TXm < 8 && (size_t)8 * q.nz * 8 <= 160 * 1024) q.TXm = 8;
+  while (q.nx % q.TXm) q.TXm >>= 1;
   q.nrows = (long)c->nzh * q.ny;
   q.R = 1;
   while (q.R < 16 && (size_t)2 * q.R * 2 * q.nx * sizeof(double2) <= 64 * 1024) q.R <<= 1;
@@ -1217,7 +1229,8 @@ cudaError_t emit_divzm(LaunchSink& s, int k) {
   a.inv_nxnz = 1.0 / ((double)q.nx * q.nz);
   a.sk = c->stepk + stepk_index(k);
   a.u_out = c->bl ? c->f.u_out : nullptr;
-  return emit<DivzMK<RES>>(s, a, dim3(q.nx / q.TX, q.ny), dim3(256), q.smz / 2);
+  a.TX = q.TXm;
+  return emit<DivzMK<RES>>(s, a, dim3(q.nx / q.TXm, q.ny), dim3(256), (size_t)q.TXm * q.nz * sizeof(float2));
 }
 
 cudaError_t emit_xm(LaunchSink& s, bool fwd) {
@@ -1266,8 +1279,9 @@ template <bool ACC>
 cudaError_t emit_ifftzm(LaunchSink& s) {
   ns_ctx* c = s.c;
   const PoisShape q = pois_shape(c);
-  return emit<IfftzMK<ACC>>(s, typename IfftzMK<ACC>::Args{sp32(c), c->twz32, phi1(c), c->phi, q.nx, q.ny, q.nz, q.pz, q.TX},
-                            dim3(q.nx / q.TX, q.ny), dim3(256), q.smz / 2);
+  return emit<IfftzMK<ACC>>(s, typename IfftzMK<ACC>::Args{sp32(c), c->twz32, phi1(c), c->phi, q.nx, q.ny, q.nz, q.pz,
+                                                           q.TXm},
+                            dim3(q.nx / q.TXm, q.ny), dim3(256), (size_t)q.TXm * q.nz * sizeof(float2));
 }
 
 void single_kernel_dct_fwd(ns_ctx* c, unsigned bx, size_t smx, long nrows, int nx, int px, int R) {
