@@ -344,19 +344,22 @@ void ns_batch_destroy(ns_batch* b);
  * is one GPU's share in the paper's multi-GPU method.  Everything along x and z is local to a slab;
  * the y sweep of the ADI factorisation is split across slabs by PDD (Sec. 3.2, Eq. (Zpdd): one
  * exchange of end values with the two neighbours, Algorithm 1) or PPT (Eq. (Zppt): all-gather of
- * the end values), and the Poisson y solve of every (kx, kz) line by PPT.  Built for periodic x,
- * NS_FP64 and the plain pressure update (other configurations: NS_ERR_ARG); every slab needs at
- * least 3 rows (ny >= 3 p).
+ * the end values), and the Poisson y solve of every (kx, kz) line by PPT.  With inflow /
+ * convective outflow in x, the outflow mass-flux correction sums every slab's share (FLUX
+ * exchange, an all-gather of one double).  Built for NS_FP64, the plain pressure update and fixed
+ * inflow planes (other configurations: NS_ERR_ARG); every slab needs at least 3 rows (ny >= 3 p).
  *
  * Local fields.  A slab's u, w, p hold rows j0-hb .. j1+ha-1 and its v the faces j0-hb .. j1+ha,
  * where hb = (r > 0) and ha = (r < p-1) are the halo rows below and above (layouts as above with
- * ny replaced by the local row count nyl + hb + ha).  The caller fills the owned rows; the halo
- * rows are filled by the exchanges.
+ * ny replaced by the local row count nyl + hb + ha); so do the five boundary planes of inflow /
+ * outflow x.  The caller fills the owned rows (and, for the boundary planes, the halo rows too);
+ * the halo rows of u, v, w, p are filled by the exchanges.
  *
  * Exchanges.  A sub-step is six phases (NS_SLAB_*) with an exchange after each:
- *   PACK (before the first sub-step only) -> HALO -> RHS -> ADIY -> ADIZ -> VSTAR -> POIS -> POIS
- *   -> PHI -> PHI -> PROJECT -> HALO (ready for the next sub-step's RHS)
- * where the exchange named after a phase is NS_XCH_<name>.  For exchange x every slab has a send
+ *   PACK (before the first sub-step only) -> HALO -> RHS -> ADIY -> ADIZ -> VSTAR, FLUX -> POIS
+ *   -> POIS -> PHI -> PHI -> PROJECT -> HALO (ready for the next sub-step's RHS)
+ * where the exchange named after a phase is NS_XCH_<name> (FLUX only matters with inflow /
+ * outflow x; with periodic x it carries nothing the slabs read).  For exchange x every slab has a send
  * buffer of ns_slab_slot_bytes bytes and a receive buffer of p such slots; after the phase that
  * writes its send buffer, the caller copies slab s's send buffer into slot s of every slab r that
  * reads it (ns_slab_slots: slots lo .. hi of slab r; the slab's own slot, where read, it writes
@@ -364,7 +367,8 @@ void ns_batch_destroy(ns_batch* b);
  * GPU, device copies.  Buffers come from ns_slab_buffers.
  * ------------------------------------------------------------------------------------------- */
 typedef struct ns_slab ns_slab;
-enum { NS_XCH_HALO = 0, NS_XCH_ADIY = 1, NS_XCH_VSTAR = 2, NS_XCH_POIS = 3, NS_XCH_PHI = 4, NS_XCH_COUNT = 5 };
+enum { NS_XCH_HALO = 0, NS_XCH_ADIY = 1, NS_XCH_VSTAR = 2, NS_XCH_POIS = 3, NS_XCH_PHI = 4, NS_XCH_FLUX = 5,
+       NS_XCH_COUNT = 6 };
 enum { NS_SLAB_PACK = 0, NS_SLAB_RHS = 1, NS_SLAB_ADIZ = 2, NS_SLAB_POIS = 3, NS_SLAB_PHI = 4,
        NS_SLAB_PROJECT = 5 };
 

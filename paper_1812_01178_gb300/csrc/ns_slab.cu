@@ -2,7 +2,8 @@
 // algorithms", and Algorithm 1): the domain is cut into p slabs of whole x-z planes, slab r holding
 // the cell rows [j0, j1) of y.  Everything along x and z (RHS, x and z sweeps, x and z
 // transforms, projection) is local to a slab; the two solves along y are split across slabs with
-// the partitioned tridiagonal algorithms of Sec. 3.2:
+// the partitioned tridiagonal algorithms of Sec. 3.2 (inflow / convective outflow in x adds one
+// all-gather of each slab's share of the outflow flux correction):
 //   * the y sweep of the ADI factorisation by PDD (one exchange of the end values x~_1, x~_m with
 //     the two neighbouring slabs, Algorithm 1) where the coupling PDD drops is negligible, else
 //     by PPT (all-gather of the end values, every slab solving the whole reduced system);
@@ -65,7 +66,6 @@ std::string check_slab(const ns_config* cfg, int p, int r) {
   if (!cfg || !cfg->yf) return "cfg or cfg->yf is NULL";
   if (p < 1 || p > 64) return "p must be in [1, 64]";
   if (r < 0 || r >= p) return "r must be in [0, p)";
-  if (cfg->bc_x != 0) return "slabs are built for periodic x";
   if (cfg->precision != NS_FP64) return "slabs are built for NS_FP64";
   if (cfg->pressure_update != NS_PRESSURE_DELTA || cfg->recycle_i != 0)
     return "slabs are built for the plain pressure update without recycling";
@@ -94,6 +94,7 @@ size_t slot_bytes(const ns_config* g, int xch) {
     case NS_XCH_VSTAR: return al256(plane);
     case NS_XCH_POIS: return al256(2 * nzh * g->nx * 16);
     case NS_XCH_PHI: return al256(plane);
+    case NS_XCH_FLUX: return 256;  // one double: this slab's share of Q_in - Q_out
     default: return 0;
   }
 }
@@ -390,6 +391,42 @@ __global__ void __launch_bounds__(128) slab_pois_correct(const PArgs a) {
   for (int j = 0; j < a.m; ++j) d[j * sd] -= V[(long)j * a.nx] * ylo + W[(long)j * a.nx] * yhi;
 }
 
+// Outflow mass-flux correction across slabs (inflow / outflow x): each slab sums
+// (u_in - u_out) dy_j over its own rows (one block, fixed order) into its FLUX send buffer and its
+// own slot; after the all-gather every slab adds the p shares in slab order and shifts u_out by
+// the same amount on all its rows (halo rows too: they mirror the neighbours' own rows).
+__global__ void __launch_bounds__(1024) slab_flux_partial(const double* __restrict__ u, const double* __restrict__ u_out,
+                                                          const double* __restrict__ gc, int nx, int nyv, int nz,
+                                                          int jo, int m, double* send, double* own) {
+  __shared__ double red[1024];
+  const double* dy = gc + GC_DY * (nyv + 1);
+  const long n = (long)nz * m;
+  double acc = 0.0;
+  for (long q = threadIdx.x; q < n; q += blockDim.x) {
+    const int j = jo + (int)(q % m);
+    const long pq = (q / m) * nyv + j;  // plane index k * rows + j
+    acc += (__ldg(u + pq * nx) - u_out[pq]) * __ldg(dy + j);
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s2 = blockDim.x / 2; s2 > 0; s2 >>= 1) {
+    if (threadIdx.x < s2) red[threadIdx.x] += red[threadIdx.x + s2];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    *send = red[0];
+    *own = red[0];
+  }
+}
+
+__global__ void slab_flux_apply(double* __restrict__ u_out, long n, const double* __restrict__ recv, size_t slot, int p,
+                                double dz_over_area) {
+  double tot = 0.0;
+  for (int q = 0; q < p; ++q) tot += recv[(size_t)q * slot];
+  const double corr = tot * dz_over_area;
+  for (long q = (long)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (long)gridDim.x * blockDim.x) u_out[q] += corr;
+}
+
 ns_status slab_fail(ns_slab* s, ns_status st, const std::string& m) {
   if (s) s->err = m;
   ns_set_thread_error(m.c_str());
@@ -584,9 +621,11 @@ ns_status build_slab_tables(ns_slab* s, char* base) {
   std::vector<double> a(ny), b(ny), cc(ny);
   for (int kz = 0; kz < nzh; ++kz)
     for (int i = 0; i < nx; ++i) {
+      // periodic x: the DFT's wavenumbers; inflow / outflow: the cosine transform's (DCT-II)
       const int ii = i <= nx - i ? i : nx - i;
-      const double lam = (2.0 / (dx * dx)) * (1.0 - std::cos(2.0 * PI * ii / nx)) +
-                         (2.0 / (dz * dz)) * (1.0 - std::cos(2.0 * PI * kz / nz));
+      const double lamx = g->bc_x == 1 ? (2.0 / (dx * dx)) * (1.0 - std::cos(PI * i / nx))
+                                       : (2.0 / (dx * dx)) * (1.0 - std::cos(2.0 * PI * ii / nx));
+      const double lam = lamx + (2.0 / (dz * dz)) * (1.0 - std::cos(2.0 * PI * kz / nz));
       for (int j = 0; j < ny; ++j) {
         a[j] = GC(GC_PA, j);
         cc[j] = GC(GC_PC, j);
@@ -662,6 +701,7 @@ ns_status ns_slab_slots(int p, int r, int xch, int ymode, int* lo, int* hi) {
     case NS_XCH_VSTAR: *lo = r, *hi = above; break;
     case NS_XCH_POIS: *lo = 0, *hi = p - 1; break;
     case NS_XCH_PHI: *lo = below, *hi = r; break;
+    case NS_XCH_FLUX: *lo = 0, *hi = p - 1; break;
     default: return NS_ERR_ARG;
   }
   return NS_OK;
@@ -750,6 +790,7 @@ ns_status ns_slab_phase(ns_slab* s, int phase, int k) {
     case NS_SLAB_RHS:
       if ((e = unpack_halo(s)) != cudaSuccess) break;
       if ((e = launch_rhs(c, k)) != cudaSuccess) break;
+      if ((e = launch_outflow(c, k)) != cudaSuccess) break;  // inflow / outflow only
       if ((e = launch_adi_x(c, k)) != cudaSuccess) break;
       slab_ysweep_local<<<ygrid, 128, 0, c->stream>>>(y_args(s, k));
       e = cudaGetLastError();
@@ -758,10 +799,24 @@ ns_status ns_slab_phase(ns_slab* s, int phase, int k) {
       slab_ysweep_correct<<<ygrid, 128, 0, c->stream>>>(y_args(s, k));
       if ((e = cudaGetLastError()) != cudaSuccess) break;
       if ((e = launch_adi_z(c, k)) != cudaSuccess) break;
-      if (s->r > 0)  // v* on face j0, which slab r-1 reads for the divergence of its top row
-        e = copy_row_out(c->f.v, s->nyv + 1, s->hb, nx, nz, (double*)s->send[NS_XCH_VSTAR], c->stream);
+      if (s->r > 0 &&  // v* on face j0, which slab r-1 reads for the divergence of its top row
+          (e = copy_row_out(c->f.v, s->nyv + 1, s->hb, nx, nz, (double*)s->send[NS_XCH_VSTAR], c->stream)) !=
+              cudaSuccess)
+        break;
+      if (c->bl) {  // this slab's share of the inflow - outflow volume flux
+        slab_flux_partial<<<1, 1024, 0, c->stream>>>(c->f.u, c->f.u_out, c->gc, nx, s->nyv, nz, s->hb, s->nyl,
+                                                     (double*)s->send[NS_XCH_FLUX],
+                                                     (double*)(s->recv[NS_XCH_FLUX] + (size_t)s->r * s->slot[NS_XCH_FLUX]));
+        e = cudaGetLastError();
+      }
       break;
     case NS_SLAB_POIS:
+      if (c->bl) {  // u_out shifted so that the outflow flux equals the inflow flux (every slab alike)
+        const double area = (s->gyf[s->gcfg.ny] - s->gyf[0]) * s->gcfg.lz;
+        slab_flux_apply<<<64, 256, 0, c->stream>>>(c->f.u_out, (long)nz * s->nyv, (const double*)s->recv[NS_XCH_FLUX],
+                                                   s->slot[NS_XCH_FLUX] / 8, s->p, c->dz / area);
+        if ((e = cudaGetLastError()) != cudaSuccess) break;
+      }
       if (s->r < s->p - 1 &&
           (e = copy_row_in(c->f.v, s->nyv + 1, s->hb + s->nyl, nx, nz,
                            (const double*)(s->recv[NS_XCH_VSTAR] + (size_t)(s->r + 1) * s->slot[NS_XCH_VSTAR]),

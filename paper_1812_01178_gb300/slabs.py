@@ -20,12 +20,12 @@ import numpy as np
 
 from . import binding as B
 
-NS_XCH_HALO, NS_XCH_ADIY, NS_XCH_VSTAR, NS_XCH_POIS, NS_XCH_PHI, NS_XCH_COUNT = range(6)
+NS_XCH_HALO, NS_XCH_ADIY, NS_XCH_VSTAR, NS_XCH_POIS, NS_XCH_PHI, NS_XCH_FLUX, NS_XCH_COUNT = range(7)
 NS_SLAB_PACK, NS_SLAB_RHS, NS_SLAB_ADIZ, NS_SLAB_POIS, NS_SLAB_PHI, NS_SLAB_PROJECT = range(6)
 
-# one RK3 sub-step: each phase, then the exchange that moves what it wrote
-SUBSTEP = ((NS_SLAB_RHS, NS_XCH_ADIY), (NS_SLAB_ADIZ, NS_XCH_VSTAR), (NS_SLAB_POIS, NS_XCH_POIS),
-           (NS_SLAB_PHI, NS_XCH_PHI), (NS_SLAB_PROJECT, NS_XCH_HALO))
+# one RK3 sub-step: each phase, then the exchanges that move what it wrote
+SUBSTEP = ((NS_SLAB_RHS, (NS_XCH_ADIY,)), (NS_SLAB_ADIZ, (NS_XCH_VSTAR, NS_XCH_FLUX)),
+           (NS_SLAB_POIS, (NS_XCH_POIS,)), (NS_SLAB_PHI, (NS_XCH_PHI,)), (NS_SLAB_PROJECT, (NS_XCH_HALO,)))
 
 
 def rows(ny, p, r):
@@ -57,17 +57,18 @@ def run_steps(slabs, exchange, nsteps, first=True):
         exchange(NS_XCH_HALO)
     for _ in range(nsteps):
         for k in range(3):
-            for ph, xch in SUBSTEP:
+            for ph, xchs in SUBSTEP:
                 for s in slabs:
                     s.phase(ph, k)
-                exchange(xch)
+                for xch in xchs:
+                    exchange(xch)
 
 
 class Slab:
     """Slab r of p of the whole-domain case: its fields (rows j0-hb .. j1+ha-1, v faces
     j0-hb .. j1+ha) are cut from the whole-domain arrays u, v, w, p given (host arrays)."""
 
-    def __init__(self, case, p, r, u, v, w, pr, ymode=B.NS_PART_AUTO, device="cuda:0", stream=None):
+    def __init__(self, case, p, r, u, v, w, pr, ymode=B.NS_PART_AUTO, device="cuda:0", stream=None, bl=None):
         import torch
         self.torch = torch
         self.case, self.p, self.r = case, p, r
@@ -86,8 +87,14 @@ class Slab:
             raise B.NSError(B.NS_ERR_ARG, "configuration not supported by the slab decomposition")
         self.ws = torch.empty(nbytes, dtype=torch.uint8, device=dev)
         self.stream = stream if stream is not None else torch.cuda.current_stream(dev)
-        self.fields = B.ns_fields(self.u.data_ptr(), self.v.data_ptr(), self.w.data_ptr(), self.pr.data_ptr(),
-                                  None, None, None, None, None)
+        # boundary planes of inflow / outflow x (index k * rows + j), halo rows included
+        self.bl = None
+        bptr = [None] * 5
+        if case.bc_x == 1:
+            names = ("u_out", "v_in", "v_out", "w_in", "w_out")
+            self.bl = {q: put(bl[q][:, lo:hi + (1 if q[0] == "v" else 0)]) for q in names}
+            bptr = [self.bl[q].data_ptr() for q in names]
+        self.fields = B.ns_fields(self.u.data_ptr(), self.v.data_ptr(), self.w.data_ptr(), self.pr.data_ptr(), *bptr)
         self.h = C.c_void_p()
         st = B.lib().ns_slab_init(C.byref(self.h), C.byref(self.cfg), p, r, ymode, C.byref(self.fields),
                                   self.ws.data_ptr(), nbytes, self.stream.cuda_stream)
@@ -127,6 +134,13 @@ class Slab:
         return (self.u[:, a:b].cpu().numpy(), self.v[:, a:vb].cpu().numpy(), self.w[:, a:b].cpu().numpy(),
                 self.pr[:, a:b].cpu().numpy())
 
+    def owned_planes(self):
+        """The owned rows of the boundary planes (inflow / outflow x), as host arrays."""
+        self.sync()
+        a, b = self.hb, self.hb + (self.j1 - self.j0)
+        vb = b + (1 if self.r == self.p - 1 else 0)
+        return {q: t[:, a:(vb if q[0] == "v" else b)].cpu().numpy() for q, t in self.bl.items()}
+
     def close(self):
         if getattr(self, "h", None) is not None and self.h.value:
             B.lib().ns_slab_destroy(self.h)
@@ -158,11 +172,17 @@ class DistExchange:
     """The exchanges of this rank's slab over torch.distributed (one slab per rank, rank = slab
     index, world size = p).  An exchange whose every slot is read by every slab is an all-gather;
     the others are point-to-point sends to the slabs that read this slab's slot and receives from
-    the slots this slab reads."""
+    the slots this slab reads.  host=True stages device buffers through host memory, for a
+    backend that moves host tensors only (gloo)."""
 
-    def __init__(self, dist, p, r, ymode, send, recv):
+    def __init__(self, dist, p, r, ymode, send, recv, host=False):
         self.dist, self.p, self.r, self.ymode = dist, p, r, ymode
         self.send, self.recv = send, recv   # per exchange: send tensor, (p, slot) receive tensor
+        self.host = host
+        if host:
+            import torch
+            self.hsend = [torch.empty(t.shape, dtype=t.dtype) for t in send]
+            self.hrecv = [torch.empty(t.shape, dtype=t.dtype) for t in recv]
 
     def readers(self, xch):
         """Slabs other than this one that read this slab's slot."""
@@ -170,20 +190,31 @@ class DistExchange:
                 <= slots(self.p, t, xch, self.ymode)[1]]
 
     def __call__(self, xch):
+        if not self.host:
+            self._move(xch, self.send[xch], self.recv[xch])
+            return
+        self.hsend[xch].copy_(self.send[xch])  # waits for the phase that wrote it (same stream)
+        self._move(xch, self.hsend[xch], self.hrecv[xch])
+        lo, hi = slots(self.p, self.r, xch, self.ymode)
+        for s in range(lo, hi + 1):
+            if s != self.r:  # this slab's own slot is written by the library
+                self.recv[xch][s].copy_(self.hrecv[xch][s])
+
+    def _move(self, xch, send, recv):
         dist, p, r = self.dist, self.p, self.r
         lo, hi = slots(p, r, xch, self.ymode)
         if (lo, hi) == (0, p - 1) and all(slots(p, t, xch, self.ymode) == (0, p - 1) for t in range(p)):
-            dist.all_gather(list(self.recv[xch].unbind(0)), self.send[xch])
+            dist.all_gather(list(recv.unbind(0)), send)
             return
-        recvs = [(s, self.recv[xch][s]) for s in range(lo, hi + 1) if s != r]
+        recvs = [(s, recv[s]) for s in range(lo, hi + 1) if s != r]
         sends = self.readers(xch)
         if dist.get_backend() == "nccl":
             # NCCL point-to-point must be one group: neighbours that each send before they receive
             # would otherwise wait for one another
             ops = [dist.P2POp(dist.irecv, t, s) for s, t in recvs]
-            ops += [dist.P2POp(dist.isend, self.send[xch], t) for t in sends]
+            ops += [dist.P2POp(dist.isend, send, t) for t in sends]
             reqs = dist.batch_isend_irecv(ops) if ops else []
         else:
-            reqs = [dist.irecv(t, s) for s, t in recvs] + [dist.isend(self.send[xch], t) for t in sends]
+            reqs = [dist.irecv(t, s) for s, t in recvs] + [dist.isend(send, t) for t in sends]
         for q in reqs:
             q.wait()

@@ -143,3 +143,25 @@ def test_checkpoint_at_a_step_boundary_resumes_bitwise(bl):
             assert np.array_equal(t, c.boundary()[q])
     a.close()
     c.close()
+
+
+def test_fp64_fma_probe():
+    """The FP64 throughput probe behind the roofline denominator: arguments checked on the host,
+    every chain's sum finite and equal across threads that start alike, and a rate within the
+    FP64 unit counts of the part (at most 2 FMA per clock per SM at the highest SM clock)."""
+    need_gpu()
+    import ctypes
+    L = B.lib()
+    out = torch.empty(4 * 256, dtype=torch.float64, device="cuda")
+    st = torch.cuda.current_stream().cuda_stream
+    assert L.ns_fp64_fma_probe(None, 4, 8, st) == B.NS_ERR_ARG
+    assert L.ns_fp64_fma_probe(ctypes.c_void_p(out.data_ptr()), 0, 8, st) == B.NS_ERR_ARG
+    assert L.ns_fp64_fma_probe(ctypes.c_void_p(out.data_ptr()), 4, 0, st) == B.NS_ERR_ARG
+    B.ns_fp64_fma_probe(out.data_ptr(), 4, 64, st)
+    v = out.view(4, 256).cpu().numpy()
+    assert np.isfinite(v).all()
+    assert np.array_equal(v[0], v[3])  # every block starts its threads alike
+    import bench
+    tflops, _ = bench.measure_fp64_peak(torch, B, torch.device("cuda", 0), reps=2)
+    props = torch.cuda.get_device_properties(0)
+    assert 0.1 < tflops < props.multi_processor_count * 2 * 2 * 2.2e9 / 1e12, tflops

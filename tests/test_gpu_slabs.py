@@ -114,6 +114,31 @@ def test_slabs_bench_workload_four_slabs():
         assert errs[name] < 1e-12, (name, errs)
 
 
+@pytest.mark.parametrize("P", [2, 4])
+def test_slabs_boundary_layer_match_the_oracle(P):
+    """The paper's flat-plate configuration (inflow / convective outflow in x, stress-free top) in
+    slabs: the outflow planes advance on every slab's rows, and the outflow mass-flux correction
+    adds every slab's share (FLUX all-gather) before the Poisson solve."""
+    case, u, v, w, p, bl = I.boundary_layer(64, 24, 16, amp=0.05, seed=9, re=200.0)
+    g = O.Grid.from_case(case)
+    u, v, w, bl = O.make_divergence_free_bl(g, u, v, w, bl)
+    slabs = [S.Slab(case, P, r, u, v, w, p, bl=bl) for r in range(P)]
+    S.run_steps(slabs, S.LocalExchange(slabs), 2)
+    parts = [s.owned() for s in slabs]
+    planes = [s.owned_planes() for s in slabs]
+    for s in slabs:
+        s.close()
+    got = tuple(np.concatenate([q[f] for q in parts], axis=1) for f in range(4))
+    ref = O.step_bl(g, dict(u=u, v=v, w=w, p=p, bl=bl), case.dt, case.re, case.fx, 2, case.u_conv)
+    errs = field_rel_errors(got, (ref["u"], ref["v"], ref["w"], ref["p"]))
+    for name in ("u", "v", "w", "p"):
+        assert errs[name] < 1e-11, (name, errs)
+    for q in ("u_out", "v_out", "w_out"):
+        plane = np.concatenate([pl[q] for pl in planes], axis=1)
+        np.testing.assert_allclose(plane, ref["bl"][q], rtol=0, atol=1e-11 * np.abs(ref["bl"][q]).max())
+    assert np.abs(O.divergence_bl(g, *got[:3], ref["bl"])).max() < 1e-10
+
+
 def test_slab_arguments_rejected_on_the_host():
     case, g, u, v, w, p = _projected((32, 24, 16), 1)
     with pytest.raises(B.NSError):
@@ -121,3 +146,41 @@ def test_slab_arguments_rejected_on_the_host():
     case.precision = B.NS_MIXED
     with pytest.raises(B.NSError):
         S.Slab(case, 2, 0, u, v, w, p)
+
+
+def _rank_worker(rank, world, port, case, fields, steps, out_dir):
+    import os
+    import sys
+    import torch.distributed as dist
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    from paper_1812_01178_gb300 import slabs as S2
+    dist.init_process_group("gloo", init_method="tcp://127.0.0.1:%d" % port, rank=rank, world_size=world)
+    try:
+        slab = S2.Slab(case, world, rank, *fields)
+        ex = S2.DistExchange(dist, world, rank, slab.ymode, slab.send, slab.recv, host=True)
+        S2.run_steps([slab], ex, steps)
+        np.savez(os.path.join(out_dir, "rank%d.npz" % rank), *slab.owned())
+        slab.close()
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2, 4])
+def test_slabs_as_separate_processes(world, tmp_path):
+    """One slab per process (the paper's one slab per GPU), the exchanges over torch.distributed:
+    gloo between processes that share this GPU, the device buffers staged through host memory.
+    No kernel waits on another process: every exchange is a host-side message between phases."""
+    import socket
+    import torch.multiprocessing as mp
+    case, g, u, v, w, p = _projected((64, 48, 32), 21)
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        port = sk.getsockname()[1]
+    mp.start_processes(_rank_worker, args=(world, port, case, (u, v, w, p), 2, str(tmp_path)), nprocs=world,
+                       join=True, start_method="spawn")
+    parts = [np.load(tmp_path / ("rank%d.npz" % r)) for r in range(world)]
+    got = tuple(np.concatenate([q["arr_%d" % f] for q in parts], axis=1) for f in range(4))
+    ref = O.step(g, dict(u=u, v=v, w=w, p=p), case.dt, case.re, case.fx, 2)
+    errs = field_rel_errors(got, (ref["u"], ref["v"], ref["w"], ref["p"]))
+    for name in ("u", "v", "w", "p"):
+        assert errs[name] < 1e-11, (name, errs)

@@ -39,6 +39,7 @@ def test_slots_each_slab_reads():
         assert S.slots(p, r, S.NS_XCH_VSTAR, B.NS_PART_PDD) == (r, above)
         assert S.slots(p, r, S.NS_XCH_POIS, B.NS_PART_PDD) == (0, p - 1)
         assert S.slots(p, r, S.NS_XCH_PHI, B.NS_PART_PDD) == (below, r)
+        assert S.slots(p, r, S.NS_XCH_FLUX, B.NS_PART_PDD) == (0, p - 1)
 
 
 def test_rows_and_slot_sizes():
@@ -63,13 +64,13 @@ class _FakeSlab:
 
     def __init__(self, r, send, log):
         self.r, self.send, self.log = r, send, log
-        self.next = {ph: x for ph, x in S.SUBSTEP}
-        self.next[S.NS_SLAB_PACK] = S.NS_XCH_HALO
+        self.next = {ph: xs for ph, xs in S.SUBSTEP}
+        self.next[S.NS_SLAB_PACK] = (S.NS_XCH_HALO,)
 
     def phase(self, ph, k):
         self.log.append((ph, k))
-        x = self.next[ph]
-        self.send[x].copy_(torch.full_like(self.send[x], (self.r * 16 + x * 3 + k) % 256))
+        for x in self.next[ph]:
+            self.send[x].copy_(torch.full_like(self.send[x], (self.r * 16 + x * 3 + k) % 256))
 
 
 def _worker(rank, world, port, ymode):
@@ -98,7 +99,7 @@ def _worker(rank, world, port, ymode):
         S.run_steps([slab], exchange, 1)
         # PACK, HALO, then per sub-step RHS/ADIY, ADIZ/VSTAR, POIS/POIS, PHI/PHI, PROJECT/HALO
         assert [ph for ph, _ in log] == [S.NS_SLAB_PACK] + [ph for _ in range(3) for ph, _ in S.SUBSTEP]
-        assert seen == [S.NS_XCH_HALO] + [x for _ in range(3) for _, x in S.SUBSTEP]
+        assert seen == [S.NS_XCH_HALO] + [x for _ in range(3) for _, xs in S.SUBSTEP for x in xs]
     finally:
         dist.destroy_process_group()
 
