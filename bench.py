@@ -523,6 +523,69 @@ def start_bl_names():
     return ("u_out", "v_in", "v_out", "w_in", "w_out")
 
 
+# ------------------------------------------------------------------------------ y slabs
+def bench_slabs(B, torch, dev, s_single, case, steps=5):
+    """The bench workload split into p y-slabs held on this one GPU (the paper's decomposition,
+    Sec. 3.2, with the exchanges as device copies): time per step against the single context,
+    and the difference of the fields after the timed steps.  This measures what the decomposition
+    itself costs (reduced systems, spike corrections, halo rows, exchange copies), not multi-GPU
+    scaling."""
+    from paper_1812_01178_gb300 import slabs as S
+    start = [t.detach().cpu().numpy() for t in (s_single.u, s_single.v, s_single.w, s_single.p)]
+    one = B.Solver(case, *start, device=str(dev))
+    one.step(1)
+    for t, a in zip((one.u, one.v, one.w, one.p), start):
+        t.copy_(torch.from_numpy(a))
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(one.stream)
+    one.step(steps)
+    ev1.record(one.stream)
+    torch.cuda.synchronize()
+    t_one = ev0.elapsed_time(ev1) / steps
+    ref = [t.cpu().numpy() for t in (one.u, one.v, one.w, one.p)]
+    one.close()
+    out = {"workload": "turbulent_channel_%dx%dx%d_fp64" % (case.nx, case.ny, case.nz), "steps": steps,
+           "single_context_ms_per_step": t_one,
+           "timing": "CUDA events around steps issued phase by phase from the host, one stream per slab",
+           "exchange": "device copies between slabs on one GPU (slabs.LocalExchange), ordered by events"}
+    for p in (2, 4):
+        # one stream per slab: the slabs' kernels overlap on the GPU as they would on p GPUs
+        slabs = [S.Slab(case, p, r, *start, device=str(dev), stream=torch.cuda.Stream(dev)) for r in range(p)]
+        ex = S.LocalExchange(slabs)
+        S.run_steps(slabs, ex, 1)  # warm-up
+        torch.cuda.synchronize()
+        for sl in slabs:  # restore the start (halo rows come from the first exchange)
+            sl.u.copy_(torch.from_numpy(start[0][:, sl.j0 - sl.hb:sl.j1 + sl.ha].copy()))
+            sl.v.copy_(torch.from_numpy(start[1][:, sl.j0 - sl.hb:sl.j1 + sl.ha + 1].copy()))
+            sl.w.copy_(torch.from_numpy(start[2][:, sl.j0 - sl.hb:sl.j1 + sl.ha].copy()))
+            sl.pr.copy_(torch.from_numpy(start[3][:, sl.j0 - sl.hb:sl.j1 + sl.ha].copy()))
+        torch.cuda.synchronize()
+        ev0.record(slabs[0].stream)
+        for sl in slabs[1:]:
+            sl.stream.wait_event(ev0)
+        S.run_steps(slabs, ex, steps)
+        for sl in slabs[1:]:
+            e = torch.cuda.Event()
+            e.record(sl.stream)
+            slabs[0].stream.wait_event(e)
+        ev1.record(slabs[0].stream)
+        torch.cuda.synchronize()
+        t_p = ev0.elapsed_time(ev1) / steps
+        parts = [sl.owned() for sl in slabs]
+        got = [np.concatenate([q[f] for q in parts], axis=1) for f in range(4)]
+        vel = math.sqrt(sum(float(np.linalg.norm(a)) ** 2 for a in ref[:3]))
+        err = {n: float(np.linalg.norm(g - r)) / vel for n, g, r in zip("uvw", got[:3], ref[:3])}
+        out["p%d" % p] = {"ms_per_step": t_p, "vs_single_context": t_p / t_one,
+                          "y_sweep": "PDD" if slabs[0].ymode == B.NS_PART_PDD else "PPT",
+                          "pdd_dropped": slabs[0].ydrop, "rel_l2_vs_single_context": err,
+                          "rows_per_slab": [sl.j1 - sl.j0 for sl in slabs]}
+        for sl in slabs:
+            sl.close()
+    return out
+
+
 # ------------------------------------------------------------------------------ main
 def main():
     ap = argparse.ArgumentParser()
@@ -532,11 +595,12 @@ def main():
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--no-cfl", action="store_true")
     ap.add_argument("--no-bl", action="store_true", help="skip the 134M- and 604M-cell boundary-layer records")
+    ap.add_argument("--no-slabs", action="store_true", help="skip the y-slab record (slabs held on one GPU)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -680,6 +744,24 @@ def main():
                 "frac": ach / hbm, "traffic": traffic, "peak_source": "%s hbm_gbs" % hbm_kind,
                 "algorithmic_bytes_per_launch": b * cells}
 
+    # end to end through the host-buffer entry point (pinned host memory)
+    hu = torch.from_numpy(np.ascontiguousarray(u0)).pin_memory().numpy()
+    hv = torch.from_numpy(np.ascontiguousarray(v0)).pin_memory().numpy()
+    hw = torch.from_numpy(np.ascontiguousarray(w0)).pin_memory().numpy()
+    hp = torch.from_numpy(np.ascontiguousarray(p0)).pin_memory().numpy()
+    e2e = None
+    if args.e2e_steps > 0:
+        B.ns_step_host(s.ctx, hu, hv, hw, hp, 1)
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            B.ns_step_host(s.ctx, hu, hv, hw, hp, 1)
+        te = max_over_ranks(torch, dist, time.perf_counter() - t0, dev)
+        nbytes = (hu.nbytes + hv.nbytes + hw.nbytes + hp.nbytes)
+        e2e = {"value": job_throughput(world, cells, args.e2e_steps, te), "unit": UNIT, "h2d_bytes_per_step": nbytes,
+               "d2h_bytes_per_step": nbytes, "steps": args.e2e_steps,
+               "path": "ns_step_host: pinned host state -> device, one step, device -> host, sync"}
     # mixed precision on the same workload: throughput, speedup, and difference from FP64
     mixed = None
     if args.precision == "fp64" and not args.no_mixed:
@@ -738,24 +820,11 @@ def main():
         bls = {"1024x256x512": bench_boundary_layer(B, torch, I, dev, gpu_index, 1024, 256, 512, 50, True),
                "2048x288x1024": bench_boundary_layer(B, torch, I, dev, gpu_index, 2048, 288, 1024, 20, False)}
 
-    # end to end through the host-buffer entry point (pinned host memory)
-    hu = torch.from_numpy(np.ascontiguousarray(u0)).pin_memory().numpy()
-    hv = torch.from_numpy(np.ascontiguousarray(v0)).pin_memory().numpy()
-    hw = torch.from_numpy(np.ascontiguousarray(w0)).pin_memory().numpy()
-    hp = torch.from_numpy(np.ascontiguousarray(p0)).pin_memory().numpy()
-    e2e = None
-    if args.e2e_steps > 0:
-        B.ns_step_host(s.ctx, hu, hv, hw, hp, 1)
-        if dist:
-            dist.barrier()
-        t0 = time.perf_counter()
-        for _ in range(args.e2e_steps):
-            B.ns_step_host(s.ctx, hu, hv, hw, hp, 1)
-        te = max_over_ranks(torch, dist, time.perf_counter() - t0, dev)
-        nbytes = (hu.nbytes + hv.nbytes + hw.nbytes + hp.nbytes)
-        e2e = {"value": job_throughput(world, cells, args.e2e_steps, te), "unit": UNIT, "h2d_bytes_per_step": nbytes,
-               "d2h_bytes_per_step": nbytes, "steps": args.e2e_steps,
-               "path": "ns_step_host: pinned host state -> device, one step, device -> host, sync"}
+    # the y-slab decomposition with its slabs on this GPU (one GPU only)
+    slabrec = None
+    if args.precision == "fp64" and not args.no_slabs and world == 1:
+        slabrec = bench_slabs(B, torch, dev, s, case)
+
     s.close()
     if dist:
         dist.destroy_process_group()
@@ -767,7 +836,7 @@ def main():
            "data": "synthetic (seeded Re_tau 395 log-law channel field, 10% Gaussian fluctuations, projected)",
            "config": config, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
            "fp64_peak": ({"tflops": fp64_live[0], "source": fp64_live[1]} if fp64_live else None),
-           "gpu_launches": len(kern) * 3 * args.steps, "clocks": ck, "mixed": mixed, "fixed_cfl": cflsec, "ensemble": ensemble, "boundary_layer": bls,
+           "gpu_launches": len(kern) * 3 * args.steps, "clocks": ck, "mixed": mixed, "fixed_cfl": cflsec, "ensemble": ensemble, "boundary_layer": bls, "slabs_one_gpu": slabrec,
            "kernels": {k: {kk: (round(vv, 4) if vv is not None else None) for kk, vv in d.items()}
                        for k, d in kern.items()}}
     print(json.dumps(out))

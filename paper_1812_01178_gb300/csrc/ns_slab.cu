@@ -277,24 +277,57 @@ struct YArgs {
   int qlo, qhi;      // entries of h this slab reads
 };
 
+// the line of component comp (u, w: the centre class; v: the face class); the argument arrays are
+// selected with constant indices, so the kernel arguments stay in the constant bank
+struct YLine {
+  double* line;
+  const double* T;
+  int m;
+};
+__device__ __forceinline__ YLine y_line(const YArgs& a, int comp, int k, int i) {
+  const bool f = comp == 1;
+  double* r = comp == 0 ? a.r[0] : (f ? a.r[1] : a.r[2]);
+  const int rows = f ? a.rows[1] : a.rows[0];
+  const int jo = f ? a.jo[1] : a.jo[0];
+  return YLine{r + ((long)k * rows + jo) * a.nx + i, f ? a.tab[1] : a.tab[0], f ? a.m[1] : a.m[0]};
+}
+
 __global__ void __launch_bounds__(128) slab_ysweep_local(const YArgs a) {
   const int comp = blockIdx.z, k = blockIdx.y, i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= a.nx) return;
-  const int cl = comp == 1;
-  const int m = a.m[cl];
-  const double* T = a.tab[cl];
+  const YLine L = y_line(a, comp, k, i);
+  const int m = L.m;
+  const double* T = L.T;
   const double *A = T, *IP = T + m, *CP = T + 2 * m;
-  double* line = a.r[comp] + ((long)k * a.rows[comp] + a.jo[cl]) * a.nx + i;
+  double* line = L.line;
   const long s = a.nx;
+  // rows fetched U at a time ahead of the recurrence (their latency overlaps it)
+  constexpr int U = 4;
   double prev = 0.0;
-  for (int j = 0; j < m; ++j) {
-    prev = (line[j * s] - A[j] * prev) * IP[j];
-    line[j * s] = prev;
+  for (int j0 = 0; j0 < m; j0 += U) {
+    double dv[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (j0 + u < m) dv[u] = line[(long)(j0 + u) * s];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (j0 + u < m) {
+        prev = (dv[u] - __ldg(A + j0 + u) * prev) * __ldg(IP + j0 + u);
+        line[(long)(j0 + u) * s] = prev;
+      }
   }
   double x = prev;
-  for (int j = m - 2; j >= 0; --j) {
-    x = line[j * s] - CP[j] * x;
-    line[j * s] = x;
+  for (int j1 = m - 2; j1 >= 0; j1 -= U) {
+    double dv[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (j1 - u >= 0) dv[u] = line[(long)(j1 - u) * s];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (j1 - u >= 0) {
+        x = dv[u] - __ldg(CP + j1 - u) * x;
+        line[(long)(j1 - u) * s] = x;
+      }
   }
   const long plane = (long)a.nz * a.nx, o = (long)k * a.nx + i;
   const double x1 = line[0], xm = line[(long)(m - 1) * s];
@@ -307,9 +340,9 @@ __global__ void __launch_bounds__(128) slab_ysweep_local(const YArgs a) {
 __global__ void __launch_bounds__(128) slab_ysweep_correct(const YArgs a) {
   const int comp = blockIdx.z, k = blockIdx.y, i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= a.nx) return;
-  const int cl = comp == 1;
-  const int m = a.m[cl];
-  const double* T = a.tab[cl];
+  const YLine L = y_line(a, comp, k, i);
+  const int m = L.m;
+  const double* T = L.T;
   const double *V = T + 3 * m, *W = T + 4 * m, *CLO = T + 5 * m, *CHI = CLO + a.Q;
   const long plane = (long)a.nz * a.nx, o = (long)k * a.nx + i;
   // h[2t] = x~^(t)_m (slot t, end 1), h[2t+1] = x~^(t+1)_1 (slot t + 1, end 0)
@@ -321,7 +354,7 @@ __global__ void __launch_bounds__(128) slab_ysweep_correct(const YArgs a) {
     ylo = fma(CLO[q], h, ylo);
     yhi = fma(CHI[q], h, yhi);
   }
-  double* line = a.r[comp] + ((long)k * a.rows[comp] + a.jo[cl]) * a.nx + i;
+  double* line = L.line;
   const long s = a.nx;
   for (int j = 0; j < m; ++j) line[j * s] -= V[j] * ylo + W[j] * yhi;
 }
@@ -349,16 +382,41 @@ __global__ void __launch_bounds__(128) slab_pois_local(const PArgs a) {
   const double* F = a.finv + (long)kz * a.m * a.nx + i;
   const double* C = a.fcp + (long)kz * a.m * a.nx + i;
   const bool g = a.gauge && i == 0 && kz == 0;
+  constexpr int U = 4;  // rows fetched U at a time ahead of the recurrence
+  const int m = a.m;
   double prev = 0.0;
-  for (int j = 0; j < a.m; ++j) {
-    const double dj = (g && j == 0) ? 0.0 : d[j * sd];
-    prev = (dj - (j ? a.pa[j] : 0.0) * prev) * F[(long)j * a.nx];
-    d[j * sd] = prev;
+  for (int j0 = 0; j0 < m; j0 += U) {
+    double dv[U], fv[U], av[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (j0 + u < m) {
+        dv[u] = d[(long)(j0 + u) * sd];
+        fv[u] = __ldg(F + (long)(j0 + u) * a.nx);
+        av[u] = (j0 + u) ? __ldg(a.pa + j0 + u) : 0.0;
+      }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (j0 + u < m) {
+        const double dj = (g && j0 + u == 0) ? 0.0 : dv[u];
+        prev = (dj - av[u] * prev) * fv[u];
+        d[(long)(j0 + u) * sd] = prev;
+      }
   }
   double x = prev;
-  for (int j = a.m - 2; j >= 0; --j) {
-    x = d[j * sd] - C[(long)j * a.nx] * x;
-    d[j * sd] = x;
+  for (int j1 = m - 2; j1 >= 0; j1 -= U) {
+    double dv[U], cv[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (j1 - u >= 0) {
+        dv[u] = d[(long)(j1 - u) * sd];
+        cv[u] = __ldg(C + (long)(j1 - u) * a.nx);
+      }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (j1 - u >= 0) {
+        x = dv[u] - cv[u] * x;
+        d[(long)(j1 - u) * sd] = x;
+      }
   }
   const long o0 = 2 * (((long)0 * a.nzh + kz) * a.nx + i) + part;
   const long o1 = 2 * (((long)1 * a.nzh + kz) * a.nx + i) + part;

@@ -96,6 +96,8 @@ class Slab:
             bptr = [self.bl[q].data_ptr() for q in names]
         self.fields = B.ns_fields(self.u.data_ptr(), self.v.data_ptr(), self.w.data_ptr(), self.pr.data_ptr(), *bptr)
         self.h = C.c_void_p()
+        if stream is not None:  # the uploads above ran on the current stream
+            torch.cuda.current_stream(dev).synchronize()
         st = B.lib().ns_slab_init(C.byref(self.h), C.byref(self.cfg), p, r, ymode, C.byref(self.fields),
                                   self.ws.data_ptr(), nbytes, self.stream.cuda_stream)
         if st != B.NS_OK:
@@ -155,17 +157,37 @@ class Slab:
 
 class LocalExchange:
     """The exchanges of p slabs held on one device: slot s of every slab that reads it receives
-    slab s's send buffer by a device copy on the current stream (the slabs' stream)."""
+    slab s's send buffer by a device copy on the reading slab's stream.  Slabs may have streams of
+    their own (their kernels then overlap, as on separate GPUs): a copy waits for the phase that
+    wrote its source, and a slab's next phase waits for every copy of this exchange."""
 
     def __init__(self, slabs):
         self.slabs = slabs
+        self.torch = slabs[0].torch
 
     def __call__(self, xch):
+        torch = self.torch
+        written = []
+        for s in self.slabs:
+            e = torch.cuda.Event()
+            e.record(s.stream)
+            written.append(e)
         for t in self.slabs:
             lo, hi = t.slots(xch)
-            for s in range(lo, hi + 1):
-                if s != t.r:
-                    t.recv[xch][s].copy_(self.slabs[s].send[xch])
+            with torch.cuda.stream(t.stream):
+                for q in range(lo, hi + 1):
+                    if q != t.r:
+                        t.stream.wait_event(written[q])
+                        t.recv[xch][q].copy_(self.slabs[q].send[xch])
+        copied = []
+        for t in self.slabs:
+            e = torch.cuda.Event()
+            e.record(t.stream)
+            copied.append(e)
+        for s in self.slabs:
+            for q, e in enumerate(copied):
+                if q != s.r:
+                    s.stream.wait_event(e)
 
 
 class DistExchange:

@@ -56,6 +56,21 @@ def test_slabs_match_the_oracle(shape, P):
         assert mode == B.NS_PART_PDD  # weak coupling at this dt across slabs of 12 and 24 rows
 
 
+def test_slabs_on_streams_of_their_own():
+    """Each slab on its own stream (their kernels overlap, as on separate GPUs); the exchange
+    copies are ordered by events.  Same result as the slabs on one stream, to the last bit."""
+    case, g, u, v, w, p = _projected((64, 48, 32), 13)
+    a, _ = _run_slabs(case, u, v, w, p, 4, 2)
+    slabs = [S.Slab(case, 4, r, u, v, w, p, stream=torch.cuda.Stream()) for r in range(4)]
+    S.run_steps(slabs, S.LocalExchange(slabs), 2)
+    parts = [s.owned() for s in slabs]
+    for s in slabs:
+        s.close()
+    b = tuple(np.concatenate([q[f] for q in parts], axis=1) for f in range(4))
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+
+
 def test_slabs_match_the_single_context_path():
     case, g, u, v, w, p = _projected((64, 48, 32), 5)
     got, _ = _run_slabs(case, u, v, w, p, 4, 3)
