@@ -382,6 +382,17 @@ size_t ns_slab_slot_bytes(const ns_config* cfg, int p, int xch);
  * the slab's y-sweep mode (NS_PART_PDD: neighbours only; NS_PART_PPT: every slab).  Host only. */
 ns_status ns_slab_slots(int p, int r, int xch, int ymode, int* lo, int* hi);
 
+/* Host-only reference of the slab algebra (no device work): solves the tridiagonal line
+ * a_j x_{j-1} + b_j x_j + c_j x_{j+1} = d_j of n unknowns (a_0, c_{n-1} ignored) cut into p blocks
+ * as ns_slab_rows cuts ny rows, with the tables the slabs use (the same builder): every block of
+ * A~ solved alone, the end values gathered, and the reduced system of Sec. 3.2 solved by PPT
+ * (Eq. (Zppt), exact) or PDD (Eq. (Zpdd), the couplings between interfaces dropped), then each
+ * block corrected.  mode is NS_PART_PPT or NS_PART_PDD; x (n doubles, host) receives the solution;
+ * *dropped (if not NULL) the largest coupling PDD drops.  NS_ERR_ARG for NULL arrays, p < 1 or
+ * n < 2p; NS_ERR_STATE for a singular reduced system. */
+ns_status ns_slab_solve_line_host(int n, const double* a, const double* b, const double* c, const double* d, int p,
+                                  int mode, double* x, double* dropped);
+
 /* Workspace bytes of slab r (its sub-grid context, the slab tables and the exchange buffers); 0 if
  * the configuration is not supported. */
 size_t ns_slab_workspace_bytes(const ns_config* cfg, int p, int r);

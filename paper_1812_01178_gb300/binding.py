@@ -32,7 +32,7 @@ EXPORTS = ["ns_workspace_bytes", "ns_init", "ns_rhs", "ns_adi_sweep", "ns_poisso
            "ns_batch_sync", "ns_batch_last_error", "ns_batch_destroy",
            "ns_slab_rows", "ns_slab_slot_bytes", "ns_slab_slots", "ns_slab_workspace_bytes", "ns_slab_init",
            "ns_slab_phase", "ns_slab_buffers", "ns_slab_mode", "ns_slab_context", "ns_slab_sync",
-           "ns_slab_last_error", "ns_slab_destroy"]
+           "ns_slab_last_error", "ns_slab_destroy", "ns_slab_solve_line_host"]
 NS_STATIC_SCRATCH_BYTES = 48 * 1024 * 1024
 
 
@@ -110,6 +110,7 @@ def lib(path: str = LIB_PATH):
     L.ns_slab_last_error.restype = C.c_char_p
     L.ns_slab_destroy.argtypes = [vp]
     L.ns_slab_destroy.restype = None
+    L.ns_slab_solve_line_host.argtypes = [i, P(d), P(d), P(d), P(d), i, i, P(d), P(d)]
     L.ns_sync.argtypes = [vp]
     L.ns_last_error.argtypes = [vp]
     L.ns_last_error.restype = C.c_char_p

@@ -765,6 +765,45 @@ ns_status ns_slab_slots(int p, int r, int xch, int ymode, int* lo, int* hi) {
   return NS_OK;
 }
 
+ns_status ns_slab_solve_line_host(int n, const double* a, const double* b, const double* c, const double* d, int p,
+                                  int mode, double* x, double* dropped) {
+  if (!a || !b || !c || !d || !x || p < 1 || n < 2 * p || (mode != NS_PART_PPT && mode != NS_PART_PDD))
+    return NS_ERR_ARG;
+  std::vector<int> lo(p), hi(p);
+  for (int q = 0; q < p; ++q) slab_rows(n, p, q, &lo[q], &hi[q]);
+  std::vector<double> scr, h(2 * (size_t)(p - 1), 0.0);
+  std::vector<SplitOut> tab(p);
+  // each slab's tables, and its block solve x~ (the slab kernels' forward and back sweeps)
+  for (int r = 0; r < p; ++r) {
+    split_line(a, b, c, lo, hi, r, mode == NS_PART_PDD, tab[r], scr);
+    if (!tab[r].ok) return NS_ERR_STATE;
+    const SplitOut& o = tab[r];
+    const int m = hi[r] - lo[r];
+    double prev = 0.0;
+    for (int j = 0; j < m; ++j) {
+      prev = (d[lo[r] + j] - o.a[j] * prev) * o.ip[j];
+      x[lo[r] + j] = prev;
+    }
+    for (int j = m - 2; j >= 0; --j) x[lo[r] + j] -= o.cp[j] * x[lo[r] + j + 1];
+  }
+  // the gathered end values h[2t] = x~^(t)_m, h[2t+1] = x~^(t+1)_1, then each slab's correction
+  for (int t = 0; t + 1 < p; ++t) {
+    h[2 * t] = x[hi[t] - 1];
+    h[2 * t + 1] = x[lo[t + 1]];
+  }
+  for (int r = 0; r < p; ++r) {
+    const SplitOut& o = tab[r];
+    double ylo = 0.0, yhi = 0.0;
+    for (size_t q = 0; q < h.size(); ++q) {
+      ylo += o.clo[q] * h[q];
+      yhi += o.chi[q] * h[q];
+    }
+    for (int j = 0; j < hi[r] - lo[r]; ++j) x[lo[r] + j] -= o.v[j] * ylo + o.w[j] * yhi;
+  }
+  if (dropped) *dropped = tab[0].drop;
+  return NS_OK;
+}
+
 size_t ns_slab_workspace_bytes(const ns_config* cfg, int p, int r) {
   if (!check_slab(cfg, p, r).empty()) return 0;
   std::vector<double> yf;

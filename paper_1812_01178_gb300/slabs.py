@@ -47,6 +47,20 @@ def slot_bytes(cfg, p, xch):
     return B.lib().ns_slab_slot_bytes(C.byref(cfg), p, xch)
 
 
+def solve_line_host(a, b, c, d, p, mode):
+    """ns_slab_solve_line_host: one tridiagonal line solved the slabs' way on the host (no GPU).
+    Returns (x, largest coupling PDD drops)."""
+    arr = [np.ascontiguousarray(q, dtype=np.float64) for q in (a, b, c, d)]
+    n = arr[3].size
+    x = np.empty(n)
+    drop = C.c_double()
+    P = lambda q: q.ctypes.data_as(C.POINTER(C.c_double))
+    st = B.lib().ns_slab_solve_line_host(n, *[P(q) for q in arr], p, mode, P(x), C.byref(drop))
+    if st != B.NS_OK:
+        raise B.NSError(st, "ns_slab_solve_line_host failed")
+    return x, drop.value
+
+
 def run_steps(slabs, exchange, nsteps, first=True):
     """nsteps time steps (three sub-steps each) of the slabs in `slabs` (all p slabs on one device,
     or this rank's one slab), exchanging with exchange(xch) after every phase.  first=True packs and

@@ -7,6 +7,7 @@ import os
 import socket
 import sys
 
+import numpy as np
 import pytest
 
 torch = pytest.importorskip("torch")
@@ -113,3 +114,54 @@ def _free_port():
 @pytest.mark.parametrize("world,ymode", [(2, B.NS_PART_PDD), (3, B.NS_PART_PDD), (3, B.NS_PART_PPT)])
 def test_gloo_ranks_exchange_what_each_slab_reads(world, ymode):
     mp.start_processes(_worker, args=(world, _free_port(), ymode), nprocs=world, join=True, start_method="spawn")
+
+
+def _rows(n, rng, strength):
+    """Random tridiagonal rows; strength = how far the diagonal exceeds |a| + |c|."""
+    a = -rng.uniform(0.5, 1.5, n)
+    c = -rng.uniform(0.5, 1.5, n)
+    b = np.abs(a) + np.abs(c) + strength * rng.uniform(0.5, 1.5, n)
+    return a, b, c
+
+
+@pytest.mark.parametrize("n,p", [(12, 4), (48, 3), (64, 8), (30, 2)])
+@pytest.mark.parametrize("strength", [20.0, 0.05])
+def test_slab_line_algebra_equals_the_dense_partitioned_solves(n, p, strength):
+    """The slab tables (block factors, spikes, reduced-system rows) solve a line exactly as the
+    oracle's dense matrices of Sec. 3.2 do: PPT (Eq. Zppt) equals the whole-line Thomas solve, PDD
+    (Eq. Zpdd) equals the dense PDD, dropped couplings included, and reports the coupling PDD
+    drops.  Strongly dominant rows make PDD exact as well; weakly dominant ones make it visibly
+    approximate."""
+    from oracle import ns_oracle as O
+    rng = np.random.default_rng(n * 10 + p)
+    a, b, c = _rows(n, rng, strength)
+    d = rng.standard_normal(n)
+    ref = O.thomas(a, b, c, d)
+    x_ppt, _ = S.solve_line_host(a, b, c, d, p, B.NS_PART_PPT)
+    np.testing.assert_allclose(x_ppt, O.ppt_solve(a, b, c, d, p), rtol=0, atol=1e-13 * np.abs(ref).max())
+    np.testing.assert_allclose(x_ppt, ref, rtol=0, atol=1e-13 * np.abs(ref).max())
+    x_pdd, drop = S.solve_line_host(a, b, c, d, p, B.NS_PART_PDD)
+    np.testing.assert_allclose(x_pdd, O.pdd_solve(a, b, c, d, p), rtol=0, atol=1e-13 * np.abs(ref).max())
+    assert drop == pytest.approx(O.pdd_dropped_coupling(a, b, c, p), rel=1e-12, abs=1e-300)
+    if strength < 1 and p > 2:
+        assert np.abs(x_pdd - ref).max() > 1e-6 * np.abs(ref).max()  # PDD's dropped coupling shows
+
+
+def test_slab_line_algebra_poisson_rows_with_the_gauge():
+    """Rows of the Poisson y solve (zero normal gradient, the (0, 0) mode's gauge row phi_0 = 0)
+    split into 4 slabs by PPT equal the whole-line solve (the slabs' Poisson path)."""
+    from oracle import ns_oracle as O
+    from paper_1812_01178_gb300 import inputs as I
+    case, *_ = I.small_channel(16, 48, 8)
+    g = O.Grid.from_case(case)
+    pa, pc = O.poisson_ycoeffs(g)
+    rng = np.random.default_rng(3)
+    d = rng.standard_normal(g.ny)
+    for lam in (0.0, 0.3, 40.0):
+        a, c = pa.copy(), pc.copy()
+        b = -(a + c) - lam
+        if lam == 0.0:
+            a[0], b[0], c[0], d[0] = 0.0, 1.0, 0.0, 0.0
+        ref = O.thomas(a, b, c, d)
+        x, _ = S.solve_line_host(a, b, c, d, 4, B.NS_PART_PPT)
+        np.testing.assert_allclose(x, ref, rtol=0, atol=1e-11 * np.abs(ref).max())
