@@ -1,4 +1,4 @@
-"""Benchmark: grid-point-steps/s of the fractional-step NS step on one GB300 (and N replicas).
+"""Benchmark: grid-point-steps/s of the fractional-step NS step on one GB300 (N replicas, or N y-slabs).
 
 Default workload: the turbulent-channel-sized FP64 step, 256 x 192 x 256 cells, periodic x and z,
 tanh-stretched y with no-slip walls, Re_tau = 395 log-law field with 10 % Gaussian fluctuations
@@ -10,8 +10,10 @@ inverse x FFT, inverse z FFT, projection.
 
 Prints one JSON line.  N > 1 runs under torch.distributed.run: every rank advances its own
 replica (the single-instance path has no data-path exchange), value = cells*steps summed over
-ranks / max-over-ranks time.  --impl reference times the FP64 CPU oracle on the same workload
-(bounded samples of it) on the host cores.
+ranks / max-over-ranks time.  With --slabs the N ranks instead share the one workload as N
+y-slabs (the paper's multi-GPU decomposition, strong scaling; --backend gloo for ranks sharing a
+GPU).  --impl reference times the FP64 CPU oracle on the same workload (bounded samples of it) on
+the host cores.
 """
 from __future__ import annotations
 
@@ -586,6 +588,57 @@ def bench_slabs(B, torch, dev, s_single, case, steps=5):
     return out
 
 
+def run_slabs_mode(args, torch, B, dev, dist, world, rank, case, u0, v0, w0, p0, config, gpu_index):
+    """--slabs: the bench workload cut into `world` y-slabs, one per rank, as the paper's multi-GPU
+    method does (Sec. 3.2, Algorithm 1): strong scaling of the one workload.  The exchanges go over
+    torch.distributed (NCCL between GPUs; gloo, staged through host memory, for a run whose ranks
+    share a GPU).  Every rank projects the same seeded field with one context, keeps its slab, and
+    steps; the time is the slowest rank's."""
+    from paper_1812_01178_gb300 import slabs as S
+    s0 = B.Solver(case, u0, v0, w0, p0, device=str(dev))
+    s0.make_divergence_free()
+    start = [t.cpu().numpy() for t in (s0.u, s0.v, s0.w, s0.p)]
+    s0.close()
+    slab = S.Slab(case, world, rank, *start, device=str(dev))
+    if dist is None:  # one slab: every slot it reads is its own, which the library writes
+        ex = lambda xch: None
+    else:
+        ex = S.DistExchange(dist, world, rank, slab.ymode, slab.send, slab.recv, host=(args.backend == "gloo"))
+    S.run_steps([slab], ex, args.warmup)
+    slab.sync()
+    if dist:
+        dist.barrier()
+    clocks = ClockSampler(gpu_index)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    ev0.record(slab.stream)
+    S.run_steps([slab], ex, args.steps, first=False)  # the warm-up's last exchange filled the halos
+    ev1.record(slab.stream)
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    if dist:
+        dist.barrier()
+    t_max = max_over_ranks(torch, dist, ev0.elapsed_time(ev1), dev if args.backend == "nccl" else "cpu")
+    cells = case.cells()
+    rows = [S.rows(case.ny, world, r) for r in range(world)]
+    ymode = "PDD" if slab.ymode == B.NS_PART_PDD else "PPT"
+    slab.close()
+    if rank != 0:
+        return
+    config = dict(config, parallelism="y-slabs x%d (%s)" % (world, args.backend),
+                  slab_rows=[j1 - j0 for j0, j1 in rows], y_sweep=ymode)
+    out = {"metric": METRIC, "value": cells * args.steps / (t_max * 1e-3), "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+           "scaling": "strong", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic (seeded Re_tau 395 log-law channel field, 10% Gaussian fluctuations, projected)",
+           "config": config, "clocks": ck, "e2e": None,
+           "note": "one y-slab per rank, exchanges over torch.distributed between phases (host-driven)"}
+    print(json.dumps(out))
+
+
 # ------------------------------------------------------------------------------ main
 def main():
     ap = argparse.ArgumentParser()
@@ -601,6 +654,10 @@ def main():
     ap.add_argument("--no-cfl", action="store_true")
     ap.add_argument("--no-bl", action="store_true", help="skip the 134M- and 604M-cell boundary-layer records")
     ap.add_argument("--no-slabs", action="store_true", help="skip the y-slab record (slabs held on one GPU)")
+    ap.add_argument("--slabs", action="store_true",
+                    help="N > 1: cut the workload into N y-slabs, one per rank (strong scaling), instead of replicas")
+    ap.add_argument("--backend", choices=["nccl", "gloo"], default="nccl",
+                    help="process group of --slabs (gloo stages the exchanges through host memory)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -640,7 +697,7 @@ def main():
 
     # cpu baseline first, in this process, before any CUDA work
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.slabs:
         F = 1  # the whole workload: two RK3 steps, about 18 s on 16 host cores
         val, t = oracle_baseline(case, u0, v0, w0, p0, F, 6)
         cpu = {"value": val, "unit": UNIT, "cores": os.cpu_count(), "cpu": host_cpu(), "kind": "oracle",
@@ -651,12 +708,24 @@ def main():
     import __graft_entry__
     __graft_entry__.build()
 
+    # ranks sharing a GPU (only with --slabs --backend gloo) take it modulo the visible devices
+    local = local % max(1, torch.cuda.device_count()) if args.backend == "gloo" else local
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     dist = None
     if world > 1:
         import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=dev)
+        if args.backend == "gloo":
+            dist.init_process_group("gloo")
+        else:
+            dist.init_process_group("nccl", device_id=dev)
+    if args.slabs:
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+        run_slabs_mode(args, torch, B, dev, dist, world, rank, case, u0, v0, w0, p0, config,
+                       vis.split(",")[local] if vis else str(local))
+        if dist:
+            dist.destroy_process_group()
+        return
 
     fp64_live = None
     try:

@@ -199,3 +199,28 @@ def test_slabs_as_separate_processes(world, tmp_path):
     errs = field_rel_errors(got, (ref["u"], ref["v"], ref["w"], ref["p"]))
     for name in ("u", "v", "w", "p"):
         assert errs[name] < 1e-11, (name, errs)
+
+
+def test_bench_slab_mode_two_ranks_share_the_gpu():
+    """bench.py --slabs under torch.distributed.run: the bench workload cut into two y-slabs, one
+    per rank, the exchanges over gloo staged through host memory (both ranks on this GPU).  One JSON
+    line with the contract's keys, strong scaling."""
+    import json
+    import os
+    import socket
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        port = sk.getsockname()[1]
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2", "--master-addr",
+           "127.0.0.1", "--master-port", str(port), os.path.join(root, "bench.py"), "--gpus", "2", "--slabs",
+           "--backend", "gloo", "--steps", "2", "--warmup", "3"]
+    r = subprocess.run(cmd, capture_output=True, text=True, timeout=900, cwd=root)
+    assert r.returncode == 0, r.stderr[-3000:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1, r.stdout[-2000:]
+    d = json.loads(lines[0])
+    assert d["n_gpus"] == 2 and d["scaling"] == "strong" and d["steps"] == 2 and d["value"] > 0
+    assert d["config"]["slab_rows"] == [96, 96] and d["config"]["y_sweep"] == "PDD"
