@@ -264,9 +264,17 @@ enum {
   NS_BUF_RU = 0, NS_BUF_RV = 1, NS_BUF_RW = 2,   /* r / delta (double, or float if NS_MIXED) */
   NS_BUF_NU = 3, NS_BUF_NV = 4, NS_BUF_NW = 5,   /* N_prev (double, or float if NS_MIXED) */
   NS_BUF_PHI = 6,                               /* phi, double, nz*ny*nx */
-  NS_BUF_SPEC = 7                               /* spectral buffer, complex double,
+  NS_BUF_SPEC = 7,                              /* spectral buffer, complex double,
                                                    (nz/2+1)*ny*nx, layout [kz][j][kx]; NS_MIXED:
                                                    the FP64 right-hand side of the Poisson solve */
+  NS_BUF_POIS_MODE = 8                          /* NS_MIXED only: one byte per Poisson mode,
+                                                   layout [kz][kx], (nz/2+1)*nx; 1 where its y
+                                                   solve may run in FP32 arithmetic (kz > 0 and
+                                                   the Skeel condition number of its y matrix
+                                                   <= 4096), 0 where it runs in FP64.  With nx
+                                                   a multiple of 16 the solve goes by tiles of 16
+                                                   kx, in FP32 only where all 16 flags are 1.
+                                                   NS_ERR_UNSUPPORTED for an FP64 context */
 };
 ns_status ns_get_buffer(ns_ctx* ctx, int which, void** ptr, size_t* bytes);
 
@@ -317,6 +325,10 @@ ns_status ns_batch_init(ns_batch** out, const ns_config* cfgs, const ns_fields* 
 
 /* nsteps time steps of every instance (graph captured on first use and replayed). */
 ns_status ns_batch_step(ns_batch* b, int nsteps);
+
+/* Number of kernel launches in one ns_step time step: the kernel nodes of the step's graph (it is
+ * captured here if ns_step has not run yet).  -1 on error (ns_last_error). */
+int ns_launches_per_step(ns_ctx* ctx);
 
 /* Number of kernel launches in one batched time step (3 sub-steps x stages x kernel variants). */
 int ns_batch_launches_per_step(ns_batch* b);

@@ -18,14 +18,14 @@ NS_OK, NS_ERR_ARG, NS_ERR_SIZE, NS_ERR_CUDA, NS_ERR_TIMEOUT, NS_ERR_STATE, NS_ER
 NS_FP64, NS_MIXED = 0, 1
 NS_PART_AUTO, NS_PART_PPT, NS_PART_PDD = 0, 1, 2
 NS_PRESSURE_DELTA, NS_PRESSURE_KIM_MOIN = 0, 1
-NS_BUF_RU, NS_BUF_RV, NS_BUF_RW, NS_BUF_NU, NS_BUF_NV, NS_BUF_NW, NS_BUF_PHI, NS_BUF_SPEC = range(8)
+NS_BUF_RU, NS_BUF_RV, NS_BUF_RW, NS_BUF_NU, NS_BUF_NV, NS_BUF_NW, NS_BUF_PHI, NS_BUF_SPEC, NS_BUF_POIS_MODE = range(9)
 
 STATUS_NAMES = {0: "NS_OK", 1: "NS_ERR_ARG", 2: "NS_ERR_SIZE", 3: "NS_ERR_CUDA", 4: "NS_ERR_TIMEOUT",
                 5: "NS_ERR_STATE", 6: "NS_ERR_UNSUPPORTED"}
 
 # Every symbol declared in include/ns.h.
 EXPORTS = ["ns_workspace_bytes", "ns_init", "ns_rhs", "ns_adi_sweep", "ns_poisson_solve", "ns_project",
-           "ns_substep", "ns_step", "ns_convective_rate", "ns_set_dt", "ns_step_cfl", "ns_step_profiled", "ns_kernel_count", "ns_kernel_name", "ns_step_host", "ns_make_divergence_free", "ns_set_partition",
+           "ns_substep", "ns_step", "ns_launches_per_step", "ns_convective_rate", "ns_set_dt", "ns_step_cfl", "ns_step_profiled", "ns_kernel_count", "ns_kernel_name", "ns_step_host", "ns_make_divergence_free", "ns_set_partition",
            "ns_get_partition", "ns_autotune", "ns_get_buffer", "ns_poisson_solve_static", "ns_fp64_fma_probe", "ns_sync",
            "ns_last_error", "ns_destroy", "ns_batch_workspace_bytes", "ns_batch_init", "ns_batch_step",
            "ns_batch_launches_per_step", "ns_batch_autotune", "ns_batch_set_partition", "ns_batch_instance",
@@ -121,6 +121,7 @@ def lib(path: str = LIB_PATH):
     L.ns_batch_init.argtypes = [P(vp), P(ns_config), P(ns_fields), i, vp, sz, vp]
     L.ns_batch_step.argtypes = [vp, i]
     L.ns_batch_launches_per_step.argtypes = [vp]
+    L.ns_launches_per_step.argtypes = [vp]
     L.ns_batch_autotune.argtypes = [vp]
     L.ns_batch_set_partition.argtypes = [vp, i, i, i]
     L.ns_batch_instance.argtypes = [vp, i]
@@ -339,6 +340,8 @@ class Solver:
         c = self.case
         if which == NS_BUF_SPEC:
             return raw.view(torch.float64).view(c.nz // 2 + 1, c.ny, c.nx, 2)
+        if which == NS_BUF_POIS_MODE:
+            return raw.view(c.nz // 2 + 1, c.nx)
         if which == NS_BUF_PHI:
             return raw.view(torch.float64).view(c.nz, c.ny, c.nx)
         dt = torch.float32 if self.es == 4 else torch.float64
@@ -362,6 +365,12 @@ class Solver:
 
     def step(self, n=1):
         ns_step(self.ctx, n)
+
+    def launches_per_step(self):
+        n = lib().ns_launches_per_step(self.ctx)
+        if n < 0:
+            raise NSError(NS_ERR_CUDA, lib().ns_last_error(self.ctx).decode())
+        return n
 
     def step_profiled(self, n=1):
         return ns_step_profiled(self.ctx, n)

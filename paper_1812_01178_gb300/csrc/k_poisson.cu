@@ -331,11 +331,10 @@ __device__ __forceinline__ double tdma_cv(float x) { return f2d(x); }
 __device__ __forceinline__ void tdma_st(double* p, double x) { *p = x; }
 __device__ __forceinline__ void tdma_st(float* p, double x) { *p = d2f_rn(x); }
 
-template <typename T>
+template <typename T, int U = 4>
 __device__ __forceinline__ void tdma_line(T* d, long sd, const double* __restrict__ finv,
                                           const double* __restrict__ fcp, const double* __restrict__ pa, int nx,
                                           int ny, bool gauge) {
-  constexpr int U = 4;
   // two register sets, A and B, take turns: no copies between them (a copy of a register whose
   // load is in flight would wait for it)
   // (the spectrum values stay in their storage type until used: a conversion right after the load
@@ -454,6 +453,67 @@ struct FftxPK {
     cp_async_wait<0>();
   }
 };
+
+// The same line solve in FP32 arithmetic (mixed form, on the (kx, kz) modes pois_factor_kernel
+// marks): factors 1/pivot and c/pivot are the FP64 ones rounded to float, a_j in float.  No gauge
+// row: the (0, 0) mode always takes the FP64 solve.  Global: the factors and a_j are read through
+// the read-only path (else they sit in shared memory); nx is the factors' row stride.
+template <bool Global, int U>
+__device__ __forceinline__ void tdma_line32(float* d, long sd, const float* __restrict__ finv,
+                                            const float* __restrict__ fcp, const float* __restrict__ pa, int nx,
+                                            int ny) {
+  auto ld = [](const float* p) { return Global ? __ldg(p) : *p; };
+  float Ad[U] = {}, Bd[U] = {}, Af[U] = {}, Aa[U] = {}, Bf[U] = {}, Ba[U] = {};
+  auto load_f = [&](int j0, float* D, float* F, float* A) {
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (j0 + u < ny) {
+        D[u] = d[(long)(j0 + u) * sd];
+        F[u] = ld(finv + (long)(j0 + u) * nx);
+        A[u] = ld(pa + j0 + u);  // a_0 = 0
+      }
+  };
+  float prev = 0.0f;
+  auto sweep_f = [&](int j0, const float* D, const float* F, const float* A) {
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (j0 + u < ny) {
+        prev = __fmul_rn(__fmaf_rn(-A[u], prev, D[u]), F[u]);
+        d[(long)(j0 + u) * sd] = prev;
+      }
+  };
+  load_f(0, Ad, Af, Aa);
+  for (int j0 = 0; j0 < ny; j0 += 2 * U) {
+    load_f(j0 + U, Bd, Bf, Ba);
+    sweep_f(j0, Ad, Af, Aa);
+    load_f(j0 + 2 * U, Ad, Af, Aa);
+    sweep_f(j0 + U, Bd, Bf, Ba);
+  }
+  float next = prev;
+  auto load_b = [&](int j1, float* D, float* C) {
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (j1 - u >= 0) {
+        D[u] = d[(long)(j1 - u) * sd];
+        C[u] = ld(fcp + (long)(j1 - u) * nx);
+      }
+  };
+  auto sweep_b = [&](int j1, const float* D, const float* C) {
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (j1 - u >= 0) {
+        next = __fmaf_rn(-C[u], next, D[u]);
+        d[(long)(j1 - u) * sd] = next;
+      }
+  };
+  load_b(ny - 2, Ad, Af);
+  for (int j1 = ny - 2; j1 >= 0; j1 -= 2 * U) {
+    load_b(j1 - U, Bd, Bf);
+    sweep_b(j1, Ad, Af);
+    load_b(j1 - 2 * U, Ad, Af);
+    sweep_b(j1 - U, Bd, Bf);
+  }
+}
 
 // ------------------------------------------------------------------------------------------
 // y tridiagonal per (kx, kz), two threads per line (real, imaginary part), factors 1/pivot and
@@ -693,17 +753,21 @@ struct DivzMK {
   }
 };
 
-// y tridiagonal per (kx, kz) of the mixed form: complex64 spectrum, FP64 arithmetic and factors
-// (the same recurrences as TdmaK)
+// y tridiagonal per (kx, kz) of the mixed form on the complex64 spectrum: FP64 arithmetic and
+// factors (the same recurrences as TdmaK) on the kz = 0 modes and the ill-conditioned low modes,
+// FP32 on the rest (mode[kz][kx] = 1, set by pois_factor_kernel)
 struct TdmaMK {
   struct Args {
     float2* spec;
     const double2* fac;
     const double* gc;
     int nx, ny, nzh;
+    const float* fac32;         // 1/pivot and c/pivot planes in float, nzh * ny * nx each
+    const float* pa32;          // a_j in float
+    const unsigned char* mode;  // nzh * nx: 1 = FP32 solve
   };
   static constexpr int kThreads = 128;
-  static constexpr int kMinBlocks = 8;
+  static constexpr int kMinBlocks = 6;
   static __device__ __forceinline__ void run(const Args& a, const dim3 bid_, const dim3) {
     const int nx = a.nx, ny = a.ny;
     const int t = bid_.x * blockDim.x + threadIdx.x;
@@ -713,10 +777,93 @@ struct TdmaMK {
     const long base = (long)kz * ny * nx + i;
     float* d = reinterpret_cast<float*>(a.spec + base) + part;
     const long sd = 2L * nx;
+    if (a.mode[(long)kz * nx + i]) {
+      const float* f32 = a.fac32 + base;
+      tdma_line32<true, 4>(d, sd, f32, f32 + (long)a.nzh * ny * nx, a.pa32, nx, ny);
+      return;
+    }
     const double* finv = reinterpret_cast<const double*>(a.fac) + base;
     const double* fcp = finv + (long)a.nzh * ny * nx;
     const double* pa = a.gc + GC_PA * (ny + 1);
     tdma_line(d, sd, finv, fcp, pa, nx, ny, i == 0 && kz == 0);
+  }
+};
+
+// The same y solve staged in shared memory (nx a multiple of 16): one block per tile of TL = 16
+// consecutive kx of one kz, from a tile list built at init.  The block copies the tile's
+// complex64 rows and a_j into shared memory with every copy in flight at once (cp.async), one
+// warp sweeps the TL lines (real and imaginary part on two lanes) from there, and the block writes
+// the rows back; a line then waits on shared memory, not on one global load per row.
+//  - FP32 tiles (every mode flagged): the float factor planes are staged too; FP32 arithmetic.
+//  - FP64 tiles (the first n64 of the list: the kz = 0 tiles and those holding an ill-conditioned
+//    mode): FP64 arithmetic with the FP64 factors and a_j read from global memory 8 to 16 rows
+//    ahead, so that the FP64 pipe (a warp's instruction takes 64 cycles of an SM sub-partition's
+//    FP64 unit) sets the pace rather than the load latency.  They come first in the launch so
+//    that their longer sweeps overlap the FP32 tiles.
+struct TdmaSK {
+  struct Args {
+    float2* spec;
+    const float* fac32;   // 1/pivot and c/pivot planes in float, nzh * ny * nx each
+    const double* fac64;  // the same in FP64
+    const float* pa32;    // a_j
+    const double* pa64;
+    const int* tiles;     // tile q: kz * (nx / TL) + x tile; the n64 FP64 tiles first
+    int n64;
+    int nx, ny, nzh;
+  };
+  static constexpr int TL = 16;
+  static constexpr int kThreads = 64;
+  static constexpr int kMinBlocks = 4;
+  // D [ny][TL] float2, IP and CP [ny][TL] float, a_j [ny] float
+  static size_t smem_bytes(int ny) { return (size_t)ny * TL * 16 + (size_t)ny * 4; }
+  static __device__ __forceinline__ void run(const Args& a, const dim3 bid_, const dim3) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int nx = a.nx, ny = a.ny;
+    const int ntx = nx / TL;
+    const int tile = __ldg(a.tiles + bid_.x);
+    const bool f64 = (int)bid_.x < a.n64;
+    const int kz = tile / ntx, i0 = (tile - kz * ntx) * TL;
+    float2* D = reinterpret_cast<float2*>(smem_raw);          // [ny][TL]
+    float* IP = reinterpret_cast<float*>(D + (size_t)ny * TL);  // [ny][TL]
+    float* CP = IP + (size_t)ny * TL;                           // [ny][TL]
+    float* A32 = CP + (size_t)ny * TL;                          // [ny]
+    const long plane = (long)a.nzh * ny * nx;
+    const long row0 = (long)kz * ny * nx + i0;
+    constexpr int dq = TL * 8 / 16, fq = TL * 4 / 16;  // 16-byte pieces per row
+    for (int q = threadIdx.x; q < ny * dq; q += blockDim.x) {
+      const int j = q / dq, r = q - j * dq;
+      cp_async16(reinterpret_cast<float4*>(D + (size_t)j * TL) + r,
+                 reinterpret_cast<const float4*>(a.spec + row0 + (long)j * nx) + r);
+    }
+    if (!f64) {
+      for (int q = threadIdx.x; q < ny * fq; q += blockDim.x) {
+        const int j = q / fq, r = q - j * fq;
+        cp_async16(reinterpret_cast<float4*>(IP + (size_t)j * TL) + r,
+                   reinterpret_cast<const float4*>(a.fac32 + row0 + (long)j * nx) + r);
+        cp_async16(reinterpret_cast<float4*>(CP + (size_t)j * TL) + r,
+                   reinterpret_cast<const float4*>(a.fac32 + plane + row0 + (long)j * nx) + r);
+      }
+      for (int j = threadIdx.x; j < ny; j += blockDim.x) A32[j] = __ldg(a.pa32 + j);
+    }
+    cp_async_commit();
+    cp_async_wait<0>();
+    __syncthreads();
+    if (threadIdx.x < 2 * TL) {
+      // the sweeps load rows a few ahead into registers (two sets taking turns), so that a line
+      // waits on the arithmetic, not on each row's shared-memory loads
+      const int l = threadIdx.x >> 1, part = threadIdx.x & 1;
+      float* d = reinterpret_cast<float*>(D) + 2 * l + part;  // row stride 2 TL floats
+      if (f64)  // the (0, 0) mode's row 0 is the gauge phi_0 = 0 (factor row 1, 0)
+        tdma_line<float, 8>(d, 2 * TL, a.fac64 + row0 + l, a.fac64 + plane + row0 + l, a.pa64, nx, ny,
+                            kz == 0 && i0 + l == 0);
+      else
+        tdma_line32<false, 8>(d, 2 * TL, IP + l, CP + l, A32, TL, ny);
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < ny * dq; q += blockDim.x) {
+      const int j = q / dq, r = q - j * dq;
+      reinterpret_cast<float4*>(a.spec + row0 + (long)j * nx)[r] = reinterpret_cast<const float4*>(D + (size_t)j * TL)[r];
+    }
   }
 };
 
@@ -1093,10 +1240,17 @@ __global__ void __launch_bounds__(128) rate_kernel(const double* __restrict__ u,
 
 // ------------------------------------------------------------------------------------------
 // factor table of the y systems: per (kx, kz, j): (1/pivot_j, c_j/pivot_j).  Init only.
+// The mixed form (fac32 != null) also gets the factors rounded to float and one flag per mode:
+// FP32 y solves where kz > 0 and the Skeel condition number of the mode's matrix A,
+// kappa = || |A^-1| |A| 1 ||_inf, is at most kappa_max.  -A is an M-matrix (a_j, c_j >= 0 and
+// a diagonal larger by lam), so |A^-1| |A| 1 = y with -A y = |A| 1, |A| 1 = 2 (a_j + c_j) + lam,
+// found by one more solve with the FP64 factors (scratch: the FP64 spectrum, idle at init).  The
+// kz = 0 modes (the gauge among them) and the ill-conditioned lowest modes keep FP64 arithmetic.
 // ------------------------------------------------------------------------------------------
 __global__ void pois_factor_kernel(double2* __restrict__ fac, const double* __restrict__ gc,
                                    const double* __restrict__ lamx, const double* __restrict__ lamz, int nx, int ny,
-                                   int nzh) {
+                                   int nzh, float* __restrict__ fac32, unsigned char* __restrict__ mode,
+                                   double* __restrict__ scratch, double kappa_max) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int kz = blockIdx.y;
   if (i >= nx || kz >= nzh) return;
@@ -1121,7 +1275,30 @@ __global__ void pois_factor_kernel(double2* __restrict__ fac, const double* __re
     const long q = ((long)kz * ny + j) * nx + i;
     f[q] = ip;
     f[(long)nzh * ny * nx + q] = cprev;
+    if (fac32) {
+      fac32[q] = (float)ip;
+      fac32[(long)nzh * ny * nx + q] = (float)cprev;
+    }
   }
+  if (!fac32) return;
+  bool fp32 = false;
+  if (kz > 0) {
+    const double* f = reinterpret_cast<const double*>(fac);
+    double prev = 0.0;
+    for (int j = 0; j < ny; ++j) {  // A y' = -|A| 1, y = -y'
+      const long q = ((long)kz * ny + j) * nx + i;
+      prev = (-(2.0 * (pa[j] + pc[j]) + lam) - pa[j] * prev) * f[q];
+      scratch[q] = prev;
+    }
+    double kappa = fabs(prev);
+    for (int j = ny - 2; j >= 0; --j) {
+      const long q = ((long)kz * ny + j) * nx + i;
+      prev = scratch[q] - f[(long)nzh * ny * nx + q] * prev;
+      kappa = fmax(kappa, fabs(prev));
+    }
+    fp32 = kappa <= kappa_max;
+  }
+  mode[(long)kz * nx + i] = fp32 ? 1 : 0;
 }
 
 }  // namespace
@@ -1137,6 +1314,7 @@ cudaError_t poisson_set_attributes() {
   set_smem_limit<FftxK<1>>(200 * 1024);
   set_smem_limit<FftxPK<-1>>(200 * 1024);
   set_smem_limit<FftxPK<1>>(200 * 1024);
+  set_smem_limit<TdmaSK>(NS_SMEM_MAX);
   cudaFuncSetAttribute(dctx_fwd_kernel<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   cudaFuncSetAttribute(dctx_inv_kernel<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   return cudaGetLastError();
@@ -1152,9 +1330,14 @@ cudaError_t launch_convective_rate(ns_ctx* c) {
   return cudaGetLastError();
 }
 
+size_t pois_staged_smem(int ny) { return TdmaSK::smem_bytes(ny); }
+int pois_staged_tile() { return TdmaSK::TL; }
+
 cudaError_t launch_pois_factor(ns_ctx* c, const double* lamx, const double* lamz) {
   dim3 grid((c->cfg.nx + 127) / 128, c->nzh);
-  pois_factor_kernel<<<grid, 128, 0, c->launch>>>(c->pois, c->gc, lamx, lamz, c->cfg.nx, c->cfg.ny, c->nzh);
+  pois_factor_kernel<<<grid, 128, 0, c->launch>>>(c->pois, c->gc, lamx, lamz, c->cfg.nx, c->cfg.ny, c->nzh,
+                                                  c->pois32 ? c->pois_f32 : nullptr, c->pois_mode,
+                                                  reinterpret_cast<double*>(c->spec), NS_POIS_FP32_KAPPA);
   return cudaGetLastError();
 }
 
@@ -1271,8 +1454,13 @@ cudaError_t emit_xm(LaunchSink& s, bool fwd) {
 cudaError_t emit_tdmam(LaunchSink& s) {
   ns_ctx* c = s.c;
   const PoisShape q = pois_shape(c);
-  return emit<TdmaMK>(s, TdmaMK::Args{sp32(c), c->pois, c->gc, q.nx, q.ny, c->nzh}, dim3((2 * q.nx + 127) / 128, c->nzh),
-                      dim3(128), 0);
+  if (c->pois_tiles)  // staged: the FP64 tiles, then the FP32 ones, in one launch
+    return emit<TdmaSK>(s,
+                        TdmaSK::Args{sp32(c), c->pois_f32, reinterpret_cast<const double*>(c->pois), c->pois_pa32,
+                                     c->gc + GC_PA * (q.ny + 1), c->pois_tiles, c->ntile64, q.nx, q.ny, c->nzh},
+                        dim3((unsigned)(c->ntile64 + c->ntile32)), dim3(TdmaSK::kThreads), TdmaSK::smem_bytes(q.ny));
+  return emit<TdmaMK>(s, TdmaMK::Args{sp32(c), c->pois, c->gc, q.nx, q.ny, c->nzh, c->pois_f32, c->pois_pa32, c->pois_mode},
+                      dim3((2 * q.nx + 127) / 128, c->nzh), dim3(128), 0);
 }
 
 template <bool ACC>

@@ -105,6 +105,7 @@ ns_layout make_layout(const ns_config* c) {
                                                al256(nx * 8)
                                          : 0;
   sz[LB_DT] = al256(sizeof(DtCtl)) + 8 * dt_scratch_doubles((int)nz, x_table_elems(c), line_table_floats(c));
+  sz[LB_POIS32] = c->precision == NS_MIXED ? pois32_bytes(nx, ny, nzh) : 0;
   size_t o = 0;
   for (int b = 0; b < LB_COUNT; ++b) {
     L.off[b] = o;
@@ -112,6 +113,35 @@ ns_layout make_layout(const ns_config* c) {
   }
   L.total = o;
   return L;
+}
+
+// Tile list of the mixed form's staged Poisson y solve, from the mode flags pois_factor_kernel
+// wrote: tiles of pois_staged_tile() kx holding a mode that takes FP64 first, then the tiles whose
+// modes all take FP32.  The register form stays (pois_tiles = null) when nx is not a multiple of
+// the tile width or a tile does not fit in shared memory.
+ns_status build_pois_tiles(ns_ctx* c) {
+  const int nx = c->cfg.nx, ny = c->cfg.ny, nzh = c->nzh, TL = pois_staged_tile();
+  if (nx % TL != 0 || pois_staged_smem(ny) > (size_t)NS_SMEM_MAX) {
+    c->pois_tiles = nullptr;
+    return NS_OK;
+  }
+  std::vector<unsigned char> mode((size_t)nzh * nx);
+  if (cudaMemcpy(mode.data(), c->pois_mode, mode.size(), cudaMemcpyDeviceToHost) != cudaSuccess) return NS_ERR_CUDA;
+  std::vector<int> t64, t32;
+  const int ntx = nx / TL;
+  for (int kz = 0; kz < nzh; ++kz)
+    for (int t = 0; t < ntx; ++t) {
+      bool all = true;
+      for (int l = 0; l < TL; ++l) all = all && mode[(size_t)kz * nx + t * TL + l];
+      (all ? t32 : t64).push_back(kz * ntx + t);
+    }
+  c->ntile64 = (int)t64.size();
+  c->ntile32 = (int)t32.size();
+  t64.insert(t64.end(), t32.begin(), t32.end());
+  if (upload_raw(c, c->pois_tiles, t64.data(), t64.size() * sizeof(int)) != cudaSuccess ||
+      cudaStreamSynchronize(c->stream) != cudaSuccess)
+    return NS_ERR_CUDA;
+  return NS_OK;
 }
 
 cudaError_t upload_d(ns_ctx* c, void* dst, const std::vector<double>& src) {
@@ -398,6 +428,12 @@ ns_status ns_init(ns_ctx** out, const ns_config* cfg, const ns_fields* fields, v
     c->twz32 = (float2*)t32;
     c->twx32 = (float2*)(t32 + al256(fft_twiddle_doubles(nz) * 4));
     c->twd32 = (float2*)(t32 + al256(fft_twiddle_doubles(nz) * 4) + al256(fft_twiddle_doubles(nx) * 4));
+    char* p32 = base + c->lay.off[LB_POIS32];
+    const size_t planes = al256(2 * (size_t)c->nzh * ny * nx * 4);
+    c->pois_f32 = (float*)p32;
+    c->pois_pa32 = (float*)(p32 + planes);
+    c->pois_mode = (unsigned char*)(p32 + planes + al256((size_t)ny * 4));
+    c->pois_tiles = (int*)(p32 + planes + al256((size_t)ny * 4) + al256((size_t)c->nzh * nx));
   }
   double* lamz_d = (double*)(base + c->lay.off[LB_LAMZ]);
 
@@ -463,9 +499,11 @@ ns_status ns_init(ns_ctx** out, const ns_config* cfg, const ns_fields* fields, v
     if (upload_d(c, c->twd, td) != cudaSuccess) st = NS_ERR_CUDA;
     if (c->pois32) {  // the same tables rounded to float for the FP32 transforms of the mixed form
       const std::vector<float> fz(tw.begin(), tw.end()), fx(tx.begin(), tx.end()), fd(td.begin(), td.end());
+      const std::vector<float> pa32(gc.begin() + (size_t)GC_PA * G, gc.begin() + (size_t)GC_PA * G + ny);
       if (upload_raw(c, c->twz32, fz.data(), fz.size() * 4) != cudaSuccess ||
           upload_raw(c, c->twx32, fx.data(), fx.size() * 4) != cudaSuccess ||
-          upload_raw(c, c->twd32, fd.data(), fd.size() * 4) != cudaSuccess)
+          upload_raw(c, c->twd32, fd.data(), fd.size() * 4) != cudaSuccess ||
+          upload_raw(c, c->pois_pa32, pa32.data(), pa32.size() * 4) != cudaSuccess)
         st = NS_ERR_CUDA;
     }
     for (int q = 0; q < c->nzh; ++q) lz[q] = (2.0 / (c->dz * c->dz)) * (1.0 - std::cos(2.0 * PI * q / nz));
@@ -476,6 +514,7 @@ ns_status ns_init(ns_ctx** out, const ns_config* cfg, const ns_fields* fields, v
     if (st == NS_OK && adi_set_attributes() != cudaSuccess) st = NS_ERR_CUDA;
     if (st == NS_OK && launch_pois_factor(c, lamx_d, lamz_d) != cudaSuccess) st = NS_ERR_CUDA;
     if (st == NS_OK && cudaStreamSynchronize(c->stream) != cudaSuccess) st = NS_ERR_CUDA;
+    if (st == NS_OK && c->pois32) st = build_pois_tiles(c);
   }
   // N_prev starts at zero (sub-step 0 does not read it; zero keeps it finite)
   if (st == NS_OK) {
@@ -563,6 +602,34 @@ ns_status ns_step(ns_ctx* c, int nsteps) {
   for (int s = 0; s < nsteps; ++s)
     if ((e = cudaGraphLaunch(c->gexec, c->stream)) != cudaSuccess) return cuda_fail(c, e, "graph launch");
   return NS_OK;
+}
+
+int ns_launches_per_step(ns_ctx* c) {
+  if (!c) return -1;
+  if (capturing(c)) {
+    fail(c, NS_ERR_STATE, "ns_launches_per_step during capture");
+    return -1;
+  }
+  if (!c->have_graph) {
+    if (capture_step(c, false, &c->graph, &c->gexec) != NS_OK) return -1;
+    c->have_graph = true;
+  }
+  size_t n = 0;
+  if (cudaGraphGetNodes(c->graph, nullptr, &n) != cudaSuccess) {
+    fail(c, NS_ERR_CUDA, "graph nodes");
+    return -1;
+  }
+  std::vector<cudaGraphNode_t> nodes(n);
+  if (n && cudaGraphGetNodes(c->graph, nodes.data(), &n) != cudaSuccess) {
+    fail(c, NS_ERR_CUDA, "graph nodes");
+    return -1;
+  }
+  int k = 0;
+  for (size_t q = 0; q < n; ++q) {
+    cudaGraphNodeType t;
+    if (cudaGraphNodeGetType(nodes[q], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++k;
+  }
+  return k;
 }
 
 ns_status ns_convective_rate(ns_ctx* c, double* rate) {
@@ -904,9 +971,15 @@ ns_status ns_autotune(ns_ctx* c) { return autotune_ctx(c, true); }
 ns_status ns_get_buffer(ns_ctx* c, int which, void** ptr, size_t* bytes) {
   if (!c || !ptr) return NS_ERR_ARG;
   static const int map[8] = {LB_RU, LB_RV, LB_RW, LB_NU, LB_NV, LB_NW, LB_PHI, LB_SPEC};
-  if (which < 0 || which > 7) return fail(c, NS_ERR_ARG, "unknown buffer");
-  const int b = map[which];
+  if (which < 0 || which > 8) return fail(c, NS_ERR_ARG, "unknown buffer");
   const size_t nx = c->cfg.nx, ny = c->cfg.ny, nz = c->cfg.nz;
+  if (which == NS_BUF_POIS_MODE) {
+    if (!c->pois32) return fail(c, NS_ERR_UNSUPPORTED, "the Poisson mode flags exist only in the mixed form");
+    *ptr = c->pois_mode;
+    if (bytes) *bytes = (size_t)c->nzh * nx;
+    return NS_OK;
+  }
+  const int b = map[which];
   size_t n;
   switch (which) {
     case NS_BUF_RV:

@@ -92,9 +92,11 @@ ns_status make_plan(ns_batch* b) {
       BatchPlanner pl;
       for (ns_ctx* c : b->inst) {
         LaunchSink s{c, &pl};
+        pl.next_instance();
         cudaError_t e = BATCH_STAGES[st](s, k);
         if (e != cudaSuccess) return bfail(b, NS_ERR_CUDA, std::string("plan ") + BATCH_STAGE_NAMES[st]);
       }
+      pl.order();
       for (const BatchGroup& g : pl.groups) {
         const int n = (int)g.grid.size();
         cudaError_t e = cudaSuccess;

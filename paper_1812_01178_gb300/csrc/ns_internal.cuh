@@ -5,6 +5,7 @@
 #include <stdint.h>
 #include <string>
 #include <utility>
+#include <algorithm>
 #include <vector>
 
 #include "../../include/ns.h"
@@ -158,7 +159,8 @@ struct ns_layout {
 
 enum {
   LB_RU = 0, LB_RV, LB_RW, LB_NU, LB_NV, LB_NW, LB_PHI, LB_SPEC, LB_POIS, LB_GC, LB_XTAB, LB_YTAB,
-  LB_ZTAB, LB_TWZ, LB_TWX, LB_LAMX, LB_LAMZ, LB_RTAB, LB_DOUT, LB_TWD, LB_RCY, LB_STEPK, LB_PTAB, LB_TW32, LB_DT, LB_COUNT
+  LB_ZTAB, LB_TWZ, LB_TWX, LB_LAMX, LB_LAMZ, LB_RTAB, LB_DOUT, LB_TWD, LB_RCY, LB_STEPK, LB_PTAB, LB_TW32, LB_DT,
+  LB_POIS32, LB_COUNT
 };
 
 // dt-dependent constants of one RK3 sub-step (entries 0..2) and of the projection of an initial
@@ -237,6 +239,16 @@ struct ns_ctx {
   // refinement (k_poisson.cu); off for FP64 contexts
   bool pois32 = false;
   float2 *twz32 = nullptr, *twx32 = nullptr, *twd32 = nullptr;
+  // its y solves: the FP64 factors rounded to float (two planes), a_j in float, and one flag per
+  // (kz, kx) mode, 1 where the solve runs in FP32 (pois_factor_kernel)
+  float* pois_f32 = nullptr;
+  float* pois_pa32 = nullptr;
+  unsigned char* pois_mode = nullptr;
+  // the staged y solve's tiles of pois_staged_tile() kx (nx a multiple of it, a tile within
+  // shared memory): the ntile64 tiles holding a mode that takes FP64, then the ntile32 others;
+  // null: the register form
+  int* pois_tiles = nullptr;
+  int ntile32 = 0, ntile64 = 0;
   double* flux;             // [0]: inflow flux, [1]: last outflow correction (diagnostics)
   unsigned long long* rate; // bits of the convective rate of ns_convective_rate (in the flux block)
   std::vector<double> gc_h; // host copy of the grid coefficients (tables are rebuilt when dt changes)
@@ -370,10 +382,14 @@ cudaError_t set_smem_limit(int bytes) {
 // Launch sink.  Every stage is written once as `stage(LaunchSink&, substep)` and emits its kernel
 // with emit<K>(sink, args, grid, block, smem): a single-instance sink launches at once on the
 // context's stream; a batch sink hands the launch to a planner that groups the instances of a
-// stage by functor type K and later launches each group as one persistent batched_kernel<K>.
+// stage by functor type K and by the launch's place in the instance's sequence for that stage
+// (instances of different shapes may emit different sequences, e.g. the y solve of the mixed
+// form), and later launches the groups in the order of those places, each as one persistent
+// batched_kernel<K>.
 // ---------------------------------------------------------------------------------------------
 struct BatchGroup {
   const void* key;                      // identifies K
+  int ord;                              // place of the launch in each instance's sequence
   size_t arg_size;
   std::vector<unsigned char> args;      // packed K::Args, one per instance of the group
   std::vector<int> first;               // block prefix, first[0] = 0
@@ -387,6 +403,13 @@ struct BatchGroup {
 
 struct BatchPlanner {
   std::vector<BatchGroup> groups;
+  int ord = 0;  // place of the next launch in the current instance's sequence
+  void next_instance() { ord = 0; }
+  // groups in launch order: by place, then by first appearance
+  void order() {
+    std::stable_sort(groups.begin(), groups.end(),
+                     [](const BatchGroup& x, const BatchGroup& y) { return x.ord < y.ord; });
+  }
   template <typename K>
   static cudaError_t enqueue_k(const void* dargs, const BatchMap& m, unsigned grid, dim3 block, size_t smem,
                                cudaStream_t s) {
@@ -404,11 +427,12 @@ struct BatchPlanner {
     static const char key = 0;
     BatchGroup* g = nullptr;
     for (auto& q : groups)
-      if (q.key == &key) g = &q;
+      if (q.key == &key && q.ord == ord) g = &q;
     if (!g) {
       groups.emplace_back();
       g = &groups.back();
       g->key = &key;
+      g->ord = ord;
       g->arg_size = sizeof(typename K::Args);
       g->first.push_back(0);
       g->block = block;
@@ -421,6 +445,7 @@ struct BatchPlanner {
     g->grid.push_back(make_uint3(grid.x, grid.y, grid.z));
     g->first.push_back(g->first.back() + (int)(grid.x * grid.y * grid.z));
     if (smem > g->smem) g->smem = smem;
+    ++ord;
     return cudaSuccess;
   }
 };
@@ -506,3 +531,19 @@ size_t adi_z_tab_count(int nz);
 // K, lambda^1 .. lambda^NS_ZF_KMAX.
 constexpr int NS_ZF_KMAX = 8;
 inline size_t ztab_entries(int nz) { return 4 * (size_t)nz + 2 + 4 + NS_ZF_KMAX; }
+
+// The mixed form solves a Poisson y system in FP32 arithmetic when kz > 0 and its Skeel condition
+// number is at most this: the FP32 Thomas error then stays near the FP32 transforms' own rounding
+// (a few 1e-7 of the line on the stretched channel and boundary-layer grids), which the FP64
+// refinement absorbs like theirs.
+constexpr double NS_POIS_FP32_KAPPA = 4096.0;
+// bytes of the mixed form's FP32 y-solve block: two float factor planes, a_j, the mode flags
+inline size_t pois32_bytes(size_t nx, size_t ny, size_t nzh) {
+  auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
+  return al(2 * nzh * ny * nx * 4) + al(ny * 4) + al(nzh * nx) + al(nzh * (nx / 8 + 1) * 4);
+}
+// largest dynamic shared memory of one block (227 KB)
+constexpr int NS_SMEM_MAX = 227 * 1024;
+// shared memory and tile width (kx) of the staged Poisson y solve of the mixed form (k_poisson.cu)
+size_t pois_staged_smem(int ny);
+int pois_staged_tile();

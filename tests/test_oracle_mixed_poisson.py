@@ -10,13 +10,15 @@ import pytest
 
 from oracle import ns_oracle as O
 from paper_1812_01178_gb300 import inputs as I
+from tests import poisson_modes as PM
 
 sf = pytest.importorskip("scipy.fft")
 
 
-def _poisson(g, rhs, fp32):
+def _poisson(g, rhs, fp32, y32=None):
     """D G phi = rhs: z real transform, x transform, y Thomas per (kx, kz) in FP64, inverses;
-    with fp32 the transforms and the spectrum are single precision (phi returned in FP32)."""
+    with fp32 the transforms and the spectrum are single precision (phi returned in FP32); y32, a
+    [kz, kx] mask, runs those modes' y solves in FP32 arithmetic (the mixed form's split)."""
     a, c = O.poisson_ycoeffs(g)
     lx = O.modified_wavenumbers(g.nx, g.dx)
     lz = O.modified_wavenumbers(g.nz, g.dz)[: g.nz // 2 + 1]
@@ -29,7 +31,10 @@ def _poisson(g, rhs, fp32):
     B[0, 0, 0], C[0, 0, 0] = 1.0, 0.0
     d = d.copy()
     d[0, 0, 0] = 0.0
-    ph = np.moveaxis(O.thomas(A, B, C, d), -1, 1)
+    ph = O.thomas(A, B, C, d)
+    if y32 is not None:
+        ph[y32] = PM.thomas32(A[y32], B[y32], C[y32], d[y32])
+    ph = np.moveaxis(ph, -1, 1)
     if fp32:
         ph = ph.astype(np.complex64)
     phi = sf.irfft(sf.ifft(ph, axis=2), n=g.nz, axis=0)
@@ -40,8 +45,11 @@ def _lap(g, phi):
     return O.divergence(g, *O.gradient(g, phi))
 
 
+@pytest.mark.parametrize("y32", [False, True])
 @pytest.mark.parametrize("low", [0.0, 20.0])
-def test_fp32_transforms_need_one_fp64_refinement(low):
+def test_fp32_transforms_need_one_fp64_refinement(low, y32):
+    """Also with the y solves of the well-conditioned modes (kz > 0, Skeel condition <= 4096) in
+    FP32 arithmetic, as the mixed form runs them: one refinement still reaches the FP64 level."""
     case, u, v, w, p = I.small_channel(32, 24, 32, seed=12, amp=0.3)
     g = O.Grid.from_case(case)
     if low:  # add a divergence in the lowest (kx, kz) modes
@@ -55,13 +63,52 @@ def test_fp32_transforms_need_one_fp64_refinement(low):
     nb = np.abs(b).max()
     phi64 = _poisson(g, b, False)
     assert np.abs(b - _lap(g, phi64)).max() < 1e-12 * nb
-    phi1 = _poisson(g, b, True).astype(np.float64)
+    sel = None
+    if y32:
+        sel, _ = PM.fp32_modes(g, False)
+        assert 0.5 < sel.mean() < 1.0 and not sel[0].any()
+    phi1 = _poisson(g, b, True, sel).astype(np.float64)
     r1 = b - _lap(g, phi1)
     assert 1e-9 * nb < np.abs(r1).max() < 1e-4 * nb  # the FP32 level: not good enough alone
-    phi = phi1 + _poisson(g, r1, True).astype(np.float64)
+    phi = phi1 + _poisson(g, r1, True, sel).astype(np.float64)
     r2 = b - _lap(g, phi)
     assert np.abs(r2).max() < 1e-10 * nb
     assert np.abs(r2).max() < 1e-3 * np.abs(r1).max()
     # the refined phi equals the FP64 solve up to the gauge constant
     e = (phi - phi.mean()) - (phi64 - phi64.mean())
     assert np.abs(e).max() < 1e-9 * np.abs(phi64).max()
+
+
+@pytest.mark.parametrize("bl", [False, True])
+def test_skeel_condition_by_one_solve_and_fp32_line_solves(bl):
+    """The mode selection's two parts on the stretched y grids of the 256x192x256 channel and of
+    the 1024x256x512 boundary layer: (1) kappa by one Thomas solve equals the definition
+    || |A^-1| |A| 1 ||_inf by a dense inverse; (2) the FP32 sweep with rounded FP64 factors solves
+    a mode's system to the FP32 level, and one refinement on the FP64 residual to the FP64 level;
+    (3) kappa falls with the wavenumber, so the FP64 modes are the lowest ones."""
+    if bl:
+        g = O.Grid.from_case(I.boundary_layer_case(1024, 256, 512))
+    else:
+        g = O.Grid(256, 192, 256, 2 * math.pi, math.pi, I.channel_faces(192, 2.0))
+    a, c = O.poisson_ycoeffs(g)
+    lam = PM.mode_lambdas(g, bl)
+    rng = np.random.default_rng(7)
+    kz_kx = [(1, 0), (1, 1), (5, 3), (10, 10), (40, 40), (60, 100)]
+    kaps = []
+    for kz, kx in kz_kx:
+        L = lam[kz, kx]
+        k1 = PM.skeel(a, c, np.array([L]))[0]
+        assert abs(k1 - PM.skeel_dense(a, c, L)) < 1e-9 * k1
+        kaps.append(k1)
+        A = np.diag(-(a + c) - L) + np.diag(a[1:], -1) + np.diag(c[:-1], 1)
+        d = rng.standard_normal(g.ny) + 1j * rng.standard_normal(g.ny)
+        x = np.linalg.solve(A, d)
+        Bd = (-(a + c) - L)[None, :]
+        x1 = PM.thomas32(a[None, :], Bd, c[None, :], d[None, :])[0].astype(np.complex128)
+        x2 = x1 + PM.thomas32(a[None, :], Bd, c[None, :], (d - A @ x1)[None, :])[0].astype(np.complex128)
+        e1 = np.abs(x1 - x).max() / np.abs(x).max()
+        e2 = np.abs(x2 - x).max() / np.abs(x).max()
+        assert 1e-9 < e1 < 2e-6, (kz, kx, e1)
+        assert e2 < 1e-11, (kz, kx, e2)
+    assert all(k0 > k1 for k0, k1 in zip(kaps, kaps[1:]))
+    assert kaps[0] > 1e4 and kaps[-1] < PM.KAPPA_MAX
