@@ -697,22 +697,38 @@ struct DivzMK {
         }
       }
       const float* __restrict__ f = a.phi1;
-      for (int q = threadIdx.x; q < TX * nz; q += blockDim.x) {
+      // two elements per thread and pass, their loads all issued before either is used
+      constexpr int G = 2;
+      const int nq = TX * nz;
+      for (int q0 = threadIdx.x; q0 < nq; q0 += G * blockDim.x) {
+      float F0[G], FE[G], FW[G], FS[G], FN[G], FU[G], FD[G];
+      double BS[G];
+#pragma unroll
+      for (int g = 0; g < G; ++g) {
+        const int q = min(q0 + g * (int)blockDim.x, nq - 1);
         const int il = q % TX, k = q / TX, i = i0 + il;
         const long row = k * pl + (long)j * nx, cc = row + i;
-        const float f0 = __ldg(f + cc);
-        float fe, fw;
+        F0[g] = __ldg(f + cc);
         if (a.bl) {
-          fe = (i + 1 < nx) ? __ldg(f + cc + 1) : f0;
-          fw = (i > 0) ? __ldg(f + cc - 1) : f0;
+          FE[g] = __ldg(f + cc + ((i + 1 < nx) ? 1 : 0));
+          FW[g] = __ldg(f + cc - ((i > 0) ? 1 : 0));
         } else {
-          fe = __ldg(f + row + ((i + 1 == nx) ? 0 : i + 1));
-          fw = __ldg(f + row + ((i == 0) ? nx - 1 : i - 1));
+          FE[g] = __ldg(f + row + ((i + 1 == nx) ? 0 : i + 1));
+          FW[g] = __ldg(f + row + ((i == 0) ? nx - 1 : i - 1));
         }
-        const float fs = j > 0 ? __ldg(f + cc - nx) : f0;
-        const float fn = j + 1 < ny ? __ldg(f + cc + nx) : f0;
+        FS[g] = __ldg(f + cc - (j > 0 ? nx : 0));
+        FN[g] = __ldg(f + cc + (j + 1 < ny ? nx : 0));
         const int kp = (k + 1 == nz) ? 0 : k + 1, km = (k == 0) ? nz - 1 : k - 1;
-        const float fu = __ldg(f + kp * pl + (long)j * nx + i), fd = __ldg(f + km * pl + (long)j * nx + i);
+        FU[g] = __ldg(f + kp * pl + (long)j * nx + i);
+        FD[g] = __ldg(f + km * pl + (long)j * nx + i);
+        BS[g] = __ldg(a.bs + cc);
+      }
+#pragma unroll
+      for (int g = 0; g < G; ++g) {
+        const int q = q0 + g * blockDim.x;
+        if (q >= nq) break;
+        const int il = q % TX, k = q / TX;
+        const float f0 = F0[g], fe = FE[g], fw = FW[g], fs = FS[g], fn = FN[g], fu = FU[g], fd = FD[g];
         float sxh, sxl, szh, szl;
         ff_two_sum(fe, fw, sxh, sxl);
         ff_two_sum(fu, fd, szh, szl);
@@ -736,8 +752,9 @@ struct DivzMK {
         e = __fmaf_rn(wl[4], fn, e);
         ff_two_sum(S, -p, S, t);
         C = __fsub_rn(__fadd_rn(C, t), e);
-        const double r = (__ldg(a.bs + cc) + f2d(S)) + f2d(C);
+        const double r = (BS[g] + f2d(S)) + f2d(C);
         reinterpret_cast<float*>(A + (il >> 1) * nz + k)[il & 1] = 0.5f * d2f_rn(r);
+      }
       }
     }
     __syncthreads();
@@ -889,26 +906,62 @@ struct IfftzMK {
     const int i0 = bid_.x * TX;
     const int j = bid_.y;
     const int nh = nz >> 1;
-    for (int q = threadIdx.x; q < nseq * (nh + 1); q += blockDim.x) {
-      const int c = q % nseq, m = q / nseq;
-      const long o = ((long)m * ny + j) * nx + i0 + 2 * c;
-      float2 xa = a.spec[o], xb = a.spec[o + 1];
-      if (m == 0 || m == nh) {
-        xa.y = 0.0f;
-        xb.y = 0.0f;
+    const long pl = (long)ny * nx;
+    // ACC: the tile of phi1 this block adds to ([nz][TX] floats after A, B) is copied in at once
+    // (cp.async), so that the output loop does not wait on a global load per element
+    float* P1 = reinterpret_cast<float*>(B + nseq * nz);
+    if (ACC) {
+      if ((TX & 3) == 0) {
+        const int pr = TX >> 2;  // 16-byte pieces per row
+        for (int q = threadIdx.x; q < nz * pr; q += blockDim.x) {
+          const int k = q / pr, r = q - k * pr;
+          cp_async16(reinterpret_cast<float4*>(P1 + k * TX) + r,
+                     reinterpret_cast<const float4*>(a.phi1 + k * pl + (long)j * nx + i0) + r);
+        }
+        cp_async_commit();
+      } else {
+        for (int q = threadIdx.x; q < nz * TX; q += blockDim.x)
+          P1[q] = a.phi1[(q / TX) * pl + (long)j * nx + i0 + q % TX];
       }
-      A[c * nz + m] = make_float2(xa.x - xb.y, xa.y + xb.x);
-      if (m > 0 && m < nh) A[c * nz + nz - m] = make_float2(xa.x + xb.y, xb.x - xa.y);
     }
+    // spectrum loads in groups of four per thread, all issued before any is used
+    constexpr int G = 4;
+    const int nq = nseq * (nh + 1);
+    for (int q0 = threadIdx.x; q0 < nq; q0 += G * blockDim.x) {
+      float2 xa[G], xb[G];
+#pragma unroll
+      for (int g = 0; g < G; ++g) {
+        const int q = q0 + g * blockDim.x;
+        if (q < nq) {
+          const int c = q % nseq, m = q / nseq;
+          const long o = ((long)m * ny + j) * nx + i0 + 2 * c;
+          xa[g] = a.spec[o];
+          xb[g] = a.spec[o + 1];
+        }
+      }
+#pragma unroll
+      for (int g = 0; g < G; ++g) {
+        const int q = q0 + g * blockDim.x;
+        if (q < nq) {
+          const int c = q % nseq, m = q / nseq;
+          if (m == 0 || m == nh) {
+            xa[g].y = 0.0f;
+            xb[g].y = 0.0f;
+          }
+          A[c * nz + m] = make_float2(xa[g].x - xb[g].y, xa[g].y + xb[g].x);
+          if (m > 0 && m < nh) A[c * nz + nz - m] = make_float2(xa[g].x + xb[g].y, xb[g].x - xa[g].y);
+        }
+      }
+    }
+    if (ACC) cp_async_wait<0>();
     __syncthreads();
     const float2* R = stockham<1, float2>(A, B, nz, a.pz, nseq, a.twz);
-    const long pl = (long)ny * nx;
     for (int q = threadIdx.x; q < TX * nz; q += blockDim.x) {
       const int il = q % TX, k = q / TX;
       const float2 t = R[(il >> 1) * nz + k];
       const float val = (il & 1) ? t.y : t.x;
       const long cc = k * pl + (long)j * nx + i0 + il;
-      if (ACC) a.phi[cc] = f2d(a.phi1[cc]) + f2d(val);
+      if (ACC) a.phi[cc] = f2d(P1[q]) + f2d(val);
       else a.phi1[cc] = val;
     }
   }
@@ -1469,7 +1522,8 @@ cudaError_t emit_ifftzm(LaunchSink& s) {
   const PoisShape q = pois_shape(c);
   return emit<IfftzMK<ACC>>(s, typename IfftzMK<ACC>::Args{sp32(c), c->twz32, phi1(c), c->phi, q.nx, q.ny, q.nz, q.pz,
                                                            q.TXm},
-                            dim3(q.nx / q.TXm, q.ny), dim3(256), (size_t)q.TXm * q.nz * sizeof(float2));
+                            dim3(q.nx / q.TXm, q.ny), dim3(256),
+                            (size_t)q.TXm * q.nz * (sizeof(float2) + (ACC ? sizeof(float) : 0)));
 }
 
 void single_kernel_dct_fwd(ns_ctx* c, unsigned bx, size_t smx, long nrows, int nx, int px, int R) {
