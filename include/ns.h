@@ -358,8 +358,11 @@ void ns_batch_destroy(ns_batch* b);
  * exchange of end values with the two neighbours, Algorithm 1) or PPT (Eq. (Zppt): all-gather of
  * the end values), and the Poisson y solve of every (kx, kz) line by PPT.  With inflow /
  * convective outflow in x, the outflow mass-flux correction sums every slab's share (FLUX
- * exchange, an all-gather of one double).  Built for NS_FP64, the plain pressure update and fixed
- * inflow planes (other configurations: NS_ERR_ARG); every slab needs at least 3 rows (ny >= 3 p).
+ * exchange, an all-gather of one double); with the recycling inflow (recycle_i != 0) every slab
+ * packs the recycle-plane samples of its rows (RCY exchange, an all-gather) and, in sub-step 0,
+ * writes the inflow rows it holds from the whole plane (Sec. 2.1; the recycling of one context).
+ * Built for NS_FP64 and the plain pressure update (other configurations: NS_ERR_ARG); every slab
+ * needs at least 3 rows (ny >= 3 p).
  *
  * Local fields.  A slab's u, w, p hold rows j0-hb .. j1+ha-1 and its v the faces j0-hb .. j1+ha,
  * where hb = (r > 0) and ha = (r < p-1) are the halo rows below and above (layouts as above with
@@ -368,10 +371,12 @@ void ns_batch_destroy(ns_batch* b);
  * the halo rows of u, v, w, p are filled by the exchanges.
  *
  * Exchanges.  A sub-step is six phases (NS_SLAB_*) with an exchange after each:
- *   PACK (before the first sub-step only) -> HALO -> RHS -> ADIY -> ADIZ -> VSTAR, FLUX -> POIS
- *   -> POIS -> PHI -> PHI -> PROJECT -> HALO (ready for the next sub-step's RHS)
+ *   PACK (before the first sub-step only) -> HALO, RCY -> RHS -> ADIY -> ADIZ -> VSTAR, FLUX -> POIS
+ *   -> POIS -> PHI -> PHI -> PROJECT -> HALO (ready for the next sub-step's RHS), and RCY after
+ *   the PROJECT of sub-step 2
  * where the exchange named after a phase is NS_XCH_<name> (FLUX only matters with inflow /
- * outflow x; with periodic x it carries nothing the slabs read).  For exchange x every slab has a send
+ * outflow x; with periodic x it carries nothing the slabs read; RCY has slots of 0 bytes, and
+ * nothing to move, without recycling).  For exchange x every slab has a send
  * buffer of ns_slab_slot_bytes bytes and a receive buffer of p such slots; after the phase that
  * writes its send buffer, the caller copies slab s's send buffer into slot s of every slab r that
  * reads it (ns_slab_slots: slots lo .. hi of slab r; the slab's own slot, where read, it writes
@@ -380,7 +385,7 @@ void ns_batch_destroy(ns_batch* b);
  * ------------------------------------------------------------------------------------------- */
 typedef struct ns_slab ns_slab;
 enum { NS_XCH_HALO = 0, NS_XCH_ADIY = 1, NS_XCH_VSTAR = 2, NS_XCH_POIS = 3, NS_XCH_PHI = 4, NS_XCH_FLUX = 5,
-       NS_XCH_COUNT = 6 };
+       NS_XCH_RCY = 6, NS_XCH_COUNT = 7 };
 enum { NS_SLAB_PACK = 0, NS_SLAB_RHS = 1, NS_SLAB_ADIZ = 2, NS_SLAB_POIS = 3, NS_SLAB_PHI = 4,
        NS_SLAB_PROJECT = 5 };
 

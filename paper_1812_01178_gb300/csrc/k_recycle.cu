@@ -11,7 +11,10 @@
 //      inner mean gamma U, outer gamma U + (1 - gamma) U_inf, mean V unscaled, mean W zero,
 //      fluctuations times gamma, blended with Lund's weight
 //      W(eta) = (1 + tanh(4 (eta - 0.2) / (0.6 eta + 0.2)) / tanh 4) / 2 (1 above eta = 1).
-// Writes u on face 0, v_in and w_in.
+// Writes u on face 0, v_in and w_in.  The recycle plane comes from the fields (one context) or
+// from samples gathered from every y slab (ns_slab.cu: each slab packs its own rows, an all-gather
+// gives every slab the whole plane, and every slab writes the inflow rows it holds); the
+// arithmetic is the same either way.
 #include "ns_internal.cuh"
 
 namespace {
@@ -37,20 +40,53 @@ __host__ __device__ inline RcyView rcy_view(double* b, int ny) {
   return v;
 }
 
-__global__ void __launch_bounds__(256) recycle_means_kernel(const double* __restrict__ u, const double* __restrict__ v,
-                                                            const double* __restrict__ w, double* rcy, int nx,
-                                                            int ny, int nz, int ir) {
+// Samples of the recycle plane, rows and faces of the whole domain: u on face i_r, v and w
+// averaged over the centres i_r - 1 and i_r.  From the fields, or (g set) from a gathered buffer
+// where row j's nz samples start at uoff[j] (u), woff[j] (w) and face f's at voff[f] (v).
+struct RcySrc {
+  const double* u;
+  const double* v;
+  const double* w;
+  int nx, ny, ir;
+  const double* g;
+  const long* uoff;
+  const long* woff;
+  const long* voff;
+  __device__ __forceinline__ double ur(int j, int k) const {
+    if (g) return g[__ldg(uoff + j) + k];
+    return __ldg(u + ((long)k * ny + j) * nx + ir);
+  }
+  __device__ __forceinline__ double wr(int j, int k) const {
+    if (g) return g[__ldg(woff + j) + k];
+    const long c = ((long)k * ny + j) * nx;
+    return 0.5 * (__ldg(w + c + ir - 1) + __ldg(w + c + ir));
+  }
+  __device__ __forceinline__ double vr(int f, int k) const {
+    if (g) return g[__ldg(voff + f) + k];
+    const long c = ((long)k * (ny + 1) + f) * nx;
+    return 0.5 * (__ldg(v + c + ir - 1) + __ldg(v + c + ir));
+  }
+};
+
+// Where the inflow planes go: rows rows of cells (and rows + 1 faces) of the arrays held here,
+// local row 0 being row jg0 of the whole domain (one context: rows = ny, jg0 = 0).
+struct RcyDst {
+  double* u;     // u on face 0 of every local row: u[(k rows + jl) nx]
+  double* v_in;  // [k (rows + 1) + fl]
+  double* w_in;  // [k rows + jl]
+  int nx, rows, jg0;
+};
+
+__global__ void __launch_bounds__(256) recycle_means_kernel(const RcySrc src, double* rcy, int ny, int nz) {
   const int j = blockIdx.x;  // 0..ny
   const RcyView R = rcy_view(rcy, ny);
   __shared__ double red[3][256];
   double su = 0.0, sv = 0.0, sw = 0.0;
   for (int k = threadIdx.x; k < nz; k += blockDim.x) {
-    const long fv = ((long)k * (ny + 1) + j) * nx;
-    sv += 0.5 * (__ldg(v + fv + ir - 1) + __ldg(v + fv + ir));
+    sv += src.vr(j, k);
     if (j < ny) {
-      const long c = ((long)k * ny + j) * nx;
-      su += __ldg(u + c + ir);
-      sw += 0.5 * (__ldg(w + c + ir - 1) + __ldg(w + c + ir));
+      su += src.ur(j, k);
+      sw += src.wr(j, k);
     }
   }
   red[0][threadIdx.x] = su;
@@ -108,52 +144,42 @@ __device__ __forceinline__ double lund_weight(double eta) {
   return 0.5 * (1.0 + tanh(4.0 * (eta - 0.2) / (0.6 * eta + 0.2)) / tanh(4.0));
 }
 
-__global__ void __launch_bounds__(128) recycle_apply_kernel(double* __restrict__ u, const double* __restrict__ v,
-                                                            const double* __restrict__ w, double* __restrict__ v_in,
-                                                            double* __restrict__ w_in, const double* rcy, int nx,
-                                                            int ny, int nz, int ir, double delta_in, double u_inf) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;  // 0..ny
+__global__ void __launch_bounds__(128) recycle_apply_kernel(const RcySrc src, const RcyDst dst, const double* rcy,
+                                                            int ny, double delta_in, double u_inf) {
+  const int jl = blockIdx.x * blockDim.x + threadIdx.x;  // local row / face 0..rows
   const int k = blockIdx.y;
-  if (j > ny) return;
+  if (jl > dst.rows) return;
+  const int j = dst.jg0 + jl;  // row / face of the whole domain
   const RcyView R = rcy_view(const_cast<double*>(rcy), ny);
   const double gam = R.sc[0], r = R.sc[1];
-  if (j < ny) {
+  if (jl < dst.rows) {
     // centre samples with the wall point (y = 0, value 0) in front: sample q is centre q - 1
     const double y = R.ys[j + 1];
     const double yi = gam * y, yo = r * y;
-    const long row = (long)k * ny * nx;
     auto Uc = [&](int q) { return q == 0 ? 0.0 : R.U[q - 1]; };
-    auto up = [&](int q) { return q == 0 ? 0.0 : __ldg(u + row + (long)(q - 1) * nx + ir) - R.U[q - 1]; };
-    auto wp = [&](int q) {
-      if (q == 0) return 0.0;
-      const long c = row + (long)(q - 1) * nx;
-      return 0.5 * (__ldg(w + c + ir - 1) + __ldg(w + c + ir)) - R.W[q - 1];
-    };
+    auto up = [&](int q) { return q == 0 ? 0.0 : src.ur(q - 1, k) - R.U[q - 1]; };
+    auto wp = [&](int q) { return q == 0 ? 0.0 : src.wr(q - 1, k) - R.W[q - 1]; };
     const double W = lund_weight(y / delta_in);
     const double Ui = gam * interp(yi, R.ys, ny + 1, Uc);
     const double Uo = gam * interp(yo, R.ys, ny + 1, Uc) + (1.0 - gam) * u_inf;
     const double ui = gam * interp(yi, R.ys, ny + 1, up), uo = gam * interp(yo, R.ys, ny + 1, up);
-    u[row + (long)j * nx] = (1.0 - W) * (Ui + ui) + W * (Uo + uo);
+    dst.u[((long)k * dst.rows + jl) * dst.nx] = (1.0 - W) * (Ui + ui) + W * (Uo + uo);
     const double wi = gam * interp(yi, R.ys, ny + 1, wp), wo = gam * interp(yo, R.ys, ny + 1, wp);
-    w_in[(long)k * ny + j] = (1.0 - W) * wi + W * wo;
+    dst.w_in[(long)k * dst.rows + jl] = (1.0 - W) * wi + W * wo;
   }
   {
     double val = 0.0;
     if (j > 0 && j < ny) {
       const double y = R.yf[j];
       const double yi = gam * y, yo = r * y;
-      const long rowv = (long)k * (ny + 1) * nx;
       auto Vf = [&](int q) { return R.V[q]; };
-      auto vp = [&](int q) {
-        const long c = rowv + (long)q * nx;
-        return 0.5 * (__ldg(v + c + ir - 1) + __ldg(v + c + ir)) - R.V[q];
-      };
+      auto vp = [&](int q) { return src.vr(q, k) - R.V[q]; };
       const double W = lund_weight(y / delta_in);
       const double Vi = interp(yi, R.yf, ny + 1, Vf), Vo = interp(yo, R.yf, ny + 1, Vf);
       const double vi = gam * interp(yi, R.yf, ny + 1, vp), vo = gam * interp(yo, R.yf, ny + 1, vp);
       val = (1.0 - W) * (Vi + vi) + W * (Vo + vo);
     }
-    v_in[(long)k * (ny + 1) + j] = val;
+    dst.v_in[(long)k * (dst.rows + 1) + jl] = val;
   }
 }
 
@@ -161,23 +187,44 @@ __global__ void __launch_bounds__(128) recycle_apply_kernel(double* __restrict__
 
 size_t recycle_block_doubles(int ny) { return 5 * (size_t)ny + 4 + 2; }
 
+void recycle_grid_host(const double* yf, int ny, double* h) {
+  for (size_t q = 0; q < recycle_block_doubles(ny); ++q) h[q] = 0.0;
+  h[0] = yf[0];
+  for (int j = 0; j < ny; ++j) h[1 + j] = 0.5 * (yf[j] + yf[j + 1]);
+  for (int j = 0; j <= ny; ++j) h[ny + 1 + j] = yf[j];
+}
+
 cudaError_t recycle_upload_grid(ns_ctx* c) {
   const int ny = c->cfg.ny;
-  std::vector<double> h(recycle_block_doubles(ny), 0.0);
-  h[0] = c->yf[0];
-  for (int j = 0; j < ny; ++j) h[1 + j] = 0.5 * (c->yf[j] + c->yf[j + 1]);
-  for (int j = 0; j <= ny; ++j) h[ny + 1 + j] = c->yf[j];
+  std::vector<double> h(recycle_block_doubles(ny));
+  recycle_grid_host(c->yf.data(), ny, h.data());
   cudaError_t e = cudaMemcpyAsync(c->rcy, h.data(), h.size() * 8, cudaMemcpyHostToDevice, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   return e;
 }
 
+namespace {
+cudaError_t recycle_run(const RcySrc& src, const RcyDst& dst, double* rcy, int ny, int nz, double delta_in,
+                        double u_inf, cudaStream_t st) {
+  recycle_means_kernel<<<ny + 1, 256, 0, st>>>(src, rcy, ny, nz);
+  recycle_scalars_kernel<<<1, 32, 0, st>>>(rcy, ny, delta_in, u_inf);
+  recycle_apply_kernel<<<dim3((dst.rows + 1 + 127) / 128, nz), 128, 0, st>>>(src, dst, rcy, ny, delta_in, u_inf);
+  return cudaGetLastError();
+}
+}  // namespace
+
 cudaError_t launch_recycle(ns_ctx* c, int k) {
   if (k != 0 || !c->cfg.recycle_i) return cudaSuccess;
-  const int nx = c->cfg.nx, ny = c->cfg.ny, nz = c->cfg.nz, ir = c->cfg.recycle_i;
-  recycle_means_kernel<<<ny + 1, 256, 0, c->launch>>>(c->f.u, c->f.v, c->f.w, c->rcy, nx, ny, nz, ir);
-  recycle_scalars_kernel<<<1, 32, 0, c->launch>>>(c->rcy, ny, c->cfg.delta_in, c->cfg.u_conv);
-  recycle_apply_kernel<<<dim3((ny + 1 + 127) / 128, nz), 128, 0, c->launch>>>(
-      c->f.u, c->f.v, c->f.w, c->f.v_in, c->f.w_in, c->rcy, nx, ny, nz, ir, c->cfg.delta_in, c->cfg.u_conv);
-  return cudaGetLastError();
+  const int nx = c->cfg.nx, ny = c->cfg.ny, nz = c->cfg.nz;
+  const RcySrc src{c->f.u, c->f.v, c->f.w, nx, ny, c->cfg.recycle_i, nullptr, nullptr, nullptr, nullptr};
+  const RcyDst dst{c->f.u, c->f.v_in, c->f.w_in, nx, ny, 0};
+  return recycle_run(src, dst, c->rcy, ny, nz, c->cfg.delta_in, c->cfg.u_conv, c->launch);
+}
+
+cudaError_t launch_recycle_gathered(const double* g, const long* uoff, const long* woff, const long* voff, double* rcy,
+                                    int ny, int nz, double delta_in, double u_inf, double* u, double* v_in,
+                                    double* w_in, int nx, int rows, int jg0, cudaStream_t st) {
+  const RcySrc src{nullptr, nullptr, nullptr, nx, ny, 0, g, uoff, woff, voff};
+  const RcyDst dst{u, v_in, w_in, nx, rows, jg0};
+  return recycle_run(src, dst, rcy, ny, nz, delta_in, u_inf, st);
 }

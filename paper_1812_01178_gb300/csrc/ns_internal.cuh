@@ -514,6 +514,15 @@ inline int stepk_index(int k) { return k < 0 ? 3 : k; }
 cudaError_t launch_recycle(ns_ctx* c, int k);    // recycled inflow planes (sub-step 0, if enabled)
 size_t recycle_block_doubles(int ny);
 cudaError_t recycle_upload_grid(ns_ctx* c);
+// the grid part of a recycling block for faces yf[0..ny] (host; the rest zero)
+void recycle_grid_host(const double* yf, int ny, double* h);
+// Recycling from a gathered recycle plane (y slabs): g holds the whole domain's samples (row j of
+// u at g + uoff[j], of w at g + woff[j], face f of v at g + voff[f], nz each); rcy is a recycling
+// block of the whole grid (ny rows); the inflow rows written are the rows local rows of u (face 0
+// of each), v_in (rows + 1 faces) and w_in held here, local row 0 being row jg0 of the domain.
+cudaError_t launch_recycle_gathered(const double* g, const long* uoff, const long* woff, const long* voff, double* rcy,
+                                    int ny, int nz, double delta_in, double u_inf, double* u, double* v_in,
+                                    double* w_in, int nx, int rows, int jg0, cudaStream_t st);
 cudaError_t poisson_set_attributes();  // once per process and device, outside any capture
 
 // Sets the message ns_last_error(NULL) returns on this thread.

@@ -49,6 +49,10 @@ struct ns_slab {
   char* send[NS_XCH_COUNT] = {};
   char* recv[NS_XCH_COUNT] = {};
   size_t slot[NS_XCH_COUNT] = {};
+  // recycling inflow: a recycling block of the whole grid and, per row / face of the whole
+  // domain, where its samples sit in the gathered RCY buffer (u, w rows; v faces)
+  double* rcy = nullptr;
+  long* rcy_off = nullptr;  // uoff[ny], woff[ny], voff[ny + 1]
   void* ws = nullptr;
   bool own_ws = false;
   std::string err;
@@ -67,11 +71,18 @@ std::string check_slab(const ns_config* cfg, int p, int r) {
   if (p < 1 || p > 64) return "p must be in [1, 64]";
   if (r < 0 || r >= p) return "r must be in [0, p)";
   if (cfg->precision != NS_FP64) return "slabs are built for NS_FP64";
-  if (cfg->pressure_update != NS_PRESSURE_DELTA || cfg->recycle_i != 0)
-    return "slabs are built for the plain pressure update without recycling";
+  if (cfg->pressure_update != NS_PRESSURE_DELTA) return "slabs are built for the plain pressure update";
+  if (cfg->recycle_i != 0) {
+    if (cfg->bc_x != 1) return "recycling needs inflow / outflow in x (bc_x = 1)";
+    if (cfg->recycle_i < 1 || cfg->recycle_i >= cfg->nx) return "recycle_i must be in [1, nx - 1]";
+    if (!(cfg->delta_in > 0.0) || !std::isfinite(cfg->delta_in)) return "delta_in must be positive and finite";
+  }
   if (cfg->ny < 3 * p) return "every slab needs at least 3 rows (ny >= 3 p)";
   return "";
 }
+
+// most rows of any slab
+int rows_max(int ny, int p) { return (ny + p - 1) / p; }
 
 // the sub-grid of slab r: its rows plus one halo row on each side that has a neighbour
 void sub_config(const ns_config* g, int p, int r, std::vector<double>& yf, ns_config* out, int* hb, int* ha) {
@@ -84,11 +95,14 @@ void sub_config(const ns_config* g, int p, int r, std::vector<double>& yf, ns_co
   out->ny = (j1 - j0) + *hb + *ha;
   out->yf = yf.data();
   out->bc_ytop = r == p - 1 ? g->bc_ytop : 0;
+  out->recycle_i = 0;  // the slab recycles from the gathered plane of the whole domain
 }
 
-size_t slot_bytes(const ns_config* g, int xch) {
+size_t slot_bytes(const ns_config* g, int p, int xch) {
   const size_t plane = (size_t)g->nz * g->nx * 8, nzh = g->nz / 2 + 1;
   switch (xch) {
+    case NS_XCH_RCY:  // u and w samples of the slab's rows, v of its faces (rows_max + 1 slots)
+      return g->recycle_i ? al256((3 * (size_t)rows_max(g->ny, p) + 1) * g->nz * 8) : 0;
     case NS_XCH_HALO: return al256(2 * 4 * plane);
     case NS_XCH_ADIY: return al256(2 * 3 * plane);
     case NS_XCH_VSTAR: return al256(plane);
@@ -107,7 +121,8 @@ size_t extra_bytes(const ns_config* g, int p, int r) {
   size_t b = 0;
   b += 6 * al256((5 * (nyl + 1) + 2 * Q) * 8);                      // y-sweep tables
   b += 4 * al256(nzh * nyl * g->nx * 8) + al256(nzh * g->nx * 2 * Q * 8 + 8);  // Poisson tables
-  for (int x = 0; x < NS_XCH_COUNT; ++x) b += (1 + (size_t)p) * slot_bytes(g, x);
+  for (int x = 0; x < NS_XCH_COUNT; ++x) b += (1 + (size_t)p) * slot_bytes(g, p, x);
+  if (g->recycle_i) b += al256(recycle_block_doubles(g->ny) * 8) + al256((3 * (size_t)g->ny + 1) * 8);
   return b;
 }
 
@@ -506,6 +521,42 @@ cudaError_t copy_row_in(double* f, int rows, int jrow, int nx, int nz, const dou
                            cudaMemcpyDeviceToDevice, st);
 }
 
+// Recycle-plane samples of this slab's rows for the RCY all-gather: u on face ir of rows
+// j0 .. j1-1, w and v averaged over the centres ir-1 and ir (rows j0 .. j1-1; faces j0 .. j1-1,
+// and face ny on the last slab), written [row][k] into the send buffer and the slab's own slot.
+__global__ void slab_rcy_pack(const double* __restrict__ u, const double* __restrict__ v,
+                              const double* __restrict__ w, int nx, int nyv, int nz, int hb, int nyl, int nface,
+                              int ir, long rm, double* __restrict__ send, double* __restrict__ own) {
+  const long q = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int jl = (int)(q / nz), k = (int)(q - (long)jl * nz);
+  if (jl >= nface) return;
+  const long o = (long)jl * nz + k;
+  if (jl < nyl) {
+    const long c = ((long)k * nyv + hb + jl) * nx;
+    const double ur = u[c + ir], wr = 0.5 * (w[c + ir - 1] + w[c + ir]);
+    send[o] = ur;
+    own[o] = ur;
+    send[rm * nz + o] = wr;
+    own[rm * nz + o] = wr;
+  }
+  const long cv = ((long)k * (nyv + 1) + hb + jl) * nx;
+  const double vr = 0.5 * (v[cv + ir - 1] + v[cv + ir]);
+  send[2 * rm * nz + o] = vr;
+  own[2 * rm * nz + o] = vr;
+}
+
+cudaError_t pack_rcy(ns_slab* s) {
+  if (!s->gcfg.recycle_i) return cudaSuccess;
+  ns_ctx* c = s->c;
+  const int nz = c->cfg.nz, nface = s->nyl + (s->r == s->p - 1 ? 1 : 0);
+  const long n = (long)nface * nz;
+  slab_rcy_pack<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(
+      c->f.u, c->f.v, c->f.w, c->cfg.nx, s->nyv, nz, s->hb, s->nyl, nface, s->gcfg.recycle_i,
+      rows_max(s->gcfg.ny, s->p), (double*)s->send[NS_XCH_RCY],
+      (double*)(s->recv[NS_XCH_RCY] + (size_t)s->r * s->slot[NS_XCH_RCY]));
+  return cudaGetLastError();
+}
+
 // halo send buffer: part 0 (to slab r-1) = u, w, p of row j0 and v of face j0; part 1 (to slab
 // r+1) = u, w, p of row j1-1 and v of face j1-1
 cudaError_t pack_halo(ns_slab* s) {
@@ -721,8 +772,27 @@ ns_status build_slab_tables(ns_slab* s, char* base) {
       cudaError_t e = cudaMemcpy(q.first, q.second->data(), q.second->size() * 8, cudaMemcpyHostToDevice);
       if (e != cudaSuccess) return cuda_fail(s, "slab Poisson tables", e);
     }
+  if (g->recycle_i) {  // recycling block of the whole grid, sample offsets in the gathered buffer
+    std::vector<double> hr(recycle_block_doubles(ny));
+    recycle_grid_host(s->gyf.data(), ny, hr.data());
+    s->rcy = (double*)take(hr.size() * 8);
+    const long sd = (long)(slot_bytes(g, p, NS_XCH_RCY) / 8), rm = rows_max(ny, p);
+    std::vector<long> off(3 * (size_t)ny + 1);
+    for (int q = 0; q < p; ++q) {
+      for (int j = clo[q]; j < chi[q]; ++j) {
+        off[j] = q * sd + (long)(j - clo[q]) * nz;               // u
+        off[ny + j] = q * sd + (rm + j - clo[q]) * (long)nz;     // w
+        off[2 * ny + j] = q * sd + (2 * rm + j - clo[q]) * (long)nz;  // v, face j
+      }
+    }
+    off[3 * ny] = (p - 1) * sd + (2 * rm + ny - clo[p - 1]) * (long)nz;  // v, the top face
+    s->rcy_off = (long*)take(off.size() * 8);
+    cudaError_t e = cudaMemcpy(s->rcy, hr.data(), hr.size() * 8, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(s->rcy_off, off.data(), off.size() * 8, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(s, "slab recycling tables", e);
+  }
   for (int x = 0; x < NS_XCH_COUNT; ++x) {
-    s->slot[x] = slot_bytes(g, x);
+    s->slot[x] = slot_bytes(g, p, x);
     s->send[x] = take(s->slot[x]);
     s->recv[x] = take((size_t)p * s->slot[x]);
     cudaError_t e = cudaMemset(s->recv[x], 0, (size_t)p * s->slot[x]);
@@ -743,7 +813,7 @@ ns_status ns_slab_rows(int ny, int p, int r, int* j0, int* j1) {
 
 size_t ns_slab_slot_bytes(const ns_config* cfg, int p, int xch) {
   if (!check_slab(cfg, p, 0).empty() || xch < 0 || xch >= NS_XCH_COUNT) return 0;
-  return slot_bytes(cfg, xch);
+  return slot_bytes(cfg, p, xch);
 }
 
 ns_status ns_slab_slots(int p, int r, int xch, int ymode, int* lo, int* hi) {
@@ -760,6 +830,7 @@ ns_status ns_slab_slots(int p, int r, int xch, int ymode, int* lo, int* hi) {
     case NS_XCH_POIS: *lo = 0, *hi = p - 1; break;
     case NS_XCH_PHI: *lo = below, *hi = r; break;
     case NS_XCH_FLUX: *lo = 0, *hi = p - 1; break;
+    case NS_XCH_RCY: *lo = 0, *hi = p - 1; break;
     default: return NS_ERR_ARG;
   }
   return NS_OK;
@@ -882,10 +953,18 @@ ns_status ns_slab_phase(ns_slab* s, int phase, int k) {
   cudaError_t e = cudaSuccess;
   switch (phase) {
     case NS_SLAB_PACK:
-      e = pack_halo(s);
+      if ((e = pack_halo(s)) != cudaSuccess) break;
+      e = pack_rcy(s);
       break;
     case NS_SLAB_RHS:
       if ((e = unpack_halo(s)) != cudaSuccess) break;
+      if (k == 0 && s->gcfg.recycle_i) {  // inflow planes of every row held here, from the whole plane
+        const int ny = s->gcfg.ny;
+        e = launch_recycle_gathered((const double*)s->recv[NS_XCH_RCY], s->rcy_off, s->rcy_off + ny,
+                                    s->rcy_off + 2 * ny, s->rcy, ny, nz, s->gcfg.delta_in, s->gcfg.u_conv, c->f.u,
+                                    c->f.v_in, c->f.w_in, nx, s->nyv, s->j0 - s->hb, c->stream);
+        if (e != cudaSuccess) break;
+      }
       if ((e = launch_rhs(c, k)) != cudaSuccess) break;
       if ((e = launch_outflow(c, k)) != cudaSuccess) break;  // inflow / outflow only
       if ((e = launch_adi_x(c, k)) != cudaSuccess) break;
@@ -939,7 +1018,8 @@ ns_status ns_slab_phase(ns_slab* s, int phase, int k) {
                            c->stream)) != cudaSuccess)
         break;
       if ((e = launch_project(c, k)) != cudaSuccess) break;
-      e = pack_halo(s);
+      if ((e = pack_halo(s)) != cudaSuccess) break;
+      if (k == 2) e = pack_rcy(s);  // the recycle plane the next step's sub-step 0 reads
       break;
     default:
       return slab_fail(s, NS_ERR_ARG, "unknown phase");

@@ -20,10 +20,11 @@ import numpy as np
 
 from . import binding as B
 
-NS_XCH_HALO, NS_XCH_ADIY, NS_XCH_VSTAR, NS_XCH_POIS, NS_XCH_PHI, NS_XCH_FLUX, NS_XCH_COUNT = range(7)
+NS_XCH_HALO, NS_XCH_ADIY, NS_XCH_VSTAR, NS_XCH_POIS, NS_XCH_PHI, NS_XCH_FLUX, NS_XCH_RCY, NS_XCH_COUNT = range(8)
 NS_SLAB_PACK, NS_SLAB_RHS, NS_SLAB_ADIZ, NS_SLAB_POIS, NS_SLAB_PHI, NS_SLAB_PROJECT = range(6)
 
-# one RK3 sub-step: each phase, then the exchanges that move what it wrote
+# one RK3 sub-step: each phase, then the exchanges that move what it wrote (with the recycling
+# inflow, the PACK phase and the PROJECT phase of sub-step 2 are also followed by RCY)
 SUBSTEP = ((NS_SLAB_RHS, (NS_XCH_ADIY,)), (NS_SLAB_ADIZ, (NS_XCH_VSTAR, NS_XCH_FLUX)),
            (NS_SLAB_POIS, (NS_XCH_POIS,)), (NS_SLAB_PHI, (NS_XCH_PHI,)), (NS_SLAB_PROJECT, (NS_XCH_HALO,)))
 
@@ -64,11 +65,15 @@ def solve_line_host(a, b, c, d, p, mode):
 def run_steps(slabs, exchange, nsteps, first=True):
     """nsteps time steps (three sub-steps each) of the slabs in `slabs` (all p slabs on one device,
     or this rank's one slab), exchanging with exchange(xch) after every phase.  first=True packs and
-    exchanges the halo rows before the first sub-step (the fields were just filled)."""
+    exchanges the halo rows (and the recycle plane) before the first sub-step (the fields were just
+    filled)."""
+    rcy = bool(getattr(getattr(slabs[0], "case", None), "recycle_i", 0))
     if first:
         for s in slabs:
             s.phase(NS_SLAB_PACK, 0)
         exchange(NS_XCH_HALO)
+        if rcy:
+            exchange(NS_XCH_RCY)
     for _ in range(nsteps):
         for k in range(3):
             for ph, xchs in SUBSTEP:
@@ -76,6 +81,8 @@ def run_steps(slabs, exchange, nsteps, first=True):
                     s.phase(ph, k)
                 for xch in xchs:
                     exchange(xch)
+            if rcy and k == 2:
+                exchange(NS_XCH_RCY)
 
 
 class Slab:

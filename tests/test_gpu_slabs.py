@@ -154,6 +154,42 @@ def test_slabs_boundary_layer_match_the_oracle(P):
     assert np.abs(O.divergence_bl(g, *got[:3], ref["bl"])).max() < 1e-10
 
 
+@pytest.mark.parametrize("P", [2, 3, 4])
+def test_slabs_recycled_boundary_layer_match_the_oracle(P):
+    """The paper's production configuration: the flat plate with the recycling inflow, in slabs.
+    Every slab packs the recycle-plane samples of its rows, an all-gather (RCY) gives each the whole
+    plane, and in sub-step 0 each writes the inflow rows it holds (halo rows included) from the
+    whole plane.  Against the oracle's recycled steps and the single-context recycled path."""
+    case, u, v, w, p, bl = I.boundary_layer(64, 24, 16, amp=0.05, seed=5, re=300.0)
+    case.recycle_i, case.delta_in = 40, 1.1
+    g = O.Grid.from_case(case)
+    u, v, w, bl = O.make_divergence_free_bl(g, u, v, w, bl)
+    slabs = [S.Slab(case, P, r, u, v, w, p, bl=bl) for r in range(P)]
+    S.run_steps(slabs, S.LocalExchange(slabs), 3)
+    parts = [s.owned() for s in slabs]
+    planes = [s.owned_planes() for s in slabs]
+    for s in slabs:
+        s.close()
+    got = tuple(np.concatenate([q[f] for q in parts], axis=1) for f in range(4))
+    ref = O.step_bl_recycled(g, dict(u=u, v=v, w=w, p=p, bl=bl), case.dt, case.re, case.fx, case.recycle_i,
+                             case.delta_in, nsteps=3, u_conv=case.u_conv)
+    errs = field_rel_errors(got, (ref["u"], ref["v"], ref["w"], ref["p"]))
+    for name in ("u", "v", "w", "p"):
+        assert errs[name] < 1e-11, (name, errs)
+    for q in ("v_in", "w_in", "u_out", "v_out", "w_out"):
+        plane = np.concatenate([pl[q] for pl in planes], axis=1)
+        np.testing.assert_allclose(plane, ref["bl"][q], rtol=0, atol=1e-11 * (np.abs(ref["bl"][q]).max() + 1e-300))
+    one = B.Solver(case, u, v, w, p, bl=bl)
+    one.step(3)
+    errs = field_rel_errors(got, one.state())
+    inflow = one.state()[0][:, :, 0]
+    one.close()
+    for name in ("u", "v", "w", "p"):
+        assert errs[name] < 1e-12, (name, errs)
+    assert not np.allclose(inflow, u[:, :, 0])  # the inflow did change
+    assert np.abs(O.divergence_bl(g, *got[:3], ref["bl"])).max() < 1e-10
+
+
 def test_slab_arguments_rejected_on_the_host():
     case, g, u, v, w, p = _projected((32, 24, 16), 1)
     with pytest.raises(B.NSError):

@@ -41,6 +41,7 @@ def test_slots_each_slab_reads():
         assert S.slots(p, r, S.NS_XCH_POIS, B.NS_PART_PDD) == (0, p - 1)
         assert S.slots(p, r, S.NS_XCH_PHI, B.NS_PART_PDD) == (below, r)
         assert S.slots(p, r, S.NS_XCH_FLUX, B.NS_PART_PDD) == (0, p - 1)
+        assert S.slots(p, r, S.NS_XCH_RCY, B.NS_PART_PDD) == (0, p - 1)
 
 
 def test_rows_and_slot_sizes():
@@ -56,35 +57,49 @@ def test_rows_and_slot_sizes():
     assert S.slot_bytes(cfg, 4, S.NS_XCH_VSTAR) == plane
     assert S.slot_bytes(cfg, 4, S.NS_XCH_PHI) == plane
     assert S.slot_bytes(cfg, 4, S.NS_XCH_POIS) == 2 * 17 * 64 * 16   # complex ends per (kx, kz)
+    assert S.slot_bytes(cfg, 4, S.NS_XCH_RCY) == 0  # no recycling: nothing to gather
     assert B.lib().ns_slab_workspace_bytes(B.make_config(case), 13, 0) == 0  # fewer than 3 rows a slab
+    # with the recycling inflow: u and w samples of up to ceil(ny / p) rows, v of one face more
+    case, *_ = I.boundary_layer(64, 37, 32, amp=0.0)
+    case.recycle_i, case.delta_in = 40, 1.0
+    cfg = B.make_config(case)
+    assert S.slot_bytes(cfg, 4, S.NS_XCH_RCY) == -(-(3 * 10 + 1) * 32 * 8 // 256) * 256
+    case.recycle_i = 64  # outside [1, nx - 1]
+    assert S.slot_bytes(B.make_config(case), 4, S.NS_XCH_RCY) == 0
 
 
 class _FakeSlab:
     """Stands in for a slab on the host: a phase writes a tag (slab, exchange, sub-step) into the
     send buffer of the exchange that follows it and records itself."""
 
-    def __init__(self, r, send, log):
-        self.r, self.send, self.log = r, send, log
+    def __init__(self, r, send, log, case):
+        self.r, self.send, self.log, self.case = r, send, log, case
         self.next = {ph: xs for ph, xs in S.SUBSTEP}
-        self.next[S.NS_SLAB_PACK] = (S.NS_XCH_HALO,)
+        self.next[S.NS_SLAB_PACK] = (S.NS_XCH_HALO, S.NS_XCH_RCY)
 
     def phase(self, ph, k):
         self.log.append((ph, k))
-        for x in self.next[ph]:
+        xs = self.next[ph] + ((S.NS_XCH_RCY,) if ph == S.NS_SLAB_PROJECT and k == 2 else ())
+        for x in xs:
             self.send[x].copy_(torch.full_like(self.send[x], (self.r * 16 + x * 3 + k) % 256))
 
 
-def _worker(rank, world, port, ymode):
+def _worker(rank, world, port, ymode, recycle=False):
     sys.path.insert(0, ROOT)
     dist.init_process_group("gloo", init_method="tcp://127.0.0.1:%d" % port, rank=rank, world_size=world)
     try:
-        case, *_ = I.small_channel(16, 3 * world + 2, 8)
+        if recycle:  # the recycling inflow adds the RCY all-gather after PACK and after sub-step 2
+            case, *_ = I.boundary_layer(16, 3 * world + 2, 8, amp=0.0)
+            case.recycle_i, case.delta_in = 5, 1.0
+        else:
+            case, *_ = I.small_channel(16, 3 * world + 2, 8)
         cfg = B.make_config(case)
         sizes = [S.slot_bytes(cfg, world, x) for x in range(S.NS_XCH_COUNT)]
+        assert (sizes[S.NS_XCH_RCY] > 0) == recycle
         send = [torch.zeros(n, dtype=torch.uint8) for n in sizes]
         recv = [torch.full((world, n), 255, dtype=torch.uint8) for n in sizes]
         log = []
-        slab = _FakeSlab(rank, send, log)
+        slab = _FakeSlab(rank, send, log, case)
         ex = S.DistExchange(dist, world, rank, ymode, send, recv)
         seen = []
 
@@ -98,9 +113,11 @@ def _worker(rank, world, port, ymode):
             seen.append(x)
 
         S.run_steps([slab], exchange, 1)
-        # PACK, HALO, then per sub-step RHS/ADIY, ADIZ/VSTAR, POIS/POIS, PHI/PHI, PROJECT/HALO
+        # PACK, HALO (RCY), then per sub-step RHS/ADIY, ADIZ/VSTAR, POIS/POIS, PHI/PHI, PROJECT/HALO
+        # (and RCY after sub-step 2)
+        rc = [S.NS_XCH_RCY] if recycle else []
         assert [ph for ph, _ in log] == [S.NS_SLAB_PACK] + [ph for _ in range(3) for ph, _ in S.SUBSTEP]
-        assert seen == [S.NS_XCH_HALO] + [x for _ in range(3) for _, xs in S.SUBSTEP for x in xs]
+        assert seen == [S.NS_XCH_HALO] + rc + [x for k in range(3) for _, xs in S.SUBSTEP for x in xs] + rc
     finally:
         dist.destroy_process_group()
 
@@ -111,9 +128,11 @@ def _free_port():
         return s.getsockname()[1]
 
 
-@pytest.mark.parametrize("world,ymode", [(2, B.NS_PART_PDD), (3, B.NS_PART_PDD), (3, B.NS_PART_PPT)])
-def test_gloo_ranks_exchange_what_each_slab_reads(world, ymode):
-    mp.start_processes(_worker, args=(world, _free_port(), ymode), nprocs=world, join=True, start_method="spawn")
+@pytest.mark.parametrize("world,ymode,recycle", [(2, B.NS_PART_PDD, False), (3, B.NS_PART_PDD, False),
+                                                 (3, B.NS_PART_PPT, False), (3, B.NS_PART_PDD, True)])
+def test_gloo_ranks_exchange_what_each_slab_reads(world, ymode, recycle):
+    mp.start_processes(_worker, args=(world, _free_port(), ymode, recycle), nprocs=world, join=True,
+                       start_method="spawn")
 
 
 def _rows(n, rng, strength):
