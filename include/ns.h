@@ -205,6 +205,10 @@ ns_status ns_convective_rate(ns_ctx* ctx, double* rate);
 ns_status ns_set_dt(ns_ctx* ctx, double dt);
 ns_status ns_step_cfl(ns_ctx* ctx, int nsteps, double cfl, double* dts);
 
+/* Number of kernel launches in one ns_step time step: the kernel nodes of the step's graph (it is
+ * captured here if ns_step has not run yet).  -1 on error (ns_last_error). */
+int ns_launches_per_step(ns_ctx* ctx);
+
 /* ns_step with per-kernel timing: replays a captured step that also records a CUDA event before
  * every kernel (and after the last) on the context's stream, waits for each step, and adds each
  * kernel's event-to-event time (ms) into kernel_ms[ns_kernel_name index], summed over the three
@@ -325,10 +329,6 @@ ns_status ns_batch_init(ns_batch** out, const ns_config* cfgs, const ns_fields* 
 
 /* nsteps time steps of every instance (graph captured on first use and replayed). */
 ns_status ns_batch_step(ns_batch* b, int nsteps);
-
-/* Number of kernel launches in one ns_step time step: the kernel nodes of the step's graph (it is
- * captured here if ns_step has not run yet).  -1 on error (ns_last_error). */
-int ns_launches_per_step(ns_ctx* ctx);
 
 /* Number of kernel launches in one batched time step (3 sub-steps x stages x kernel variants). */
 int ns_batch_launches_per_step(ns_batch* b);
