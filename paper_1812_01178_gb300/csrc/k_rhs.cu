@@ -339,17 +339,39 @@ struct RhsTiledK {
     }
   };
   // y-face fluxes on face jf (Fuv, Fvw), zero on the walls
+  // Each product loop gives every thread the item q = tid first (every loop has at least 256
+  // items).  In the FP32 form that item's tile offsets are worked out once, before the march in y,
+  // and only the few items q >= 256 take the general index arithmetic: the FP32 RHS is
+  // issue-bound.  (The FP64 form keeps the general loops: the offsets cost it registers.)
+  constexpr bool kHoist = sizeof(T) == 4;
+  const int hk = tid / (RT_X + 1), hi = tid % (RT_X + 1);   // items of the (RT_X + 1)-wide loops
+  const int gk = tid / RT_X, gi = tid % RT_X;               // items of the RT_X-wide loops
+  const int eA = (hk + 1) * RT_PX + hi + 1, fA = hk * (RT_X + 1) + hi;
+  const int eB = (gk + 1) * RT_PX + gi + 1, fB = gk * RT_X + gi;
+  auto PL = [&](int f, int j) -> T* { return S.pl[f][j & 3]; };
+  // y-face fluxes on face jf (Fuv, Fvw), zero on the walls
   auto face_fluxes = [&](int jf) {
     const bool inner = jf >= 1 && jf <= ny - 1;
     const T wl = inner ? C(GC_WLO, jf) : (T)0, wh = inner ? C(GC_WHI, jf) : (T)0;
-    for (int q = tid; q < RT_Z * (RT_X + 1); q += RT_X * RT_Z) {
+    int q0 = tid;
+    if constexpr (kHoist) {
+      const T* u0 = PL(0, jf - 1);
+      const T* u1 = PL(0, jf);
+      const T* v1 = PL(1, jf);
+      const T* w0 = PL(2, jf - 1);
+      const T* w1 = PL(2, jf);
+      (&S.fuv[jf & 1][0][0])[fA] = inner ? (wl * u0[eA] + wh * u1[eA]) * (v1[eA - 1] + v1[eA]) : (T)0;
+      (&S.fvw[jf & 1][0][0])[fB] = inner ? (v1[eB - RT_PX] + v1[eB]) * (wl * w0[eB] + wh * w1[eB]) : (T)0;
+      q0 = tid + RT_X * RT_Z;
+    }
+    for (int q = q0; q < RT_Z * (RT_X + 1); q += RT_X * RT_Z) {
       const int kk = q / (RT_X + 1), ii = q % (RT_X + 1);
       T f = 0;
       if (inner)
         f = (wl * P(0, jf - 1, kk, ii) + wh * P(0, jf, kk, ii)) * (P(1, jf, kk, ii - 1) + P(1, jf, kk, ii));
       S.fuv[jf & 1][kk][ii] = f;
     }
-    for (int q = tid; q < (RT_Z + 1) * RT_X; q += RT_X * RT_Z) {
+    for (int q = q0; q < (RT_Z + 1) * RT_X; q += RT_X * RT_Z) {
       const int kk = q / RT_X, ii = q % RT_X;
       T f = 0;
       if (inner)
@@ -359,17 +381,28 @@ struct RhsTiledK {
   };
   // centre-plane products of plane j (Q1, Q3, Fuw)
   auto centre_products = [&](int j) {
-    for (int q = tid; q < RT_Z * (RT_X + 1); q += RT_X * RT_Z) {
+    int q0 = tid;
+    if constexpr (kHoist) {
+      const T* u = PL(0, j);
+      const T* w = PL(2, j);
+      const T s1 = u[eA - 1] + u[eA];  // Q1 item: x = i0 - 1 + hi, z row hk
+      (&S.q1[0][0])[fA] = s1 * s1;
+      const T s3 = w[eB - RT_PX] + w[eB];  // Q3 item: z = k0 - 1 + gk
+      (&S.q3[0][0])[fB] = s3 * s3;
+      (&S.fuw[0][0])[fA] = (u[eA - RT_PX] + u[eA]) * (w[eA - 1] + w[eA]);
+      q0 = tid + RT_X * RT_Z;
+    }
+    for (int q = q0; q < RT_Z * (RT_X + 1); q += RT_X * RT_Z) {
       const int kk = q / (RT_X + 1), ii = q % (RT_X + 1) - 1;
       const T s = P(0, j, kk, ii) + P(0, j, kk, ii + 1);
       S.q1[kk][ii + 1] = s * s;
     }
-    for (int q = tid; q < (RT_Z + 1) * RT_X; q += RT_X * RT_Z) {
+    for (int q = q0; q < (RT_Z + 1) * RT_X; q += RT_X * RT_Z) {
       const int kk = q / RT_X - 1, ii = q % RT_X;
       const T s = P(2, j, kk, ii) + P(2, j, kk + 1, ii);
       S.q3[kk + 1][ii] = s * s;
     }
-    for (int q = tid; q < (RT_Z + 1) * (RT_X + 1); q += RT_X * RT_Z) {
+    for (int q = q0; q < (RT_Z + 1) * (RT_X + 1); q += RT_X * RT_Z) {
       const int kk = q / (RT_X + 1), ii = q % (RT_X + 1);
       S.fuw[kk][ii] = (P(0, j, kk - 1, ii) + P(0, j, kk, ii)) * (P(2, j, kk, ii - 1) + P(2, j, kk, ii));
     }
