@@ -361,8 +361,9 @@ void ns_batch_destroy(ns_batch* b);
  * exchange, an all-gather of one double); with the recycling inflow (recycle_i != 0) every slab
  * packs the recycle-plane samples of its rows (RCY exchange, an all-gather) and, in sub-step 0,
  * writes the inflow rows it holds from the whole plane (Sec. 2.1; the recycling of one context).
- * Built for NS_FP64 and the plain pressure update (other configurations: NS_ERR_ARG); every slab
- * needs at least 3 rows (ny >= 3 p).
+ * Built for NS_FP64 (with either pressure update; the PHI exchange carries phi of each slab's end
+ * rows both ways, for the gradient and for the Kim-Moin Laplacian); other precisions give
+ * NS_ERR_ARG; every slab needs at least 3 rows (ny >= 3 p).
  *
  * Local fields.  A slab's u, w, p hold rows j0-hb .. j1+ha-1 and its v the faces j0-hb .. j1+ha,
  * where hb = (r > 0) and ha = (r < p-1) are the halo rows below and above (layouts as above with

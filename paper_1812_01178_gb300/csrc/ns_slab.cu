@@ -71,7 +71,6 @@ std::string check_slab(const ns_config* cfg, int p, int r) {
   if (p < 1 || p > 64) return "p must be in [1, 64]";
   if (r < 0 || r >= p) return "r must be in [0, p)";
   if (cfg->precision != NS_FP64) return "slabs are built for NS_FP64";
-  if (cfg->pressure_update != NS_PRESSURE_DELTA) return "slabs are built for the plain pressure update";
   if (cfg->recycle_i != 0) {
     if (cfg->bc_x != 1) return "recycling needs inflow / outflow in x (bc_x = 1)";
     if (cfg->recycle_i < 1 || cfg->recycle_i >= cfg->nx) return "recycle_i must be in [1, nx - 1]";
@@ -107,7 +106,7 @@ size_t slot_bytes(const ns_config* g, int p, int xch) {
     case NS_XCH_ADIY: return al256(2 * 3 * plane);
     case NS_XCH_VSTAR: return al256(plane);
     case NS_XCH_POIS: return al256(2 * nzh * g->nx * 16);
-    case NS_XCH_PHI: return al256(plane);
+    case NS_XCH_PHI: return al256(2 * plane);  // part 0: row j0 (to slab r-1), part 1: row j1-1 (to r+1)
     case NS_XCH_FLUX: return 256;  // one double: this slab's share of Q_in - Q_out
     default: return 0;
   }
@@ -828,7 +827,7 @@ ns_status ns_slab_slots(int p, int r, int xch, int ymode, int* lo, int* hi) {
       break;
     case NS_XCH_VSTAR: *lo = r, *hi = above; break;
     case NS_XCH_POIS: *lo = 0, *hi = p - 1; break;
-    case NS_XCH_PHI: *lo = below, *hi = r; break;
+    case NS_XCH_PHI: *lo = below, *hi = above; break;
     case NS_XCH_FLUX: *lo = 0, *hi = p - 1; break;
     case NS_XCH_RCY: *lo = 0, *hi = p - 1; break;
     default: return NS_ERR_ARG;
@@ -1008,19 +1007,29 @@ ns_status ns_slab_phase(ns_slab* s, int phase, int k) {
       if ((e = cudaGetLastError()) != cudaSuccess) break;
       if ((e = launch_pois_fftx_inv(c, k)) != cudaSuccess) break;
       if ((e = launch_pois_ifftz(c, k)) != cudaSuccess) break;
-      if (s->r < s->p - 1)  // phi of row j1-1, which slab r+1 reads for the gradient at its face j1
-        e = copy_row_out(c->phi, s->nyv, s->hb + s->nyl - 1, nx, nz, (double*)s->send[NS_XCH_PHI], c->stream);
+      // phi of row j1-1, which slab r+1 reads for the gradient at its face j1, and of row j0, which
+      // slab r-1 reads for the Laplacian of phi at its row j0-1 (the Kim-Moin pressure update)
+      if (s->r < s->p - 1 &&
+          (e = copy_row_out(c->phi, s->nyv, s->hb + s->nyl - 1, nx, nz,
+                            (double*)s->send[NS_XCH_PHI] + (size_t)nz * nx, c->stream)) != cudaSuccess)
+        break;
+      if (s->r > 0) e = copy_row_out(c->phi, s->nyv, s->hb, nx, nz, (double*)s->send[NS_XCH_PHI], c->stream);
       break;
-    case NS_SLAB_PROJECT:
-      if (s->r > 0 &&
-          (e = copy_row_in(c->phi, s->nyv, 0, nx, nz,
-                           (const double*)(s->recv[NS_XCH_PHI] + (size_t)(s->r - 1) * s->slot[NS_XCH_PHI]),
-                           c->stream)) != cudaSuccess)
+    case NS_SLAB_PROJECT: {
+      const size_t sl = s->slot[NS_XCH_PHI] / 8, plane = (size_t)nz * nx;
+      const double* rb = (const double*)s->recv[NS_XCH_PHI];
+      if (s->r > 0 &&  // halo row below: slab r-1's row j0-1
+          (e = copy_row_in(c->phi, s->nyv, 0, nx, nz, rb + (size_t)(s->r - 1) * sl + plane, c->stream)) != cudaSuccess)
+        break;
+      if (s->r < s->p - 1 &&  // halo row above: slab r+1's row j1
+          (e = copy_row_in(c->phi, s->nyv, s->hb + s->nyl, nx, nz, rb + (size_t)(s->r + 1) * sl, c->stream)) !=
+              cudaSuccess)
         break;
       if ((e = launch_project(c, k)) != cudaSuccess) break;
       if ((e = pack_halo(s)) != cudaSuccess) break;
       if (k == 2) e = pack_rcy(s);  // the recycle plane the next step's sub-step 0 reads
       break;
+    }
     default:
       return slab_fail(s, NS_ERR_ARG, "unknown phase");
   }

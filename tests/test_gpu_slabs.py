@@ -190,6 +190,21 @@ def test_slabs_recycled_boundary_layer_match_the_oracle(P):
     assert np.abs(O.divergence_bl(g, *got[:3], ref["bl"])).max() < 1e-10
 
 
+@pytest.mark.parametrize("P", [2, 3])
+def test_slabs_kim_moin_pressure_update(P):
+    """The Kim-Moin pressure update p += phi - beta_k lap(phi) in slabs: the Laplacian of phi at a
+    slab's end rows reads the neighbours' phi rows, which the PHI exchange carries both ways."""
+    case, g, u, v, w, p = _projected((32, 24, 16), 3, amp=0.2, re=40.0)
+    case.pressure_update = B.NS_PRESSURE_KIM_MOIN
+    got, _ = _run_slabs(case, u, v, w, p, P, 2)
+    ref = O.step(g, dict(u=u, v=v, w=w, p=p), case.dt, case.re, case.fx, 2, pressure="kim_moin")
+    errs = field_rel_errors(got, (ref["u"], ref["v"], ref["w"], ref["p"]))
+    for name in ("u", "v", "w", "p"):
+        assert errs[name] < 1e-11, (name, errs)
+    plain = O.step(g, dict(u=u, v=v, w=w, p=p), case.dt, case.re, case.fx, 2)
+    assert field_rel_errors(got, (plain["u"], plain["v"], plain["w"], plain["p"]))["p"] > 1e-6  # the forms differ
+
+
 def test_slab_arguments_rejected_on_the_host():
     case, g, u, v, w, p = _projected((32, 24, 16), 1)
     with pytest.raises(B.NSError):

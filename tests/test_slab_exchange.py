@@ -39,7 +39,7 @@ def test_slots_each_slab_reads():
         assert S.slots(p, r, S.NS_XCH_ADIY, B.NS_PART_PPT) == (0, p - 1)
         assert S.slots(p, r, S.NS_XCH_VSTAR, B.NS_PART_PDD) == (r, above)
         assert S.slots(p, r, S.NS_XCH_POIS, B.NS_PART_PDD) == (0, p - 1)
-        assert S.slots(p, r, S.NS_XCH_PHI, B.NS_PART_PDD) == (below, r)
+        assert S.slots(p, r, S.NS_XCH_PHI, B.NS_PART_PDD) == (below, above)
         assert S.slots(p, r, S.NS_XCH_FLUX, B.NS_PART_PDD) == (0, p - 1)
         assert S.slots(p, r, S.NS_XCH_RCY, B.NS_PART_PDD) == (0, p - 1)
 
@@ -55,7 +55,7 @@ def test_rows_and_slot_sizes():
     assert S.slot_bytes(cfg, 4, S.NS_XCH_HALO) == 8 * plane      # u, w, p, v rows, both sides
     assert S.slot_bytes(cfg, 4, S.NS_XCH_ADIY) == 6 * plane      # x~_1, x~_m of u, v, w
     assert S.slot_bytes(cfg, 4, S.NS_XCH_VSTAR) == plane
-    assert S.slot_bytes(cfg, 4, S.NS_XCH_PHI) == plane
+    assert S.slot_bytes(cfg, 4, S.NS_XCH_PHI) == 2 * plane     # phi of both end rows
     assert S.slot_bytes(cfg, 4, S.NS_XCH_POIS) == 2 * 17 * 64 * 16   # complex ends per (kx, kz)
     assert S.slot_bytes(cfg, 4, S.NS_XCH_RCY) == 0  # no recycling: nothing to gather
     assert B.lib().ns_slab_workspace_bytes(B.make_config(case), 13, 0) == 0  # fewer than 3 rows a slab
