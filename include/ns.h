@@ -237,7 +237,7 @@ ns_status ns_make_divergence_free(ns_ctx* ctx);
 
 /* Partitioning of the x-line solver (Sec. 3.2): P partitions of M = nx/P rows per line, P a
  * power of two from 1 to 32, M in {1, 2, 3, 4, 6, 8, 9, 12, 16} (rows held in registers) or, at
- * P = 32, M in {24, 32, 48, 64} (long lines staged in shared memory); other P give NS_ERR_ARG.
+ * P = 32, M in {24, 32, 48, 64, 96, 128} (long lines staged in shared memory); other P give NS_ERR_ARG.
  * mode 0 = automatic (PDD when the coupling PDD drops is below its tolerance for every sub-step,
  * else PPT), 1 = PPT, 2 = PDD.  Rebuilds the tables and drops the captured graph.  The default P
  * is the largest admissible one with at least 8 rows per partition.

@@ -203,7 +203,7 @@ struct AdiXK {
 };
 
 // ----------------------------------------------------------------------------------------------
-// x, long lines (M = 32 or 64 rows per partition, P = 32): the same algebra with each warp's line
+// x, long lines (M = 24 ... 128 rows per partition, P = 32): the same algebra with each warp's line
 // staged in shared memory at stride M+1 per partition (conflict-free for 8-byte elements), the
 // per-partition tables read through L1.  One warp per line, four warps per block.
 // ----------------------------------------------------------------------------------------------
@@ -716,6 +716,8 @@ cudaError_t launch_x_m(LaunchSink& s, int k) {
     case 32: return launch_x_long_t<T, 32>(s, k);
     case 48: return launch_x_long_t<T, 48>(s, k);
     case 64: return launch_x_long_t<T, 64>(s, k);
+    case 96: return launch_x_long_t<T, 96>(s, k);
+    case 128: return launch_x_long_t<T, 128>(s, k);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -819,9 +821,11 @@ cudaError_t x_attributes() {
     return e;
   if ((e = set_smem_limit<AdiXLongK<T, 24>>(4 * 32 * 25 * (int)sizeof(T))) != cudaSuccess ||
       (e = set_smem_limit<AdiXLongK<T, 32>>(4 * 32 * 33 * (int)sizeof(T))) != cudaSuccess ||
-      (e = set_smem_limit<AdiXLongK<T, 48>>(4 * 32 * 49 * (int)sizeof(T))) != cudaSuccess)
+      (e = set_smem_limit<AdiXLongK<T, 48>>(4 * 32 * 49 * (int)sizeof(T))) != cudaSuccess ||
+      (e = set_smem_limit<AdiXLongK<T, 64>>(4 * 32 * 65 * (int)sizeof(T))) != cudaSuccess ||
+      (e = set_smem_limit<AdiXLongK<T, 96>>(4 * 32 * 97 * (int)sizeof(T))) != cudaSuccess)
     return e;
-  return set_smem_limit<AdiXLongK<T, 64>>(4 * 32 * 65 * (int)sizeof(T));
+  return set_smem_limit<AdiXLongK<T, 128>>(4 * 32 * 129 * (int)sizeof(T));
 }
 
 template <int P, int M>

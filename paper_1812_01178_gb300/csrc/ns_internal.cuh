@@ -67,12 +67,12 @@ inline void fft_twiddles(int N, double* out) {
 
 // Partition shapes the x solver is built for: P lanes (a power of two <= 32) of M rows, with
 // M <= 16 from {1, 2, 3, 4, 6, 8, 9, 12, 16} (rows in registers) or, at P = 32, the long-line
-// shapes M in {24, 32, 48, 64} (lines staged in shared memory).
+// shapes M in {24, 32, 48, 64, 96, 128} (lines staged in shared memory; nx up to 4096).
 inline bool x_partition_ok(int P, int M) {
   if (P < 1 || P > 32 || (P & (P - 1)) != 0) return false;
   switch (M) {
     case 1: case 2: case 3: case 4: case 6: case 8: case 9: case 12: case 16: return true;
-    case 24: case 32: case 48: case 64: return P == 32;
+    case 24: case 32: case 48: case 64: case 96: case 128: return P == 32;
     default: return false;
   }
 }

@@ -60,6 +60,53 @@ def test_smallest_grid_steps_parity(precision, bound):
     s.close()
 
 
+@pytest.mark.parametrize("shape", [(4096, 4, 8), (3072, 4, 8), (8, 1024, 8), (8, 4, 4096), (8, 4, 3072)])
+@pytest.mark.parametrize("precision,bound,pbound", [(0, 1e-11, 1e-11), (1, 1e-6, 3e-5)])
+def test_largest_extents_steps_parity(shape, precision, bound, pbound):
+    """Each extent at the largest size the library takes, the other two at their smallest: nx
+    4096 and 3072 (the x lines as 32 partitions of 128 and 96 rows staged in shared memory, x
+    transforms of one row per block), ny 1024 (the y lines and the Poisson y solve at full length),
+    nz 4096 and 3072 (z tiles of two columns, the factorised z sweep's start sums), in both
+    precisions.  The mixed form's bound on p is wider here: its FP32 increments carry the x
+    viscous term, whose weight grows as 1/dx^2, and the pressure sees their divergence through
+    1/dx; on 4 x 8 cross-sections its p error grows smoothly from 3e-7 at nx = 512 to 9e-6 at
+    nx = 4096 (u 4e-9 to 2e-7), while the FP64 form stays at 1e-14.  Its divergence after the
+    projection sits at the floor of the refinement's float-float residual, about 2^-46 of the
+    largest stencil term, which grows as 1/h^2 with the smallest spacing h: measured 5e-10 at
+    dx = 2 pi / 4096, 3e-9 at the wall rows of ny = 1024, 8e-9 at dz = pi / 4096 (1e-15 on the
+    bench grids); the bound here is 2e-8 (the FP64 form: 1e-10)."""
+    case, u, v, w, p = I.small_channel(*shape, seed=13)
+    case.dt = 1e-3
+    case.precision = precision
+    g = O.Grid.from_case(case)
+    u, v, w = O.make_divergence_free(g, u, v, w)
+    ref = O.step(g, dict(u=u, v=v, w=w, p=p), case.dt, case.re, case.fx, nsteps=2)
+    s = B.Solver(case, u, v, w, p)
+    s.step(2)
+    got = s.state()
+    errs = field_rel_errors(got, (ref["u"], ref["v"], ref["w"], ref["p"]))
+    for name in ("u", "v", "w"):
+        assert errs[name] < bound, (name, errs)
+    assert errs["p"] < pbound, errs
+    assert np.abs(O.divergence(g, *got[:3])).max() < (1e-10 if precision == 0 else 2e-8)
+    s.close()
+
+
+def test_largest_x_boundary_layer():
+    """Inflow / convective outflow at nx = 4096: the cosine transforms of one 4096-point row per
+    block, the x lines with the outflow face, against the oracle."""
+    case, u, v, w, p, bl = I.boundary_layer(4096, 6, 8, amp=0.05, seed=4, re=200.0)
+    g = O.Grid.from_case(case)
+    u, v, w, bl = O.make_divergence_free_bl(g, u, v, w, bl)
+    ref = O.step_bl(g, dict(u=u, v=v, w=w, p=p, bl=bl), case.dt, case.re, case.fx, 2, case.u_conv)
+    s = B.Solver(case, u, v, w, p, bl=bl)
+    s.step(2)
+    errs = field_rel_errors(s.state(), (ref["u"], ref["v"], ref["w"], ref["p"]))
+    for name in ("u", "v", "w", "p"):
+        assert errs[name] < 1e-11, (name, errs)
+    s.close()
+
+
 @pytest.mark.parametrize("mode", [B.NS_PART_PPT, B.NS_PART_PDD])
 def test_single_partition_is_plain_thomas(mode):
     """P = 1: no reduced system; PDD and PPT both reduce to the whole-line solve."""
