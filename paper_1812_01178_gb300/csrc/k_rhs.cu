@@ -229,6 +229,8 @@ struct RhsTile {
   T q1[RT_Z][RT_X + 1];                      // x = i0-1 .. i0+TX-1
   T q3[RT_Z + 1][RT_X];                      // z = k0-1 .. k0+TZ-1
   T fuw[RT_Z + 1][RT_X + 1];                 // x = i0 .. i0+TX, z = k0 .. k0+TZ
+  T rt[RT_NPL][RT_COUNT];                    // per-row assembly coefficients of row j (j mod 4)
+  T wf[RT_NPL][2];                           // interpolation weights WLO, WHI of face j (j mod 4)
 };
 
 // State values entering the FP32 tile: the hardware conversion (one instruction on the FP64
@@ -352,7 +354,7 @@ struct RhsTiledK {
   // y-face fluxes on face jf (Fuv, Fvw), zero on the walls
   auto face_fluxes = [&](int jf) {
     const bool inner = jf >= 1 && jf <= ny - 1;
-    const T wl = inner ? C(GC_WLO, jf) : (T)0, wh = inner ? C(GC_WHI, jf) : (T)0;
+    const T wl = S.wf[jf & 3][0], wh = S.wf[jf & 3][1];  // zero off the interior faces
     int q0 = tid;
     if constexpr (kHoist) {
       const T* u0 = PL(0, jf - 1);
@@ -431,9 +433,16 @@ struct RhsTiledK {
   TR* nw = (TR*)a.nw;
   const int i = i0 + tx, k = k0 + tz;
 
+  // The per-row coefficients every thread of the block reads (R, and the face weights of the
+  // y fluxes) are fetched by a few threads into a small ring in shared memory, one step ahead of
+  // their use, instead of by every thread through the read-only path.
+  auto fetch_face = [&](int jf, int q) {
+    S.wf[jf & 3][q] = (jf >= 1 && jf <= ny - 1) ? C(GC_WLO + q, jf) : (T)0;
+  };
   // prologue: planes jb-1, jb, jb+1; fluxes of face jb; Q2 of centre jb-1
   load_plane(jb - 1);
   load_plane(jb);
+  if (tid < 2) fetch_face(jb, tid);
   __syncthreads();
   face_fluxes(jb);
   T q2prev = 0;
@@ -442,6 +451,8 @@ struct RhsTiledK {
     q2prev = (jb >= 1) ? s * s : (T)0;
   }
   for (int j = jb; j <= jlast; ++j) {
+    if (tid < RT_COUNT) S.rt[j & 3][tid] = R(tid, j);
+    else if (tid < RT_COUNT + 2) fetch_face(j + 1, tid - RT_COUNT);
     load_plane(j + 1);
     __syncthreads();
     face_fluxes(j + 1);
@@ -456,13 +467,13 @@ struct RhsTiledK {
         rv[cf] = (TR)0;
         nv[cf] = (TR)0;
       } else {
-        const T n = (S.fuv[j & 1][tz][tx + 1] - S.fuv[j & 1][tz][tx]) * hidx + (q2 - q2prev) * R(RT_QIHC, j) +
+        const T n = (S.fuv[j & 1][tz][tx + 1] - S.fuv[j & 1][tz][tx]) * hidx + (q2 - q2prev) * S.rt[j & 3][RT_QIHC] +
                     (S.fvw[j & 1][tz + 1][tx] - S.fvw[j & 1][tz][tx]) * hidz;
         const T v0 = P(1, j, tz, tx);
-        T r = cn * n + R(RT_CGY, j) * (P(3, j, tz, tx) - P(3, j - 1, tz, tx));
+        T r = cn * n + S.rt[j & 3][RT_CGY] * (P(3, j, tz, tx) - P(3, j - 1, tz, tx));
         r += cx * (P(1, j, tz, tx + 1) + P(1, j, tz, tx - 1));
         r += cz * (P(1, j, tz + 1, tx) + P(1, j, tz - 1, tx));
-        r += R(RT_AF, j) * P(1, j - 1, tz, tx) + R(RT_CF, j) * P(1, j + 1, tz, tx) + R(RT_DF, j) * v0;
+        r += S.rt[j & 3][RT_AF] * P(1, j - 1, tz, tx) + S.rt[j & 3][RT_CF] * P(1, j + 1, tz, tx) + S.rt[j & 3][RT_DF] * v0;
         if (use_prev) r += cp * (T)nv[cf];
         rv[cf] = (TR)r;
         nv[cf] = (TR)n;
@@ -471,8 +482,8 @@ struct RhsTiledK {
     }
     if (j < ny) {
       const long cc = ((long)k * ny + j) * nx + i;
-      const T hidy = R(RT_HIDY, j);
-      const T cA = R(RT_AC, j), cC = R(RT_CC, j), cD = R(RT_DC, j);
+      const T hidy = S.rt[j & 3][RT_HIDY];
+      const T cA = S.rt[j & 3][RT_AC], cC = S.rt[j & 3][RT_CC], cD = S.rt[j & 3][RT_DC];
       // ---------------- u at (xf_i, yc_j, zc_k)
       {
         const T u0 = P(0, j, tz, tx);
