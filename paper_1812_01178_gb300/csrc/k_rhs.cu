@@ -473,7 +473,10 @@ struct RhsTiledK {
         T r = cn * n + S.rt[j & 3][RT_CGY] * (P(3, j, tz, tx) - P(3, j - 1, tz, tx));
         r += cx * (P(1, j, tz, tx + 1) + P(1, j, tz, tx - 1));
         r += cz * (P(1, j, tz + 1, tx) + P(1, j, tz - 1, tx));
-        r += S.rt[j & 3][RT_AF] * P(1, j - 1, tz, tx) + S.rt[j & 3][RT_CF] * P(1, j + 1, tz, tx) + S.rt[j & 3][RT_DF] * v0;
+        // one FMA per term on r (a sum of the three products first would add an instruction)
+        r += S.rt[j & 3][RT_AF] * P(1, j - 1, tz, tx);
+        r += S.rt[j & 3][RT_CF] * P(1, j + 1, tz, tx);
+        r += S.rt[j & 3][RT_DF] * v0;
         if (use_prev) r += cp * (T)nv[cf];
         rv[cf] = (TR)r;
         nv[cf] = (TR)n;
@@ -493,7 +496,9 @@ struct RhsTiledK {
         T r = cn * n + cb + cgx * (P(3, j, tz, tx) - P(3, j, tz, tx - 1));
         r += cx * (P(0, j, tz, tx + 1) + P(0, j, tz, tx - 1));
         r += cz * (P(0, j, tz + 1, tx) + P(0, j, tz - 1, tx));
-        r += cA * P(0, j - 1, tz, tx) + cC * P(0, j + 1, tz, tx) + cD * u0;
+        r += cA * P(0, j - 1, tz, tx);
+        r += cC * P(0, j + 1, tz, tx);
+        r += cD * u0;
         if (use_prev) r += cp * (T)nu[cc];
         const bool fixed = a.bl && i == 0;  // inflow face of u
         ru[cc] = fixed ? (TR)0 : (TR)r;
@@ -508,7 +513,9 @@ struct RhsTiledK {
         T r = cn * n + cgz * (P(3, j, tz, tx) - P(3, j, tz - 1, tx));
         r += cx * (P(2, j, tz, tx + 1) + P(2, j, tz, tx - 1));
         r += cz * (P(2, j, tz + 1, tx) + P(2, j, tz - 1, tx));
-        r += cA * P(2, j - 1, tz, tx) + cC * P(2, j + 1, tz, tx) + cD * w0;
+        r += cA * P(2, j - 1, tz, tx);
+        r += cC * P(2, j + 1, tz, tx);
+        r += cD * w0;
         if (use_prev) r += cp * (T)nw[cc];
         rw[cc] = (TR)r;
         nw[cc] = (TR)n;
