@@ -458,68 +458,67 @@ struct RhsTiledK {
     face_fluxes(j + 1);
     centre_products(j);
     __syncthreads();
+    // The three components are assembled in one straight-line block (v also on the wall faces
+    // and u, w also on the face row j = ny, where the planes read are zero and the results are
+    // not stored), so that the compiler can interleave their three FP64 chains.
+    const bool vrow = j > 0 && j < ny;  // interior v face
+    const bool crow = j < ny;           // a row of cells
+    const long cf = ((long)k * ny1 + j) * nx + i;
+    const long cc = ((long)k * ny + (crow ? j : 0)) * nx + i;
+    const T* rt = S.rt[j & 3];
     // ---------------- v at face j
-    {
-      const long cf = ((long)k * ny1 + j) * nx + i;
-      const T sv = P(1, j, tz, tx) + P(1, j + 1, tz, tx);
-      const T q2 = sv * sv;  // Q2 of centre j (zero planes beyond the top)
-      if (j == 0 || j == ny) {
-        rv[cf] = (TR)0;
-        nv[cf] = (TR)0;
-      } else {
-        const T n = (S.fuv[j & 1][tz][tx + 1] - S.fuv[j & 1][tz][tx]) * hidx + (q2 - q2prev) * S.rt[j & 3][RT_QIHC] +
-                    (S.fvw[j & 1][tz + 1][tx] - S.fvw[j & 1][tz][tx]) * hidz;
-        const T v0 = P(1, j, tz, tx);
-        T r = cn * n + S.rt[j & 3][RT_CGY] * (P(3, j, tz, tx) - P(3, j - 1, tz, tx));
-        r += cx * (P(1, j, tz, tx + 1) + P(1, j, tz, tx - 1));
-        r += cz * (P(1, j, tz + 1, tx) + P(1, j, tz - 1, tx));
-        // one FMA per term on r (a sum of the three products first would add an instruction)
-        r += S.rt[j & 3][RT_AF] * P(1, j - 1, tz, tx);
-        r += S.rt[j & 3][RT_CF] * P(1, j + 1, tz, tx);
-        r += S.rt[j & 3][RT_DF] * v0;
-        if (use_prev) r += cp * (T)nv[cf];
-        rv[cf] = (TR)r;
-        nv[cf] = (TR)n;
+    const T sv = P(1, j, tz, tx) + P(1, j + 1, tz, tx);
+    const T q2 = sv * sv;  // Q2 of centre j (zero planes beyond the top)
+    const T nvv = (S.fuv[j & 1][tz][tx + 1] - S.fuv[j & 1][tz][tx]) * hidx + (q2 - q2prev) * rt[RT_QIHC] +
+                  (S.fvw[j & 1][tz + 1][tx] - S.fvw[j & 1][tz][tx]) * hidz;
+    q2prev = q2;
+    const T v0 = P(1, j, tz, tx);
+    T rv_ = cn * nvv + rt[RT_CGY] * (P(3, j, tz, tx) - P(3, j - 1, tz, tx));
+    rv_ += cx * (P(1, j, tz, tx + 1) + P(1, j, tz, tx - 1));
+    rv_ += cz * (P(1, j, tz + 1, tx) + P(1, j, tz - 1, tx));
+    // one FMA per term on r (a sum of the three products first would add an instruction)
+    rv_ += rt[RT_AF] * P(1, j - 1, tz, tx);
+    rv_ += rt[RT_CF] * P(1, j + 1, tz, tx);
+    rv_ += rt[RT_DF] * v0;
+    // ---------------- u at (xf_i, yc_j, zc_k)
+    const T hidy = rt[RT_HIDY];
+    const T cA = rt[RT_AC], cC = rt[RT_CC], cD = rt[RT_DC];
+    const T u0 = P(0, j, tz, tx);
+    const T nuu = (S.q1[tz][tx + 1] - S.q1[tz][tx]) * qidx +
+                  (S.fuv[(j + 1) & 1][tz][tx] - S.fuv[j & 1][tz][tx]) * hidy +
+                  (S.fuw[tz + 1][tx] - S.fuw[tz][tx]) * qidz;
+    T ru_ = cn * nuu + cb + cgx * (P(3, j, tz, tx) - P(3, j, tz, tx - 1));
+    ru_ += cx * (P(0, j, tz, tx + 1) + P(0, j, tz, tx - 1));
+    ru_ += cz * (P(0, j, tz + 1, tx) + P(0, j, tz - 1, tx));
+    ru_ += cA * P(0, j - 1, tz, tx);
+    ru_ += cC * P(0, j + 1, tz, tx);
+    ru_ += cD * u0;
+    // ---------------- w at (xc_i, yc_j, zf_k)
+    const T w0 = P(2, j, tz, tx);
+    const T nww = (S.fuw[tz][tx + 1] - S.fuw[tz][tx]) * qidx +
+                  (S.fvw[(j + 1) & 1][tz][tx] - S.fvw[j & 1][tz][tx]) * hidy +
+                  (S.q3[tz + 1][tx] - S.q3[tz][tx]) * qidz;
+    T rw_ = cn * nww + cgz * (P(3, j, tz, tx) - P(3, j, tz - 1, tx));
+    rw_ += cx * (P(2, j, tz, tx + 1) + P(2, j, tz, tx - 1));
+    rw_ += cz * (P(2, j, tz + 1, tx) + P(2, j, tz - 1, tx));
+    rw_ += cA * P(2, j - 1, tz, tx);
+    rw_ += cC * P(2, j + 1, tz, tx);
+    rw_ += cD * w0;
+    if (use_prev) {
+      if (vrow) rv_ += cp * (T)nv[cf];
+      if (crow) {
+        ru_ += cp * (T)nu[cc];
+        rw_ += cp * (T)nw[cc];
       }
-      q2prev = q2;
     }
-    if (j < ny) {
-      const long cc = ((long)k * ny + j) * nx + i;
-      const T hidy = S.rt[j & 3][RT_HIDY];
-      const T cA = S.rt[j & 3][RT_AC], cC = S.rt[j & 3][RT_CC], cD = S.rt[j & 3][RT_DC];
-      // ---------------- u at (xf_i, yc_j, zc_k)
-      {
-        const T u0 = P(0, j, tz, tx);
-        const T n = (S.q1[tz][tx + 1] - S.q1[tz][tx]) * qidx +
-                    (S.fuv[(j + 1) & 1][tz][tx] - S.fuv[j & 1][tz][tx]) * hidy +
-                    (S.fuw[tz + 1][tx] - S.fuw[tz][tx]) * qidz;
-        T r = cn * n + cb + cgx * (P(3, j, tz, tx) - P(3, j, tz, tx - 1));
-        r += cx * (P(0, j, tz, tx + 1) + P(0, j, tz, tx - 1));
-        r += cz * (P(0, j, tz + 1, tx) + P(0, j, tz - 1, tx));
-        r += cA * P(0, j - 1, tz, tx);
-        r += cC * P(0, j + 1, tz, tx);
-        r += cD * u0;
-        if (use_prev) r += cp * (T)nu[cc];
-        const bool fixed = a.bl && i == 0;  // inflow face of u
-        ru[cc] = fixed ? (TR)0 : (TR)r;
-        nu[cc] = fixed ? (TR)0 : (TR)n;
-      }
-      // ---------------- w at (xc_i, yc_j, zf_k)
-      {
-        const T w0 = P(2, j, tz, tx);
-        const T n = (S.fuw[tz][tx + 1] - S.fuw[tz][tx]) * qidx +
-                    (S.fvw[(j + 1) & 1][tz][tx] - S.fvw[j & 1][tz][tx]) * hidy +
-                    (S.q3[tz + 1][tx] - S.q3[tz][tx]) * qidz;
-        T r = cn * n + cgz * (P(3, j, tz, tx) - P(3, j, tz - 1, tx));
-        r += cx * (P(2, j, tz, tx + 1) + P(2, j, tz, tx - 1));
-        r += cz * (P(2, j, tz + 1, tx) + P(2, j, tz - 1, tx));
-        r += cA * P(2, j - 1, tz, tx);
-        r += cC * P(2, j + 1, tz, tx);
-        r += cD * w0;
-        if (use_prev) r += cp * (T)nw[cc];
-        rw[cc] = (TR)r;
-        nw[cc] = (TR)n;
-      }
+    rv[cf] = vrow ? (TR)rv_ : (TR)0;
+    nv[cf] = vrow ? (TR)nvv : (TR)0;
+    if (crow) {
+      const bool fixed = a.bl && i == 0;  // inflow face of u
+      ru[cc] = fixed ? (TR)0 : (TR)ru_;
+      nu[cc] = fixed ? (TR)0 : (TR)nuu;
+      rw[cc] = (TR)rw_;
+      nw[cc] = (TR)nww;
     }
   }
 
