@@ -142,7 +142,9 @@ ns_status ns_init(ns_ctx** out, const ns_config* cfg, const ns_fields* fields,
  *   r_i = dt [ -gamma_k N_i(u) - zeta_k N_prev_i - alpha_k G_i p + (alpha_k/Re) L u_i + alpha_k f_i ]
  * with N = divergence-form convection (Eq. NSmomentum, 2nd-order central), L the viscous
  * operator and G the pressure gradient.  Writes r into the workspace buffers NS_BUF_RU/RV/RW
- * and N(u) into NS_BUF_NU/NV/NW (it is N_prev of the next sub-step; substep 0 ignores it). */
+ * and -dt gamma_k N(u) into NS_BUF_NU/NV/NW: N is formed and kept already multiplied by its weight
+ * in r, and read back by the next sub-step as N_prev with weight zeta_(k+1) / gamma_k (substep 0
+ * ignores it). */
 ns_status ns_rhs(ns_ctx* ctx, int substep);
 
 /* One ADI factor (Sec. 2.2): solves (I - beta_k delta_dd) x = r in place on the r buffers for
@@ -266,7 +268,8 @@ ns_status ns_autotune(ns_ctx* ctx);
 /* Workspace buffers, for inspection and for stage-by-stage testing. */
 enum {
   NS_BUF_RU = 0, NS_BUF_RV = 1, NS_BUF_RW = 2,   /* r / delta (double, or float if NS_MIXED) */
-  NS_BUF_NU = 3, NS_BUF_NV = 4, NS_BUF_NW = 5,   /* N_prev (double, or float if NS_MIXED) */
+  NS_BUF_NU = 3, NS_BUF_NV = 4, NS_BUF_NW = 5,   /* -dt gamma_k N of the last ns_rhs (double, or
+                                                   float if NS_MIXED) */
   NS_BUF_PHI = 6,                               /* phi, double, nz*ny*nx */
   NS_BUF_SPEC = 7,                              /* spectral buffer, complex double,
                                                    (nz/2+1)*ny*nx, layout [kz][j][kx]; NS_MIXED:

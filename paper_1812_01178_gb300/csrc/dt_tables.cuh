@@ -63,9 +63,13 @@ NS_HD void dt_stepk(const DtSpec& s, int q, StepK& sk) {
   const double idx = 1.0 / s.dx, idz = 1.0 / s.dz, idx2 = idx * idx, idz2 = idz * idz;
   const double inv_re = spec_inv_re(s);
   // tiled RHS constants, each rounded to double and to float as the expressions would be in that
-  // type (products of the double inputs rounded once; cx, cz formed in the type itself)
-  const double d[11] = {0.25 * idx, 0.25 * idz, 0.5 * idx, 0.5 * idz, -dt * gam, -dt * zet,
-                        -dt * alp * idx, -dt * alp * idz, 0.0, 0.0, dt * alp * s.fx};
+  // type (products of the double inputs rounded once; cx, cz formed in the type itself).  The
+  // convection N is formed and stored pre-multiplied by cn = -dt gamma_k (its difference weights
+  // carry cn), so the weight of the stored N of sub-step k-1 is cp = zeta_k / gamma_(k-1).
+  const double cn = -dt * gam;
+  const double d[11] = {0.25 * idx * cn, 0.25 * idz * cn, 0.5 * idx * cn, 0.5 * idz * cn, cn,
+                        k > 0 ? zet / rk_gamma(k - 1) : 0.0, -dt * alp * idx, -dt * alp * idz, 0.0, 0.0,
+                        dt * alp * s.fx};
   const double cl = dt * alp * inv_re;
   for (int i = 0; i < 11; ++i) {
     sk.kd[i] = d[i];
@@ -106,14 +110,14 @@ NS_HD void dt_rtab_row(const DtSpec& s, int k, int j, double* rt, float* rtf) {
     v[RT_AC] = cl * spec_gc(s, GC_AC, j);
     v[RT_CC] = cl * spec_gc(s, GC_CC, j);
     v[RT_DC] = -cl * (dd + spec_gc(s, GC_AC, j) + spec_gc(s, GC_CC, j));
-    v[RT_HIDY] = 0.5 * spec_gc(s, GC_IDY, j);
+    v[RT_HIDY] = 0.5 * spec_gc(s, GC_IDY, j) * (-s.dt * rk_gamma(k));  // the convection weight cn
   }
   if (j >= 1 && j < ny) {
     v[RT_AF] = cl * spec_gc(s, GC_AF, j);
     v[RT_CF] = cl * spec_gc(s, GC_CF, j);
     v[RT_DF] = -cl * (dd + spec_gc(s, GC_AF, j) + spec_gc(s, GC_CF, j));
     v[RT_CGY] = -s.dt * rk_alpha(k) * spec_gc(s, GC_IHC, j);
-    v[RT_QIHC] = 0.25 * spec_gc(s, GC_IHC, j);
+    v[RT_QIHC] = 0.25 * spec_gc(s, GC_IHC, j) * (-s.dt * rk_gamma(k));
   }
   for (int f = 0; f < RT_COUNT; ++f) {
     rt[(size_t)f * G + j] = v[f];

@@ -36,6 +36,7 @@ struct RhsArgs {
   int nx, ny, nz;
   double idx, idz, idx2, idz2;
   double dt, gam, zet, alp, inv_re, fx;
+  double cprev;     // zeta_k / gamma_(k-1): weight of the stored (pre-multiplied) N of sub-step k-1
   const StepK* sk;  // dt-dependent constants of this sub-step (device; read by the Dyn variants)
   StepK kc;         // the same values as kernel arguments (read by the fixed-dt variants)
 };
@@ -96,8 +97,11 @@ struct RhsK {
   auto C = [&](int f, int jj) -> T { return from_double<T>(__ldg(a.gc + f * G + jj)); };
 
   const T idx = (T)a.idx, idz = (T)a.idz, idx2 = (T)a.idx2, idz2 = (T)a.idz2;
-  const T dt = (T)(Dyn ? a.sk->dt : a.kc.dt), gam = (T)a.gam, zet = (T)a.zet, alp = (T)a.alp;
+  const T dt = (T)(Dyn ? a.sk->dt : a.kc.dt), alp = (T)a.alp;
   const T avis = (T)(a.alp * a.inv_re);
+  // N is stored pre-multiplied by cn = -dt gamma_k, as in the tiled form; the stored N of the
+  // previous sub-step enters with zeta_k / gamma_(k-1)
+  const T cn = -dt * (T)a.gam, cpn = (T)a.cprev;
   const T half = (T)0.5, quarter = (T)0.25, two = (T)2;
 
   TR* ru = (TR*)a.ru;
@@ -135,11 +139,12 @@ struct RhsK {
       const T lap = (uxp - two * u0 + uxm) * idx2 + (uzp - two * u0 + uzm) * idz2 + ac * uym -
                     (ac + cy) * u0 + cy * uyp;
       const T gp = (Pp(i, j, k) - Pp(imx, j, k)) * idx;
-      T r = -gam * n - alp * gp + avis * lap + (T)(a.alp * a.fx);
-      if (a.zet != 0.0) r -= zet * (T)nu[cc];
+      const T nt = cn * n;
+      T r = dt * (-alp * gp + avis * lap + (T)(a.alp * a.fx)) + nt;
+      if (a.zet != 0.0) r += cpn * (T)nu[cc];
       const bool fixed = bl && i == 0;  // inflow face
-      ru[cc] = fixed ? (TR)0 : (TR)(dt * r);
-      nu[cc] = fixed ? (TR)0 : (TR)n;
+      ru[cc] = fixed ? (TR)0 : (TR)r;
+      nu[cc] = fixed ? (TR)0 : (TR)nt;
     }
     // ---------------- w at (xc_i, yc_j, zf_k)
     {
@@ -161,10 +166,11 @@ struct RhsK {
       const T lap = (wxp - two * w0 + wxm) * idx2 + (wzp - two * w0 + wzm) * idz2 + ac * wym -
                     (ac + cy) * w0 + cy * wyp;
       const T gp = (Pp(i, j, k) - Pp(i, j, km)) * idz;
-      T r = -gam * n - alp * gp + avis * lap;
-      if (a.zet != 0.0) r -= zet * (T)nw[cc];
-      rw[cc] = (TR)(dt * r);
-      nw[cc] = (TR)n;
+      const T nt = cn * n;
+      T r = dt * (-alp * gp + avis * lap) + nt;
+      if (a.zet != 0.0) r += cpn * (T)nw[cc];
+      rw[cc] = (TR)r;
+      nw[cc] = (TR)nt;
     }
   }
   // ---------------- v at (xc_i, yf_j, zc_k)
@@ -193,10 +199,11 @@ struct RhsK {
     const T lap = (vxp - two * v0 + vxm) * idx2 + (vzp - two * v0 + vzm) * idz2 + af * vym -
                   (af + cyf) * v0 + cyf * vyp;
     const T gp = (Pp(i, j, k) - Pp(i, j - 1, k)) * ihc;
-    T r = -gam * n - alp * gp + avis * lap;
-    if (a.zet != 0.0) r -= zet * (T)nv[cf];
-    rv[cf] = (TR)(dt * r);
-    nv[cf] = (TR)n;
+    const T nt = cn * n;
+    T r = dt * (-alp * gp + avis * lap) + nt;
+    if (a.zet != 0.0) r += cpn * (T)nv[cf];
+    rv[cf] = (TR)r;
+    nv[cf] = (TR)nt;
   }
 
   }
@@ -411,14 +418,15 @@ struct RhsTiledK {
   };
 
   // r = cn N + cp N_prev + cgx (p_i - p_{i-1}) + cx (f_{i+1} + f_{i-1}) + cz (f_{k+1} + f_{k-1})
-  //     + cA f_{j-1} + cC f_{j+1} + cD f (+ cb for u), with every constant pre-multiplied by dt
+  //     + cA f_{j-1} + cC f_{j+1} + cD f (+ cb for u), with every constant pre-multiplied by dt;
+  // cn N is formed directly (the difference weights carry cn) and stored as the next N_prev
   auto K = [&](int q) -> T {
     const StepK& sk = Dyn ? *a.sk : a.kc;
     if constexpr (sizeof(T) == 4) return sk.kf[q];
     else return sk.kd[q];
   };
   const T qidx = K(RK_QIDX), qidz = K(RK_QIDZ), hidx = K(RK_HIDX), hidz = K(RK_HIDZ);
-  const T cn = K(RK_CN), cp = K(RK_CP), cgx = K(RK_CGX), cgz = K(RK_CGZ), cx = K(RK_CX), cz = K(RK_CZ);
+  const T cp = K(RK_CP), cgx = K(RK_CGX), cgz = K(RK_CGZ), cx = K(RK_CX), cz = K(RK_CZ);
   const T cb = K(RK_CB);
   const bool use_prev = a.zet != 0.0;
   auto R = [&](int f, int jj) -> T {
@@ -473,7 +481,7 @@ struct RhsTiledK {
                   (S.fvw[j & 1][tz + 1][tx] - S.fvw[j & 1][tz][tx]) * hidz;
     q2prev = q2;
     const T v0 = P(1, j, tz, tx);
-    T rv_ = cn * nvv + rt[RT_CGY] * (P(3, j, tz, tx) - P(3, j - 1, tz, tx));
+    T rv_ = nvv + rt[RT_CGY] * (P(3, j, tz, tx) - P(3, j - 1, tz, tx));
     rv_ += cx * (P(1, j, tz, tx + 1) + P(1, j, tz, tx - 1));
     rv_ += cz * (P(1, j, tz + 1, tx) + P(1, j, tz - 1, tx));
     // one FMA per term on r (a sum of the three products first would add an instruction)
@@ -487,7 +495,7 @@ struct RhsTiledK {
     const T nuu = (S.q1[tz][tx + 1] - S.q1[tz][tx]) * qidx +
                   (S.fuv[(j + 1) & 1][tz][tx] - S.fuv[j & 1][tz][tx]) * hidy +
                   (S.fuw[tz + 1][tx] - S.fuw[tz][tx]) * qidz;
-    T ru_ = cn * nuu + cb + cgx * (P(3, j, tz, tx) - P(3, j, tz, tx - 1));
+    T ru_ = nuu + cb + cgx * (P(3, j, tz, tx) - P(3, j, tz, tx - 1));
     ru_ += cx * (P(0, j, tz, tx + 1) + P(0, j, tz, tx - 1));
     ru_ += cz * (P(0, j, tz + 1, tx) + P(0, j, tz - 1, tx));
     ru_ += cA * P(0, j - 1, tz, tx);
@@ -498,7 +506,7 @@ struct RhsTiledK {
     const T nww = (S.fuw[tz][tx + 1] - S.fuw[tz][tx]) * qidx +
                   (S.fvw[(j + 1) & 1][tz][tx] - S.fvw[j & 1][tz][tx]) * hidy +
                   (S.q3[tz + 1][tx] - S.q3[tz][tx]) * qidz;
-    T rw_ = cn * nww + cgz * (P(3, j, tz, tx) - P(3, j, tz - 1, tx));
+    T rw_ = nww + cgz * (P(3, j, tz, tx) - P(3, j, tz - 1, tx));
     rw_ += cx * (P(2, j, tz, tx + 1) + P(2, j, tz, tx - 1));
     rw_ += cz * (P(2, j, tz + 1, tx) + P(2, j, tz - 1, tx));
     rw_ += cA * P(2, j - 1, tz, tx);
@@ -575,6 +583,7 @@ cudaError_t stage_rhs(LaunchSink& s, int k) {
   a.dt = c->cfg.dt;
   a.gam = NS_GAMMA[k];
   a.zet = NS_ZETA[k];
+  a.cprev = k > 0 ? NS_ZETA[k] / NS_GAMMA[k - 1] : 0.0;
   a.alp = NS_ALPHA[k];
   a.inv_re = c->cfg.re > 0 ? 1.0 / c->cfg.re : 0.0;
   a.fx = c->cfg.fx;

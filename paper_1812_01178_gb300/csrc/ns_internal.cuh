@@ -122,13 +122,14 @@ enum { GC_DY = 0, GC_IDY, GC_HC, GC_IHC, GC_WLO, GC_WHI, GC_AC, GC_CC, GC_AF, GC
 //   AC/CC/DC : cl A_j, cl C_j, -cl (2/dx^2 + 2/dz^2 + A_j + C_j) at centres (AC, CC of GC_*)
 //   AF/CF/DF : the same at interior faces (AF, CF of GC_*)
 //   CGY      : -dt alpha_k / hc_j (pressure gradient at face j)
-//   HIDY     : 1 / (2 dy_j),   QIHC : 1 / (4 hc_j)
+//   HIDY     : cn / (2 dy_j),   QIHC : cn / (4 hc_j), with cn = -dt gamma_k
 enum { RT_AC = 0, RT_CC, RT_DC, RT_AF, RT_CF, RT_DF, RT_CGY, RT_HIDY, RT_QIHC, RT_COUNT };
 
-// Constants of the tiled RHS in StepK::kd / kf: quarter and half inverse spacings in x and z, the
-// convection weights -dt gamma_k and -dt zeta_k, the pressure-gradient and viscous weights
-// -dt alpha_k / dx, -dt alpha_k / dz, dt alpha_k / (Re dx^2), dt alpha_k / (Re dz^2), and the body
-// force dt alpha_k fx.
+// Constants of the tiled RHS in StepK::kd / kf: quarter and half inverse spacings in x and z times
+// the convection weight cn = -dt gamma_k (the RHS forms and stores N pre-multiplied by cn), cn
+// itself, the weight zeta_k / gamma_(k-1) of the stored N of the previous sub-step, the pressure-
+// gradient and viscous weights -dt alpha_k / dx, -dt alpha_k / dz, dt alpha_k / (Re dx^2),
+// dt alpha_k / (Re dz^2), and the body force dt alpha_k fx.
 enum { RK_QIDX, RK_QIDZ, RK_HIDX, RK_HIDZ, RK_CN, RK_CP, RK_CGX, RK_CGZ, RK_CX, RK_CZ, RK_CB };
 
 // RK3 constants (Sec. 2.2): gamma, zeta, alpha = gamma + zeta.
