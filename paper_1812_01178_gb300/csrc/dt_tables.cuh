@@ -104,20 +104,28 @@ NS_HD void dt_rtab_row(const DtSpec& s, int k, int j, double* rt, float* rtf) {
   const int ny = s.ny, G = ny + 1;
   const double cl = s.dt * rk_alpha(k) * spec_inv_re(s);
   const double dd = 2.0 / (s.dx * s.dx) + 2.0 / (s.dz * s.dz);
+  const double cn = -s.dt * rk_gamma(k);  // the convection weight
+  // interpolation weight of the lower centre at face jf, zero at the walls
+  auto wlo = [&](int jf) { return (jf >= 1 && jf < ny) ? spec_gc(s, GC_WLO, jf) : 0.0; };
   double v[RT_COUNT];
   for (int f = 0; f < RT_COUNT; ++f) v[f] = 0.0;
   if (j < ny) {
     v[RT_AC] = cl * spec_gc(s, GC_AC, j);
     v[RT_CC] = cl * spec_gc(s, GC_CC, j);
     v[RT_DC] = -cl * (dd + spec_gc(s, GC_AC, j) + spec_gc(s, GC_CC, j));
-    v[RT_HIDY] = 0.5 * spec_gc(s, GC_IDY, j) * (-s.dt * rk_gamma(k));  // the convection weight cn
+    const double hidy = 0.5 * spec_gc(s, GC_IDY, j) * cn;
+    v[RT_HYM] = -hidy * wlo(j);
+    v[RT_HYP] = hidy * wlo(j + 1);
   }
   if (j >= 1 && j < ny) {
     v[RT_AF] = cl * spec_gc(s, GC_AF, j);
     v[RT_CF] = cl * spec_gc(s, GC_CF, j);
     v[RT_DF] = -cl * (dd + spec_gc(s, GC_AF, j) + spec_gc(s, GC_CF, j));
     v[RT_CGY] = -s.dt * rk_alpha(k) * spec_gc(s, GC_IHC, j);
-    v[RT_QIHC] = 0.25 * spec_gc(s, GC_IHC, j) * (-s.dt * rk_gamma(k));
+    v[RT_QIHC] = 0.25 * spec_gc(s, GC_IHC, j) * cn;
+    v[RT_HXW] = 0.5 / s.dx * cn * wlo(j);
+    v[RT_HZW] = 0.5 / s.dz * cn * wlo(j);
+    v[RT_RHO] = spec_gc(s, GC_WHI, j) / spec_gc(s, GC_WLO, j);
   }
   for (int f = 0; f < RT_COUNT; ++f) {
     rt[(size_t)f * G + j] = v[f];

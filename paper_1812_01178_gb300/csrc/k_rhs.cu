@@ -237,7 +237,7 @@ struct RhsTile {
   T q3[RT_Z + 1][RT_X];                      // z = k0-1 .. k0+TZ-1
   T fuw[RT_Z + 1][RT_X + 1];                 // x = i0 .. i0+TX, z = k0 .. k0+TZ
   T rt[RT_NPL][RT_COUNT];                    // per-row assembly coefficients of row j (j mod 4)
-  T wf[RT_NPL][2];                           // interpolation weights WLO, WHI of face j (j mod 4)
+  T wf[RT_NPL];                              // RHO = WHI / WLO of face j (j mod 4), zero at the walls
 };
 
 // State values entering the FP32 tile: the hardware conversion (one instruction on the FP64
@@ -248,6 +248,15 @@ __device__ __forceinline__ T plane_cvt(double x) {
   if constexpr (sizeof(T) == 4) return __double2float_rn(x);
   else return x;
 }
+
+// 8-byte global -> shared copy that completes asynchronously (cp.async, waited for by
+// cp.async.wait_all); with valid false nothing is read and the 8 bytes are zero-filled
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem, bool valid) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(sa), "l"(gmem), "r"(valid ? 8 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit8() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all8() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 template <typename T, typename TR, bool Dyn>
 struct RhsTiledK {
@@ -264,18 +273,16 @@ struct RhsTiledK {
   static Args make(RhsArgs a, int jchunk) { return Args{a, jchunk}; }
   static __device__ __forceinline__ void run(const Args& a_, const dim3 bid_, const dim3 gdim_) {
     const RhsArgs& a = a_.a;
-    int jchunk = a_.jchunk;
+    const int i0 = bid_.x * RT_X, k0 = bid_.y * RT_Z;
+    const int jb = bid_.z * a_.jchunk;
 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   RhsTile<T>& S = *reinterpret_cast<RhsTile<T>*>(smem_raw);
   const int nx = a.nx, ny = a.ny, nz = a.nz, ny1 = ny + 1, G = ny + 1;
   const int tx = threadIdx.x, tz = threadIdx.y, tid = tz * RT_X + tx;
-  const int i0 = bid_.x * RT_X, k0 = bid_.y * RT_Z;
-  const int jb = bid_.z * jchunk;
-  const int je = min(jb + jchunk, ny);
+  const int je = min(jb + a_.jchunk, ny);
   const int jlast = (je == ny) ? ny : je - 1;  // v rows: the last chunk also writes face ny
 
-  auto C = [&](int f, int jj) -> T { return from_double<T>(__ldg(a.gc + f * G + jj)); };
   auto P = [&](int f, int j, int kk, int ii) -> T& { return S.pl[f][j & 3][(kk + 1) * RT_PX + ii + 1]; };
 
   // Plane loads.  Each thread owns up to two positions of the (RT_PZ x RT_PX) halo plane and
@@ -306,12 +313,24 @@ struct RhsTiledK {
       }
     }
   }
+  // FP64: planes are copied global -> shared by cp.async one step ahead (plane j + 2 is issued in
+  // step j, after the barrier that ends every read of plane j - 2 in its buffer, and waited for in
+  // step j + 1), so that no block stalls on its own plane loads; x-boundary halo positions are
+  // formed by plain loads.  FP32 converts on the way and loads through registers.
+  constexpr bool kAsync = sizeof(T) == 8;
   auto load_plane = [&](int j) {
     const bool jc = j >= 0 && j < ny, jv = j >= 0 && j <= ny;
     const long jo = (long)j * nx;
 #pragma unroll
     for (int r = 0; r < kPos; ++r) {
-      if (pos[r] >= 0) {
+      if (kAsync && pos[r] >= 0) {
+        const int e = pos[r];
+        const long o = oc[r] + jo, q = ov[r] + jo;
+        cp_async8(&S.pl[0][j & 3][e], a.u + (jc ? o : 0), jc);
+        cp_async8(&S.pl[1][j & 3][e], a.v + (jv ? q : 0), jv);
+        cp_async8(&S.pl[2][j & 3][e], a.w + (jc ? o : 0), jc);
+        cp_async8(&S.pl[3][j & 3][e], a.p + (jc ? o : 0), jc);
+      } else if (pos[r] >= 0) {
         const int e = pos[r];
         const long o = oc[r] + jo, q = ov[r] + jo;
         T vu = (T)0, vv = (T)0, vw = (T)0, vp = (T)0;
@@ -346,51 +365,81 @@ struct RhsTiledK {
         S.pl[3][j & 3][e] = (T)0;
       }
     }
+    if (kAsync) cp_async_commit8();
   };
-  // y-face fluxes on face jf (Fuv, Fvw), zero on the walls
   // Each product loop gives every thread the item q = tid first (every loop has at least 256
   // items).  In the FP32 form that item's tile offsets are worked out once, before the march in y,
   // and only the few items q >= 256 take the general index arithmetic: the FP32 RHS is
-  // issue-bound.  (The FP64 form keeps the general loops: the offsets cost it registers.)
+  // issue-bound.  (The FP64 form takes the general index arithmetic for both: the offsets cost it
+  // registers.)
   constexpr bool kHoist = sizeof(T) == 4;
   const int hk = tid / (RT_X + 1), hi = tid % (RT_X + 1);   // items of the (RT_X + 1)-wide loops
   const int gk = tid / RT_X, gi = tid % RT_X;               // items of the RT_X-wide loops
   const int eA = (hk + 1) * RT_PX + hi + 1, fA = hk * (RT_X + 1) + hi;
   const int eB = (gk + 1) * RT_PX + gi + 1, fB = gk * RT_X + gi;
   auto PL = [&](int f, int j) -> T* { return S.pl[f][j & 3]; };
-  // y-face fluxes on face jf (Fuv, Fvw), zero on the walls
+  // y-face fluxes on face jf, zero on the walls, each divided by the interpolation weight WLO_jf
+  // (which the difference weights carry): Fuv = (u_{j-1} + RHO u_j)(v_{i-1} + v_i) and
+  // Fvw = (v_{k-1} + v_k)(w_{j-1} + RHO w_j), one FMA, one add and one product each
+  // Every product loop has NT <= n < 2 NT items: thread tid takes item tid.  In the FP32 form the
+  // n - NT items past NT go to the threads from `off` on: Fuv and Q1's extra items to warp 0,
+  // Fvw and Q3's to warp 1 and Fuw's to warps 2 and 3, so that the four SM sub-partitions (warp w
+  // issues on sub-partition w mod 4) share them (FP32 RHS 0.242 -> 0.237 ms).  The FP64 form keeps
+  // them on the first threads (spread, it took 74 registers instead of 67 and 1.58 ms instead of
+  // 1.55).
+  constexpr int NT = RT_X * RT_Z;
+  auto second = [&](int n, int off) {
+    const int x = tid - off;
+    return (x >= 0 && x < n - NT) ? NT + x : -1;
+  };
   auto face_fluxes = [&](int jf) {
     const bool inner = jf >= 1 && jf <= ny - 1;
-    const T wl = S.wf[jf & 3][0], wh = S.wf[jf & 3][1];  // zero off the interior faces
-    int q0 = tid;
+    const T rho = S.wf[jf & 3];
+    auto fuv_at = [&](int q) {
+      const int kk = q / (RT_X + 1), ii = q % (RT_X + 1);
+      T f = 0;
+      if (inner)
+        f = (P(0, jf - 1, kk, ii) + rho * P(0, jf, kk, ii)) * (P(1, jf, kk, ii - 1) + P(1, jf, kk, ii));
+      S.fuv[jf & 1][kk][ii] = f;
+    };
+    auto fvw_at = [&](int q) {
+      const int kk = q / RT_X, ii = q % RT_X;
+      T f = 0;
+      if (inner)
+        f = (P(1, jf, kk - 1, ii) + P(1, jf, kk, ii)) * (P(2, jf - 1, kk, ii) + rho * P(2, jf, kk, ii));
+      S.fvw[jf & 1][kk][ii] = f;
+    };
     if constexpr (kHoist) {
       const T* u0 = PL(0, jf - 1);
       const T* u1 = PL(0, jf);
       const T* v1 = PL(1, jf);
       const T* w0 = PL(2, jf - 1);
       const T* w1 = PL(2, jf);
-      (&S.fuv[jf & 1][0][0])[fA] = inner ? (wl * u0[eA] + wh * u1[eA]) * (v1[eA - 1] + v1[eA]) : (T)0;
-      (&S.fvw[jf & 1][0][0])[fB] = inner ? (v1[eB - RT_PX] + v1[eB]) * (wl * w0[eB] + wh * w1[eB]) : (T)0;
-      q0 = tid + RT_X * RT_Z;
-    }
-    for (int q = q0; q < RT_Z * (RT_X + 1); q += RT_X * RT_Z) {
-      const int kk = q / (RT_X + 1), ii = q % (RT_X + 1);
-      T f = 0;
-      if (inner)
-        f = (wl * P(0, jf - 1, kk, ii) + wh * P(0, jf, kk, ii)) * (P(1, jf, kk, ii - 1) + P(1, jf, kk, ii));
-      S.fuv[jf & 1][kk][ii] = f;
-    }
-    for (int q = q0; q < (RT_Z + 1) * RT_X; q += RT_X * RT_Z) {
-      const int kk = q / RT_X, ii = q % RT_X;
-      T f = 0;
-      if (inner)
-        f = (P(1, jf, kk - 1, ii) + P(1, jf, kk, ii)) * (wl * P(2, jf - 1, kk, ii) + wh * P(2, jf, kk, ii));
-      S.fvw[jf & 1][kk][ii] = f;
+      (&S.fuv[jf & 1][0][0])[fA] = inner ? (u0[eA] + rho * u1[eA]) * (v1[eA - 1] + v1[eA]) : (T)0;
+      (&S.fvw[jf & 1][0][0])[fB] = inner ? (v1[eB - RT_PX] + v1[eB]) * (w0[eB] + rho * w1[eB]) : (T)0;
+      if (const int q = second(RT_Z * (RT_X + 1), 0); q >= 0) fuv_at(q);
+      if (const int q = second((RT_Z + 1) * RT_X, 32); q >= 0) fvw_at(q);
+    } else {
+      for (int q = tid; q < RT_Z * (RT_X + 1); q += NT) fuv_at(q);
+      for (int q = tid; q < (RT_Z + 1) * RT_X; q += NT) fvw_at(q);
     }
   };
   // centre-plane products of plane j (Q1, Q3, Fuw)
   auto centre_products = [&](int j) {
-    int q0 = tid;
+    auto q1_at = [&](int q) {
+      const int kk = q / (RT_X + 1), ii = q % (RT_X + 1) - 1;
+      const T s = P(0, j, kk, ii) + P(0, j, kk, ii + 1);
+      S.q1[kk][ii + 1] = s * s;
+    };
+    auto q3_at = [&](int q) {
+      const int kk = q / RT_X - 1, ii = q % RT_X;
+      const T s = P(2, j, kk, ii) + P(2, j, kk + 1, ii);
+      S.q3[kk + 1][ii] = s * s;
+    };
+    auto fuw_at = [&](int q) {
+      const int kk = q / (RT_X + 1), ii = q % (RT_X + 1);
+      S.fuw[kk][ii] = (P(0, j, kk - 1, ii) + P(0, j, kk, ii)) * (P(2, j, kk, ii - 1) + P(2, j, kk, ii));
+    };
     if constexpr (kHoist) {
       const T* u = PL(0, j);
       const T* w = PL(2, j);
@@ -399,21 +448,13 @@ struct RhsTiledK {
       const T s3 = w[eB - RT_PX] + w[eB];  // Q3 item: z = k0 - 1 + gk
       (&S.q3[0][0])[fB] = s3 * s3;
       (&S.fuw[0][0])[fA] = (u[eA - RT_PX] + u[eA]) * (w[eA - 1] + w[eA]);
-      q0 = tid + RT_X * RT_Z;
-    }
-    for (int q = q0; q < RT_Z * (RT_X + 1); q += RT_X * RT_Z) {
-      const int kk = q / (RT_X + 1), ii = q % (RT_X + 1) - 1;
-      const T s = P(0, j, kk, ii) + P(0, j, kk, ii + 1);
-      S.q1[kk][ii + 1] = s * s;
-    }
-    for (int q = q0; q < (RT_Z + 1) * RT_X; q += RT_X * RT_Z) {
-      const int kk = q / RT_X - 1, ii = q % RT_X;
-      const T s = P(2, j, kk, ii) + P(2, j, kk + 1, ii);
-      S.q3[kk + 1][ii] = s * s;
-    }
-    for (int q = q0; q < (RT_Z + 1) * (RT_X + 1); q += RT_X * RT_Z) {
-      const int kk = q / (RT_X + 1), ii = q % (RT_X + 1);
-      S.fuw[kk][ii] = (P(0, j, kk - 1, ii) + P(0, j, kk, ii)) * (P(2, j, kk, ii - 1) + P(2, j, kk, ii));
+      if (const int q = second(RT_Z * (RT_X + 1), 0); q >= 0) q1_at(q);
+      if (const int q = second((RT_Z + 1) * RT_X, 32); q >= 0) q3_at(q);
+      if (const int q = second((RT_Z + 1) * (RT_X + 1), 64); q >= 0) fuw_at(q);
+    } else {
+      for (int q = tid; q < RT_Z * (RT_X + 1); q += NT) q1_at(q);
+      for (int q = tid; q < (RT_Z + 1) * RT_X; q += NT) q3_at(q);
+      for (int q = tid; q < (RT_Z + 1) * (RT_X + 1); q += NT) fuw_at(q);
     }
   };
 
@@ -425,7 +466,7 @@ struct RhsTiledK {
     if constexpr (sizeof(T) == 4) return sk.kf[q];
     else return sk.kd[q];
   };
-  const T qidx = K(RK_QIDX), qidz = K(RK_QIDZ), hidx = K(RK_HIDX), hidz = K(RK_HIDZ);
+  const T qidx = K(RK_QIDX), qidz = K(RK_QIDZ);
   const T cp = K(RK_CP), cgx = K(RK_CGX), cgz = K(RK_CGZ), cx = K(RK_CX), cz = K(RK_CZ);
   const T cb = K(RK_CB);
   const bool use_prev = a.zet != 0.0;
@@ -444,14 +485,14 @@ struct RhsTiledK {
   // The per-row coefficients every thread of the block reads (R, and the face weights of the
   // y fluxes) are fetched by a few threads into a small ring in shared memory, one step ahead of
   // their use, instead of by every thread through the read-only path.
-  auto fetch_face = [&](int jf, int q) {
-    S.wf[jf & 3][q] = (jf >= 1 && jf <= ny - 1) ? C(GC_WLO + q, jf) : (T)0;
-  };
-  // prologue: planes jb-1, jb, jb+1; fluxes of face jb; Q2 of centre jb-1
+  auto fetch_face = [&](int jf) { S.wf[jf & 3] = (jf >= 1 && jf <= ny - 1) ? R(RT_RHO, jf) : (T)0; };
+  // prologue: planes jb-1, jb (jb+1 in flight); fluxes of face jb; Q2 of centre jb-1
   load_plane(jb - 1);
   load_plane(jb);
-  if (tid < 2) fetch_face(jb, tid);
+  if (kAsync) cp_async_wait_all8();
+  if (tid == 0) fetch_face(jb);
   __syncthreads();
+  if (kAsync) load_plane(jb + 1);
   face_fluxes(jb);
   T q2prev = 0;
   {
@@ -460,9 +501,11 @@ struct RhsTiledK {
   }
   for (int j = jb; j <= jlast; ++j) {
     if (tid < RT_COUNT) S.rt[j & 3][tid] = R(tid, j);
-    else if (tid < RT_COUNT + 2) fetch_face(j + 1, tid - RT_COUNT);
-    load_plane(j + 1);
+    else if (tid == RT_COUNT) fetch_face(j + 1);
+    if (kAsync) cp_async_wait_all8();  // this thread's copies of plane j + 1
+    else load_plane(j + 1);
     __syncthreads();
+    if (kAsync && j + 1 <= jlast) load_plane(j + 2);
     face_fluxes(j + 1);
     centre_products(j);
     __syncthreads();
@@ -477,8 +520,8 @@ struct RhsTiledK {
     // ---------------- v at face j
     const T sv = P(1, j, tz, tx) + P(1, j + 1, tz, tx);
     const T q2 = sv * sv;  // Q2 of centre j (zero planes beyond the top)
-    const T nvv = (S.fuv[j & 1][tz][tx + 1] - S.fuv[j & 1][tz][tx]) * hidx + (q2 - q2prev) * rt[RT_QIHC] +
-                  (S.fvw[j & 1][tz + 1][tx] - S.fvw[j & 1][tz][tx]) * hidz;
+    const T nvv = (S.fuv[j & 1][tz][tx + 1] - S.fuv[j & 1][tz][tx]) * rt[RT_HXW] + (q2 - q2prev) * rt[RT_QIHC] +
+                  (S.fvw[j & 1][tz + 1][tx] - S.fvw[j & 1][tz][tx]) * rt[RT_HZW];
     q2prev = q2;
     const T v0 = P(1, j, tz, tx);
     T rv_ = nvv + rt[RT_CGY] * (P(3, j, tz, tx) - P(3, j - 1, tz, tx));
@@ -489,11 +532,11 @@ struct RhsTiledK {
     rv_ += rt[RT_CF] * P(1, j + 1, tz, tx);
     rv_ += rt[RT_DF] * v0;
     // ---------------- u at (xf_i, yc_j, zc_k)
-    const T hidy = rt[RT_HIDY];
+    const T hym = rt[RT_HYM], hyp = rt[RT_HYP];
     const T cA = rt[RT_AC], cC = rt[RT_CC], cD = rt[RT_DC];
     const T u0 = P(0, j, tz, tx);
     const T nuu = (S.q1[tz][tx + 1] - S.q1[tz][tx]) * qidx +
-                  (S.fuv[(j + 1) & 1][tz][tx] - S.fuv[j & 1][tz][tx]) * hidy +
+                  S.fuv[(j + 1) & 1][tz][tx] * hyp + S.fuv[j & 1][tz][tx] * hym +
                   (S.fuw[tz + 1][tx] - S.fuw[tz][tx]) * qidz;
     T ru_ = nuu + cb + cgx * (P(3, j, tz, tx) - P(3, j, tz, tx - 1));
     ru_ += cx * (P(0, j, tz, tx + 1) + P(0, j, tz, tx - 1));
@@ -504,7 +547,7 @@ struct RhsTiledK {
     // ---------------- w at (xc_i, yc_j, zf_k)
     const T w0 = P(2, j, tz, tx);
     const T nww = (S.fuw[tz][tx + 1] - S.fuw[tz][tx]) * qidx +
-                  (S.fvw[(j + 1) & 1][tz][tx] - S.fvw[j & 1][tz][tx]) * hidy +
+                  S.fvw[(j + 1) & 1][tz][tx] * hyp + S.fvw[j & 1][tz][tx] * hym +
                   (S.q3[tz + 1][tx] - S.q3[tz][tx]) * qidz;
     T rw_ = nww + cgz * (P(3, j, tz, tx) - P(3, j, tz - 1, tx));
     rw_ += cx * (P(2, j, tz, tx + 1) + P(2, j, tz, tx - 1));
@@ -535,18 +578,21 @@ struct RhsTiledK {
 
 }  // namespace
 
-cudaError_t rhs_set_attributes(int* bps_fp64, int* bps_fp32) {
-  cudaError_t e;
-  if ((e = set_smem_limit<RhsTiledK<double, double, false>>((int)sizeof(RhsTile<double>))) != cudaSuccess ||
-      (e = set_smem_limit<RhsTiledK<double, double, true>>((int)sizeof(RhsTile<double>))) != cudaSuccess ||
-      (e = set_smem_limit<RhsTiledK<float, float, false>>((int)sizeof(RhsTile<float>))) != cudaSuccess ||
-      (e = set_smem_limit<RhsTiledK<float, float, true>>((int)sizeof(RhsTile<float>))) != cudaSuccess)
-    return e;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps_fp64, single_kernel<RhsTiledK<double, double, false>>,
-                                                    RT_X * RT_Z, sizeof(RhsTile<double>));
+template <typename T, bool Dyn>
+cudaError_t rhs_attributes(int* bps) {
+  using K = RhsTiledK<T, T, Dyn>;
+  const cudaError_t e = set_smem_limit<K>((int)sizeof(RhsTile<T>));
   if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps_fp32, single_kernel<RhsTiledK<float, float, false>>,
-                                                       RT_X * RT_Z, sizeof(RhsTile<float>));
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, single_kernel<K>, RT_X * RT_Z, sizeof(RhsTile<T>));
+}
+
+cudaError_t rhs_set_attributes(int* bps) {
+  cudaError_t e;
+  if ((e = rhs_attributes<double, false>(bps + 0)) != cudaSuccess ||
+      (e = rhs_attributes<double, true>(bps + 1)) != cudaSuccess ||
+      (e = rhs_attributes<float, false>(bps + 2)) != cudaSuccess)
+    return e;
+  return rhs_attributes<float, true>(bps + 3);
 }
 
 cudaError_t launch_rhs(ns_ctx* c, int k) {
@@ -555,8 +601,30 @@ cudaError_t launch_rhs(ns_ctx* c, int k) {
 }
 
 template <typename T, bool Dyn>
-cudaError_t emit_tiled(LaunchSink& s, const RhsArgs& a, int jchunk, dim3 grid, dim3 block) {
-  return emit<RhsTiledK<T, T, Dyn>>(s, RhsTiledK<T, T, Dyn>::make(a, jchunk), grid, block, sizeof(RhsTile<T>));
+cudaError_t emit_tiled(LaunchSink& s, const RhsArgs& a) {
+  // split y into chunks (each re-derives one face and two planes) so that the blocks fill whole
+  // waves of the resident capacity: minimise waves * (planes per chunk + prologue).  (Chunks of
+  // equal rows in one single wave, some spanning two tiles, were slower on both forms: neighbouring
+  // tiles then march at different y.)
+  ns_ctx* c = s.c;
+  const int tiles = (a.nx / RT_X) * (a.nz / RT_Z);
+  const int resident = c->num_sms * std::max(c->rhs_bps[(sizeof(T) == 4 ? 2 : 0) + (Dyn ? 1 : 0)], 1);
+  int best_nch = 1;
+  double best = 1e300;
+  for (int nch = 1; nch <= (a.ny + 5) / 6 && nch <= 64; ++nch) {
+    const int jc = (a.ny + nch - 1) / nch;
+    const long nb = (long)tiles * ((a.ny + jc - 1) / jc);
+    const long waves = (nb + resident - 1) / resident;
+    const double cost = (double)waves * (jc + 2.0);
+    if (cost < best - 1e-9) {
+      best = cost;
+      best_nch = nch;
+    }
+  }
+  const int jchunk = (a.ny + best_nch - 1) / best_nch;
+  const int nch = (a.ny + jchunk - 1) / jchunk;
+  return emit<RhsTiledK<T, T, Dyn>>(s, RhsTiledK<T, T, Dyn>::make(a, jchunk), dim3(a.nx / RT_X, a.nz / RT_Z, nch),
+                                    dim3(RT_X, RT_Z), sizeof(RhsTile<T>));
 }
 
 cudaError_t stage_rhs(LaunchSink& s, int k) {
@@ -598,31 +666,11 @@ cudaError_t stage_rhs(LaunchSink& s, int k) {
   a.sk = c->stepk + k;
   a.kc = c->stepk_h[k];
   if (a.nx % RT_X == 0 && a.nz % RT_Z == 0) {
-    // split y into chunks (each re-derives one face and two planes) so that the blocks fill
-    // whole waves of the resident capacity: minimise waves * (planes per chunk + prologue)
-    const int tiles = (a.nx / RT_X) * (a.nz / RT_Z);
-    const int resident = c->num_sms * (c->cfg.precision == NS_MIXED ? c->rhs_bps[1] : c->rhs_bps[0]);
-    int best_nch = 1;
-    double best = 1e300;
-    for (int nch = 1; nch <= (a.ny + 5) / 6 && nch <= 64; ++nch) {
-      const int jc = (a.ny + nch - 1) / nch;
-      const long nb = (long)tiles * ((a.ny + jc - 1) / jc);
-      const long waves = (nb + resident - 1) / resident;
-      const double cost = (double)waves * (jc + 2.0);
-      if (cost < best - 1e-9) {
-        best = cost;
-        best_nch = nch;
-      }
-    }
-    const int jchunk = (a.ny + best_nch - 1) / best_nch;
-    const int nch = (a.ny + jchunk - 1) / jchunk;
-    dim3 grid(a.nx / RT_X, a.nz / RT_Z, nch), block(RT_X, RT_Z);
     if (c->cfg.precision == NS_MIXED)
-      return c->dyn_consts ? emit_tiled<float, true>(s, a, jchunk, grid, block)
-                           : emit_tiled<float, false>(s, a, jchunk, grid, block);
-    // FP64 always reads them from device memory: the register allocation of that variant (80)
-    // is faster than the one with constant-bank operands (64) on this kernel
-    return emit_tiled<double, true>(s, a, jchunk, grid, block);
+      return c->dyn_consts ? emit_tiled<float, true>(s, a) : emit_tiled<float, false>(s, a);
+    // FP64 always reads them from device memory: the register allocation of that variant is
+    // faster than the one with constant-bank operands on this kernel
+    return emit_tiled<double, true>(s, a);
   }
   const long plane = (long)a.nx * (a.ny + 1);
   dim3 grid((unsigned)((plane + 127) / 128), (unsigned)a.nz);

@@ -458,7 +458,7 @@ ns_status ns_init(ns_ctx** out, const ns_config* cfg, const ns_fields* fields, v
     cudaGetDevice(&dev);
     c->num_sms = 152;
     cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev);
-    c->rhs_bps[0] = c->rhs_bps[1] = 1;
+    for (int& b : c->rhs_bps) b = 1;
   }
   if (st == NS_OK) st = build_dt_tables(c);
   // ---------------- x partitioned solver: default P
@@ -510,7 +510,7 @@ ns_status ns_init(ns_ctx** out, const ns_config* cfg, const ns_fields* fields, v
     if (upload_d(c, lamx_d, lx) != cudaSuccess) st = NS_ERR_CUDA;
     if (upload_d(c, lamz_d, lz) != cudaSuccess) st = NS_ERR_CUDA;
     if (st == NS_OK && poisson_set_attributes() != cudaSuccess) st = NS_ERR_CUDA;
-    if (st == NS_OK && rhs_set_attributes(&c->rhs_bps[0], &c->rhs_bps[1]) != cudaSuccess) st = NS_ERR_CUDA;
+    if (st == NS_OK && rhs_set_attributes(c->rhs_bps) != cudaSuccess) st = NS_ERR_CUDA;
     if (st == NS_OK && adi_set_attributes() != cudaSuccess) st = NS_ERR_CUDA;
     if (st == NS_OK && launch_pois_factor(c, lamx_d, lamz_d) != cudaSuccess) st = NS_ERR_CUDA;
     if (st == NS_OK && cudaStreamSynchronize(c->stream) != cudaSuccess) st = NS_ERR_CUDA;

@@ -122,8 +122,15 @@ enum { GC_DY = 0, GC_IDY, GC_HC, GC_IHC, GC_WLO, GC_WHI, GC_AC, GC_CC, GC_AF, GC
 //   AC/CC/DC : cl A_j, cl C_j, -cl (2/dx^2 + 2/dz^2 + A_j + C_j) at centres (AC, CC of GC_*)
 //   AF/CF/DF : the same at interior faces (AF, CF of GC_*)
 //   CGY      : -dt alpha_k / hc_j (pressure gradient at face j)
-//   HIDY     : cn / (2 dy_j),   QIHC : cn / (4 hc_j), with cn = -dt gamma_k
-enum { RT_AC = 0, RT_CC, RT_DC, RT_AF, RT_CF, RT_DF, RT_CGY, RT_HIDY, RT_QIHC, RT_COUNT };
+//   QIHC     : cn / (4 hc_j), with cn = -dt gamma_k
+//   RHO      : WHI / WLO of interior face j (the y-face fluxes are formed as
+//              (f_{j-1} + RHO f_j)(g + g'), i.e. divided by WLO_j; zero off the interior faces)
+//   HYM, HYP : -cn WLO_j / (2 dy_j) and cn WLO_{j+1} / (2 dy_j) at centre j: the weights of those
+//              fluxes on the faces below and above (WLO zero at the walls)
+//   HXW, HZW : cn WLO_j / (2 dx) and cn WLO_j / (2 dz) at interior face j: their weights in the
+//              x and z differences of v
+enum { RT_AC = 0, RT_CC, RT_DC, RT_AF, RT_CF, RT_DF, RT_CGY, RT_QIHC, RT_HYM, RT_HYP, RT_HXW, RT_HZW, RT_RHO,
+       RT_COUNT };
 
 // Constants of the tiled RHS in StepK::kd / kf: quarter and half inverse spacings in x and z times
 // the convection weight cn = -dt gamma_k (the RHS forms and stores N pre-multiplied by cn), cn
@@ -270,7 +277,7 @@ struct ns_ctx {
   size_t dt_xs = 0, dt_ls = 0;
   std::vector<std::pair<size_t, size_t>> dirty;  // (workspace offset, bytes) written while staging
   int num_sms;
-  int rhs_bps[2];           // resident blocks per SM of the tiled RHS (FP64, FP32)
+  int rhs_bps[4];           // resident blocks per SM of the tiled RHS (FP64, FP64 dyn, FP32, FP32 dyn)
   // partitioned x solver
   int P, M, L[3];
   int part_req;             // NS_PART_AUTO / PPT / PDD
@@ -481,7 +488,7 @@ cudaError_t stage_project(LaunchSink& s, int k);
 
 // ... and their single-instance launchers (enqueue on ctx->launch; return the launch error).
 cudaError_t launch_rhs(ns_ctx* c, int k);
-cudaError_t rhs_set_attributes(int* bps_fp64, int* bps_fp32);  // once per device, outside any capture
+cudaError_t rhs_set_attributes(int* bps);  // once per device, outside any capture
 cudaError_t launch_adi_x(ns_ctx* c, int k);
 // ns_autotune; lines = false keeps the default y and z line shapes (batched instances share them)
 ns_status autotune_ctx(ns_ctx* c, bool lines);
