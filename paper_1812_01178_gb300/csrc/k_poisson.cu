@@ -817,6 +817,75 @@ struct TdmaMK {
 //    ahead, so that the FP64 pipe (a warp's instruction takes 64 cycles of an SM sub-partition's
 //    FP64 unit) sets the pace rather than the load latency.  They come first in the launch so
 //    that their longer sweeps overlap the FP32 tiles.
+// Sweeps of the staged y solve's FP64 tiles, each with the one factor plane it reads in shared
+// memory ([ny][sf] doubles: 1/pivot for the forward sweep, c/pivot for the backward one) and the
+// spectrum column d (float, row stride sd).  The same operations as tdma_line: forward
+// prev = (d_j - a_j prev) / pivot_j (the gauge row d_0 = 0), stored rounded to float; backward
+// next = d_j - (c_j / pivot_j) next from the forward sweep's last value, which the forward sweep
+// returns unrounded.  Rows are loaded U ahead into two register sets taking turns.
+template <int U>
+__device__ __forceinline__ double tdma_fwd_s64(float* d, int sd, const double* f, int sf,
+                                               const double* __restrict__ pa, int ny, bool gauge) {
+  float Ad[U] = {}, Bd[U] = {};
+  double Af[U] = {}, Aa[U] = {}, Bf[U] = {}, Ba[U] = {};
+  auto load = [&](int j0, float* D, double* F, double* A) {
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (j0 + u < ny) {
+        D[u] = d[(j0 + u) * sd];
+        F[u] = f[(j0 + u) * sf];
+        A[u] = __ldg(pa + j0 + u);  // a_0 = 0
+      }
+  };
+  double prev = 0.0;
+  auto sweep = [&](int j0, const float* D, const double* F, const double* A) {
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (j0 + u < ny) {
+        const double dj = (gauge && j0 + u == 0) ? 0.0 : f2d(D[u]);  // the gauge row phi_0 = 0
+        prev = fma(-A[u], prev, dj) * F[u];
+        d[(j0 + u) * sd] = d2f_rn(prev);
+      }
+  };
+  load(0, Ad, Af, Aa);
+  for (int j0 = 0; j0 < ny; j0 += 2 * U) {
+    load(j0 + U, Bd, Bf, Ba);
+    sweep(j0, Ad, Af, Aa);
+    load(j0 + 2 * U, Ad, Af, Aa);
+    sweep(j0 + U, Bd, Bf, Ba);
+  }
+  return prev;
+}
+
+template <int U>
+__device__ __forceinline__ void tdma_bwd_s64(float* d, int sd, const double* f, int sf, int ny, double next) {
+  float Ad[U] = {}, Bd[U] = {};
+  double Ac[U] = {}, Bc[U] = {};
+  auto load = [&](int j1, float* D, double* C) {
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (j1 - u >= 0) {
+        D[u] = d[(j1 - u) * sd];
+        C[u] = f[(j1 - u) * sf];
+      }
+  };
+  auto sweep = [&](int j1, const float* D, const double* C) {
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (j1 - u >= 0) {
+        next = fma(-C[u], next, f2d(D[u]));
+        d[(j1 - u) * sd] = d2f_rn(next);
+      }
+  };
+  load(ny - 2, Ad, Ac);
+  for (int j1 = ny - 2; j1 >= 0; j1 -= 2 * U) {
+    load(j1 - U, Bd, Bc);
+    sweep(j1, Ad, Ac);
+    load(j1 - 2 * U, Ad, Ac);
+    sweep(j1 - U, Bd, Bc);
+  }
+}
+
 struct TdmaSK {
   struct Args {
     float2* spec;
@@ -852,7 +921,22 @@ struct TdmaSK {
       cp_async16(reinterpret_cast<float4*>(D + (size_t)j * TL) + r,
                  reinterpret_cast<const float4*>(a.spec + row0 + (long)j * nx) + r);
     }
-    if (!f64) {
+    // FP64 tiles stage their FP64 factor planes one at a time in the float factor region
+    // ([ny][TL] doubles fill ny TL 8 <= 2 ny TL 4 + ny 4 bytes): 1/pivot now, c/pivot after the
+    // forward sweep.  (Read from global memory a few rows ahead instead, each group of rows
+    // waited on the DRAM latency, and these few tiles set the launch's length.)
+    double* F64 = reinterpret_cast<double*>(IP);
+    constexpr int gq = TL * 8 / 16;  // 16-byte pieces per row of TL doubles
+    auto stage64 = [&](const double* src) {
+      for (int q = threadIdx.x; q < ny * gq; q += blockDim.x) {
+        const int j = q / gq, r = q - j * gq;
+        cp_async16(reinterpret_cast<float4*>(F64 + (size_t)j * TL) + r,
+                   reinterpret_cast<const float4*>(src + row0 + (long)j * nx) + r);
+      }
+    };
+    if (f64) {
+      stage64(a.fac64);
+    } else {
       for (int q = threadIdx.x; q < ny * fq; q += blockDim.x) {
         const int j = q / fq, r = q - j * fq;
         cp_async16(reinterpret_cast<float4*>(IP + (size_t)j * TL) + r,
@@ -865,16 +949,22 @@ struct TdmaSK {
     cp_async_commit();
     cp_async_wait<0>();
     __syncthreads();
-    if (threadIdx.x < 2 * TL) {
-      // the sweeps load rows a few ahead into registers (two sets taking turns), so that a line
-      // waits on the arithmetic, not on each row's shared-memory loads
-      const int l = threadIdx.x >> 1, part = threadIdx.x & 1;
-      float* d = reinterpret_cast<float*>(D) + 2 * l + part;  // row stride 2 TL floats
-      if (f64)  // the (0, 0) mode's row 0 is the gauge phi_0 = 0 (factor row 1, 0)
-        tdma_line<float, 8>(d, 2 * TL, a.fac64 + row0 + l, a.fac64 + plane + row0 + l, a.pa64, nx, ny,
-                            kz == 0 && i0 + l == 0);
-      else
-        tdma_line32<false, 8>(d, 2 * TL, IP + l, CP + l, A32, TL, ny);
+    // the sweeps load rows a few ahead into registers (two sets taking turns), so that a line
+    // waits on the arithmetic, not on each row's shared-memory loads
+    const int l = threadIdx.x >> 1, part = threadIdx.x & 1;
+    float* d = reinterpret_cast<float*>(D) + 2 * l + part;  // row stride 2 TL floats
+    if (f64) {
+      double last = 0.0;
+      if (threadIdx.x < 2 * TL)  // the (0, 0) mode's row 0 is the gauge phi_0 = 0 (factor row 1, 0)
+        last = tdma_fwd_s64<8>(d, 2 * TL, F64 + l, TL, a.pa64, ny, kz == 0 && i0 + l == 0);
+      __syncthreads();  // the 1/pivot plane is no longer read
+      stage64(a.fac64 + plane);
+      cp_async_commit();
+      cp_async_wait<0>();
+      __syncthreads();
+      if (threadIdx.x < 2 * TL) tdma_bwd_s64<8>(d, 2 * TL, F64 + l, TL, ny, last);
+    } else if (threadIdx.x < 2 * TL) {
+      tdma_line32<false, 8>(d, 2 * TL, IP + l, CP + l, A32, TL, ny);
     }
     __syncthreads();
     for (int q = threadIdx.x; q < ny * dq; q += blockDim.x) {
@@ -1069,6 +1159,8 @@ struct ProjectK {
 // the real and imaginary parts of v (separated through V_{N-l}), X_l = Re(w_l V_a) + i Re(w_l V_b),
 // w_l = exp(-i pi l / (2N)).  Inverse (unnormalised, N times the DCT-III inverse):
 // V_l = conj(w_l) (X_l - i X_{N-l}) (X_N = 0), v = IFFT(V), x_{2n} = v_n, x_{2n+1} = v_{N-1-n}.
+// twd holds w_l for l < N and then w_l / 2: the forward kernel takes the halved entries, which
+// absorb the 1/2 of the real / imaginary separation exactly (a power of two).
 // ------------------------------------------------------------------------------------------
 template <typename C>
 __global__ void __launch_bounds__(256) dctx_fwd_kernel(C* __restrict__ spec, const C* __restrict__ twx,
@@ -1091,10 +1183,10 @@ __global__ void __launch_bounds__(256) dctx_fwd_kernel(C* __restrict__ spec, con
     const int rr = q / nx, l = q - rr * nx;
     const C vl = V[rr * nx + l];
     const C vn = V[rr * nx + (l == 0 ? 0 : nx - l)];
-    const C w = __ldg(twd + l);
+    const C w = __ldg(twd + nx + l);  // w_l / 2
     using R_ = typename Cplx<C>::R;
-    const R_ ax = (R_)0.5 * (vl.x + vn.x), ay = (R_)0.5 * (vl.y - vn.y);
-    const R_ bx = (R_)0.5 * (vl.y + vn.y), by = (R_)0.5 * (vn.x - vl.x);
+    const R_ ax = vl.x + vn.x, ay = vl.y - vn.y;
+    const R_ bx = vl.y + vn.y, by = vn.x - vl.x;
     g[q] = Cplx<C>::mk(fmaT(w.x, ax, -w.y * ay), fmaT(w.x, bx, -w.y * by));
   }
 }

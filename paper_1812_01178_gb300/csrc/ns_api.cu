@@ -97,12 +97,12 @@ ns_layout make_layout(const ns_config* c) {
   sz[LB_LAMZ] = nzh * 8;
   sz[LB_RTAB] = 3 * al256((size_t)RT_COUNT * (ny + 1) * 8) + 3 * al256((size_t)RT_COUNT * (ny + 1) * 4);
   sz[LB_DOUT] = 3 * al256((ny + 1) * nz * 8) + 256;
-  sz[LB_TWD] = nx * 16;
+  sz[LB_TWD] = nx * 32;
   sz[LB_RCY] = recycle_block_doubles((int)ny) * 8;
   sz[LB_STEPK] = NS_STEPK * sizeof(StepK);
   sz[LB_PTAB] = 9 * al256(line_table_floats(c) * 4);
   sz[LB_TW32] = c->precision == NS_MIXED ? al256(fft_twiddle_doubles((int)nz) * 4) + al256(fft_twiddle_doubles((int)nx) * 4) +
-                                               al256(nx * 8)
+                                               al256(nx * 16)
                                          : 0;
   sz[LB_DT] = al256(sizeof(DtCtl)) + 8 * dt_scratch_doubles((int)nz, x_table_elems(c), line_table_floats(c));
   sz[LB_POIS32] = c->precision == NS_MIXED ? pois32_bytes(nx, ny, nzh) : 0;
@@ -491,10 +491,12 @@ ns_status ns_init(ns_ctx** out, const ns_config* cfg, const ns_fields* fields, v
         lx[q] = (2.0 / (c->dx * c->dx)) * (1.0 - std::cos(2.0 * PI * qq / nx));
       }
     }
-    std::vector<double> td(2 * nx);
+    std::vector<double> td(4 * nx);  // w_l, then w_l / 2 (exact) for the forward transform
     for (int q = 0; q < nx; ++q) {
       td[2 * q] = std::cos(PI * q / (2.0 * nx));
       td[2 * q + 1] = -std::sin(PI * q / (2.0 * nx));
+      td[2 * (nx + q)] = 0.5 * td[2 * q];
+      td[2 * (nx + q) + 1] = 0.5 * td[2 * q + 1];
     }
     if (upload_d(c, c->twd, td) != cudaSuccess) st = NS_ERR_CUDA;
     if (c->pois32) {  // the same tables rounded to float for the FP32 transforms of the mixed form

@@ -242,7 +242,7 @@ struct ns_ctx {
   float* rtabf[3];          // float copies of rtab for the FP32 form
   int bl;                   // inflow / convective outflow in x
   double* dout[3];          // outflow-plane increments of the current sub-step (u, v, w)
-  double2* twd;             // exp(-i pi l / (2 nx)), l < nx: post-twiddles of the x cosine transform
+  double2* twd;             // exp(-i pi l / (2 nx)), l < nx, then the same halved: x cosine transform twiddles
   // the mixed form's Poisson solve: FP32 transforms (twiddles rounded to float) and one FP64
   // refinement (k_poisson.cu); off for FP64 contexts
   bool pois32 = false;
