@@ -806,79 +806,70 @@ struct TdmaMK {
   }
 };
 
-// The same y solve staged in shared memory (nx a multiple of 16): one block per tile of TL = 16
-// consecutive kx of one kz, from a tile list built at init.  The block copies the tile's
-// complex64 rows and a_j into shared memory with every copy in flight at once (cp.async), one
-// warp sweeps the TL lines (real and imaginary part on two lanes) from there, and the block writes
-// the rows back; a line then waits on shared memory, not on one global load per row.
-//  - FP32 tiles (every mode flagged): the float factor planes are staged too; FP32 arithmetic.
-//  - FP64 tiles (the first n64 of the list: the kz = 0 tiles and those holding an ill-conditioned
-//    mode): FP64 arithmetic with the FP64 factors and a_j read from global memory 8 to 16 rows
-//    ahead, so that the FP64 pipe (a warp's instruction takes 64 cycles of an SM sub-partition's
-//    FP64 unit) sets the pace rather than the load latency.  They come first in the launch so
-//    that their longer sweeps overlap the FP32 tiles.
-// Sweeps of the staged y solve's FP64 tiles, each with the one factor plane it reads in shared
-// memory ([ny][sf] doubles: 1/pivot for the forward sweep, c/pivot for the backward one) and the
-// spectrum column d (float, row stride sd).  The same operations as tdma_line: forward
-// prev = (d_j - a_j prev) / pivot_j (the gauge row d_0 = 0), stored rounded to float; backward
-// next = d_j - (c_j / pivot_j) next from the forward sweep's last value, which the forward sweep
-// returns unrounded.  Rows are loaded U ahead into two register sets taking turns.
+// Sweeps of the staged y solve's FP64 tiles over a range of rows, with the factor plane they
+// read staged in shared memory (f[(j - fo) * sf] doubles: 1/pivot for the forward sweep, c/pivot
+// for the backward one) and the spectrum column d (float, row stride sd).  The same operations as
+// tdma_line: forward prev = (d_j - a_j prev) / pivot_j (the gauge row d_0 = 0), stored rounded to
+// float; backward next = d_j - (c_j / pivot_j) next, starting from the forward sweep's last value
+// unrounded.  prev / next carry from one range to the next.  Rows are loaded U ahead into two
+// register sets taking turns.
 template <int U>
-__device__ __forceinline__ double tdma_fwd_s64(float* d, int sd, const double* f, int sf,
-                                               const double* __restrict__ pa, int ny, bool gauge) {
+__device__ __forceinline__ void tdma_fwd_s64(float* d, int sd, const double* f, int fo, int sf,
+                                             const double* __restrict__ pa, int jb, int je, bool gauge,
+                                             double& prev) {
   float Ad[U] = {}, Bd[U] = {};
   double Af[U] = {}, Aa[U] = {}, Bf[U] = {}, Ba[U] = {};
   auto load = [&](int j0, float* D, double* F, double* A) {
 #pragma unroll
     for (int u = 0; u < U; ++u)
-      if (j0 + u < ny) {
+      if (j0 + u < je) {
         D[u] = d[(j0 + u) * sd];
-        F[u] = f[(j0 + u) * sf];
+        F[u] = f[(j0 + u - fo) * sf];
         A[u] = __ldg(pa + j0 + u);  // a_0 = 0
       }
   };
-  double prev = 0.0;
   auto sweep = [&](int j0, const float* D, const double* F, const double* A) {
 #pragma unroll
     for (int u = 0; u < U; ++u)
-      if (j0 + u < ny) {
+      if (j0 + u < je) {
         const double dj = (gauge && j0 + u == 0) ? 0.0 : f2d(D[u]);  // the gauge row phi_0 = 0
         prev = fma(-A[u], prev, dj) * F[u];
         d[(j0 + u) * sd] = d2f_rn(prev);
       }
   };
-  load(0, Ad, Af, Aa);
-  for (int j0 = 0; j0 < ny; j0 += 2 * U) {
+  load(jb, Ad, Af, Aa);
+  for (int j0 = jb; j0 < je; j0 += 2 * U) {
     load(j0 + U, Bd, Bf, Ba);
     sweep(j0, Ad, Af, Aa);
     load(j0 + 2 * U, Ad, Af, Aa);
     sweep(j0 + U, Bd, Bf, Ba);
   }
-  return prev;
 }
 
+// rows jhi down to jlo
 template <int U>
-__device__ __forceinline__ void tdma_bwd_s64(float* d, int sd, const double* f, int sf, int ny, double next) {
+__device__ __forceinline__ void tdma_bwd_s64(float* d, int sd, const double* f, int fo, int sf, int jlo, int jhi,
+                                             double& next) {
   float Ad[U] = {}, Bd[U] = {};
   double Ac[U] = {}, Bc[U] = {};
   auto load = [&](int j1, float* D, double* C) {
 #pragma unroll
     for (int u = 0; u < U; ++u)
-      if (j1 - u >= 0) {
+      if (j1 - u >= jlo) {
         D[u] = d[(j1 - u) * sd];
-        C[u] = f[(j1 - u) * sf];
+        C[u] = f[(j1 - u - fo) * sf];
       }
   };
   auto sweep = [&](int j1, const float* D, const double* C) {
 #pragma unroll
     for (int u = 0; u < U; ++u)
-      if (j1 - u >= 0) {
+      if (j1 - u >= jlo) {
         next = fma(-C[u], next, f2d(D[u]));
         d[(j1 - u) * sd] = d2f_rn(next);
       }
   };
-  load(ny - 2, Ad, Ac);
-  for (int j1 = ny - 2; j1 >= 0; j1 -= 2 * U) {
+  load(jhi, Ad, Ac);
+  for (int j1 = jhi; j1 >= jlo; j1 -= 2 * U) {
     load(j1 - U, Bd, Bc);
     sweep(j1, Ad, Ac);
     load(j1 - 2 * U, Ad, Ac);
@@ -886,22 +877,96 @@ __device__ __forceinline__ void tdma_bwd_s64(float* d, int sd, const double* f, 
   }
 }
 
+// The FP32 sweep of one mode from its staged 1/pivot column (ip, stride sip: the FP64 factor
+// rounded to float) and rows[j] = (a_j, c_j, ., .) in float (a_0 = 0, c_{ny-1} = 0): the forward
+// sweep as tdma_line32, the backward one with c_j / pivot_j formed as c_j * ip_j in FP32 (one
+// rounding more than the stored factor, which saves staging a second factor plane).
+template <int U>
+__device__ __forceinline__ void tdma_line32_ip(float* d, int sd, const float* ip, int sip, const float4* rows,
+                                               int ny) {
+  float Ad[U] = {}, Bd[U] = {}, Af[U] = {}, Bf[U] = {};
+  float4 Ar[U] = {}, Br[U] = {};
+  auto load_f = [&](int j0, float* D, float* F, float4* R) {
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (j0 + u < ny) {
+        D[u] = d[(j0 + u) * sd];
+        F[u] = ip[(j0 + u) * sip];
+        R[u] = rows[j0 + u];
+      }
+  };
+  float prev = 0.0f;
+  auto sweep_f = [&](int j0, const float* D, const float* F, const float4* R) {
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (j0 + u < ny) {
+        prev = __fmul_rn(__fmaf_rn(-R[u].x, prev, D[u]), F[u]);
+        d[(j0 + u) * sd] = prev;
+      }
+  };
+  load_f(0, Ad, Af, Ar);
+  for (int j0 = 0; j0 < ny; j0 += 2 * U) {
+    load_f(j0 + U, Bd, Bf, Br);
+    sweep_f(j0, Ad, Af, Ar);
+    load_f(j0 + 2 * U, Ad, Af, Ar);
+    sweep_f(j0 + U, Bd, Bf, Br);
+  }
+  float next = prev;
+  auto load_b = [&](int j1, float* D, float* F, float4* R) {
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (j1 - u >= 0) {
+        D[u] = d[(j1 - u) * sd];
+        F[u] = ip[(j1 - u) * sip];
+        R[u] = rows[j1 - u];
+      }
+  };
+  auto sweep_b = [&](int j1, const float* D, const float* F, const float4* R) {
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (j1 - u >= 0) {
+        next = __fmaf_rn(-__fmul_rn(R[u].y, F[u]), next, D[u]);
+        d[(j1 - u) * sd] = next;
+      }
+  };
+  load_b(ny - 2, Ad, Af, Ar);
+  for (int j1 = ny - 2; j1 >= 0; j1 -= 2 * U) {
+    load_b(j1 - U, Bd, Bf, Br);
+    sweep_b(j1, Ad, Af, Ar);
+    load_b(j1 - 2 * U, Ad, Af, Ar);
+    sweep_b(j1 - U, Bd, Bf, Br);
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// Staged y solve of the mixed form: a block of two warps takes a tile of TL consecutive kx of one
+// kz.  The tile's spectrum columns, [ny][TL] complex64, are copied into shared memory (cp.async),
+// one warp sweeps the TL lines (a lane per real / imaginary part) and the tile is written back.
+// FP32 tiles (every mode kz > 0 with Skeel condition <= NS_POIS_FP32_KAPPA) also stage the float
+// 1/pivot plane and form c/pivot from it (tdma_line32_ip).  (Factors formed in FP32 on the way,
+// with no plane staged, lose accuracy in proportion to the Skeel condition: about 5e-6 instead of
+// 2e-7 at 3600 on the stretched channel grid.)  FP64 tiles (kz = 0 and the ill-conditioned
+// lowest modes; the n64 tiles first in the launch) read the FP64 factor planes, staged in shared
+// memory half a plane at a time: 1/pivot rows [0, hy), [hy, ny), then c/pivot rows [hy, ny),
+// [0, hy).
+// ------------------------------------------------------------------------------------------
 struct TdmaSK {
   struct Args {
     float2* spec;
-    const float* fac32;   // 1/pivot and c/pivot planes in float, nzh * ny * nx each
-    const double* fac64;  // the same in FP64
-    const float* pa32;    // a_j
-    const double* pa64;
-    const int* tiles;     // tile q: kz * (nx / TL) + x tile; the n64 FP64 tiles first
+    const double* fac64;   // 1/pivot and c/pivot planes in FP64, nzh * ny * nx each
+    const float* fac32;    // 1/pivot in float, nzh * ny * nx
+    const float4* rows32;  // (a_j, c_j, -(a_j + c_j), 0) in float
+    const double* pa64;    // a_j
+    const int* tiles;      // tile q: kz * (nx / TL) + x tile; the n64 FP64 tiles first
     int n64;
     int nx, ny, nzh;
   };
   static constexpr int TL = 16;
   static constexpr int kThreads = 64;
-  static constexpr int kMinBlocks = 4;
-  // D [ny][TL] float2, IP and CP [ny][TL] float, a_j [ny] float
-  static size_t smem_bytes(int ny) { return (size_t)ny * TL * 16 + (size_t)ny * 4; }
+  static constexpr int kMinBlocks = 5;
+  // D [ny][TL] float2, then one region of ny * 80 bytes: FP32 tiles' 1/pivot [ny][TL] float and
+  // rows [ny] float4; FP64 tiles' half factor plane [(ny + 1) / 2][TL] double
+  static size_t smem_bytes(int ny) { return (size_t)ny * TL * 8 + (size_t)ny * 80; }
   static __device__ __forceinline__ void run(const Args& a, const dim3 bid_, const dim3) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int nx = a.nx, ny = a.ny;
@@ -909,62 +974,65 @@ struct TdmaSK {
     const int tile = __ldg(a.tiles + bid_.x);
     const bool f64 = (int)bid_.x < a.n64;
     const int kz = tile / ntx, i0 = (tile - kz * ntx) * TL;
-    float2* D = reinterpret_cast<float2*>(smem_raw);          // [ny][TL]
-    float* IP = reinterpret_cast<float*>(D + (size_t)ny * TL);  // [ny][TL]
-    float* CP = IP + (size_t)ny * TL;                           // [ny][TL]
-    float* A32 = CP + (size_t)ny * TL;                          // [ny]
+    float2* D = reinterpret_cast<float2*>(smem_raw);                     // [ny][TL]
+    unsigned char* X = smem_raw + (size_t)ny * TL * 8;                   // the region
+    float* IP = reinterpret_cast<float*>(X);                             // [ny][TL]
+    float4* ROWS = reinterpret_cast<float4*>(X + (size_t)ny * TL * 4);   // [ny]
+    double* F64 = reinterpret_cast<double*>(X);                          // [(ny + 1) / 2][TL]
     const long plane = (long)a.nzh * ny * nx;
     const long row0 = (long)kz * ny * nx + i0;
-    constexpr int dq = TL * 8 / 16, fq = TL * 4 / 16;  // 16-byte pieces per row
+    constexpr int dq = TL * 8 / 16, gq = TL * 8 / 16, fq = TL * 4 / 16;  // 16-byte pieces per row of D, F64, IP
     for (int q = threadIdx.x; q < ny * dq; q += blockDim.x) {
       const int j = q / dq, r = q - j * dq;
       cp_async16(reinterpret_cast<float4*>(D + (size_t)j * TL) + r,
                  reinterpret_cast<const float4*>(a.spec + row0 + (long)j * nx) + r);
     }
-    // FP64 tiles stage their FP64 factor planes one at a time in the float factor region
-    // ([ny][TL] doubles fill ny TL 8 <= 2 ny TL 4 + ny 4 bytes): 1/pivot now, c/pivot after the
-    // forward sweep.  (Read from global memory a few rows ahead instead, each group of rows
-    // waited on the DRAM latency, and these few tiles set the launch's length.)
-    double* F64 = reinterpret_cast<double*>(IP);
-    constexpr int gq = TL * 8 / 16;  // 16-byte pieces per row of TL doubles
-    auto stage64 = [&](const double* src) {
-      for (int q = threadIdx.x; q < ny * gq; q += blockDim.x) {
+    // rows [j0, j1) of an FP64 factor plane into F64
+    auto stage64 = [&](const double* src, int j0, int j1) {
+      for (int q = threadIdx.x; q < (j1 - j0) * gq; q += blockDim.x) {
         const int j = q / gq, r = q - j * gq;
         cp_async16(reinterpret_cast<float4*>(F64 + (size_t)j * TL) + r,
-                   reinterpret_cast<const float4*>(src + row0 + (long)j * nx) + r);
+                   reinterpret_cast<const float4*>(src + row0 + (long)(j0 + j) * nx) + r);
       }
     };
+    auto landed = [&]() {
+      cp_async_commit();
+      cp_async_wait<0>();
+      __syncthreads();
+    };
+    const int hy = (ny + 1) >> 1;
     if (f64) {
-      stage64(a.fac64);
+      stage64(a.fac64, 0, hy);
     } else {
       for (int q = threadIdx.x; q < ny * fq; q += blockDim.x) {
         const int j = q / fq, r = q - j * fq;
         cp_async16(reinterpret_cast<float4*>(IP + (size_t)j * TL) + r,
                    reinterpret_cast<const float4*>(a.fac32 + row0 + (long)j * nx) + r);
-        cp_async16(reinterpret_cast<float4*>(CP + (size_t)j * TL) + r,
-                   reinterpret_cast<const float4*>(a.fac32 + plane + row0 + (long)j * nx) + r);
       }
-      for (int j = threadIdx.x; j < ny; j += blockDim.x) A32[j] = __ldg(a.pa32 + j);
+      for (int j = threadIdx.x; j < ny; j += blockDim.x) cp_async16(ROWS + j, a.rows32 + j);
     }
-    cp_async_commit();
-    cp_async_wait<0>();
-    __syncthreads();
-    // the sweeps load rows a few ahead into registers (two sets taking turns), so that a line
-    // waits on the arithmetic, not on each row's shared-memory loads
+    landed();
     const int l = threadIdx.x >> 1, part = threadIdx.x & 1;
     float* d = reinterpret_cast<float*>(D) + 2 * l + part;  // row stride 2 TL floats
+    const bool sweeper = threadIdx.x < 2 * TL;
     if (f64) {
-      double last = 0.0;
-      if (threadIdx.x < 2 * TL)  // the (0, 0) mode's row 0 is the gauge phi_0 = 0 (factor row 1, 0)
-        last = tdma_fwd_s64<8>(d, 2 * TL, F64 + l, TL, a.pa64, ny, kz == 0 && i0 + l == 0);
-      __syncthreads();  // the 1/pivot plane is no longer read
-      stage64(a.fac64 + plane);
-      cp_async_commit();
-      cp_async_wait<0>();
+      const bool gauge = kz == 0 && i0 + l == 0;  // the (0, 0) mode's row 0: phi_0 = 0
+      double v = 0.0;
+      if (sweeper) tdma_fwd_s64<8>(d, 2 * TL, F64 + l, 0, TL, a.pa64, 0, hy, gauge, v);
       __syncthreads();
-      if (threadIdx.x < 2 * TL) tdma_bwd_s64<8>(d, 2 * TL, F64 + l, TL, ny, last);
-    } else if (threadIdx.x < 2 * TL) {
-      tdma_line32<false, 8>(d, 2 * TL, IP + l, CP + l, A32, TL, ny);
+      stage64(a.fac64, hy, ny);
+      landed();
+      if (sweeper) tdma_fwd_s64<8>(d, 2 * TL, F64 + l, hy, TL, a.pa64, hy, ny, gauge, v);
+      __syncthreads();
+      stage64(a.fac64 + plane, hy, ny);
+      landed();
+      if (sweeper) tdma_bwd_s64<8>(d, 2 * TL, F64 + l, hy, TL, hy, ny - 2, v);
+      __syncthreads();
+      stage64(a.fac64 + plane, 0, hy);
+      landed();
+      if (sweeper) tdma_bwd_s64<8>(d, 2 * TL, F64 + l, 0, TL, 0, min(hy - 1, ny - 2), v);
+    } else if (sweeper) {
+      tdma_line32_ip<8>(d, 2 * TL, IP + l, TL, ROWS, ny);
     }
     __syncthreads();
     for (int q = threadIdx.x; q < ny * dq; q += blockDim.x) {
@@ -1601,7 +1669,7 @@ cudaError_t emit_tdmam(LaunchSink& s) {
   const PoisShape q = pois_shape(c);
   if (c->pois_tiles)  // staged: the FP64 tiles, then the FP32 ones, in one launch
     return emit<TdmaSK>(s,
-                        TdmaSK::Args{sp32(c), c->pois_f32, reinterpret_cast<const double*>(c->pois), c->pois_pa32,
+                        TdmaSK::Args{sp32(c), reinterpret_cast<const double*>(c->pois), c->pois_f32, c->pois_rows32,
                                      c->gc + GC_PA * (q.ny + 1), c->pois_tiles, c->ntile64, q.nx, q.ny, c->nzh},
                         dim3((unsigned)(c->ntile64 + c->ntile32)), dim3(TdmaSK::kThreads), TdmaSK::smem_bytes(q.ny));
   return emit<TdmaMK>(s, TdmaMK::Args{sp32(c), c->pois, c->gc, q.nx, q.ny, c->nzh, c->pois_f32, c->pois_pa32, c->pois_mode},

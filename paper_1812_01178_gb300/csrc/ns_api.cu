@@ -434,6 +434,8 @@ ns_status ns_init(ns_ctx** out, const ns_config* cfg, const ns_fields* fields, v
     c->pois_pa32 = (float*)(p32 + planes);
     c->pois_mode = (unsigned char*)(p32 + planes + al256((size_t)ny * 4));
     c->pois_tiles = (int*)(p32 + planes + al256((size_t)ny * 4) + al256((size_t)c->nzh * nx));
+    c->pois_rows32 = (float4*)(p32 + planes + al256((size_t)ny * 4) + al256((size_t)c->nzh * nx) +
+                               al256((size_t)c->nzh * (nx / 8 + 1) * 4));
   }
   double* lamz_d = (double*)(base + c->lay.off[LB_LAMZ]);
 
@@ -502,7 +504,15 @@ ns_status ns_init(ns_ctx** out, const ns_config* cfg, const ns_fields* fields, v
     if (c->pois32) {  // the same tables rounded to float for the FP32 transforms of the mixed form
       const std::vector<float> fz(tw.begin(), tw.end()), fx(tx.begin(), tx.end()), fd(td.begin(), td.end());
       const std::vector<float> pa32(gc.begin() + (size_t)GC_PA * G, gc.begin() + (size_t)GC_PA * G + ny);
-      if (upload_raw(c, c->twz32, fz.data(), fz.size() * 4) != cudaSuccess ||
+      std::vector<float> rows32(4 * (size_t)ny, 0.0f);  // (a_j, c_j, -(a_j + c_j), 0)
+      for (int j = 0; j < ny; ++j) {
+        const double aj = gc[(size_t)GC_PA * G + j], cj = gc[(size_t)GC_PC * G + j];
+        rows32[4 * j] = (float)aj;
+        rows32[4 * j + 1] = (float)cj;
+        rows32[4 * j + 2] = (float)(-(aj + cj));
+      }
+      if (upload_raw(c, c->pois_rows32, rows32.data(), rows32.size() * 4) != cudaSuccess ||
+          upload_raw(c, c->twz32, fz.data(), fz.size() * 4) != cudaSuccess ||
           upload_raw(c, c->twx32, fx.data(), fx.size() * 4) != cudaSuccess ||
           upload_raw(c, c->twd32, fd.data(), fd.size() * 4) != cudaSuccess ||
           upload_raw(c, c->pois_pa32, pa32.data(), pa32.size() * 4) != cudaSuccess)

@@ -247,8 +247,9 @@ struct ns_ctx {
   // refinement (k_poisson.cu); off for FP64 contexts
   bool pois32 = false;
   float2 *twz32 = nullptr, *twx32 = nullptr, *twd32 = nullptr;
-  // its y solves: the FP64 factors rounded to float (two planes), a_j in float, and one flag per
-  // (kz, kx) mode, 1 where the solve runs in FP32 (pois_factor_kernel)
+  // its y solves: the FP64 factors rounded to float (two planes; the staged form reads only the
+  // first), a_j in float, and one flag per (kz, kx) mode, 1 where the solve runs in FP32
+  // (pois_factor_kernel)
   float* pois_f32 = nullptr;
   float* pois_pa32 = nullptr;
   unsigned char* pois_mode = nullptr;
@@ -257,6 +258,8 @@ struct ns_ctx {
   // null: the register form
   int* pois_tiles = nullptr;
   int ntile32 = 0, ntile64 = 0;
+  // the staged FP32 sweeps' rows (a_j, c_j, -(a_j + c_j), 0) in float (they form c/pivot)
+  float4* pois_rows32 = nullptr;
   double* flux;             // [0]: inflow flux, [1]: last outflow correction (diagnostics)
   unsigned long long* rate; // bits of the convective rate of ns_convective_rate (in the flux block)
   std::vector<double> gc_h; // host copy of the grid coefficients (tables are rebuilt when dt changes)
@@ -557,7 +560,7 @@ constexpr double NS_POIS_FP32_KAPPA = 4096.0;
 // bytes of the mixed form's FP32 y-solve block: two float factor planes, a_j, the mode flags
 inline size_t pois32_bytes(size_t nx, size_t ny, size_t nzh) {
   auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
-  return al(2 * nzh * ny * nx * 4) + al(ny * 4) + al(nzh * nx) + al(nzh * (nx / 8 + 1) * 4);
+  return al(2 * nzh * ny * nx * 4) + al(ny * 4) + al(nzh * nx) + al(nzh * (nx / 8 + 1) * 4) + al(ny * 16);
 }
 // largest dynamic shared memory of one block (227 KB)
 constexpr int NS_SMEM_MAX = 227 * 1024;

@@ -46,9 +46,11 @@ def fp32_modes(g, bl):
     return kap <= KAPPA_MAX, kap
 
 
-def thomas32(a, b, c, d):
+def thomas32(a, b, c, d, cp_from_ip=False):
     """Thomas sweeps in FP32 on complex64 data, with the factors 1/pivot and c/pivot formed in
-    FP64 and rounded to float.  a, b, c: (..., ny) real; d: (..., ny) complex."""
+    FP64 and rounded to float.  a, b, c: (..., ny) real; d: (..., ny) complex.  cp_from_ip: the
+    staged form's backward factor, c_j rounded to float times the float 1/pivot (rounded again),
+    instead of the rounded FP64 c/pivot."""
     ny = d.shape[-1]
     ip = np.empty(b.shape)
     cp = np.empty(b.shape)
@@ -58,6 +60,8 @@ def thomas32(a, b, c, d):
         prev = c[..., j] * ip[..., j]
         cp[..., j] = prev
     ip, cp, a32 = ip.astype(np.float32), cp.astype(np.float32), a.astype(np.float32)
+    if cp_from_ip:
+        cp = (np.asarray(c, dtype=np.float32) * ip).astype(np.float32)
     x = d.astype(np.complex64)
     p = np.zeros(d.shape[:-1], np.complex64)
     for j in range(ny):

@@ -33,7 +33,7 @@ def _poisson(g, rhs, fp32, y32=None):
     d[0, 0, 0] = 0.0
     ph = O.thomas(A, B, C, d)
     if y32 is not None:
-        ph[y32] = PM.thomas32(A[y32], B[y32], C[y32], d[y32])
+        ph[y32] = PM.thomas32(A[y32], B[y32], C[y32], d[y32], cp_from_ip=True)  # as the staged form
     ph = np.moveaxis(ph, -1, 1)
     if fp32:
         ph = ph.astype(np.complex64)
@@ -83,8 +83,10 @@ def test_fp32_transforms_need_one_fp64_refinement(low, y32):
 def test_skeel_condition_by_one_solve_and_fp32_line_solves(bl):
     """The mode selection's two parts on the stretched y grids of the 256x192x256 channel and of
     the 1024x256x512 boundary layer: (1) kappa by one Thomas solve equals the definition
-    || |A^-1| |A| 1 ||_inf by a dense inverse; (2) the FP32 sweep with rounded FP64 factors solves
-    a mode's system to the FP32 level, and one refinement on the FP64 residual to the FP64 level;
+    || |A^-1| |A| 1 ||_inf by a dense inverse; (2) the FP32 sweep with rounded FP64 factors (c/pivot
+    stored, or formed from the float 1/pivot as the staged form does) solves a mode's system to the
+    FP32 level, and one refinement on the FP64 residual to the FP64 level (1e-12 where kappa <=
+    4096);
     (3) kappa falls with the wavenumber, so the FP64 modes are the lowest ones."""
     if bl:
         g = O.Grid.from_case(I.boundary_layer_case(1024, 256, 512))
@@ -104,11 +106,12 @@ def test_skeel_condition_by_one_solve_and_fp32_line_solves(bl):
         d = rng.standard_normal(g.ny) + 1j * rng.standard_normal(g.ny)
         x = np.linalg.solve(A, d)
         Bd = (-(a + c) - L)[None, :]
-        x1 = PM.thomas32(a[None, :], Bd, c[None, :], d[None, :])[0].astype(np.complex128)
-        x2 = x1 + PM.thomas32(a[None, :], Bd, c[None, :], (d - A @ x1)[None, :])[0].astype(np.complex128)
-        e1 = np.abs(x1 - x).max() / np.abs(x).max()
-        e2 = np.abs(x2 - x).max() / np.abs(x).max()
-        assert 1e-9 < e1 < 2e-6, (kz, kx, e1)
-        assert e2 < 1e-11, (kz, kx, e2)
+        for from_ip in (False, True):  # the register form's stored c/pivot, the staged form's c * (1/pivot)
+            x1 = PM.thomas32(a[None, :], Bd, c[None, :], d[None, :], from_ip)[0].astype(np.complex128)
+            x2 = x1 + PM.thomas32(a[None, :], Bd, c[None, :], (d - A @ x1)[None, :], from_ip)[0].astype(np.complex128)
+            e1 = np.abs(x1 - x).max() / np.abs(x).max()
+            e2 = np.abs(x2 - x).max() / np.abs(x).max()
+            assert 1e-9 < e1 < 2e-6, (kz, kx, from_ip, e1)
+            assert e2 < (1e-11 if k1 > PM.KAPPA_MAX else 1e-12), (kz, kx, from_ip, e2)
     assert all(k0 > k1 for k0, k1 in zip(kaps, kaps[1:]))
     assert kaps[0] > 1e4 and kaps[-1] < PM.KAPPA_MAX
