@@ -806,35 +806,62 @@ struct TdmaMK {
   }
 };
 
+// Float-float values h + l (|l| <= ulp(h) / 2 once renormalised), for the staged y solve's FP64
+// tiles: the recurrences of those ill-conditioned modes carried in about 48 bits on the FP32 pipe
+// (a warp's FP64 instruction streams through a unit of two lanes per clock, and a sweep's
+// dependent FP64 operations set the launch's length).
+struct FF {
+  float h, l;
+};
+// Fast2Sum (|s| >= |e|, or s = 0)
+__device__ __forceinline__ FF ff_norm(float s, float e) {
+  const float h = __fadd_rn(s, e);
+  return FF{h, __fsub_rn(e, __fsub_rn(h, s))};
+}
+// a b: the exact product of the high parts (TwoProd) plus the cross terms
+__device__ __forceinline__ FF ff_mul(FF a, FF b) {
+  float p, e;
+  ff_two_prod(a.h, b.h, p, e);
+  e = __fmaf_rn(a.h, b.l, __fmaf_rn(a.l, b.h, e));
+  return ff_norm(p, e);
+}
+// x - b for a float x
+__device__ __forceinline__ FF ff_sub(float x, FF b) {
+  float s, e;
+  ff_two_sum(x, -b.h, s, e);
+  return ff_norm(s, __fsub_rn(e, b.l));
+}
+
 // Sweeps of the staged y solve's FP64 tiles over a range of rows, with the factor plane they
-// read staged in shared memory (f[(j - fo) * sf] doubles: 1/pivot for the forward sweep, c/pivot
-// for the backward one) and the spectrum column d (float, row stride sd).  The same operations as
-// tdma_line: forward prev = (d_j - a_j prev) / pivot_j (the gauge row d_0 = 0), stored rounded to
-// float; backward next = d_j - (c_j / pivot_j) next, starting from the forward sweep's last value
-// unrounded.  prev / next carry from one range to the next.  Rows are loaded U ahead into two
-// register sets taking turns.
+// read staged in shared memory as float-float pairs (f[(j - fo) * sf]: 1/pivot for the forward
+// sweep, c/pivot for the backward one), a_j as rows[j].x + rows[j].w, and the spectrum column d
+// (float, row stride sd).  Forward prev = (d_j - a_j prev) / pivot_j (the gauge row d_0 = 0),
+// backward next = d_j - (c_j / pivot_j) next from the forward sweep's last value; each row is
+// stored rounded to float (the high part).  prev / next carry from one range to the next.  Rows
+// are loaded U ahead into two register sets taking turns.
 template <int U>
-__device__ __forceinline__ void tdma_fwd_s64(float* d, int sd, const double* f, int fo, int sf,
-                                             const double* __restrict__ pa, int jb, int je, bool gauge,
-                                             double& prev) {
+__device__ __forceinline__ void tdma_fwd_ff(float* d, int sd, const float2* f, int fo, int sf, const float4* rows,
+                                            int jb, int je, bool gauge, FF& prev) {
   float Ad[U] = {}, Bd[U] = {};
-  double Af[U] = {}, Aa[U] = {}, Bf[U] = {}, Ba[U] = {};
-  auto load = [&](int j0, float* D, double* F, double* A) {
+  float2 Af[U] = {}, Bf[U] = {}, Aa[U] = {}, Ba[U] = {};
+  auto load = [&](int j0, float* D, float2* F, float2* A) {
 #pragma unroll
     for (int u = 0; u < U; ++u)
       if (j0 + u < je) {
         D[u] = d[(j0 + u) * sd];
         F[u] = f[(j0 + u - fo) * sf];
-        A[u] = __ldg(pa + j0 + u);  // a_0 = 0
+        const float4 r = rows[j0 + u];  // a_0 = 0
+        A[u] = make_float2(r.x, r.w);
       }
   };
-  auto sweep = [&](int j0, const float* D, const double* F, const double* A) {
+  auto sweep = [&](int j0, const float* D, const float2* F, const float2* A) {
 #pragma unroll
     for (int u = 0; u < U; ++u)
       if (j0 + u < je) {
-        const double dj = (gauge && j0 + u == 0) ? 0.0 : f2d(D[u]);  // the gauge row phi_0 = 0
-        prev = fma(-A[u], prev, dj) * F[u];
-        d[(j0 + u) * sd] = d2f_rn(prev);
+        const float dj = (gauge && j0 + u == 0) ? 0.0f : D[u];  // the gauge row phi_0 = 0
+        const FF t = ff_sub(dj, ff_mul(FF{A[u].x, A[u].y}, prev));
+        prev = ff_mul(t, FF{F[u].x, F[u].y});
+        d[(j0 + u) * sd] = prev.h;
       }
   };
   load(jb, Ad, Af, Aa);
@@ -848,11 +875,11 @@ __device__ __forceinline__ void tdma_fwd_s64(float* d, int sd, const double* f, 
 
 // rows jhi down to jlo
 template <int U>
-__device__ __forceinline__ void tdma_bwd_s64(float* d, int sd, const double* f, int fo, int sf, int jlo, int jhi,
-                                             double& next) {
+__device__ __forceinline__ void tdma_bwd_ff(float* d, int sd, const float2* f, int fo, int sf, int jlo, int jhi,
+                                            FF& next) {
   float Ad[U] = {}, Bd[U] = {};
-  double Ac[U] = {}, Bc[U] = {};
-  auto load = [&](int j1, float* D, double* C) {
+  float2 Ac[U] = {}, Bc[U] = {};
+  auto load = [&](int j1, float* D, float2* C) {
 #pragma unroll
     for (int u = 0; u < U; ++u)
       if (j1 - u >= jlo) {
@@ -860,12 +887,12 @@ __device__ __forceinline__ void tdma_bwd_s64(float* d, int sd, const double* f, 
         C[u] = f[(j1 - u - fo) * sf];
       }
   };
-  auto sweep = [&](int j1, const float* D, const double* C) {
+  auto sweep = [&](int j1, const float* D, const float2* C) {
 #pragma unroll
     for (int u = 0; u < U; ++u)
       if (j1 - u >= jlo) {
-        next = fma(-C[u], next, f2d(D[u]));
-        d[(j1 - u) * sd] = d2f_rn(next);
+        next = ff_sub(D[u], ff_mul(FF{C[u].x, C[u].y}, next));
+        d[(j1 - u) * sd] = next.h;
       }
   };
   load(jhi, Ad, Ac);
@@ -947,16 +974,16 @@ __device__ __forceinline__ void tdma_line32_ip(float* d, int sd, const float* ip
 // with no plane staged, lose accuracy in proportion to the Skeel condition: about 5e-6 instead of
 // 2e-7 at 3600 on the stretched channel grid.)  FP64 tiles (kz = 0 and the ill-conditioned
 // lowest modes; the n64 tiles first in the launch) read the FP64 factor planes, staged in shared
-// memory half a plane at a time: 1/pivot rows [0, hy), [hy, ny), then c/pivot rows [hy, ny),
-// [0, hy).
+// memory half a plane at a time (1/pivot rows [0, hy), [hy, ny), then c/pivot rows [hy, ny),
+// [0, hy)) and split there into float-float pairs, and sweep in float-float arithmetic
+// (tdma_fwd_ff / tdma_bwd_ff).
 // ------------------------------------------------------------------------------------------
 struct TdmaSK {
   struct Args {
     float2* spec;
     const double* fac64;   // 1/pivot and c/pivot planes in FP64, nzh * ny * nx each
     const float* fac32;    // 1/pivot in float, nzh * ny * nx
-    const float4* rows32;  // (a_j, c_j, -(a_j + c_j), 0) in float
-    const double* pa64;    // a_j
+    const float4* rows32;  // (a_j, c_j, -(a_j + c_j), a_j - (float)a_j) in float
     const int* tiles;      // tile q: kz * (nx / TL) + x tile; the n64 FP64 tiles first
     int n64;
     int nx, ny, nzh;
@@ -964,9 +991,10 @@ struct TdmaSK {
   static constexpr int TL = 16;
   static constexpr int kThreads = 64;
   static constexpr int kMinBlocks = 5;
-  // D [ny][TL] float2, then one region of ny * 80 bytes: FP32 tiles' 1/pivot [ny][TL] float and
-  // rows [ny] float4; FP64 tiles' half factor plane [(ny + 1) / 2][TL] double
-  static size_t smem_bytes(int ny) { return (size_t)ny * TL * 8 + (size_t)ny * 80; }
+  // D [ny][TL] float2, then one region of ny * 80 + 64 bytes: FP32 tiles' 1/pivot [ny][TL] float
+  // and rows [ny] float4; FP64 tiles' half factor plane [(ny + 1) / 2][TL] double (then float2
+  // pairs in place) and rows [ny] float4
+  static size_t smem_bytes(int ny) { return (size_t)ny * TL * 8 + (size_t)ny * 80 + 64; }
   static __device__ __forceinline__ void run(const Args& a, const dim3 bid_, const dim3) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int nx = a.nx, ny = a.ny;
@@ -979,6 +1007,8 @@ struct TdmaSK {
     float* IP = reinterpret_cast<float*>(X);                             // [ny][TL]
     float4* ROWS = reinterpret_cast<float4*>(X + (size_t)ny * TL * 4);   // [ny]
     double* F64 = reinterpret_cast<double*>(X);                          // [(ny + 1) / 2][TL]
+    float2* F2 = reinterpret_cast<float2*>(X);                           // the same, split
+    float4* ROWS64 = reinterpret_cast<float4*>(X + (size_t)((ny + 1) >> 1) * TL * 8);  // [ny]
     const long plane = (long)a.nzh * ny * nx;
     const long row0 = (long)kz * ny * nx + i0;
     constexpr int dq = TL * 8 / 16, gq = TL * 8 / 16, fq = TL * 4 / 16;  // 16-byte pieces per row of D, F64, IP
@@ -1000,9 +1030,20 @@ struct TdmaSK {
       cp_async_wait<0>();
       __syncthreads();
     };
+    // the staged rows [0, n) of F64 split in place into float-float pairs (x = h + l to about
+    // 2^-48 of x)
+    auto split = [&](int n) {
+      for (int q = threadIdx.x; q < n * TL; q += blockDim.x) {
+        const double x = F64[q];
+        const float h = __double2float_rn(x);
+        F2[q] = make_float2(h, __double2float_rn(x - (double)h));
+      }
+      __syncthreads();
+    };
     const int hy = (ny + 1) >> 1;
     if (f64) {
       stage64(a.fac64, 0, hy);
+      for (int j = threadIdx.x; j < ny; j += blockDim.x) cp_async16(ROWS64 + j, a.rows32 + j);
     } else {
       for (int q = threadIdx.x; q < ny * fq; q += blockDim.x) {
         const int j = q / fq, r = q - j * fq;
@@ -1017,20 +1058,24 @@ struct TdmaSK {
     const bool sweeper = threadIdx.x < 2 * TL;
     if (f64) {
       const bool gauge = kz == 0 && i0 + l == 0;  // the (0, 0) mode's row 0: phi_0 = 0
-      double v = 0.0;
-      if (sweeper) tdma_fwd_s64<8>(d, 2 * TL, F64 + l, 0, TL, a.pa64, 0, hy, gauge, v);
+      FF v{0.0f, 0.0f};
+      split(hy);
+      if (sweeper) tdma_fwd_ff<8>(d, 2 * TL, F2 + l, 0, TL, ROWS64, 0, hy, gauge, v);
       __syncthreads();
       stage64(a.fac64, hy, ny);
       landed();
-      if (sweeper) tdma_fwd_s64<8>(d, 2 * TL, F64 + l, hy, TL, a.pa64, hy, ny, gauge, v);
+      split(ny - hy);
+      if (sweeper) tdma_fwd_ff<8>(d, 2 * TL, F2 + l, hy, TL, ROWS64, hy, ny, gauge, v);
       __syncthreads();
       stage64(a.fac64 + plane, hy, ny);
       landed();
-      if (sweeper) tdma_bwd_s64<8>(d, 2 * TL, F64 + l, hy, TL, hy, ny - 2, v);
+      split(ny - hy);
+      if (sweeper) tdma_bwd_ff<8>(d, 2 * TL, F2 + l, hy, TL, hy, ny - 2, v);
       __syncthreads();
       stage64(a.fac64 + plane, 0, hy);
       landed();
-      if (sweeper) tdma_bwd_s64<8>(d, 2 * TL, F64 + l, 0, TL, 0, min(hy - 1, ny - 2), v);
+      split(hy);
+      if (sweeper) tdma_bwd_ff<8>(d, 2 * TL, F2 + l, 0, TL, 0, min(hy - 1, ny - 2), v);
     } else if (sweeper) {
       tdma_line32_ip<8>(d, 2 * TL, IP + l, TL, ROWS, ny);
     }
@@ -1670,7 +1715,7 @@ cudaError_t emit_tdmam(LaunchSink& s) {
   if (c->pois_tiles)  // staged: the FP64 tiles, then the FP32 ones, in one launch
     return emit<TdmaSK>(s,
                         TdmaSK::Args{sp32(c), reinterpret_cast<const double*>(c->pois), c->pois_f32, c->pois_rows32,
-                                     c->gc + GC_PA * (q.ny + 1), c->pois_tiles, c->ntile64, q.nx, q.ny, c->nzh},
+                                     c->pois_tiles, c->ntile64, q.nx, q.ny, c->nzh},
                         dim3((unsigned)(c->ntile64 + c->ntile32)), dim3(TdmaSK::kThreads), TdmaSK::smem_bytes(q.ny));
   return emit<TdmaMK>(s, TdmaMK::Args{sp32(c), c->pois, c->gc, q.nx, q.ny, c->nzh, c->pois_f32, c->pois_pa32, c->pois_mode},
                       dim3((2 * q.nx + 127) / 128, c->nzh), dim3(128), 0);

@@ -504,12 +504,13 @@ ns_status ns_init(ns_ctx** out, const ns_config* cfg, const ns_fields* fields, v
     if (c->pois32) {  // the same tables rounded to float for the FP32 transforms of the mixed form
       const std::vector<float> fz(tw.begin(), tw.end()), fx(tx.begin(), tx.end()), fd(td.begin(), td.end());
       const std::vector<float> pa32(gc.begin() + (size_t)GC_PA * G, gc.begin() + (size_t)GC_PA * G + ny);
-      std::vector<float> rows32(4 * (size_t)ny, 0.0f);  // (a_j, c_j, -(a_j + c_j), 0)
+      std::vector<float> rows32(4 * (size_t)ny, 0.0f);  // (a_j, c_j, -(a_j + c_j), a_j - (float)a_j)
       for (int j = 0; j < ny; ++j) {
         const double aj = gc[(size_t)GC_PA * G + j], cj = gc[(size_t)GC_PC * G + j];
         rows32[4 * j] = (float)aj;
         rows32[4 * j + 1] = (float)cj;
         rows32[4 * j + 2] = (float)(-(aj + cj));
+        rows32[4 * j + 3] = (float)(aj - (double)(float)aj);
       }
       if (upload_raw(c, c->pois_rows32, rows32.data(), rows32.size() * 4) != cudaSuccess ||
           upload_raw(c, c->twz32, fz.data(), fz.size() * 4) != cudaSuccess ||

@@ -258,7 +258,8 @@ struct ns_ctx {
   // null: the register form
   int* pois_tiles = nullptr;
   int ntile32 = 0, ntile64 = 0;
-  // the staged FP32 sweeps' rows (a_j, c_j, -(a_j + c_j), 0) in float (they form c/pivot)
+  // the staged y solve's rows (a_j, c_j, -(a_j + c_j), a_j - (float)a_j) in float: the FP32
+  // sweeps form c/pivot from them, the FP64 tiles take a_j as a float-float pair
   float4* pois_rows32 = nullptr;
   double* flux;             // [0]: inflow flux, [1]: last outflow correction (diagnostics)
   unsigned long long* rate; // bits of the convective rate of ns_convective_rate (in the flux block)
