@@ -70,3 +70,79 @@ def thomas32(a, b, c, d, cp_from_ip=False):
     for j in range(ny - 2, -1, -1):
         x[..., j] = x[..., j] - cp[..., j] * x[..., j + 1]
     return x
+
+
+def _fma32(a, b, c):
+    """a b + c rounded once to float (float inputs: the product is exact in float64)."""
+    return np.float32(np.float64(a) * np.float64(b) + np.float64(c))
+
+
+def _ff_norm(s, e):
+    h = np.float32(s + e)
+    return h, np.float32(e - np.float32(h - s))
+
+
+def _ff_mul(a, b):
+    p = np.float32(a[0] * b[0])
+    e = _fma32(a[0], b[0], -p)
+    e = _fma32(a[0], b[1], _fma32(a[1], b[0], e))
+    return _ff_norm(p, e)
+
+
+def _ff_sub(x, b):
+    s = np.float32(x - b[0])
+    bb = np.float32(s - x)
+    e = np.float32(np.float32(x - np.float32(s - bb)) + np.float32(-b[0] - bb))
+    return _ff_norm(s, np.float32(e - b[1]))
+
+
+def _ff_split(x):
+    h = np.float32(x)
+    return h, np.float32(x - np.float64(h))
+
+
+def thomas_ff(a, b, c, d):
+    """The staged form's sweep of an FP64 mode in float-float arithmetic, one real line: factors
+    1/pivot and c/pivot formed in FP64 and split into two floats, a_j split likewise, the
+    recurrences carried as float pairs, every row stored rounded to float (the spectrum is
+    float).  a, b, c, d: (ny,) real; returns float32 (ny,)."""
+    ny = len(d)
+    ip, cp = np.empty(ny), np.empty(ny)
+    prev = 0.0
+    for j in range(ny):
+        ip[j] = 1.0 / (b[j] - a[j] * prev)
+        prev = c[j] * ip[j]
+        cp[j] = prev
+    out = np.empty(ny, np.float32)
+    p = (np.float32(0), np.float32(0))
+    for j in range(ny):
+        p = _ff_mul(_ff_sub(np.float32(d[j]), _ff_mul(_ff_split(a[j]), p)), _ff_split(ip[j]))
+        out[j] = p[0]
+    n = p
+    for j in range(ny - 2, -1, -1):
+        n = _ff_sub(out[j], _ff_mul(_ff_split(cp[j]), n))
+        out[j] = n[0]
+    return out
+
+
+def thomas64_stored32(a, b, c, d):
+    """The same sweep in FP64 arithmetic with every row stored rounded to float (the FP64-mode
+    sweep of the register form)."""
+    ny = len(d)
+    ip, cp = np.empty(ny), np.empty(ny)
+    prev = 0.0
+    for j in range(ny):
+        ip[j] = 1.0 / (b[j] - a[j] * prev)
+        prev = c[j] * ip[j]
+        cp[j] = prev
+    out = np.empty(ny, np.float32)
+    p = 0.0
+    for j in range(ny):
+        p = (np.float64(np.float32(d[j])) - a[j] * p) * ip[j]
+        out[j] = np.float32(p)
+    n = p
+    for j in range(ny - 2, -1, -1):
+        n = np.float64(out[j]) - cp[j] * n
+        out[j] = np.float32(n)
+    return out
+

@@ -115,3 +115,36 @@ def test_skeel_condition_by_one_solve_and_fp32_line_solves(bl):
             assert e2 < (1e-11 if k1 > PM.KAPPA_MAX else 1e-12), (kz, kx, from_ip, e2)
     assert all(k0 > k1 for k0, k1 in zip(kaps, kaps[1:]))
     assert kaps[0] > 1e4 and kaps[-1] < PM.KAPPA_MAX
+
+
+@pytest.mark.parametrize("bl", [False, True])
+def test_float_float_sweep_of_the_fp64_modes(bl):
+    """The staged form sweeps its FP64 modes (kz = 0 and Skeel condition > 4096) in float-float
+    arithmetic: on those modes of the stretched channel and boundary-layer grids its error on a
+    random right-hand side stays within 1.5 times that of the FP64-arithmetic sweep (both store
+    the rows in float), before and after one refinement on the FP64 residual (the refined error
+    of a mode is set by its conditioning and the float rows, the same for both)."""
+    if bl:
+        g = O.Grid.from_case(I.boundary_layer_case(1024, 256, 512))
+    else:
+        g = O.Grid(256, 192, 256, 2 * math.pi, math.pi, I.channel_faces(192, 2.0))
+    a, c = O.poisson_ycoeffs(g)
+    lam = PM.mode_lambdas(g, bl)
+    rng = np.random.default_rng(11)
+    for kz, kx in [(0, 1), (0, 7), (1, 0), (1, 1), (2, 2)]:
+        L = lam[kz, kx]
+        if kz > 0:
+            assert PM.skeel(a, c, np.array([L]))[0] > PM.KAPPA_MAX  # an FP64 mode
+        B = -(a + c) - L
+        A = np.diag(B) + np.diag(a[1:], -1) + np.diag(c[:-1], 1)
+        d = rng.standard_normal(g.ny).astype(np.float32).astype(np.float64)
+        x = np.linalg.solve(A, d)
+        err = lambda y: np.abs(y - x).max() / np.abs(x).max()
+        xf = PM.thomas_ff(a, B, c, d).astype(np.float64)
+        x6 = PM.thomas64_stored32(a, B, c, d).astype(np.float64)
+        assert err(xf) <= 1.5 * err(x6) + 1e-12, (kz, kx, err(xf), err(x6))
+        x2 = xf + PM.thomas_ff(a, B, c, d - A @ xf).astype(np.float64)
+        y2 = x6 + PM.thomas64_stored32(a, B, c, d - A @ x6).astype(np.float64)
+        assert err(x2) <= 1.5 * err(y2) + 1e-14, (kz, kx, err(x2), err(y2))
+        assert err(x2) < 1e-2 * err(xf), (kz, kx, err(x2), err(xf))
+
