@@ -280,7 +280,9 @@ enum {
                                                    the Skeel condition number of its y matrix
                                                    <= 4096), 0 where it runs in FP64.  With nx
                                                    a multiple of 16 the solve goes by tiles of 16
-                                                   kx, in FP32 only where all 16 flags are 1.
+                                                   kx, in FP32 only where all 16 flags are 1, the
+                                                   other tiles in float-float arithmetic (about
+                                                   48 bits) from the FP64 factors.
                                                    NS_ERR_UNSUPPORTED for an FP64 context */
 };
 ns_status ns_get_buffer(ns_ctx* ctx, int which, void** ptr, size_t* bytes);
