@@ -1,9 +1,8 @@
 """The Poisson solve of the mixed form (FP32 transforms, FP64 right-hand side, y solves in FP32
 arithmetic on the well-conditioned modes and in FP64 on the rest (float-float in the staged
-tiles), one refinement on the FP64
-residual) against the FP64 oracle: phi, the projected fields and the divergence, for periodic and
-inflow / outflow x, power-of-two and radix-3 sizes, and a right-hand side dominated by the lowest
-wavenumbers; and the per-mode choice of arithmetic."""
+tiles), one refinement on the FP64 residual) against the FP64 oracle: phi, the projected fields
+and the divergence, for periodic and inflow / outflow x, power-of-two and radix-3 sizes, and a
+right-hand side dominated by the lowest wavenumbers; and the per-mode choice of arithmetic."""
 import math
 
 import numpy as np
